@@ -1,0 +1,240 @@
+/*
+ * rbmd.h -- C ABI of the B300 random-batch nonbonded step (arXiv 2407.09315).
+ *
+ * The library computes, for N point charges with Lennard-Jones types in a cubic
+ * periodic box of side L (Sec. 2.2: neutral system, V = L^3):
+ *   - the random batch Ewald (RBE) long-range force (Sec. 2.2, Eq. 12,
+ *     Algorithm 1): P Fourier modes k = 2 pi m / L, m != 0, drawn i.i.d. with
+ *     probability exp(-k^2/4 alpha)/S, the structure factors
+ *     rho(k) = sum_j q_j exp(i k.r_j) (Eq. 9), and
+ *     F_i = -sum_l (S/P) 4 pi coulomb_k q_i k_l / (V k_l^2) Im(e^{-i k_l.r_i} rho_l);
+ *   - the random batch list (RBL) short-range force (Sec. 2.3, Eqs. 13-16,
+ *     Algorithm 2): an exact core list (r < r_core), a reweighted random batch of
+ *     p shell neighbours (r_core <= r <= r_cut, weight N_s/p), erfc-Coulomb
+ *     (Eq. 10) plus Lennard-Jones (Eq. 2, Lorentz-Berthelot mixing Eq. 4), and
+ *     the momentum correction F_corr = -(1/N) sum_i (F_core + F_shell*) (Eq. 16);
+ *   - velocity-Verlet with an optional Berendsen thermostat (Sec. 2.1).
+ *
+ * Naming: r_core is the paper's inner radius r_c and r_cut its outer radius r_s.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" must be device memory of the context's GPU
+ *     (for example torch CUDA tensors); "host" marks host memory; "host or
+ *     device" accepts either (copied with cudaMemcpyDefault under unified
+ *     addressing; pinned host memory keeps the copy asynchronous).
+ *   - Real-valued arrays are float for RBMD_FP32 contexts and double for
+ *     RBMD_FP64 contexts ("real" below).  Vectors are [N][3], row-major,
+ *     in the caller's atom order (atom id = row index).
+ *   - The caller owns every buffer it passes; rbmd_init copies the inputs into
+ *     the context's own layout and the context owns all its device state.
+ *   - Work is queued on the stream given to rbmd_init.  Calls that return host
+ *     values (rbmd_energy, rbmd_get_state, rbmd_sync, rbmd_rbe_modes) wait for
+ *     the stream; the others return as soon as the work is queued.
+ *   - Errors are returned, never raised or aborted on.  Device-side faults
+ *     (non-finite forces, timeouts) are latched in a device error word and
+ *     returned by the next call that synchronises.
+ *   - `step` keys every random draw (RBE modes and RBL batches): the same state
+ *     and step give bit-identical results.
+ *   - A context is not thread-safe; use one context per stream.
+ */
+#ifndef RBMD_H
+#define RBMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbmd_ctx rbmd_ctx;
+
+typedef enum {
+    RBMD_OK = 0,
+    RBMD_ERR_INVALID = 1,        /* bad argument or parameter */
+    RBMD_ERR_NOT_NEUTRAL = 2,    /* |sum q| > 1e-6 * sum |q| (Sec. 2.2 needs neutrality) */
+    RBMD_ERR_BOX_TOO_SMALL = 3,  /* r_cut >= L/2: minimum image not unique */
+    RBMD_ERR_OOM = 4,            /* a device allocation failed */
+    RBMD_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    RBMD_ERR_CELL_OVERFLOW = 6,  /* a cell or list exceeded its capacity */
+    RBMD_ERR_NONFINITE = 7,      /* a force or velocity became NaN/Inf */
+    RBMD_ERR_TIMEOUT = 8,        /* a bounded device wait gave up */
+    RBMD_ERR_UNSUPPORTED = 9     /* combination of options not built */
+} rbmd_status;
+
+typedef enum { RBMD_FP32 = 0, RBMD_FP64 = 1 } rbmd_precision;
+
+/* rbmd_params.flags */
+#define RBMD_FULL_EWALD_MODES 1u /* RBE uses every m != 0 with |m_d| <= M and weights
+                                    exp(-k^2/4 alpha): the Ewald series of Eq. 11 */
+#define RBMD_RBL_EXACT 2u        /* RBL keeps every shell neighbour with weight 1 */
+#define RBMD_NO_RBE 4u           /* skip the long-range part (LJ-fluid runs) */
+#define RBMD_NO_RBL 8u           /* skip the short-range part */
+
+typedef struct {
+    int64_t n_atoms;     /* N >= 1 */
+    int32_t n_types;     /* LJ types, 1..64 */
+    int32_t rbe_P;       /* RBE batch size P >= 1 (Eq. 12) */
+    double box_length;   /* L > 0 */
+    double alpha;        /* splitting parameter of Eq. 6 (erfc(sqrt(alpha) r)) */
+    double r_core;       /* inner radius (paper r_c), 0 <= r_core <= r_cut */
+    double r_cut;        /* outer radius (paper r_s), r_cut < L/2 */
+    int32_t rbl_p;       /* RBL shell batch size p, 1..128 (Eq. 15) */
+    int32_t thermostat;  /* 0 none (NVE), 1 Berendsen */
+    double coulomb_k;    /* Coulomb prefactor (1/(4 pi eps0) of Eq. 3; Bjerrum length in reduced units) */
+    double dt;           /* time step */
+    double temperature;  /* Berendsen target T0 (k_B = 1) */
+    double tau_T;        /* Berendsen coupling time; <= 0 selects 0.1 */
+    uint64_t seed;       /* Philox key of every random draw */
+    uint32_t replica;    /* replica index mixed into the random streams */
+    int32_t precision;   /* rbmd_precision */
+    uint32_t flags;      /* RBMD_* flags above */
+    int32_t cell_div;    /* cells per r_cut along each axis: 1 or 2; 0 = autotune */
+} rbmd_params;
+
+/* Energies and diagnostics (host, FP64).  Potential terms follow Eq. 8 with the
+ * random-batch estimators: e_rbe = coulomb_k (2 pi S/(V P)) sum_l |rho_l|^2/k_l^2
+ * (unbiased for Eq. 8's long-range term), e_coul_real and e_lj use the RBL list
+ * with 1/2 sum_i [sum_{C(i)} u_ij + (N_s/p) sum_{B(i)} u_ij]. */
+typedef struct {
+    double e_coul_real;   /* erfc-Coulomb over the RBL lists */
+    double e_lj;          /* Lennard-Jones over the RBL lists */
+    double e_rbe;         /* RBE estimate of the Fourier-space energy */
+    double e_self;        /* -coulomb_k sqrt(alpha/pi) sum q^2 */
+    double e_potential;   /* sum of the four terms above */
+    double e_kinetic;     /* 1/2 sum v^2 (unit masses) */
+    double temperature;   /* 2 KE / (3N - 3) */
+    double S;             /* normaliser sum_{m != 0} exp(-k^2/4 alpha) */
+    double fsum_short[3]; /* sum_i (F_core + F_shell*) before the correction */
+    int64_t step;         /* step the energies were evaluated at */
+    int32_t max_shell;    /* largest N_s over atoms */
+    int32_t max_cell;     /* largest cell occupancy */
+} rbmd_energy_terms;
+
+/* Name of a status code (static string). */
+const char *rbmd_status_string(rbmd_status s);
+
+/* Library version string (static). */
+const char *rbmd_version(void);
+
+/*
+ * rbmd_init -- create a context (Sec. 2.1 workflow: read the configuration,
+ * map the particle arrays to the device).
+ *   params   host, read once.
+ *   pos      device, real [N][3]; wrapped into [0, L) and stored as 32-bit
+ *            fixed-point fractions u = floor(x * 2^32 / L).
+ *   vel      device, real [N][3], or NULL for zero velocities.
+ *   charge   device, real [N]; must be neutral (RBMD_ERR_NOT_NEUTRAL).
+ *   type     device, int32 [N] in [0, n_types), or NULL for all type 0.
+ *   lj_eps, lj_sigma  host, double [n_types]; mixed by Lorentz-Berthelot (Eq. 4).
+ *   stream   cudaStream_t to queue all work on (NULL = legacy default stream).
+ *   out      receives the context; NULL on error.
+ * Errors: INVALID (bad sizes, r_core > r_cut, p or P out of range, bad type),
+ * BOX_TOO_SMALL (r_cut >= L/2), NOT_NEUTRAL, OOM, CUDA.
+ */
+rbmd_status rbmd_init(const rbmd_params *params, const void *pos, const void *vel,
+                      const void *charge, const int32_t *type, const double *lj_eps,
+                      const double *lj_sigma, void *stream, rbmd_ctx **out);
+
+/* Free every device buffer of the context (waits for its stream). NULL is a no-op. */
+void rbmd_destroy(rbmd_ctx *ctx);
+
+/*
+ * rbmd_rbe_forces -- RBE long-range force of the current positions, Eq. 12 and
+ * Algorithm 1: draw the P modes of `step` on the device, reduce rho(k_l) over all
+ * N charges, then F_i for every atom.
+ *   force      device, real [N][3]; overwritten, or added to when accumulate != 0.
+ * With RBMD_FULL_EWALD_MODES the full Ewald Fourier force of Eq. 11 is computed.
+ */
+rbmd_status rbmd_rbe_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumulate);
+
+/*
+ * rbmd_rbl_forces -- RBL short-range force, Eqs. 13-16 and Algorithm 2: cell
+ * binning, exact core list, a random batch of p shell neighbours of `step`
+ * weighted N_s/p, erfc-Coulomb + LJ pair forces and the momentum correction of
+ * Eq. 16 added to every atom.
+ *   force      device, real [N][3]; overwritten, or added to when accumulate != 0.
+ */
+rbmd_status rbmd_rbl_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumulate);
+
+/* rbmd_forces -- RBE + RBL (with correction) in one call; same arguments. */
+rbmd_status rbmd_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumulate);
+
+/*
+ * rbmd_step -- advance n_steps velocity-Verlet steps (Sec. 2.1): half kick,
+ * drift of the fixed-point positions (wrapping is modular), forces of the new
+ * configuration keyed by the new step number, half kick, Berendsen rescale.
+ * The context's step counter advances by n_steps.  Queued as one CUDA graph per
+ * step after the first call.
+ */
+rbmd_status rbmd_step(rbmd_ctx *ctx, int64_t n_steps);
+
+/*
+ * rbmd_energy -- energies and diagnostics of the current state, with the random
+ * draws of `step` (out: host).  Synchronises; returns a latched device error.
+ */
+rbmd_status rbmd_energy(rbmd_ctx *ctx, int64_t step, rbmd_energy_terms *out);
+
+/*
+ * rbmd_energy_backward -- gradients of E = e_coul_real + e_lj + e_rbe + e_self
+ * (rbmd_energy's potential, draws of `step`) times grad_out.
+ *   d_pos    device, real [N][3], dE/dr (or NULL)
+ *   d_q      device, real [N], dE/dq (or NULL)
+ *   d_eps    host, double [n_types], dE/d eps_t (or NULL)
+ *   d_sigma  host, double [n_types], dE/d sigma_t (or NULL)
+ * The RBL energy weights a pair by its list weight, so dE/dr is the
+ * symmetrised force -(1/2) sum_j (W_ij + W_ji) u'(r_ij) r_hat (the paper's
+ * one-sided RBL force is not a gradient); with RBMD_RBL_EXACT it equals -F.
+ * Synchronises when d_eps or d_sigma is requested.
+ */
+rbmd_status rbmd_energy_backward(rbmd_ctx *ctx, int64_t step, double grad_out, void *d_pos,
+                                 void *d_q, double *d_eps, double *d_sigma);
+
+/* Checkpoint: positions (real [N][3], decoded x = u L / 2^32), velocities
+ * (real [N][3]) and the step counter.  Buffers host or device. get_state
+ * synchronises. */
+rbmd_status rbmd_get_state(rbmd_ctx *ctx, void *pos, void *vel, int64_t *step);
+rbmd_status rbmd_set_state(rbmd_ctx *ctx, const void *pos, const void *vel, int64_t step);
+
+/* Exact checkpoint: fixed-point positions u (uint32 [N][3]), velocities
+ * (real [N][3], or NULL to keep them) and the step counter.  Host or device
+ * buffers.  A save + load round trip is bit-identical. */
+rbmd_status rbmd_get_state_u(rbmd_ctx *ctx, uint32_t *u, void *vel, int64_t *step);
+rbmd_status rbmd_set_state_u(rbmd_ctx *ctx, const uint32_t *u, const void *vel, int64_t step);
+
+/* Wait for the stream and return (then clear) the latched device error. */
+rbmd_status rbmd_sync(rbmd_ctx *ctx);
+
+/*
+ * Inspection of the random draws, for verification.
+ * rbmd_rbe_modes: the P modes m_l of `step` (host int32 [P][3], or NULL) and the
+ *   structure factors rho_l (host double [P][2] = re, im, or NULL), reduced on the
+ *   device in the context's precision.  In full-Ewald mode P is the full mode count
+ *   (rbmd_rbe_mode_count).  Synchronises.
+ * rbmd_rbl_lists: per atom (caller order) the core count |C(i)|, shell count N_s,
+ *   and the batch B(i) as atom ids ascending, -1 padded (device int32 [N], [N],
+ *   [N][p]; any may be NULL).
+ */
+int64_t rbmd_rbe_mode_count(rbmd_ctx *ctx);
+rbmd_status rbmd_rbe_modes(rbmd_ctx *ctx, int64_t step, int32_t *m, double *rho);
+rbmd_status rbmd_rbl_lists(rbmd_ctx *ctx, int64_t step, int32_t *n_core, int32_t *n_shell,
+                           int32_t *batch);
+
+/*
+ * rbmd_sampler_table -- host-side inverse-CDF thresholds of the per-dimension
+ * sampler (Eq. 12 density factorises as prod_d exp(-a m_d^2), a = pi^2/(alpha L^2)):
+ * M = ceil(sqrt(ln(1e16)/a)); T[j] = min(2^64-1, floor(CDF_j 2^64)), j = 0..2M.
+ * Call with T == NULL to get M; T must hold 2M+1 entries.  H (may be NULL)
+ * receives sum_{|m|<=M} exp(-a m^2), so S = H^3 - 1.
+ */
+rbmd_status rbmd_sampler_table(double box_length, double alpha, int32_t *M, uint64_t *T,
+                               double *H);
+
+/* Device error word injection for failure-path tests: sets the latched error to
+ * `code` exactly as a kernel would. */
+rbmd_status rbmd_debug_latch_error(rbmd_ctx *ctx, int32_t code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBMD_H */
