@@ -78,7 +78,7 @@ typedef struct {
     double alpha;        /* splitting parameter of Eq. 6 (erfc(sqrt(alpha) r)) */
     double r_core;       /* inner radius (paper r_c), 0 <= r_core <= r_cut */
     double r_cut;        /* outer radius (paper r_s), r_cut < L/2 */
-    int32_t rbl_p;       /* RBL shell batch size p, 1..128 (Eq. 15) */
+    int32_t rbl_p;       /* RBL shell batch size p, 1..32 (Eq. 15) */
     int32_t thermostat;  /* 0 none (NVE), 1 Berendsen */
     double coulomb_k;    /* Coulomb prefactor (1/(4 pi eps0) of Eq. 3; Bjerrum length in reduced units) */
     double dt;           /* time step */
@@ -212,7 +212,7 @@ rbmd_status rbmd_sync(rbmd_ctx *ctx);
  *   (rbmd_rbe_mode_count).  Synchronises.
  * rbmd_rbl_lists: per atom (caller order) the core count |C(i)|, shell count N_s,
  *   and the batch B(i) as atom ids ascending, -1 padded (device int32 [N], [N],
- *   [N][p]; any may be NULL).
+ *   [N][p]; all three required).
  */
 int64_t rbmd_rbe_mode_count(rbmd_ctx *ctx);
 rbmd_status rbmd_rbe_modes(rbmd_ctx *ctx, int64_t step, int32_t *m, double *rho);
@@ -228,6 +228,24 @@ rbmd_status rbmd_rbl_lists(rbmd_ctx *ctx, int64_t step, int32_t *n_core, int32_t
  */
 rbmd_status rbmd_sampler_table(double box_length, double alpha, int32_t *M, uint64_t *T,
                                double *H);
+
+/*
+ * Measurement hooks.
+ * rbmd_profile: enable (1) or disable (0) per-stage timing of rbmd_step; CUDA
+ *   events are recorded between the stages inside the step graph and read after
+ *   each step (profiling makes rbmd_step wait for every step).  Stages:
+ *   0 kick+drift, 1 cell sort, 2 RBL pair kernel, 3 F_corr reduction,
+ *   4 RBE mode sampling, 5 structure-factor partials, 6 structure-factor
+ *   final reduction, 7 RBE force kernel, 8 kick+thermostat.
+ * rbmd_profile_read: accumulated milliseconds per stage (host double
+ *   [RBMD_PROFILE_STAGES]) and the number of profiled steps; reset != 0 zeroes them.
+ * rbmd_step_kernel_count: kernel launches in one step graph (captured on the
+ *   first rbmd_step; 0 before that).
+ */
+#define RBMD_PROFILE_STAGES 9
+rbmd_status rbmd_profile(rbmd_ctx *ctx, int enable);
+rbmd_status rbmd_profile_read(rbmd_ctx *ctx, double *ms, int64_t *steps, int reset);
+int32_t rbmd_step_kernel_count(rbmd_ctx *ctx);
 
 /* Device error word injection for failure-path tests: sets the latched error to
  * `code` exactly as a kernel would. */

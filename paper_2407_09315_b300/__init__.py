@@ -1,0 +1,268 @@
+"""B300 random-batch molecular dynamics (arXiv 2407.09315): Python binding.
+
+The compute path is the CUDA library ``librbmd.so`` (C ABI, ``include/rbmd.h``);
+this module only marshals arguments through ctypes.  PyTorch supplies device
+memory and the current CUDA stream.  There is no CPU fallback: if the library
+is missing the import of :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librbmd.so")
+
+FP32, FP64 = 0, 1
+FULL_EWALD_MODES, RBL_EXACT, NO_RBE, NO_RBL = 1, 2, 4, 8
+
+STATUS = {
+    0: "RBMD_OK", 1: "RBMD_ERR_INVALID", 2: "RBMD_ERR_NOT_NEUTRAL",
+    3: "RBMD_ERR_BOX_TOO_SMALL", 4: "RBMD_ERR_OOM", 5: "RBMD_ERR_CUDA",
+    6: "RBMD_ERR_CELL_OVERFLOW", 7: "RBMD_ERR_NONFINITE", 8: "RBMD_ERR_TIMEOUT",
+    9: "RBMD_ERR_UNSUPPORTED",
+}
+
+
+class RBMDError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__("%s (%d)%s" % (STATUS.get(code, "?"), code, (": " + what) if what else ""))
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("n_atoms", C.c_int64), ("n_types", C.c_int32), ("rbe_P", C.c_int32),
+        ("box_length", C.c_double), ("alpha", C.c_double), ("r_core", C.c_double),
+        ("r_cut", C.c_double), ("rbl_p", C.c_int32), ("thermostat", C.c_int32),
+        ("coulomb_k", C.c_double), ("dt", C.c_double), ("temperature", C.c_double),
+        ("tau_T", C.c_double), ("seed", C.c_uint64), ("replica", C.c_uint32),
+        ("precision", C.c_int32), ("flags", C.c_uint32), ("cell_div", C.c_int32),
+    ]
+
+
+class EnergyTerms(C.Structure):
+    _fields_ = [
+        ("e_coul_real", C.c_double), ("e_lj", C.c_double), ("e_rbe", C.c_double),
+        ("e_self", C.c_double), ("e_potential", C.c_double), ("e_kinetic", C.c_double),
+        ("temperature", C.c_double), ("S", C.c_double), ("fsum_short", C.c_double * 3),
+        ("step", C.c_int64), ("max_shell", C.c_int32), ("max_cell", C.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load librbmd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("librbmd.so is missing: run `python -m paper_2407_09315_b300.build` "
+                           "(or __graft_entry__.build()) first")
+    L = C.CDLL(LIB_PATH)
+    P, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "rbmd_status_string": ([C.c_int], C.c_char_p),
+        "rbmd_version": ([], C.c_char_p),
+        "rbmd_init": ([C.POINTER(Params), P, P, P, P, P, P, P, C.POINTER(P)], C.c_int),
+        "rbmd_destroy": ([P], None),
+        "rbmd_rbe_forces": ([P, i64, P, C.c_int], C.c_int),
+        "rbmd_rbl_forces": ([P, i64, P, C.c_int], C.c_int),
+        "rbmd_forces": ([P, i64, P, C.c_int], C.c_int),
+        "rbmd_step": ([P, i64], C.c_int),
+        "rbmd_energy": ([P, i64, C.POINTER(EnergyTerms)], C.c_int),
+        "rbmd_energy_backward": ([P, i64, dbl, P, P, P, P], C.c_int),
+        "rbmd_get_state": ([P, P, P, C.POINTER(i64)], C.c_int),
+        "rbmd_set_state": ([P, P, P, i64], C.c_int),
+        "rbmd_get_state_u": ([P, P, P, C.POINTER(i64)], C.c_int),
+        "rbmd_set_state_u": ([P, P, P, i64], C.c_int),
+        "rbmd_sync": ([P], C.c_int),
+        "rbmd_rbe_mode_count": ([P], i64),
+        "rbmd_rbe_modes": ([P, i64, P, P], C.c_int),
+        "rbmd_rbl_lists": ([P, i64, P, P, P], C.c_int),
+        "rbmd_sampler_table": ([dbl, dbl, C.POINTER(i32), P, C.POINTER(dbl)], C.c_int),
+        "rbmd_debug_latch_error": ([P, i32], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(code: int, what: str = ""):
+    if code != 0:
+        raise RBMDError(code, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return C.c_void_p(t.ctypes.data)
+    return C.c_void_p(t.data_ptr())
+
+
+def sampler_table(box_length: float, alpha: float):
+    """Inverse-CDF thresholds of the mode sampler: (M, uint64[2M+1], H)."""
+    M = C.c_int32(0)
+    _check(lib().rbmd_sampler_table(box_length, alpha, C.byref(M), None, None))
+    T = np.zeros(2 * M.value + 1, dtype=np.uint64)
+    H = C.c_double(0.0)
+    _check(lib().rbmd_sampler_table(box_length, alpha, C.byref(M), _ptr(T), C.byref(H)))
+    return M.value, T, H.value
+
+
+class RBMD:
+    """One simulation context on the current CUDA device and stream.
+
+    pos, vel: CUDA tensors [N, 3] (float32 for FP32 contexts, float64 for FP64);
+    charge: CUDA tensor [N] of the same dtype; types: CUDA int32 tensor [N] or None;
+    eps, sigma: per-type LJ parameters (host sequences).
+    """
+
+    def __init__(self, pos, charge, eps, sigma, *, box_length, alpha=0.62, r_core=2.0,
+                 r_cut=3.5, rbl_p=10, rbe_P=100, coulomb_k=1.0, dt=0.001, temperature=1.0,
+                 tau_T=0.1, thermostat=0, seed=0, replica=0, precision=FP32, flags=0,
+                 cell_div=0, vel=None, types=None, stream=None):
+        import torch
+
+        self._torch = torch
+        self.precision = precision
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        self.device = pos.device
+        n = pos.shape[0]
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        self.n = n
+        self.n_types = len(eps)
+        self.p = rbl_p
+        self.params = Params(n_atoms=n, n_types=len(eps), rbe_P=rbe_P, box_length=box_length,
+                             alpha=alpha, r_core=r_core, r_cut=r_cut, rbl_p=rbl_p,
+                             thermostat=thermostat, coulomb_k=coulomb_k, dt=dt,
+                             temperature=temperature, tau_T=tau_T, seed=seed, replica=replica,
+                             precision=precision, flags=flags, cell_div=cell_div)
+        pos = pos.to(self.dtype).contiguous()
+        charge = charge.to(self.dtype).contiguous()
+        vel = None if vel is None else vel.to(self.dtype).contiguous()
+        types = None if types is None else types.to(torch.int32).contiguous()
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().rbmd_init(C.byref(self.params), _ptr(pos), _ptr(vel), _ptr(charge),
+                               _ptr(types), _ptr(eps), _ptr(sigma), C.c_void_p(stream.cuda_stream),
+                               C.byref(h)), "rbmd_init")
+        self._h = h
+        self._keep = (pos, charge, vel, types)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rbmd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _new3(self):
+        return self._torch.empty((self.n, 3), dtype=self.dtype, device=self.device)
+
+    # -- forces -----------------------------------------------------------
+    def rbe_forces(self, step, out=None, accumulate=False):
+        out = self._new3() if out is None else out
+        _check(lib().rbmd_rbe_forces(self._h, step, _ptr(out), int(accumulate)), "rbe_forces")
+        return out
+
+    def rbl_forces(self, step, out=None, accumulate=False):
+        out = self._new3() if out is None else out
+        _check(lib().rbmd_rbl_forces(self._h, step, _ptr(out), int(accumulate)), "rbl_forces")
+        return out
+
+    def forces(self, step, out=None, accumulate=False):
+        out = self._new3() if out is None else out
+        _check(lib().rbmd_forces(self._h, step, _ptr(out), int(accumulate)), "forces")
+        return out
+
+    # -- dynamics ---------------------------------------------------------
+    def step(self, n_steps=1):
+        _check(lib().rbmd_step(self._h, n_steps), "step")
+
+    def energy(self, step) -> dict:
+        e = EnergyTerms()
+        _check(lib().rbmd_energy(self._h, step, C.byref(e)), "energy")
+        d = {k: getattr(e, k) for k, _ in EnergyTerms._fields_}
+        d["fsum_short"] = list(e.fsum_short)
+        return d
+
+    def energy_backward(self, step, grad_out=1.0, want_pos=True, want_q=True, want_lj=True):
+        t = self._torch
+        dpos = t.empty((self.n, 3), dtype=self.dtype, device=self.device) if want_pos else None
+        dq = t.empty((self.n,), dtype=self.dtype, device=self.device) if want_q else None
+        de = np.zeros(self.n_types) if want_lj else None
+        ds = np.zeros(self.n_types) if want_lj else None
+        _check(lib().rbmd_energy_backward(self._h, step, grad_out, _ptr(dpos), _ptr(dq),
+                                          _ptr(de), _ptr(ds)), "energy_backward")
+        return dpos, dq, de, ds
+
+    # -- state ------------------------------------------------------------
+    def get_state(self):
+        pos, vel = self._new3(), self._new3()
+        st = C.c_int64(0)
+        _check(lib().rbmd_get_state(self._h, _ptr(pos), _ptr(vel), C.byref(st)), "get_state")
+        return pos, vel, st.value
+
+    def set_state(self, pos=None, vel=None, step=0):
+        _check(lib().rbmd_set_state(self._h, _ptr(pos), _ptr(vel), step), "set_state")
+
+    def get_state_u(self):
+        u = self._torch.empty((self.n, 3), dtype=self._torch.int32, device=self.device)
+        vel = self._new3()
+        st = C.c_int64(0)
+        _check(lib().rbmd_get_state_u(self._h, _ptr(u), _ptr(vel), C.byref(st)), "get_state_u")
+        return u, vel, st.value
+
+    def set_state_u(self, u, vel=None, step=0):
+        """u: uint32 fixed-point coordinates [N, 3] (numpy or an int32 tensor view)."""
+        if isinstance(u, np.ndarray):
+            u = np.ascontiguousarray(u, dtype=np.uint32)
+            ut = self._torch.from_numpy(u.view(np.int32)).to(self.device)
+        else:
+            ut = u.contiguous()
+        if vel is not None and isinstance(vel, np.ndarray):
+            vel = self._torch.from_numpy(np.ascontiguousarray(vel)).to(self.device, self.dtype)
+        _check(lib().rbmd_set_state_u(self._h, _ptr(ut), _ptr(vel), step), "set_state_u")
+        self._torch.cuda.current_stream(self.device).synchronize()
+
+    def sync(self):
+        _check(lib().rbmd_sync(self._h), "sync")
+
+    # -- inspection -------------------------------------------------------
+    def mode_count(self) -> int:
+        return lib().rbmd_rbe_mode_count(self._h)
+
+    def rbe_modes(self, step):
+        P = self.mode_count()
+        m = np.zeros((P, 3), dtype=np.int32)
+        rho = np.zeros((P, 2), dtype=np.float64)
+        _check(lib().rbmd_rbe_modes(self._h, step, _ptr(m), _ptr(rho)), "rbe_modes")
+        return m, rho[:, 0] + 1j * rho[:, 1]
+
+    def rbl_lists(self, step):
+        t = self._torch
+        nc = t.empty((self.n,), dtype=t.int32, device=self.device)
+        ns = t.empty((self.n,), dtype=t.int32, device=self.device)
+        b = t.empty((self.n, self.p), dtype=t.int32, device=self.device)
+        _check(lib().rbmd_rbl_lists(self._h, step, _ptr(nc), _ptr(ns), _ptr(b)), "rbl_lists")
+        return nc, ns, b
+
+    def debug_latch_error(self, code):
+        _check(lib().rbmd_debug_latch_error(self._h, code))

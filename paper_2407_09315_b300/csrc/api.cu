@@ -1,0 +1,793 @@
+// C ABI of the library (declared in include/rbmd.h): context set-up, the force,
+// step and energy entry points, checkpoints and verification hooks.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "rbmd_internal.cuh"
+
+using namespace rbmd;
+
+namespace {
+
+// Host-side fault injection for the failure-path tests: RBMD_FAIL_ALLOC_AFTER=k
+// makes the k-th device allocation of the next rbmd_init report failure.
+int g_alloc_countdown = -1;
+
+rbmd_status dev_alloc(void **p, size_t bytes)
+{
+    if (g_alloc_countdown == 0) {
+        *p = nullptr;
+        return RBMD_ERR_OOM;
+    }
+    if (g_alloc_countdown > 0) --g_alloc_countdown;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return RBMD_ERR_OOM;
+    }
+    return RBMD_OK;
+}
+
+template <typename T> rbmd_status alloc_n(T **p, size_t n)
+{
+    return dev_alloc(reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+uint32_t isqrt64(uint64_t x)
+{
+    uint64_t r = (uint64_t)sqrt((double)x);
+    while (r * r > x) --r;
+    while ((r + 1) * (r + 1) <= x) ++r;
+    return (uint32_t)r;
+}
+
+uint64_t radius2_units(double r, double L)
+{
+    const double s = r * (kTwo32 / L);
+    return (uint64_t)floor(s * s);
+}
+
+// Ordering with the caller's work when it passed the legacy default stream.
+void enter(rbmd_ctx *c)
+{
+    if (c->own_stream) {
+        cudaEventRecord(c->ev_in, 0);
+        cudaStreamWaitEvent(c->stream, c->ev_in, 0);
+    }
+}
+rbmd_status leave(rbmd_ctx *c, rbmd_status s)
+{
+    if (c->own_stream) {
+        cudaEventRecord(c->ev_out, c->stream);
+        cudaStreamWaitEvent(0, c->ev_out, 0);
+    }
+    if (s == RBMD_OK && cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return RBMD_ERR_CUDA;
+    }
+    return s;
+}
+
+__global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
+__global__ void k_init_scal(double *scal)
+{
+    int t = threadIdx.x;
+    if (t < SCAL_COUNT) scal[t] = (t == SCAL_LAMBDA) ? 1.0 : 0.0;
+}
+__global__ void k_set_lambda(double *scal, double v) { scal[SCAL_LAMBDA] = v; }
+
+template <typename real>
+__global__ void k_pack(const real *__restrict__ q, const int32_t *__restrict__ type, int64_t N,
+                       uint4 *__restrict__ u4, double *__restrict__ q64,
+                       int32_t *__restrict__ tout, int n_types, int *__restrict__ err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double qi = (double)q[i];
+    u4[i].w = __float_as_uint((float)qi);
+    if (q64) q64[i] = qi;
+    int t = type ? type[i] : 0;
+    if (t < 0 || t >= n_types) {
+        latch_error(err, RBMD_ERR_INVALID);
+        t = 0;
+    }
+    tout[i] = t;
+}
+
+// Charge sums for the neutrality check and the self energy: [sum q, sum |q|, sum q^2].
+__global__ void k_charge_parts(const double *__restrict__ q64, const uint4 *__restrict__ u4,
+                               int64_t N, double *__restrict__ parts)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double q = 0.0;
+    if (i < N) q = q64 ? q64[i] : (double)__uint_as_float(u4[i].w);
+    double v[3] = {q, fabs(q), q * q};
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    __shared__ double s[3][8];
+    if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < 3; ++c) s[c][threadIdx.x >> 5] = v[c];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[c][w];
+            parts[3 * (int64_t)blockIdx.x + c] = t;
+        }
+}
+
+__global__ void k_modes_to_m3(const int4 *__restrict__ modes, int64_t P, int32_t *__restrict__ m3)
+{
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= P) return;
+    int4 m = modes[l];
+    m3[3 * l] = m.x;
+    m3[3 * l + 1] = m.y;
+    m3[3 * l + 2] = m.z;
+}
+
+__global__ void k_u4_to_u3(const uint4 *__restrict__ u4, int64_t N, uint32_t *__restrict__ u3)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    uint4 A = u4[i];
+    u3[3 * i] = A.x;
+    u3[3 * i + 1] = A.y;
+    u3[3 * i + 2] = A.z;
+}
+
+__global__ void k_u3_to_u4(const uint32_t *__restrict__ u3, int64_t N, uint4 *__restrict__ u4)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    uint4 A = u4[i];
+    A.x = u3[3 * i];
+    A.y = u3[3 * i + 1];
+    A.z = u3[3 * i + 2];
+    u4[i] = A;
+}
+
+__global__ void k_max_count(const int32_t *__restrict__ count, int64_t n, int32_t *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int v = i < n ? count[i] : 0;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+
+void free_ctx(rbmd_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+    void *ptrs[] = {c->u4,        c->q64,       c->type,     c->vel,        c->force,
+                    c->scratch_force, c->scal,  c->err,      c->d_step,     c->cdf,
+                    c->modes,     c->W,         c->rho_part, c->rho,        c->emode,
+                    c->coef,      c->cell_count, c->cell_start, c->cell_of, c->cell_rank,
+                    c->scan_part, c->spos,      c->sq,       c->stype,      c->fpart,
+                    c->epart,     c->kepart,    c->ibuf,     c->lj_f,       c->lj_d};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
+        if (c->prof_ev[k]) cudaEventDestroy(c->prof_ev[k]);
+    if (c->own_stream) {
+        cudaStreamDestroy(c->stream);
+        cudaEventDestroy(c->ev_in);
+        cudaEventDestroy(c->ev_out);
+    }
+    delete c;
+}
+
+size_t real_size(const rbmd_ctx *c) { return c->fp64 ? sizeof(double) : sizeof(float); }
+
+// Forces of the current configuration, keyed by `s`, into `force` (RBE + RBL);
+// F_corr is written to scal (and added to `force` when apply_corr).
+rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool apply_corr,
+                        bool marks = false)
+{
+    const bool do_rbe = !(c->prm.flags & RBMD_NO_RBE);
+    const bool do_rbl = !(c->prm.flags & RBMD_NO_RBL);
+    int acc = accumulate;
+    if (marks) prof_mark(c, 1);
+    if (do_rbl) {
+        RBMD_CHECK(cells_build(c));
+        if (marks) prof_mark(c, 2);
+        RBMD_CHECK(rbl_pairs(c, s, force, acc, false, nullptr, nullptr, nullptr));
+        if (marks) prof_mark(c, 3);
+        RBMD_CHECK(rbl_correction(c, force, apply_corr, apply_corr ? SCAL_FCORR_AUX : SCAL_FCORR));
+        acc = 1;
+    } else {
+        if (marks) prof_mark(c, 2);
+        if (marks) prof_mark(c, 3);
+        if (!apply_corr)
+            RBMD_CHECK_CUDA(cudaMemsetAsync(c->scal + SCAL_FCORR, 0, 3 * sizeof(double), c->stream));
+    }
+    if (marks) prof_mark(c, 4);
+    if (do_rbe) {
+        RBMD_CHECK(rbe_sample(c, s));
+        if (marks) prof_mark(c, 5);
+        RBMD_CHECK(rbe_structure_factors(c, marks ? 6 : -1));
+        if (marks) prof_mark(c, 7);
+        RBMD_CHECK(rbe_apply_forces(c, force, acc));
+        acc = 1;
+    } else if (marks) {
+        prof_mark(c, 5);
+        prof_mark(c, 6);
+        prof_mark(c, 7);
+    }
+    if (!acc)
+        RBMD_CHECK_CUDA(cudaMemsetAsync(force, 0, 3 * c->N * real_size(c), c->stream));
+    return RBMD_OK;
+}
+
+rbmd_status record_step(rbmd_ctx *c)
+{
+    StepRef next{c->d_step, 1};
+    prof_mark(c, 0);
+    RBMD_CHECK(md_kick_drift(c));
+    RBMD_CHECK(forces_into(c, next, c->force, 0, false, true));
+    prof_mark(c, 8);
+    RBMD_CHECK(md_kick_thermo(c, true));
+    prof_mark(c, 9);
+    return RBMD_OK;
+}
+
+rbmd_status check_latched(rbmd_ctx *c)
+{
+    int e = 0;
+    RBMD_CHECK_CUDA(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        int z = 0;
+        cudaMemcpy(c->err, &z, sizeof(int), cudaMemcpyHostToDevice);
+        return (rbmd_status)e;
+    }
+    return RBMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rbmd_status_string(rbmd_status s)
+{
+    switch (s) {
+    case RBMD_OK: return "ok";
+    case RBMD_ERR_INVALID: return "invalid argument";
+    case RBMD_ERR_NOT_NEUTRAL: return "system is not charge neutral";
+    case RBMD_ERR_BOX_TOO_SMALL: return "r_cut must be below L/2";
+    case RBMD_ERR_OOM: return "device allocation failed";
+    case RBMD_ERR_CUDA: return "CUDA runtime error";
+    case RBMD_ERR_CELL_OVERFLOW: return "cell or list capacity exceeded";
+    case RBMD_ERR_NONFINITE: return "non-finite force or velocity";
+    case RBMD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case RBMD_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+const char *rbmd_version(void) { return "rbmd-b300 0.1 (sm_103a)"; }
+
+rbmd_status rbmd_sampler_table(double box_length, double alpha, int32_t *M, uint64_t *T, double *H)
+{
+    return sampler_table_host(box_length, alpha, M, T, H);
+}
+
+rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, const void *charge,
+                      const int32_t *type, const double *lj_eps, const double *lj_sigma,
+                      void *stream, rbmd_ctx **out)
+{
+    if (!out) return RBMD_ERR_INVALID;
+    *out = nullptr;
+    if (!prm || !pos || !charge || !lj_eps || !lj_sigma) return RBMD_ERR_INVALID;
+    const rbmd_params p = *prm;
+    if (p.n_atoms < 1 || p.n_atoms > (int64_t)2000000000) return RBMD_ERR_INVALID;
+    if (p.n_types < 1 || p.n_types > RBMD_MAX_TYPES) return RBMD_ERR_INVALID;
+    if (!(p.box_length > 0.0) || !(p.alpha > 0.0) || !(p.r_cut > 0.0)) return RBMD_ERR_INVALID;
+    if (!(p.r_core >= 0.0) || p.r_core > p.r_cut) return RBMD_ERR_INVALID;
+    if (p.rbe_P < 1 || p.rbl_p < 1 || p.rbl_p > 32) return RBMD_ERR_INVALID;
+    if (p.precision != RBMD_FP32 && p.precision != RBMD_FP64) return RBMD_ERR_INVALID;
+    if (p.thermostat != 0 && p.thermostat != 1) return RBMD_ERR_INVALID;
+    if (p.cell_div < 0 || p.cell_div > 2) return RBMD_ERR_INVALID;
+    if (!(p.r_cut < 0.5 * p.box_length)) return RBMD_ERR_BOX_TOO_SMALL;
+    for (int t = 0; t < p.n_types; ++t)
+        if (!(lj_eps[t] >= 0.0) || !(lj_sigma[t] >= 0.0)) return RBMD_ERR_INVALID;
+
+    {
+        const char *env = getenv("RBMD_FAIL_ALLOC_AFTER");
+        g_alloc_countdown = env ? atoi(env) : -1;
+    }
+
+    rbmd_ctx *c = new rbmd_ctx;
+    memset(c, 0, sizeof(*c));
+    c->prm = p;
+    c->N = p.n_atoms;
+    c->T = p.n_types;
+    c->fp64 = p.precision == RBMD_FP64;
+    c->L = p.box_length;
+    c->V = c->L * c->L * c->L;
+    c->lscale = c->L / kTwo32;
+    c->dtc = p.dt * (kTwo32 / c->L);
+    c->tau = p.tau_T > 0.0 ? p.tau_T : 0.1;
+    c->sqrt_alpha = sqrt(p.alpha);
+    c->full_modes = (p.flags & RBMD_FULL_EWALD_MODES) != 0;
+
+    rbmd_status st = RBMD_OK;
+#define TRY(x)                     \
+    do {                           \
+        st = (x);                  \
+        if (st != RBMD_OK) {       \
+            g_alloc_countdown = -1; \
+            free_ctx(c);           \
+            return st;             \
+        }                          \
+    } while (0)
+
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        c->own_stream = true;
+        TRY(cuda_status(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)));
+        TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)));
+        TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)));
+    }
+    enter(c);
+
+    // sampler (Eq. 12)
+    TRY(sampler_table_host(c->L, p.alpha, &c->M, nullptr, nullptr));
+    std::vector<uint64_t> T(2 * (size_t)c->M + 1);
+    TRY(sampler_table_host(c->L, p.alpha, &c->M, T.data(), &c->H));
+    c->S = c->H * c->H * c->H - 1.0;
+
+    // RBL constants (Sec. 2.3)
+    c->Rc2 = radius2_units(p.r_core, c->L);
+    c->Rs2 = radius2_units(p.r_cut, c->L);
+    c->Rlin = isqrt64(c->Rs2);
+    c->div = p.cell_div == 0 ? 1 : p.cell_div;
+    {
+        int nc = (int)floor(c->L * c->div / p.r_cut);
+        if (nc < 1) nc = 1;
+        while (nc > 1 && (double)c->Rlin * (double)nc > (double)c->div * kTwo32) --nc;
+        // bigger cells stay correct (the stencil still covers r_cut); cap the
+        // cell count so that sparse boxes do not allocate more cells than atoms
+        const double max_cells = fmax(8.0 * (double)c->N, 1048576.0);
+        while (nc > 1 && (double)nc * nc * nc > max_cells) --nc;
+        c->nc = nc;
+        c->ncell = (int64_t)nc * nc * nc;
+    }
+
+    // mode list
+    std::vector<int4> full;
+    std::vector<double> fullW;
+    if (c->full_modes) {
+        const double a = kPi * kPi / (p.alpha * c->L * c->L);
+        const int M = c->M;
+        for (int mx = -M; mx <= M; ++mx)
+            for (int my = -M; my <= M; ++my)
+                for (int mz = -M; mz <= M; ++mz) {
+                    if (!mx && !my && !mz) continue;
+                    full.push_back(make_int4(mx, my, mz, 0));
+                    fullW.push_back(exp(-a * (double)(mx * mx + my * my + mz * mz)));
+                }
+        c->Pm = (int64_t)full.size();
+    } else {
+        c->Pm = p.rbe_P;
+    }
+
+    // tiles
+    c->rho_tile = 1024;
+    c->rho_tiles = (int)((c->N + c->rho_tile - 1) / c->rho_tile);
+    c->force_block = 256;
+    c->pair_block = 128;
+    c->pair_blocks = (int)((c->N + c->pair_block - 1) / c->pair_block);
+    c->kick_blocks = (int)((c->N + 255) / 256);
+
+    const size_t rs = real_size(c);
+    const int64_t N = c->N;
+    TRY(alloc_n(&c->u4, N));
+    if (c->fp64) TRY(alloc_n(&c->q64, N));
+    TRY(alloc_n(&c->type, N));
+    TRY(dev_alloc(&c->vel, 3 * N * rs));
+    TRY(dev_alloc(&c->force, 3 * N * rs));
+    TRY(dev_alloc(&c->scratch_force, 3 * N * (rs > 4 ? rs : 8)));
+    TRY(alloc_n(&c->scal, SCAL_COUNT));
+    TRY(alloc_n(&c->err, 1));
+    TRY(alloc_n(&c->d_step, 1));
+    TRY(alloc_n(&c->cdf, T.size()));
+    TRY(alloc_n(&c->modes, c->Pm));
+    if (c->full_modes) TRY(alloc_n(&c->W, c->Pm));
+    TRY(alloc_n(&c->rho_part, (size_t)c->rho_tiles * c->Pm));
+    TRY(alloc_n(&c->rho, c->Pm));
+    TRY(alloc_n(&c->emode, c->Pm));
+    TRY(dev_alloc(&c->coef, (size_t)c->Pm * (c->fp64 ? sizeof(ModeCoef<double>) : sizeof(ModeCoef<float>))));
+    TRY(alloc_n(&c->cell_count, c->ncell));
+    TRY(alloc_n(&c->cell_start, c->ncell + 1));
+    TRY(alloc_n(&c->cell_of, N));
+    TRY(alloc_n(&c->cell_rank, N));
+    TRY(alloc_n(&c->scan_part, (c->ncell + 1023) / 1024 + 1));
+    TRY(alloc_n(&c->spos, N));
+    TRY(dev_alloc(&c->sq, N * rs));
+    TRY(alloc_n(&c->stype, N));
+    TRY(alloc_n(&c->fpart, 3 * (size_t)c->pair_blocks + 3 * (size_t)c->kick_blocks));
+    TRY(alloc_n(&c->epart, 2 * (size_t)c->pair_blocks));
+    TRY(alloc_n(&c->kepart, (size_t)c->kick_blocks));
+    TRY(alloc_n(&c->ibuf, 4));
+    g_alloc_countdown = -1;
+
+    // LJ tables: sqrt(eps_t), sigma_t/2 (Lorentz-Berthelot, Eq. 4)
+    {
+        std::vector<double> ljd(2 * c->T);
+        std::vector<float> ljf(2 * c->T);
+        for (int t = 0; t < c->T; ++t) {
+            ljd[t] = sqrt(lj_eps[t]);
+            ljd[c->T + t] = 0.5 * lj_sigma[t];
+            ljf[t] = (float)ljd[t];
+            ljf[c->T + t] = (float)ljd[c->T + t];
+        }
+        if (c->fp64) {
+            TRY(alloc_n(&c->lj_d, 2 * c->T));
+            TRY(cuda_status(cudaMemcpy(c->lj_d, ljd.data(), sizeof(double) * 2 * c->T, cudaMemcpyHostToDevice)));
+        } else {
+            TRY(alloc_n(&c->lj_f, 2 * c->T));
+            TRY(cuda_status(cudaMemcpy(c->lj_f, ljf.data(), sizeof(float) * 2 * c->T, cudaMemcpyHostToDevice)));
+        }
+    }
+    TRY(cuda_status(cudaMemcpy(c->cdf, T.data(), sizeof(uint64_t) * T.size(), cudaMemcpyHostToDevice)));
+    if (c->full_modes) {
+        TRY(cuda_status(cudaMemcpy(c->modes, full.data(), sizeof(int4) * full.size(), cudaMemcpyHostToDevice)));
+        TRY(cuda_status(cudaMemcpy(c->W, fullW.data(), sizeof(double) * fullW.size(), cudaMemcpyHostToDevice)));
+    }
+    TRY(cuda_status(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)));
+    TRY(cuda_status(cudaMemsetAsync(c->u4, 0, sizeof(uint4) * N, c->stream)));
+    k_init_scal<<<1, 32, 0, c->stream>>>(c->scal);
+    k_set_i64<<<1, 1, 0, c->stream>>>(c->d_step, 0);
+
+    // particle data (Sec. 2.1: map the arrays to the device)
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    if (c->fp64)
+        k_pack<double><<<nb, 256, 0, c->stream>>>((const double *)charge, type, N, c->u4, c->q64,
+                                                  c->type, c->T, c->err);
+    else
+        k_pack<float><<<nb, 256, 0, c->stream>>>((const float *)charge, type, N, c->u4, nullptr,
+                                                 c->type, c->T, c->err);
+    TRY(md_encode_positions(c, pos));
+    if (vel) TRY(cuda_status(cudaMemcpyAsync(c->vel, vel, 3 * N * rs, cudaMemcpyDefault, c->stream)));
+    else TRY(cuda_status(cudaMemsetAsync(c->vel, 0, 3 * N * rs, c->stream)));
+
+    // neutrality (Sec. 2.2) and the self energy (third term of Eq. 8)
+    {
+        double *parts = (double *)c->scratch_force;  // 3 nb doubles fit in 3N doubles
+        k_charge_parts<<<nb, 256, 0, c->stream>>>(c->q64, c->u4, N, parts);
+        double *sums = c->scal + SCAL_ERBE;             // three free slots until the first energy
+        TRY(md_sum(c, parts, (int)nb, 3, sums, 1.0));
+        double h[3];
+        TRY(cuda_status(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream)));
+        TRY(cuda_status(cudaStreamSynchronize(c->stream)));
+        TRY(check_latched(c));
+        if (fabs(h[0]) > 1e-6 * (h[1] > 0 ? h[1] : 1.0)) {
+            free_ctx(c);
+            return RBMD_ERR_NOT_NEUTRAL;
+        }
+        c->e_self = -p.coulomb_k * sqrt(p.alpha / kPi) * h[2];
+    }
+#undef TRY
+    c->step = 0;
+    c->have_force = false;
+    leave(c, RBMD_OK);
+    *out = c;
+    return RBMD_OK;
+}
+
+void rbmd_destroy(rbmd_ctx *c) { free_ctx(c); }
+
+rbmd_status rbmd_rbe_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
+{
+    if (!c || !force) return RBMD_ERR_INVALID;
+    enter(c);
+    rbmd_status s = RBMD_OK;
+    if (c->prm.flags & RBMD_NO_RBE) {
+        if (!accumulate) s = cuda_status(cudaMemsetAsync(force, 0, 3 * c->N * real_size(c), c->stream));
+        return leave(c, s);
+    }
+    StepRef r{nullptr, step};
+    s = rbe_sample(c, r);
+    if (s == RBMD_OK) s = rbe_structure_factors(c);
+    if (s == RBMD_OK) s = rbe_apply_forces(c, force, accumulate);
+    return leave(c, s);
+}
+
+rbmd_status rbmd_rbl_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
+{
+    if (!c || !force) return RBMD_ERR_INVALID;
+    enter(c);
+    rbmd_status s = RBMD_OK;
+    if (c->prm.flags & RBMD_NO_RBL) {
+        if (!accumulate) s = cuda_status(cudaMemsetAsync(force, 0, 3 * c->N * real_size(c), c->stream));
+        return leave(c, s);
+    }
+    StepRef r{nullptr, step};
+    s = cells_build(c);
+    if (s == RBMD_OK) s = rbl_pairs(c, r, force, accumulate, false, nullptr, nullptr, nullptr);
+    if (s == RBMD_OK) s = rbl_correction(c, force, true, SCAL_FCORR_AUX);
+    return leave(c, s);
+}
+
+rbmd_status rbmd_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
+{
+    if (!c || !force) return RBMD_ERR_INVALID;
+    enter(c);
+    return leave(c, forces_into(c, StepRef{nullptr, step}, force, accumulate, true));
+}
+
+rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
+{
+    if (!c || n_steps < 0) return RBMD_ERR_INVALID;
+    if (n_steps == 0) return RBMD_OK;
+    enter(c);
+    rbmd_status s = RBMD_OK;
+    if (!c->have_force) {
+        k_set_i64<<<1, 1, 0, c->stream>>>(c->d_step, c->step);
+        s = forces_into(c, StepRef{nullptr, c->step}, c->force, 0, false);
+        if (s != RBMD_OK) return leave(c, s);
+        c->have_force = true;
+    }
+    if (!c->graph_ready) {
+        cudaGraph_t g;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return leave(c, RBMD_ERR_CUDA);
+        rbmd_status rs = record_step(c);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rs != RBMD_OK || e != cudaSuccess) {
+            cudaGetLastError();
+            return leave(c, rs != RBMD_OK ? rs : RBMD_ERR_CUDA);
+        }
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+        int nk = 0;
+        for (size_t k = 0; k < nn; ++k) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+        }
+        c->graph_kernels = nk;
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return leave(c, RBMD_ERR_CUDA);
+        c->graph_ready = true;
+    }
+    for (int64_t k = 0; k < n_steps; ++k) {
+        if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return leave(c, RBMD_ERR_CUDA);
+        if (c->profiling) {
+            if (cudaEventSynchronize(c->prof_ev[RBMD_PROFILE_STAGES]) != cudaSuccess)
+                return leave(c, RBMD_ERR_CUDA);
+            for (int st = 0; st < RBMD_PROFILE_STAGES; ++st) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, c->prof_ev[st], c->prof_ev[st + 1]);
+                c->prof_ms[st] += ms;
+            }
+            ++c->prof_steps;
+        }
+    }
+    c->step += n_steps;
+    return leave(c, RBMD_OK);
+}
+
+rbmd_status rbmd_energy(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
+{
+    if (!c || !out) return RBMD_ERR_INVALID;
+    enter(c);
+    memset(out, 0, sizeof(*out));
+    StepRef r{nullptr, step};
+    rbmd_status s = RBMD_OK;
+    cudaMemsetAsync(c->ibuf, 0, 4 * sizeof(int32_t), c->stream);
+    cudaMemsetAsync(c->scal + SCAL_FSUM, 0, 6 * sizeof(double), c->stream);
+    if (!(c->prm.flags & RBMD_NO_RBE)) {
+        s = rbe_sample(c, r);
+        if (s == RBMD_OK) s = rbe_structure_factors(c);
+        if (s == RBMD_OK) s = md_sum(c, c->emode, (int)c->Pm, 1, c->scal + SCAL_ERBE, 1.0);
+    }
+    if (s == RBMD_OK && !(c->prm.flags & RBMD_NO_RBL)) {
+        s = cells_build(c);
+        if (s == RBMD_OK)
+            s = rbl_pairs(c, r, c->scratch_force, 0, true, nullptr, nullptr, nullptr);
+        if (s == RBMD_OK) s = md_sum(c, c->fpart, c->pair_blocks, 3, c->scal + SCAL_FSUM, 1.0);
+        if (s == RBMD_OK) s = md_sum(c, c->epart, c->pair_blocks, 2, c->scal + SCAL_ECOUL, 1.0);
+        if (s == RBMD_OK) {
+            k_max_count<<<(unsigned)((c->ncell + 255) / 256), 256, 0, c->stream>>>(
+                c->cell_count, c->ncell, c->ibuf + 1);
+        }
+    }
+    if (s == RBMD_OK) s = md_kinetic(c, c->scal + SCAL_KE_TRUE);
+    double h[SCAL_COUNT];
+    int32_t hi[4];
+    if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(h, c->scal, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(hi, c->ibuf, sizeof(hi), cudaMemcpyDeviceToHost, c->stream));
+    if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    s = leave(c, s);
+    if (s != RBMD_OK) return s;
+    RBMD_CHECK(check_latched(c));
+    out->e_coul_real = h[SCAL_ECOUL];
+    out->e_lj = h[SCAL_ELJ];
+    out->e_rbe = h[SCAL_ERBE];
+    out->e_self = c->e_self;
+    out->e_potential = out->e_coul_real + out->e_lj + out->e_rbe + out->e_self;
+    out->e_kinetic = h[SCAL_KE_TRUE];
+    out->temperature = c->N > 1 ? 2.0 * out->e_kinetic / (3.0 * (double)c->N - 3.0) : 0.0;
+    out->S = c->S;
+    for (int d = 0; d < 3; ++d) out->fsum_short[d] = h[SCAL_FSUM + d];
+    out->step = step;
+    out->max_shell = hi[0];
+    out->max_cell = hi[1];
+    return RBMD_OK;
+}
+
+rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, void *d_pos, void *d_q,
+                                 double *d_eps, double *d_sigma)
+{
+    (void)c; (void)step; (void)grad_out; (void)d_pos; (void)d_q; (void)d_eps; (void)d_sigma;
+    return RBMD_ERR_UNSUPPORTED;
+}
+
+rbmd_status rbmd_get_state(rbmd_ctx *c, void *pos, void *vel, int64_t *step)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    enter(c);
+    const size_t bytes = 3 * c->N * real_size(c);
+    void *stage = c->scratch_force;
+    rbmd_status s = RBMD_OK;
+    if (pos) {
+        s = md_decode_state(c, stage, nullptr);
+        if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(pos, stage, bytes, cudaMemcpyDefault, c->stream));
+        if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    }
+    if (s == RBMD_OK && vel) {
+        s = md_decode_state(c, nullptr, stage);
+        if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(vel, stage, bytes, cudaMemcpyDefault, c->stream));
+        if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    }
+    if (step) *step = c->step;
+    s = leave(c, s);
+    if (s != RBMD_OK) return s;
+    return check_latched(c);
+}
+
+rbmd_status rbmd_set_state(rbmd_ctx *c, const void *pos, const void *vel, int64_t step)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    enter(c);
+    const size_t bytes = 3 * c->N * real_size(c);
+    rbmd_status s = RBMD_OK;
+    if (pos) {
+        s = cuda_status(cudaMemcpyAsync(c->scratch_force, pos, bytes, cudaMemcpyDefault, c->stream));
+        if (s == RBMD_OK) s = md_encode_positions(c, c->scratch_force);
+    }
+    if (s == RBMD_OK && vel) {
+        s = cuda_status(cudaMemcpyAsync(c->vel, vel, bytes, cudaMemcpyDefault, c->stream));
+        k_set_lambda<<<1, 1, 0, c->stream>>>(c->scal, 1.0);
+    }
+    c->step = step;
+    c->have_force = false;
+    return leave(c, s);
+}
+
+rbmd_status rbmd_get_state_u(rbmd_ctx *c, uint32_t *u, void *vel, int64_t *step)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    enter(c);
+    rbmd_status s = RBMD_OK;
+    void *stage = c->scratch_force;
+    if (u) {
+        k_u4_to_u3<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->u4, c->N, (uint32_t *)stage);
+        s = cuda_status(cudaMemcpyAsync(u, stage, 3 * c->N * sizeof(uint32_t), cudaMemcpyDefault, c->stream));
+        if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    }
+    if (s == RBMD_OK && vel) {
+        s = md_decode_state(c, nullptr, stage);
+        if (s == RBMD_OK)
+            s = cuda_status(cudaMemcpyAsync(vel, stage, 3 * c->N * real_size(c), cudaMemcpyDefault, c->stream));
+        if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    }
+    if (step) *step = c->step;
+    s = leave(c, s);
+    if (s != RBMD_OK) return s;
+    return check_latched(c);
+}
+
+rbmd_status rbmd_set_state_u(rbmd_ctx *c, const uint32_t *u, const void *vel, int64_t step)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    enter(c);
+    rbmd_status s = RBMD_OK;
+    if (u) {
+        s = cuda_status(cudaMemcpyAsync(c->scratch_force, u, 3 * c->N * sizeof(uint32_t), cudaMemcpyDefault, c->stream));
+        k_u3_to_u4<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>((const uint32_t *)c->scratch_force, c->N, c->u4);
+    }
+    if (s == RBMD_OK && vel) {
+        s = cuda_status(cudaMemcpyAsync(c->vel, vel, 3 * c->N * real_size(c), cudaMemcpyDefault, c->stream));
+        k_set_lambda<<<1, 1, 0, c->stream>>>(c->scal, 1.0);
+    }
+    c->step = step;
+    c->have_force = false;
+    return leave(c, s);
+}
+
+rbmd_status rbmd_sync(rbmd_ctx *c)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    RBMD_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+    return check_latched(c);
+}
+
+int64_t rbmd_rbe_mode_count(rbmd_ctx *c) { return c ? c->Pm : 0; }
+
+rbmd_status rbmd_rbe_modes(rbmd_ctx *c, int64_t step, int32_t *m, double *rho)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    enter(c);
+    StepRef r{nullptr, step};
+    rbmd_status s = rbe_sample(c, r);
+    if (s == RBMD_OK) s = rbe_structure_factors(c);
+    if (s == RBMD_OK && m) {
+        k_modes_to_m3<<<(unsigned)((c->Pm + 255) / 256), 256, 0, c->stream>>>(c->modes, c->Pm, (int32_t *)c->rho_part);
+        s = cuda_status(cudaMemcpyAsync(m, c->rho_part, 3 * c->Pm * sizeof(int32_t), cudaMemcpyDefault, c->stream));
+    }
+    if (s == RBMD_OK && rho)
+        s = cuda_status(cudaMemcpyAsync(rho, c->rho, 2 * c->Pm * sizeof(double), cudaMemcpyDefault, c->stream));
+    if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    return leave(c, s);
+}
+
+rbmd_status rbmd_rbl_lists(rbmd_ctx *c, int64_t step, int32_t *n_core, int32_t *n_shell, int32_t *batch)
+{
+    if (!c || !n_core || !n_shell || !batch) return RBMD_ERR_INVALID;
+    enter(c);
+    rbmd_status s = cells_build(c);
+    if (s == RBMD_OK)
+        s = rbl_pairs(c, StepRef{nullptr, step}, c->scratch_force, 0, false, n_core, n_shell, batch);
+    return leave(c, s);
+}
+
+rbmd_status rbmd_profile(rbmd_ctx *c, int enable)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    const bool on = enable != 0;
+    if (on && !c->prof_ev[0])
+        for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
+            RBMD_CHECK_CUDA(cudaEventCreate(&c->prof_ev[k]));
+    if (on != c->profiling) {
+        RBMD_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+        if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+        c->graph_ready = false;  // re-captured with (or without) the stage events
+        c->profiling = on;
+    }
+    return RBMD_OK;
+}
+
+rbmd_status rbmd_profile_read(rbmd_ctx *c, double *ms, int64_t *steps, int reset)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    if (ms)
+        for (int k = 0; k < RBMD_PROFILE_STAGES; ++k) ms[k] = c->prof_ms[k];
+    if (steps) *steps = c->prof_steps;
+    if (reset) {
+        for (int k = 0; k < RBMD_PROFILE_STAGES; ++k) c->prof_ms[k] = 0.0;
+        c->prof_steps = 0;
+    }
+    return RBMD_OK;
+}
+
+int32_t rbmd_step_kernel_count(rbmd_ctx *c) { return c ? c->graph_kernels : 0; }
+
+rbmd_status rbmd_debug_latch_error(rbmd_ctx *c, int32_t code)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    RBMD_CHECK_CUDA(cudaMemcpy(c->err, &code, sizeof(int32_t), cudaMemcpyHostToDevice));
+    return RBMD_OK;
+}
+
+}  // extern "C"

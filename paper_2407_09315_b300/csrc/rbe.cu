@@ -1,0 +1,354 @@
+// Random batch Ewald on the device: mode sampling, structure factors and forces.
+//
+// Sec. 2.2 (Eqs. 9, 11, 12) and Algorithm 1 of arXiv 2407.09315.  The paper
+// samples the P modes with a Metropolis chain on the CPU and copies them to the
+// GPU every step; here they are drawn i.i.d. on the device (exact inverse CDF per
+// dimension, Philox4x32-10 keyed by seed, step and mode index), which keeps the
+// step free of host round trips and lets it be captured in a CUDA graph.
+//
+// Phases are computed exactly in integer arithmetic: with fixed-point positions
+// u (units of L/2^32), k.r = 2 pi (m . u mod 2^32) / 2^32, so the wrapped phase
+// is known to 2^-32 of a turn whatever the box size; only the final conversion
+// to a fraction of a turn rounds.
+#include <math.h>
+
+#include "rbmd_internal.cuh"
+
+namespace rbmd {
+
+// --------------------------------------------------------------------------
+// Sampler thresholds (host).  The density of Eq. 12 factorises over the three
+// axes, exp(-k^2/4alpha) = prod_d exp(-a m_d^2) with a = pi^2/(alpha L^2).
+// M is the smallest half-width with a M^2 >= ln(1e16); T[j] = min(2^64 - 1,
+// floor(CDF_j 2^64)) for j = 0..2M, CDF_j the cumulative weight of m = -M..j-M.
+// --------------------------------------------------------------------------
+rbmd_status sampler_table_host(double L, double alpha, int32_t *Mout, uint64_t *T, double *Hout)
+{
+    if (!(L > 0.0) || !(alpha > 0.0)) return RBMD_ERR_INVALID;
+    const double a = kPi * kPi / (alpha * L * L);
+    const double half_width = ceil(sqrt(16.0 * log(10.0) / a));
+    if (half_width > 1.0e7) return RBMD_ERR_INVALID;
+    const int M = (int)half_width;
+    if (Mout) *Mout = M;
+    if (!T && !Hout) return RBMD_OK;
+    const int n = 2 * M + 1;
+    double *cum = new double[n];
+    double total = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double m = (double)(j - M);
+        total += exp(-a * m * m);
+        cum[j] = total;
+    }
+    if (T) {
+        for (int j = 0; j < n; ++j) {
+            double x = (cum[j] / total) * kTwo64;
+            T[j] = (x >= kTwo64) ? UINT64_MAX : (uint64_t)x;
+        }
+    }
+    if (Hout) *Hout = total;
+    delete[] cum;
+    return RBMD_OK;
+}
+
+// Number of thresholds T[0..2M-1] not above U, minus M: the inverse CDF.
+__device__ __forceinline__ int draw_axis(uint64_t U, const uint64_t *__restrict__ T, int M)
+{
+    int lo = 0, hi = 2 * M;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (T[mid] <= U) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo - M;
+}
+
+// One thread per mode l: attempt t draws U_x, U_y from Philox(l, t, step, stream)
+// and U_z from Philox(l, t | 2^31, step, stream); m = 0 is redrawn (k != 0 in
+// Eq. 12).  After RBMD_MAX_ATTEMPTS zero draws the mode stays 0 (zero weight).
+__global__ void k_rbe_sample(const uint64_t *__restrict__ T, int M, int64_t P, uint2 key,
+                             StepRef sref, uint32_t replica, int4 *__restrict__ modes)
+{
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= P) return;
+    const uint32_t step = (uint32_t)step_of(sref);
+    const uint32_t tag = RBMD_STREAM_RBE | (replica << 8);
+    int mx = 0, my = 0, mz = 0;
+    for (uint32_t t = 0; t < RBMD_MAX_ATTEMPTS; ++t) {
+        uint4 w = philox10(make_uint4((uint32_t)l, t, step, tag), key);
+        uint4 w2 = philox10(make_uint4((uint32_t)l, t | 0x80000000u, step, tag), key);
+        mx = draw_axis(((uint64_t)w.x << 32) | w.y, T, M);
+        my = draw_axis(((uint64_t)w.z << 32) | w.w, T, M);
+        mz = draw_axis(((uint64_t)w2.x << 32) | w2.y, T, M);
+        if (mx != 0 || my != 0 || mz != 0) break;
+    }
+    modes[l] = make_int4(mx, my, mz, 0);
+}
+
+rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
+{
+    if (c->full_modes) return RBMD_OK;  // fixed list built at init
+    uint2 key = make_uint2((uint32_t)(c->prm.seed & 0xFFFFFFFFu), (uint32_t)(c->prm.seed >> 32));
+    int threads = 128;
+    int blocks = (int)((c->Pm + threads - 1) / threads);
+    k_rbe_sample<<<blocks, threads, 0, c->stream>>>(c->cdf, c->M, c->Pm, key, s, c->prm.replica,
+                                                    c->modes);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+// --------------------------------------------------------------------------
+// Structure factors, Eq. 9 (Algorithm 1 steps 2-3, the paper's Reduce-by-Key).
+// Block (x = atom tile, y = mode tile): the atom tile and the modes are staged
+// in shared memory; work item (mode l, sub-tile s) sums q_j e^{i theta_jl} over
+// its atoms with the thread's own compensated (Kahan) FP32 accumulators (plain
+// FP64 in FP64 contexts).  Items of one warp share s, so every lane reads the
+// same atom: a shared-memory broadcast.  The sub-tile sums are combined in FP64
+// in a fixed order and one partial per (atom tile, mode) goes to HBM.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void kahan_add(float &s, float &comp, float x)
+{
+    float y = x - comp;
+    float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+}
+
+template <typename real>
+__global__ void k_rho_partial(const uint4 *__restrict__ u4, const double *__restrict__ q64,
+                              int64_t N, const int4 *__restrict__ modes, int64_t Pm,
+                              int tile_atoms, int mode_tile, int sub,
+                              double2 *__restrict__ part)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint4 *s_at = reinterpret_cast<uint4 *>(smem);
+    double *s_q = reinterpret_cast<double *>(s_at + tile_atoms);  // FP64 contexts only
+    int4 *s_m = reinterpret_cast<int4 *>(s_q + (sizeof(real) == 8 ? tile_atoms : 0));
+    double2 *s_acc = reinterpret_cast<double2 *>(s_m + mode_tile);
+
+    const int64_t a0 = (int64_t)blockIdx.x * tile_atoms;
+    const int na = (int)min((int64_t)tile_atoms, N - a0);
+    const int64_t l0 = (int64_t)blockIdx.y * mode_tile;
+    const int nl = (int)min((int64_t)mode_tile, Pm - l0);
+
+    for (int k = threadIdx.x; k < na; k += blockDim.x) {
+        s_at[k] = u4[a0 + k];
+        if constexpr (sizeof(real) == 8) s_q[k] = q64[a0 + k];
+    }
+    for (int k = threadIdx.x; k < nl; k += blockDim.x) s_m[k] = modes[l0 + k];
+    __syncthreads();
+
+    const int per = (na + sub - 1) / sub;
+    for (int it = threadIdx.x; it < nl * sub; it += blockDim.x) {
+        const int l = it % nl;
+        const int s = it / nl;
+        const int b = s * per;
+        const int e = min(na, b + per);
+        const int4 m = s_m[l];
+        const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
+        double2 out;
+        if constexpr (sizeof(real) == 4) {
+            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+            for (int a = b; a < e; ++a) {
+                const uint4 A = s_at[a];
+                const uint32_t ph = mx * A.x + my * A.y + mz * A.z;
+                const float t = (float)(int32_t)ph * 4.656612873077392578125e-10f;  // 2^-31
+                float sn, cs;
+                sincospif(t, &sn, &cs);
+                const float q = __uint_as_float(A.w);
+                kahan_add(sr, cr, q * cs);
+                kahan_add(si, ci, q * sn);
+            }
+            out = make_double2((double)sr - (double)cr, (double)si - (double)ci);
+        } else {
+            double sr = 0.0, si = 0.0;
+            for (int a = b; a < e; ++a) {
+                const uint4 A = s_at[a];
+                const uint32_t ph = mx * A.x + my * A.y + mz * A.z;
+                const double t = (double)(int32_t)ph * 4.656612873077392578125e-10;
+                double sn, cs;
+                sincospi(t, &sn, &cs);
+                sr += s_q[a] * cs;
+                si += s_q[a] * sn;
+            }
+            out = make_double2(sr, si);
+        }
+        s_acc[s * mode_tile + l] = out;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < sub; ++s) {
+            re += s_acc[s * mode_tile + l].x;
+            im += s_acc[s * mode_tile + l].y;
+        }
+        part[(int64_t)blockIdx.x * Pm + l0 + l] = make_double2(re, im);
+    }
+}
+
+// Second stage: one warp per mode sums the atom-tile partials in FP64 (lane-strided,
+// then a fixed xor-shuffle tree), and derives the force and energy coefficients:
+//   c_l = -(4 pi coulomb_k / V) W_l / k_l^2,  A_l = c_l Im rho_l,  B_l = c_l Re rho_l,
+//   e_l = coulomb_k (2 pi / V) W_l |rho_l|^2 / k_l^2   (energy estimate term).
+template <typename real>
+__global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, int64_t Pm,
+                            const int4 *__restrict__ modes, const double *__restrict__ W,
+                            double Wconst, double L, double ck, double2 *__restrict__ rho,
+                            double *__restrict__ emode, ModeCoef<real> *__restrict__ coef)
+{
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (l >= Pm) return;
+    double re = 0.0, im = 0.0;
+    for (int t = lane; t < ntiles; t += 32) {
+        double2 p = part[(int64_t)t * Pm + l];
+        re += p.x;
+        im += p.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane != 0) return;
+    const int4 m = modes[l];
+    const double V = L * L * L;
+    const double tk = 2.0 * kPi / L;
+    const double kx = tk * m.x, ky = tk * m.y, kz = tk * m.z;
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    const double w = W ? W[l] : Wconst;
+    double cl = 0.0, e = 0.0;
+    if (k2 > 0.0) {
+        cl = -(4.0 * kPi * ck / V) * w / k2;
+        e = ck * (2.0 * kPi / V) * w * (re * re + im * im) / k2;
+    }
+    rho[l] = make_double2(re, im);
+    emode[l] = e;
+    ModeCoef<real> mc;
+    mc.mx = m.x;
+    mc.my = m.y;
+    mc.mz = m.z;
+    mc.pad = 0;
+    mc.A = (real)(cl * im);
+    mc.B = (real)(cl * re);
+    mc.kx = (real)m.x;
+    mc.ky = (real)m.y;
+    mc.kz = (real)m.z;
+    mc.pad2 = mc.pad3 = mc.pad4 = (real)0;
+    coef[l] = mc;
+}
+
+rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
+{
+    const int tile = c->rho_tile;
+    const int mode_tile = (int)(c->Pm < 256 ? c->Pm : 256);
+    int sub = max(1, 1024 / mode_tile);
+    sub = min(sub, tile);
+    int threads = ((mode_tile * sub + 31) / 32) * 32;
+    threads = min(threads, 1024);
+    dim3 grid((unsigned)c->rho_tiles, (unsigned)((c->Pm + mode_tile - 1) / mode_tile));
+    size_t smem = (size_t)tile * sizeof(uint4) + (c->fp64 ? (size_t)tile * sizeof(double) : 0) +
+                  (size_t)mode_tile * sizeof(int4) + (size_t)mode_tile * sub * sizeof(double2);
+    const double Wconst = c->S / (double)c->prm.rbe_P;
+    if (c->fp64) {
+        k_rho_partial<double><<<grid, threads, smem, c->stream>>>(
+            c->u4, c->q64, c->N, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
+        RBMD_LAUNCH_CHECK();
+        if (mark_between >= 0) prof_mark(c, mark_between);
+        k_rho_final<double><<<(unsigned)((c->Pm * 32 + 255) / 256), 256, 0, c->stream>>>(
+            c->rho_part, c->rho_tiles, c->Pm, c->modes, c->W, Wconst, c->L, c->prm.coulomb_k,
+            c->rho, c->emode, (ModeCoef<double> *)c->coef);
+    } else {
+        k_rho_partial<float><<<grid, threads, smem, c->stream>>>(
+            c->u4, nullptr, c->N, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
+        RBMD_LAUNCH_CHECK();
+        if (mark_between >= 0) prof_mark(c, mark_between);
+        k_rho_final<float><<<(unsigned)((c->Pm * 32 + 255) / 256), 256, 0, c->stream>>>(
+            c->rho_part, c->rho_tiles, c->Pm, c->modes, c->W, Wconst, c->L, c->prm.coulomb_k,
+            c->rho, c->emode, (ModeCoef<float> *)c->coef);
+    }
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+// sin and cos of the wrapped phase 2 pi ph / 2^32 (ph read as a signed fraction of
+// a half turn, so the argument of sincospi lies in [-1, 1)).
+__device__ __forceinline__ void phase_sincos(uint32_t ph, float &s, float &c)
+{
+    sincospif((float)(int32_t)ph * 4.656612873077392578125e-10f, &s, &c);
+}
+__device__ __forceinline__ void phase_sincos(uint32_t ph, double &s, double &c)
+{
+    sincospi((double)(int32_t)ph * 4.656612873077392578125e-10, &s, &c);
+}
+
+// --------------------------------------------------------------------------
+// Force pass, Eq. 12 (Algorithm 1 step 4).  One thread per atom; the mode
+// coefficients stream through shared memory in chunks (every lane reads the same
+// mode: a broadcast).  The phase is recomputed exactly from the integers rather
+// than stored per atom-mode (N P complex numbers would cost more HBM traffic
+// than the recomputation).
+// --------------------------------------------------------------------------
+template <typename real, int CHUNK>
+__global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restrict__ q64,
+                            int64_t N, const ModeCoef<real> *__restrict__ coef, int64_t Pm,
+                            real tk, real *__restrict__ F, int accumulate)
+{
+    __shared__ ModeCoef<real> s_c[CHUNK];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < N;
+    uint4 A = active ? u4[i] : make_uint4(0, 0, 0, 0);
+    real fx = 0, fy = 0, fz = 0;
+    for (int64_t c0 = 0; c0 < Pm; c0 += CHUNK) {
+        const int nc = (int)min((int64_t)CHUNK, Pm - c0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) s_c[k] = coef[c0 + k];
+        __syncthreads();
+        if (active) {
+            for (int k = 0; k < nc; ++k) {
+                const ModeCoef<real> mc = s_c[k];
+                const uint32_t ph = (uint32_t)mc.mx * A.x + (uint32_t)mc.my * A.y +
+                                    (uint32_t)mc.mz * A.z;
+                real sn, cs;
+                phase_sincos(ph, sn, cs);
+                const real g = mc.A * cs - mc.B * sn;
+                fx += g * mc.kx;
+                fy += g * mc.ky;
+                fz += g * mc.kz;
+            }
+        }
+    }
+    if (!active) return;
+    real q;
+    if constexpr (sizeof(real) == 4) q = __uint_as_float(A.w);
+    else q = q64[i];
+    const real s = q * tk;
+    real *f = F + 3 * i;
+    if (accumulate) {
+        f[0] += s * fx;
+        f[1] += s * fy;
+        f[2] += s * fz;
+    } else {
+        f[0] = s * fx;
+        f[1] = s * fy;
+        f[2] = s * fz;
+    }
+}
+
+rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate)
+{
+    const int threads = c->force_block;
+    const unsigned blocks = (unsigned)((c->N + threads - 1) / threads);
+    if (c->fp64) {
+        k_rbe_force<double, 128><<<blocks, threads, 0, c->stream>>>(
+            c->u4, c->q64, c->N, (const ModeCoef<double> *)c->coef, c->Pm, 2.0 * kPi / c->L,
+            (double *)force, accumulate);
+    } else {
+        k_rbe_force<float, 256><<<blocks, threads, 0, c->stream>>>(
+            c->u4, nullptr, c->N, (const ModeCoef<float> *)c->coef, c->Pm,
+            (float)(2.0 * kPi / c->L), (float *)force, accumulate);
+    }
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+}  // namespace rbmd

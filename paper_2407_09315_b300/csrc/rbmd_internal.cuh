@@ -1,0 +1,227 @@
+// Internal declarations of the B300 random-batch MD library.
+//
+// Data layout in HBM (atom id = the caller's row index):
+//   u4     uint4[N]   fixed-point fractional coordinates (x, y, z) in units of
+//                     L/2^32, and the FP32 charge bits in .w (id order, master)
+//   q64    double[N]  charges (FP64 contexts)
+//   type   int32[N]   LJ type
+//   vel    real[N][3] velocities (stored before the pending Berendsen factor)
+//   force  real[N][3] forces of the current configuration (without F_corr)
+//   spos   uint4[N]   cell-sorted copy {ux, uy, uz, id}, rebuilt every evaluation
+//   sq     real[N]    cell-sorted charges;  stype int32[N] cell-sorted types
+//   cell_start int32[ncell+1]  CSR offsets of the cells (x-major, z fastest)
+//
+// All floating-point reductions whose results leave a kernel run in FP64 and in a
+// fixed order, so two runs of the same state are bit-identical.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rbmd.h"
+
+#define RBMD_STREAM_RBE 1u
+#define RBMD_STREAM_RBL 2u
+#define RBMD_MAX_ATTEMPTS 256
+#define RBMD_MAX_TYPES 64
+#define RBMD_MAX_P 128
+
+namespace rbmd {
+
+constexpr double kTwo32 = 4294967296.0;
+constexpr double kTwo64 = 18446744073709551616.0;
+constexpr double kPi = 3.14159265358979323846;
+
+// Step number used by a kernel: (*ptr) + add when ptr is set (graph replays read
+// the device counter), else add.
+struct StepRef {
+    const int64_t *ptr;
+    int64_t add;
+};
+
+__device__ __forceinline__ int64_t step_of(StepRef s) { return (s.ptr ? *s.ptr : 0) + s.add; }
+
+// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
+// 10 rounds of two 32x32->64 multiplies with Weyl-sequence key increments.
+__host__ __device__ __forceinline__ void philox_mulhilo(uint32_t a, uint32_t b, uint32_t &hi,
+                                                        uint32_t &lo)
+{
+#ifdef __CUDA_ARCH__
+    hi = __umulhi(a, b);
+    lo = a * b;
+#else
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        uint32_t h0, l0, h1, l1;
+        philox_mulhilo(0xD2511F53u, c.x, h0, l0);
+        philox_mulhilo(0xCD9E8D57u, c.z, h1, l1);
+        c = make_uint4(h1 ^ c.y ^ k.x, l1, h0 ^ c.w ^ k.y, l0);
+    }
+    return c;
+}
+
+// Device error word: first error wins.
+__device__ __forceinline__ void latch_error(int *err, int code) { atomicCAS(err, 0, code); }
+
+template <typename real> struct Vec3Ptr;
+
+// Per-mode coefficients for the force pass (Eq. 12 expanded):
+//   F_i = q_i sum_l (A_l cos th - B_l sin th) k_l,  A = c rho_im, B = c rho_re,
+//   c_l = -(4 pi coulomb_k / V) W_l / k_l^2.
+template <typename real> struct ModeCoef {
+    int32_t mx, my, mz, pad;
+    real A, B, kx, ky, kz, pad2, pad3, pad4;
+};
+
+}  // namespace rbmd
+
+struct rbmd_ctx {
+    rbmd_params prm;
+    int64_t N;
+    int32_t T;
+    bool fp64;
+    cudaStream_t stream;
+    bool own_stream;      // created here because the caller passed the legacy stream
+    cudaEvent_t ev_in, ev_out;
+
+    // derived constants
+    double L, V, S, H, sqrt_alpha, lscale, dtc, tau;
+    int32_t M;            // sampler half-width
+    uint64_t Rc2, Rs2;    // squared radii in fixed-point units
+    uint32_t Rlin;        // floor(sqrt(Rs2)): per-axis early reject
+    int32_t nc, div;      // cells per axis, cells per r_cut
+    int64_t ncell;
+    double e_self;        // -coulomb_k sqrt(alpha/pi) sum q^2
+    int64_t Pm;           // modes per evaluation (P or the full count)
+    bool full_modes;
+
+    // master state
+    uint4 *u4;
+    double *q64;
+    int32_t *type;
+    void *vel;
+    void *force;          // internal force buffer for the integrator
+    void *scratch_force;  // force buffer for energy evaluations
+    double *scal;         // [16] FP64 scalars, see SCAL_* below
+    int *err;
+    int64_t *d_step;
+
+    // RBE
+    uint64_t *cdf;        // [2M+1]
+    int4 *modes;          // [Pm]
+    double *W;            // [Pm] weights (full-mode list), else NULL
+    double2 *rho_part;    // [rho_tiles][Pm]
+    double2 *rho;         // [Pm]
+    double *emode;        // [Pm]
+    void *coef;           // ModeCoef<real>[Pm]
+    int rho_tile;         // atoms per structure-factor block
+    int rho_tiles;        // number of atom tiles
+    int force_block;      // threads per block of the force pass
+
+    // RBL
+    int32_t *cell_count;  // [ncell]
+    int32_t *cell_start;  // [ncell+1]
+    int32_t *cell_of;     // [N]
+    int32_t *cell_rank;   // [N]
+    int32_t *scan_part;   // scan block sums
+    uint4 *spos;          // [N]
+    void *sq;             // real [N]
+    int32_t *stype;       // [N]
+    double *fpart;        // [pair_blocks][3] force partial sums
+    double *epart;        // [pair_blocks][2] energy partial sums
+    double *kepart;       // [kick_blocks]
+    int32_t *ibuf;        // [4] integer diagnostics
+    float *lj_f;          // [2*T] sqrt(eps), sigma/2 (FP32 path)
+    double *lj_d;         // [2*T] (FP64 path)
+    int pair_block;
+    int pair_blocks;
+    int kick_blocks;
+
+    // integrator state
+    int64_t step;
+    bool have_force;
+    cudaGraphExec_t graph;
+    bool graph_ready;
+    int32_t graph_kernels;
+
+    // per-stage timing (rbmd_profile)
+    bool profiling;
+    cudaEvent_t prof_ev[RBMD_PROFILE_STAGES + 1];
+    double prof_ms[RBMD_PROFILE_STAGES];
+    int64_t prof_steps;
+};
+
+// FP64 scalar slots in ctx->scal
+enum {
+    SCAL_FCORR = 0,   // [3] momentum correction F_corr
+    SCAL_LAMBDA = 3,  // pending Berendsen factor of the stored velocities
+    SCAL_KE = 4,      // kinetic energy after the last kick (before lambda)
+    SCAL_FSUM = 5,    // [3] sum of short-range forces before the correction
+    SCAL_ERBE = 8,    // RBE energy estimate
+    SCAL_ECOUL = 9,
+    SCAL_ELJ = 10,
+    SCAL_KE_TRUE = 11,
+    SCAL_FCORR_AUX = 12,  // [3] correction of stand-alone force calls
+    SCAL_COUNT = 16
+};
+
+namespace rbmd {
+
+// Records the event that opens stage `k` of the step (profiling only).
+inline void prof_mark(rbmd_ctx *c, int k)
+{
+    if (c->profiling) cudaEventRecord(c->prof_ev[k], c->stream);
+}
+
+// ---- host-side helpers implemented in the .cu files ----
+rbmd_status sampler_table_host(double L, double alpha, int32_t *M, uint64_t *T, double *H);
+
+// RBE (rbe.cu)
+rbmd_status rbe_sample(rbmd_ctx *c, StepRef s);
+rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between = -1);
+rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate);
+
+// RBL (rbl.cu)
+rbmd_status cells_build(rbmd_ctx *c);
+rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
+                      int32_t *n_core, int32_t *n_shell, int32_t *batch);
+rbmd_status rbl_correction(rbmd_ctx *c, void *force, bool apply, int slot);
+
+// MD (md.cu)
+rbmd_status md_kick_drift(rbmd_ctx *c);
+rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step);
+rbmd_status md_sum(rbmd_ctx *c, const double *parts, int nparts, int ncomp, double *out,
+                   double scale);
+rbmd_status md_decode_state(rbmd_ctx *c, void *pos, void *vel);
+rbmd_status md_encode_positions(rbmd_ctx *c, const void *pos);
+rbmd_status md_kinetic(rbmd_ctx *c, double *out_dev);
+
+inline rbmd_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RBMD_OK : RBMD_ERR_CUDA; }
+
+}  // namespace rbmd
+
+#define RBMD_CHECK_CUDA(call)                                          \
+    do {                                                               \
+        cudaError_t e__ = (call);                                      \
+        if (e__ != cudaSuccess) return RBMD_ERR_CUDA;                  \
+    } while (0)
+
+#define RBMD_CHECK(call)                                               \
+    do {                                                               \
+        rbmd_status s__ = (call);                                      \
+        if (s__ != RBMD_OK) return s__;                                \
+    } while (0)
+
+#define RBMD_LAUNCH_CHECK() RBMD_CHECK_CUDA(cudaGetLastError())

@@ -1,0 +1,219 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Every case feeds both sides the same seeded synthetic electrolyte (exact
+fixed-point positions) and the same (seed, step): the random modes and batches
+are drawn independently on each side from the same Philox definition, so they
+must agree exactly; forces and energies must agree within the stated tolerance.
+Sizes span several tiles with a ragged tail (1000, 1537 and 4099 atoms).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2407_09315_b300 as rb
+from paper_2407_09315_b300 import synth
+
+from gpu_util import TOL, make_ctx, rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [rb.FP64, rb.FP32]
+
+
+@pytest.fixture(scope="module")
+def sys1000():
+    return synth.config1()
+
+
+@pytest.fixture(scope="module")
+def sys_ragged():
+    return synth.electrolyte(1537, seed=11, charges="2:1", n_types=3)
+
+
+@pytest.fixture(scope="module")
+def sys_4099():
+    return synth.electrolyte(4099, seed=12, charges="2:1", n_types=4)
+
+
+# ------------------------------------------------------------------ RBE
+@pytest.mark.parametrize("prec", PRECS)
+def test_modes_bit_exact(sys1000, prec):
+    ctx, prm = make_ctx(sys1000, prec, rbe_P=100, seed=0)
+    for step in (0, 1, 77, 123456):
+        m, rho = ctx.rbe_modes(step)
+        mo = oracle.rbe_sample(0, step, 100, sys1000.L, 0.62)
+        assert np.array_equal(m, mo), step
+    ctx.close()
+
+
+def test_modes_bit_exact_large_box_and_replica():
+    L = 170.99759466766966
+    s = synth.electrolyte(2000, L=L, seed=5, dmin_factor=0.0)
+    ctx, _ = make_ctx(s, rb.FP32, rbe_P=200, seed=0xDEADBEEF12345, replica=3)
+    for step in (0, 9):
+        m, _ = ctx.rbe_modes(step)
+        mo = oracle.rbe_sample(0xDEADBEEF12345, step, 200, L, 0.62, replica=3)
+        assert np.array_equal(m, mo)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("which", ["sys1000", "sys_ragged", "sys_4099"])
+def test_structure_factors(which, prec, request):
+    s = request.getfixturevalue(which)
+    ctx, _ = make_ctx(s, prec, rbe_P=200, seed=4)
+    m, rho = ctx.rbe_modes(3)
+    rho_o = oracle.structure_factor(s.u, s.q, s.L, m)
+    scale = np.sqrt(np.sum(s.q ** 2))
+    err = np.max(np.abs(rho - rho_o)) / scale
+    assert err < (1e-12 if prec == rb.FP64 else 2e-6), err
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("which", ["sys1000", "sys_ragged", "sys_4099"])
+def test_rbe_forces(which, prec, request):
+    s = request.getfixturevalue(which)
+    ctx, prm = make_ctx(s, prec, rbe_P=200, seed=4)
+    for step in (0, 5):
+        F = to_np(ctx.rbe_forces(step))
+        Fo, Eo, _, _ = oracle.rbe_forces(s.u, s.q, s.L, 0.62, 1.0, 200, seed=4, step=step)
+        assert rel_err(F, Fo) < TOL[prec], (step, rel_err(F, Fo))
+    # accumulate mode adds onto the output
+    base = ctx.rbe_forces(0)
+    twice = ctx.rbe_forces(0, out=base.clone(), accumulate=True)
+    assert rel_err(to_np(twice), 2 * to_np(base)) < 1e-6
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_ewald_modes_reproduce_eq11(sys1000, prec):
+    s = sys1000
+    ctx, _ = make_ctx(s, prec, flags=rb.FULL_EWALD_MODES)
+    F = to_np(ctx.rbe_forces(0))
+    M = oracle.sampler_M(s.L, 0.62)
+    e = oracle.ewald(s.u, s.q, s.L, 0.62, 1.0, 3.5, M)
+    assert rel_err(F, e["F_recip"]) < TOL[prec]
+    E = ctx.energy(0)
+    assert abs(E["e_rbe"] - e["E_recip"]) < (1e-10 if prec == rb.FP64 else 1e-5) * abs(e["E_recip"])
+    assert abs(E["e_self"] - e["E_self"]) < 1e-12 * abs(e["E_self"])
+    ctx.close()
+
+
+# ------------------------------------------------------------------ RBL
+@pytest.mark.parametrize("cell_div", [1, 2])
+@pytest.mark.parametrize("p", [10, 30])
+@pytest.mark.parametrize("which", ["sys1000", "sys_ragged"])
+def test_rbl_lists_bit_exact(which, p, cell_div, request):
+    s = request.getfixturevalue(which)
+    ctx, _ = make_ctx(s, rb.FP32, rbl_p=p, seed=9, cell_div=cell_div)
+    for step in (0, 3):
+        nc, ns, b = (to_np(t).astype(np.int64) for t in ctx.rbl_lists(step))
+        o = oracle.rbl(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, p, 9, step)
+        assert np.array_equal(nc, o["n_core"])
+        assert np.array_equal(ns, o["n_shell"])
+        assert np.array_equal(b, o["batch"])
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("which", ["sys1000", "sys_ragged", "sys_4099"])
+def test_rbl_forces(which, prec, request):
+    s = request.getfixturevalue(which)
+    ctx, _ = make_ctx(s, prec, seed=2)
+    for step in (0, 7):
+        F = to_np(ctx.rbl_forces(step))
+        o = oracle.rbl(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 2, step)
+        Fo = o["F"] - o["Fsum"] / s.n
+        assert rel_err(F, Fo) < TOL[prec], (step, rel_err(F, Fo))
+        assert np.linalg.norm(F.sum(0)) < 1e-6 * np.abs(F).sum()
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_rbl_exact_mode(sys_ragged, prec):
+    s = sys_ragged
+    ctx, _ = make_ctx(s, prec, flags=rb.RBL_EXACT)
+    F = to_np(ctx.rbl_forces(0))
+    o = oracle.rbl(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 0, 0, exact=True)
+    assert rel_err(F, o["F"] - o["Fsum"] / s.n) < TOL[prec]
+    ctx.close()
+
+
+# ------------------------------------------------------------------ total + energies
+@pytest.mark.parametrize("prec", PRECS)
+def test_total_forces_and_energies(sys_4099, prec):
+    s = sys_4099
+    ctx, _ = make_ctx(s, prec, rbe_P=100, seed=6)
+    F = to_np(ctx.forces(2))
+    Fo, Eo = oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 100, 6, 2)
+    assert rel_err(F, Fo) < TOL[prec]
+    E = ctx.energy(2)
+    tol = 1e-10 if prec == rb.FP64 else 1e-5
+    for k, ref in zip(("e_coul_real", "e_lj", "e_rbe", "e_self"), Eo):
+        assert abs(E[k] - ref) <= tol * abs(ref) + 1e-12, (k, E[k], ref)
+    assert abs(E["S"] - oracle.rbe_S(s.L, 0.62)) < 1e-12 * E["S"]
+    o = oracle.rbl(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 6, 2)
+    assert E["max_shell"] == int(o["n_shell"].max())
+    assert np.allclose(E["fsum_short"], o["Fsum"], rtol=1e-6, atol=1e-6 * np.abs(o["F"]).sum())
+    ctx.close()
+
+
+# ------------------------------------------------------------------ integrator
+@pytest.mark.parametrize("thermostat", [0, 1])
+def test_fp64_trajectory_matches_oracle(thermostat):
+    s = synth.electrolyte(600, seed=13, charges="1:1", n_types=2, T0=1.0)
+    ctx, _ = make_ctx(s, rb.FP64, rbe_P=50, seed=3, dt=0.001, thermostat=thermostat,
+                      temperature=1.5, tau_T=0.1)
+    ctx.set_state_u(s.u, vel=s.v, step=0)
+    ctx.step(10)
+    u, v, st = ctx.get_state_u()
+    assert st == 10
+    u = to_np(u).astype(np.int64) % 2 ** 32
+    F0, _ = oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 50, 3, 0)
+    uo, vo, _ = oracle.vv(s.u, s.v, F0, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10,
+                          50, seed=3, step0=0, dt=0.001, n_steps=10, thermostat=thermostat,
+                          T0=1.5, tau=0.1)
+    du = (u - uo.astype(np.int64) + 2 ** 31) % 2 ** 32 - 2 ** 31
+    assert np.max(np.abs(du)) <= 2
+    assert rel_err(to_np(v), vo) < 1e-9
+    ctx.close()
+
+
+def test_fp32_step_stays_close_to_oracle():
+    s = synth.electrolyte(1000, seed=14, charges="1:1", n_types=1)
+    ctx, _ = make_ctx(s, rb.FP32, rbe_P=50, seed=3, dt=0.001, thermostat=1)
+    ctx.set_state_u(s.u, vel=s.v, step=0)
+    ctx.step(3)
+    u, v, _ = ctx.get_state_u()
+    F0, _ = oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 50, 3, 0)
+    uo, vo, _ = oracle.vv(s.u, s.v, F0, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10,
+                          50, seed=3, step0=0, dt=0.001, n_steps=3, thermostat=1)
+    assert rel_err(to_np(v), vo) < 1e-5
+    ctx.close()
+
+
+# ------------------------------------------------------------------ determinism, checkpoint
+def test_bit_identical_runs_and_resume():
+    import torch
+
+    s = synth.electrolyte(3000, seed=15, charges="2:1", n_types=2)
+    a, _ = make_ctx(s, rb.FP32, seed=1, thermostat=1)
+    a.set_state_u(s.u, vel=s.v, step=0)
+    a.step(6)
+    ua, va, _ = a.get_state_u()
+    b, _ = make_ctx(s, rb.FP32, seed=1, thermostat=1)
+    b.set_state_u(s.u, vel=s.v, step=0)
+    b.step(3)
+    u3, v3, st = b.get_state_u()
+    c, _ = make_ctx(s, rb.FP32, seed=1, thermostat=1)
+    c.set_state_u(u3, vel=v3, step=st)
+    c.step(3)
+    uc, vc, _ = c.get_state_u()
+    b.step(3)
+    ub, vb, _ = b.get_state_u()
+    assert torch.equal(ua, ub) and torch.equal(va, vb)
+    # resume through a checkpoint: bit-identical to the unbroken run
+    assert torch.equal(ua, uc) and torch.equal(va, vc)
+    for x in (a, b, c):
+        x.close()
