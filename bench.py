@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the random-batch MD step on B300 (arXiv 2407.09315 workload).
+
+Default workload: the N = 1,000,000 2:1 electrolyte (333,333 cations +2,
+666,666 anions -1, one neutral atom; 4 LJ types, sigma ~ U[0.8, 1.2],
+epsilon ~ U[0.5, 1.5]; density 0.2; L = 170.998), alpha = 0.62, P = 200,
+r_core = 2.0, r_cut = 3.5, p = 10, dt = 0.001, Berendsen T0 = 1.  One step is
+a full velocity-Verlet step: half kick + drift, RBE (mode sampling, structure
+factors, force), RBL (cell sort, core list + shell batch pair forces, momentum
+correction), half kick + thermostat.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the context's stream; the L2 cache (126 MB, larger than the 1M-atom working
+set) is flushed by writing a 256 MB buffer before every timed step, outside
+the timed region.  The FP64 path is timed the same way on the same system.
+`e2e` times the force step through the C ABI with host buffers: positions
+copied in from pinned host memory, forces copied back, every step.
+
+--impl reference times the FP64 CPU oracle (the checker, run as it stands on
+the host cores) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/step and atom-steps/s at 1M atoms (RBE+RBL), FP32 path vs plain FP64 path"
+UNIT = "atom-steps/s"
+PARAMS = dict(alpha=0.62, r_core=2.0, r_cut=3.5, rbl_p=10, rbe_P=200, coulomb_k=1.0,
+              dt=0.001, temperature=1.0, tau_T=0.1, thermostat=1)
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic FP32-pipe lane operations per unit of work (each elementary
+# function counted as one operation; FMA as one): see the design doc, roofline.
+OPS_RHO_PER_ATOM_MODE = 8      # 3 phase IMAD, 1 convert, sin, cos, 2 FMA
+OPS_FORCE_PER_ATOM_MODE = 11   # 3 phase IMAD, 1 convert, sin, cos, 2 (g), 3 FMA
+OPS_CLASSIFY_PER_NEIGHBOUR = 7  # 3 sub, 3 IMAD, 1 compare
+OPS_PHILOX = 80                # 10 rounds x (2 mul.hi + 2 mul.lo + 4 xor/add)
+OPS_PAIR = 22                  # r^2, rsqrt, erfc, exp, Coulomb, LJ, accumulate
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=400_000)
+    ap.add_argument("--ref-sample", type=int, default=100_000)
+    return ap.parse_args()
+
+
+def make_system(n, seed):
+    from paper_2407_09315_b300 import synth
+    return synth.electrolyte(n, seed=seed, charges="2:1", n_types=4)
+
+
+def workload_config(args, world):
+    return {"workload": "2:1 electrolyte, N=%d per GPU, density 0.2, 4 LJ types, P=%d, "
+                        "p=%d, r_core=%.1f, r_cut=%.1f, alpha=%.2f, Berendsen NVT"
+                        % (args.n, PARAMS["rbe_P"], PARAMS["rbl_p"], PARAMS["r_core"],
+                           PARAMS["r_cut"], PARAMS["alpha"]),
+            "n_atoms_per_gpu": args.n, "global_atoms": args.n * world,
+            "parallelism": "independent replicas" if world > 1 else "single GPU",
+            "l2": "flushed (256 MB write) before every timed step"}
+
+
+# --------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names[1:], f[5:9]):
+                if val.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- ours
+def make_ctx(system, precision, device):
+    import torch
+    import paper_2407_09315_b300 as rb
+
+    dt = torch.float64 if precision == rb.FP64 else torch.float32
+    ctx = rb.RBMD(torch.from_numpy(system.x).to(device, dt), torch.from_numpy(system.q).to(device, dt),
+                  system.eps, system.sig, box_length=system.L, precision=precision,
+                  vel=torch.from_numpy(system.v).to(device, dt),
+                  types=torch.from_numpy(system.types).to(device), seed=2, **PARAMS)
+    ctx.set_state_u(system.u, vel=system.v, step=0)
+    return ctx
+
+
+def time_steps(ctx, K, W, flush, profile):
+    import torch
+
+    stream = torch.cuda.current_stream()
+    if profile:
+        ctx.profile(True)
+    for _ in range(W):
+        flush.fill_(1)
+        ctx.step(1)
+    torch.cuda.synchronize()
+    if profile:
+        ctx.profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        ctx.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    stages = ctx.profile_read(reset=True)[0] if profile else None
+    return ms, stages
+
+
+def mean_lists(system):
+    """Mean core and shell neighbour counts of a uniform fluid at this density."""
+    import math
+    n = system.n / system.L ** 3
+    core = n * 4.0 / 3.0 * math.pi * PARAMS["r_core"] ** 3
+    shell = n * 4.0 / 3.0 * math.pi * (PARAMS["r_cut"] ** 3 - PARAMS["r_core"] ** 3)
+    return core, shell
+
+
+def roofline(stages_ms_per_step, system, peaks_clock_mhz):
+    """Roofline object for the stage with the largest share of the step."""
+    N, P, p = system.n, PARAMS["rbe_P"], PARAMS["rbl_p"]
+    core, shell = mean_lists(system)
+    ops = {
+        "rho_partial": N * P * OPS_RHO_PER_ATOM_MODE,
+        "rbe_force": N * P * OPS_FORCE_PER_ATOM_MODE,
+        "rbl_pair": N * (OPS_CLASSIFY_PER_NEIGHBOUR * (core + shell) + OPS_PHILOX * shell
+                         + OPS_PAIR * (core + min(shell, p))),
+    }
+    top = max(ops, key=lambda k: stages_ms_per_step.get(k, 0.0))
+    t = stages_ms_per_step[top] * 1e-3
+    clock = 2032.0 if not peaks_clock_mhz else peaks_clock_mhz
+    peak = 148 * 128 * clock * 1e6 / 1e12  # Top/s, one FP32 lane-op per lane per clock
+    achieved = ops[top] / t / 1e12
+    return {"bound": "alu", "kernel": top, "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "Top/s (FP32-pipe lane ops)", "frac": round(achieved / peak, 4),
+            "traffic": None, "ms_per_launch": round(stages_ms_per_step[top], 4),
+            "algorithmic_ops_per_launch": ops[top]}
+
+
+def e2e_force_step(ctx, system, K, W, device):
+    """Force step through the C ABI with host buffers: positions in, forces out."""
+    import torch
+
+    dt = ctx.dtype
+    host_pos = torch.from_numpy(system.x).to(dt).pin_memory()
+    host_f = torch.empty((system.n, 3), dtype=dt).pin_memory()
+    dev_f = torch.empty((system.n, 3), dtype=dt, device=device)
+    stream = torch.cuda.current_stream()
+    for k in range(W):
+        ctx.set_state(pos=host_pos, step=k)
+        ctx.forces(k, out=dev_f)
+        host_f.copy_(dev_f, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(K):
+        ctx.set_state(pos=host_pos, step=k)
+        ctx.forces(k, out=dev_f)
+        host_f.copy_(dev_f, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1) / K
+    nbytes = 3 * system.n * (8 if dt == torch.float64 else 4)
+    return {"value": system.n / (max(ms, wall * 1e3 / K) * 1e-3), "unit": UNIT,
+            "ms_per_step": max(ms, wall * 1e3 / K), "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes,
+            "what": "rbmd_set_state(host pinned positions) + rbmd_forces + D2H of the forces"}
+
+
+def cpu_baseline(n_sample, seed):
+    import oracle
+    s = make_system(n_sample, seed)
+    t0 = time.perf_counter()
+    oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, PARAMS["alpha"], 1.0, PARAMS["r_core"],
+                  PARAMS["r_cut"], PARAMS["rbl_p"], PARAMS["rbe_P"], 2, 0)
+    t = time.perf_counter() - t0
+    return {"value": n_sample / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one FP64 force evaluation (RBE + RBL + F_corr) of a %d-atom system of the "
+                      "same recipe, single thread, %.1f s" % (n_sample, t)}
+
+
+def run_ours(args):
+    import torch
+    import paper_2407_09315_b300 as rb
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+
+    system = make_system(args.n, 2 + rank)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    ctx = make_ctx(system, rb.FP32, device)
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ms, stages = time_steps(ctx, args.steps, args.warmup, flush, profile=True)
+    clk = clocks.stop()
+    kernels_per_step = ctx.step_kernel_count()
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = args.n * world / (ms_per_step * 1e-3)
+    stage_ms = {k: v / args.steps for k, v in stages.items()}
+
+    e2e = None
+    if not args.skip_e2e:
+        e2e = e2e_force_step(ctx, system, args.e2e_steps, 2, device)
+    ctx.close()
+
+    fp64 = None
+    if not args.skip_fp64:
+        c64 = make_ctx(system, rb.FP64, device)
+        ms64, st64 = time_steps(c64, args.fp64_steps, 2, flush, profile=True)
+        c64.close()
+        m64 = sum(ms64) / len(ms64)
+        fp64 = {"ms_per_step": round(m64, 4), "atom_steps_per_s": args.n / (m64 * 1e-3),
+                "stage_ms": {k: round(v / args.fp64_steps, 4) for k, v in st64.items()}}
+
+    if rank != 0:
+        return
+    peak_clock = clk["sm_max_mhz"] if clk else None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "ms_per_step_median": round(statistics.median(ms), 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded 2:1 electrolyte, see DESIGN.md)",
+        "config": workload_config(args, world),
+        "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
+        "roofline": roofline(stage_ms, system, 2032.0),
+        "gpu_launches": kernels_per_step * args.steps,
+        "kernels_per_step": kernels_per_step,
+    }
+    if fp64:
+        out["fp64"] = fp64
+        out["speedup_fp32_over_fp64"] = round(fp64["ms_per_step"] / ms_per_step, 2)
+    if e2e:
+        out["e2e"] = e2e
+    if clk:
+        out["clocks"] = clk
+    out["paper_context"] = ("8.20 ms/step nonbonded at N=1e6 (SPC/E water, A100 + 1 CPU core); "
+                            "different workload and hardware, not a target")
+    if not args.skip_cpu and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample, 2)
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    import oracle
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    s = make_system(args.ref_sample, 2)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, PARAMS["alpha"], 1.0,
+                      PARAMS["r_core"], PARAMS["r_cut"], PARAMS["rbl_p"], PARAMS["rbe_P"], 2, k)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    sec = sum(times) / len(times)
+    value = args.ref_sample / sec
+    sample = ("one FP64 force evaluation (RBE + RBL + F_corr) per step of a %d-atom system of the "
+              "same recipe, single thread" % args.ref_sample)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded 2:1 electrolyte, see DESIGN.md)",
+           "config": workload_config(args, world),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -86,6 +86,9 @@ def lib():
         "rbmd_rbl_lists": ([P, i64, P, P, P], C.c_int),
         "rbmd_sampler_table": ([dbl, dbl, C.POINTER(i32), P, C.POINTER(dbl)], C.c_int),
         "rbmd_debug_latch_error": ([P, i32], C.c_int),
+        "rbmd_profile": ([P, C.c_int], C.c_int),
+        "rbmd_profile_read": ([P, P, C.POINTER(i64), C.c_int], C.c_int),
+        "rbmd_step_kernel_count": ([P], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -263,6 +266,22 @@ class RBMD:
         b = t.empty((self.n, self.p), dtype=t.int32, device=self.device)
         _check(lib().rbmd_rbl_lists(self._h, step, _ptr(nc), _ptr(ns), _ptr(b)), "rbl_lists")
         return nc, ns, b
+
+    # -- measurement ------------------------------------------------------
+    PROFILE_STAGES = ("kick_drift", "cell_sort", "rbl_pair", "f_corr", "rbe_sample",
+                      "rho_partial", "rho_final", "rbe_force", "kick_thermo")
+
+    def profile(self, enable=True):
+        _check(lib().rbmd_profile(self._h, int(enable)), "profile")
+
+    def profile_read(self, reset=False):
+        ms = np.zeros(len(self.PROFILE_STAGES))
+        n = C.c_int64(0)
+        _check(lib().rbmd_profile_read(self._h, _ptr(ms), C.byref(n), int(reset)), "profile_read")
+        return dict(zip(self.PROFILE_STAGES, ms.tolist())), n.value
+
+    def step_kernel_count(self) -> int:
+        return lib().rbmd_step_kernel_count(self._h)
 
     def debug_latch_error(self, code):
         _check(lib().rbmd_debug_latch_error(self._h, code))

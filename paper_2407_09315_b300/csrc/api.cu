@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/rbmd.h): context set-up, the force,
 // step and energy entry points, checkpoints and verification hooks.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -170,7 +171,8 @@ void free_ctx(rbmd_ctx *c)
                     c->modes,     c->W,         c->rho_part, c->rho,        c->emode,
                     c->coef,      c->cell_count, c->cell_start, c->cell_of, c->cell_rank,
                     c->scan_part, c->spos,      c->sq,       c->stype,      c->fpart,
-                    c->epart,     c->kepart,    c->ibuf,     c->lj_f,       c->lj_d};
+                    c->epart,     c->kepart,    c->ibuf,     c->lj_f,       c->lj_d,
+                    c->lcore,     c->lshell,    c->ncount,   c->bk};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -347,7 +349,7 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     c->Rc2 = radius2_units(p.r_core, c->L);
     c->Rs2 = radius2_units(p.r_cut, c->L);
     c->Rlin = isqrt64(c->Rs2);
-    c->div = p.cell_div == 0 ? 1 : p.cell_div;
+    c->div = p.cell_div == 0 ? 2 : p.cell_div;
     {
         int nc = (int)floor(c->L * c->div / p.r_cut);
         if (nc < 1) nc = 1;
@@ -382,8 +384,27 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     c->rho_tile = 1024;
     c->rho_tiles = (int)((c->N + c->rho_tile - 1) / c->rho_tile);
     c->force_block = 256;
-    c->pair_block = 128;
+    c->pair_block = kPairBlock;
     c->pair_blocks = (int)((c->N + c->pair_block - 1) / c->pair_block);
+    c->pair_parts = (c->pair_blocks + 64) * (kPairBlock / 32);  // + fallback kernel blocks
+    {
+        // list capacities: mean + 8 sd + 8 of a uniform fluid at this density,
+        // rounded up to a multiple of 4; atoms beyond them take the exact fallback
+        const double n = (double)c->N / c->V;
+        const double mc = n * 4.0 / 3.0 * kPi * p.r_core * p.r_core * p.r_core;
+        const double ms = n * 4.0 / 3.0 * kPi * (p.r_cut * p.r_cut * p.r_cut) - mc;
+        c->list_cc = ((int)ceil(mc + 8.0 * sqrt(mc) + 8.0) + 3) / 4 * 4;
+        c->list_cs = ((int)ceil(ms + 8.0 * sqrt(ms) + 8.0) + 3) / 4 * 4;
+        // RBMD_LIST_CAPS="cc,cs" shrinks the capacities so that tests can drive
+        // atoms through the overflow path
+        if (const char *env = getenv("RBMD_LIST_CAPS")) {
+            int cc = 0, cs = 0;
+            if (sscanf(env, "%d,%d", &cc, &cs) == 2 && cc >= 1 && cs >= 1) {
+                c->list_cc = cc;
+                c->list_cs = cs;
+            }
+        }
+    }
     c->kick_blocks = (int)((c->N + 255) / 256);
 
     const size_t rs = real_size(c);
@@ -412,8 +433,12 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     TRY(alloc_n(&c->spos, N));
     TRY(dev_alloc(&c->sq, N * rs));
     TRY(alloc_n(&c->stype, N));
-    TRY(alloc_n(&c->fpart, 3 * (size_t)c->pair_blocks + 3 * (size_t)c->kick_blocks));
-    TRY(alloc_n(&c->epart, 2 * (size_t)c->pair_blocks));
+    TRY(alloc_n(&c->fpart, 3 * (size_t)c->pair_parts));
+    TRY(alloc_n(&c->lcore, (size_t)N * c->list_cc));
+    TRY(alloc_n(&c->lshell, (size_t)N * c->list_cs));
+    TRY(alloc_n(&c->ncount, (size_t)N));
+    TRY(alloc_n(&c->bk, (size_t)N * p.rbl_p));
+    TRY(alloc_n(&c->epart, 2 * (size_t)c->pair_parts));
     TRY(alloc_n(&c->kepart, (size_t)c->kick_blocks));
     TRY(alloc_n(&c->ibuf, 4));
     g_alloc_countdown = -1;
@@ -535,11 +560,32 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
         if (s != RBMD_OK) return leave(c, s);
         c->have_force = true;
     }
+    if (c->profiling && c->prof_eager) {
+        // profiled steps launched one kernel at a time, events between stages
+        for (int64_t k = 0; k < n_steps; ++k) {
+            s = record_step(c);
+            if (s != RBMD_OK) return leave(c, s);
+            if (cudaEventSynchronize(c->prof_ev[RBMD_PROFILE_STAGES]) != cudaSuccess)
+                return leave(c, RBMD_ERR_CUDA);
+            for (int st = 0; st < RBMD_PROFILE_STAGES; ++st) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, c->prof_ev[st], c->prof_ev[st + 1]) == cudaSuccess)
+                    c->prof_ms[st] += ms;
+                else
+                    cudaGetLastError();
+            }
+            ++c->prof_steps;
+        }
+        c->step += n_steps;
+        return leave(c, RBMD_OK);
+    }
     if (!c->graph_ready) {
         cudaGraph_t g;
         if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return leave(c, RBMD_ERR_CUDA);
+        c->capturing = true;
         rbmd_status rs = record_step(c);
+        c->capturing = false;
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (rs != RBMD_OK || e != cudaSuccess) {
             cudaGetLastError();
@@ -563,13 +609,22 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
     for (int64_t k = 0; k < n_steps; ++k) {
         if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return leave(c, RBMD_ERR_CUDA);
         if (c->profiling) {
-            if (cudaEventSynchronize(c->prof_ev[RBMD_PROFILE_STAGES]) != cudaSuccess)
-                return leave(c, RBMD_ERR_CUDA);
-            for (int st = 0; st < RBMD_PROFILE_STAGES; ++st) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, c->prof_ev[st], c->prof_ev[st + 1]);
-                c->prof_ms[st] += ms;
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) return leave(c, RBMD_ERR_CUDA);
+            float ms[RBMD_PROFILE_STAGES];
+            bool ok = true;
+            for (int st = 0; st < RBMD_PROFILE_STAGES && ok; ++st)
+                ok = cudaEventElapsedTime(&ms[st], c->prof_ev[st], c->prof_ev[st + 1]) == cudaSuccess;
+            if (!ok) {
+                // event nodes of this graph cannot be timed: drop the graph and
+                // profile the following steps with eager launches
+                cudaGetLastError();
+                cudaGraphExecDestroy(c->graph);
+                c->graph_ready = false;
+                c->prof_eager = true;
+                c->step += k + 1;
+                return leave(c, rbmd_step(c, n_steps - k - 1));
             }
+            for (int st = 0; st < RBMD_PROFILE_STAGES; ++st) c->prof_ms[st] += ms[st];
             ++c->prof_steps;
         }
     }
@@ -595,8 +650,8 @@ rbmd_status rbmd_energy(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
         s = cells_build(c);
         if (s == RBMD_OK)
             s = rbl_pairs(c, r, c->scratch_force, 0, true, nullptr, nullptr, nullptr);
-        if (s == RBMD_OK) s = md_sum(c, c->fpart, c->pair_blocks, 3, c->scal + SCAL_FSUM, 1.0);
-        if (s == RBMD_OK) s = md_sum(c, c->epart, c->pair_blocks, 2, c->scal + SCAL_ECOUL, 1.0);
+        if (s == RBMD_OK) s = md_sum(c, c->fpart, c->pair_parts, 3, c->scal + SCAL_FSUM, 1.0);
+        if (s == RBMD_OK) s = md_sum(c, c->epart, c->pair_parts, 2, c->scal + SCAL_ECOUL, 1.0);
         if (s == RBMD_OK) {
             k_max_count<<<(unsigned)((c->ncell + 255) / 256), 256, 0, c->stream>>>(
                 c->cell_count, c->ncell, c->ibuf + 1);

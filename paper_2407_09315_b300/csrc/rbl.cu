@@ -182,7 +182,21 @@ rbmd_status cells_build(rbmd_ctx *c)
     return RBMD_OK;
 }
 
-// ---------------------------------------------------------------- pair kernel
+// ---------------------------------------------------------------- pair kernels
+//
+// Algorithm 2 runs as three kernels with one thread per cell-sorted atom, so that
+// each stays small and runs at high occupancy (the short-range step is bound by
+// memory latency and dependent integer chains, not by arithmetic throughput):
+//   k_rbl_scan    step 1: classify every candidate of the neighbour cells and
+//                 store the core and shell lists (sorted indices, capacity CC and
+//                 CS per atom); the counts are exact even when a list is full;
+//   k_rbl_select  step 1: Philox priorities of the shell members and the
+//                 bottom-p batch;
+//   k_rbl_force   step 2: core forces plus the batch forces weighted N_s/p, and
+//                 per-warp FP64 partial sums for F_corr (step 3).
+// An atom whose lists overflowed is skipped by select and force and handled
+// exactly by k_rbl_fused, which recomputes its neighbourhood on its own (it does
+// nothing, apart from zeroing its partial sums, when no list overflowed).
 template <typename real> struct PairArgs {
     const uint4 *spos;
     const real *sq;
@@ -197,12 +211,21 @@ template <typename real> struct PairArgs {
     StepRef step;
     uint32_t tag;
     real ck, alpha, sqrt_alpha, c2, lscale;
+    float cull_r;      // r_cut in cell widths, with a safety margin
     real *F;
     int accumulate;
-    double *fpart;    // [gridDim][3]
-    double *epart;    // [gridDim][2]
-    int32_t *imax;    // [0] max N_s
-    int32_t *n_core, *n_shell, *batch;
+    double *fpart;     // [parts][3]: pair kernel per warp, then the fallback per warp
+    double *epart;     // [parts][2]
+    int64_t fb_part0;  // first partial slot of the fallback kernel
+    int32_t *imax;     // [0] max N_s
+    int32_t *n_core, *n_shell, *batch;  // verification outputs (caller order) or NULL
+    // lists (cell-sorted order)
+    int32_t *lcore;    // [N][CC]
+    int32_t *lshell;   // [N][CS]
+    int2 *ncount;      // [N] (|C|, N_s)
+    int32_t *bk;       // [N][p] sorted indices of the batch
+    int32_t *ovf;      // [0] set when any list overflowed
+    int CC, CS;
 };
 
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
@@ -213,12 +236,12 @@ __device__ __forceinline__ float exp_r(float x) { return expf(x); }
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 
 // Force on i from j (d = r_j - r_i, minimum image) for erfc-Coulomb (Eq. 10) +
-// Lennard-Jones (Eq. 2) with Lorentz-Berthelot parameters (Eq. 4); adds w * F_ij
-// to f and, with ENERGY, w * u_ij to (ec, el).
+// Lennard-Jones (Eq. 2) with Lorentz-Berthelot parameters (Eq. 4); adds F_ij to
+// f and, with ENERGY, u_ij to (ec, el).
 template <typename real, bool ENERGY>
 __device__ __forceinline__ void pair_eval(const PairArgs<real> &a, real dx, real dy, real dz,
-                                          real qq, real eps, real sig, real w, real &fx,
-                                          real &fy, real &fz, double &ec, double &el)
+                                          real qq, real eps, real sig, real &fx, real &fy,
+                                          real &fz, double &ec, double &el)
 {
     const real r2 = dx * dx + dy * dy + dz * dz;
     const real rinv = rsqrt_r(r2);
@@ -230,256 +253,556 @@ __device__ __forceinline__ void pair_eval(const PairArgs<real> &a, real dx, real
     const real s6 = s2 * s2 * s2;
     const real s12 = s6 * s6;
     const real glj = (real)24 * eps * ((real)2 * s12 - s6);  // r * (-dU_lj/dr)
-    const real g = w * (gc + glj) * rinv * rinv;
+    const real g = (gc + glj) * rinv * rinv;
     fx -= g * dx;
     fy -= g * dy;
     fz -= g * dz;
     if constexpr (ENERGY) {
-        ec += (double)(w * qq * er * rinv);
-        el += (double)(w * (real)4 * eps * (s12 - s6));
+        ec += (double)(qq * er * rinv);
+        el += (double)((real)4 * eps * (s12 - s6));
     }
 }
 
-// Bottom-p selection over (priority, id), kept in registers: the slots are
-// addressed with compile-time indices only (predicated), so no local memory.
-template <int CAP> struct BottomP {
-    uint64_t pri[CAP];
-    int32_t k[CAP];
-    int n;
-    int mpos;  // slot of the current maximum (valid once n == p)
-
-    __device__ __forceinline__ void init() { n = 0; mpos = 0; }
-
-    __device__ __forceinline__ static bool greater(uint64_t pa, int ka, uint64_t pb, int kb,
-                                                   const uint4 *spos)
-    {
-        if (pa != pb) return pa > pb;
-        return spos[ka].w > spos[kb].w;  // equal priorities: larger id is "greater"
-    }
-
-    __device__ __forceinline__ void find_max(int p, const uint4 *spos)
-    {
-        uint64_t mp = pri[0];
-        int mk = k[0], pos = 0;
-#pragma unroll
-        for (int e = 1; e < CAP; ++e) {
-            if (e < p && greater(pri[e], k[e], mp, mk, spos)) {
-                mp = pri[e];
-                mk = k[e];
-                pos = e;
-            }
-        }
-        mpos = pos;
-    }
-
-    __device__ __forceinline__ void insert(uint64_t pr, int kk, int p, const uint4 *spos)
-    {
-        if (n < p) {
-#pragma unroll
-            for (int e = 0; e < CAP; ++e)
-                if (e == n) { pri[e] = pr; k[e] = kk; }
-            ++n;
-            if (n == p) find_max(p, spos);
-            return;
-        }
-        uint64_t mp = 0;
-        int mk = 0;
-#pragma unroll
-        for (int e = 0; e < CAP; ++e)
-            if (e == mpos) { mp = pri[e]; mk = k[e]; }
-        if (!greater(mp, mk, pr, kk, spos)) return;
-#pragma unroll
-        for (int e = 0; e < CAP; ++e)
-            if (e == mpos) { pri[e] = pr; k[e] = kk; }
-        find_max(p, spos);
-    }
+// Per-atom context for pair evaluations.
+template <typename real> struct AtomI {
+    uint4 A;
+    real qi, se, hs;
 };
 
-template <typename real, int CAP, bool ENERGY, bool LISTS>
-__global__ void __launch_bounds__(128) k_rbl_pair(PairArgs<real> a)
+template <typename real, bool ENERGY>
+__device__ __forceinline__ void eval_k(const PairArgs<real> &a, const real *s_lj,
+                                       const AtomI<real> &I, int k, real &fx, real &fy, real &fz,
+                                       double &ec, double &el)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *s_lj = reinterpret_cast<real *>(smem_raw);
-    for (int t = threadIdx.x; t < 2 * a.T; t += blockDim.x) s_lj[t] = a.lj[t];
-    __syncthreads();
+    const uint4 B = a.spos[k];
+    const int tj = a.stype[k];
+    pair_eval<real, ENERGY>(a, (real)(int32_t)(B.x - I.A.x) * a.lscale,
+                            (real)(int32_t)(B.y - I.A.y) * a.lscale,
+                            (real)(int32_t)(B.z - I.A.z) * a.lscale, I.qi * a.sq[k],
+                            I.se * s_lj[tj], I.hs + s_lj[a.T + tj], fx, fy, fz, ec, el);
+}
 
-    const int64_t is = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = is < a.N;
-    real fx = 0, fy = 0, fz = 0;
-    double ec = 0.0, el = 0.0;
-    int ns = 0, ncore = 0;
-    uint32_t id_i = 0;
-    if (active) {
-        const uint4 A = a.spos[is];
-        id_i = A.w;
-        const real qi = a.sq[is] * a.ck;
-        const int ti = a.stype[is];
-        const real se_i = s_lj[ti], hs_i = s_lj[a.T + ti];
-        const int nc = a.nc, dv = a.div;
-        const int cx = cell_coord(A.x, nc), cy = cell_coord(A.y, nc), cz = cell_coord(A.z, nc);
-        const bool full = nc >= 2 * dv + 1;  // else every cell along an axis, once
-        const int span = full ? 2 * dv + 1 : nc;
-        const uint32_t step = (uint32_t)step_of(a.step);
-        BottomP<CAP> heap;
-        heap.init();
-        real bx = 0, by = 0, bz = 0;
-        double bec = 0.0, bel = 0.0;
+// Philox4x32-10 of the batch priority for the counter (id_i, id_j, step, tag).
+// Round 0 multiplies only the words id_i and step, so its result is the same for
+// every j of atom i except for one xor with id_j: it is computed once per atom
+// and each candidate runs rounds 1-9 only.
+struct Philox0 {
+    uint32_t x, y, z, w;  // round-0 output with id_j = 0
+};
 
-        for (int ox = 0; ox < span; ++ox) {
-            int gx = full ? cx - dv + ox : ox;
+__device__ __forceinline__ Philox0 philox_round0(uint32_t id_i, uint32_t step, uint32_t tag,
+                                                 uint2 key)
+{
+    uint32_t h0, l0, h1, l1;
+    philox_mulhilo(0xD2511F53u, id_i, h0, l0);
+    philox_mulhilo(0xCD9E8D57u, step, h1, l1);
+    return Philox0{h1 ^ key.x, l1, h0 ^ tag ^ key.y, l0};
+}
+
+__device__ __forceinline__ uint2 philox_rest(const Philox0 &r0, uint32_t id_j, uint2 key)
+{
+    uint4 c = make_uint4(r0.x ^ id_j, r0.y, r0.z, r0.w);
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        key.x += 0x9E3779B9u;
+        key.y += 0xBB67AE85u;
+        uint32_t h0, l0, h1, l1;
+        philox_mulhilo(0xD2511F53u, c.x, h0, l0);
+        philox_mulhilo(0xCD9E8D57u, c.z, h1, l1);
+        c = make_uint4(h1 ^ c.y ^ key.x, l1, h0 ^ c.w ^ key.y, l0);
+    }
+    return make_uint2(c.x, c.y);  // priority = x << 32 | y
+}
+
+// Bottom-p selection over (priority, id), in registers, keyed by the high 32
+// bits of the priority.  The CAP slots hold a sorted list, ascending.  For a
+// batch size p < CAP the lowest CAP - p slots hold "minus infinity" markers, so
+// the largest kept entry is always slot CAP - 1; empty slots hold "plus
+// infinity" (key 0xFFFFFFFF).  An insertion is a branch-free shift in which every
+// slot is updated independently (no serial compare chain).  If the candidate's
+// high word equals a slot's key (probability about 2^-32 per slot) the exact
+// path ranks that slot by the full 64-bit priorities and then the atom id.
+constexpr int SEL_NEG = -2;  // slot marker: minus infinity
+constexpr int SEL_POS = -1;  // slot marker: plus infinity (empty)
+
+struct SelCtx {
+    const uint4 *spos;
+    Philox0 r0;
+    uint2 key;
+};
+
+// true if slot (sorted index hk) orders before the candidate with atom id `id`.
+__device__ __noinline__ bool sel_slot_before(const SelCtx &s, int hk, uint32_t id)
+{
+    if (hk == SEL_NEG) return true;
+    if (hk == SEL_POS) return false;
+    const uint32_t hid = s.spos[hk].w;
+    const uint2 pa = philox_rest(s.r0, hid, s.key), pb = philox_rest(s.r0, id, s.key);
+    if (pa.x != pb.x) return pa.x < pb.x;
+    if (pa.y != pb.y) return pa.y < pb.y;
+    return hid < id;
+}
+
+template <int CAP>
+__device__ __forceinline__ void sel_init(uint32_t (&hh)[CAP], int (&hk)[CAP], int p)
+{
+#pragma unroll
+    for (int e = 0; e < CAP; ++e) {
+        const bool neg = e < CAP - p;
+        hh[e] = neg ? 0u : 0xFFFFFFFFu;
+        hk[e] = neg ? SEL_NEG : SEL_POS;
+    }
+}
+
+template <int CAP>
+__device__ __forceinline__ void sel_insert(uint32_t (&hh)[CAP], int (&hk)[CAP], uint32_t h, int k,
+                                           uint32_t id, const SelCtx &s)
+{
+    bool below[CAP];  // slot e orders before the candidate (a prefix: the list is sorted)
+    bool tie = false;
+#pragma unroll
+    for (int e = 0; e < CAP; ++e) {
+        below[e] = hh[e] < h;
+        tie |= hh[e] == h;
+    }
+    if (tie) {
+#pragma unroll
+        for (int e = 0; e < CAP; ++e)
+            if (hh[e] == h) below[e] = sel_slot_before(s, hk[e], id);
+    }
+    if (below[CAP - 1]) return;  // not below the largest kept entry
+    // drop slot CAP-1 and insert: slots below stay, the first slot not below
+    // takes the candidate, the rest take their lower neighbour
+#pragma unroll
+    for (int e = CAP - 1; e > 0; --e) {
+        const bool b = below[e], bp = below[e - 1];
+        const uint32_t nh = b ? hh[e] : (bp ? h : hh[e - 1]);
+        const int nk = b ? hk[e] : (bp ? k : hk[e - 1]);
+        hh[e] = nh;
+        hk[e] = nk;
+    }
+    if (!below[0]) {
+        hh[0] = h;
+        hk[0] = k;
+    }
+}
+
+__device__ __forceinline__ float cell_frac(uint32_t u, int nc)
+{
+    return (float)(uint32_t)((uint64_t)u * (uint64_t)nc) * 2.3283064365386963e-10f;  // 2^-32
+}
+
+// Calls f(kb, ke) for the contiguous sorted-atom ranges that cover the neighbour
+// cells of position A: the (x, y) rows of the stencil, each as at most two z
+// ranges (periodic wrap).  Rows and z cells that cannot hold an atom within r_cut
+// are skipped by a conservative float test with a 1e-5 margin: this only saves
+// work, membership itself is decided on integers.
+template <typename real, class F>
+__device__ __forceinline__ void stencil_ranges(const PairArgs<real> &a, const uint4 &A, F &&f)
+{
+    const int nc = a.nc, dv = a.div;
+    const int cx = cell_coord(A.x, nc), cy = cell_coord(A.y, nc), cz = cell_coord(A.z, nc);
+    const bool full = nc >= 2 * dv + 1;  // else every cell along an axis, once
+    const int span = full ? 2 * dv + 1 : nc;
+    const float fxc = cell_frac(A.x, nc), fyc = cell_frac(A.y, nc), fzc = cell_frac(A.z, nc);
+    const float Rw = a.cull_r, Rw2 = a.cull_r * a.cull_r;
+    for (int ox = 0; ox < span; ++ox) {
+        float wx = 0.f;
+        int gx = ox;
+        if (full) {
+            const int o = ox - dv;
+            wx = o > 0 ? (float)o - fxc : (o < 0 ? fxc + (float)(-o - 1) : 0.f);
+            if (wx > Rw) continue;
+            gx = cx + o;
             gx += (gx < 0) ? nc : 0;
             gx -= (gx >= nc) ? nc : 0;
-            for (int oy = 0; oy < span; ++oy) {
-                int gy = full ? cy - dv + oy : oy;
+        }
+        for (int oy = 0; oy < span; ++oy) {
+            float wy = 0.f;
+            int gy = oy;
+            if (full) {
+                const int o = oy - dv;
+                wy = o > 0 ? (float)o - fyc : (o < 0 ? fyc + (float)(-o - 1) : 0.f);
+                gy = cy + o;
                 gy += (gy < 0) ? nc : 0;
                 gy -= (gy >= nc) ? nc : 0;
-                const int64_t row = ((int64_t)gx * nc + gy) * nc;
-                // the z cells of this row as at most two contiguous atom ranges
-                int r0b, r0e, r1b = 0, r1e = 0;
-                if (!full) {
-                    r0b = a.cell_start[row];
-                    r0e = a.cell_start[row + nc];
+            }
+            const float rem = Rw2 - wx * wx - wy * wy;
+            if (full && rem < 0.f) continue;
+            const int64_t row = ((int64_t)gx * nc + gy) * nc;
+            int rb0, re0, rb1 = 0, re1 = 0;
+            if (!full) {
+                rb0 = a.cell_start[row];
+                re0 = a.cell_start[row + nc];
+            } else {
+                // z cells reachable within the remaining radius, relative to cz
+                const float rz = sqrtf(fmaxf(rem, 0.f));
+                const int z0 = cz + max(-dv, (int)floorf(fzc - rz));
+                const int z1 = cz + min(dv, (int)floorf(fzc + rz));  // inclusive, may wrap
+                if (z0 < 0) {
+                    rb0 = a.cell_start[row + z0 + nc];
+                    re0 = a.cell_start[row + nc];
+                    rb1 = a.cell_start[row];
+                    re1 = a.cell_start[row + z1 + 1];
+                } else if (z1 >= nc) {
+                    rb0 = a.cell_start[row + z0];
+                    re0 = a.cell_start[row + nc];
+                    rb1 = a.cell_start[row];
+                    re1 = a.cell_start[row + z1 - nc + 1];
                 } else {
-                    const int zlo = cz - dv, zhi = cz + dv;
-                    if (zlo < 0) {
-                        r0b = a.cell_start[row + zlo + nc];
-                        r0e = a.cell_start[row + nc];
-                        r1b = a.cell_start[row];
-                        r1e = a.cell_start[row + zhi + 1];
-                    } else if (zhi >= nc) {
-                        r0b = a.cell_start[row + zlo];
-                        r0e = a.cell_start[row + nc];
-                        r1b = a.cell_start[row];
-                        r1e = a.cell_start[row + zhi - nc + 1];
-                    } else {
-                        r0b = a.cell_start[row + zlo];
-                        r0e = a.cell_start[row + zhi + 1];
-                    }
-                }
-                for (int pass = 0; pass < 2; ++pass) {
-                    const int kb = pass ? r1b : r0b, ke = pass ? r1e : r0e;
-                    for (int k = kb; k < ke; ++k) {
-                        if (k == is) continue;
-                        const uint4 B = a.spos[k];
-                        const int32_t dx = (int32_t)(B.x - A.x);
-                        const int32_t dy = (int32_t)(B.y - A.y);
-                        const int32_t dz = (int32_t)(B.z - A.z);
-                        // |d| > Rlin on any axis: outside r_cut (unsigned wrap test)
-                        if ((uint32_t)dx + a.Rlin > 2u * a.Rlin) continue;
-                        if ((uint32_t)dy + a.Rlin > 2u * a.Rlin) continue;
-                        if ((uint32_t)dz + a.Rlin > 2u * a.Rlin) continue;
-                        const uint64_t D = (uint64_t)((int64_t)dx * dx) +
-                                           (uint64_t)((int64_t)dy * dy) +
-                                           (uint64_t)((int64_t)dz * dz);
-                        if (D > a.Rs2) continue;
-                        const bool core = D < a.Rc2;
-                        if (core) ++ncore;
-                        else ++ns;
-                        if (core || a.exact) {
-                            const int tj = a.stype[k];
-                            pair_eval<real, ENERGY>(a, (real)dx * a.lscale, (real)dy * a.lscale,
-                                                    (real)dz * a.lscale, qi * a.sq[k],
-                                                    se_i * s_lj[tj], hs_i + s_lj[a.T + tj],
-                                                    (real)1, fx, fy, fz, ec, el);
-                        } else {
-                            const uint4 w = philox10(make_uint4(id_i, B.w, step, a.tag), a.key);
-                            heap.insert(((uint64_t)w.x << 32) | w.y, k, a.p, a.spos);
-                        }
-                    }
+                    rb0 = a.cell_start[row + z0];
+                    re0 = a.cell_start[row + z1 + 1];
                 }
             }
+            f(rb0, re0);
+            if (rb1 < re1) f(rb1, re1);
         }
-        if (!a.exact) {
-            const int nb = heap.n;
-            const real wgt = ns > a.p ? (real)ns / (real)a.p : (real)1;
-#pragma unroll
-            for (int e = 0; e < CAP; ++e) {
-                if (e < nb) {
-                    const int k = heap.k[e];
-                    const uint4 B = a.spos[k];
-                    const int tj = a.stype[k];
-                    pair_eval<real, ENERGY>(a, (real)(int32_t)(B.x - A.x) * a.lscale,
-                                            (real)(int32_t)(B.y - A.y) * a.lscale,
-                                            (real)(int32_t)(B.z - A.z) * a.lscale, qi * a.sq[k],
-                                            se_i * s_lj[tj], hs_i + s_lj[a.T + tj], (real)1, bx,
-                                            by, bz, bec, bel);
-                }
-            }
-            fx += wgt * bx;
-            fy += wgt * by;
-            fz += wgt * bz;
-            if constexpr (ENERGY) {
-                ec += (double)wgt * bec;
-                el += (double)wgt * bel;
-            }
-            if constexpr (LISTS) {
-                int32_t ids[CAP];
-#pragma unroll
-                for (int e = 0; e < CAP; ++e) ids[e] = e < nb ? (int32_t)a.spos[heap.k[e]].w : INT32_MAX;
-                for (int x = 1; x < nb; ++x) {  // insertion sort (verification path only)
-                    int32_t v = ids[x];
-                    int y = x - 1;
-                    while (y >= 0 && ids[y] > v) { ids[y + 1] = ids[y]; --y; }
-                    ids[y + 1] = v;
-                }
-                for (int e = 0; e < a.p; ++e)
-                    a.batch[(int64_t)id_i * a.p + e] = (e < nb && e < CAP) ? ids[e] : -1;
-            }
-        }
-        real *f = a.F + 3 * (int64_t)id_i;
-        if (a.accumulate) {
-            f[0] += fx;
-            f[1] += fy;
-            f[2] += fz;
-        } else {
-            f[0] = fx;
-            f[1] = fy;
-            f[2] = fz;
-        }
-        if constexpr (LISTS) {
-            a.n_core[id_i] = ncore;
-            a.n_shell[id_i] = ns;
-            if (a.exact)
-                for (int e = 0; e < a.p; ++e) a.batch[(int64_t)id_i * a.p + e] = -1;
-        }
-        if constexpr (ENERGY) atomicMax(a.imax, ns);
     }
+}
 
-    // block partial sums (fixed order) of F_short and of the energies
+// 0: not a neighbour, 1: core (D < Rc2), 2: shell (Rc2 <= D <= Rs2).  Integer
+// minimum image d = (int32)(u_j - u_i); D = sum d^2 in uint64 (cannot overflow).
+template <typename real>
+__device__ __forceinline__ int classify(const PairArgs<real> &a, const uint4 &A, const uint4 &B)
+{
+    const int32_t dx = (int32_t)(B.x - A.x);
+    const int32_t dy = (int32_t)(B.y - A.y);
+    const int32_t dz = (int32_t)(B.z - A.z);
+    const uint32_t R2x = 2u * a.Rlin;
+    // |d| > Rlin on any axis: outside r_cut (unsigned wrap test)
+    if (((uint32_t)dx + a.Rlin > R2x) | ((uint32_t)dy + a.Rlin > R2x) |
+        ((uint32_t)dz + a.Rlin > R2x))
+        return 0;
+    const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
+                       (uint64_t)((int64_t)dz * dz);
+    if (D > a.Rs2) return 0;
+    return D < a.Rc2 ? 1 : 2;
+}
+
+template <typename real>
+__device__ __forceinline__ bool overflowed(const PairArgs<real> &a, int2 cnt)
+{
+    return cnt.x > a.CC || cnt.y > a.CS;
+}
+
+// Step 1a: lists.
+template <typename real, bool ENERGY, bool LISTS>
+__global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
+{
+    const int64_t is = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (is >= a.N) return;
+    const uint4 A = a.spos[is];
+    int32_t *lc = a.lcore + is * a.CC;
+    int32_t *ls = a.lshell + is * a.CS;
+    int ncore = 0, ns = 0;
+    stencil_ranges(a, A, [&](int kb, int ke) {
+        for (int k = kb; k < ke; k += 4) {
+            uint4 B[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) B[q] = (k + q < ke) ? a.spos[k + q] : A;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = (k + q < ke && k + q != (int)is) ? classify(a, A, B[q]) : 0;
+                if (c == 1) {
+                    if (ncore < a.CC) lc[ncore] = k + q;
+                    ++ncore;
+                } else if (c == 2) {
+                    if (ns < a.CS) ls[ns] = k + q;
+                    ++ns;
+                }
+            }
+        }
+    });
+    const int2 cnt = make_int2(ncore, ns);
+    a.ncount[is] = cnt;
+    if (overflowed(a, cnt)) *a.ovf = 1;
+    if constexpr (ENERGY) atomicMax(a.imax, ns);
+    if constexpr (LISTS) {
+        a.n_core[A.w] = ncore;
+        a.n_shell[A.w] = ns;
+        if (a.exact)
+            for (int e = 0; e < a.p; ++e) a.batch[(int64_t)A.w * a.p + e] = -1;
+    }
+}
+
+// Step 1b: the batch B(i), the p shell members with the smallest Philox priority
+// (all of them when N_s <= p), as sorted indices in bk[i][0..min(N_s,p)).
+template <typename real, int CAP, bool LISTS>
+__global__ void __launch_bounds__(256) k_rbl_select(PairArgs<real> a)
+{
+    const int64_t is = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (is >= a.N) return;
+    const int2 cnt = a.ncount[is];
+    if (overflowed(a, cnt)) return;
+    const int ns = cnt.y;
+    const int32_t *ls = a.lshell + is * a.CS;
+    int32_t *bk = a.bk + is * a.p;
+    const uint32_t id_i = a.spos[is].w;
+    int nb = 0;
+    if (ns <= a.p) {
+        for (int e = 0; e < ns; ++e) bk[e] = ls[e];
+        nb = ns;
+    } else {
+        const SelCtx sel{a.spos, philox_round0(id_i, (uint32_t)step_of(a.step), a.tag, a.key),
+                         a.key};
+        uint32_t hh[CAP];
+        int hk[CAP];
+        sel_init<CAP>(hh, hk, a.p);
+        for (int e = 0; e < ns; ++e) {
+            const int k = ls[e];
+            const uint32_t id = a.spos[k].w;
+            const uint2 w = philox_rest(sel.r0, id, a.key);
+            sel_insert<CAP>(hh, hk, w.x, k, id, sel);
+        }
+#pragma unroll
+        for (int e = 0; e < CAP; ++e)
+            if (hk[e] >= 0) bk[nb++] = hk[e];
+    }
+    if constexpr (LISTS) {
+        // batch ids ascending, -1 padded (verification path only)
+        int32_t *out = a.batch + (int64_t)id_i * a.p;
+        for (int e = 0; e < a.p; ++e) out[e] = -1;
+        for (int e = 0; e < nb; ++e) {
+            const int32_t v = (int32_t)a.spos[bk[e]].w;
+            int y = e - 1;
+            while (y >= 0 && out[y] > v) {
+                out[y + 1] = out[y];
+                --y;
+            }
+            out[y + 1] = v;
+        }
+    }
+}
+
+// Step 2 (+ the partial sums of step 3).
+template <typename real, bool ENERGY>
+__global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
+{
+    __shared__ real s_lj[2 * RBMD_MAX_TYPES];
+    for (int t = threadIdx.x; t < 2 * a.T; t += blockDim.x) s_lj[t] = a.lj[t];
+    __syncthreads();
+    const int64_t is = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    real fx = 0, fy = 0, fz = 0;
+    double ec = 0.0, el = 0.0;
+    if (is < a.N) {
+        const int2 cnt = a.ncount[is];
+        if (!overflowed(a, cnt)) {
+            AtomI<real> I;
+            I.A = a.spos[is];
+            I.qi = a.sq[is] * a.ck;
+            const int ti = a.stype[is];
+            I.se = s_lj[ti];
+            I.hs = s_lj[a.T + ti];
+            const int32_t *lc = a.lcore + is * a.CC;
+            for (int e = 0; e < cnt.x; ++e) eval_k<real, ENERGY>(a, s_lj, I, lc[e], fx, fy, fz, ec, el);
+            if (a.exact) {
+                const int32_t *ls = a.lshell + is * a.CS;
+                for (int e = 0; e < cnt.y; ++e)
+                    eval_k<real, ENERGY>(a, s_lj, I, ls[e], fx, fy, fz, ec, el);
+            } else {
+                const int nb = min(cnt.y, a.p);
+                const real w = cnt.y > a.p ? (real)cnt.y / (real)a.p : (real)1;
+                const int32_t *bk = a.bk + is * a.p;
+                real bx = 0, by = 0, bz = 0;
+                double bec = 0.0, bel = 0.0;
+                for (int e = 0; e < nb; ++e) eval_k<real, ENERGY>(a, s_lj, I, bk[e], bx, by, bz, bec, bel);
+                fx += w * bx;
+                fy += w * by;
+                fz += w * bz;
+                if constexpr (ENERGY) {
+                    ec += (double)w * bec;
+                    el += (double)w * bel;
+                }
+            }
+            real *f = a.F + 3 * (int64_t)I.A.w;
+            if (a.accumulate) {
+                f[0] += fx;
+                f[1] += fy;
+                f[2] += fz;
+            } else {
+                f[0] = fx;
+                f[1] = fy;
+                f[2] = fz;
+            }
+        }
+    }
     double v[5] = {(double)fx, (double)fy, (double)fz, 0.5 * ec, 0.5 * el};
 #pragma unroll
     for (int c = 0; c < 5; ++c)
         for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-    __shared__ double s_acc[5][32];
-    const int warp = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0)
-        for (int c = 0; c < 5; ++c) s_acc[c][warp] = v[c];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        double t[5] = {0, 0, 0, 0, 0};
-        for (int w = 0; w < nw; ++w)
-            for (int c = 0; c < 5; ++c) t[c] += s_acc[c][w];
-        a.fpart[3 * (int64_t)blockIdx.x + 0] = t[0];
-        a.fpart[3 * (int64_t)blockIdx.x + 1] = t[1];
-        a.fpart[3 * (int64_t)blockIdx.x + 2] = t[2];
+    if ((threadIdx.x & 31) == 0) {
+        const int64_t part = (int64_t)blockIdx.x * (kPairBlock / 32) + (threadIdx.x >> 5);
+        a.fpart[3 * part + 0] = v[0];
+        a.fpart[3 * part + 1] = v[1];
+        a.fpart[3 * part + 2] = v[2];
         if constexpr (ENERGY) {
-            a.epart[2 * (int64_t)blockIdx.x + 0] = t[3];
-            a.epart[2 * (int64_t)blockIdx.x + 1] = t[4];
+            a.epart[2 * part + 0] = v[3];
+            a.epart[2 * part + 1] = v[4];
+        }
+    }
+}
+
+// Exact fallback for atoms whose lists overflowed (Algorithm 2 for one atom,
+// fused, with the candidate list in shared memory and flushed when full).
+// Grid-stride over the sorted atoms in a fixed order, so the partial sums stay
+// deterministic.  Returns at once (after zeroing its partial slots) when no
+// list overflowed.
+constexpr int FB_BLOCKS = 64;
+constexpr int FB_LIST = 44;
+
+template <typename real, int CAP, bool ENERGY, bool LISTS>
+__global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
+{
+    __shared__ real s_lj[2 * RBMD_MAX_TYPES];
+    __shared__ int32_t s_k[FB_LIST][kPairBlock];
+    __shared__ uint32_t s_id[FB_LIST][kPairBlock];
+    const int tid = threadIdx.x;
+    real fx = 0, fy = 0, fz = 0;
+    double ec = 0.0, el = 0.0;
+    const bool any = *a.ovf != 0;
+    if (any) {
+        for (int t = tid; t < 2 * a.T; t += blockDim.x) s_lj[t] = a.lj[t];
+        __syncthreads();
+        for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.N;
+             base += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t is = base + tid;
+            if (is >= a.N || !overflowed(a, a.ncount[is])) continue;
+            AtomI<real> I;
+            I.A = a.spos[is];
+            I.qi = a.sq[is] * a.ck;
+            const int ti = a.stype[is];
+            I.se = s_lj[ti];
+            I.hs = s_lj[a.T + ti];
+            const uint32_t id_i = I.A.w;
+            const SelCtx sel{a.spos, philox_round0(id_i, (uint32_t)step_of(a.step), a.tag, a.key),
+                             a.key};
+            uint32_t hh[CAP];
+            int hk[CAP];
+            sel_init<CAP>(hh, hk, a.p);
+            real ax = 0, ay = 0, az = 0;
+            double aec = 0.0, ael = 0.0;
+            int lc = 0, lsn = 0, ncore = 0, ns = 0;
+            auto flush = [&]() {
+                for (int e = 0; e < lsn; ++e) {
+                    const int k = s_k[FB_LIST - 1 - e][tid];
+                    if (a.exact) {
+                        eval_k<real, ENERGY>(a, s_lj, I, k, ax, ay, az, aec, ael);
+                    } else {
+                        const uint32_t id = s_id[FB_LIST - 1 - e][tid];
+                        const uint2 w = philox_rest(sel.r0, id, a.key);
+                        sel_insert<CAP>(hh, hk, w.x, k, id, sel);
+                    }
+                }
+                for (int e = 0; e < lc; ++e) eval_k<real, ENERGY>(a, s_lj, I, s_k[e][tid], ax, ay, az, aec, ael);
+                lc = 0;
+                lsn = 0;
+            };
+            stencil_ranges(a, I.A, [&](int kb, int ke) {
+                for (int k = kb; k < ke; ++k) {
+                    if (k == (int)is) continue;
+                    const uint4 B = a.spos[k];
+                    const int c = classify(a, I.A, B);
+                    if (c == 1) {
+                        s_k[lc][tid] = k;
+                        ++lc;
+                        ++ncore;
+                    } else if (c == 2) {
+                        s_k[FB_LIST - 1 - lsn][tid] = k;
+                        s_id[FB_LIST - 1 - lsn][tid] = B.w;
+                        ++lsn;
+                        ++ns;
+                    }
+                    if (lc + lsn == FB_LIST) flush();
+                }
+            });
+            flush();
+            if (!a.exact) {
+                const real w = ns > a.p ? (real)ns / (real)a.p : (real)1;
+                real bx = 0, by = 0, bz = 0;
+                double bec = 0.0, bel = 0.0;
+#pragma unroll
+                for (int e = 0; e < CAP; ++e)
+                    if (hk[e] >= 0) eval_k<real, ENERGY>(a, s_lj, I, hk[e], bx, by, bz, bec, bel);
+                ax += w * bx;
+                ay += w * by;
+                az += w * bz;
+                if constexpr (ENERGY) {
+                    aec += (double)w * bec;
+                    ael += (double)w * bel;
+                }
+                if constexpr (LISTS) {
+                    int32_t *out = a.batch + (int64_t)id_i * a.p;
+                    for (int e = 0; e < a.p; ++e) out[e] = -1;
+                    int nb = 0;
+#pragma unroll
+                    for (int e = 0; e < CAP; ++e) {
+                        if (hk[e] < 0) continue;
+                        const int32_t v = (int32_t)a.spos[hk[e]].w;
+                        int y = nb - 1;
+                        while (y >= 0 && out[y] > v) {
+                            out[y + 1] = out[y];
+                            --y;
+                        }
+                        out[y + 1] = v;
+                        ++nb;
+                    }
+                }
+            }
+            real *f = a.F + 3 * (int64_t)id_i;
+            if (a.accumulate) {
+                f[0] += ax;
+                f[1] += ay;
+                f[2] += az;
+            } else {
+                f[0] = ax;
+                f[1] = ay;
+                f[2] = az;
+            }
+            fx += ax;
+            fy += ay;
+            fz += az;
+            ec += aec;
+            el += ael;
+        }
+    }
+    double v[5] = {(double)fx, (double)fy, (double)fz, 0.5 * ec, 0.5 * el};
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    if ((tid & 31) == 0) {
+        const int64_t part = a.fb_part0 + (int64_t)blockIdx.x * (kPairBlock / 32) + (tid >> 5);
+        a.fpart[3 * part + 0] = v[0];
+        a.fpart[3 * part + 1] = v[1];
+        a.fpart[3 * part + 2] = v[2];
+        if constexpr (ENERGY) {
+            a.epart[2 * part + 0] = v[3];
+            a.epart[2 * part + 1] = v[4];
         }
     }
 }
 
 template <typename real, int CAP>
-static void launch_pair(const PairArgs<real> &a, int blocks, int threads, size_t smem,
-                        cudaStream_t st, bool energy, bool lists)
+static void launch_rbl(const PairArgs<real> &a, cudaStream_t st, bool energy, bool lists)
 {
+    const unsigned nb256 = (unsigned)((a.N + 255) / 256);
+    const unsigned nbp = (unsigned)((a.N + kPairBlock - 1) / kPairBlock);
     if (lists) {
-        if (energy) k_rbl_pair<real, CAP, true, true><<<blocks, threads, smem, st>>>(a);
-        else k_rbl_pair<real, CAP, false, true><<<blocks, threads, smem, st>>>(a);
+        if (energy) k_rbl_scan<real, true, true><<<nb256, 256, 0, st>>>(a);
+        else k_rbl_scan<real, false, true><<<nb256, 256, 0, st>>>(a);
+        if (!a.exact) k_rbl_select<real, CAP, true><<<nb256, 256, 0, st>>>(a);
     } else {
-        if (energy) k_rbl_pair<real, CAP, true, false><<<blocks, threads, smem, st>>>(a);
-        else k_rbl_pair<real, CAP, false, false><<<blocks, threads, smem, st>>>(a);
+        if (energy) k_rbl_scan<real, true, false><<<nb256, 256, 0, st>>>(a);
+        else k_rbl_scan<real, false, false><<<nb256, 256, 0, st>>>(a);
+        if (!a.exact) k_rbl_select<real, CAP, false><<<nb256, 256, 0, st>>>(a);
+    }
+    if (energy) k_rbl_force<real, true><<<nbp, kPairBlock, 0, st>>>(a);
+    else k_rbl_force<real, false><<<nbp, kPairBlock, 0, st>>>(a);
+    if (lists) {
+        if (energy) k_rbl_fused<real, CAP, true, true><<<FB_BLOCKS, kPairBlock, 0, st>>>(a);
+        else k_rbl_fused<real, CAP, false, true><<<FB_BLOCKS, kPairBlock, 0, st>>>(a);
+    } else {
+        if (energy) k_rbl_fused<real, CAP, true, false><<<FB_BLOCKS, kPairBlock, 0, st>>>(a);
+        else k_rbl_fused<real, CAP, false, false><<<FB_BLOCKS, kPairBlock, 0, st>>>(a);
     }
 }
 
@@ -510,21 +833,29 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     a.sqrt_alpha = (real)sqrt(c->prm.alpha);
     a.c2 = (real)(2.0 * sqrt(c->prm.alpha / kPi));
     a.lscale = (real)c->lscale;
+    a.cull_r = (float)(c->prm.r_cut * c->nc / c->L * (1.0 + 1e-5) + 1e-6);
     a.F = (real *)force;
     a.accumulate = accumulate;
     a.fpart = c->fpart;
     a.epart = c->epart;
+    a.fb_part0 = c->pair_blocks * (int64_t)(kPairBlock / 32);
     a.imax = c->ibuf;
     a.n_core = n_core;
     a.n_shell = n_shell;
     a.batch = batch;
+    a.lcore = c->lcore;
+    a.lshell = c->lshell;
+    a.ncount = c->ncount;
+    a.bk = c->bk;
+    a.ovf = c->ibuf + 2;
+    a.CC = c->list_cc;
+    a.CS = c->list_cs;
+    RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf + 2, 0, sizeof(int32_t), c->stream));
     const bool lists = n_core != nullptr;
-    const int threads = c->pair_block;
-    const int blocks = c->pair_blocks;
-    const size_t smem = sizeof(real) * 2 * c->T;
     const int p = c->prm.rbl_p;
-    if (p <= 16) launch_pair<real, 16>(a, blocks, threads, smem, c->stream, energy, lists);
-    else if (p <= 32) launch_pair<real, 32>(a, blocks, threads, smem, c->stream, energy, lists);
+    if (p <= 10) launch_rbl<real, 10>(a, c->stream, energy, lists);
+    else if (p <= 16) launch_rbl<real, 16>(a, c->stream, energy, lists);
+    else if (p <= 32) launch_rbl<real, 32>(a, c->stream, energy, lists);
     else return RBMD_ERR_UNSUPPORTED;
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
@@ -554,7 +885,7 @@ __global__ void k_add_corr(real *__restrict__ F, int64_t N, const double *__rest
 // kicks instead of in a separate pass.
 rbmd_status rbl_correction(rbmd_ctx *c, void *force, bool apply, int slot)
 {
-    RBMD_CHECK(md_sum(c, c->fpart, c->pair_blocks, 3, c->scal + slot, -1.0 / (double)c->N));
+    RBMD_CHECK(md_sum(c, c->fpart, c->pair_parts, 3, c->scal + slot, -1.0 / (double)c->N));
     if (apply) {
         const unsigned nb = (unsigned)((c->N + 255) / 256);
         if (c->fp64) k_add_corr<double><<<nb, 256, 0, c->stream>>>((double *)force, c->N, c->scal + slot);

@@ -31,6 +31,7 @@ namespace rbmd {
 constexpr double kTwo32 = 4294967296.0;
 constexpr double kTwo64 = 18446744073709551616.0;
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kPairBlock = 128;  // threads per block of the RBL pair kernel
 
 // Step number used by a kernel: (*ptr) + add when ptr is set (graph replays read
 // the device counter), else add.
@@ -147,6 +148,12 @@ struct rbmd_ctx {
     double *lj_d;         // [2*T] (FP64 path)
     int pair_block;
     int pair_blocks;
+    int pair_parts;       // per-warp partial sums: pair kernel, then the fallback
+    int32_t *lcore;       // [N][list_cc] core lists (cell-sorted order)
+    int32_t *lshell;      // [N][list_cs] shell lists
+    int2 *ncount;         // [N] (|C|, N_s)
+    int32_t *bk;          // [N][p] batch (sorted indices)
+    int list_cc, list_cs; // list capacities per atom
     int kick_blocks;
 
     // integrator state
@@ -158,6 +165,8 @@ struct rbmd_ctx {
 
     // per-stage timing (rbmd_profile)
     bool profiling;
+    bool capturing;       // inside the stream capture of the step graph
+    bool prof_eager;      // graph event nodes not timeable: profile without the graph
     cudaEvent_t prof_ev[RBMD_PROFILE_STAGES + 1];
     double prof_ms[RBMD_PROFILE_STAGES];
     int64_t prof_steps;
@@ -182,7 +191,9 @@ namespace rbmd {
 // Records the event that opens stage `k` of the step (profiling only).
 inline void prof_mark(rbmd_ctx *c, int k)
 {
-    if (c->profiling) cudaEventRecord(c->prof_ev[k], c->stream);
+    if (!c->profiling) return;
+    if (c->capturing) cudaEventRecordWithFlags(c->prof_ev[k], c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(c->prof_ev[k], c->stream);
 }
 
 // ---- host-side helpers implemented in the .cu files ----

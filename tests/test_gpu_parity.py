@@ -217,3 +217,45 @@ def test_bit_identical_runs_and_resume():
     assert torch.equal(ua, uc) and torch.equal(va, vc)
     for x in (a, b, c):
         x.close()
+
+
+def test_profiled_steps_match_unprofiled():
+    import torch
+
+    s = synth.electrolyte(2500, seed=16, charges="2:1", n_types=2)
+    a, _ = make_ctx(s, rb.FP32, seed=1, thermostat=1)
+    a.set_state_u(s.u, vel=s.v, step=0)
+    a.step(4)
+    ua, va, _ = a.get_state_u()
+    b, _ = make_ctx(s, rb.FP32, seed=1, thermostat=1)
+    b.set_state_u(s.u, vel=s.v, step=0)
+    b.profile(True)
+    b.step(4)
+    ub, vb, st = b.get_state_u()
+    stages, n = b.profile_read(reset=True)
+    assert st == 4 and n >= 3
+    assert torch.equal(ua, ub) and torch.equal(va, vb)
+    assert stages["rbl_pair"] > 0 and stages["rho_partial"] > 0 and stages["rbe_force"] > 0
+    assert b.step_kernel_count() in (0, a.step_kernel_count())
+    assert a.step_kernel_count() >= 10
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_list_overflow_fallback_is_exact(sys_ragged, prec, monkeypatch):
+    # Capacities far below the neighbour counts: (almost) every atom takes the
+    # fused fallback path; lists, forces and energies must not change.
+    s = sys_ragged
+    monkeypatch.setenv("RBMD_LIST_CAPS", "3,7")
+    ctx, _ = make_ctx(s, prec, seed=2, rbe_P=50)
+    monkeypatch.delenv("RBMD_LIST_CAPS")
+    nc, ns, b = (to_np(t).astype(np.int64) for t in ctx.rbl_lists(4))
+    o = oracle.rbl(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 2, 4)
+    assert np.array_equal(nc, o["n_core"]) and np.array_equal(ns, o["n_shell"])
+    assert np.array_equal(b, o["batch"])
+    F = to_np(ctx.rbl_forces(4))
+    assert rel_err(F, o["F"] - o["Fsum"] / s.n) < TOL[prec]
+    E = ctx.energy(4)
+    assert abs(E["e_lj"] - o["E_lj"]) <= (1e-10 if prec == rb.FP64 else 1e-5) * abs(o["E_lj"])
+    ctx.close()
