@@ -247,6 +247,39 @@ rbmd_status rbmd_profile(rbmd_ctx *ctx, int enable);
 rbmd_status rbmd_profile_read(rbmd_ctx *ctx, double *ms, int64_t *steps, int reset);
 int32_t rbmd_step_kernel_count(rbmd_ctx *ctx);
 
+/*
+ * rbmd_rbe_forces_noalloc -- the RBE force of rbmd_rbe_forces (same mode draws,
+ * same structure factors and force pass, FP32 arithmetic) for callers that
+ * cannot allocate device memory: code that runs while another framework owns
+ * all device memory through its own pool, or a latency-critical path where a
+ * cudaMalloc would synchronise the device.  It needs no context and allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library call); the paper has
+ * no counterpart of this call.
+ *   u          device, uint32 [N][3]: fixed-point fractional positions,
+ *              x = u L / 2^32 (as rbmd_get_state_u returns them).
+ *   charge     device, float [N].
+ *   force      device, float [N][3], overwritten.
+ *   alpha, coulomb_k, P, seed, step, replica: as in rbmd_params / rbmd_rbe_forces.
+ *   stream     cudaStream_t to queue on (NULL = legacy default stream).
+ * Scratch: one static device array of RBMD_NOALLOC_SCRATCH_BYTES, held by every
+ * GPU that loads the library until the process exits and shared by all calls.
+ * Each call writes every scratch value it reads, so nothing carries over from
+ * the previous call, but calls that overlap on the GPU (two streams of the
+ * same device) race on it; calls are also not thread-safe on the host.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.
+ * Errors: RBMD_ERR_INVALID for null pointers, N < 1 or N > 2^31 - 1,
+ * P > RBMD_NOALLOC_MAX_P, or a sampler table longer than RBMD_NOALLOC_MAX_TABLE
+ * entries (box too large for alpha); RBMD_ERR_CUDA if a launch fails.
+ */
+#define RBMD_NOALLOC_MAX_P 512
+#define RBMD_NOALLOC_MAX_TABLE 4096
+#define RBMD_NOALLOC_SCRATCH_BYTES 2359296u /* 2.25 MiB */
+rbmd_status rbmd_rbe_forces_noalloc(const uint32_t *u, const float *charge, int64_t n_atoms,
+                                    double box_length, double alpha, double coulomb_k,
+                                    int32_t P, uint64_t seed, int64_t step, uint32_t replica,
+                                    float *force, void *stream);
+
 /* Device error word injection for failure-path tests: sets the latched error to
  * `code` exactly as a kernel would. */
 rbmd_status rbmd_debug_latch_error(rbmd_ctx *ctx, int32_t code);

@@ -89,6 +89,8 @@ def lib():
         "rbmd_profile": ([P, C.c_int], C.c_int),
         "rbmd_profile_read": ([P, P, C.POINTER(i64), C.c_int], C.c_int),
         "rbmd_step_kernel_count": ([P], i32),
+        "rbmd_rbe_forces_noalloc": ([P, P, i64, dbl, dbl, dbl, i32, C.c_uint64, i64, C.c_uint32,
+                                     P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -119,6 +121,24 @@ def sampler_table(box_length: float, alpha: float):
     H = C.c_double(0.0)
     _check(lib().rbmd_sampler_table(box_length, alpha, C.byref(M), _ptr(T), C.byref(H)))
     return M.value, T, H.value
+
+
+def rbe_forces_noalloc(u, charge, box_length, *, alpha, coulomb_k, P, seed, step, out,
+                       replica=0, stream=None):
+    """RBE force without a context or any device allocation (FP32).
+
+    u: CUDA int32/uint32 tensor [N, 3] of fixed-point positions; charge: CUDA
+    float32 [N]; out: CUDA float32 [N, 3], overwritten.  For callers that cannot
+    allocate device memory; all scratch is a fixed static device array.
+    """
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream(out.device)
+    _check(lib().rbmd_rbe_forces_noalloc(_ptr(u), _ptr(charge), int(u.shape[0]), box_length,
+                                         alpha, coulomb_k, P, seed, step, replica, _ptr(out),
+                                         C.c_void_p(stream.cuda_stream)), "rbe_forces_noalloc")
+    return out
 
 
 class RBMD:
