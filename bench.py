@@ -186,8 +186,9 @@ def roofline(stages_ms_per_step, system, peaks_clock_mhz):
     ops = {
         "rho_partial": N * P * OPS_RHO_PER_ATOM_MODE,
         "rbe_force": N * P * OPS_FORCE_PER_ATOM_MODE,
-        "rbl_pair": N * (OPS_CLASSIFY_PER_NEIGHBOUR * (core + shell) + OPS_PHILOX * shell
-                         + OPS_PAIR * (core + min(shell, p))),
+        "rbl_scan": N * OPS_CLASSIFY_PER_NEIGHBOUR * (core + shell),
+        "rbl_select": N * OPS_PHILOX * shell,
+        "rbl_force": N * OPS_PAIR * (core + min(shell, p)),
     }
     top = max(ops, key=lambda k: stages_ms_per_step.get(k, 0.0))
     t = stages_ms_per_step[top] * 1e-3

@@ -234,15 +234,16 @@ rbmd_status rbmd_sampler_table(double box_length, double alpha, int32_t *M, uint
  * rbmd_profile: enable (1) or disable (0) per-stage timing of rbmd_step; CUDA
  *   events are recorded between the stages inside the step graph and read after
  *   each step (profiling makes rbmd_step wait for every step).  Stages:
- *   0 kick+drift, 1 cell sort, 2 RBL pair kernel, 3 F_corr reduction,
- *   4 RBE mode sampling, 5 structure-factor partials, 6 structure-factor
- *   final reduction, 7 RBE force kernel, 8 kick+thermostat.
+ *   0 kick+drift, 1 cell sort, 2 RBL list scan, 3 RBL batch selection,
+ *   4 RBL pair forces (+ overflow fallback), 5 F_corr reduction,
+ *   6 RBE mode sampling, 7 structure-factor partials, 8 structure-factor
+ *   final reduction, 9 RBE force kernel, 10 kick+thermostat.
  * rbmd_profile_read: accumulated milliseconds per stage (host double
  *   [RBMD_PROFILE_STAGES]) and the number of profiled steps; reset != 0 zeroes them.
  * rbmd_step_kernel_count: kernel launches in one step graph (captured on the
  *   first rbmd_step; 0 before that).
  */
-#define RBMD_PROFILE_STAGES 9
+#define RBMD_PROFILE_STAGES 11
 rbmd_status rbmd_profile(rbmd_ctx *ctx, int enable);
 rbmd_status rbmd_profile_read(rbmd_ctx *ctx, double *ms, int64_t *steps, int reset);
 int32_t rbmd_step_kernel_count(rbmd_ctx *ctx);

@@ -288,8 +288,9 @@ class RBMD:
         return nc, ns, b
 
     # -- measurement ------------------------------------------------------
-    PROFILE_STAGES = ("kick_drift", "cell_sort", "rbl_pair", "f_corr", "rbe_sample",
-                      "rho_partial", "rho_final", "rbe_force", "kick_thermo")
+    PROFILE_STAGES = ("kick_drift", "cell_sort", "rbl_scan", "rbl_select", "rbl_force",
+                      "f_corr", "rbe_sample", "rho_partial", "rho_final", "rbe_force",
+                      "kick_thermo")
 
     def profile(self, enable=True):
         _check(lib().rbmd_profile(self._h, int(enable)), "profile")

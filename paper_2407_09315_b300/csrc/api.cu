@@ -172,7 +172,7 @@ void free_ctx(rbmd_ctx *c)
                     c->coef,      c->cell_count, c->cell_start, c->cell_of, c->cell_rank,
                     c->scan_part, c->spos,      c->sq,       c->stype,      c->fpart,
                     c->epart,     c->kepart,    c->ibuf,     c->lj_f,       c->lj_d,
-                    c->lcore,     c->lshell,    c->ncount,   c->bk};
+                    c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -198,29 +198,26 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
     if (marks) prof_mark(c, 1);
     if (do_rbl) {
         RBMD_CHECK(cells_build(c));
-        if (marks) prof_mark(c, 2);
-        RBMD_CHECK(rbl_pairs(c, s, force, acc, false, nullptr, nullptr, nullptr));
-        if (marks) prof_mark(c, 3);
+        if (marks) prof_mark(c, 2);  // stages 3 and 4 are marked inside
+        RBMD_CHECK(rbl_pairs(c, s, force, acc, false, nullptr, nullptr, nullptr, marks));
+        if (marks) prof_mark(c, 5);
         RBMD_CHECK(rbl_correction(c, force, apply_corr, apply_corr ? SCAL_FCORR_AUX : SCAL_FCORR));
         acc = 1;
     } else {
-        if (marks) prof_mark(c, 2);
-        if (marks) prof_mark(c, 3);
+        for (int k = 2; k <= 5 && marks; ++k) prof_mark(c, k);
         if (!apply_corr)
             RBMD_CHECK_CUDA(cudaMemsetAsync(c->scal + SCAL_FCORR, 0, 3 * sizeof(double), c->stream));
     }
-    if (marks) prof_mark(c, 4);
+    if (marks) prof_mark(c, 6);
     if (do_rbe) {
         RBMD_CHECK(rbe_sample(c, s));
-        if (marks) prof_mark(c, 5);
-        RBMD_CHECK(rbe_structure_factors(c, marks ? 6 : -1));
         if (marks) prof_mark(c, 7);
+        RBMD_CHECK(rbe_structure_factors(c, marks ? 8 : -1));
+        if (marks) prof_mark(c, 9);
         RBMD_CHECK(rbe_apply_forces(c, force, acc));
         acc = 1;
     } else if (marks) {
-        prof_mark(c, 5);
-        prof_mark(c, 6);
-        prof_mark(c, 7);
+        for (int k = 7; k <= 9; ++k) prof_mark(c, k);
     }
     if (!acc)
         RBMD_CHECK_CUDA(cudaMemsetAsync(force, 0, 3 * c->N * real_size(c), c->stream));
@@ -233,9 +230,9 @@ rbmd_status record_step(rbmd_ctx *c)
     prof_mark(c, 0);
     RBMD_CHECK(md_kick_drift(c));
     RBMD_CHECK(forces_into(c, next, c->force, 0, false, true));
-    prof_mark(c, 8);
+    prof_mark(c, 10);
     RBMD_CHECK(md_kick_thermo(c, true));
-    prof_mark(c, 9);
+    prof_mark(c, 11);
     return RBMD_OK;
 }
 
@@ -416,6 +413,7 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     TRY(dev_alloc(&c->force, 3 * N * rs));
     TRY(dev_alloc(&c->scratch_force, 3 * N * (rs > 4 ? rs : 8)));
     TRY(alloc_n(&c->scal, SCAL_COUNT));
+    TRY(alloc_n(&c->red_tmp, (size_t)RED_BLOCKS * 8));
     TRY(alloc_n(&c->err, 1));
     TRY(alloc_n(&c->d_step, 1));
     TRY(alloc_n(&c->cdf, T.size()));

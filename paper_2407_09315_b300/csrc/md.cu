@@ -37,10 +37,40 @@ __global__ void k_sum_parts(const double *__restrict__ parts, int nparts, int nc
     }
 }
 
+// First stage for long inputs: block b sums the contiguous chunk b of the
+// partials (fixed order inside the block), one vector per block.
+__global__ void k_sum_chunks(const double *__restrict__ parts, int nparts, int ncomp, int chunk,
+                             double *__restrict__ out)
+{
+    __shared__ double s[256];
+    const int j0 = blockIdx.x * chunk, j1 = min(nparts, j0 + chunk);
+    for (int c = 0; c < ncomp; ++c) {
+        double v = 0.0;
+        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) v += parts[(int64_t)j * ncomp + c];
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+            if (threadIdx.x < (unsigned)o) s[threadIdx.x] += s[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[(int64_t)blockIdx.x * ncomp + c] = s[0];
+        __syncthreads();
+    }
+}
+
 rbmd_status md_sum(rbmd_ctx *c, const double *parts, int nparts, int ncomp, double *out,
                    double scale)
 {
-    k_sum_parts<<<1, 256, 0, c->stream>>>(parts, nparts, ncomp, out, scale);
+    if (nparts > 4096 && ncomp <= 8) {
+        // two fixed-order stages: RED_BLOCKS chunk sums, then one block
+        const int chunk = (nparts + RED_BLOCKS - 1) / RED_BLOCKS;
+        const int nb = (nparts + chunk - 1) / chunk;
+        k_sum_chunks<<<nb, 256, 0, c->stream>>>(parts, nparts, ncomp, chunk, c->red_tmp);
+        RBMD_LAUNCH_CHECK();
+        k_sum_parts<<<1, 256, 0, c->stream>>>(c->red_tmp, nb, ncomp, out, scale);
+    } else {
+        k_sum_parts<<<1, 256, 0, c->stream>>>(parts, nparts, ncomp, out, scale);
+    }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }

@@ -782,19 +782,23 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
 }
 
 template <typename real, int CAP>
-static void launch_rbl(const PairArgs<real> &a, cudaStream_t st, bool energy, bool lists)
+static void launch_rbl(rbmd_ctx *c, const PairArgs<real> &a, cudaStream_t st, bool energy,
+                       bool lists, bool marks)
 {
     const unsigned nb256 = (unsigned)((a.N + 255) / 256);
     const unsigned nbp = (unsigned)((a.N + kPairBlock - 1) / kPairBlock);
     if (lists) {
         if (energy) k_rbl_scan<real, true, true><<<nb256, 256, 0, st>>>(a);
         else k_rbl_scan<real, false, true><<<nb256, 256, 0, st>>>(a);
+        if (marks) prof_mark(c, 3);
         if (!a.exact) k_rbl_select<real, CAP, true><<<nb256, 256, 0, st>>>(a);
     } else {
         if (energy) k_rbl_scan<real, true, false><<<nb256, 256, 0, st>>>(a);
         else k_rbl_scan<real, false, false><<<nb256, 256, 0, st>>>(a);
+        if (marks) prof_mark(c, 3);
         if (!a.exact) k_rbl_select<real, CAP, false><<<nb256, 256, 0, st>>>(a);
     }
+    if (marks) prof_mark(c, 4);
     if (energy) k_rbl_force<real, true><<<nbp, kPairBlock, 0, st>>>(a);
     else k_rbl_force<real, false><<<nbp, kPairBlock, 0, st>>>(a);
     if (lists) {
@@ -808,7 +812,7 @@ static void launch_rbl(const PairArgs<real> &a, cudaStream_t st, bool energy, bo
 
 template <typename real>
 static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
-                               int32_t *n_core, int32_t *n_shell, int32_t *batch)
+                               int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks)
 {
     PairArgs<real> a;
     a.spos = c->spos;
@@ -853,19 +857,20 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf + 2, 0, sizeof(int32_t), c->stream));
     const bool lists = n_core != nullptr;
     const int p = c->prm.rbl_p;
-    if (p <= 10) launch_rbl<real, 10>(a, c->stream, energy, lists);
-    else if (p <= 16) launch_rbl<real, 16>(a, c->stream, energy, lists);
-    else if (p <= 32) launch_rbl<real, 32>(a, c->stream, energy, lists);
+    if (p <= 10) launch_rbl<real, 10>(c, a, c->stream, energy, lists, marks);
+    else if (p <= 16) launch_rbl<real, 16>(c, a, c->stream, energy, lists, marks);
+    else if (p <= 32) launch_rbl<real, 32>(c, a, c->stream, energy, lists, marks);
     else return RBMD_ERR_UNSUPPORTED;
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
 
 rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
-                      int32_t *n_core, int32_t *n_shell, int32_t *batch)
+                      int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks)
 {
-    if (c->fp64) return rbl_pairs_t<double>(c, s, force, accumulate, energy, n_core, n_shell, batch);
-    return rbl_pairs_t<float>(c, s, force, accumulate, energy, n_core, n_shell, batch);
+    if (c->fp64)
+        return rbl_pairs_t<double>(c, s, force, accumulate, energy, n_core, n_shell, batch, marks);
+    return rbl_pairs_t<float>(c, s, force, accumulate, energy, n_core, n_shell, batch, marks);
 }
 
 // ---------------------------------------------------------------- correction

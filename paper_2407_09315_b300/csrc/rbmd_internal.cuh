@@ -32,6 +32,7 @@ constexpr double kTwo32 = 4294967296.0;
 constexpr double kTwo64 = 18446744073709551616.0;
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kPairBlock = 128;  // threads per block of the RBL pair kernel
+constexpr int RED_BLOCKS = 256;  // first-stage blocks of the long FP64 reductions
 
 // Step number used by a kernel: (*ptr) + add when ptr is set (graph replays read
 // the device counter), else add.
@@ -116,6 +117,7 @@ struct rbmd_ctx {
     void *force;          // internal force buffer for the integrator
     void *scratch_force;  // force buffer for energy evaluations
     double *scal;         // [16] FP64 scalars, see SCAL_* below
+    double *red_tmp;      // [RED_BLOCKS][8] first stage of long reductions
     int *err;
     int64_t *d_step;
 
@@ -207,7 +209,7 @@ rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate);
 // RBL (rbl.cu)
 rbmd_status cells_build(rbmd_ctx *c);
 rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
-                      int32_t *n_core, int32_t *n_shell, int32_t *batch);
+                      int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks = false);
 rbmd_status rbl_correction(rbmd_ctx *c, void *force, bool apply, int slot);
 
 // MD (md.cu)
