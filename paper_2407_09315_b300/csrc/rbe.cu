@@ -105,6 +105,19 @@ rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
 // same atom: a shared-memory broadcast.  The sub-tile sums are combined in FP64
 // in a fixed order and one partial per (atom tile, mode) goes to HBM.
 // --------------------------------------------------------------------------
+// sin and cos of the wrapped phase 2 pi ph / 2^32.  ph is read as a signed
+// fraction of a turn, so the angle lies in [-pi, pi): there the hardware SFU
+// sin/cos (__sincosf) needs no range reduction and its documented absolute error
+// is at most 2^-21.41.  The FP64 path uses sincospi.
+__device__ __forceinline__ void phase_sincos(uint32_t ph, float &s, float &c)
+{
+    __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &s, &c);  // 2 pi / 2^32
+}
+__device__ __forceinline__ void phase_sincos(uint32_t ph, double &s, double &c)
+{
+    sincospi((double)(int32_t)ph * 4.656612873077392578125e-10, &s, &c);
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &comp, float x)
 {
     float y = x - comp;
@@ -151,9 +164,8 @@ __global__ void k_rho_partial(const uint4 *__restrict__ u4, const double *__rest
             for (int a = b; a < e; ++a) {
                 const uint4 A = s_at[a];
                 const uint32_t ph = mx * A.x + my * A.y + mz * A.z;
-                const float t = (float)(int32_t)ph * 4.656612873077392578125e-10f;  // 2^-31
                 float sn, cs;
-                sincospif(t, &sn, &cs);
+                phase_sincos(ph, sn, cs);
                 const float q = __uint_as_float(A.w);
                 kahan_add(sr, cr, q * cs);
                 kahan_add(si, ci, q * sn);
@@ -164,9 +176,8 @@ __global__ void k_rho_partial(const uint4 *__restrict__ u4, const double *__rest
             for (int a = b; a < e; ++a) {
                 const uint4 A = s_at[a];
                 const uint32_t ph = mx * A.x + my * A.y + mz * A.z;
-                const double t = (double)(int32_t)ph * 4.656612873077392578125e-10;
                 double sn, cs;
-                sincospi(t, &sn, &cs);
+                phase_sincos(ph, sn, cs);
                 sr += s_q[a] * cs;
                 si += s_q[a] * sn;
             }
@@ -268,17 +279,6 @@ rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
     }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
-}
-
-// sin and cos of the wrapped phase 2 pi ph / 2^32 (ph read as a signed fraction of
-// a half turn, so the argument of sincospi lies in [-1, 1)).
-__device__ __forceinline__ void phase_sincos(uint32_t ph, float &s, float &c)
-{
-    sincospif((float)(int32_t)ph * 4.656612873077392578125e-10f, &s, &c);
-}
-__device__ __forceinline__ void phase_sincos(uint32_t ph, double &s, double &c)
-{
-    sincospi((double)(int32_t)ph * 4.656612873077392578125e-10, &s, &c);
 }
 
 // --------------------------------------------------------------------------

@@ -626,9 +626,10 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
             }
         }
     }
+    constexpr int NV = ENERGY ? 5 : 3;  // FP64 shuffles are costly: only what is used
     double v[5] = {(double)fx, (double)fy, (double)fz, 0.5 * ec, 0.5 * el};
 #pragma unroll
-    for (int c = 0; c < 5; ++c)
+    for (int c = 0; c < NV; ++c)
         for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
     if ((threadIdx.x & 31) == 0) {
         const int64_t part = (int64_t)blockIdx.x * (kPairBlock / 32) + (threadIdx.x >> 5);
@@ -765,9 +766,10 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
             el += ael;
         }
     }
+    constexpr int NV = ENERGY ? 5 : 3;
     double v[5] = {(double)fx, (double)fy, (double)fz, 0.5 * ec, 0.5 * el};
 #pragma unroll
-    for (int c = 0; c < 5; ++c)
+    for (int c = 0; c < NV; ++c)
         for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
     if ((tid & 31) == 0) {
         const int64_t part = a.fb_part0 + (int64_t)blockIdx.x * (kPairBlock / 32) + (tid >> 5);
