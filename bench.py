@@ -179,6 +179,24 @@ def mean_lists(system):
     return core, shell
 
 
+def captured_traffic():
+    """DRAM bytes per launch from the committed ncu summary, per stage, or {} when
+    a kernel source changed since the capture (the counters no longer apply)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "hot_kernels_step_1M.md")
+    try:
+        m = re.search(r"```json\n(.*?)\n```", open(path).read(), re.S)
+        d = json.loads(m.group(1))
+        for name, sha in d["sources_sha256"].items():
+            src = os.path.join(ROOT, "paper_2407_09315_b300", "csrc", name)
+            if hashlib.sha256(open(src, "rb").read()).hexdigest() != sha:
+                return {}
+        return d["traffic_bytes"]
+    except Exception:
+        return {}
+
+
 def roofline(stages_ms_per_step, system, peaks_clock_mhz):
     """Roofline object for the stage with the largest share of the step."""
     N, P, p = system.n, PARAMS["rbe_P"], PARAMS["rbl_p"]
@@ -195,9 +213,11 @@ def roofline(stages_ms_per_step, system, peaks_clock_mhz):
     clock = 2032.0 if not peaks_clock_mhz else peaks_clock_mhz
     peak = 148 * 128 * clock * 1e6 / 1e12  # Top/s, one FP32 lane-op per lane per clock
     achieved = ops[top] / t / 1e12
+    traffic = captured_traffic().get(top) if N == 1_000_000 else None
     return {"bound": "alu", "kernel": top, "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "Top/s (FP32-pipe lane ops)", "frac": round(achieved / peak, 4),
-            "traffic": None, "ms_per_launch": round(stages_ms_per_step[top], 4),
+            "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2032 MHz (see DESIGN.md)",
+            "traffic": traffic, "ms_per_launch": round(stages_ms_per_step[top], 4),
             "algorithmic_ops_per_launch": ops[top]}
 
 
