@@ -50,6 +50,8 @@ def lib():
                               i64, u32, i32, i32, i64, P, P, P, P, P, P, i32, P, P, P]
         L.orc_forces.argtypes = [i64, P, P, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, i32, i32,
                                  u64, i64, u32, i32, P, P]
+        L.orc_energy_grad.argtypes = [i64, P, P, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, i32,
+                                      i32, u64, i64, u32, i32, P, P, P, P, P]
         L.orc_vv.argtypes = [i64, P, P, P, P, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, i32,
                              i32, u64, i64, u32, i32, dbl, i32, dbl, dbl, i64]
         _lib = L
@@ -253,3 +255,24 @@ def vv(u, v, F, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P, se
 def decode(u, L):
     """x = u * L / 2^32 in FP64."""
     return np.asarray(u, dtype=np.float64) * (L / 4294967296.0)
+
+
+def energy_grad(u, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P, seed, step,
+                replica=0, exact=False):
+    """Total potential E[4] and its gradients (dr [n,3], dq [n], deps [T], dsig [T])
+    with the list weights of the step held fixed."""
+    u = _u(u)
+    q = _d(q)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    eps = _d(eps)
+    sig = _d(sig)
+    n = len(u)
+    E = np.zeros(4)
+    dr = np.zeros((n, 3))
+    dq = np.zeros(n)
+    de = np.zeros(len(eps))
+    ds = np.zeros(len(eps))
+    lib().orc_energy_grad(n, _p(u), _p(q), _p(types), len(eps), _p(eps), _p(sig), L, alpha,
+                          coulomb_k, r_core, r_cut, p, P, seed, step, replica, int(exact),
+                          _p(E), _p(dr), _p(dq), _p(de), _p(ds))
+    return E, dr, dq, de, ds

@@ -717,3 +717,141 @@ void orc_vv(int64_t n, uint32_t *u, double *v, double *F, const double *q, const
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of the total potential of one step,                            */
+/*   E = E_coul_real + E_lj + E_rbe + E_self,                               */
+/* with the list energy E_RBL = 1/2 sum_i sum_j W_ij u_ij (W_ij = 1 for j in */
+/* C(i), N_s(i)/p for j in B(i), 0 otherwise; u_ij = coulomb_k q_i q_j       */
+/* erfc(sqrt(alpha) r)/r + 4 eps_ij[(sigma_ij/r)^12 - (sigma_ij/r)^6],        */
+/* Eqs. 2, 4, 10), the RBE estimate E_rbe = coulomb_k (2 pi S/(V P))         */
+/* sum_l |rho_l|^2 / k_l^2 and E_self = -coulomb_k sqrt(alpha/pi) sum q^2.   */
+/* The weights W are held fixed (they change only when a list membership    */
+/* changes, where E is discontinuous).  Chain rule pair by pair: each       */
+/* ordered pair (i, j) adds 1/2 W_ij du_ij to both atoms it touches.        */
+/* Outputs: E_out[4] (as orc_forces), dr [n][3], dq [n], deps [T], dsig [T]. */
+/* ------------------------------------------------------------------------ */
+void orc_energy_grad(int64_t n, const uint32_t *u, const double *q, const int32_t *type,
+                     int32_t n_types, const double *eps, const double *sig, double L,
+                     double alpha, double coulomb_k, double r_core, double r_cut, int32_t p,
+                     int32_t P, uint64_t seed, int64_t step, uint32_t replica, int32_t exact,
+                     double *E_out, double *dr, double *dq, double *deps, double *dsig)
+{
+    double V = L * L * L;
+    double sa = sqrt(alpha);
+    double *x = (double *)malloc(sizeof(double) * (size_t)(3 * (n > 0 ? n : 1)));
+    orc_decode(n, u, L, x);
+    for (int64_t s = 0; s < 3 * n; ++s) dr[s] = 0.0;
+    for (int64_t i = 0; i < n; ++i) dq[i] = 0.0;
+    for (int t = 0; t < n_types; ++t) { deps[t] = 0.0; dsig[t] = 0.0; }
+    double Ec = 0.0, El = 0.0;
+
+    /* short range: lists of every atom */
+    orc_rbl_sys S;
+    memset(&S, 0, sizeof(S));
+    S.n = n; S.u = u; S.q = q; S.type = type; S.n_types = n_types; S.eps = eps; S.sig = sig;
+    S.L = L; S.alpha = alpha; S.coulomb_k = coulomb_k; S.r_core = r_core; S.r_cut = r_cut;
+    S.p = p; S.seed = seed; S.step = step; S.replica = replica; S.exact = exact;
+    S.Rc2 = orc_rbl_R2(r_core, L);
+    S.Rs2 = orc_rbl_R2(r_cut, L);
+    orc_build_cells(&S);
+    orc_list cand = {0}, core = {0}, shell = {0};
+    int64_t cap_b = 16;
+    int64_t *bt = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap_b);
+    for (int64_t i = 0; i < n; ++i) {
+        orc_candidates(&S, i, &cand);
+        if (cand.count > cap_b) {
+            cap_b = cand.count;
+            bt = (int64_t *)realloc(bt, sizeof(int64_t) * (size_t)cap_b);
+        }
+        int32_t nb = 0;
+        double w = orc_rbl_lists(&S, i, &cand, &core, &shell, bt, &nb);
+        int64_t ntot = core.count + nb;
+        for (int64_t e = 0; e < ntot; ++e) {
+            int64_t j = e < core.count ? core.ids[e] : bt[e - core.count];
+            double W = e < core.count ? 1.0 : w;
+            double r3[3];
+            for (int d = 0; d < 3; ++d) {
+                double dd = x[3 * i + d] - x[3 * j + d];
+                dd -= L * nearbyint(dd / L);
+                r3[d] = dd;
+            }
+            double r = sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
+            int a = type[i], b = type[j];
+            double eij = sqrt(eps[a] * eps[b]);
+            double sij = 0.5 * (sig[a] + sig[b]);
+            double sr6 = pow(sij / r, 6.0), sr12 = sr6 * sr6;
+            double erfr = erfc(sa * r) / r;
+            double uc = coulomb_k * q[i] * q[j] * erfr;
+            double ul = 4.0 * eij * (sr12 - sr6);
+            Ec += 0.5 * W * uc;
+            El += 0.5 * W * ul;
+            /* du/dr */
+            double duc = -coulomb_k * q[i] * q[j] *
+                         (erfc(sa * r) / (r * r) + 2.0 * sa / sqrt(ORC_PI) * exp(-alpha * r * r) / r);
+            double dul = -24.0 * eij * (2.0 * sr12 - sr6) / r;
+            double g = 0.5 * W * (duc + dul);
+            for (int d = 0; d < 3; ++d) {
+                dr[3 * i + d] += g * r3[d] / r;
+                dr[3 * j + d] -= g * r3[d] / r;
+            }
+            /* charges */
+            dq[i] += 0.5 * W * coulomb_k * q[j] * erfr;
+            dq[j] += 0.5 * W * coulomb_k * q[i] * erfr;
+            /* LJ parameters through Lorentz-Berthelot (Eq. 4) */
+            double due = 4.0 * (sr12 - sr6);                   /* du/d eps_ij */
+            double dus = 4.0 * eij * (12.0 * sr12 - 6.0 * sr6) / sij; /* du/d sigma_ij */
+            deps[a] += 0.5 * W * due * 0.5 * sqrt(eps[b] / eps[a]);
+            deps[b] += 0.5 * W * due * 0.5 * sqrt(eps[a] / eps[b]);
+            dsig[a] += 0.5 * W * dus * 0.5;
+            dsig[b] += 0.5 * W * dus * 0.5;
+        }
+    }
+    free(bt);
+    free(cand.ids); free(core.ids); free(shell.ids);
+    free(S.cell_start);
+    free(S.cell_atoms);
+
+    /* RBE estimate: E = sum_l Wl (2 pi/V) |rho_l|^2/k^2 with Wl = coulomb_k S / P */
+    int32_t *m = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * (P > 0 ? P : 1)));
+    orc_rbe_sample(seed, step, replica, P, L, alpha, m);
+    double Ssum = orc_rbe_S(L, alpha);
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(2 * (P > 0 ? P : 1)));
+    orc_structure_factor(n, u, q, L, P, m, rho);
+    double Erbe = 0.0;
+    for (int l = 0; l < P; ++l) {
+        double kx = 2.0 * ORC_PI * m[3 * l] / L, ky = 2.0 * ORC_PI * m[3 * l + 1] / L,
+               kz = 2.0 * ORC_PI * m[3 * l + 2] / L;
+        double k2 = kx * kx + ky * ky + kz * kz;
+        if (k2 == 0.0) continue;
+        double c = coulomb_k * (Ssum / P) * (2.0 * ORC_PI / V) / k2;
+        double re = rho[2 * l], im = rho[2 * l + 1];
+        Erbe += c * (re * re + im * im);
+        for (int64_t i = 0; i < n; ++i) {
+            double th = kx * x[3 * i] + ky * x[3 * i + 1] + kz * x[3 * i + 2];
+            double cs = cos(th), sn = sin(th);
+            /* d|rho|^2/dq_i = 2 (re cos + im sin); d|rho|^2/dr_i = 2 q_i k (im cos - re sin) */
+            dq[i] += c * 2.0 * (re * cs + im * sn);
+            double gr = c * 2.0 * q[i] * (im * cs - re * sn);
+            dr[3 * i] += gr * kx;
+            dr[3 * i + 1] += gr * ky;
+            dr[3 * i + 2] += gr * kz;
+        }
+    }
+    free(rho);
+    free(m);
+
+    /* self energy */
+    double q2 = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        q2 += q[i] * q[i];
+        dq[i] += -2.0 * coulomb_k * sqrt(alpha / ORC_PI) * q[i];
+    }
+    if (E_out) {
+        E_out[0] = Ec;
+        E_out[1] = El;
+        E_out[2] = Erbe;
+        E_out[3] = -coulomb_k * sqrt(alpha / ORC_PI) * q2;
+    }
+    free(x);
+}
