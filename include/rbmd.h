@@ -183,11 +183,25 @@ rbmd_status rbmd_energy(rbmd_ctx *ctx, int64_t step, rbmd_energy_terms *out);
  *   d_sigma  host, double [n_types], dE/d sigma_t (or NULL)
  * The RBL energy weights a pair by its list weight, so dE/dr is the
  * symmetrised force -(1/2) sum_j (W_ij + W_ji) u'(r_ij) r_hat (the paper's
- * one-sided RBL force is not a gradient); with RBMD_RBL_EXACT it equals -F.
- * Synchronises when d_eps or d_sigma is requested.
+ * one-sided RBL force is not a gradient); with RBMD_RBL_EXACT it equals -F
+ * without the momentum correction.  The list weights are those of `step` and
+ * are held fixed (E jumps where a membership changes).  Always synchronises
+ * (the lists of the step must be complete: list capacities grow if needed).
+ * dE/d eps_t needs eps_t > 0.
  */
 rbmd_status rbmd_energy_backward(rbmd_ctx *ctx, int64_t step, double grad_out, void *d_pos,
                                  void *d_q, double *d_eps, double *d_sigma);
+
+/*
+ * rbmd_set_charges -- replace the per-atom charges (device, real [N], caller
+ * order).  Neutrality is not re-checked, so that charge derivatives can be taken
+ * by perturbation; the Fourier sum omits k = 0 either way (Sec. 2.2).
+ * Synchronises.  The next rbmd_step recomputes the forces.
+ * rbmd_set_lj -- replace the per-type LJ parameters (host, double [n_types];
+ * Lorentz-Berthelot mixing, Eq. 4).  Synchronises.
+ */
+rbmd_status rbmd_set_charges(rbmd_ctx *ctx, const void *charge);
+rbmd_status rbmd_set_lj(rbmd_ctx *ctx, const double *lj_eps, const double *lj_sigma);
 
 /* Checkpoint: positions (real [N][3], decoded x = u L / 2^32), velocities
  * (real [N][3]) and the step counter.  Buffers host or device. get_state

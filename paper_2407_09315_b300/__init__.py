@@ -89,6 +89,8 @@ def lib():
         "rbmd_profile": ([P, C.c_int], C.c_int),
         "rbmd_profile_read": ([P, P, C.POINTER(i64), C.c_int], C.c_int),
         "rbmd_step_kernel_count": ([P], i32),
+        "rbmd_set_charges": ([P, P], C.c_int),
+        "rbmd_set_lj": ([P, P, P], C.c_int),
         "rbmd_rbe_forces_noalloc": ([P, P, i64, dbl, dbl, dbl, i32, C.c_uint64, i64, C.c_uint32,
                                      P, P], C.c_int),
     }
@@ -235,6 +237,15 @@ class RBMD:
         _check(lib().rbmd_energy_backward(self._h, step, grad_out, _ptr(dpos), _ptr(dq),
                                           _ptr(de), _ptr(ds)), "energy_backward")
         return dpos, dq, de, ds
+
+    def set_charges(self, q):
+        q = q.to(self.device, self.dtype).contiguous()
+        _check(lib().rbmd_set_charges(self._h, _ptr(q)), "set_charges")
+
+    def set_lj(self, eps, sigma):
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        _check(lib().rbmd_set_lj(self._h, _ptr(eps), _ptr(sigma)), "set_lj")
 
     # -- state ------------------------------------------------------------
     def get_state(self):

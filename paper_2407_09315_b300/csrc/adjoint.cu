@@ -1,0 +1,264 @@
+// Adjoint of the total potential (rbmd_energy_backward): gradients of
+//   E = E_coul_real + E_lj + E_rbe + E_self
+// with respect to positions, charges and the per-type LJ parameters, with the
+// random draws of the step held fixed.  The paper gives forces only; this is
+// the gradient of its energy expressions (Eqs. 2, 4, 8, 10 with the random-batch
+// estimators of Eqs. 12 and 15):
+//   E_RBL = 1/2 sum_i sum_j W_ij u_ij,  W_ij = 1 (j in C(i)), N_s(i)/p (j in B(i));
+// since the lists are one-sided, dE/dr_k = sum_j 1/2 (W_kj + W_jk) u'(r_kj) r_hat,
+// which needs, for every shell neighbour j of k, whether k is in j's batch: the
+// kernel reads j's batch from the lists the forward pass built.
+#include <math.h>
+
+#include "rbmd_internal.cuh"
+
+namespace rbmd {
+
+// d_pos = 0, d_q = g * dE_self/dq = -2 g coulomb_k sqrt(alpha/pi) q
+template <typename real>
+__global__ void k_adj_init(real *__restrict__ dpos, real *__restrict__ dq,
+                           const uint4 *__restrict__ u4, const double *__restrict__ q64,
+                           int64_t N, double gself)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (dpos) {
+        dpos[3 * i] = 0;
+        dpos[3 * i + 1] = 0;
+        dpos[3 * i + 2] = 0;
+    }
+    if (dq) {
+        double q;
+        if constexpr (sizeof(real) == 4) q = (double)__uint_as_float(u4[i].w);
+        else q = q64[i];
+        dq[i] = (real)(gself * q);
+    }
+}
+
+template <typename real> struct AdjArgs {
+    const uint4 *spos;
+    const real *sq;
+    const int32_t *stype;
+    const int32_t *lcore, *lshell, *bk;
+    const int2 *ncount;
+    int64_t N;
+    int CC, CS, p, T, exact;
+    real ck, alpha, sqrt_alpha, c2, lscale;
+    const real *eps, *sig;  // per type (host values copied in)
+    double g;               // grad_out
+    real *dpos, *dq;
+    double *tpart;          // [blocks][2T] per-block (d eps, d sigma) partial sums
+};
+
+__device__ __forceinline__ float erfc_a(float x) { return erfcf(x); }
+__device__ __forceinline__ double erfc_a(double x) { return erfc(x); }
+__device__ __forceinline__ float exp_a(float x) { return expf(x); }
+__device__ __forceinline__ double exp_a(double x) { return exp(x); }
+__device__ __forceinline__ float sqrt_a(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_a(double x) { return sqrt(x); }
+
+constexpr int ADJ_BLOCK = 128;
+
+// One thread per cell-sorted atom k.  Symmetric weights for dE/dr and dE/dq;
+// one-sided weights W_kj for the type sums (each ordered pair counted once).
+template <typename real>
+__global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
+{
+    __shared__ double s_t[2 * RBMD_MAX_TYPES][ADJ_BLOCK / 32];
+    double acc[2 * RBMD_MAX_TYPES];
+    for (int t = 0; t < 2 * a.T; ++t) acc[t] = 0.0;
+    const int64_t ks = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ks < a.N) {
+        const uint4 A = a.spos[ks];
+        const real qk = a.sq[ks];
+        const int tk = a.stype[ks];
+        const int2 cnt = a.ncount[ks];
+        const int nbk = min(cnt.y, a.p);
+        const real wk = cnt.y > a.p ? (real)cnt.y / (real)a.p : (real)1;
+        const int32_t *bk_k = a.bk + ks * a.p;
+        real gx = 0, gy = 0, gz = 0, gq = 0;
+        const int ntot = cnt.x + cnt.y;
+        for (int e = 0; e < ntot; ++e) {
+            const bool core = e < cnt.x;
+            const int js = core ? a.lcore[ks * a.CC + e] : a.lshell[ks * a.CS + (e - cnt.x)];
+            real Wkj = 1, Wjk = 1;
+            if (!core && !a.exact) {
+                Wkj = 0;
+                for (int b = 0; b < nbk; ++b)
+                    if (bk_k[b] == js) Wkj = wk;
+                const int2 cj = a.ncount[js];
+                const int nbj = min(cj.y, a.p);
+                Wjk = 0;
+                const int32_t *bk_j = a.bk + (int64_t)js * a.p;
+                for (int b = 0; b < nbj; ++b)
+                    if (bk_j[b] == (int32_t)ks) Wjk = cj.y > a.p ? (real)cj.y / (real)a.p : (real)1;
+            }
+            const real W = (real)0.5 * (Wkj + Wjk);
+            if (W == (real)0 && Wkj == (real)0) continue;
+            const uint4 B = a.spos[js];
+            const real dx = (real)(int32_t)(B.x - A.x) * a.lscale;  // r_j - r_k
+            const real dy = (real)(int32_t)(B.y - A.y) * a.lscale;
+            const real dz = (real)(int32_t)(B.z - A.z) * a.lscale;
+            const real r2 = dx * dx + dy * dy + dz * dz;
+            const real r = sqrt_a(r2);
+            const real rinv = (real)1 / r;
+            const int tj = a.stype[js];
+            const real qj = a.sq[js];
+            const real eij = sqrt_a(a.eps[tk] * a.eps[tj]);
+            const real sij = (real)0.5 * (a.sig[tk] + a.sig[tj]);
+            const real s2 = sij * sij * rinv * rinv;
+            const real s6 = s2 * s2 * s2, s12 = s6 * s6;
+            const real er = erfc_a(a.sqrt_alpha * r);
+            // u'(r) of erfc-Coulomb and LJ
+            const real du = -a.ck * qk * qj * (er * rinv * rinv + a.c2 * exp_a(-a.alpha * r2) * rinv) -
+                            (real)24 * eij * ((real)2 * s12 - s6) * rinv;
+            // dE/dr_k: u'(r) (r_k - r_j)/r = -u'(r) d / r
+            const real f = W * du * rinv;
+            gx -= f * dx;
+            gy -= f * dy;
+            gz -= f * dz;
+            gq += W * a.ck * qj * er * rinv;
+            if (Wkj != (real)0) {
+                // one-sided: 1/2 W_kj du/d eps_kj d eps_kj/d eps_t (Eq. 4), same for sigma
+                const double hw = 0.5 * (double)Wkj;
+                const double due = 4.0 * ((double)s12 - (double)s6);
+                const double dus = 4.0 * (double)eij * (12.0 * (double)s12 - 6.0 * (double)s6) / (double)sij;
+                acc[tk] += hw * due * 0.5 * sqrt((double)a.eps[tj] / (double)a.eps[tk]);
+                acc[tj] += hw * due * 0.5 * sqrt((double)a.eps[tk] / (double)a.eps[tj]);
+                acc[a.T + tk] += hw * dus * 0.5;
+                acc[a.T + tj] += hw * dus * 0.5;
+            }
+        }
+        const int64_t id = A.w;
+        if (a.dpos) {
+            a.dpos[3 * id] += (real)a.g * gx;
+            a.dpos[3 * id + 1] += (real)a.g * gy;
+            a.dpos[3 * id + 2] += (real)a.g * gz;
+        }
+        if (a.dq) a.dq[id] += (real)a.g * gq;
+    }
+    // per-type block partials, fixed order
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = 0; t < 2 * a.T; ++t) {
+        double v = acc[t] * a.g;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) s_t[t][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * a.T) {
+        double v = 0.0;
+        for (int w = 0; w < ADJ_BLOCK / 32; ++w) v += s_t[threadIdx.x][w];
+        a.tpart[(int64_t)blockIdx.x * 2 * a.T + threadIdx.x] = v;
+    }
+}
+
+// RBE part: dE/dr_i = -F_i (Eq. 12) and dE/dq_i = -sum_l (B_l cos th + A_l sin th),
+// with the coefficients of the forward pass (A = c Im rho, B = c Re rho).
+template <typename real, int CHUNK>
+__global__ void k_rbe_adjoint(const uint4 *__restrict__ u4, const double *__restrict__ q64,
+                              int64_t N, const ModeCoef<real> *__restrict__ coef, int64_t Pm,
+                              real tk, double g, real *__restrict__ dpos, real *__restrict__ dq)
+{
+    __shared__ ModeCoef<real> s_c[CHUNK];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < N;
+    const uint4 A = active ? u4[i] : make_uint4(0, 0, 0, 0);
+    real fx = 0, fy = 0, fz = 0, phi = 0;
+    for (int64_t c0 = 0; c0 < Pm; c0 += CHUNK) {
+        const int nc = (int)min((int64_t)CHUNK, Pm - c0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) s_c[k] = coef[c0 + k];
+        __syncthreads();
+        if (!active) continue;
+        for (int k = 0; k < nc; ++k) {
+            const ModeCoef<real> mc = s_c[k];
+            const uint32_t ph = (uint32_t)mc.mx * A.x + (uint32_t)mc.my * A.y + (uint32_t)mc.mz * A.z;
+            real sn, cs;
+            if constexpr (sizeof(real) == 4)
+                sincospif((float)(int32_t)ph * 4.656612873077392578125e-10f, (float *)&sn, (float *)&cs);
+            else
+                sincospi((double)(int32_t)ph * 4.656612873077392578125e-10, (double *)&sn, (double *)&cs);
+            const real gg = mc.A * cs - mc.B * sn;
+            fx += gg * mc.kx;
+            fy += gg * mc.ky;
+            fz += gg * mc.kz;
+            phi -= mc.B * cs + mc.A * sn;
+        }
+    }
+    if (!active) return;
+    real q;
+    if constexpr (sizeof(real) == 4) q = __uint_as_float(A.w);
+    else q = q64[i];
+    const real s = (real)g * q * tk;
+    if (dpos) {
+        dpos[3 * i] -= s * fx;
+        dpos[3 * i + 1] -= s * fy;
+        dpos[3 * i + 2] -= s * fz;
+    }
+    if (dq) dq[i] += (real)g * phi;
+}
+
+template <typename real>
+static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double *tsum_dev,
+                             const double *eps_h, const double *sig_h)
+{
+    const unsigned nb = (unsigned)((c->N + 255) / 256);
+    const double gself = -2.0 * g * c->prm.coulomb_k * sqrt(c->prm.alpha / kPi);
+    k_adj_init<real><<<nb, 256, 0, c->stream>>>((real *)dpos, (real *)dq, c->u4, c->q64, c->N, gself);
+    RBMD_LAUNCH_CHECK();
+    if (!(c->prm.flags & RBMD_NO_RBL)) {
+        AdjArgs<real> a;
+        a.spos = c->spos;
+        a.sq = (const real *)c->sq;
+        a.stype = c->stype;
+        a.lcore = c->lcore;
+        a.lshell = c->lshell;
+        a.bk = c->bk;
+        a.ncount = c->ncount;
+        a.N = c->N;
+        a.CC = c->list_cc;
+        a.CS = c->list_cs;
+        a.p = c->prm.rbl_p;
+        a.T = c->T;
+        a.exact = (c->prm.flags & RBMD_RBL_EXACT) ? 1 : 0;
+        a.ck = (real)c->prm.coulomb_k;
+        a.alpha = (real)c->prm.alpha;
+        a.sqrt_alpha = (real)sqrt(c->prm.alpha);
+        a.c2 = (real)(2.0 * sqrt(c->prm.alpha / kPi));
+        a.lscale = (real)c->lscale;
+        a.eps = (const real *)c->adj_lj;
+        a.sig = (const real *)c->adj_lj + c->T;
+        a.g = g;
+        a.dpos = (real *)dpos;
+        a.dq = (real *)dq;
+        a.tpart = c->adj_tpart;
+        const unsigned nba = (unsigned)((c->N + ADJ_BLOCK - 1) / ADJ_BLOCK);
+        k_rbl_adjoint<real><<<nba, ADJ_BLOCK, 0, c->stream>>>(a);
+        RBMD_LAUNCH_CHECK();
+        RBMD_CHECK(md_sum(c, c->adj_tpart, (int)nba, 2 * c->T, tsum_dev, 1.0));
+    } else {
+        RBMD_CHECK_CUDA(cudaMemsetAsync(tsum_dev, 0, sizeof(double) * 2 * c->T, c->stream));
+    }
+    if (!(c->prm.flags & RBMD_NO_RBE)) {
+        if constexpr (sizeof(real) == 4)
+            k_rbe_adjoint<float, 256><<<nb, 256, 0, c->stream>>>(
+                c->u4, nullptr, c->N, (const ModeCoef<float> *)c->coef, c->Pm,
+                (float)(2.0 * kPi / c->L), g, (float *)dpos, (float *)dq);
+        else
+            k_rbe_adjoint<double, 128><<<nb, 256, 0, c->stream>>>(
+                c->u4, c->q64, c->N, (const ModeCoef<double> *)c->coef, c->Pm, 2.0 * kPi / c->L,
+                g, (double *)dpos, (double *)dq);
+        RBMD_LAUNCH_CHECK();
+    }
+    (void)eps_h;
+    (void)sig_h;
+    return RBMD_OK;
+}
+
+rbmd_status adjoint_run(rbmd_ctx *c, double g, void *dpos, void *dq, double *tsum_dev)
+{
+    if (c->fp64) return adjoint_t<double>(c, g, dpos, dq, tsum_dev, nullptr, nullptr);
+    return adjoint_t<float>(c, g, dpos, dq, tsum_dev, nullptr, nullptr);
+}
+
+}  // namespace rbmd

@@ -172,7 +172,8 @@ void free_ctx(rbmd_ctx *c)
                     c->coef,      c->cell_count, c->cell_start, c->cell_of, c->cell_rank,
                     c->scan_part, c->spos,      c->sq,       c->stype,      c->fpart,
                     c->epart,     c->kepart,    c->ibuf,     c->lj_f,       c->lj_d,
-                    c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp};
+                    c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp,
+                    c->adj_lj,    c->adj_tpart, c->adj_tsum};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -186,6 +187,34 @@ void free_ctx(rbmd_ctx *c)
 }
 
 size_t real_size(const rbmd_ctx *c) { return c->fp64 ? sizeof(double) : sizeof(float); }
+
+// Per-type LJ tables for the pair kernels (sqrt(eps), sigma/2) and the adjoint
+// (eps, sigma), from host arrays.
+rbmd_status upload_lj(rbmd_ctx *c, const double *eps, const double *sig)
+{
+    std::vector<double> ljd(2 * c->T), raw(2 * c->T);
+    std::vector<float> ljf(2 * c->T), rawf(2 * c->T);
+    for (int t = 0; t < c->T; ++t) {
+        if (!(eps[t] >= 0.0) || !(sig[t] >= 0.0)) return RBMD_ERR_INVALID;
+        ljd[t] = sqrt(eps[t]);
+        ljd[c->T + t] = 0.5 * sig[t];
+        raw[t] = eps[t];
+        raw[c->T + t] = sig[t];
+    }
+    for (int t = 0; t < 2 * c->T; ++t) {
+        ljf[t] = (float)ljd[t];
+        rawf[t] = (float)raw[t];
+    }
+    RBMD_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->fp64) {
+        RBMD_CHECK_CUDA(cudaMemcpy(c->lj_d, ljd.data(), sizeof(double) * 2 * c->T, cudaMemcpyHostToDevice));
+        RBMD_CHECK_CUDA(cudaMemcpy(c->adj_lj, raw.data(), sizeof(double) * 2 * c->T, cudaMemcpyHostToDevice));
+    } else {
+        RBMD_CHECK_CUDA(cudaMemcpy(c->lj_f, ljf.data(), sizeof(float) * 2 * c->T, cudaMemcpyHostToDevice));
+        RBMD_CHECK_CUDA(cudaMemcpy(c->adj_lj, rawf.data(), sizeof(float) * 2 * c->T, cudaMemcpyHostToDevice));
+    }
+    return RBMD_OK;
+}
 
 // Forces of the current configuration, keyed by `s`, into `force` (RBE + RBL);
 // F_corr is written to scal (and added to `force` when apply_corr).
@@ -436,29 +465,18 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     TRY(alloc_n(&c->lshell, (size_t)N * c->list_cs));
     TRY(alloc_n(&c->ncount, (size_t)N));
     TRY(alloc_n(&c->bk, (size_t)N * p.rbl_p));
+    TRY(dev_alloc(&c->adj_lj, 2 * (size_t)c->T * rs));
+    TRY(alloc_n(&c->adj_tpart, (size_t)((N + 127) / 128) * 2 * c->T));
+    TRY(alloc_n(&c->adj_tsum, 2 * (size_t)c->T));
     TRY(alloc_n(&c->epart, 2 * (size_t)c->pair_parts));
     TRY(alloc_n(&c->kepart, (size_t)c->kick_blocks));
     TRY(alloc_n(&c->ibuf, 4));
     g_alloc_countdown = -1;
 
     // LJ tables: sqrt(eps_t), sigma_t/2 (Lorentz-Berthelot, Eq. 4)
-    {
-        std::vector<double> ljd(2 * c->T);
-        std::vector<float> ljf(2 * c->T);
-        for (int t = 0; t < c->T; ++t) {
-            ljd[t] = sqrt(lj_eps[t]);
-            ljd[c->T + t] = 0.5 * lj_sigma[t];
-            ljf[t] = (float)ljd[t];
-            ljf[c->T + t] = (float)ljd[c->T + t];
-        }
-        if (c->fp64) {
-            TRY(alloc_n(&c->lj_d, 2 * c->T));
-            TRY(cuda_status(cudaMemcpy(c->lj_d, ljd.data(), sizeof(double) * 2 * c->T, cudaMemcpyHostToDevice)));
-        } else {
-            TRY(alloc_n(&c->lj_f, 2 * c->T));
-            TRY(cuda_status(cudaMemcpy(c->lj_f, ljf.data(), sizeof(float) * 2 * c->T, cudaMemcpyHostToDevice)));
-        }
-    }
+    if (c->fp64) TRY(alloc_n(&c->lj_d, 2 * c->T));
+    else TRY(alloc_n(&c->lj_f, 2 * c->T));
+    TRY(upload_lj(c, lj_eps, lj_sigma));
     TRY(cuda_status(cudaMemcpy(c->cdf, T.data(), sizeof(uint64_t) * T.size(), cudaMemcpyHostToDevice)));
     if (c->full_modes) {
         TRY(cuda_status(cudaMemcpy(c->modes, full.data(), sizeof(int4) * full.size(), cudaMemcpyHostToDevice)));
@@ -682,8 +700,92 @@ rbmd_status rbmd_energy(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
 rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, void *d_pos, void *d_q,
                                  double *d_eps, double *d_sigma)
 {
-    (void)c; (void)step; (void)grad_out; (void)d_pos; (void)d_q; (void)d_eps; (void)d_sigma;
-    return RBMD_ERR_UNSUPPORTED;
+    if (!c) return RBMD_ERR_INVALID;
+    enter(c);
+    StepRef r{nullptr, step};
+    rbmd_status s = RBMD_OK;
+    if (!(c->prm.flags & RBMD_NO_RBL)) {
+        // complete lists of the step: grow the capacities until nothing overflows
+        for (int attempt = 0; attempt < 8; ++attempt) {
+            s = cells_build(c);
+            if (s == RBMD_OK) s = rbl_lists(c, r);
+            int32_t h[3] = {0, 0, 0};
+            if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(h, c->ibuf, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+            if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+            if (s != RBMD_OK) return leave(c, s);
+            if (h[2] == 0) break;
+            s = rbl_max_counts(c, c->ibuf);
+            if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(h, c->ibuf, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+            if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+            if (s != RBMD_OK) return leave(c, s);
+            const int cc = (max(h[0], c->list_cc) + 8 + 3) / 4 * 4, cs = (max(h[1], c->list_cs) + 8 + 3) / 4 * 4;
+            uint32_t *lc = nullptr, *ls = nullptr;
+            if (dev_alloc((void **)&lc, sizeof(int32_t) * (size_t)c->N * cc) != RBMD_OK ||
+                dev_alloc((void **)&ls, sizeof(int32_t) * (size_t)c->N * cs) != RBMD_OK) {
+                if (lc) cudaFree(lc);
+                return leave(c, RBMD_ERR_OOM);
+            }
+            cudaFree(c->lcore);
+            cudaFree(c->lshell);
+            c->lcore = (int32_t *)lc;
+            c->lshell = (int32_t *)ls;
+            c->list_cc = cc;
+            c->list_cs = cs;
+            if (c->graph_ready) {  // the step graph holds the old list pointers
+                cudaGraphExecDestroy(c->graph);
+                c->graph_ready = false;
+            }
+        }
+    }
+    if (!(c->prm.flags & RBMD_NO_RBE)) {
+        s = rbe_sample(c, r);
+        if (s == RBMD_OK) s = rbe_structure_factors(c);
+        if (s != RBMD_OK) return leave(c, s);
+    }
+    s = adjoint_run(c, grad_out, d_pos, d_q, c->adj_tsum);
+    if (s == RBMD_OK && (d_eps || d_sigma)) {
+        std::vector<double> h(2 * c->T);
+        s = cuda_status(cudaMemcpyAsync(h.data(), c->adj_tsum, sizeof(double) * 2 * c->T,
+                                        cudaMemcpyDeviceToHost, c->stream));
+        if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+        if (s == RBMD_OK)
+            for (int t = 0; t < c->T; ++t) {
+                if (d_eps) d_eps[t] = h[t];
+                if (d_sigma) d_sigma[t] = h[c->T + t];
+            }
+    }
+    return leave(c, s);
+}
+
+rbmd_status rbmd_set_charges(rbmd_ctx *c, const void *charge)
+{
+    if (!c || !charge) return RBMD_ERR_INVALID;
+    enter(c);
+    const unsigned nb = (unsigned)((c->N + 255) / 256);
+    if (c->fp64)
+        k_pack<double><<<nb, 256, 0, c->stream>>>((const double *)charge, c->type, c->N, c->u4, c->q64,
+                                                  c->type, c->T, c->err);
+    else
+        k_pack<float><<<nb, 256, 0, c->stream>>>((const float *)charge, c->type, c->N, c->u4, nullptr,
+                                                 c->type, c->T, c->err);
+    double *parts = (double *)c->scratch_force;
+    k_charge_parts<<<nb, 256, 0, c->stream>>>(c->q64, c->u4, c->N, parts);
+    double h[3];
+    rbmd_status s = md_sum(c, parts, (int)nb, 3, c->scal + SCAL_ERBE, 1.0);
+    if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(h, c->scal + SCAL_ERBE, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    if (s == RBMD_OK) c->e_self = -c->prm.coulomb_k * sqrt(c->prm.alpha / kPi) * h[2];
+    c->have_force = false;
+    return leave(c, s);
+}
+
+rbmd_status rbmd_set_lj(rbmd_ctx *c, const double *lj_eps, const double *lj_sigma)
+{
+    if (!c || !lj_eps || !lj_sigma) return RBMD_ERR_INVALID;
+    enter(c);
+    rbmd_status s = upload_lj(c, lj_eps, lj_sigma);
+    c->have_force = false;
+    return leave(c, s);
 }
 
 rbmd_status rbmd_get_state(rbmd_ctx *c, void *pos, void *vel, int64_t *step)

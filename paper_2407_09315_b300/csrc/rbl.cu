@@ -15,6 +15,7 @@
 //  - F_corr (Eq. 16): per-block FP64 sums of the short-range force, reduced in a
 //    fixed order.
 #include <math.h>
+#include <string.h>
 
 #include "rbmd_internal.cuh"
 
@@ -863,6 +864,73 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     else if (p <= 16) launch_rbl<real, 16>(c, a, c->stream, energy, lists, marks);
     else if (p <= 32) launch_rbl<real, 32>(c, a, c->stream, energy, lists, marks);
     else return RBMD_ERR_UNSUPPORTED;
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+// Lists and batches of step s only (Algorithm 2 step 1), for the adjoint.
+template <typename real>
+static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
+{
+    PairArgs<real> a;
+    memset(&a, 0, sizeof(a));
+    a.spos = c->spos;
+    a.sq = (const real *)c->sq;
+    a.stype = c->stype;
+    a.cell_start = c->cell_start;
+    a.N = c->N;
+    a.nc = c->nc;
+    a.div = c->div;
+    a.T = c->T;
+    a.p = c->prm.rbl_p;
+    a.exact = (c->prm.flags & RBMD_RBL_EXACT) ? 1 : 0;
+    a.Rc2 = c->Rc2;
+    a.Rs2 = c->Rs2;
+    a.Rlin = c->Rlin;
+    a.key = make_uint2((uint32_t)(c->prm.seed & 0xFFFFFFFFu), (uint32_t)(c->prm.seed >> 32));
+    a.step = s;
+    a.tag = RBMD_STREAM_RBL | (c->prm.replica << 8);
+    a.cull_r = (float)(c->prm.r_cut * c->nc / c->L * (1.0 + 1e-5) + 1e-6);
+    a.imax = c->ibuf;
+    a.lcore = c->lcore;
+    a.lshell = c->lshell;
+    a.ncount = c->ncount;
+    a.bk = c->bk;
+    a.ovf = c->ibuf + 2;
+    a.CC = c->list_cc;
+    a.CS = c->list_cs;
+    RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf, 0, 3 * sizeof(int32_t), c->stream));
+    const unsigned nb256 = (unsigned)((a.N + 255) / 256);
+    k_rbl_scan<real, true, false><<<nb256, 256, 0, c->stream>>>(a);
+    if (!a.exact) {
+        const int p = c->prm.rbl_p;
+        if (p <= 10) k_rbl_select<real, 10, false><<<nb256, 256, 0, c->stream>>>(a);
+        else if (p <= 16) k_rbl_select<real, 16, false><<<nb256, 256, 0, c->stream>>>(a);
+        else k_rbl_select<real, 32, false><<<nb256, 256, 0, c->stream>>>(a);
+    }
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+__global__ void k_max_counts(const int2 *__restrict__ cnt, int64_t N, int32_t *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int2 c = cnt[i];
+    atomicMax(out, c.x);
+    atomicMax(out + 1, c.y);
+}
+
+rbmd_status rbl_lists(rbmd_ctx *c, StepRef s)
+{
+    if (c->fp64) return rbl_lists_t<double>(c, s);
+    return rbl_lists_t<float>(c, s);
+}
+
+rbmd_status rbl_max_counts(rbmd_ctx *c, int32_t *out_dev)
+{
+    RBMD_CHECK_CUDA(cudaMemsetAsync(out_dev, 0, 2 * sizeof(int32_t), c->stream));
+    k_max_counts<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->ncount, c->N, out_dev);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }

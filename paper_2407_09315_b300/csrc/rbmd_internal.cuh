@@ -156,6 +156,9 @@ struct rbmd_ctx {
     int2 *ncount;         // [N] (|C|, N_s)
     int32_t *bk;          // [N][p] batch (sorted indices)
     int list_cc, list_cs; // list capacities per atom
+    void *adj_lj;         // real [2T]: eps_t, sigma_t (adjoint)
+    double *adj_tpart;    // [adjoint blocks][2T]
+    double *adj_tsum;     // [2T]
     int kick_blocks;
 
     // integrator state
@@ -211,6 +214,12 @@ rbmd_status cells_build(rbmd_ctx *c);
 rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
                       int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks = false);
 rbmd_status rbl_correction(rbmd_ctx *c, void *force, bool apply, int slot);
+
+rbmd_status rbl_lists(rbmd_ctx *c, StepRef s);
+rbmd_status rbl_max_counts(rbmd_ctx *c, int32_t *out_dev);
+
+// adjoint (adjoint.cu)
+rbmd_status adjoint_run(rbmd_ctx *c, double g, void *dpos, void *dq, double *tsum_dev);
 
 // MD (md.cu)
 rbmd_status md_kick_drift(rbmd_ctx *c);
