@@ -36,6 +36,7 @@ UNIT = "atom-steps/s"
 PARAMS = dict(alpha=0.62, r_core=2.0, r_cut=3.5, rbl_p=10, rbe_P=200, coulomb_k=1.0,
               dt=0.001, temperature=1.0, tau_T=0.1, thermostat=1)
 L2_FLUSH_BYTES = 256 << 20
+WORKLOAD = ["c3"]
 
 # Algorithmic FP32-pipe lane operations per unit of work (each elementary
 # function counted as one operation; FMA as one): see the design doc, roofline.
@@ -52,7 +53,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--skip-fp64", action="store_true")
@@ -60,19 +62,52 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=400_000)
     ap.add_argument("--ref-sample", type=int, default=100_000)
-    return ap.parse_args()
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.n is None:
+        args.n = w["n"]
+    PARAMS.update(w["params"])
+    return args
 
 
-def make_system(n, seed):
+# Workloads: "c3" is the headline (BASELINE config 3); the others are reported
+# with --workload: "c2" 100k 1:1 (config 2), "c4" 10M 1:1 with P = 500 (config 4),
+# "lj001" an LJ fluid at density 0.01 with r_core = 2.5, r_cut = 5, p = 30, RBL only
+# (the paper's Sec. 4.2 LJ efficiency runs), "el001" a 1:1 primitive electrolyte at
+# density 0.01, r_core = 6, r_cut = 12, coulomb_k = 3.5, alpha = 0.362, P = 100 (Sec. 4.2).
+WORKLOADS = {
+    "c3": dict(n=1_000_000, charges="2:1", n_types=4, density=0.2, params={}),
+    "c2": dict(n=100_000, charges="1:1", n_types=1, density=0.2, params={}),
+    "c4": dict(n=10_000_000, charges="1:1", n_types=1, density=0.2, params=dict(rbe_P=500)),
+    "lj001": dict(n=1_000_000, charges="none", n_types=1, density=0.01,
+                  params=dict(r_core=2.5, r_cut=5.0, rbl_p=30, flags=4)),
+    "el001": dict(n=100_000, charges="1:1", n_types=1, density=0.01,
+                  params=dict(r_core=6.0, r_cut=12.0, rbl_p=30, rbe_P=100, alpha=0.362,
+                              coulomb_k=3.5)),
+}
+
+
+def make_system(n, seed, workload="c3"):
     from paper_2407_09315_b300 import synth
-    return synth.electrolyte(n, seed=seed, charges="2:1", n_types=4)
+    w = WORKLOADS[workload]
+    if w["charges"] == "none":
+        s = synth.electrolyte(n, seed=seed, charges="1:1", n_types=w["n_types"],
+                              density=w["density"])
+        s.q = s.q * 0.0
+        return s
+    return synth.electrolyte(n, seed=seed, charges=w["charges"], n_types=w["n_types"],
+                             density=w["density"])
 
 
 def workload_config(args, world):
-    return {"workload": "2:1 electrolyte, N=%d per GPU, density 0.2, 4 LJ types, P=%d, "
-                        "p=%d, r_core=%.1f, r_cut=%.1f, alpha=%.2f, Berendsen NVT"
-                        % (args.n, PARAMS["rbe_P"], PARAMS["rbl_p"], PARAMS["r_core"],
-                           PARAMS["r_cut"], PARAMS["alpha"]),
+    w = WORKLOADS[args.workload]
+    kind = {"2:1": "2:1 electrolyte", "1:1": "1:1 electrolyte", "none": "LJ fluid"}[w["charges"]]
+    return {"workload": "%s, N=%d per GPU, density %g, %d LJ type(s), P=%d, p=%d, r_core=%.1f, "
+                        "r_cut=%.1f, alpha=%.3f, coulomb_k=%.1f, Berendsen NVT%s"
+                        % (kind, args.n, w["density"], w["n_types"], PARAMS["rbe_P"],
+                           PARAMS["rbl_p"], PARAMS["r_core"], PARAMS["r_cut"], PARAMS["alpha"],
+                           PARAMS["coulomb_k"], ", RBL only" if PARAMS.get("flags", 0) & 4 else ""),
+            "preset": args.workload,
             "n_atoms_per_gpu": args.n, "global_atoms": args.n * world,
             "parallelism": "independent replicas" if world > 1 else "single GPU",
             "l2": "flushed (256 MB write) before every timed step"}
@@ -173,7 +208,7 @@ def time_steps(ctx, K, W, flush, profile):
 def mean_lists(system):
     """Mean core and shell neighbour counts of a uniform fluid at this density."""
     import math
-    n = system.n / system.L ** 3
+    n = system.n / system.L ** 3  # number density
     core = n * 4.0 / 3.0 * math.pi * PARAMS["r_core"] ** 3
     shell = n * 4.0 / 3.0 * math.pi * (PARAMS["r_cut"] ** 3 - PARAMS["r_core"] ** 3)
     return core, shell
@@ -213,7 +248,7 @@ def roofline(stages_ms_per_step, system, peaks_clock_mhz):
     clock = 2032.0 if not peaks_clock_mhz else peaks_clock_mhz
     peak = 148 * 128 * clock * 1e6 / 1e12  # Top/s, one FP32 lane-op per lane per clock
     achieved = ops[top] / t / 1e12
-    traffic = captured_traffic().get(top) if N == 1_000_000 else None
+    traffic = captured_traffic().get(top) if (N == 1_000_000 and WORKLOAD[0] == "c3") else None
     return {"bound": "alu", "kernel": top, "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "Top/s (FP32-pipe lane ops)", "frac": round(achieved / peak, 4),
             "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2032 MHz (see DESIGN.md)",
@@ -255,12 +290,12 @@ def e2e_force_step(ctx, system, K, W, device):
             "what": "rbmd_set_state(host pinned positions) + rbmd_forces + D2H of the forces"}
 
 
-def cpu_baseline(n_sample, seed):
+def cpu_baseline(n_sample, seed, workload="c3"):
     import oracle
-    s = make_system(n_sample, seed)
+    s = make_system(n_sample, seed, workload)
     t0 = time.perf_counter()
-    oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, PARAMS["alpha"], 1.0, PARAMS["r_core"],
-                  PARAMS["r_cut"], PARAMS["rbl_p"], PARAMS["rbe_P"], 2, 0)
+    oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, PARAMS["alpha"], PARAMS["coulomb_k"],
+                  PARAMS["r_core"], PARAMS["r_cut"], PARAMS["rbl_p"], PARAMS["rbe_P"], 2, 0)
     t = time.perf_counter() - t0
     return {"value": n_sample / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "one FP64 force evaluation (RBE + RBL + F_corr) of a %d-atom system of the "
@@ -281,10 +316,15 @@ def run_ours(args):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
 
-    system = make_system(args.n, 2 + rank)
+    WORKLOAD[0] = args.workload
+    system = make_system(args.n, 2 + rank, args.workload)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
 
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(device)[0]
     ctx = make_ctx(system, rb.FP32, device)
+    torch.cuda.synchronize()
+    footprint = free0 - torch.cuda.mem_get_info(device)[0]
     clocks = Clocks(local)
     if dist:
         dist.barrier()
@@ -330,6 +370,7 @@ def run_ours(args):
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
         "roofline": roofline(stage_ms, system, 2032.0),
         "gpu_launches": kernels_per_step * args.steps,
+        "device_memory_bytes": int(footprint),
         "kernels_per_step": kernels_per_step,
     }
     if fp64:
@@ -342,7 +383,7 @@ def run_ours(args):
     out["paper_context"] = ("8.20 ms/step nonbonded at N=1e6 (SPC/E water, A100 + 1 CPU core); "
                             "different workload and hardware, not a target")
     if not args.skip_cpu and world == 1:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample, 2)
+        out["cpu_baseline"] = cpu_baseline(min(args.cpu_sample, args.n), 2, args.workload)
     print(json.dumps(out), flush=True)
 
 
@@ -354,18 +395,18 @@ def run_reference(args):
     if rank != 0:
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    s = make_system(args.ref_sample, 2)
+    s = make_system(min(args.ref_sample, args.n), 2, args.workload)
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, PARAMS["alpha"], 1.0,
+        oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, PARAMS["alpha"], PARAMS["coulomb_k"],
                       PARAMS["r_core"], PARAMS["r_cut"], PARAMS["rbl_p"], PARAMS["rbe_P"], 2, k)
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
     sec = sum(times) / len(times)
-    value = args.ref_sample / sec
+    value = s.n / sec
     sample = ("one FP64 force evaluation (RBE + RBL + F_corr) per step of a %d-atom system of the "
-              "same recipe, single thread" % args.ref_sample)
+              "same recipe, single thread" % s.n)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
