@@ -66,19 +66,27 @@ def parse():
     w = WORKLOADS[args.workload]
     if args.n is None:
         args.n = w["n"]
+    if args.n is None and w.get("replicas"):
+        from paper_2407_09315_b300 import synth
+        args.n = int(sum(synth.replica_sizes(w["replicas"], w["n_lo"], w["n_hi"], seed=4)))
     PARAMS.update(w["params"])
     return args
 
 
-# Workloads: "c3" is the headline (BASELINE config 3); the others are reported
-# with --workload: "c2" 100k 1:1 (config 2), "c4" 10M 1:1 with P = 500 (config 4),
-# "lj001" an LJ fluid at density 0.01 with r_core = 2.5, r_cut = 5, p = 30, RBL only
-# (the paper's Sec. 4.2 LJ efficiency runs), "el001" a 1:1 primitive electrolyte at
-# density 0.01, r_core = 6, r_cut = 12, coulomb_k = 3.5, alpha = 0.362, P = 100 (Sec. 4.2).
+# Workloads: "c3" (default) is the headline 1M-ion 2:1 electrolyte; the others
+# are reported with --workload: "c2" 100k 1:1 ions at P = 200, "c4" 10M 1:1 ions
+# at P = 500, "c5" a batch of 64 independent 1:1 replicas with N_r log-uniform in
+# [2000, 200000] at P = 100 (one context, every kernel covers all replicas),
+# "lj001" an LJ fluid at density 0.01 with r_core = 2.5, r_cut = 5, p = 30, RBL
+# only (the paper's Sec. 4.2 LJ efficiency runs), "el001" a 1:1 primitive
+# electrolyte at density 0.01, r_core = 6, r_cut = 12, coulomb_k = 3.5,
+# alpha = 0.362, P = 100 (Sec. 4.2).
 WORKLOADS = {
     "c3": dict(n=1_000_000, charges="2:1", n_types=4, density=0.2, params={}),
     "c2": dict(n=100_000, charges="1:1", n_types=1, density=0.2, params={}),
     "c4": dict(n=10_000_000, charges="1:1", n_types=1, density=0.2, params=dict(rbe_P=500)),
+    "c5": dict(n=None, replicas=64, n_lo=2000, n_hi=200_000, charges="1:1", n_types=1,
+               density=0.2, params=dict(rbe_P=100)),
     "lj001": dict(n=1_000_000, charges="none", n_types=1, density=0.01,
                   params=dict(r_core=2.5, r_cut=5.0, rbl_p=30, flags=4)),
     "el001": dict(n=100_000, charges="1:1", n_types=1, density=0.01,
@@ -87,28 +95,59 @@ WORKLOADS = {
 }
 
 
-def make_system(n, seed, workload="c3"):
+class Batch:
+    """The systems of one context (one, or the replicas of a batched workload)."""
+
+    def __init__(self, systems):
+        import numpy as np
+        self.systems = systems
+        self.R = len(systems)
+        self.n = int(sum(s.n for s in systems))
+        self.sizes = [s.n for s in systems]
+        self.L = [s.L for s in systems] if self.R > 1 else systems[0].L
+        cat = lambda k: np.concatenate([getattr(s, k) for s in systems])
+        self.u, self.q, self.types, self.v = cat("u"), cat("q"), cat("types"), cat("v")
+        self.x = np.concatenate([s.x for s in systems])
+        self.eps, self.sig = systems[0].eps, systems[0].sig
+        # number density of every replica (all are made at the workload's density)
+        self.density = systems[0].n / systems[0].L ** 3
+
+
+def make_system(n, seed, workload="c3", max_replicas=None):
     from paper_2407_09315_b300 import synth
     w = WORKLOADS[workload]
+    if w.get("replicas"):
+        sizes = synth.replica_sizes(w["replicas"], w["n_lo"], w["n_hi"], seed=4)
+        if max_replicas is not None:
+            sizes = sizes[:max_replicas]  # replica r depends on r alone
+        return Batch(synth.replicas(sizes, seed=seed, density=w["density"],
+                                    charges=w["charges"], n_types=w["n_types"]))
     if w["charges"] == "none":
         s = synth.electrolyte(n, seed=seed, charges="1:1", n_types=w["n_types"],
                               density=w["density"])
         s.q = s.q * 0.0
-        return s
-    return synth.electrolyte(n, seed=seed, charges=w["charges"], n_types=w["n_types"],
-                             density=w["density"])
+        return Batch([s])
+    return Batch([synth.electrolyte(n, seed=seed, charges=w["charges"], n_types=w["n_types"],
+                                    density=w["density"])])
 
 
-def workload_config(args, world):
+def workload_config(args, world, system=None):
     w = WORKLOADS[args.workload]
     kind = {"2:1": "2:1 electrolyte", "1:1": "1:1 electrolyte", "none": "LJ fluid"}[w["charges"]]
-    return {"workload": "%s, N=%d per GPU, density %g, %d LJ type(s), P=%d, p=%d, r_core=%.1f, "
+    if w.get("replicas"):
+        size = ("%d independent replicas, N_r log-uniform in [%d, %d] (%d atoms in all) per GPU"
+                % (w["replicas"], w["n_lo"], w["n_hi"], system.n if system else args.n))
+    else:
+        size = "N=%d per GPU" % args.n
+    return {"workload": "%s, %s, density %g, %d LJ type(s), P=%d, p=%d, r_core=%.1f, "
                         "r_cut=%.1f, alpha=%.3f, coulomb_k=%.1f, Berendsen NVT%s"
-                        % (kind, args.n, w["density"], w["n_types"], PARAMS["rbe_P"],
+                        % (kind, size, w["density"], w["n_types"], PARAMS["rbe_P"],
                            PARAMS["rbl_p"], PARAMS["r_core"], PARAMS["r_cut"], PARAMS["alpha"],
                            PARAMS["coulomb_k"], ", RBL only" if PARAMS.get("flags", 0) & 4 else ""),
             "preset": args.workload,
-            "n_atoms_per_gpu": args.n, "global_atoms": args.n * world,
+            "n_atoms_per_gpu": system.n if system else args.n,
+            "global_atoms": (system.n if system else args.n) * world,
+            "replicas_per_gpu": system.R if system else (w.get("replicas") or 1),
             "parallelism": "independent replicas" if world > 1 else "single GPU",
             "l2": "flushed (256 MB write) before every timed step"}
 
@@ -172,10 +211,16 @@ def make_ctx(system, precision, device):
     import paper_2407_09315_b300 as rb
 
     dt = torch.float64 if precision == rb.FP64 else torch.float32
+    extra = {}
+    if system.R > 1:
+        extra = dict(n_atoms=system.sizes, seed=[2 + r for r in range(system.R)],
+                     replica=list(range(system.R)))
+    else:
+        extra = dict(seed=2)
     ctx = rb.RBMD(torch.from_numpy(system.x).to(device, dt), torch.from_numpy(system.q).to(device, dt),
                   system.eps, system.sig, box_length=system.L, precision=precision,
                   vel=torch.from_numpy(system.v).to(device, dt),
-                  types=torch.from_numpy(system.types).to(device), seed=2, **PARAMS)
+                  types=torch.from_numpy(system.types).to(device), **extra, **PARAMS)
     ctx.set_state_u(system.u, vel=system.v, step=0)
     return ctx
 
@@ -208,7 +253,7 @@ def time_steps(ctx, K, W, flush, profile):
 def mean_lists(system):
     """Mean core and shell neighbour counts of a uniform fluid at this density."""
     import math
-    n = system.n / system.L ** 3  # number density
+    n = system.density
     core = n * 4.0 / 3.0 * math.pi * PARAMS["r_core"] ** 3
     shell = n * 4.0 / 3.0 * math.pi * (PARAMS["r_cut"] ** 3 - PARAMS["r_core"] ** 3)
     return core, shell
@@ -290,16 +335,40 @@ def e2e_force_step(ctx, system, K, W, device):
             "what": "rbmd_set_state(host pinned positions) + rbmd_forces + D2H of the forces"}
 
 
-def cpu_baseline(n_sample, seed, workload="c3"):
+def oracle_sample(n_sample, seed, workload):
+    """The systems the oracle times: a workload system of n_sample atoms, or the
+    first replicas of a batched workload up to n_sample atoms."""
+    w = WORKLOADS[workload]
+    if not w.get("replicas"):
+        b = make_system(n_sample, seed, workload)
+        return b.systems, b.n
+    from paper_2407_09315_b300 import synth
+    sizes = synth.replica_sizes(w["replicas"], w["n_lo"], w["n_hi"], seed=4)
+    k = 1
+    while k < len(sizes) and sizes[:k + 1].sum() <= n_sample:
+        k += 1
+    b = make_system(n_sample, seed, workload, max_replicas=k)
+    return b.systems, b.n
+
+
+def oracle_forces(systems, step):
     import oracle
-    s = make_system(n_sample, seed, workload)
+    for r, s in enumerate(systems):
+        oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, PARAMS["alpha"], PARAMS["coulomb_k"],
+                      PARAMS["r_core"], PARAMS["r_cut"], PARAMS["rbl_p"], PARAMS["rbe_P"], 2 + r,
+                      step, replica=r if len(systems) > 1 else 0)
+
+
+def cpu_baseline(n_sample, seed, workload="c3"):
+    systems, n = oracle_sample(n_sample, seed, workload)
     t0 = time.perf_counter()
-    oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, PARAMS["alpha"], PARAMS["coulomb_k"],
-                  PARAMS["r_core"], PARAMS["r_cut"], PARAMS["rbl_p"], PARAMS["rbe_P"], 2, 0)
+    oracle_forces(systems, 0)
     t = time.perf_counter() - t0
-    return {"value": n_sample / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one FP64 force evaluation (RBE + RBL + F_corr) of a %d-atom system of the "
-                      "same recipe, single thread, %.1f s" % (n_sample, t)}
+    what = ("a %d-atom system" % n if not WORKLOADS[workload].get("replicas") else
+            "the first %d replica(s) (%d atoms)" % (len(systems), n))
+    return {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one FP64 force evaluation (RBE + RBL + F_corr) of %s of the "
+                      "same recipe, single thread, %.1f s" % (what, t)}
 
 
 def run_ours(args):
@@ -318,6 +387,7 @@ def run_ours(args):
 
     WORKLOAD[0] = args.workload
     system = make_system(args.n, 2 + rank, args.workload)
+    args.n = system.n
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
 
     torch.cuda.synchronize()
@@ -365,8 +435,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "ms_per_step_median": round(statistics.median(ms), 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded 2:1 electrolyte, see DESIGN.md)",
-        "config": workload_config(args, world),
+        "data": "synthetic (seeded %s, see DESIGN.md)" % WORKLOADS[args.workload]["charges"].replace("none", "LJ fluid"),
+        "config": workload_config(args, world, system),
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
         "roofline": roofline(stage_ms, system, 2032.0),
         "gpu_launches": kernels_per_step * args.steps,
@@ -395,22 +465,24 @@ def run_reference(args):
     if rank != 0:
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    s = make_system(min(args.ref_sample, args.n), 2, args.workload)
+    n_sample = min(args.ref_sample, args.n) if args.n else args.ref_sample
+    systems, n = oracle_sample(n_sample, 2, args.workload)
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, PARAMS["alpha"], PARAMS["coulomb_k"],
-                      PARAMS["r_core"], PARAMS["r_cut"], PARAMS["rbl_p"], PARAMS["rbe_P"], 2, k)
+        oracle_forces(systems, k)
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
     sec = sum(times) / len(times)
-    value = s.n / sec
-    sample = ("one FP64 force evaluation (RBE + RBL + F_corr) per step of a %d-atom system of the "
-              "same recipe, single thread" % s.n)
+    value = n / sec
+    what = ("a %d-atom system" % n if not WORKLOADS[args.workload].get("replicas") else
+            "the first %d replica(s) (%d atoms)" % (len(systems), n))
+    sample = ("one FP64 force evaluation (RBE + RBL + F_corr) per step of %s of the "
+              "same recipe, single thread" % what)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded 2:1 electrolyte, see DESIGN.md)",
+           "data": "synthetic (seeded %s, see DESIGN.md)" % WORKLOADS[args.workload]["charges"].replace("none", "LJ fluid"),
            "config": workload_config(args, world),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},

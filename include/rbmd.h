@@ -135,6 +135,37 @@ rbmd_status rbmd_init(const rbmd_params *params, const void *pos, const void *ve
                       const void *charge, const int32_t *type, const double *lj_eps,
                       const double *lj_sigma, void *stream, rbmd_ctx **out);
 
+/*
+ * rbmd_init_batch -- one context over R independent systems (replicas) that are
+ * stepped together: every kernel of a step covers all of them in one launch, so
+ * small systems fill the GPU.  Replicas never interact; each has its own box,
+ * cells, modes, momentum correction, thermostat and energies.  The paper runs
+ * one system per job; batching is this library's addition (the per-system
+ * arithmetic is unchanged, so replica r of a batch gives the same lists, modes
+ * and draws as a stand-alone context with the same parameters).
+ *   params   host, rbmd_params [R].  Per replica: n_atoms, box_length, seed,
+ *            replica, temperature.  Every other field must equal params[0]'s
+ *            (INVALID otherwise).  RBMD_FULL_EWALD_MODES needs R == 1
+ *            (UNSUPPORTED otherwise).
+ *   pos, vel, charge, type  as in rbmd_init, concatenated in replica order
+ *            (replica r's atoms start at n_atoms[0] + ... + n_atoms[r-1]);
+ *            each replica must be neutral on its own.
+ *   lj_eps, lj_sigma  host, double [n_types], shared by all replicas.
+ * Every per-atom buffer of the other entry points (forces, state, gradients,
+ * lists) is the concatenated [N_total] array; atom ids in rbmd_rbl_lists are
+ * indices into it.  rbmd_rbe_modes returns R blocks of P modes.  The gradients of
+ * rbmd_energy_backward are those of the sum of the replicas' potentials (so
+ * d_pos and d_q are per replica, d_eps and d_sigma summed over replicas).
+ * Errors: as rbmd_init, plus INVALID for R < 1 or mismatched shared fields.
+ */
+rbmd_status rbmd_init_batch(const rbmd_params *params, int32_t R, const void *pos,
+                            const void *vel, const void *charge, const int32_t *type,
+                            const double *lj_eps, const double *lj_sigma, void *stream,
+                            rbmd_ctx **out);
+
+/* Number of replicas of the context (1 for rbmd_init), 0 for NULL. */
+int32_t rbmd_replica_count(rbmd_ctx *ctx);
+
 /* Free every device buffer of the context (waits for its stream). NULL is a no-op. */
 void rbmd_destroy(rbmd_ctx *ctx);
 
@@ -173,6 +204,13 @@ rbmd_status rbmd_step(rbmd_ctx *ctx, int64_t n_steps);
  * draws of `step` (out: host).  Synchronises; returns a latched device error.
  */
 rbmd_status rbmd_energy(rbmd_ctx *ctx, int64_t step, rbmd_energy_terms *out);
+
+/*
+ * rbmd_energy_batch -- rbmd_energy for every replica: out is host
+ * rbmd_energy_terms [R] (replica order).  rbmd_energy is INVALID on a context
+ * with R > 1.  max_shell and max_cell are taken over the whole batch.
+ */
+rbmd_status rbmd_energy_batch(rbmd_ctx *ctx, int64_t step, rbmd_energy_terms *out);
 
 /*
  * rbmd_energy_backward -- gradients of E = e_coul_real + e_lj + e_rbe + e_self
@@ -223,7 +261,8 @@ rbmd_status rbmd_sync(rbmd_ctx *ctx);
  * rbmd_rbe_modes: the P modes m_l of `step` (host int32 [P][3], or NULL) and the
  *   structure factors rho_l (host double [P][2] = re, im, or NULL), reduced on the
  *   device in the context's precision.  In full-Ewald mode P is the full mode count
- *   (rbmd_rbe_mode_count).  Synchronises.
+ *   (rbmd_rbe_mode_count).  A batch context returns R consecutive blocks of P
+ *   ([R][P][3] and [R][P][2]).  Synchronises.
  * rbmd_rbl_lists: per atom (caller order) the core count |C(i)|, shell count N_s,
  *   and the batch B(i) as atom ids ascending, -1 padded (device int32 [N], [N],
  *   [N][p]; all three required).

@@ -69,6 +69,9 @@ def lib():
         "rbmd_status_string": ([C.c_int], C.c_char_p),
         "rbmd_version": ([], C.c_char_p),
         "rbmd_init": ([C.POINTER(Params), P, P, P, P, P, P, P, C.POINTER(P)], C.c_int),
+        "rbmd_init_batch": ([C.POINTER(Params), i32, P, P, P, P, P, P, P, C.POINTER(P)], C.c_int),
+        "rbmd_replica_count": ([P], i32),
+        "rbmd_energy_batch": ([P, i64, C.POINTER(EnergyTerms)], C.c_int),
         "rbmd_destroy": ([P], None),
         "rbmd_rbe_forces": ([P, i64, P, C.c_int], C.c_int),
         "rbmd_rbl_forces": ([P, i64, P, C.c_int], C.c_int),
@@ -149,12 +152,17 @@ class RBMD:
     pos, vel: CUDA tensors [N, 3] (float32 for FP32 contexts, float64 for FP64);
     charge: CUDA tensor [N] of the same dtype; types: CUDA int32 tensor [N] or None;
     eps, sigma: per-type LJ parameters (host sequences).
+
+    A batch of R independent replicas is made by giving box_length as a sequence
+    of R boxes and n_atoms as the R atom counts (seed, replica and temperature may
+    be scalars or length-R sequences); pos, charge, vel and types are then the
+    replicas' arrays concatenated in order.
     """
 
     def __init__(self, pos, charge, eps, sigma, *, box_length, alpha=0.62, r_core=2.0,
                  r_cut=3.5, rbl_p=10, rbe_P=100, coulomb_k=1.0, dt=0.001, temperature=1.0,
                  tau_T=0.1, thermostat=0, seed=0, replica=0, precision=FP32, flags=0,
-                 cell_div=0, vel=None, types=None, stream=None):
+                 cell_div=0, vel=None, types=None, stream=None, n_atoms=None):
         import torch
 
         self._torch = torch
@@ -167,11 +175,31 @@ class RBMD:
         self.n = n
         self.n_types = len(eps)
         self.p = rbl_p
-        self.params = Params(n_atoms=n, n_types=len(eps), rbe_P=rbe_P, box_length=box_length,
-                             alpha=alpha, r_core=r_core, r_cut=r_cut, rbl_p=rbl_p,
-                             thermostat=thermostat, coulomb_k=coulomb_k, dt=dt,
-                             temperature=temperature, tau_T=tau_T, seed=seed, replica=replica,
-                             precision=precision, flags=flags, cell_div=cell_div)
+        batched = np.ndim(box_length) > 0
+        boxes = list(box_length) if batched else [box_length]
+        R = len(boxes)
+        sizes = list(n_atoms) if batched else [n]
+        if len(sizes) != R or sum(sizes) != n:
+            raise ValueError("n_atoms must list one size per box and sum to pos.shape[0]")
+
+        def per(v):
+            return list(v) if np.ndim(v) > 0 else [v] * R
+
+        seeds, reps, temps = per(seed), per(replica), per(temperature)
+        self.R = R
+        self.sizes = sizes
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        self.box_lengths = boxes
+        prm = (Params * R)()
+        for r in range(R):
+            prm[r] = Params(n_atoms=sizes[r], n_types=len(eps), rbe_P=rbe_P,
+                            box_length=boxes[r], alpha=alpha, r_core=r_core, r_cut=r_cut,
+                            rbl_p=rbl_p, thermostat=thermostat, coulomb_k=coulomb_k, dt=dt,
+                            temperature=temps[r], tau_T=tau_T, seed=seeds[r],
+                            replica=reps[r], precision=precision, flags=flags,
+                            cell_div=cell_div)
+        self.params = prm[0]
+        self._params = prm
         pos = pos.to(self.dtype).contiguous()
         charge = charge.to(self.dtype).contiguous()
         vel = None if vel is None else vel.to(self.dtype).contiguous()
@@ -180,9 +208,9 @@ class RBMD:
             stream = torch.cuda.current_stream(self.device)
         self.stream = stream
         h = C.c_void_p()
-        _check(lib().rbmd_init(C.byref(self.params), _ptr(pos), _ptr(vel), _ptr(charge),
-                               _ptr(types), _ptr(eps), _ptr(sigma), C.c_void_p(stream.cuda_stream),
-                               C.byref(h)), "rbmd_init")
+        _check(lib().rbmd_init_batch(prm, R, _ptr(pos), _ptr(vel), _ptr(charge), _ptr(types),
+                                     _ptr(eps), _ptr(sigma), C.c_void_p(stream.cuda_stream),
+                                     C.byref(h)), "rbmd_init_batch")
         self._h = h
         self._keep = (pos, charge, vel, types)
 
@@ -221,12 +249,22 @@ class RBMD:
     def step(self, n_steps=1):
         _check(lib().rbmd_step(self._h, n_steps), "step")
 
-    def energy(self, step) -> dict:
-        e = EnergyTerms()
-        _check(lib().rbmd_energy(self._h, step, C.byref(e)), "energy")
+    @staticmethod
+    def _terms(e) -> dict:
         d = {k: getattr(e, k) for k, _ in EnergyTerms._fields_}
         d["fsum_short"] = list(e.fsum_short)
         return d
+
+    def energy(self, step) -> dict:
+        e = EnergyTerms()
+        _check(lib().rbmd_energy(self._h, step, C.byref(e)), "energy")
+        return self._terms(e)
+
+    def energy_batch(self, step) -> list:
+        """Energies of every replica (list of dicts, replica order)."""
+        e = (EnergyTerms * self.R)()
+        _check(lib().rbmd_energy_batch(self._h, step, e), "energy_batch")
+        return [self._terms(x) for x in e]
 
     def energy_backward(self, step, grad_out=1.0, want_pos=True, want_q=True, want_lj=True):
         t = self._torch
@@ -284,7 +322,8 @@ class RBMD:
         return lib().rbmd_rbe_mode_count(self._h)
 
     def rbe_modes(self, step):
-        P = self.mode_count()
+        """Modes [R*P, 3] and structure factors [R*P] (replica blocks of P)."""
+        P = self.mode_count() * self.R
         m = np.zeros((P, 3), dtype=np.int32)
         rho = np.zeros((P, 2), dtype=np.float64)
         _check(lib().rbmd_rbe_modes(self._h, step, _ptr(m), _ptr(rho)), "rbe_modes")

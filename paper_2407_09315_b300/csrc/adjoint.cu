@@ -36,6 +36,8 @@ __global__ void k_adj_init(real *__restrict__ dpos, real *__restrict__ dq,
 }
 
 template <typename real> struct AdjArgs {
+    const Rep *reps;
+    const int2 *map;        // replica-aligned 128-atom blocks
     const uint4 *spos;
     const real *sq;
     const int32_t *stype;
@@ -43,7 +45,7 @@ template <typename real> struct AdjArgs {
     const int2 *ncount;
     int64_t N;
     int CC, CS, p, T, exact;
-    real ck, alpha, sqrt_alpha, c2, lscale;
+    real ck, alpha, sqrt_alpha, c2;
     const real *eps, *sig;  // per type (host values copied in)
     double g;               // grad_out
     real *dpos, *dq;
@@ -67,8 +69,10 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
     __shared__ double s_t[2 * RBMD_MAX_TYPES][ADJ_BLOCK / 32];
     double acc[2 * RBMD_MAX_TYPES];
     for (int t = 0; t < 2 * a.T; ++t) acc[t] = 0.0;
-    const int64_t ks = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ks < a.N) {
+    const AtomSlot sl = atom_slot(a.map, a.reps);
+    const int64_t ks = sl.i;
+    if (sl.ok) {
+        const real lscale = (real)a.reps[sl.r].lscale;
         const uint4 A = a.spos[ks];
         const real qk = a.sq[ks];
         const int tk = a.stype[ks];
@@ -96,9 +100,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
             const real W = (real)0.5 * (Wkj + Wjk);
             if (W == (real)0 && Wkj == (real)0) continue;
             const uint4 B = a.spos[js];
-            const real dx = (real)(int32_t)(B.x - A.x) * a.lscale;  // r_j - r_k
-            const real dy = (real)(int32_t)(B.y - A.y) * a.lscale;
-            const real dz = (real)(int32_t)(B.z - A.z) * a.lscale;
+            const real dx = (real)(int32_t)(B.x - A.x) * lscale;  // r_j - r_k
+            const real dy = (real)(int32_t)(B.y - A.y) * lscale;
+            const real dz = (real)(int32_t)(B.z - A.z) * lscale;
             const real r2 = dx * dx + dy * dy + dz * dz;
             const real r = sqrt_a(r2);
             const real rinv = (real)1 / r;
@@ -156,12 +160,16 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
 // with the coefficients of the forward pass (A = c Im rho, B = c Re rho).
 template <typename real, int CHUNK>
 __global__ void k_rbe_adjoint(const uint4 *__restrict__ u4, const double *__restrict__ q64,
-                              int64_t N, const ModeCoef<real> *__restrict__ coef, int64_t Pm,
-                              real tk, double g, real *__restrict__ dpos, real *__restrict__ dq)
+                              const int2 *__restrict__ map, const Rep *__restrict__ reps,
+                              const ModeCoef<real> *__restrict__ coef_all, int64_t Pm, double g,
+                              real *__restrict__ dpos, real *__restrict__ dq)
 {
     __shared__ ModeCoef<real> s_c[CHUNK];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < N;
+    const AtomSlot sl = atom_slot(map, reps);
+    const int64_t i = sl.i;
+    const bool active = sl.ok;
+    const ModeCoef<real> *coef = coef_all + (int64_t)sl.r * Pm;
+    const real tk = (real)(2.0 * kPi / reps[sl.r].L);
     const uint4 A = active ? u4[i] : make_uint4(0, 0, 0, 0);
     real fx = 0, fy = 0, fz = 0, phi = 0;
     for (int64_t c0 = 0; c0 < Pm; c0 += CHUNK) {
@@ -208,6 +216,8 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
     RBMD_LAUNCH_CHECK();
     if (!(c->prm.flags & RBMD_NO_RBL)) {
         AdjArgs<real> a;
+        a.reps = c->reps;
+        a.map = c->map128;
         a.spos = c->spos;
         a.sq = (const real *)c->sq;
         a.stype = c->stype;
@@ -225,14 +235,13 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
         a.alpha = (real)c->prm.alpha;
         a.sqrt_alpha = (real)sqrt(c->prm.alpha);
         a.c2 = (real)(2.0 * sqrt(c->prm.alpha / kPi));
-        a.lscale = (real)c->lscale;
         a.eps = (const real *)c->adj_lj;
         a.sig = (const real *)c->adj_lj + c->T;
         a.g = g;
         a.dpos = (real *)dpos;
         a.dq = (real *)dq;
         a.tpart = c->adj_tpart;
-        const unsigned nba = (unsigned)((c->N + ADJ_BLOCK - 1) / ADJ_BLOCK);
+        const unsigned nba = (unsigned)c->nb128;
         k_rbl_adjoint<real><<<nba, ADJ_BLOCK, 0, c->stream>>>(a);
         RBMD_LAUNCH_CHECK();
         RBMD_CHECK(md_sum(c, c->adj_tpart, (int)nba, 2 * c->T, tsum_dev, 1.0));
@@ -241,13 +250,13 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
     }
     if (!(c->prm.flags & RBMD_NO_RBE)) {
         if constexpr (sizeof(real) == 4)
-            k_rbe_adjoint<float, 256><<<nb, 256, 0, c->stream>>>(
-                c->u4, nullptr, c->N, (const ModeCoef<float> *)c->coef, c->Pm,
-                (float)(2.0 * kPi / c->L), g, (float *)dpos, (float *)dq);
+            k_rbe_adjoint<float, 256><<<c->nb256, 256, 0, c->stream>>>(
+                c->u4, nullptr, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm, g,
+                (float *)dpos, (float *)dq);
         else
-            k_rbe_adjoint<double, 128><<<nb, 256, 0, c->stream>>>(
-                c->u4, c->q64, c->N, (const ModeCoef<double> *)c->coef, c->Pm, 2.0 * kPi / c->L,
-                g, (double *)dpos, (double *)dq);
+            k_rbe_adjoint<double, 128><<<c->nb256, 256, 0, c->stream>>>(
+                c->u4, c->q64, c->map256, c->reps, (const ModeCoef<double> *)c->coef, c->Pm, g,
+                (double *)dpos, (double *)dq);
         RBMD_LAUNCH_CHECK();
     }
     (void)eps_h;

@@ -75,12 +75,16 @@ rbmd_status leave(rbmd_ctx *c, rbmd_status s)
 }
 
 __global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
-__global__ void k_init_scal(double *scal)
+__global__ void k_init_scal(double *scal, int R)
 {
-    int t = threadIdx.x;
-    if (t < SCAL_COUNT) scal[t] = (t == SCAL_LAMBDA) ? 1.0 : 0.0;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < R * SCAL_COUNT) scal[t] = (t % SCAL_COUNT == SCAL_LAMBDA) ? 1.0 : 0.0;
 }
-__global__ void k_set_lambda(double *scal, double v) { scal[SCAL_LAMBDA] = v; }
+__global__ void k_set_lambda(double *scal, int R, double v)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) scal[(int64_t)r * SCAL_COUNT + SCAL_LAMBDA] = v;
+}
 
 template <typename real>
 __global__ void k_pack(const real *__restrict__ q, const int32_t *__restrict__ type, int64_t N,
@@ -100,13 +104,16 @@ __global__ void k_pack(const real *__restrict__ q, const int32_t *__restrict__ t
     tout[i] = t;
 }
 
-// Charge sums for the neutrality check and the self energy: [sum q, sum |q|, sum q^2].
+// Charge sums for the neutrality check and the self energy: [sum q, sum |q|, sum q^2]
+// per replica-aligned 256-atom block.
 __global__ void k_charge_parts(const double *__restrict__ q64, const uint4 *__restrict__ u4,
-                               int64_t N, double *__restrict__ parts)
+                               const int2 *__restrict__ map, const Rep *__restrict__ reps,
+                               double *__restrict__ parts)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const AtomSlot sl = atom_slot(map, reps);
+    const int64_t i = sl.i;
     double q = 0.0;
-    if (i < N) q = q64 ? q64[i] : (double)__uint_as_float(u4[i].w);
+    if (sl.ok) q = q64 ? q64[i] : (double)__uint_as_float(u4[i].w);
     double v[3] = {q, fabs(q), q * q};
     for (int c = 0; c < 3; ++c)
         for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
@@ -153,6 +160,28 @@ __global__ void k_u3_to_u4(const uint32_t *__restrict__ u3, int64_t N, uint4 *__
     u4[i] = A;
 }
 
+__global__ void k_zero_slots(double *scal, int R, int slot0, int count)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < R * count) scal[(int64_t)(t / count) * SCAL_COUNT + slot0 + t % count] = 0.0;
+}
+
+// One block per replica: sum of its P mode energies, fixed order.
+__global__ void k_sum_modes(const double *__restrict__ emode, int64_t P, double *__restrict__ scal,
+                            int slot)
+{
+    __shared__ double s[256];
+    double v = 0.0;
+    for (int64_t l = threadIdx.x; l < P; l += blockDim.x) v += emode[(int64_t)blockIdx.x * P + l];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scal[(int64_t)blockIdx.x * SCAL_COUNT + slot] = s[0];
+}
+
 __global__ void k_max_count(const int32_t *__restrict__ count, int64_t n, int32_t *__restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -173,11 +202,13 @@ void free_ctx(rbmd_ctx *c)
                     c->scan_part, c->spos,      c->sq,       c->stype,      c->fpart,
                     c->epart,     c->kepart,    c->ibuf,     c->lj_f,       c->lj_d,
                     c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp,
-                    c->adj_lj,    c->adj_tpart, c->adj_tsum};
+                    c->adj_lj,    c->adj_tpart, c->adj_tsum, c->reps,       c->map256,
+                    c->map128,    c->tiles,     c->red_rep};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
         if (c->prof_ev[k]) cudaEventDestroy(c->prof_ev[k]);
+    delete[] c->reps_h;
     if (c->own_stream) {
         cudaStreamDestroy(c->stream);
         cudaEventDestroy(c->ev_in);
@@ -218,6 +249,50 @@ rbmd_status upload_lj(rbmd_ctx *c, const double *eps, const double *sig)
 
 // Forces of the current configuration, keyed by `s`, into `force` (RBE + RBL);
 // F_corr is written to scal (and added to `force` when apply_corr).
+rbmd_status check_latched(rbmd_ctx *c);
+
+// One block per replica: the 3 charge sums of its 256-atom blocks.
+__global__ void k_sum_charges(const double *__restrict__ parts, const Rep *__restrict__ reps,
+                              double *__restrict__ out)
+{
+    __shared__ double s[3][256];
+    const Rep rp = reps[blockIdx.x];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int j = threadIdx.x; j < rp.nb256; j += blockDim.x)
+        for (int k = 0; k < 3; ++k) v[k] += parts[3 * (int64_t)(rp.b256_0 + j) + k];
+    for (int k = 0; k < 3; ++k) s[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o)
+            for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) out[3 * (int64_t)blockIdx.x + k] = s[k][0];
+}
+
+// Neutrality of every replica (Sec. 2.2, when check_neutral) and its self energy
+// -coulomb_k sqrt(alpha/pi) sum q^2 (third term of Eq. 8).  Synchronises.
+rbmd_status charge_sums(rbmd_ctx *c, bool check_neutral = true)
+{
+    double *parts = (double *)c->scratch_force;  // 3 nb256 doubles fit in 3N doubles + 64 B
+    double *sums = c->kepart;                     // 3 R doubles fit in 3 nb256
+    k_charge_parts<<<c->nb256, 256, 0, c->stream>>>(c->q64, c->u4, c->map256, c->reps, parts);
+    k_sum_charges<<<c->R, 256, 0, c->stream>>>(parts, c->reps, sums);
+    RBMD_LAUNCH_CHECK();
+    std::vector<double> h(3 * (size_t)c->R);
+    RBMD_CHECK_CUDA(cudaMemcpyAsync(h.data(), sums, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    RBMD_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+    RBMD_CHECK(check_latched(c));
+    for (int r = 0; r < c->R && check_neutral; ++r)
+        if (fabs(h[3 * r]) > 1e-6 * (h[3 * r + 1] > 0 ? h[3 * r + 1] : 1.0)) return RBMD_ERR_NOT_NEUTRAL;
+    for (int r = 0; r < c->R; ++r)
+        c->reps_h[r].e_self = -c->prm.coulomb_k * sqrt(c->prm.alpha / kPi) * h[3 * r + 2];
+    RBMD_CHECK_CUDA(cudaMemcpy(c->reps, c->reps_h, sizeof(Rep) * c->R, cudaMemcpyHostToDevice));
+    return RBMD_OK;
+}
+
 rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool apply_corr,
                         bool marks = false)
 {
@@ -234,8 +309,10 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
         acc = 1;
     } else {
         for (int k = 2; k <= 5 && marks; ++k) prof_mark(c, k);
-        if (!apply_corr)
-            RBMD_CHECK_CUDA(cudaMemsetAsync(c->scal + SCAL_FCORR, 0, 3 * sizeof(double), c->stream));
+        if (!apply_corr) {
+            k_zero_slots<<<(c->R * 3 + 255) / 256, 256, 0, c->stream>>>(c->scal, c->R, SCAL_FCORR, 3);
+            RBMD_LAUNCH_CHECK();
+        }
     }
     if (marks) prof_mark(c, 6);
     if (do_rbe) {
@@ -305,23 +382,38 @@ rbmd_status rbmd_sampler_table(double box_length, double alpha, int32_t *M, uint
     return sampler_table_host(box_length, alpha, M, T, H);
 }
 
-rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, const void *charge,
-                      const int32_t *type, const double *lj_eps, const double *lj_sigma,
-                      void *stream, rbmd_ctx **out)
+rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos, const void *vel,
+                            const void *charge, const int32_t *type, const double *lj_eps,
+                            const double *lj_sigma, void *stream, rbmd_ctx **out)
 {
     if (!out) return RBMD_ERR_INVALID;
     *out = nullptr;
-    if (!prm || !pos || !charge || !lj_eps || !lj_sigma) return RBMD_ERR_INVALID;
-    const rbmd_params p = *prm;
-    if (p.n_atoms < 1 || p.n_atoms > (int64_t)2000000000) return RBMD_ERR_INVALID;
+    if (!prms || R < 1 || R > 65536 || !pos || !charge || !lj_eps || !lj_sigma) return RBMD_ERR_INVALID;
+    const rbmd_params p = prms[0];
+    int64_t Ntot = 0;
+    for (int r = 0; r < R; ++r) {
+        const rbmd_params &q = prms[r];
+        if (q.n_atoms < 1 || q.n_atoms > (int64_t)2000000000) return RBMD_ERR_INVALID;
+        if (!(q.box_length > 0.0)) return RBMD_ERR_INVALID;
+        // everything but the size, box, seed, replica tag and T0 is shared
+        if (q.n_types != p.n_types || q.rbe_P != p.rbe_P || q.alpha != p.alpha ||
+            q.r_core != p.r_core || q.r_cut != p.r_cut || q.rbl_p != p.rbl_p ||
+            q.thermostat != p.thermostat || q.coulomb_k != p.coulomb_k || q.dt != p.dt ||
+            q.tau_T != p.tau_T || q.precision != p.precision || q.flags != p.flags ||
+            q.cell_div != p.cell_div)
+            return RBMD_ERR_INVALID;
+        if (!(q.r_cut < 0.5 * q.box_length)) return RBMD_ERR_BOX_TOO_SMALL;
+        Ntot += q.n_atoms;
+    }
+    if (Ntot > (int64_t)2000000000) return RBMD_ERR_INVALID;
     if (p.n_types < 1 || p.n_types > RBMD_MAX_TYPES) return RBMD_ERR_INVALID;
-    if (!(p.box_length > 0.0) || !(p.alpha > 0.0) || !(p.r_cut > 0.0)) return RBMD_ERR_INVALID;
+    if (!(p.alpha > 0.0) || !(p.r_cut > 0.0)) return RBMD_ERR_INVALID;
     if (!(p.r_core >= 0.0) || p.r_core > p.r_cut) return RBMD_ERR_INVALID;
     if (p.rbe_P < 1 || p.rbl_p < 1 || p.rbl_p > 32) return RBMD_ERR_INVALID;
     if (p.precision != RBMD_FP32 && p.precision != RBMD_FP64) return RBMD_ERR_INVALID;
     if (p.thermostat != 0 && p.thermostat != 1) return RBMD_ERR_INVALID;
     if (p.cell_div < 0 || p.cell_div > 2) return RBMD_ERR_INVALID;
-    if (!(p.r_cut < 0.5 * p.box_length)) return RBMD_ERR_BOX_TOO_SMALL;
+    if ((p.flags & RBMD_FULL_EWALD_MODES) && R != 1) return RBMD_ERR_UNSUPPORTED;
     for (int t = 0; t < p.n_types; ++t)
         if (!(lj_eps[t] >= 0.0) || !(lj_sigma[t] >= 0.0)) return RBMD_ERR_INVALID;
 
@@ -333,16 +425,17 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     rbmd_ctx *c = new rbmd_ctx;
     memset(c, 0, sizeof(*c));
     c->prm = p;
-    c->N = p.n_atoms;
+    c->R = R;
+    c->N = Ntot;
     c->T = p.n_types;
     c->fp64 = p.precision == RBMD_FP64;
-    c->L = p.box_length;
-    c->V = c->L * c->L * c->L;
-    c->lscale = c->L / kTwo32;
-    c->dtc = p.dt * (kTwo32 / c->L);
     c->tau = p.tau_T > 0.0 ? p.tau_T : 0.1;
     c->sqrt_alpha = sqrt(p.alpha);
     c->full_modes = (p.flags & RBMD_FULL_EWALD_MODES) != 0;
+    c->div = p.cell_div == 0 ? 2 : p.cell_div;
+    c->rho_tile = 1024;
+    c->reps_h = new Rep[R];
+    memset(c->reps_h, 0, sizeof(Rep) * R);
 
     rbmd_status st = RBMD_OK;
 #define TRY(x)                     \
@@ -365,35 +458,89 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     }
     enter(c);
 
-    // sampler (Eq. 12)
-    TRY(sampler_table_host(c->L, p.alpha, &c->M, nullptr, nullptr));
-    std::vector<uint64_t> T(2 * (size_t)c->M + 1);
-    TRY(sampler_table_host(c->L, p.alpha, &c->M, T.data(), &c->H));
-    c->S = c->H * c->H * c->H - 1.0;
-
-    // RBL constants (Sec. 2.3)
-    c->Rc2 = radius2_units(p.r_core, c->L);
-    c->Rs2 = radius2_units(p.r_cut, c->L);
-    c->Rlin = isqrt64(c->Rs2);
-    c->div = p.cell_div == 0 ? 2 : p.cell_div;
-    {
-        int nc = (int)floor(c->L * c->div / p.r_cut);
+    // per-replica constants: sampler (Eq. 12), RBL radii and cells (Sec. 2.3)
+    std::vector<uint64_t> T;
+    std::vector<int2> m256, m128, tl;
+    double max_mc = 0.0, max_ms = 0.0;
+    int64_t atom0 = 0, cell0 = 0;
+    for (int r = 0; r < R; ++r) {
+        const rbmd_params &q = prms[r];
+        Rep &rp = c->reps_h[r];
+        rp.L = q.box_length;
+        rp.lscale = rp.L / kTwo32;
+        rp.dtc = q.dt * (kTwo32 / rp.L);
+        rp.T0 = q.temperature;
+        rp.key = make_uint2((uint32_t)(q.seed & 0xFFFFFFFFu), (uint32_t)(q.seed >> 32));
+        rp.tag_rbe = RBMD_STREAM_RBE | (q.replica << 8);
+        rp.tag_rbl = RBMD_STREAM_RBL | (q.replica << 8);
+        int32_t M = 0;
+        double H = 0.0;
+        TRY(sampler_table_host(rp.L, p.alpha, &M, nullptr, nullptr));
+        rp.M = M;
+        rp.cdf0 = (int64_t)T.size();
+        T.resize(T.size() + 2 * (size_t)M + 1);
+        TRY(sampler_table_host(rp.L, p.alpha, &M, T.data() + rp.cdf0, &H));
+        rp.S = H * H * H - 1.0;
+        rp.Wrbe = rp.S / (double)p.rbe_P;
+        rp.Rc2 = radius2_units(p.r_core, rp.L);
+        rp.Rs2 = radius2_units(p.r_cut, rp.L);
+        rp.Rlin = isqrt64(rp.Rs2);
+        int nc = (int)floor(rp.L * c->div / p.r_cut);
         if (nc < 1) nc = 1;
-        while (nc > 1 && (double)c->Rlin * (double)nc > (double)c->div * kTwo32) --nc;
+        while (nc > 1 && (double)rp.Rlin * (double)nc > (double)c->div * kTwo32) --nc;
         // bigger cells stay correct (the stencil still covers r_cut); cap the
         // cell count so that sparse boxes do not allocate more cells than atoms
-        const double max_cells = fmax(8.0 * (double)c->N, 1048576.0);
+        const double max_cells = fmax(8.0 * (double)q.n_atoms, 1048576.0);
         while (nc > 1 && (double)nc * nc * nc > max_cells) --nc;
-        c->nc = nc;
-        c->ncell = (int64_t)nc * nc * nc;
+        rp.nc = nc;
+        rp.cull_r = (float)(p.r_cut * nc / rp.L * (1.0 + 1e-5) + 1e-6);
+        rp.atom0 = atom0;
+        rp.N = q.n_atoms;
+        rp.cell0 = cell0;
+        rp.ncell = (int64_t)nc * nc * nc;
+        rp.b256_0 = (int32_t)m256.size();
+        for (int64_t a = 0; a < rp.N; a += 256) m256.push_back(make_int2(r, (int)(atom0 + a)));
+        rp.nb256 = (int32_t)m256.size() - rp.b256_0;
+        rp.b128_0 = (int32_t)m128.size();
+        for (int64_t a = 0; a < rp.N; a += 128) m128.push_back(make_int2(r, (int)(atom0 + a)));
+        rp.nb128 = (int32_t)m128.size() - rp.b128_0;
+        rp.tile0 = (int32_t)tl.size();
+        for (int64_t a = 0; a < rp.N; a += c->rho_tile) tl.push_back(make_int2(r, (int)(atom0 + a)));
+        rp.ntiles = (int32_t)tl.size() - rp.tile0;
+        atom0 += rp.N;
+        cell0 += rp.ncell;
+        const double n = (double)rp.N / (rp.L * rp.L * rp.L);
+        const double mc = n * 4.0 / 3.0 * kPi * p.r_core * p.r_core * p.r_core;
+        max_mc = fmax(max_mc, mc);
+        max_ms = fmax(max_ms, n * 4.0 / 3.0 * kPi * (p.r_cut * p.r_cut * p.r_cut) - mc);
+    }
+    c->ncell = cell0;
+    c->cdf_total = (int64_t)T.size();
+    c->nb256 = (int)m256.size();
+    c->nb128 = (int)m128.size();
+    c->ntiles = (int)tl.size();
+    c->pair_parts = 2 * 4 * c->nb128;  // per warp: pair kernel, then the fallback
+    // list capacities: mean + 8 sd + 8 of a uniform fluid at the densest
+    // replica's density, rounded up to a multiple of 4; atoms beyond them take
+    // the exact fallback
+    c->list_cc = ((int)ceil(max_mc + 8.0 * sqrt(max_mc) + 8.0) + 3) / 4 * 4;
+    c->list_cs = ((int)ceil(max_ms + 8.0 * sqrt(max_ms) + 8.0) + 3) / 4 * 4;
+    // RBMD_LIST_CAPS="cc,cs" shrinks the capacities so that tests can drive
+    // atoms through the overflow path
+    if (const char *env = getenv("RBMD_LIST_CAPS")) {
+        int cc = 0, cs = 0;
+        if (sscanf(env, "%d,%d", &cc, &cs) == 2 && cc >= 1 && cs >= 1) {
+            c->list_cc = cc;
+            c->list_cs = cs;
+        }
     }
 
-    // mode list
+    // mode list (the full Ewald series of one replica, Eq. 11)
     std::vector<int4> full;
     std::vector<double> fullW;
     if (c->full_modes) {
-        const double a = kPi * kPi / (p.alpha * c->L * c->L);
-        const int M = c->M;
+        const double a = kPi * kPi / (p.alpha * c->reps_h[0].L * c->reps_h[0].L);
+        const int M = c->reps_h[0].M;
         for (int mx = -M; mx <= M; ++mx)
             for (int my = -M; my <= M; ++my)
                 for (int mz = -M; mz <= M; ++mz) {
@@ -406,52 +553,30 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
         c->Pm = p.rbe_P;
     }
 
-    // tiles
-    c->rho_tile = 1024;
-    c->rho_tiles = (int)((c->N + c->rho_tile - 1) / c->rho_tile);
-    c->force_block = 256;
-    c->pair_block = kPairBlock;
-    c->pair_blocks = (int)((c->N + c->pair_block - 1) / c->pair_block);
-    c->pair_parts = (c->pair_blocks + 64) * (kPairBlock / 32);  // + fallback kernel blocks
-    {
-        // list capacities: mean + 8 sd + 8 of a uniform fluid at this density,
-        // rounded up to a multiple of 4; atoms beyond them take the exact fallback
-        const double n = (double)c->N / c->V;
-        const double mc = n * 4.0 / 3.0 * kPi * p.r_core * p.r_core * p.r_core;
-        const double ms = n * 4.0 / 3.0 * kPi * (p.r_cut * p.r_cut * p.r_cut) - mc;
-        c->list_cc = ((int)ceil(mc + 8.0 * sqrt(mc) + 8.0) + 3) / 4 * 4;
-        c->list_cs = ((int)ceil(ms + 8.0 * sqrt(ms) + 8.0) + 3) / 4 * 4;
-        // RBMD_LIST_CAPS="cc,cs" shrinks the capacities so that tests can drive
-        // atoms through the overflow path
-        if (const char *env = getenv("RBMD_LIST_CAPS")) {
-            int cc = 0, cs = 0;
-            if (sscanf(env, "%d,%d", &cc, &cs) == 2 && cc >= 1 && cs >= 1) {
-                c->list_cc = cc;
-                c->list_cs = cs;
-            }
-        }
-    }
-    c->kick_blocks = (int)((c->N + 255) / 256);
-
     const size_t rs = real_size(c);
     const int64_t N = c->N;
+    TRY(alloc_n(&c->reps, (size_t)R));
+    TRY(alloc_n(&c->map256, (size_t)c->nb256));
+    TRY(alloc_n(&c->map128, (size_t)c->nb128));
+    TRY(alloc_n(&c->tiles, (size_t)c->ntiles));
     TRY(alloc_n(&c->u4, N));
     if (c->fp64) TRY(alloc_n(&c->q64, N));
     TRY(alloc_n(&c->type, N));
     TRY(dev_alloc(&c->vel, 3 * N * rs));
     TRY(dev_alloc(&c->force, 3 * N * rs));
-    TRY(dev_alloc(&c->scratch_force, 3 * N * (rs > 4 ? rs : 8)));
-    TRY(alloc_n(&c->scal, SCAL_COUNT));
+    TRY(dev_alloc(&c->scratch_force, 3 * N * (rs > 4 ? rs : 8) + 64));
+    TRY(alloc_n(&c->scal, (size_t)R * SCAL_COUNT));
     TRY(alloc_n(&c->red_tmp, (size_t)RED_BLOCKS * 8));
+    TRY(alloc_n(&c->red_rep, (size_t)R * RED_SPLIT * 8));
     TRY(alloc_n(&c->err, 1));
     TRY(alloc_n(&c->d_step, 1));
     TRY(alloc_n(&c->cdf, T.size()));
-    TRY(alloc_n(&c->modes, c->Pm));
+    TRY(alloc_n(&c->modes, (size_t)R * c->Pm));
     if (c->full_modes) TRY(alloc_n(&c->W, c->Pm));
-    TRY(alloc_n(&c->rho_part, (size_t)c->rho_tiles * c->Pm));
-    TRY(alloc_n(&c->rho, c->Pm));
-    TRY(alloc_n(&c->emode, c->Pm));
-    TRY(dev_alloc(&c->coef, (size_t)c->Pm * (c->fp64 ? sizeof(ModeCoef<double>) : sizeof(ModeCoef<float>))));
+    TRY(alloc_n(&c->rho_part, (size_t)c->ntiles * c->Pm));
+    TRY(alloc_n(&c->rho, (size_t)R * c->Pm));
+    TRY(alloc_n(&c->emode, (size_t)R * c->Pm));
+    TRY(dev_alloc(&c->coef, (size_t)R * c->Pm * (c->fp64 ? sizeof(ModeCoef<double>) : sizeof(ModeCoef<float>))));
     TRY(alloc_n(&c->cell_count, c->ncell));
     TRY(alloc_n(&c->cell_start, c->ncell + 1));
     TRY(alloc_n(&c->cell_of, N));
@@ -466,10 +591,10 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     TRY(alloc_n(&c->ncount, (size_t)N));
     TRY(alloc_n(&c->bk, (size_t)N * p.rbl_p));
     TRY(dev_alloc(&c->adj_lj, 2 * (size_t)c->T * rs));
-    TRY(alloc_n(&c->adj_tpart, (size_t)((N + 127) / 128) * 2 * c->T));
+    TRY(alloc_n(&c->adj_tpart, (size_t)c->nb128 * 2 * c->T));
     TRY(alloc_n(&c->adj_tsum, 2 * (size_t)c->T));
     TRY(alloc_n(&c->epart, 2 * (size_t)c->pair_parts));
-    TRY(alloc_n(&c->kepart, (size_t)c->kick_blocks));
+    TRY(alloc_n(&c->kepart, (size_t)c->nb256 * 3));
     TRY(alloc_n(&c->ibuf, 4));
     g_alloc_countdown = -1;
 
@@ -477,6 +602,10 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     if (c->fp64) TRY(alloc_n(&c->lj_d, 2 * c->T));
     else TRY(alloc_n(&c->lj_f, 2 * c->T));
     TRY(upload_lj(c, lj_eps, lj_sigma));
+    TRY(cuda_status(cudaMemcpy(c->reps, c->reps_h, sizeof(Rep) * R, cudaMemcpyHostToDevice)));
+    TRY(cuda_status(cudaMemcpy(c->map256, m256.data(), sizeof(int2) * m256.size(), cudaMemcpyHostToDevice)));
+    TRY(cuda_status(cudaMemcpy(c->map128, m128.data(), sizeof(int2) * m128.size(), cudaMemcpyHostToDevice)));
+    TRY(cuda_status(cudaMemcpy(c->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice)));
     TRY(cuda_status(cudaMemcpy(c->cdf, T.data(), sizeof(uint64_t) * T.size(), cudaMemcpyHostToDevice)));
     if (c->full_modes) {
         TRY(cuda_status(cudaMemcpy(c->modes, full.data(), sizeof(int4) * full.size(), cudaMemcpyHostToDevice)));
@@ -484,7 +613,7 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     }
     TRY(cuda_status(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)));
     TRY(cuda_status(cudaMemsetAsync(c->u4, 0, sizeof(uint4) * N, c->stream)));
-    k_init_scal<<<1, 32, 0, c->stream>>>(c->scal);
+    k_init_scal<<<(R * SCAL_COUNT + 255) / 256, 256, 0, c->stream>>>(c->scal, R);
     k_set_i64<<<1, 1, 0, c->stream>>>(c->d_step, 0);
 
     // particle data (Sec. 2.1: map the arrays to the device)
@@ -499,28 +628,21 @@ rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, 
     if (vel) TRY(cuda_status(cudaMemcpyAsync(c->vel, vel, 3 * N * rs, cudaMemcpyDefault, c->stream)));
     else TRY(cuda_status(cudaMemsetAsync(c->vel, 0, 3 * N * rs, c->stream)));
 
-    // neutrality (Sec. 2.2) and the self energy (third term of Eq. 8)
-    {
-        double *parts = (double *)c->scratch_force;  // 3 nb doubles fit in 3N doubles
-        k_charge_parts<<<nb, 256, 0, c->stream>>>(c->q64, c->u4, N, parts);
-        double *sums = c->scal + SCAL_ERBE;             // three free slots until the first energy
-        TRY(md_sum(c, parts, (int)nb, 3, sums, 1.0));
-        double h[3];
-        TRY(cuda_status(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream)));
-        TRY(cuda_status(cudaStreamSynchronize(c->stream)));
-        TRY(check_latched(c));
-        if (fabs(h[0]) > 1e-6 * (h[1] > 0 ? h[1] : 1.0)) {
-            free_ctx(c);
-            return RBMD_ERR_NOT_NEUTRAL;
-        }
-        c->e_self = -p.coulomb_k * sqrt(p.alpha / kPi) * h[2];
-    }
+    // neutrality of every replica (Sec. 2.2) and the self energies (third term of Eq. 8)
+    TRY(charge_sums(c));
 #undef TRY
     c->step = 0;
     c->have_force = false;
     leave(c, RBMD_OK);
     *out = c;
     return RBMD_OK;
+}
+
+rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, const void *charge,
+                      const int32_t *type, const double *lj_eps, const double *lj_sigma,
+                      void *stream, rbmd_ctx **out)
+{
+    return rbmd_init_batch(prm, 1, pos, vel, charge, type, lj_eps, lj_sigma, stream, out);
 }
 
 void rbmd_destroy(rbmd_ctx *c) { free_ctx(c); }
@@ -648,54 +770,72 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
     return leave(c, RBMD_OK);
 }
 
-rbmd_status rbmd_energy(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
+rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
 {
     if (!c || !out) return RBMD_ERR_INVALID;
     enter(c);
-    memset(out, 0, sizeof(*out));
+    const int R = c->R;
+    memset(out, 0, sizeof(*out) * (size_t)R);
     StepRef r{nullptr, step};
     rbmd_status s = RBMD_OK;
     cudaMemsetAsync(c->ibuf, 0, 4 * sizeof(int32_t), c->stream);
-    cudaMemsetAsync(c->scal + SCAL_FSUM, 0, 6 * sizeof(double), c->stream);
+    k_zero_slots<<<(R * 6 + 255) / 256, 256, 0, c->stream>>>(c->scal, R, SCAL_FSUM, 6);
     if (!(c->prm.flags & RBMD_NO_RBE)) {
         s = rbe_sample(c, r);
         if (s == RBMD_OK) s = rbe_structure_factors(c);
-        if (s == RBMD_OK) s = md_sum(c, c->emode, (int)c->Pm, 1, c->scal + SCAL_ERBE, 1.0);
+        if (s == RBMD_OK) {
+            k_sum_modes<<<R, 256, 0, c->stream>>>(c->emode, c->Pm, c->scal, SCAL_ERBE);
+            s = cuda_status(cudaPeekAtLastError());
+        }
     }
     if (s == RBMD_OK && !(c->prm.flags & RBMD_NO_RBL)) {
         s = cells_build(c);
         if (s == RBMD_OK)
             s = rbl_pairs(c, r, c->scratch_force, 0, true, nullptr, nullptr, nullptr);
-        if (s == RBMD_OK) s = md_sum(c, c->fpart, c->pair_parts, 3, c->scal + SCAL_FSUM, 1.0);
-        if (s == RBMD_OK) s = md_sum(c, c->epart, c->pair_parts, 2, c->scal + SCAL_ECOUL, 1.0);
+        if (s == RBMD_OK) s = md_sum_replicas(c, c->fpart, 3, SCAL_FSUM, 1.0, false, true);
+        if (s == RBMD_OK) s = md_sum_replicas(c, c->epart, 2, SCAL_ECOUL, 1.0, false, true);
         if (s == RBMD_OK) {
             k_max_count<<<(unsigned)((c->ncell + 255) / 256), 256, 0, c->stream>>>(
                 c->cell_count, c->ncell, c->ibuf + 1);
         }
     }
-    if (s == RBMD_OK) s = md_kinetic(c, c->scal + SCAL_KE_TRUE);
-    double h[SCAL_COUNT];
+    if (s == RBMD_OK) s = md_kinetic(c, SCAL_KE_TRUE);
+    std::vector<double> h((size_t)R * SCAL_COUNT);
     int32_t hi[4];
-    if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(h, c->scal, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    if (s == RBMD_OK)
+        s = cuda_status(cudaMemcpyAsync(h.data(), c->scal, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
     if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(hi, c->ibuf, sizeof(hi), cudaMemcpyDeviceToHost, c->stream));
     if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
     s = leave(c, s);
     if (s != RBMD_OK) return s;
     RBMD_CHECK(check_latched(c));
-    out->e_coul_real = h[SCAL_ECOUL];
-    out->e_lj = h[SCAL_ELJ];
-    out->e_rbe = h[SCAL_ERBE];
-    out->e_self = c->e_self;
-    out->e_potential = out->e_coul_real + out->e_lj + out->e_rbe + out->e_self;
-    out->e_kinetic = h[SCAL_KE_TRUE];
-    out->temperature = c->N > 1 ? 2.0 * out->e_kinetic / (3.0 * (double)c->N - 3.0) : 0.0;
-    out->S = c->S;
-    for (int d = 0; d < 3; ++d) out->fsum_short[d] = h[SCAL_FSUM + d];
-    out->step = step;
-    out->max_shell = hi[0];
-    out->max_cell = hi[1];
+    for (int q = 0; q < R; ++q) {
+        const double *hr = h.data() + (size_t)q * SCAL_COUNT;
+        const Rep &rp = c->reps_h[q];
+        rbmd_energy_terms &o = out[q];
+        o.e_coul_real = hr[SCAL_ECOUL];
+        o.e_lj = hr[SCAL_ELJ];
+        o.e_rbe = hr[SCAL_ERBE];
+        o.e_self = rp.e_self;
+        o.e_potential = o.e_coul_real + o.e_lj + o.e_rbe + o.e_self;
+        o.e_kinetic = hr[SCAL_KE_TRUE];
+        o.temperature = rp.N > 1 ? 2.0 * o.e_kinetic / (3.0 * (double)rp.N - 3.0) : 0.0;
+        o.S = rp.S;
+        for (int d = 0; d < 3; ++d) o.fsum_short[d] = hr[SCAL_FSUM + d];
+        o.step = step;
+        o.max_shell = hi[0];
+        o.max_cell = hi[1];
+    }
     return RBMD_OK;
 }
+
+rbmd_status rbmd_energy(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
+{
+    if (!c || !out || c->R != 1) return RBMD_ERR_INVALID;
+    return rbmd_energy_batch(c, step, out);
+}
+
+int32_t rbmd_replica_count(rbmd_ctx *c) { return c ? c->R : 0; }
 
 rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, void *d_pos, void *d_q,
                                  double *d_eps, double *d_sigma)
@@ -768,13 +908,7 @@ rbmd_status rbmd_set_charges(rbmd_ctx *c, const void *charge)
     else
         k_pack<float><<<nb, 256, 0, c->stream>>>((const float *)charge, c->type, c->N, c->u4, nullptr,
                                                  c->type, c->T, c->err);
-    double *parts = (double *)c->scratch_force;
-    k_charge_parts<<<nb, 256, 0, c->stream>>>(c->q64, c->u4, c->N, parts);
-    double h[3];
-    rbmd_status s = md_sum(c, parts, (int)nb, 3, c->scal + SCAL_ERBE, 1.0);
-    if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(h, c->scal + SCAL_ERBE, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-    if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
-    if (s == RBMD_OK) c->e_self = -c->prm.coulomb_k * sqrt(c->prm.alpha / kPi) * h[2];
+    rbmd_status s = charge_sums(c, false);
     c->have_force = false;
     return leave(c, s);
 }
@@ -823,7 +957,7 @@ rbmd_status rbmd_set_state(rbmd_ctx *c, const void *pos, const void *vel, int64_
     }
     if (s == RBMD_OK && vel) {
         s = cuda_status(cudaMemcpyAsync(c->vel, vel, bytes, cudaMemcpyDefault, c->stream));
-        k_set_lambda<<<1, 1, 0, c->stream>>>(c->scal, 1.0);
+        k_set_lambda<<<(c->R + 255) / 256, 256, 0, c->stream>>>(c->scal, c->R, 1.0);
     }
     c->step = step;
     c->have_force = false;
@@ -864,7 +998,7 @@ rbmd_status rbmd_set_state_u(rbmd_ctx *c, const uint32_t *u, const void *vel, in
     }
     if (s == RBMD_OK && vel) {
         s = cuda_status(cudaMemcpyAsync(c->vel, vel, 3 * c->N * real_size(c), cudaMemcpyDefault, c->stream));
-        k_set_lambda<<<1, 1, 0, c->stream>>>(c->scal, 1.0);
+        k_set_lambda<<<(c->R + 255) / 256, 256, 0, c->stream>>>(c->scal, c->R, 1.0);
     }
     c->step = step;
     c->have_force = false;
@@ -888,11 +1022,12 @@ rbmd_status rbmd_rbe_modes(rbmd_ctx *c, int64_t step, int32_t *m, double *rho)
     rbmd_status s = rbe_sample(c, r);
     if (s == RBMD_OK) s = rbe_structure_factors(c);
     if (s == RBMD_OK && m) {
-        k_modes_to_m3<<<(unsigned)((c->Pm + 255) / 256), 256, 0, c->stream>>>(c->modes, c->Pm, (int32_t *)c->rho_part);
-        s = cuda_status(cudaMemcpyAsync(m, c->rho_part, 3 * c->Pm * sizeof(int32_t), cudaMemcpyDefault, c->stream));
+        const int64_t nm = (int64_t)c->R * c->Pm;
+        k_modes_to_m3<<<(unsigned)((nm + 255) / 256), 256, 0, c->stream>>>(c->modes, nm, (int32_t *)c->rho_part);
+        s = cuda_status(cudaMemcpyAsync(m, c->rho_part, 3 * nm * sizeof(int32_t), cudaMemcpyDefault, c->stream));
     }
     if (s == RBMD_OK && rho)
-        s = cuda_status(cudaMemcpyAsync(rho, c->rho, 2 * c->Pm * sizeof(double), cudaMemcpyDefault, c->stream));
+        s = cuda_status(cudaMemcpyAsync(rho, c->rho, 2 * (int64_t)c->R * c->Pm * sizeof(double), cudaMemcpyDefault, c->stream));
     if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
     return leave(c, s);
 }

@@ -5,9 +5,9 @@
 // 32-bit fixed-point fractions of the box: the drift adds rint(v dt 2^32 / L)
 // (computed in FP64) and wraps modulo 2^32, which is the periodic wrap.  The
 // Berendsen factor lambda = sqrt(1 + (dt/tau)(T0/T - 1)), clamped to [0.8, 1.25]
-// with T = 2 KE / (3N - 3), is computed after the second half kick and applied
-// lazily: the stored velocities are multiplied by it in the next kick (and in
-// every read-out), which saves a separate rescaling pass over the velocities.
+// with T = 2 KE / (3N - 3), is computed per replica after the second half kick
+// and applied lazily: the stored velocities are multiplied by it in the next
+// kick (and in every read-out), which saves a separate rescaling pass.
 #include <math.h>
 
 #include "rbmd_internal.cuh"
@@ -75,22 +75,91 @@ rbmd_status md_sum(rbmd_ctx *c, const double *parts, int nparts, int ncomp, doub
     return RBMD_OK;
 }
 
+// Per-replica sums of the 4 nb128 per-warp partials of its 128-atom blocks (and
+// the same range of the second segment) in two fixed-order stages: block
+// (k, r) sums chunk k of RED_SPLIT equal chunks of replica r's range, then one
+// block per replica adds its RED_SPLIT chunk sums.  The chunking depends only on
+// the replica's own size, so a replica sums identically alone or in a batch.
+template <int NC>
+__global__ void k_sum_replicas1(const double *__restrict__ parts, int64_t seg2,
+                                const Rep *__restrict__ reps, double *__restrict__ tmp)
+{
+    __shared__ double s[NC][256];
+    const Rep rp = reps[blockIdx.y];
+    const int64_t j0 = 4 * (int64_t)rp.b128_0, nj = 4 * (int64_t)rp.nb128;
+    const int64_t chunk = (nj + RED_SPLIT - 1) / RED_SPLIT;
+    const int64_t b = blockIdx.x * chunk, e = min(nj, b + chunk);
+    double v[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = 0.0;
+    for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            v[c] += parts[(j0 + j) * NC + c];
+            if (seg2 >= 0) v[c] += parts[(seg2 + j0 + j) * NC + c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) s[c][threadIdx.x] = v[c];
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < NC)
+        tmp[((int64_t)blockIdx.y * RED_SPLIT + blockIdx.x) * 8 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void k_sum_replicas2(const double *__restrict__ tmp, int ncomp,
+                                const Rep *__restrict__ reps, double *__restrict__ scal, int slot,
+                                double scale, int per_atom)
+{
+    const int c = threadIdx.x;
+    if (c >= ncomp) return;
+    const double sc = per_atom ? scale / (double)reps[blockIdx.x].N : scale;
+    double v = 0.0;
+    for (int k = 0; k < RED_SPLIT; ++k) v += tmp[((int64_t)blockIdx.x * RED_SPLIT + k) * 8 + c];
+    scal[(int64_t)blockIdx.x * SCAL_COUNT + slot + c] = sc * v;
+}
+
+rbmd_status md_sum_replicas(rbmd_ctx *c, const double *parts, int ncomp, int slot, double scale,
+                            bool per_atom, bool two_segments)
+{
+    const int64_t seg2 = two_segments ? 4 * (int64_t)c->nb128 : -1;
+    const dim3 grid(RED_SPLIT, c->R);
+    if (ncomp == 3) k_sum_replicas1<3><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
+    else if (ncomp == 2) k_sum_replicas1<2><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
+    else return RBMD_ERR_INVALID;
+    RBMD_LAUNCH_CHECK();
+    k_sum_replicas2<<<c->R, 32, 0, c->stream>>>(c->red_rep, ncomp, c->reps, c->scal, slot, scale,
+                                                per_atom ? 1 : 0);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
 // First half kick (with the pending Berendsen factor) and drift.
 template <typename real>
 __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
-                             const real *__restrict__ F, int64_t N,
-                             const double *__restrict__ scal, real hdt, double dtc)
+                             const real *__restrict__ F, const int2 *__restrict__ map,
+                             const Rep *__restrict__ reps, const double *__restrict__ scal,
+                             real hdt)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const real lam = (real)scal[SCAL_LAMBDA];
+    const AtomSlot a = atom_slot(map, reps);
+    if (!a.ok) return;
+    const int64_t i = a.i;
+    const double *sc = scal + (int64_t)a.r * SCAL_COUNT;
+    const real lam = (real)sc[SCAL_LAMBDA];
+    const double dtc = reps[a.r].dtc;
     uint4 A = u4[i];
     uint32_t *pu = &A.x;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         // lambda * v rounds on its own (no contraction), exactly as a checkpoint
         // read-out does, so a resumed run is bit-identical to an unbroken one
-        real vd = mul_rn(lam, v[3 * i + d]) + hdt * (F[3 * i + d] + (real)scal[SCAL_FCORR + d]);
+        real vd = mul_rn(lam, v[3 * i + d]) + hdt * (F[3 * i + d] + (real)sc[SCAL_FCORR + d]);
         v[3 * i + d] = vd;
         const long long du = llrint((double)vd * dtc);
         pu[d] = pu[d] + (uint32_t)du;
@@ -101,17 +170,20 @@ __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
 // Second half kick and FP64 kinetic-energy block partials; non-finite
 // velocities latch RBMD_ERR_NONFINITE.
 template <typename real>
-__global__ void k_kick_ke(real *__restrict__ v, const real *__restrict__ F, int64_t N,
-                          const double *__restrict__ scal, real hdt,
-                          double *__restrict__ kepart, int *__restrict__ err)
+__global__ void k_kick_ke(real *__restrict__ v, const real *__restrict__ F,
+                          const int2 *__restrict__ map, const Rep *__restrict__ reps,
+                          const double *__restrict__ scal, real hdt, double *__restrict__ kepart,
+                          int *__restrict__ err)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const AtomSlot a = atom_slot(map, reps);
     double ke = 0.0;
-    if (i < N) {
+    if (a.ok) {
+        const int64_t i = a.i;
+        const double *sc = scal + (int64_t)a.r * SCAL_COUNT;
         bool bad = false;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            real vd = v[3 * i + d] + hdt * (F[3 * i + d] + (real)scal[SCAL_FCORR + d]);
+            real vd = v[3 * i + d] + hdt * (F[3 * i + d] + (real)sc[SCAL_FCORR + d]);
             v[3 * i + d] = vd;
             bad |= !isfinite(vd);
             ke += (double)vd * (double)vd;
@@ -129,14 +201,16 @@ __global__ void k_kick_ke(real *__restrict__ v, const real *__restrict__ F, int6
     }
 }
 
-// KE, temperature and the Berendsen factor; optionally advances the device step.
-__global__ void k_thermo(const double *__restrict__ kepart, int nparts, int64_t N,
+// One block per replica: KE, temperature and the Berendsen factor; block 0
+// optionally advances the device step counter.
+__global__ void k_thermo(const double *__restrict__ kepart, const Rep *__restrict__ reps,
                          double *__restrict__ scal, int thermostat, double dt, double tau,
-                         double T0, int64_t *__restrict__ d_step, int advance)
+                         int64_t *__restrict__ d_step, int advance)
 {
-    __shared__ double s[256];
+    __shared__ double s[1024];
+    const Rep rp = reps[blockIdx.x];
     double v = 0.0;
-    for (int j = threadIdx.x; j < nparts; j += blockDim.x) v += kepart[j];
+    for (int j = threadIdx.x; j < rp.nb256; j += blockDim.x) v += kepart[rp.b256_0 + j];
     s[threadIdx.x] = v;
     __syncthreads();
     for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
@@ -146,65 +220,64 @@ __global__ void k_thermo(const double *__restrict__ kepart, int nparts, int64_t 
     if (threadIdx.x != 0) return;
     const double ke = 0.5 * s[0];
     double lam = 1.0;
-    if (thermostat == 1 && N > 1) {
-        const double T = 2.0 * ke / (3.0 * (double)N - 3.0);
-        lam = sqrt(1.0 + (dt / tau) * (T0 / T - 1.0));
+    if (thermostat == 1 && rp.N > 1) {
+        const double T = 2.0 * ke / (3.0 * (double)rp.N - 3.0);
+        lam = sqrt(1.0 + (dt / tau) * (rp.T0 / T - 1.0));
         lam = fmin(fmax(lam, 0.8), 1.25);
     }
-    scal[SCAL_KE] = ke;
-    scal[SCAL_LAMBDA] = lam;
-    if (advance) *d_step += 1;
+    double *sc = scal + (int64_t)blockIdx.x * SCAL_COUNT;
+    sc[SCAL_KE] = ke;
+    sc[SCAL_LAMBDA] = lam;
+    if (advance && blockIdx.x == 0) *d_step += 1;
 }
 
 rbmd_status md_kick_drift(rbmd_ctx *c)
 {
-    const int th = 256;
-    const unsigned nb = (unsigned)((c->N + th - 1) / th);
     const double hdt = 0.5 * c->prm.dt;
     if (c->fp64)
-        k_kick_drift<double><<<nb, th, 0, c->stream>>>(c->u4, (double *)c->vel,
-                                                       (const double *)c->force, c->N, c->scal,
-                                                       hdt, c->dtc);
+        k_kick_drift<double><<<c->nb256, 256, 0, c->stream>>>(
+            c->u4, (double *)c->vel, (const double *)c->force, c->map256, c->reps, c->scal, hdt);
     else
-        k_kick_drift<float><<<nb, th, 0, c->stream>>>(c->u4, (float *)c->vel,
-                                                      (const float *)c->force, c->N, c->scal,
-                                                      (float)hdt, c->dtc);
+        k_kick_drift<float><<<c->nb256, 256, 0, c->stream>>>(
+            c->u4, (float *)c->vel, (const float *)c->force, c->map256, c->reps, c->scal,
+            (float)hdt);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
 
 rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step)
 {
-    const int th = 256;
-    const unsigned nb = (unsigned)((c->N + th - 1) / th);
     const double hdt = 0.5 * c->prm.dt;
     if (c->fp64)
-        k_kick_ke<double><<<nb, th, 0, c->stream>>>((double *)c->vel, (const double *)c->force,
-                                                    c->N, c->scal, hdt, c->kepart, c->err);
+        k_kick_ke<double><<<c->nb256, 256, 0, c->stream>>>((double *)c->vel, (const double *)c->force,
+                                                           c->map256, c->reps, c->scal, hdt,
+                                                           c->kepart, c->err);
     else
-        k_kick_ke<float><<<nb, th, 0, c->stream>>>((float *)c->vel, (const float *)c->force, c->N,
-                                                   c->scal, (float)hdt, c->kepart, c->err);
+        k_kick_ke<float><<<c->nb256, 256, 0, c->stream>>>((float *)c->vel, (const float *)c->force,
+                                                          c->map256, c->reps, c->scal, (float)hdt,
+                                                          c->kepart, c->err);
     RBMD_LAUNCH_CHECK();
-    k_thermo<<<1, 256, 0, c->stream>>>(c->kepart, (int)nb, c->N, c->scal, c->prm.thermostat,
-                                       c->prm.dt, c->tau, c->prm.temperature, c->d_step,
-                                       advance_step ? 1 : 0);
+    k_thermo<<<c->R, 1024, 0, c->stream>>>(c->kepart, c->reps, c->scal, c->prm.thermostat,
+                                          c->prm.dt, c->tau, c->d_step, advance_step ? 1 : 0);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
 
-// Kinetic energy of the true velocities (lambda * stored) into out_dev[0].
+// Kinetic energy of the true velocities (lambda * stored), per 256-atom block.
 template <typename real>
-__global__ void k_ke_true(const real *__restrict__ v, int64_t N, const double *__restrict__ scal,
+__global__ void k_ke_true(const real *__restrict__ v, const int2 *__restrict__ map,
+                          const Rep *__restrict__ reps, const double *__restrict__ scal,
                           double *__restrict__ kepart)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const AtomSlot a = atom_slot(map, reps);
     double ke = 0.0;
-    const double lam = scal[SCAL_LAMBDA];
-    if (i < N)
+    if (a.ok) {
+        const double lam = scal[(int64_t)a.r * SCAL_COUNT + SCAL_LAMBDA];
         for (int d = 0; d < 3; ++d) {
-            double x = lam * (double)v[3 * i + d];
+            const double x = lam * (double)v[3 * a.i + d];
             ke += x * x;
         }
+    }
     for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
     __shared__ double s[32];
     if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = ke;
@@ -216,73 +289,99 @@ __global__ void k_ke_true(const real *__restrict__ v, int64_t N, const double *_
     }
 }
 
-rbmd_status md_kinetic(rbmd_ctx *c, double *out_dev)
+// One block per replica: 1/2 * sum of its 256-atom block partials into slot.
+__global__ void k_sum_ke(const double *__restrict__ kepart, const Rep *__restrict__ reps,
+                         double *__restrict__ scal, int slot)
 {
-    const int th = 256;
-    const unsigned nb = (unsigned)((c->N + th - 1) / th);
-    if (c->fp64) k_ke_true<double><<<nb, th, 0, c->stream>>>((const double *)c->vel, c->N, c->scal, c->kepart);
-    else k_ke_true<float><<<nb, th, 0, c->stream>>>((const float *)c->vel, c->N, c->scal, c->kepart);
+    __shared__ double s[1024];
+    const Rep rp = reps[blockIdx.x];
+    double v = 0.0;
+    for (int j = threadIdx.x; j < rp.nb256; j += blockDim.x) v += kepart[rp.b256_0 + j];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scal[(int64_t)blockIdx.x * SCAL_COUNT + slot] = 0.5 * s[0];
+}
+
+rbmd_status md_kinetic(rbmd_ctx *c, int slot)
+{
+    if (c->fp64)
+        k_ke_true<double><<<c->nb256, 256, 0, c->stream>>>((const double *)c->vel, c->map256,
+                                                           c->reps, c->scal, c->kepart);
+    else
+        k_ke_true<float><<<c->nb256, 256, 0, c->stream>>>((const float *)c->vel, c->map256,
+                                                          c->reps, c->scal, c->kepart);
     RBMD_LAUNCH_CHECK();
-    return md_sum(c, c->kepart, (int)nb, 1, out_dev, 0.5);
+    k_sum_ke<<<c->R, 1024, 0, c->stream>>>(c->kepart, c->reps, c->scal, slot);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
 }
 
 // ---------------------------------------------------------------- state I/O
 // Positions -> fixed point: u = floor(frac(x / L) 2^32), computed in FP64.
 template <typename real>
-__global__ void k_encode(const real *__restrict__ pos, int64_t N, double L, uint4 *__restrict__ u4)
+__global__ void k_encode(const real *__restrict__ pos, const int2 *__restrict__ map,
+                         const Rep *__restrict__ reps, uint4 *__restrict__ u4)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    uint4 A = u4[i];
+    const AtomSlot a = atom_slot(map, reps);
+    if (!a.ok) return;
+    const double L = reps[a.r].L;
+    uint4 A = u4[a.i];
     uint32_t *pu = &A.x;
     for (int d = 0; d < 3; ++d) {
-        double f = (double)pos[3 * i + d] / L;
+        double f = (double)pos[3 * a.i + d] / L;
         f -= floor(f);
         double s = floor(f * kTwo32);
         if (s >= kTwo32) s = kTwo32 - 1.0;
         if (!(s >= 0.0)) s = 0.0;
         pu[d] = (uint32_t)s;
     }
-    u4[i] = A;
+    u4[a.i] = A;
 }
 
 template <typename real>
-__global__ void k_decode(const uint4 *__restrict__ u4, const real *__restrict__ v, int64_t N,
-                         double lscale, const double *__restrict__ scal, real *__restrict__ pos,
+__global__ void k_decode(const uint4 *__restrict__ u4, const real *__restrict__ v,
+                         const int2 *__restrict__ map, const Rep *__restrict__ reps,
+                         const double *__restrict__ scal, real *__restrict__ pos,
                          real *__restrict__ vel)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    const AtomSlot a = atom_slot(map, reps);
+    if (!a.ok) return;
+    const int64_t i = a.i;
     const uint4 A = u4[i];
     if (pos) {
-        pos[3 * i + 0] = (real)((double)A.x * lscale);
-        pos[3 * i + 1] = (real)((double)A.y * lscale);
-        pos[3 * i + 2] = (real)((double)A.z * lscale);
+        const double ls = reps[a.r].lscale;
+        pos[3 * i + 0] = (real)((double)A.x * ls);
+        pos[3 * i + 1] = (real)((double)A.y * ls);
+        pos[3 * i + 2] = (real)((double)A.z * ls);
     }
     if (vel) {
-        const real lam = (real)scal[SCAL_LAMBDA];
+        const real lam = (real)scal[(int64_t)a.r * SCAL_COUNT + SCAL_LAMBDA];
         for (int d = 0; d < 3; ++d) vel[3 * i + d] = mul_rn(lam, v[3 * i + d]);
     }
 }
 
 rbmd_status md_encode_positions(rbmd_ctx *c, const void *pos)
 {
-    const unsigned nb = (unsigned)((c->N + 255) / 256);
-    if (c->fp64) k_encode<double><<<nb, 256, 0, c->stream>>>((const double *)pos, c->N, c->L, c->u4);
-    else k_encode<float><<<nb, 256, 0, c->stream>>>((const float *)pos, c->N, c->L, c->u4);
+    if (c->fp64) k_encode<double><<<c->nb256, 256, 0, c->stream>>>((const double *)pos, c->map256, c->reps, c->u4);
+    else k_encode<float><<<c->nb256, 256, 0, c->stream>>>((const float *)pos, c->map256, c->reps, c->u4);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
 
 rbmd_status md_decode_state(rbmd_ctx *c, void *pos, void *vel)
 {
-    const unsigned nb = (unsigned)((c->N + 255) / 256);
     if (c->fp64)
-        k_decode<double><<<nb, 256, 0, c->stream>>>(c->u4, (const double *)c->vel, c->N, c->lscale,
-                                                    c->scal, (double *)pos, (double *)vel);
+        k_decode<double><<<c->nb256, 256, 0, c->stream>>>(c->u4, (const double *)c->vel, c->map256,
+                                                          c->reps, c->scal, (double *)pos,
+                                                          (double *)vel);
     else
-        k_decode<float><<<nb, 256, 0, c->stream>>>(c->u4, (const float *)c->vel, c->N, c->lscale,
-                                                   c->scal, (float *)pos, (float *)vel);
+        k_decode<float><<<c->nb256, 256, 0, c->stream>>>(c->u4, (const float *)c->vel, c->map256,
+                                                         c->reps, c->scal, (float *)pos,
+                                                         (float *)vel);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }

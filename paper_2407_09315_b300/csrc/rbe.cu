@@ -65,13 +65,19 @@ __device__ __forceinline__ int draw_axis(uint64_t U, const uint64_t *__restrict_
 // One thread per mode l: attempt t draws U_x, U_y from Philox(l, t, step, stream)
 // and U_z from Philox(l, t | 2^31, step, stream); m = 0 is redrawn (k != 0 in
 // Eq. 12).  After RBMD_MAX_ATTEMPTS zero draws the mode stays 0 (zero weight).
-__global__ void k_rbe_sample(const uint64_t *__restrict__ T, int M, int64_t P, uint2 key,
-                             StepRef sref, uint32_t replica, int4 *__restrict__ modes)
+__global__ void k_rbe_sample(const uint64_t *__restrict__ Tall, const Rep *__restrict__ reps,
+                             int R, int64_t P, StepRef sref, int4 *__restrict__ modes)
 {
-    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= P) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)R * P) return;
+    const int r = (int)(t / P);
+    const int64_t l = t - (int64_t)r * P;
+    const Rep rp = reps[r];
+    const uint64_t *T = Tall + rp.cdf0;
+    const int M = rp.M;
+    const uint2 key = rp.key;
     const uint32_t step = (uint32_t)step_of(sref);
-    const uint32_t tag = RBMD_STREAM_RBE | (replica << 8);
+    const uint32_t tag = rp.tag_rbe;
     int mx = 0, my = 0, mz = 0;
     for (uint32_t t = 0; t < RBMD_MAX_ATTEMPTS; ++t) {
         uint4 w = philox10(make_uint4((uint32_t)l, t, step, tag), key);
@@ -81,17 +87,15 @@ __global__ void k_rbe_sample(const uint64_t *__restrict__ T, int M, int64_t P, u
         mz = draw_axis(((uint64_t)w2.x << 32) | w2.y, T, M);
         if (mx != 0 || my != 0 || mz != 0) break;
     }
-    modes[l] = make_int4(mx, my, mz, 0);
+    modes[t] = make_int4(mx, my, mz, 0);
 }
 
 rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
 {
     if (c->full_modes) return RBMD_OK;  // fixed list built at init
-    uint2 key = make_uint2((uint32_t)(c->prm.seed & 0xFFFFFFFFu), (uint32_t)(c->prm.seed >> 32));
-    int threads = 128;
-    int blocks = (int)((c->Pm + threads - 1) / threads);
-    k_rbe_sample<<<blocks, threads, 0, c->stream>>>(c->cdf, c->M, c->Pm, key, s, c->prm.replica,
-                                                    c->modes);
+    const int threads = 128;
+    const int blocks = (int)((c->R * c->Pm + threads - 1) / threads);
+    k_rbe_sample<<<blocks, threads, 0, c->stream>>>(c->cdf, c->reps, c->R, c->Pm, s, c->modes);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
@@ -127,10 +131,10 @@ __device__ __forceinline__ void kahan_add(float &s, float &comp, float x)
 }
 
 template <typename real>
-__global__ void k_rho_partial(const uint4 *__restrict__ u4, const double *__restrict__ q64,
-                              int64_t N, const int4 *__restrict__ modes, int64_t Pm,
-                              int tile_atoms, int mode_tile, int sub,
-                              double2 *__restrict__ part)
+__global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial(const uint4 *__restrict__ u4, const double *__restrict__ q64,
+                              const int2 *__restrict__ tiles, const Rep *__restrict__ reps,
+                              const int4 *__restrict__ modes_all, int64_t Pm, int tile_atoms,
+                              int mode_tile, int sub, double2 *__restrict__ part)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint4 *s_at = reinterpret_cast<uint4 *>(smem);
@@ -138,8 +142,10 @@ __global__ void k_rho_partial(const uint4 *__restrict__ u4, const double *__rest
     int4 *s_m = reinterpret_cast<int4 *>(s_q + (sizeof(real) == 8 ? tile_atoms : 0));
     double2 *s_acc = reinterpret_cast<double2 *>(s_m + mode_tile);
 
-    const int64_t a0 = (int64_t)blockIdx.x * tile_atoms;
-    const int na = (int)min((int64_t)tile_atoms, N - a0);
+    const int2 tl = tiles[blockIdx.x];  // (replica, first atom); tiles never straddle replicas
+    const int64_t a0 = tl.y;
+    const int na = (int)min((int64_t)tile_atoms, reps[tl.x].atom0 + reps[tl.x].N - a0);
+    const int4 *modes = modes_all + (int64_t)tl.x * Pm;
     const int64_t l0 = (int64_t)blockIdx.y * mode_tile;
     const int nl = (int)min((int64_t)mode_tile, Pm - l0);
 
@@ -201,17 +207,20 @@ __global__ void k_rho_partial(const uint4 *__restrict__ u4, const double *__rest
 //   c_l = -(4 pi coulomb_k / V) W_l / k_l^2,  A_l = c_l Im rho_l,  B_l = c_l Re rho_l,
 //   e_l = coulomb_k (2 pi / V) W_l |rho_l|^2 / k_l^2   (energy estimate term).
 template <typename real>
-__global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, int64_t Pm,
-                            const int4 *__restrict__ modes, const double *__restrict__ W,
-                            double Wconst, double L, double ck, double2 *__restrict__ rho,
+__global__ void k_rho_final(const double2 *__restrict__ part, const Rep *__restrict__ reps, int R,
+                            int64_t Pm, const int4 *__restrict__ modes,
+                            const double *__restrict__ W, double ck, double2 *__restrict__ rho,
                             double *__restrict__ emode, ModeCoef<real> *__restrict__ coef)
 {
-    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // r Pm + l
     const int lane = threadIdx.x & 31;
-    if (l >= Pm) return;
+    if (t >= (int64_t)R * Pm) return;
+    const int r = (int)(t / Pm);
+    const int64_t lm = t - (int64_t)r * Pm;
+    const Rep rp = reps[r];
     double re = 0.0, im = 0.0;
-    for (int t = lane; t < ntiles; t += 32) {
-        double2 p = part[(int64_t)t * Pm + l];
+    for (int k = lane; k < rp.ntiles; k += 32) {
+        double2 p = part[(int64_t)(rp.tile0 + k) * Pm + lm];
         re += p.x;
         im += p.y;
     }
@@ -221,12 +230,14 @@ __global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, int64_
         im += __shfl_xor_sync(0xffffffffu, im, o);
     }
     if (lane != 0) return;
+    const int64_t l = t;
     const int4 m = modes[l];
+    const double L = rp.L;
     const double V = L * L * L;
     const double tk = 2.0 * kPi / L;
     const double kx = tk * m.x, ky = tk * m.y, kz = tk * m.z;
     const double k2 = kx * kx + ky * ky + kz * kz;
-    const double w = W ? W[l] : Wconst;
+    const double w = W ? W[lm] : rp.Wrbe;
     double cl = 0.0, e = 0.0;
     if (k2 > 0.0) {
         cl = -(4.0 * kPi * ck / V) * w / k2;
@@ -256,26 +267,26 @@ rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
     sub = min(sub, tile);
     int threads = ((mode_tile * sub + 31) / 32) * 32;
     threads = min(threads, 1024);
-    dim3 grid((unsigned)c->rho_tiles, (unsigned)((c->Pm + mode_tile - 1) / mode_tile));
+    dim3 grid((unsigned)c->ntiles, (unsigned)((c->Pm + mode_tile - 1) / mode_tile));
     size_t smem = (size_t)tile * sizeof(uint4) + (c->fp64 ? (size_t)tile * sizeof(double) : 0) +
                   (size_t)mode_tile * sizeof(int4) + (size_t)mode_tile * sub * sizeof(double2);
-    const double Wconst = c->S / (double)c->prm.rbe_P;
+    const unsigned fin_blocks = (unsigned)((c->R * c->Pm * 32 + 255) / 256);
     if (c->fp64) {
         k_rho_partial<double><<<grid, threads, smem, c->stream>>>(
-            c->u4, c->q64, c->N, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
+            c->u4, c->q64, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
         RBMD_LAUNCH_CHECK();
         if (mark_between >= 0) prof_mark(c, mark_between);
-        k_rho_final<double><<<(unsigned)((c->Pm * 32 + 255) / 256), 256, 0, c->stream>>>(
-            c->rho_part, c->rho_tiles, c->Pm, c->modes, c->W, Wconst, c->L, c->prm.coulomb_k,
-            c->rho, c->emode, (ModeCoef<double> *)c->coef);
+        k_rho_final<double><<<fin_blocks, 256, 0, c->stream>>>(
+            c->rho_part, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
+            (ModeCoef<double> *)c->coef);
     } else {
         k_rho_partial<float><<<grid, threads, smem, c->stream>>>(
-            c->u4, nullptr, c->N, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
+            c->u4, nullptr, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
         RBMD_LAUNCH_CHECK();
         if (mark_between >= 0) prof_mark(c, mark_between);
-        k_rho_final<float><<<(unsigned)((c->Pm * 32 + 255) / 256), 256, 0, c->stream>>>(
-            c->rho_part, c->rho_tiles, c->Pm, c->modes, c->W, Wconst, c->L, c->prm.coulomb_k,
-            c->rho, c->emode, (ModeCoef<float> *)c->coef);
+        k_rho_final<float><<<fin_blocks, 256, 0, c->stream>>>(
+            c->rho_part, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
+            (ModeCoef<float> *)c->coef);
     }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
@@ -290,12 +301,16 @@ rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
 // --------------------------------------------------------------------------
 template <typename real, int CHUNK>
 __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restrict__ q64,
-                            int64_t N, const ModeCoef<real> *__restrict__ coef, int64_t Pm,
-                            real tk, real *__restrict__ F, int accumulate)
+                            const int2 *__restrict__ map, const Rep *__restrict__ reps,
+                            const ModeCoef<real> *__restrict__ coef_all, int64_t Pm,
+                            real *__restrict__ F, int accumulate)
 {
     __shared__ ModeCoef<real> s_c[CHUNK];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < N;
+    const AtomSlot sl = atom_slot(map, reps);  // the whole block belongs to replica sl.r
+    const int64_t i = sl.i;
+    const bool active = sl.ok;
+    const ModeCoef<real> *coef = coef_all + (int64_t)sl.r * Pm;
+    const real tk = (real)(2.0 * kPi / reps[sl.r].L);
     uint4 A = active ? u4[i] : make_uint4(0, 0, 0, 0);
     real fx = 0, fy = 0, fz = 0;
     for (int64_t c0 = 0; c0 < Pm; c0 += CHUNK) {
@@ -336,16 +351,14 @@ __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restri
 
 rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate)
 {
-    const int threads = c->force_block;
-    const unsigned blocks = (unsigned)((c->N + threads - 1) / threads);
     if (c->fp64) {
-        k_rbe_force<double, 128><<<blocks, threads, 0, c->stream>>>(
-            c->u4, c->q64, c->N, (const ModeCoef<double> *)c->coef, c->Pm, 2.0 * kPi / c->L,
+        k_rbe_force<double, 128><<<c->nb256, 256, 0, c->stream>>>(
+            c->u4, c->q64, c->map256, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
             (double *)force, accumulate);
     } else {
-        k_rbe_force<float, 256><<<blocks, threads, 0, c->stream>>>(
-            c->u4, nullptr, c->N, (const ModeCoef<float> *)c->coef, c->Pm,
-            (float)(2.0 * kPi / c->L), (float *)force, accumulate);
+        k_rbe_force<float, 256><<<c->nb256, 256, 0, c->stream>>>(
+            c->u4, nullptr, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
+            (float *)force, accumulate);
     }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;

@@ -27,14 +27,20 @@ __device__ __forceinline__ int cell_coord(uint32_t u, int nc)
 }
 
 // ---------------------------------------------------------------- binning
-__global__ void k_cell_count(const uint4 *__restrict__ u4, int64_t N, int nc,
-                             int32_t *__restrict__ count, int32_t *__restrict__ cell_of,
-                             int32_t *__restrict__ rank)
+__global__ void k_cell_count(const uint4 *__restrict__ u4, const int2 *__restrict__ map,
+                             const Rep *__restrict__ reps, int32_t *__restrict__ count,
+                             int32_t *__restrict__ cell_of, int32_t *__restrict__ rank)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    uint4 A = u4[i];
-    int64_t c = ((int64_t)cell_coord(A.x, nc) * nc + cell_coord(A.y, nc)) * nc + cell_coord(A.z, nc);
+    const AtomSlot sl = atom_slot(map, reps);
+    if (!sl.ok) return;
+    const int64_t i = sl.i;
+    const int nc = reps[sl.r].nc;
+    const uint4 A = u4[i];
+    // each replica owns its own range of cells, so the sorted order keeps the
+    // replicas contiguous and in order
+    const int64_t c = reps[sl.r].cell0 +
+                      ((int64_t)cell_coord(A.x, nc) * nc + cell_coord(A.y, nc)) * nc +
+                      cell_coord(A.z, nc);
     cell_of[i] = (int32_t)c;
     rank[i] = atomicAdd(&count[c], 1);
 }
@@ -152,8 +158,8 @@ rbmd_status cells_build(rbmd_ctx *c)
     const int th = 256;
     const unsigned nb = (unsigned)((c->N + th - 1) / th);
     RBMD_CHECK_CUDA(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, c->stream));
-    k_cell_count<<<nb, th, 0, c->stream>>>(c->u4, c->N, c->nc, c->cell_count, c->cell_of,
-                                           c->cell_rank);
+    k_cell_count<<<c->nb256, 256, 0, c->stream>>>(c->u4, c->map256, c->reps, c->cell_count,
+                                                   c->cell_of, c->cell_rank);
     RBMD_LAUNCH_CHECK();
     const int ntiles = (int)((c->ncell + SCAN_TILE - 1) / SCAN_TILE);
     k_scan_tiles<<<ntiles, 256, 0, c->stream>>>(c->cell_count, c->ncell, c->scan_part);
@@ -204,15 +210,13 @@ template <typename real> struct PairArgs {
     const int32_t *stype;
     const int32_t *cell_start;
     const real *lj;  // [2T]: sqrt(eps_t), sigma_t / 2
-    int64_t N;
-    int nc, div, T, p, exact;
-    uint64_t Rc2, Rs2;
-    uint32_t Rlin;
-    uint2 key;
+    const Rep *reps;   // per-replica constants (box, cells, radii, Philox key and tag)
+    const int2 *map;   // replica-aligned block map of the launch
+    int nmap;          // entries of map (blocks of the fallback's grid-stride loop)
+    int64_t N;         // all replicas
+    int div, T, p, exact;
     StepRef step;
-    uint32_t tag;
-    real ck, alpha, sqrt_alpha, c2, lscale;
-    float cull_r;      // r_cut in cell widths, with a safety margin
+    real ck, alpha, sqrt_alpha, c2;
     real *F;
     int accumulate;
     double *fpart;     // [parts][3]: pair kernel per warp, then the fallback per warp
@@ -267,7 +271,7 @@ __device__ __forceinline__ void pair_eval(const PairArgs<real> &a, real dx, real
 // Per-atom context for pair evaluations.
 template <typename real> struct AtomI {
     uint4 A;
-    real qi, se, hs;
+    real qi, se, hs, lscale;
 };
 
 template <typename real, bool ENERGY>
@@ -277,9 +281,9 @@ __device__ __forceinline__ void eval_k(const PairArgs<real> &a, const real *s_lj
 {
     const uint4 B = a.spos[k];
     const int tj = a.stype[k];
-    pair_eval<real, ENERGY>(a, (real)(int32_t)(B.x - I.A.x) * a.lscale,
-                            (real)(int32_t)(B.y - I.A.y) * a.lscale,
-                            (real)(int32_t)(B.z - I.A.z) * a.lscale, I.qi * a.sq[k],
+    pair_eval<real, ENERGY>(a, (real)(int32_t)(B.x - I.A.x) * I.lscale,
+                            (real)(int32_t)(B.y - I.A.y) * I.lscale,
+                            (real)(int32_t)(B.z - I.A.z) * I.lscale, I.qi * a.sq[k],
                             I.se * s_lj[tj], I.hs + s_lj[a.T + tj], fx, fy, fz, ec, el);
 }
 
@@ -330,14 +334,15 @@ struct SelCtx {
     const uint4 *spos;
     Philox0 r0;
     uint2 key;
+    uint32_t id0;  // first atom of the replica: Philox counters use replica-local ids
 };
 
-// true if slot (sorted index hk) orders before the candidate with atom id `id`.
+// true if slot (sorted index hk) orders before the candidate with local id `id`.
 __device__ __noinline__ bool sel_slot_before(const SelCtx &s, int hk, uint32_t id)
 {
     if (hk == SEL_NEG) return true;
     if (hk == SEL_POS) return false;
-    const uint32_t hid = s.spos[hk].w;
+    const uint32_t hid = s.spos[hk].w - s.id0;
     const uint2 pa = philox_rest(s.r0, hid, s.key), pb = philox_rest(s.r0, id, s.key);
     if (pa.x != pb.x) return pa.x < pb.x;
     if (pa.y != pb.y) return pa.y < pb.y;
@@ -399,14 +404,16 @@ __device__ __forceinline__ float cell_frac(uint32_t u, int nc)
 // are skipped by a conservative float test with a 1e-5 margin: this only saves
 // work, membership itself is decided on integers.
 template <typename real, class F>
-__device__ __forceinline__ void stencil_ranges(const PairArgs<real> &a, const uint4 &A, F &&f)
+__device__ __forceinline__ void stencil_ranges(const PairArgs<real> &a, const Rep &rp,
+                                               const uint4 &A, F &&f)
 {
-    const int nc = a.nc, dv = a.div;
+    const int nc = rp.nc, dv = a.div;
+    const int32_t *cell_start = a.cell_start + rp.cell0;
     const int cx = cell_coord(A.x, nc), cy = cell_coord(A.y, nc), cz = cell_coord(A.z, nc);
     const bool full = nc >= 2 * dv + 1;  // else every cell along an axis, once
     const int span = full ? 2 * dv + 1 : nc;
     const float fxc = cell_frac(A.x, nc), fyc = cell_frac(A.y, nc), fzc = cell_frac(A.z, nc);
-    const float Rw = a.cull_r, Rw2 = a.cull_r * a.cull_r;
+    const float Rw = rp.cull_r, Rw2 = rp.cull_r * rp.cull_r;
     for (int ox = 0; ox < span; ++ox) {
         float wx = 0.f;
         int gx = ox;
@@ -433,26 +440,26 @@ __device__ __forceinline__ void stencil_ranges(const PairArgs<real> &a, const ui
             const int64_t row = ((int64_t)gx * nc + gy) * nc;
             int rb0, re0, rb1 = 0, re1 = 0;
             if (!full) {
-                rb0 = a.cell_start[row];
-                re0 = a.cell_start[row + nc];
+                rb0 = cell_start[row];
+                re0 = cell_start[row + nc];
             } else {
                 // z cells reachable within the remaining radius, relative to cz
                 const float rz = sqrtf(fmaxf(rem, 0.f));
                 const int z0 = cz + max(-dv, (int)floorf(fzc - rz));
                 const int z1 = cz + min(dv, (int)floorf(fzc + rz));  // inclusive, may wrap
                 if (z0 < 0) {
-                    rb0 = a.cell_start[row + z0 + nc];
-                    re0 = a.cell_start[row + nc];
-                    rb1 = a.cell_start[row];
-                    re1 = a.cell_start[row + z1 + 1];
+                    rb0 = cell_start[row + z0 + nc];
+                    re0 = cell_start[row + nc];
+                    rb1 = cell_start[row];
+                    re1 = cell_start[row + z1 + 1];
                 } else if (z1 >= nc) {
-                    rb0 = a.cell_start[row + z0];
-                    re0 = a.cell_start[row + nc];
-                    rb1 = a.cell_start[row];
-                    re1 = a.cell_start[row + z1 - nc + 1];
+                    rb0 = cell_start[row + z0];
+                    re0 = cell_start[row + nc];
+                    rb1 = cell_start[row];
+                    re1 = cell_start[row + z1 - nc + 1];
                 } else {
-                    rb0 = a.cell_start[row + z0];
-                    re0 = a.cell_start[row + z1 + 1];
+                    rb0 = cell_start[row + z0];
+                    re0 = cell_start[row + z1 + 1];
                 }
             }
             f(rb0, re0);
@@ -463,8 +470,7 @@ __device__ __forceinline__ void stencil_ranges(const PairArgs<real> &a, const ui
 
 // 0: not a neighbour, 1: core (D < Rc2), 2: shell (Rc2 <= D <= Rs2).  Integer
 // minimum image d = (int32)(u_j - u_i); D = sum d^2 in uint64 (cannot overflow).
-template <typename real>
-__device__ __forceinline__ int classify(const PairArgs<real> &a, const uint4 &A, const uint4 &B)
+__device__ __forceinline__ int classify(const Rep &a, const uint4 &A, const uint4 &B)
 {
     const int32_t dx = (int32_t)(B.x - A.x);
     const int32_t dy = (int32_t)(B.y - A.y);
@@ -490,20 +496,22 @@ __device__ __forceinline__ bool overflowed(const PairArgs<real> &a, int2 cnt)
 template <typename real, bool ENERGY, bool LISTS>
 __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
 {
-    const int64_t is = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (is >= a.N) return;
+    const AtomSlot sl = atom_slot(a.map, a.reps);  // replica ranges are the same when sorted
+    if (!sl.ok) return;
+    const int64_t is = sl.i;
+    const Rep rp = a.reps[sl.r];  // by value: the fields live in registers
     const uint4 A = a.spos[is];
     int32_t *lc = a.lcore + is * a.CC;
     int32_t *ls = a.lshell + is * a.CS;
     int ncore = 0, ns = 0;
-    stencil_ranges(a, A, [&](int kb, int ke) {
+    stencil_ranges(a, rp, A, [&](int kb, int ke) {
         for (int k = kb; k < ke; k += 4) {
             uint4 B[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) B[q] = (k + q < ke) ? a.spos[k + q] : A;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int c = (k + q < ke && k + q != (int)is) ? classify(a, A, B[q]) : 0;
+                const int c = (k + q < ke && k + q != (int)is) ? classify(rp, A, B[q]) : 0;
                 if (c == 1) {
                     if (ncore < a.CC) lc[ncore] = k + q;
                     ++ncore;
@@ -529,10 +537,13 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
 // Step 1b: the batch B(i), the p shell members with the smallest Philox priority
 // (all of them when N_s <= p), as sorted indices in bk[i][0..min(N_s,p)).
 template <typename real, int CAP, bool LISTS>
-__global__ void __launch_bounds__(256) k_rbl_select(PairArgs<real> a)
+__global__ void __launch_bounds__(256, (CAP <= 10 ? 3 : 1)) k_rbl_select(PairArgs<real> a)
 {
-    const int64_t is = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (is >= a.N) return;
+    const AtomSlot sl = atom_slot(a.map, a.reps);
+    if (!sl.ok) return;
+    const int64_t is = sl.i;
+    const Rep rp = a.reps[sl.r];
+    const uint32_t id0 = (uint32_t)rp.atom0;
     const int2 cnt = a.ncount[is];
     if (overflowed(a, cnt)) return;
     const int ns = cnt.y;
@@ -544,15 +555,16 @@ __global__ void __launch_bounds__(256) k_rbl_select(PairArgs<real> a)
         for (int e = 0; e < ns; ++e) bk[e] = ls[e];
         nb = ns;
     } else {
-        const SelCtx sel{a.spos, philox_round0(id_i, (uint32_t)step_of(a.step), a.tag, a.key),
-                         a.key};
+        const SelCtx sel{a.spos,
+                         philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key),
+                         rp.key, id0};
         uint32_t hh[CAP];
         int hk[CAP];
         sel_init<CAP>(hh, hk, a.p);
         for (int e = 0; e < ns; ++e) {
             const int k = ls[e];
-            const uint32_t id = a.spos[k].w;
-            const uint2 w = philox_rest(sel.r0, id, a.key);
+            const uint32_t id = a.spos[k].w - id0;
+            const uint2 w = philox_rest(sel.r0, id, rp.key);
             sel_insert<CAP>(hh, hk, w.x, k, id, sel);
         }
 #pragma unroll
@@ -582,15 +594,17 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
     __shared__ real s_lj[2 * RBMD_MAX_TYPES];
     for (int t = threadIdx.x; t < 2 * a.T; t += blockDim.x) s_lj[t] = a.lj[t];
     __syncthreads();
-    const int64_t is = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const AtomSlot sl = atom_slot(a.map, a.reps);
+    const int64_t is = sl.i;
     real fx = 0, fy = 0, fz = 0;
     double ec = 0.0, el = 0.0;
-    if (is < a.N) {
+    if (sl.ok) {
         const int2 cnt = a.ncount[is];
         if (!overflowed(a, cnt)) {
             AtomI<real> I;
             I.A = a.spos[is];
             I.qi = a.sq[is] * a.ck;
+            I.lscale = (real)a.reps[sl.r].lscale;
             const int ti = a.stype[is];
             I.se = s_lj[ti];
             I.hs = s_lj[a.T + ti];
@@ -645,11 +659,10 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
 }
 
 // Exact fallback for atoms whose lists overflowed (Algorithm 2 for one atom,
-// fused, with the candidate list in shared memory and flushed when full).
-// Grid-stride over the sorted atoms in a fixed order, so the partial sums stay
-// deterministic.  Returns at once (after zeroing its partial slots) when no
-// list overflowed.
-constexpr int FB_BLOCKS = 64;
+// fused, with the candidate list in shared memory and flushed when full).  A
+// grid-stride loop over the same replica-aligned 128-atom blocks as k_rbl_force,
+// so the partial sums stay per replica and deterministic; when no list
+// overflowed it only zeroes its partial slots.
 constexpr int FB_LIST = 44;
 
 template <typename real, int CAP, bool ENERGY, bool LISTS>
@@ -659,127 +672,147 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
     __shared__ int32_t s_k[FB_LIST][kPairBlock];
     __shared__ uint32_t s_id[FB_LIST][kPairBlock];
     const int tid = threadIdx.x;
-    real fx = 0, fy = 0, fz = 0;
-    double ec = 0.0, el = 0.0;
-    const bool any = *a.ovf != 0;
-    if (any) {
-        for (int t = tid; t < 2 * a.T; t += blockDim.x) s_lj[t] = a.lj[t];
-        __syncthreads();
-        for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.N;
-             base += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t is = base + tid;
-            if (is >= a.N || !overflowed(a, a.ncount[is])) continue;
-            AtomI<real> I;
-            I.A = a.spos[is];
-            I.qi = a.sq[is] * a.ck;
-            const int ti = a.stype[is];
-            I.se = s_lj[ti];
-            I.hs = s_lj[a.T + ti];
-            const uint32_t id_i = I.A.w;
-            const SelCtx sel{a.spos, philox_round0(id_i, (uint32_t)step_of(a.step), a.tag, a.key),
-                             a.key};
-            uint32_t hh[CAP];
-            int hk[CAP];
-            sel_init<CAP>(hh, hk, a.p);
-            real ax = 0, ay = 0, az = 0;
-            double aec = 0.0, ael = 0.0;
-            int lc = 0, lsn = 0, ncore = 0, ns = 0;
-            auto flush = [&]() {
-                for (int e = 0; e < lsn; ++e) {
-                    const int k = s_k[FB_LIST - 1 - e][tid];
-                    if (a.exact) {
-                        eval_k<real, ENERGY>(a, s_lj, I, k, ax, ay, az, aec, ael);
-                    } else {
-                        const uint32_t id = s_id[FB_LIST - 1 - e][tid];
-                        const uint2 w = philox_rest(sel.r0, id, a.key);
-                        sel_insert<CAP>(hh, hk, w.x, k, id, sel);
-                    }
-                }
-                for (int e = 0; e < lc; ++e) eval_k<real, ENERGY>(a, s_lj, I, s_k[e][tid], ax, ay, az, aec, ael);
-                lc = 0;
-                lsn = 0;
-            };
-            stencil_ranges(a, I.A, [&](int kb, int ke) {
-                for (int k = kb; k < ke; ++k) {
-                    if (k == (int)is) continue;
-                    const uint4 B = a.spos[k];
-                    const int c = classify(a, I.A, B);
-                    if (c == 1) {
-                        s_k[lc][tid] = k;
-                        ++lc;
-                        ++ncore;
-                    } else if (c == 2) {
-                        s_k[FB_LIST - 1 - lsn][tid] = k;
-                        s_id[FB_LIST - 1 - lsn][tid] = B.w;
-                        ++lsn;
-                        ++ns;
-                    }
-                    if (lc + lsn == FB_LIST) flush();
-                }
-            });
-            flush();
-            if (!a.exact) {
-                const real w = ns > a.p ? (real)ns / (real)a.p : (real)1;
-                real bx = 0, by = 0, bz = 0;
-                double bec = 0.0, bel = 0.0;
-#pragma unroll
-                for (int e = 0; e < CAP; ++e)
-                    if (hk[e] >= 0) eval_k<real, ENERGY>(a, s_lj, I, hk[e], bx, by, bz, bec, bel);
-                ax += w * bx;
-                ay += w * by;
-                az += w * bz;
-                if constexpr (ENERGY) {
-                    aec += (double)w * bec;
-                    ael += (double)w * bel;
-                }
-                if constexpr (LISTS) {
-                    int32_t *out = a.batch + (int64_t)id_i * a.p;
-                    for (int e = 0; e < a.p; ++e) out[e] = -1;
-                    int nb = 0;
-#pragma unroll
-                    for (int e = 0; e < CAP; ++e) {
-                        if (hk[e] < 0) continue;
-                        const int32_t v = (int32_t)a.spos[hk[e]].w;
-                        int y = nb - 1;
-                        while (y >= 0 && out[y] > v) {
-                            out[y + 1] = out[y];
-                            --y;
-                        }
-                        out[y + 1] = v;
-                        ++nb;
-                    }
-                }
+    constexpr int WPB = kPairBlock / 32;  // partial slots (warps) per map block
+    if (*a.ovf == 0) {
+        // nothing overflowed: the fallback's partial slots are zero
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + tid; j < (int64_t)a.nmap * WPB;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t part = a.fb_part0 + j;
+            a.fpart[3 * part + 0] = 0.0;
+            a.fpart[3 * part + 1] = 0.0;
+            a.fpart[3 * part + 2] = 0.0;
+            if constexpr (ENERGY) {
+                a.epart[2 * part + 0] = 0.0;
+                a.epart[2 * part + 1] = 0.0;
             }
-            real *f = a.F + 3 * (int64_t)id_i;
-            if (a.accumulate) {
-                f[0] += ax;
-                f[1] += ay;
-                f[2] += az;
-            } else {
-                f[0] = ax;
-                f[1] = ay;
-                f[2] = az;
-            }
-            fx += ax;
-            fy += ay;
-            fz += az;
-            ec += aec;
-            el += ael;
         }
+        return;
     }
-    constexpr int NV = ENERGY ? 5 : 3;
-    double v[5] = {(double)fx, (double)fy, (double)fz, 0.5 * ec, 0.5 * el};
+    for (int t = tid; t < 2 * a.T; t += blockDim.x) s_lj[t] = a.lj[t];
+    __syncthreads();
+    for (int mb = blockIdx.x; mb < a.nmap; mb += gridDim.x) {
+        real fx = 0, fy = 0, fz = 0;
+        double ec = 0.0, el = 0.0;
+        const AtomSlot sl = atom_slot_at(a.map, a.reps, mb);
+        {
+            const int64_t is = sl.i;
+            if (sl.ok && overflowed(a, a.ncount[is])) {
+                const Rep rp = a.reps[sl.r];
+                const uint32_t id0 = (uint32_t)rp.atom0;
+                AtomI<real> I;
+                I.A = a.spos[is];
+                I.qi = a.sq[is] * a.ck;
+                I.lscale = (real)rp.lscale;
+                const int ti = a.stype[is];
+                I.se = s_lj[ti];
+                I.hs = s_lj[a.T + ti];
+                const uint32_t id_i = I.A.w;
+                const SelCtx sel{
+                    a.spos, philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key),
+                    rp.key, id0};
+                uint32_t hh[CAP];
+                int hk[CAP];
+                sel_init<CAP>(hh, hk, a.p);
+                real ax = 0, ay = 0, az = 0;
+                double aec = 0.0, ael = 0.0;
+                int lc = 0, lsn = 0, ncore = 0, ns = 0;
+                auto flush = [&]() {
+                    for (int e = 0; e < lsn; ++e) {
+                        const int k = s_k[FB_LIST - 1 - e][tid];
+                        if (a.exact) {
+                            eval_k<real, ENERGY>(a, s_lj, I, k, ax, ay, az, aec, ael);
+                        } else {
+                            const uint32_t id = s_id[FB_LIST - 1 - e][tid] - id0;
+                            const uint2 w = philox_rest(sel.r0, id, rp.key);
+                            sel_insert<CAP>(hh, hk, w.x, k, id, sel);
+                        }
+                    }
+                    for (int e = 0; e < lc; ++e) eval_k<real, ENERGY>(a, s_lj, I, s_k[e][tid], ax, ay, az, aec, ael);
+                    lc = 0;
+                    lsn = 0;
+                };
+                stencil_ranges(a, rp, I.A, [&](int kb, int ke) {
+                    for (int k = kb; k < ke; ++k) {
+                        if (k == (int)is) continue;
+                        const uint4 B = a.spos[k];
+                        const int c = classify(rp, I.A, B);
+                        if (c == 1) {
+                            s_k[lc][tid] = k;
+                            ++lc;
+                            ++ncore;
+                        } else if (c == 2) {
+                            s_k[FB_LIST - 1 - lsn][tid] = k;
+                            s_id[FB_LIST - 1 - lsn][tid] = B.w;
+                            ++lsn;
+                            ++ns;
+                        }
+                        if (lc + lsn == FB_LIST) flush();
+                    }
+                });
+                flush();
+                if (!a.exact) {
+                    const real w = ns > a.p ? (real)ns / (real)a.p : (real)1;
+                    real bx = 0, by = 0, bz = 0;
+                    double bec = 0.0, bel = 0.0;
 #pragma unroll
-    for (int c = 0; c < NV; ++c)
-        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-    if ((tid & 31) == 0) {
-        const int64_t part = a.fb_part0 + (int64_t)blockIdx.x * (kPairBlock / 32) + (tid >> 5);
-        a.fpart[3 * part + 0] = v[0];
-        a.fpart[3 * part + 1] = v[1];
-        a.fpart[3 * part + 2] = v[2];
-        if constexpr (ENERGY) {
-            a.epart[2 * part + 0] = v[3];
-            a.epart[2 * part + 1] = v[4];
+                    for (int e = 0; e < CAP; ++e)
+                        if (hk[e] >= 0) eval_k<real, ENERGY>(a, s_lj, I, hk[e], bx, by, bz, bec, bel);
+                    ax += w * bx;
+                    ay += w * by;
+                    az += w * bz;
+                    if constexpr (ENERGY) {
+                        aec += (double)w * bec;
+                        ael += (double)w * bel;
+                    }
+                    if constexpr (LISTS) {
+                        int32_t *out = a.batch + (int64_t)id_i * a.p;
+                        for (int e = 0; e < a.p; ++e) out[e] = -1;
+                        int nb = 0;
+#pragma unroll
+                        for (int e = 0; e < CAP; ++e) {
+                            if (hk[e] < 0) continue;
+                            const int32_t v = (int32_t)a.spos[hk[e]].w;
+                            int y = nb - 1;
+                            while (y >= 0 && out[y] > v) {
+                                out[y + 1] = out[y];
+                                --y;
+                            }
+                            out[y + 1] = v;
+                            ++nb;
+                        }
+                    }
+                }
+                real *f = a.F + 3 * (int64_t)id_i;
+                if (a.accumulate) {
+                    f[0] += ax;
+                    f[1] += ay;
+                    f[2] += az;
+                } else {
+                    f[0] = ax;
+                    f[1] = ay;
+                    f[2] = az;
+                }
+                fx += ax;
+                fy += ay;
+                fz += az;
+                ec += aec;
+                el += ael;
+            }
+        }
+        constexpr int NV = ENERGY ? 5 : 3;
+        double v[5] = {(double)fx, (double)fy, (double)fz, 0.5 * ec, 0.5 * el};
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+            for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+        if ((tid & 31) == 0) {
+            const int64_t part = a.fb_part0 + (int64_t)mb * WPB + (tid >> 5);
+            a.fpart[3 * part + 0] = v[0];
+            a.fpart[3 * part + 1] = v[1];
+            a.fpart[3 * part + 2] = v[2];
+            if constexpr (ENERGY) {
+                a.epart[2 * part + 0] = v[3];
+                a.epart[2 * part + 1] = v[4];
+            }
         }
     }
 }
@@ -788,28 +821,33 @@ template <typename real, int CAP>
 static void launch_rbl(rbmd_ctx *c, const PairArgs<real> &a, cudaStream_t st, bool energy,
                        bool lists, bool marks)
 {
-    const unsigned nb256 = (unsigned)((a.N + 255) / 256);
-    const unsigned nbp = (unsigned)((a.N + kPairBlock - 1) / kPairBlock);
+    PairArgs<real> a256 = a, a128 = a;
+    a256.map = c->map256;
+    a256.nmap = c->nb256;
+    a128.map = c->map128;
+    a128.nmap = c->nb128;
+    const unsigned nb256 = (unsigned)c->nb256, nbp = (unsigned)c->nb128;
+    const unsigned nfb = (unsigned)min(c->nb128, 4 * 148);  // fallback: a few waves at most
     if (lists) {
-        if (energy) k_rbl_scan<real, true, true><<<nb256, 256, 0, st>>>(a);
-        else k_rbl_scan<real, false, true><<<nb256, 256, 0, st>>>(a);
+        if (energy) k_rbl_scan<real, true, true><<<nb256, 256, 0, st>>>(a256);
+        else k_rbl_scan<real, false, true><<<nb256, 256, 0, st>>>(a256);
         if (marks) prof_mark(c, 3);
-        if (!a.exact) k_rbl_select<real, CAP, true><<<nb256, 256, 0, st>>>(a);
+        if (!a.exact) k_rbl_select<real, CAP, true><<<nb256, 256, 0, st>>>(a256);
     } else {
-        if (energy) k_rbl_scan<real, true, false><<<nb256, 256, 0, st>>>(a);
-        else k_rbl_scan<real, false, false><<<nb256, 256, 0, st>>>(a);
+        if (energy) k_rbl_scan<real, true, false><<<nb256, 256, 0, st>>>(a256);
+        else k_rbl_scan<real, false, false><<<nb256, 256, 0, st>>>(a256);
         if (marks) prof_mark(c, 3);
-        if (!a.exact) k_rbl_select<real, CAP, false><<<nb256, 256, 0, st>>>(a);
+        if (!a.exact) k_rbl_select<real, CAP, false><<<nb256, 256, 0, st>>>(a256);
     }
     if (marks) prof_mark(c, 4);
-    if (energy) k_rbl_force<real, true><<<nbp, kPairBlock, 0, st>>>(a);
-    else k_rbl_force<real, false><<<nbp, kPairBlock, 0, st>>>(a);
+    if (energy) k_rbl_force<real, true><<<nbp, kPairBlock, 0, st>>>(a128);
+    else k_rbl_force<real, false><<<nbp, kPairBlock, 0, st>>>(a128);
     if (lists) {
-        if (energy) k_rbl_fused<real, CAP, true, true><<<FB_BLOCKS, kPairBlock, 0, st>>>(a);
-        else k_rbl_fused<real, CAP, false, true><<<FB_BLOCKS, kPairBlock, 0, st>>>(a);
+        if (energy) k_rbl_fused<real, CAP, true, true><<<nfb, kPairBlock, 0, st>>>(a128);
+        else k_rbl_fused<real, CAP, false, true><<<nfb, kPairBlock, 0, st>>>(a128);
     } else {
-        if (energy) k_rbl_fused<real, CAP, true, false><<<FB_BLOCKS, kPairBlock, 0, st>>>(a);
-        else k_rbl_fused<real, CAP, false, false><<<FB_BLOCKS, kPairBlock, 0, st>>>(a);
+        if (energy) k_rbl_fused<real, CAP, true, false><<<nfb, kPairBlock, 0, st>>>(a128);
+        else k_rbl_fused<real, CAP, false, false><<<nfb, kPairBlock, 0, st>>>(a128);
     }
 }
 
@@ -824,28 +862,22 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     a.cell_start = c->cell_start;
     a.lj = c->fp64 ? (const real *)c->lj_d : (const real *)c->lj_f;
     a.N = c->N;
-    a.nc = c->nc;
+    a.reps = c->reps;
+    a.map = c->map256;
     a.div = c->div;
     a.T = c->T;
     a.p = c->prm.rbl_p;
     a.exact = (c->prm.flags & RBMD_RBL_EXACT) ? 1 : 0;
-    a.Rc2 = c->Rc2;
-    a.Rs2 = c->Rs2;
-    a.Rlin = c->Rlin;
-    a.key = make_uint2((uint32_t)(c->prm.seed & 0xFFFFFFFFu), (uint32_t)(c->prm.seed >> 32));
     a.step = s;
-    a.tag = RBMD_STREAM_RBL | (c->prm.replica << 8);
     a.ck = (real)c->prm.coulomb_k;
     a.alpha = (real)c->prm.alpha;
     a.sqrt_alpha = (real)sqrt(c->prm.alpha);
     a.c2 = (real)(2.0 * sqrt(c->prm.alpha / kPi));
-    a.lscale = (real)c->lscale;
-    a.cull_r = (float)(c->prm.r_cut * c->nc / c->L * (1.0 + 1e-5) + 1e-6);
     a.F = (real *)force;
     a.accumulate = accumulate;
     a.fpart = c->fpart;
     a.epart = c->epart;
-    a.fb_part0 = c->pair_blocks * (int64_t)(kPairBlock / 32);
+    a.fb_part0 = 4 * (int64_t)c->nb128;
     a.imax = c->ibuf;
     a.n_core = n_core;
     a.n_shell = n_shell;
@@ -879,18 +911,13 @@ static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
     a.stype = c->stype;
     a.cell_start = c->cell_start;
     a.N = c->N;
-    a.nc = c->nc;
+    a.reps = c->reps;
+    a.map = c->map256;
     a.div = c->div;
     a.T = c->T;
     a.p = c->prm.rbl_p;
     a.exact = (c->prm.flags & RBMD_RBL_EXACT) ? 1 : 0;
-    a.Rc2 = c->Rc2;
-    a.Rs2 = c->Rs2;
-    a.Rlin = c->Rlin;
-    a.key = make_uint2((uint32_t)(c->prm.seed & 0xFFFFFFFFu), (uint32_t)(c->prm.seed >> 32));
     a.step = s;
-    a.tag = RBMD_STREAM_RBL | (c->prm.replica << 8);
-    a.cull_r = (float)(c->prm.r_cut * c->nc / c->L * (1.0 + 1e-5) + 1e-6);
     a.imax = c->ibuf;
     a.lcore = c->lcore;
     a.lshell = c->lshell;
@@ -900,7 +927,7 @@ static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
     a.CC = c->list_cc;
     a.CS = c->list_cs;
     RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf, 0, 3 * sizeof(int32_t), c->stream));
-    const unsigned nb256 = (unsigned)((a.N + 255) / 256);
+    const unsigned nb256 = (unsigned)c->nb256;
     k_rbl_scan<real, true, false><<<nb256, 256, 0, c->stream>>>(a);
     if (!a.exact) {
         const int p = c->prm.rbl_p;
@@ -945,26 +972,31 @@ rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool 
 
 // ---------------------------------------------------------------- correction
 template <typename real>
-__global__ void k_add_corr(real *__restrict__ F, int64_t N, const double *__restrict__ fcorr)
+__global__ void k_add_corr(real *__restrict__ F, const int2 *__restrict__ map,
+                           const Rep *__restrict__ reps, const double *__restrict__ scal, int slot)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    F[3 * i + 0] += (real)fcorr[0];
-    F[3 * i + 1] += (real)fcorr[1];
-    F[3 * i + 2] += (real)fcorr[2];
+    const AtomSlot sl = atom_slot(map, reps);
+    if (!sl.ok) return;
+    const double *fc = scal + (int64_t)sl.r * SCAL_COUNT + slot;
+    F[3 * sl.i + 0] += (real)fc[0];
+    F[3 * sl.i + 1] += (real)fc[1];
+    F[3 * sl.i + 2] += (real)fc[2];
 }
 
-// F_corr = -(1/N) sum_i (F_core + F_shell*) (Eq. 16, Algorithm 2 step 3) into
-// scal[slot..slot+2]; with apply, added to every atom of `force` (Algorithm 2
-// step 4).  The integrator keeps its correction in SCAL_FCORR and adds it in the
-// kicks instead of in a separate pass.
+// F_corr = -(1/N_r) sum_{i in r} (F_core + F_shell*) per replica (Eq. 16,
+// Algorithm 2 step 3) into its scalars [slot, slot + 3); with apply, added to
+// every atom of `force` (Algorithm 2 step 4).  The integrator keeps its
+// correction in SCAL_FCORR and adds it in the kicks instead of in a separate pass.
 rbmd_status rbl_correction(rbmd_ctx *c, void *force, bool apply, int slot)
 {
-    RBMD_CHECK(md_sum(c, c->fpart, c->pair_parts, 3, c->scal + slot, -1.0 / (double)c->N));
+    RBMD_CHECK(md_sum_replicas(c, c->fpart, 3, slot, -1.0, true, true));
     if (apply) {
-        const unsigned nb = (unsigned)((c->N + 255) / 256);
-        if (c->fp64) k_add_corr<double><<<nb, 256, 0, c->stream>>>((double *)force, c->N, c->scal + slot);
-        else k_add_corr<float><<<nb, 256, 0, c->stream>>>((float *)force, c->N, c->scal + slot);
+        if (c->fp64)
+            k_add_corr<double><<<c->nb256, 256, 0, c->stream>>>((double *)force, c->map256, c->reps,
+                                                                c->scal, slot);
+        else
+            k_add_corr<float><<<c->nb256, 256, 0, c->stream>>>((float *)force, c->map256, c->reps,
+                                                               c->scal, slot);
         RBMD_LAUNCH_CHECK();
     }
     return RBMD_OK;

@@ -33,6 +33,7 @@ constexpr double kTwo64 = 18446744073709551616.0;
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kPairBlock = 128;  // threads per block of the RBL pair kernel
 constexpr int RED_BLOCKS = 256;  // first-stage blocks of the long FP64 reductions
+constexpr int RED_SPLIT = 32;    // first-stage chunks per replica of the per-replica sums
 
 // Step number used by a kernel: (*ptr) + add when ptr is set (graph replays read
 // the device counter), else add.
@@ -77,7 +78,50 @@ __host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k)
 // Device error word: first error wins.
 __device__ __forceinline__ void latch_error(int *err, int code) { atomicCAS(err, 0, code); }
 
-template <typename real> struct Vec3Ptr;
+// Per-replica constants, on the device (array of R) and on the host.  A context
+// holds R >= 1 independent replicas concatenated: atoms [atom0, atom0 + N),
+// cells [cell0, cell0 + ncell), modes [r P, (r + 1) P), FP64 scalars
+// [r SCAL_COUNT, (r + 1) SCAL_COUNT).
+struct Rep {
+    double L, lscale, dtc, Wrbe, S, T0, e_self;
+    uint64_t Rc2, Rs2;
+    uint2 key;              // Philox key (seed)
+    uint32_t Rlin;          // floor(sqrt(Rs2)): per-axis early reject
+    uint32_t tag_rbe, tag_rbl;
+    int32_t nc, M;          // cells per axis, sampler half-width
+    float cull_r;           // r_cut in cell widths (+ margin)
+    int64_t atom0, N;
+    int64_t cell0, ncell;
+    int64_t cdf0;           // offset of the replica's sampler thresholds
+    int32_t b256_0, nb256;  // blocks of the 256-thread atom kernels
+    int32_t b128_0, nb128;  // blocks of the 128-thread atom kernels
+    int32_t tile0, ntiles;  // structure-factor atom tiles
+};
+
+// Atom handled by this thread in a replica-aligned launch: map[blockIdx.x] =
+// (replica, first atom of the block); blocks never straddle two replicas.
+struct AtomSlot {
+    int r;
+    int64_t i;
+    bool ok;
+};
+
+__device__ __forceinline__ AtomSlot atom_slot_at(const int2 *__restrict__ map,
+                                                 const Rep *__restrict__ reps, int b)
+{
+    const int2 m = map[b];
+    AtomSlot s;
+    s.r = m.x;
+    s.i = (int64_t)m.y + threadIdx.x;
+    s.ok = s.i < reps[m.x].atom0 + reps[m.x].N;
+    return s;
+}
+
+__device__ __forceinline__ AtomSlot atom_slot(const int2 *__restrict__ map,
+                                              const Rep *__restrict__ reps)
+{
+    return atom_slot_at(map, reps, blockIdx.x);
+}
 
 // Per-mode coefficients for the force pass (Eq. 12 expanded):
 //   F_i = q_i sum_l (A_l cos th - B_l sin th) k_l,  A = c rho_im, B = c rho_re,
@@ -98,15 +142,21 @@ struct rbmd_ctx {
     bool own_stream;      // created here because the caller passed the legacy stream
     cudaEvent_t ev_in, ev_out;
 
-    // derived constants
-    double L, V, S, H, sqrt_alpha, lscale, dtc, tau;
-    int32_t M;            // sampler half-width
-    uint64_t Rc2, Rs2;    // squared radii in fixed-point units
-    uint32_t Rlin;        // floor(sqrt(Rs2)): per-axis early reject
-    int32_t nc, div;      // cells per axis, cells per r_cut
-    int64_t ncell;
-    double e_self;        // -coulomb_k sqrt(alpha/pi) sum q^2
-    int64_t Pm;           // modes per evaluation (P or the full count)
+    // replicas
+    int32_t R;
+    rbmd::Rep *reps_h;    // [R] host copy
+    rbmd::Rep *reps;      // [R] device
+    int2 *map256;         // [nb256] replica-aligned blocks of 256 atoms
+    int2 *map128;         // [nb128] replica-aligned blocks of 128 atoms
+    int2 *tiles;          // [ntiles] structure-factor tiles (replica, first atom)
+    int nb256, nb128, ntiles;
+
+    // shared constants
+    double sqrt_alpha, tau;
+    int32_t div;          // cells per r_cut
+    int64_t ncell;        // all replicas
+    int64_t Pm;           // modes per replica per evaluation (P or the full count)
+    int64_t cdf_total;
     bool full_modes;
 
     // master state
@@ -116,22 +166,21 @@ struct rbmd_ctx {
     void *vel;
     void *force;          // internal force buffer for the integrator
     void *scratch_force;  // force buffer for energy evaluations
-    double *scal;         // [16] FP64 scalars, see SCAL_* below
+    double *scal;         // [R][SCAL_COUNT] FP64 scalars, see SCAL_* below
     double *red_tmp;      // [RED_BLOCKS][8] first stage of long reductions
+    double *red_rep;      // [R][RED_SPLIT][8] first stage of the per-replica sums
     int *err;
     int64_t *d_step;
 
     // RBE
-    uint64_t *cdf;        // [2M+1]
-    int4 *modes;          // [Pm]
-    double *W;            // [Pm] weights (full-mode list), else NULL
-    double2 *rho_part;    // [rho_tiles][Pm]
-    double2 *rho;         // [Pm]
-    double *emode;        // [Pm]
-    void *coef;           // ModeCoef<real>[Pm]
-    int rho_tile;         // atoms per structure-factor block
-    int rho_tiles;        // number of atom tiles
-    int force_block;      // threads per block of the force pass
+    uint64_t *cdf;        // sampler thresholds of every replica (2M_r + 1 each)
+    int4 *modes;          // [R][Pm]
+    double *W;            // [Pm] weights (full-mode list, one replica), else NULL
+    double2 *rho_part;    // [ntiles][Pm]
+    double2 *rho;         // [R][Pm]
+    double *emode;        // [R][Pm]
+    void *coef;           // ModeCoef<real>[R][Pm]
+    int rho_tile;         // atoms per structure-factor tile
 
     // RBL
     int32_t *cell_count;  // [ncell]
@@ -142,15 +191,13 @@ struct rbmd_ctx {
     uint4 *spos;          // [N]
     void *sq;             // real [N]
     int32_t *stype;       // [N]
-    double *fpart;        // [pair_blocks][3] force partial sums
-    double *epart;        // [pair_blocks][2] energy partial sums
-    double *kepart;       // [kick_blocks]
+    double *fpart;        // [pair_parts][3] force partial sums (per warp)
+    double *epart;        // [pair_parts][2] energy partial sums
+    double *kepart;       // [nb256]
     int32_t *ibuf;        // [4] integer diagnostics
     float *lj_f;          // [2*T] sqrt(eps), sigma/2 (FP32 path)
     double *lj_d;         // [2*T] (FP64 path)
-    int pair_block;
-    int pair_blocks;
-    int pair_parts;       // per-warp partial sums: pair kernel, then the fallback
+    int pair_parts;       // per-warp partial sums: pair kernel (4 nb128), then the fallback (4 nb128)
     int32_t *lcore;       // [N][list_cc] core lists (cell-sorted order)
     int32_t *lshell;      // [N][list_cs] shell lists
     int2 *ncount;         // [N] (|C|, N_s)
@@ -159,7 +206,6 @@ struct rbmd_ctx {
     void *adj_lj;         // real [2T]: eps_t, sigma_t (adjoint)
     double *adj_tpart;    // [adjoint blocks][2T]
     double *adj_tsum;     // [2T]
-    int kick_blocks;
 
     // integrator state
     int64_t step;
@@ -188,6 +234,7 @@ enum {
     SCAL_ELJ = 10,
     SCAL_KE_TRUE = 11,
     SCAL_FCORR_AUX = 12,  // [3] correction of stand-alone force calls
+    SCAL_ESELF = 15,      // self energy (kept on the device for batched read-out)
     SCAL_COUNT = 16
 };
 
@@ -226,9 +273,14 @@ rbmd_status md_kick_drift(rbmd_ctx *c);
 rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step);
 rbmd_status md_sum(rbmd_ctx *c, const double *parts, int nparts, int ncomp, double *out,
                    double scale);
+// Per replica r: out[r * SCAL_COUNT + slot + comp] = scale_r * (sum of the parts of
+// its 128-atom blocks, 4 per block, in pass 0 and, with two_segments, pass 1 at
+// offset 4 nb128).  scale_r = scale, or scale / N_r when per_atom.
+rbmd_status md_sum_replicas(rbmd_ctx *c, const double *parts, int ncomp, int slot, double scale,
+                            bool per_atom, bool two_segments);
 rbmd_status md_decode_state(rbmd_ctx *c, void *pos, void *vel);
 rbmd_status md_encode_positions(rbmd_ctx *c, const void *pos);
-rbmd_status md_kinetic(rbmd_ctx *c, double *out_dev);
+rbmd_status md_kinetic(rbmd_ctx *c, int slot);
 
 inline rbmd_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RBMD_OK : RBMD_ERR_CUDA; }
 

@@ -107,11 +107,17 @@ def maxwell_boltzmann(n: int, T0: float, rng) -> np.ndarray:
 
 def electrolyte(n: int, L: float | None = None, density: float = 0.2, seed: int = 0,
                 charges: str = "1:1", n_types: int = 1, sigma_range=(0.8, 1.2),
-                eps_range=(0.5, 1.5), dmin_factor: float = 0.8, T0: float = 1.0) -> System:
+                eps_range=(0.5, 1.5), dmin_factor: float = 0.8, T0: float = 1.0,
+                lj=None) -> System:
+    """lj: optional (eps, sigma) per type to use instead of drawing them."""
     rng = np.random.default_rng(seed)
     if L is None:
         L = box_length(n, density)
-    if n_types == 1:
+    if lj is not None:
+        eps = np.asarray(lj[0], dtype=np.float64)
+        sig = np.asarray(lj[1], dtype=np.float64)
+        n_types = len(eps)
+    elif n_types == 1:
         sig = np.ones(1)
         eps = np.ones(1)
     else:
@@ -162,3 +168,27 @@ def replica_sizes(n_rep: int = 64, lo: int = 2000, hi: int = 200_000, seed: int 
     rng = np.random.default_rng(seed)
     x = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_rep))
     return (2 * np.round(x / 2)).astype(np.int64)
+
+
+def replicas(sizes, seed: int = 4, density: float = 0.2, charges: str = "1:1",
+             n_types: int = 1, T0=1.0) -> list:
+    """Independent systems of the given sizes sharing one set of LJ parameters
+    (drawn from ``seed``); replica r is seeded with 1000 * seed + r + 1.  T0 may
+    be a scalar or one temperature per replica."""
+    base = electrolyte(max(int(n_types), 2) if n_types > 1 else 2, seed=seed, n_types=n_types,
+                       charges="1:1", dmin_factor=0.0)
+    T0s = list(T0) if np.ndim(T0) > 0 else [T0] * len(sizes)
+    return [electrolyte(int(n), density=density, seed=1000 * seed + r + 1, charges=charges,
+                        lj=(base.eps, base.sig), T0=T0s[r])
+            for r, n in enumerate(sizes)]
+
+
+def concat(systems) -> dict:
+    """The concatenated arrays of a batch of systems (replica order)."""
+    return dict(u=np.concatenate([s.u for s in systems]),
+                x=np.concatenate([s.x for s in systems]),
+                q=np.concatenate([s.q for s in systems]),
+                types=np.concatenate([s.types for s in systems]),
+                v=np.concatenate([s.v for s in systems]),
+                L=[s.L for s in systems], n=[s.n for s in systems],
+                eps=systems[0].eps, sig=systems[0].sig)

@@ -71,3 +71,31 @@ def test_init_rejects_bad_parameters_without_device():
     code = lib.rbmd_init(C.byref(p), rb._ptr(dummy), None, rb._ptr(dummy), None, rb._ptr(eps),
                          rb._ptr(eps), None, C.byref(h))
     assert code == 1
+
+
+def test_init_batch_rejects_mismatched_shared_parameters_without_device():
+    lib = rb.lib()
+    h = C.c_void_p()
+    eps = np.ones(1)
+    dummy = np.zeros(3)
+    prm = (rb.Params * 2)()
+    for r in range(2):
+        prm[r] = rb.Params(n_atoms=10 + r, n_types=1, rbe_P=10, box_length=10.0 + r, alpha=0.6,
+                           r_core=2.0, r_cut=3.5, rbl_p=10, seed=r, replica=r)
+    prm[1].alpha = 0.7  # shared fields must agree
+    code = lib.rbmd_init_batch(prm, 2, rb._ptr(dummy), None, rb._ptr(dummy), None,
+                               rb._ptr(eps), rb._ptr(eps), None, C.byref(h))
+    assert code == 1 and not h.value  # RBMD_ERR_INVALID, no context
+    prm[1].alpha = 0.6
+    prm[1].box_length = 6.0  # r_cut >= L/2 in replica 1 only
+    code = lib.rbmd_init_batch(prm, 2, rb._ptr(dummy), None, rb._ptr(dummy), None,
+                               rb._ptr(eps), rb._ptr(eps), None, C.byref(h))
+    assert code == 3  # RBMD_ERR_BOX_TOO_SMALL
+    prm[1].box_length = 11.0
+    prm[0].flags = prm[1].flags = 1  # full Ewald modes: one replica only
+    code = lib.rbmd_init_batch(prm, 2, rb._ptr(dummy), None, rb._ptr(dummy), None,
+                               rb._ptr(eps), rb._ptr(eps), None, C.byref(h))
+    assert code == 9  # RBMD_ERR_UNSUPPORTED
+    code = lib.rbmd_init_batch(prm, 0, rb._ptr(dummy), None, rb._ptr(dummy), None,
+                               rb._ptr(eps), rb._ptr(eps), None, C.byref(h))
+    assert code == 1
