@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tile shapes on workloads that autotune")
     ap.add_argument("--cpu-sample", type=int, default=400_000)
     ap.add_argument("--ref-sample", type=int, default=100_000)
     args = ap.parse_args()
@@ -86,7 +88,7 @@ WORKLOADS = {
     "c2": dict(n=100_000, charges="1:1", n_types=1, density=0.2, params={}),
     "c4": dict(n=10_000_000, charges="1:1", n_types=1, density=0.2, params=dict(rbe_P=500)),
     "c5": dict(n=None, replicas=64, n_lo=2000, n_hi=200_000, charges="1:1", n_types=1,
-               density=0.2, params=dict(rbe_P=100)),
+               density=0.2, params=dict(rbe_P=100), autotune=True),
     "lj001": dict(n=1_000_000, charges="none", n_types=1, density=0.01,
                   params=dict(r_core=2.5, r_cut=5.0, rbl_p=30, flags=4)),
     "el001": dict(n=100_000, charges="1:1", n_types=1, density=0.01,
@@ -395,6 +397,11 @@ def run_ours(args):
     ctx = make_ctx(system, rb.FP32, device)
     torch.cuda.synchronize()
     footprint = free0 - torch.cuda.mem_get_info(device)[0]
+    tiles = {"shape": ctx.tiles(), "autotuned": False}
+    if WORKLOADS[args.workload].get("autotune") and not args.no_autotune:
+        t0 = time.perf_counter()
+        tiles = {"shape": ctx.autotune(step=0), "autotuned": True,
+                 "tuning_s": round(time.perf_counter() - t0, 3)}
     clocks = Clocks(local)
     if dist:
         dist.barrier()
@@ -421,6 +428,7 @@ def run_ours(args):
     fp64 = None
     if not args.skip_fp64:
         c64 = make_ctx(system, rb.FP64, device)
+        c64.set_tiles(*tiles["shape"])
         ms64, st64 = time_steps(c64, args.fp64_steps, 2, flush, profile=True)
         c64.close()
         m64 = sum(ms64) / len(ms64)
@@ -442,6 +450,7 @@ def run_ours(args):
         "gpu_launches": kernels_per_step * args.steps,
         "device_memory_bytes": int(footprint),
         "kernels_per_step": kernels_per_step,
+        "tiles": dict(tiles, names=["cell_div", "rho_tile", "rho_mode_tile"]),
     }
     if fp64:
         out["fp64"] = fp64

@@ -166,6 +166,32 @@ rbmd_status rbmd_init_batch(const rbmd_params *params, int32_t R, const void *po
 /* Number of replicas of the context (1 for rbmd_init), 0 for NULL. */
 int32_t rbmd_replica_count(rbmd_ctx *ctx);
 
+/*
+ * Tile shapes of the hot kernels (the paper has no counterpart: these are
+ * implementation choices of this library, with no effect on the integer work).
+ *   cell_div       cells per r_cut along each axis, 1 or 2 (binning and the
+ *                  neighbour stencil, Sec. 2.3).  Lists and batches are the same
+ *                  sets for both; only the order in which pairs are summed changes.
+ *   rho_tile       atoms per structure-factor block, 512, 1024 or 2048.
+ *   rho_mode_tile  modes per structure-factor block, 64, 128 or 256.
+ * The tile shape only changes the FP rounding order of rho(k) (results stay
+ * within the precision's tolerance).  Defaults: cell_div from the parameters (2
+ * when 0), 1024, 256.
+ * rbmd_set_tiles  sets them (INVALID for other values).  Synchronises.
+ * rbmd_get_tiles  out: host int32 [3] = cell_div, rho_tile, rho_mode_tile.
+ * rbmd_autotune   times the RBL part for each cell_div and the structure factors
+ *                 for each (rho_tile, rho_mode_tile) on the current state with the
+ *                 draws of `step`, after one untimed run, 3 timed runs each, and
+ *                 keeps the fastest; chosen (host int32 [3], or NULL) receives
+ *                 them.  Synchronises.  A batch context tunes once for all
+ *                 replicas.  Scratch force buffers are overwritten; the state
+ *                 (positions, velocities, step counter) is not changed.
+ */
+rbmd_status rbmd_set_tiles(rbmd_ctx *ctx, int32_t cell_div, int32_t rho_tile,
+                           int32_t rho_mode_tile);
+rbmd_status rbmd_get_tiles(rbmd_ctx *ctx, int32_t *out);
+rbmd_status rbmd_autotune(rbmd_ctx *ctx, int64_t step, int32_t *chosen);
+
 /* Free every device buffer of the context (waits for its stream). NULL is a no-op. */
 void rbmd_destroy(rbmd_ctx *ctx);
 

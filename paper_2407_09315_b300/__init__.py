@@ -71,6 +71,9 @@ def lib():
         "rbmd_init": ([C.POINTER(Params), P, P, P, P, P, P, P, C.POINTER(P)], C.c_int),
         "rbmd_init_batch": ([C.POINTER(Params), i32, P, P, P, P, P, P, P, C.POINTER(P)], C.c_int),
         "rbmd_replica_count": ([P], i32),
+        "rbmd_set_tiles": ([P, i32, i32, i32], C.c_int),
+        "rbmd_get_tiles": ([P, P], C.c_int),
+        "rbmd_autotune": ([P, i64, P], C.c_int),
         "rbmd_energy_batch": ([P, i64, C.POINTER(EnergyTerms)], C.c_int),
         "rbmd_destroy": ([P], None),
         "rbmd_rbe_forces": ([P, i64, P, C.c_int], C.c_int),
@@ -350,6 +353,21 @@ class RBMD:
         n = C.c_int64(0)
         _check(lib().rbmd_profile_read(self._h, _ptr(ms), C.byref(n), int(reset)), "profile_read")
         return dict(zip(self.PROFILE_STAGES, ms.tolist())), n.value
+
+    def set_tiles(self, cell_div, rho_tile, rho_mode_tile):
+        _check(lib().rbmd_set_tiles(self._h, cell_div, rho_tile, rho_mode_tile), "set_tiles")
+
+    def tiles(self):
+        """(cell_div, rho_tile, rho_mode_tile) in use."""
+        out = np.zeros(3, dtype=np.int32)
+        _check(lib().rbmd_get_tiles(self._h, _ptr(out)), "get_tiles")
+        return tuple(int(x) for x in out)
+
+    def autotune(self, step=0):
+        """Time the tile-shape candidates on the current state and keep the fastest."""
+        out = np.zeros(3, dtype=np.int32)
+        _check(lib().rbmd_autotune(self._h, step, _ptr(out)), "autotune")
+        return tuple(int(x) for x in out)
 
     def step_kernel_count(self) -> int:
         return lib().rbmd_step_kernel_count(self._h)

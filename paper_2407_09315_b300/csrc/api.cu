@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "rbmd_internal.cuh"
@@ -271,6 +272,49 @@ __global__ void k_sum_charges(const double *__restrict__ parts, const Rep *__res
         for (int k = 0; k < 3; ++k) out[3 * (int64_t)blockIdx.x + k] = s[k][0];
 }
 
+// Cells of every replica for `div` cells per r_cut (Sec. 2.3 binning): the side
+// is at least r_cut / div, and the count is capped so that sparse boxes do not
+// get more cells than atoms (bigger cells stay correct: the stencil still covers
+// r_cut).  Returns the total; with apply, stores nc, the culling radius and the
+// cell ranges in the host replica table.
+int64_t cell_layout(rbmd_ctx *c, double r_cut, int div, bool apply)
+{
+    int64_t cell0 = 0;
+    for (int r = 0; r < c->R; ++r) {
+        Rep &rp = c->reps_h[r];
+        int nc = (int)floor(rp.L * div / r_cut);
+        if (nc < 1) nc = 1;
+        while (nc > 1 && (double)rp.Rlin * (double)nc > (double)div * kTwo32) --nc;
+        const double max_cells = fmax(8.0 * (double)rp.N, 1048576.0);
+        while (nc > 1 && (double)nc * nc * nc > max_cells) --nc;
+        if (apply) {
+            rp.nc = nc;
+            rp.cull_r = (float)(r_cut * nc / rp.L * (1.0 + 1e-5) + 1e-6);
+            rp.cell0 = cell0;
+            rp.ncell = (int64_t)nc * nc * nc;
+        }
+        cell0 += (int64_t)nc * nc * nc;
+    }
+    return cell0;
+}
+
+// Structure-factor tiles of `tile` atoms that never straddle replicas; returns
+// their count and, with apply, fills the map and the replicas' tile ranges.
+int tile_layout(rbmd_ctx *c, int tile, bool apply, std::vector<int2> &tl)
+{
+    tl.clear();
+    for (int r = 0; r < c->R; ++r) {
+        Rep &rp = c->reps_h[r];
+        const int t0 = (int)tl.size();
+        for (int64_t a = 0; a < rp.N; a += tile) tl.push_back(make_int2(r, (int)(rp.atom0 + a)));
+        if (apply) {
+            rp.tile0 = t0;
+            rp.ntiles = (int32_t)tl.size() - t0;
+        }
+    }
+    return (int)tl.size();
+}
+
 // Neutrality of every replica (Sec. 2.2, when check_neutral) and its self energy
 // -coulomb_k sqrt(alpha/pi) sum q^2 (third term of Eq. 8).  Synchronises.
 rbmd_status charge_sums(rbmd_ctx *c, bool check_neutral = true)
@@ -434,6 +478,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     c->full_modes = (p.flags & RBMD_FULL_EWALD_MODES) != 0;
     c->div = p.cell_div == 0 ? 2 : p.cell_div;
     c->rho_tile = 1024;
+    c->rho_mode_tile = 256;
     c->reps_h = new Rep[R];
     memset(c->reps_h, 0, sizeof(Rep) * R);
 
@@ -462,7 +507,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     std::vector<uint64_t> T;
     std::vector<int2> m256, m128, tl;
     double max_mc = 0.0, max_ms = 0.0;
-    int64_t atom0 = 0, cell0 = 0;
+    int64_t atom0 = 0;
     for (int r = 0; r < R; ++r) {
         const rbmd_params &q = prms[r];
         Rep &rp = c->reps_h[r];
@@ -485,40 +530,28 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
         rp.Rc2 = radius2_units(p.r_core, rp.L);
         rp.Rs2 = radius2_units(p.r_cut, rp.L);
         rp.Rlin = isqrt64(rp.Rs2);
-        int nc = (int)floor(rp.L * c->div / p.r_cut);
-        if (nc < 1) nc = 1;
-        while (nc > 1 && (double)rp.Rlin * (double)nc > (double)c->div * kTwo32) --nc;
-        // bigger cells stay correct (the stencil still covers r_cut); cap the
-        // cell count so that sparse boxes do not allocate more cells than atoms
-        const double max_cells = fmax(8.0 * (double)q.n_atoms, 1048576.0);
-        while (nc > 1 && (double)nc * nc * nc > max_cells) --nc;
-        rp.nc = nc;
-        rp.cull_r = (float)(p.r_cut * nc / rp.L * (1.0 + 1e-5) + 1e-6);
         rp.atom0 = atom0;
         rp.N = q.n_atoms;
-        rp.cell0 = cell0;
-        rp.ncell = (int64_t)nc * nc * nc;
         rp.b256_0 = (int32_t)m256.size();
         for (int64_t a = 0; a < rp.N; a += 256) m256.push_back(make_int2(r, (int)(atom0 + a)));
         rp.nb256 = (int32_t)m256.size() - rp.b256_0;
         rp.b128_0 = (int32_t)m128.size();
         for (int64_t a = 0; a < rp.N; a += 128) m128.push_back(make_int2(r, (int)(atom0 + a)));
         rp.nb128 = (int32_t)m128.size() - rp.b128_0;
-        rp.tile0 = (int32_t)tl.size();
-        for (int64_t a = 0; a < rp.N; a += c->rho_tile) tl.push_back(make_int2(r, (int)(atom0 + a)));
-        rp.ntiles = (int32_t)tl.size() - rp.tile0;
         atom0 += rp.N;
-        cell0 += rp.ncell;
         const double n = (double)rp.N / (rp.L * rp.L * rp.L);
         const double mc = n * 4.0 / 3.0 * kPi * p.r_core * p.r_core * p.r_core;
         max_mc = fmax(max_mc, mc);
         max_ms = fmax(max_ms, n * 4.0 / 3.0 * kPi * (p.r_cut * p.r_cut * p.r_cut) - mc);
     }
-    c->ncell = cell0;
+    // cell arrays and tile partials sized for every layout rbmd_set_tiles allows
+    c->ncell_max = std::max(cell_layout(c, p.r_cut, 1, false), cell_layout(c, p.r_cut, 2, false));
+    c->ntiles_max = tile_layout(c, 512, false, tl);
+    c->ncell = cell_layout(c, p.r_cut, c->div, true);
+    c->ntiles = tile_layout(c, c->rho_tile, true, tl);
     c->cdf_total = (int64_t)T.size();
     c->nb256 = (int)m256.size();
     c->nb128 = (int)m128.size();
-    c->ntiles = (int)tl.size();
     c->pair_parts = 2 * 4 * c->nb128;  // per warp: pair kernel, then the fallback
     // list capacities: mean + 8 sd + 8 of a uniform fluid at the densest
     // replica's density, rounded up to a multiple of 4; atoms beyond them take
@@ -558,7 +591,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(alloc_n(&c->reps, (size_t)R));
     TRY(alloc_n(&c->map256, (size_t)c->nb256));
     TRY(alloc_n(&c->map128, (size_t)c->nb128));
-    TRY(alloc_n(&c->tiles, (size_t)c->ntiles));
+    TRY(alloc_n(&c->tiles, (size_t)c->ntiles_max));
     TRY(alloc_n(&c->u4, N));
     if (c->fp64) TRY(alloc_n(&c->q64, N));
     TRY(alloc_n(&c->type, N));
@@ -573,15 +606,15 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(alloc_n(&c->cdf, T.size()));
     TRY(alloc_n(&c->modes, (size_t)R * c->Pm));
     if (c->full_modes) TRY(alloc_n(&c->W, c->Pm));
-    TRY(alloc_n(&c->rho_part, (size_t)c->ntiles * c->Pm));
+    TRY(alloc_n(&c->rho_part, (size_t)c->ntiles_max * c->Pm));
     TRY(alloc_n(&c->rho, (size_t)R * c->Pm));
     TRY(alloc_n(&c->emode, (size_t)R * c->Pm));
     TRY(dev_alloc(&c->coef, (size_t)R * c->Pm * (c->fp64 ? sizeof(ModeCoef<double>) : sizeof(ModeCoef<float>))));
-    TRY(alloc_n(&c->cell_count, c->ncell));
-    TRY(alloc_n(&c->cell_start, c->ncell + 1));
+    TRY(alloc_n(&c->cell_count, c->ncell_max));
+    TRY(alloc_n(&c->cell_start, c->ncell_max + 1));
     TRY(alloc_n(&c->cell_of, N));
     TRY(alloc_n(&c->cell_rank, N));
-    TRY(alloc_n(&c->scan_part, (c->ncell + 1023) / 1024 + 1));
+    TRY(alloc_n(&c->scan_part, (c->ncell_max + 1023) / 1024 + 1));
     TRY(alloc_n(&c->spos, N));
     TRY(dev_alloc(&c->sq, N * rs));
     TRY(alloc_n(&c->stype, N));
@@ -602,6 +635,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     if (c->fp64) TRY(alloc_n(&c->lj_d, 2 * c->T));
     else TRY(alloc_n(&c->lj_f, 2 * c->T));
     TRY(upload_lj(c, lj_eps, lj_sigma));
+    TRY(rbe_configure(c));
     TRY(cuda_status(cudaMemcpy(c->reps, c->reps_h, sizeof(Rep) * R, cudaMemcpyHostToDevice)));
     TRY(cuda_status(cudaMemcpy(c->map256, m256.data(), sizeof(int2) * m256.size(), cudaMemcpyHostToDevice)));
     TRY(cuda_status(cudaMemcpy(c->map128, m128.data(), sizeof(int2) * m128.size(), cudaMemcpyHostToDevice)));
@@ -836,6 +870,105 @@ rbmd_status rbmd_energy(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
 }
 
 int32_t rbmd_replica_count(rbmd_ctx *c) { return c ? c->R : 0; }
+
+rbmd_status rbmd_set_tiles(rbmd_ctx *c, int32_t cell_div, int32_t rho_tile, int32_t rho_mode_tile)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    if (cell_div != 1 && cell_div != 2) return RBMD_ERR_INVALID;
+    if (rho_tile != 512 && rho_tile != 1024 && rho_tile != 2048) return RBMD_ERR_INVALID;
+    if (rho_mode_tile != 64 && rho_mode_tile != 128 && rho_mode_tile != 256) return RBMD_ERR_INVALID;
+    RBMD_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<int2> tl;
+    c->ncell = cell_layout(c, c->prm.r_cut, cell_div, true);
+    c->ntiles = tile_layout(c, rho_tile, true, tl);
+    c->div = cell_div;
+    c->rho_tile = rho_tile;
+    c->rho_mode_tile = rho_mode_tile;
+    RBMD_CHECK_CUDA(cudaMemcpy(c->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice));
+    RBMD_CHECK_CUDA(cudaMemcpy(c->reps, c->reps_h, sizeof(Rep) * c->R, cudaMemcpyHostToDevice));
+    if (c->graph_ready) {  // the step graph holds the old grids
+        cudaGraphExecDestroy(c->graph);
+        c->graph_ready = false;
+    }
+    return RBMD_OK;
+}
+
+rbmd_status rbmd_get_tiles(rbmd_ctx *c, int32_t *out)
+{
+    if (!c || !out) return RBMD_ERR_INVALID;
+    out[0] = c->div;
+    out[1] = c->rho_tile;
+    out[2] = c->rho_mode_tile;
+    return RBMD_OK;
+}
+
+// Times `reps` runs of the RBL part (div only changes the cells) or the
+// structure factors (the tile shape only changes those), after one untimed run.
+static rbmd_status tune_time(rbmd_ctx *c, bool rbl, StepRef s, int reps, float *ms)
+{
+    cudaEvent_t e0, e1;
+    RBMD_CHECK_CUDA(cudaEventCreate(&e0));
+    RBMD_CHECK_CUDA(cudaEventCreate(&e1));
+    rbmd_status st = RBMD_OK;
+    for (int k = 0; k <= reps && st == RBMD_OK; ++k) {
+        if (k == 1) cudaEventRecord(e0, c->stream);
+        if (rbl) {
+            st = cells_build(c);
+            if (st == RBMD_OK) st = rbl_pairs(c, s, c->scratch_force, 0, false, nullptr, nullptr, nullptr);
+        } else {
+            st = rbe_sample(c, s);
+            if (st == RBMD_OK) st = rbe_structure_factors(c);
+        }
+    }
+    cudaEventRecord(e1, c->stream);
+    if (st == RBMD_OK) st = cuda_status(cudaEventSynchronize(e1));
+    if (st == RBMD_OK) st = cuda_status(cudaEventElapsedTime(ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+rbmd_status rbmd_autotune(rbmd_ctx *c, int64_t step, int32_t *chosen)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    enter(c);
+    const StepRef s{nullptr, step};
+    const int reps = 3;
+    int best_div = c->div, best_tile = c->rho_tile, best_mt = c->rho_mode_tile;
+    rbmd_status st = RBMD_OK;
+    if (!(c->prm.flags & RBMD_NO_RBL)) {
+        float best = 1e30f;
+        for (int div = 1; div <= 2 && st == RBMD_OK; ++div) {
+            float ms = 0.f;
+            st = rbmd_set_tiles(c, div, best_tile, best_mt);
+            if (st == RBMD_OK) st = tune_time(c, true, s, reps, &ms);
+            if (st == RBMD_OK && ms < best) {
+                best = ms;
+                best_div = div;
+            }
+        }
+    }
+    if (!(c->prm.flags & RBMD_NO_RBE)) {
+        float best = 1e30f;
+        const int tiles[3] = {512, 1024, 2048}, mts[3] = {64, 128, 256};
+        for (int a = 0; a < 3 && st == RBMD_OK; ++a)
+            for (int b = 0; b < 3 && st == RBMD_OK; ++b) {
+                float ms = 0.f;
+                st = rbmd_set_tiles(c, best_div, tiles[a], mts[b]);
+                if (st == RBMD_OK) st = tune_time(c, false, s, reps, &ms);
+                if (st == RBMD_OK && ms < best) {
+                    best = ms;
+                    best_tile = tiles[a];
+                    best_mt = mts[b];
+                }
+            }
+    }
+    if (st == RBMD_OK) st = rbmd_set_tiles(c, best_div, best_tile, best_mt);
+    if (st == RBMD_OK && chosen) st = rbmd_get_tiles(c, chosen);
+    st = leave(c, st);
+    if (st != RBMD_OK) return st;
+    return check_latched(c);
+}
 
 rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, void *d_pos, void *d_q,
                                  double *d_eps, double *d_sigma)

@@ -259,17 +259,34 @@ __global__ void k_rho_final(const double2 *__restrict__ part, const Rep *__restr
     coef[l] = mc;
 }
 
+// Dynamic shared memory of k_rho_partial for a tile shape.
+static size_t rho_smem(bool fp64, int tile, int mode_tile, int sub)
+{
+    return (size_t)tile * sizeof(uint4) + (fp64 ? (size_t)tile * sizeof(double) : 0) +
+           (size_t)mode_tile * sizeof(int4) + (size_t)mode_tile * sub * sizeof(double2);
+}
+
+rbmd_status rbe_configure(rbmd_ctx *c)
+{
+    // the largest tile shape (2048 atoms, 256 modes x 4 sub-tiles) needs 68 KB in FP64
+    const int bytes = (int)rho_smem(true, 2048, 256, 4);
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rho_partial<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rho_partial<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return RBMD_OK;
+}
+
 rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
 {
     const int tile = c->rho_tile;
-    const int mode_tile = (int)(c->Pm < 256 ? c->Pm : 256);
+    const int mode_tile = (int)(c->Pm < c->rho_mode_tile ? c->Pm : c->rho_mode_tile);
     int sub = max(1, 1024 / mode_tile);
     sub = min(sub, tile);
     int threads = ((mode_tile * sub + 31) / 32) * 32;
     threads = min(threads, 1024);
     dim3 grid((unsigned)c->ntiles, (unsigned)((c->Pm + mode_tile - 1) / mode_tile));
-    size_t smem = (size_t)tile * sizeof(uint4) + (c->fp64 ? (size_t)tile * sizeof(double) : 0) +
-                  (size_t)mode_tile * sizeof(int4) + (size_t)mode_tile * sub * sizeof(double2);
+    const size_t smem = rho_smem(c->fp64, tile, mode_tile, sub);
     const unsigned fin_blocks = (unsigned)((c->R * c->Pm * 32 + 255) / 256);
     if (c->fp64) {
         k_rho_partial<double><<<grid, threads, smem, c->stream>>>(

@@ -180,7 +180,10 @@ struct rbmd_ctx {
     double2 *rho;         // [R][Pm]
     double *emode;        // [R][Pm]
     void *coef;           // ModeCoef<real>[R][Pm]
-    int rho_tile;         // atoms per structure-factor tile
+    int rho_tile;         // atoms per structure-factor tile (512, 1024 or 2048)
+    int rho_mode_tile;    // modes per structure-factor block (64, 128 or 256)
+    int ntiles_max;       // tiles at the smallest tile size (rho_part capacity)
+    int64_t ncell_max;    // cells at the finest cell division (cell array capacity)
 
     // RBL
     int32_t *cell_count;  // [ncell]
@@ -254,6 +257,7 @@ rbmd_status sampler_table_host(double L, double alpha, int32_t *M, uint64_t *T, 
 // RBE (rbe.cu)
 rbmd_status rbe_sample(rbmd_ctx *c, StepRef s);
 rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between = -1);
+rbmd_status rbe_configure(rbmd_ctx *c);  // kernel attributes (dynamic shared memory)
 rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate);
 
 // RBL (rbl.cu)
