@@ -41,7 +41,8 @@ template <typename real> struct AdjArgs {
     const uint4 *spos;
     const real *sq;
     const int32_t *stype;
-    const int32_t *lcore, *lshell, *bk;
+    const int32_t *lcore, *lshell, *bk;  // per-atom lists, entry e of atom i at lidx(i, e, N, cap)
+    const int32_t *sidx;                 // sorted index of every atom (by global id)
     const int2 *ncount;
     int64_t N;
     int CC, CS, p, T, exact;
@@ -79,23 +80,24 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
         const int2 cnt = a.ncount[ks];
         const int nbk = min(cnt.y, a.p);
         const real wk = cnt.y > a.p ? (real)cnt.y / (real)a.p : (real)1;
-        const int32_t *bk_k = a.bk + ks * a.p;
+        const int64_t N = a.N;
+        const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
         real gx = 0, gy = 0, gz = 0, gq = 0;
         const int ntot = cnt.x + cnt.y;
         for (int e = 0; e < ntot; ++e) {
             const bool core = e < cnt.x;
-            const int js = core ? a.lcore[ks * a.CC + e] : a.lshell[ks * a.CS + (e - cnt.x)];
+            const int js = core ? a.lcore[lidx(ks, e, N, a.CC)]
+                                : a.sidx[id0 + (uint32_t)a.lshell[lidx(ks, e - cnt.x, N, a.CS)]];
             real Wkj = 1, Wjk = 1;
             if (!core && !a.exact) {
                 Wkj = 0;
                 for (int b = 0; b < nbk; ++b)
-                    if (bk_k[b] == js) Wkj = wk;
+                    if (a.bk[lidx(ks, b, N, a.p)] == js) Wkj = wk;
                 const int2 cj = a.ncount[js];
                 const int nbj = min(cj.y, a.p);
                 Wjk = 0;
-                const int32_t *bk_j = a.bk + (int64_t)js * a.p;
                 for (int b = 0; b < nbj; ++b)
-                    if (bk_j[b] == (int32_t)ks) Wjk = cj.y > a.p ? (real)cj.y / (real)a.p : (real)1;
+                    if (a.bk[lidx(js, b, N, a.p)] == (int32_t)ks) Wjk = cj.y > a.p ? (real)cj.y / (real)a.p : (real)1;
             }
             const real W = (real)0.5 * (Wkj + Wjk);
             if (W == (real)0 && Wkj == (real)0) continue;
@@ -223,6 +225,7 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
         a.stype = c->stype;
         a.lcore = c->lcore;
         a.lshell = c->lshell;
+        a.sidx = c->cell_rank;
         a.bk = c->bk;
         a.ncount = c->ncount;
         a.N = c->N;

@@ -128,10 +128,11 @@ __global__ void k_cell_scatter(const uint4 *__restrict__ u4, const double *__res
 
 // Atomic ranks make the order inside a cell arbitrary; restore atom-id order so
 // that every later floating-point sum runs in a fixed order.
+// Then record the sorted index of every atom (sidx[id] = position in spos).
 template <typename real>
 __global__ void k_cell_order(const int32_t *__restrict__ start, int64_t ncell,
                              uint4 *__restrict__ spos, real *__restrict__ sq,
-                             int32_t *__restrict__ stype)
+                             int32_t *__restrict__ stype, int32_t *__restrict__ sidx)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -151,6 +152,7 @@ __global__ void k_cell_order(const int32_t *__restrict__ start, int64_t ncell,
         sq[k + 1] = q;
         stype[k + 1] = t;
     }
+    for (int a = b; a < e; ++a) sidx[spos[a].w] = a;
 }
 
 rbmd_status cells_build(rbmd_ctx *c)
@@ -176,14 +178,14 @@ rbmd_status cells_build(rbmd_ctx *c)
                                                          (double *)c->sq, c->stype);
         RBMD_LAUNCH_CHECK();
         k_cell_order<double><<<ncb, th, 0, c->stream>>>(c->cell_start, c->ncell, c->spos,
-                                                        (double *)c->sq, c->stype);
+                                                        (double *)c->sq, c->stype, c->cell_rank);
     } else {
         k_cell_scatter<float><<<nb, th, 0, c->stream>>>(c->u4, nullptr, c->type, c->N, c->cell_of,
                                                         c->cell_rank, c->cell_start, c->spos,
                                                         (float *)c->sq, c->stype);
         RBMD_LAUNCH_CHECK();
         k_cell_order<float><<<ncb, th, 0, c->stream>>>(c->cell_start, c->ncell, c->spos,
-                                                       (float *)c->sq, c->stype);
+                                                       (float *)c->sq, c->stype, c->cell_rank);
     }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
@@ -195,10 +197,11 @@ rbmd_status cells_build(rbmd_ctx *c)
 // each stays small and runs at high occupancy (the short-range step is bound by
 // memory latency and dependent integer chains, not by arithmetic throughput):
 //   k_rbl_scan    step 1: classify every candidate of the neighbour cells and
-//                 store the core and shell lists (sorted indices, capacity CC and
-//                 CS per atom); the counts are exact even when a list is full;
+//                 store the core list (sorted indices) and the shell list (atom
+//                 ids), capacity CC and CS per atom; the counts are exact even
+//                 when a list is full;
 //   k_rbl_select  step 1: Philox priorities of the shell members and the
-//                 bottom-p batch;
+//                 bottom-p batch (sorted indices);
 //   k_rbl_force   step 2: core forces plus the batch forces weighted N_s/p, and
 //                 per-warp FP64 partial sums for F_corr (step 3).
 // An atom whose lists overflowed is skipped by select and force and handled
@@ -224,11 +227,12 @@ template <typename real> struct PairArgs {
     int64_t fb_part0;  // first partial slot of the fallback kernel
     int32_t *imax;     // [0] max N_s
     int32_t *n_core, *n_shell, *batch;  // verification outputs (caller order) or NULL
-    // lists (cell-sorted order)
-    int32_t *lcore;    // [N][CC]
-    int32_t *lshell;   // [N][CS]
+    // per-atom lists; entry e of sorted atom i is at lidx(i, e, N, capacity)
+    int32_t *lcore;    // [N][CC] sorted indices of the core members
+    int32_t *lshell;   // [N][CS] replica-local atom ids of the shell members
     int2 *ncount;      // [N] (|C|, N_s)
     int32_t *bk;       // [N][p] sorted indices of the batch
+    const int32_t *sidx;  // [N] sorted index of every atom (by global id)
     int32_t *ovf;      // [0] set when any list overflowed
     int CC, CS;
 };
@@ -331,18 +335,16 @@ constexpr int SEL_NEG = -2;  // slot marker: minus infinity
 constexpr int SEL_POS = -1;  // slot marker: plus infinity (empty)
 
 struct SelCtx {
-    const uint4 *spos;
     Philox0 r0;
     uint2 key;
-    uint32_t id0;  // first atom of the replica: Philox counters use replica-local ids
 };
 
-// true if slot (sorted index hk) orders before the candidate with local id `id`.
+// true if slot (replica-local atom id hk) orders before the candidate `id`.
 __device__ __noinline__ bool sel_slot_before(const SelCtx &s, int hk, uint32_t id)
 {
     if (hk == SEL_NEG) return true;
     if (hk == SEL_POS) return false;
-    const uint32_t hid = s.spos[hk].w - s.id0;
+    const uint32_t hid = (uint32_t)hk;
     const uint2 pa = philox_rest(s.r0, hid, s.key), pb = philox_rest(s.r0, id, s.key);
     if (pa.x != pb.x) return pa.x < pb.x;
     if (pa.y != pb.y) return pa.y < pb.y;
@@ -501,8 +503,8 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
     const int64_t is = sl.i;
     const Rep rp = a.reps[sl.r];  // by value: the fields live in registers
     const uint4 A = a.spos[is];
-    int32_t *lc = a.lcore + is * a.CC;
-    int32_t *ls = a.lshell + is * a.CS;
+    const uint32_t id0 = (uint32_t)rp.atom0;
+    const int64_t N = a.N;
     int ncore = 0, ns = 0;
     stencil_ranges(a, rp, A, [&](int kb, int ke) {
         for (int k = kb; k < ke; k += 4) {
@@ -513,10 +515,10 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
             for (int q = 0; q < 4; ++q) {
                 const int c = (k + q < ke && k + q != (int)is) ? classify(rp, A, B[q]) : 0;
                 if (c == 1) {
-                    if (ncore < a.CC) lc[ncore] = k + q;
+                    if (ncore < a.CC) a.lcore[lidx(is, ncore, N, a.CC)] = k + q;
                     ++ncore;
                 } else if (c == 2) {
-                    if (ns < a.CS) ls[ns] = k + q;
+                    if (ns < a.CS) a.lshell[lidx(is, ns, N, a.CS)] = (int32_t)(B[q].w - id0);
                     ++ns;
                 }
             }
@@ -536,6 +538,8 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
 
 // Step 1b: the batch B(i), the p shell members with the smallest Philox priority
 // (all of them when N_s <= p), as sorted indices in bk[i][0..min(N_s,p)).
+// The shell list holds atom ids, so a priority needs one list load and no
+// lookup; only the p winners are mapped to sorted indices.
 template <typename real, int CAP, bool LISTS>
 __global__ void __launch_bounds__(256, (CAP <= 10 ? 3 : 1)) k_rbl_select(PairArgs<real> a)
 {
@@ -547,36 +551,43 @@ __global__ void __launch_bounds__(256, (CAP <= 10 ? 3 : 1)) k_rbl_select(PairArg
     const int2 cnt = a.ncount[is];
     if (overflowed(a, cnt)) return;
     const int ns = cnt.y;
-    const int32_t *ls = a.lshell + is * a.CS;
-    int32_t *bk = a.bk + is * a.p;
+    const int64_t N = a.N;
     const uint32_t id_i = a.spos[is].w;
+    int32_t ids[CAP];
     int nb = 0;
     if (ns <= a.p) {
-        for (int e = 0; e < ns; ++e) bk[e] = ls[e];
+        for (int e = 0; e < ns; ++e) {
+            const int32_t id = a.lshell[lidx(is, e, N, a.CS)];
+            if constexpr (LISTS) ids[e < CAP ? e : 0] = id;
+            a.bk[lidx(is, e, N, a.p)] = a.sidx[id0 + (uint32_t)id];
+        }
         nb = ns;
     } else {
-        const SelCtx sel{a.spos,
-                         philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key),
-                         rp.key, id0};
+        const SelCtx sel{
+            philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key), rp.key};
         uint32_t hh[CAP];
         int hk[CAP];
         sel_init<CAP>(hh, hk, a.p);
+        const int32_t *ls = a.lshell + lidx(is, 0, N, a.CS);
         for (int e = 0; e < ns; ++e) {
-            const int k = ls[e];
-            const uint32_t id = a.spos[k].w - id0;
+            const uint32_t id = (uint32_t)ls[e];
             const uint2 w = philox_rest(sel.r0, id, rp.key);
-            sel_insert<CAP>(hh, hk, w.x, k, id, sel);
+            sel_insert<CAP>(hh, hk, w.x, (int)id, id, sel);
         }
 #pragma unroll
         for (int e = 0; e < CAP; ++e)
-            if (hk[e] >= 0) bk[nb++] = hk[e];
+            if (hk[e] >= 0) {
+                if constexpr (LISTS) ids[nb] = hk[e];
+                a.bk[lidx(is, nb, N, a.p)] = a.sidx[id0 + (uint32_t)hk[e]];
+                ++nb;
+            }
     }
     if constexpr (LISTS) {
         // batch ids ascending, -1 padded (verification path only)
         int32_t *out = a.batch + (int64_t)id_i * a.p;
         for (int e = 0; e < a.p; ++e) out[e] = -1;
         for (int e = 0; e < nb; ++e) {
-            const int32_t v = (int32_t)a.spos[bk[e]].w;
+            const int32_t v = (int32_t)(ids[e] + id0);
             int y = e - 1;
             while (y >= 0 && out[y] > v) {
                 out[y + 1] = out[y];
@@ -608,19 +619,22 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
             const int ti = a.stype[is];
             I.se = s_lj[ti];
             I.hs = s_lj[a.T + ti];
-            const int32_t *lc = a.lcore + is * a.CC;
-            for (int e = 0; e < cnt.x; ++e) eval_k<real, ENERGY>(a, s_lj, I, lc[e], fx, fy, fz, ec, el);
+            const int64_t N = a.N;
+            for (int e = 0; e < cnt.x; ++e)
+                eval_k<real, ENERGY>(a, s_lj, I, a.lcore[lidx(is, e, N, a.CC)], fx, fy, fz, ec, el);
             if (a.exact) {
-                const int32_t *ls = a.lshell + is * a.CS;
+                const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
                 for (int e = 0; e < cnt.y; ++e)
-                    eval_k<real, ENERGY>(a, s_lj, I, ls[e], fx, fy, fz, ec, el);
+                    eval_k<real, ENERGY>(a, s_lj, I,
+                                         a.sidx[id0 + (uint32_t)a.lshell[lidx(is, e, N, a.CS)]],
+                                         fx, fy, fz, ec, el);
             } else {
                 const int nb = min(cnt.y, a.p);
                 const real w = cnt.y > a.p ? (real)cnt.y / (real)a.p : (real)1;
-                const int32_t *bk = a.bk + is * a.p;
                 real bx = 0, by = 0, bz = 0;
                 double bec = 0.0, bel = 0.0;
-                for (int e = 0; e < nb; ++e) eval_k<real, ENERGY>(a, s_lj, I, bk[e], bx, by, bz, bec, bel);
+                for (int e = 0; e < nb; ++e)
+                    eval_k<real, ENERGY>(a, s_lj, I, a.bk[lidx(is, e, N, a.p)], bx, by, bz, bec, bel);
                 fx += w * bx;
                 fy += w * by;
                 fz += w * bz;
@@ -708,8 +722,8 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                 I.hs = s_lj[a.T + ti];
                 const uint32_t id_i = I.A.w;
                 const SelCtx sel{
-                    a.spos, philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key),
-                    rp.key, id0};
+                    philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key),
+                    rp.key};
                 uint32_t hh[CAP];
                 int hk[CAP];
                 sel_init<CAP>(hh, hk, a.p);
@@ -724,7 +738,7 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                         } else {
                             const uint32_t id = s_id[FB_LIST - 1 - e][tid] - id0;
                             const uint2 w = philox_rest(sel.r0, id, rp.key);
-                            sel_insert<CAP>(hh, hk, w.x, k, id, sel);
+                            sel_insert<CAP>(hh, hk, w.x, (int)id, id, sel);
                         }
                     }
                     for (int e = 0; e < lc; ++e) eval_k<real, ENERGY>(a, s_lj, I, s_k[e][tid], ax, ay, az, aec, ael);
@@ -756,7 +770,9 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                     double bec = 0.0, bel = 0.0;
 #pragma unroll
                     for (int e = 0; e < CAP; ++e)
-                        if (hk[e] >= 0) eval_k<real, ENERGY>(a, s_lj, I, hk[e], bx, by, bz, bec, bel);
+                        if (hk[e] >= 0)
+                            eval_k<real, ENERGY>(a, s_lj, I, a.sidx[id0 + (uint32_t)hk[e]], bx, by,
+                                                 bz, bec, bel);
                     ax += w * bx;
                     ay += w * by;
                     az += w * bz;
@@ -771,7 +787,7 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
 #pragma unroll
                         for (int e = 0; e < CAP; ++e) {
                             if (hk[e] < 0) continue;
-                            const int32_t v = (int32_t)a.spos[hk[e]].w;
+                            const int32_t v = (int32_t)(id0 + (uint32_t)hk[e]);
                             int y = nb - 1;
                             while (y >= 0 && out[y] > v) {
                                 out[y + 1] = out[y];
@@ -884,6 +900,7 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     a.batch = batch;
     a.lcore = c->lcore;
     a.lshell = c->lshell;
+    a.sidx = c->cell_rank;
     a.ncount = c->ncount;
     a.bk = c->bk;
     a.ovf = c->ibuf + 2;
@@ -921,6 +938,7 @@ static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
     a.imax = c->ibuf;
     a.lcore = c->lcore;
     a.lshell = c->lshell;
+    a.sidx = c->cell_rank;
     a.ncount = c->ncount;
     a.bk = c->bk;
     a.ovf = c->ibuf + 2;

@@ -106,6 +106,14 @@ struct AtomSlot {
     bool ok;
 };
 
+// Position of entry e of sorted atom i in a per-atom list of capacity cap.  Row
+// major: a thread's appends stay in its own row, which measured faster than the
+// column-major layout (coalesced reads, but scattered partial-line writes).
+__device__ __forceinline__ int64_t lidx(int64_t i, int e, int64_t /*N*/, int cap)
+{
+    return i * cap + e;
+}
+
 __device__ __forceinline__ AtomSlot atom_slot_at(const int2 *__restrict__ map,
                                                  const Rep *__restrict__ reps, int b)
 {
@@ -189,7 +197,7 @@ struct rbmd_ctx {
     int32_t *cell_count;  // [ncell]
     int32_t *cell_start;  // [ncell+1]
     int32_t *cell_of;     // [N]
-    int32_t *cell_rank;   // [N]
+    int32_t *cell_rank;   // [N] rank inside the cell while binning, then the sorted index
     int32_t *scan_part;   // scan block sums
     uint4 *spos;          // [N]
     void *sq;             // real [N]
@@ -201,8 +209,8 @@ struct rbmd_ctx {
     float *lj_f;          // [2*T] sqrt(eps), sigma/2 (FP32 path)
     double *lj_d;         // [2*T] (FP64 path)
     int pair_parts;       // per-warp partial sums: pair kernel (4 nb128), then the fallback (4 nb128)
-    int32_t *lcore;       // [N][list_cc] core lists (cell-sorted order)
-    int32_t *lshell;      // [N][list_cs] shell lists
+    int32_t *lcore;       // [N][list_cc] core lists (sorted indices)
+    int32_t *lshell;      // [N][list_cs] shell lists (replica-local atom ids)
     int2 *ncount;         // [N] (|C|, N_s)
     int32_t *bk;          // [N][p] batch (sorted indices)
     int list_cc, list_cs; // list capacities per atom
