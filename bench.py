@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shapes on workloads that autotune")
+    ap.add_argument("--pair-table", action="store_true",
+                    help="erfc-Coulomb pair terms from the look-up table (RBMD_PAIR_TABLE)")
     ap.add_argument("--cpu-sample", type=int, default=400_000)
     ap.add_argument("--ref-sample", type=int, default=100_000)
     args = ap.parse_args()
@@ -72,6 +74,8 @@ def parse():
         from paper_2407_09315_b300 import synth
         args.n = int(sum(synth.replica_sizes(w["replicas"], w["n_lo"], w["n_hi"], seed=4)))
     PARAMS.update(w["params"])
+    if args.pair_table:
+        PARAMS["flags"] = PARAMS.get("flags", 0) | 16
     return args
 
 
@@ -450,7 +454,7 @@ def run_ours(args):
         "gpu_launches": kernels_per_step * args.steps,
         "device_memory_bytes": int(footprint),
         "kernels_per_step": kernels_per_step,
-        "tiles": dict(tiles, names=["cell_div", "rho_tile", "rho_mode_tile"]),
+        "tiles": dict(tiles, names=["cell_div", "rho_tile", "rho_mode_tile", "pair_table"]),
     }
     if fp64:
         out["fp64"] = fp64

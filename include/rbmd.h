@@ -69,6 +69,8 @@ typedef enum { RBMD_FP32 = 0, RBMD_FP64 = 1 } rbmd_precision;
 #define RBMD_RBL_EXACT 2u        /* RBL keeps every shell neighbour with weight 1 */
 #define RBMD_NO_RBE 4u           /* skip the long-range part (LJ-fluid runs) */
 #define RBMD_NO_RBL 8u           /* skip the short-range part */
+#define RBMD_PAIR_TABLE 16u      /* erfc-Coulomb pair terms from a cubic look-up table
+                                    (Sec. 3.3; rbmd_pair_table) instead of erfc/exp */
 
 typedef struct {
     int64_t n_atoms;     /* N >= 1 */
@@ -178,19 +180,42 @@ int32_t rbmd_replica_count(rbmd_ctx *ctx);
  * within the precision's tolerance).  Defaults: cell_div from the parameters (2
  * when 0), 1024, 256.
  * rbmd_set_tiles  sets them (INVALID for other values).  Synchronises.
- * rbmd_get_tiles  out: host int32 [3] = cell_div, rho_tile, rho_mode_tile.
+ * rbmd_get_tiles  out: host int32 [4] = cell_div, rho_tile, rho_mode_tile, and 1
+ *                 when the pair look-up table is in use (rbmd_set_pair_table).
  * rbmd_autotune   times the RBL part for each cell_div and the structure factors
  *                 for each (rho_tile, rho_mode_tile) on the current state with the
  *                 draws of `step`, after one untimed run, 3 timed runs each, and
- *                 keeps the fastest; chosen (host int32 [3], or NULL) receives
- *                 them.  Synchronises.  A batch context tunes once for all
- *                 replicas.  Scratch force buffers are overwritten; the state
+ *                 keeps the fastest, then times the pair kernels with and without
+ *                 the look-up table; chosen (host int32 [4], or NULL) receives
+ *                 them as rbmd_get_tiles does.  Synchronises.  A batch context
+ *                 tunes once for all replicas.  Scratch force buffers are
+ *                 overwritten; the state
  *                 (positions, velocities, step counter) is not changed.
  */
 rbmd_status rbmd_set_tiles(rbmd_ctx *ctx, int32_t cell_div, int32_t rho_tile,
                            int32_t rho_mode_tile);
 rbmd_status rbmd_get_tiles(rbmd_ctx *ctx, int32_t *out);
 rbmd_status rbmd_autotune(rbmd_ctx *ctx, int64_t step, int32_t *chosen);
+
+/*
+ * rbmd_set_pair_table -- pair kernels evaluate the erfc-Coulomb force and energy
+ * from the look-up table (on != 0) or from erfc/exp (0); the initial choice is
+ * the RBMD_PAIR_TABLE flag.  rbmd_autotune also times both and keeps the faster
+ * (chosen[3], rbmd_get_tiles out[3]: 1 = table).  Synchronises.
+ *
+ * rbmd_pair_table -- the table itself (host), Sec. 3.3's look-up method: n cubic
+ * pieces over s = r^2 in [0, r_cut^2 (1 + 1e-6)], h = that / n; piece k, local
+ * t = s/h - k in [0, 1]: coef[8k..8k+3] = c0..c3 of the force factor
+ *   f(s) = [erfc(sqrt(alpha s))/sqrt(s) + 2 sqrt(alpha/pi) e^{-alpha s}] / s,
+ * coef[8k+4..8k+7] of the energy factor e(s) = erfc(sqrt(alpha s))/sqrt(s); for
+ * k < *i0 the pieces hold f - s^{-3/2} and e - s^{-1/2} (the bare terms are added
+ * exactly).  Cubics through the exact values at t = 0, 1/3, 2/3, 1.  coef (may be
+ * NULL) must hold 8 n doubles; *inv_h = 1/h.  Contexts use n = 1024 (FP32) and
+ * 8192 (FP64).  INVALID for alpha <= 0, r_cut <= 0 or n < 16.
+ */
+rbmd_status rbmd_set_pair_table(rbmd_ctx *ctx, int32_t on);
+rbmd_status rbmd_pair_table(double alpha, double r_cut, int32_t n, int32_t *i0, double *inv_h,
+                            double *coef);
 
 /* Free every device buffer of the context (waits for its stream). NULL is a no-op. */
 void rbmd_destroy(rbmd_ctx *ctx);

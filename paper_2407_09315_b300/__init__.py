@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librbmd.so")
 
 FP32, FP64 = 0, 1
-FULL_EWALD_MODES, RBL_EXACT, NO_RBE, NO_RBL = 1, 2, 4, 8
+FULL_EWALD_MODES, RBL_EXACT, NO_RBE, NO_RBL, PAIR_TABLE = 1, 2, 4, 8, 16
 
 STATUS = {
     0: "RBMD_OK", 1: "RBMD_ERR_INVALID", 2: "RBMD_ERR_NOT_NEUTRAL",
@@ -74,6 +74,8 @@ def lib():
         "rbmd_set_tiles": ([P, i32, i32, i32], C.c_int),
         "rbmd_get_tiles": ([P, P], C.c_int),
         "rbmd_autotune": ([P, i64, P], C.c_int),
+        "rbmd_set_pair_table": ([P, i32], C.c_int),
+        "rbmd_pair_table": ([dbl, dbl, i32, C.POINTER(i32), C.POINTER(dbl), P], C.c_int),
         "rbmd_energy_batch": ([P, i64, C.POINTER(EnergyTerms)], C.c_int),
         "rbmd_destroy": ([P], None),
         "rbmd_rbe_forces": ([P, i64, P, C.c_int], C.c_int),
@@ -129,6 +131,16 @@ def sampler_table(box_length: float, alpha: float):
     H = C.c_double(0.0)
     _check(lib().rbmd_sampler_table(box_length, alpha, C.byref(M), _ptr(T), C.byref(H)))
     return M.value, T, H.value
+
+
+def pair_table(alpha, r_cut, n):
+    """The erfc-Coulomb look-up table: (i0, inv_h, coef [n, 2, 4]) (see rbmd.h)."""
+    i0 = C.c_int32(0)
+    inv_h = C.c_double(0.0)
+    coef = np.zeros((n, 2, 4), dtype=np.float64)
+    _check(lib().rbmd_pair_table(alpha, r_cut, n, C.byref(i0), C.byref(inv_h), _ptr(coef)),
+           "pair_table")
+    return i0.value, inv_h.value, coef
 
 
 def rbe_forces_noalloc(u, charge, box_length, *, alpha, coulomb_k, P, seed, step, out,
@@ -358,14 +370,18 @@ class RBMD:
         _check(lib().rbmd_set_tiles(self._h, cell_div, rho_tile, rho_mode_tile), "set_tiles")
 
     def tiles(self):
-        """(cell_div, rho_tile, rho_mode_tile) in use."""
-        out = np.zeros(3, dtype=np.int32)
+        """(cell_div, rho_tile, rho_mode_tile, pair_table) in use."""
+        out = np.zeros(4, dtype=np.int32)
         _check(lib().rbmd_get_tiles(self._h, _ptr(out)), "get_tiles")
         return tuple(int(x) for x in out)
 
+    def set_pair_table(self, on=True):
+        _check(lib().rbmd_set_pair_table(self._h, int(bool(on))), "set_pair_table")
+
     def autotune(self, step=0):
-        """Time the tile-shape candidates on the current state and keep the fastest."""
-        out = np.zeros(3, dtype=np.int32)
+        """Time the tile-shape and pair-table candidates on the current state and keep
+        the fastest; returns tiles()."""
+        out = np.zeros(4, dtype=np.int32)
         _check(lib().rbmd_autotune(self._h, step, _ptr(out)), "autotune")
         return tuple(int(x) for x in out)
 

@@ -204,7 +204,7 @@ void free_ctx(rbmd_ctx *c)
                     c->epart,     c->kepart,    c->ibuf,     c->lj_f,       c->lj_d,
                     c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp,
                     c->adj_lj,    c->adj_tpart, c->adj_tsum, c->reps,       c->map256,
-                    c->map128,    c->tiles,     c->red_rep};
+                    c->map128,    c->tiles,     c->red_rep,   c->ptab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -634,6 +634,26 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     // LJ tables: sqrt(eps_t), sigma_t/2 (Lorentz-Berthelot, Eq. 4)
     if (c->fp64) TRY(alloc_n(&c->lj_d, 2 * c->T));
     else TRY(alloc_n(&c->lj_f, 2 * c->T));
+    {
+        // pair look-up table (Sec. 3.3), used when RBMD_PAIR_TABLE is set or the
+        // autotuner picks it
+        std::vector<double> coef;
+        c->ptab_n = c->fp64 ? 8192 : 1024;
+        double inv_h = 0.0;
+        TRY(pair_table_host(p.alpha, p.r_cut, c->ptab_n, coef, &c->ptab_i0, &inv_h));
+        c->ptab_inv_h = inv_h;
+        if (c->fp64) {
+            TRY(dev_alloc(&c->ptab, sizeof(double) * coef.size()));
+            TRY(cuda_status(cudaMemcpy(c->ptab, coef.data(), sizeof(double) * coef.size(),
+                                       cudaMemcpyHostToDevice)));
+        } else {
+            std::vector<float> cf(coef.begin(), coef.end());
+            TRY(dev_alloc(&c->ptab, sizeof(float) * cf.size()));
+            TRY(cuda_status(cudaMemcpy(c->ptab, cf.data(), sizeof(float) * cf.size(),
+                                       cudaMemcpyHostToDevice)));
+        }
+        c->use_table = (p.flags & RBMD_PAIR_TABLE) != 0;
+    }
     TRY(upload_lj(c, lj_eps, lj_sigma));
     TRY(rbe_configure(c));
     TRY(cuda_status(cudaMemcpy(c->reps, c->reps_h, sizeof(Rep) * R, cudaMemcpyHostToDevice)));
@@ -899,6 +919,19 @@ rbmd_status rbmd_get_tiles(rbmd_ctx *c, int32_t *out)
     out[0] = c->div;
     out[1] = c->rho_tile;
     out[2] = c->rho_mode_tile;
+    out[3] = c->use_table ? 1 : 0;
+    return RBMD_OK;
+}
+
+rbmd_status rbmd_set_pair_table(rbmd_ctx *c, int32_t on)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    RBMD_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+    c->use_table = on != 0;
+    if (c->graph_ready) {  // the step graph holds the old kernel arguments
+        cudaGraphExecDestroy(c->graph);
+        c->graph_ready = false;
+    }
     return RBMD_OK;
 }
 
@@ -964,6 +997,14 @@ rbmd_status rbmd_autotune(rbmd_ctx *c, int64_t step, int32_t *chosen)
             }
     }
     if (st == RBMD_OK) st = rbmd_set_tiles(c, best_div, best_tile, best_mt);
+    if (st == RBMD_OK && !(c->prm.flags & RBMD_NO_RBL)) {
+        float ms[2] = {0.f, 0.f};
+        for (int on = 0; on < 2 && st == RBMD_OK; ++on) {
+            st = rbmd_set_pair_table(c, on);
+            if (st == RBMD_OK) st = tune_time(c, true, s, reps, &ms[on]);
+        }
+        if (st == RBMD_OK) st = rbmd_set_pair_table(c, ms[1] < ms[0]);
+    }
     if (st == RBMD_OK && chosen) st = rbmd_get_tiles(c, chosen);
     st = leave(c, st);
     if (st != RBMD_OK) return st;

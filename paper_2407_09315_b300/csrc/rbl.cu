@@ -220,6 +220,9 @@ template <typename real> struct PairArgs {
     int div, T, p, exact;
     StepRef step;
     real ck, alpha, sqrt_alpha, c2;
+    const void *tab;   // pair look-up table (pairtab.cu layout, real4 [2 n]) or NULL
+    int tab_n, tab_i0;
+    real tab_inv_h;
     real *F;
     int accumulate;
     double *fpart;     // [parts][3]: pair kernel per warp, then the fallback per warp
@@ -247,27 +250,51 @@ __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 // Force on i from j (d = r_j - r_i, minimum image) for erfc-Coulomb (Eq. 10) +
 // Lennard-Jones (Eq. 2) with Lorentz-Berthelot parameters (Eq. 4); adds F_ij to
 // f and, with ENERGY, u_ij to (ec, el).
-template <typename real, bool ENERGY>
+template <typename real> struct Real4;
+template <> struct Real4<float> { using type = float4; };
+template <> struct Real4<double> { using type = double4_32a; };
+
+template <typename real, bool ENERGY, bool TAB>
 __device__ __forceinline__ void pair_eval(const PairArgs<real> &a, real dx, real dy, real dz,
                                           real qq, real eps, real sig, real &fx, real &fy,
                                           real &fz, double &ec, double &el)
 {
     const real r2 = dx * dx + dy * dy + dz * dz;
     const real rinv = rsqrt_r(r2);
-    const real r = r2 * rinv;
-    const real er = erfc_r(a.sqrt_alpha * r);
-    const real ex = exp_r(-a.alpha * r2);
-    const real gc = qq * (er * rinv + a.c2 * ex);  // r * (-dU_coul/dr)
     const real s2 = sig * sig * rinv * rinv;
     const real s6 = s2 * s2 * s2;
     const real s12 = s6 * s6;
     const real glj = (real)24 * eps * ((real)2 * s12 - s6);  // r * (-dU_lj/dr)
-    const real g = (gc + glj) * rinv * rinv;
+    real g, eu = 0;
+    if constexpr (TAB) {
+        // cubic piece of the tabulated factors at s = r^2; below the knot i0 the
+        // pieces hold the remainders and the bare Coulomb terms are added exactly
+        const real u = r2 * a.tab_inv_h;
+        const int k = min((int)u, a.tab_n - 1);
+        const real t = u - (real)k;
+        const typename Real4<real>::type *T = static_cast<const typename Real4<real>::type *>(a.tab);
+        const typename Real4<real>::type cf = T[2 * k];
+        real fc = ((cf.w * t + cf.z) * t + cf.y) * t + cf.x;
+        if (k < a.tab_i0) fc += rinv * rinv * rinv;
+        g = qq * fc + glj * rinv * rinv;
+        if constexpr (ENERGY) {
+            const typename Real4<real>::type ce = T[2 * k + 1];
+            eu = ((ce.w * t + ce.z) * t + ce.y) * t + ce.x;
+            if (k < a.tab_i0) eu += rinv;
+        }
+    } else {
+        const real r = r2 * rinv;
+        const real er = erfc_r(a.sqrt_alpha * r);
+        const real ex = exp_r(-a.alpha * r2);
+        const real gc = qq * (er * rinv + a.c2 * ex);  // r * (-dU_coul/dr)
+        g = (gc + glj) * rinv * rinv;
+        eu = er * rinv;
+    }
     fx -= g * dx;
     fy -= g * dy;
     fz -= g * dz;
     if constexpr (ENERGY) {
-        ec += (double)(qq * er * rinv);
+        ec += (double)(qq * eu);
         el += (double)((real)4 * eps * (s12 - s6));
     }
 }
@@ -278,17 +305,27 @@ template <typename real> struct AtomI {
     real qi, se, hs, lscale;
 };
 
-template <typename real, bool ENERGY>
+template <typename real, bool ENERGY, bool TAB = false>
 __device__ __forceinline__ void eval_k(const PairArgs<real> &a, const real *s_lj,
                                        const AtomI<real> &I, int k, real &fx, real &fy, real &fz,
                                        double &ec, double &el)
 {
     const uint4 B = a.spos[k];
     const int tj = a.stype[k];
-    pair_eval<real, ENERGY>(a, (real)(int32_t)(B.x - I.A.x) * I.lscale,
+    pair_eval<real, ENERGY, TAB>(a, (real)(int32_t)(B.x - I.A.x) * I.lscale,
                             (real)(int32_t)(B.y - I.A.y) * I.lscale,
                             (real)(int32_t)(B.z - I.A.z) * I.lscale, I.qi * a.sq[k],
                             I.se * s_lj[tj], I.hs + s_lj[a.T + tj], fx, fy, fz, ec, el);
+}
+
+// Table or closed forms chosen at run time (the rarely used fallback kernel).
+template <typename real, bool ENERGY>
+__device__ __forceinline__ void eval_any(const PairArgs<real> &a, const real *s_lj,
+                                         const AtomI<real> &I, int k, real &fx, real &fy, real &fz,
+                                         double &ec, double &el)
+{
+    if (a.tab) eval_k<real, ENERGY, true>(a, s_lj, I, k, fx, fy, fz, ec, el);
+    else eval_k<real, ENERGY, false>(a, s_lj, I, k, fx, fy, fz, ec, el);
 }
 
 // Philox4x32-10 of the batch priority for the counter (id_i, id_j, step, tag).
@@ -599,7 +636,7 @@ __global__ void __launch_bounds__(256, (CAP <= 10 ? 3 : 1)) k_rbl_select(PairArg
 }
 
 // Step 2 (+ the partial sums of step 3).
-template <typename real, bool ENERGY>
+template <typename real, bool ENERGY, bool TAB>
 __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
 {
     __shared__ real s_lj[2 * RBMD_MAX_TYPES];
@@ -621,12 +658,12 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
             I.hs = s_lj[a.T + ti];
             const int64_t N = a.N;
             for (int e = 0; e < cnt.x; ++e)
-                eval_k<real, ENERGY>(a, s_lj, I, a.lcore[lidx(is, e, N, a.CC)], fx, fy, fz, ec, el);
+                eval_k<real, ENERGY, TAB>(a, s_lj, I, a.lcore[lidx(is, e, N, a.CC)], fx, fy, fz, ec, el);
             if (a.exact) {
                 const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
                 for (int e = 0; e < cnt.y; ++e)
-                    eval_k<real, ENERGY>(a, s_lj, I,
-                                         a.sidx[id0 + (uint32_t)a.lshell[lidx(is, e, N, a.CS)]],
+                    eval_k<real, ENERGY, TAB>(a, s_lj, I,
+                                              a.sidx[id0 + (uint32_t)a.lshell[lidx(is, e, N, a.CS)]],
                                          fx, fy, fz, ec, el);
             } else {
                 const int nb = min(cnt.y, a.p);
@@ -634,7 +671,7 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
                 real bx = 0, by = 0, bz = 0;
                 double bec = 0.0, bel = 0.0;
                 for (int e = 0; e < nb; ++e)
-                    eval_k<real, ENERGY>(a, s_lj, I, a.bk[lidx(is, e, N, a.p)], bx, by, bz, bec, bel);
+                    eval_k<real, ENERGY, TAB>(a, s_lj, I, a.bk[lidx(is, e, N, a.p)], bx, by, bz, bec, bel);
                 fx += w * bx;
                 fy += w * by;
                 fz += w * bz;
@@ -734,14 +771,14 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                     for (int e = 0; e < lsn; ++e) {
                         const int k = s_k[FB_LIST - 1 - e][tid];
                         if (a.exact) {
-                            eval_k<real, ENERGY>(a, s_lj, I, k, ax, ay, az, aec, ael);
+                            eval_any<real, ENERGY>(a, s_lj, I, k, ax, ay, az, aec, ael);
                         } else {
                             const uint32_t id = s_id[FB_LIST - 1 - e][tid] - id0;
                             const uint2 w = philox_rest(sel.r0, id, rp.key);
                             sel_insert<CAP>(hh, hk, w.x, (int)id, id, sel);
                         }
                     }
-                    for (int e = 0; e < lc; ++e) eval_k<real, ENERGY>(a, s_lj, I, s_k[e][tid], ax, ay, az, aec, ael);
+                    for (int e = 0; e < lc; ++e) eval_any<real, ENERGY>(a, s_lj, I, s_k[e][tid], ax, ay, az, aec, ael);
                     lc = 0;
                     lsn = 0;
                 };
@@ -771,7 +808,7 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
 #pragma unroll
                     for (int e = 0; e < CAP; ++e)
                         if (hk[e] >= 0)
-                            eval_k<real, ENERGY>(a, s_lj, I, a.sidx[id0 + (uint32_t)hk[e]], bx, by,
+                            eval_any<real, ENERGY>(a, s_lj, I, a.sidx[id0 + (uint32_t)hk[e]], bx, by,
                                                  bz, bec, bel);
                     ax += w * bx;
                     ay += w * by;
@@ -856,8 +893,13 @@ static void launch_rbl(rbmd_ctx *c, const PairArgs<real> &a, cudaStream_t st, bo
         if (!a.exact) k_rbl_select<real, CAP, false><<<nb256, 256, 0, st>>>(a256);
     }
     if (marks) prof_mark(c, 4);
-    if (energy) k_rbl_force<real, true><<<nbp, kPairBlock, 0, st>>>(a128);
-    else k_rbl_force<real, false><<<nbp, kPairBlock, 0, st>>>(a128);
+    if (a.tab) {
+        if (energy) k_rbl_force<real, true, true><<<nbp, kPairBlock, 0, st>>>(a128);
+        else k_rbl_force<real, false, true><<<nbp, kPairBlock, 0, st>>>(a128);
+    } else {
+        if (energy) k_rbl_force<real, true, false><<<nbp, kPairBlock, 0, st>>>(a128);
+        else k_rbl_force<real, false, false><<<nbp, kPairBlock, 0, st>>>(a128);
+    }
     if (lists) {
         if (energy) k_rbl_fused<real, CAP, true, true><<<nfb, kPairBlock, 0, st>>>(a128);
         else k_rbl_fused<real, CAP, false, true><<<nfb, kPairBlock, 0, st>>>(a128);
@@ -889,6 +931,10 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     a.alpha = (real)c->prm.alpha;
     a.sqrt_alpha = (real)sqrt(c->prm.alpha);
     a.c2 = (real)(2.0 * sqrt(c->prm.alpha / kPi));
+    a.tab = c->use_table ? c->ptab : nullptr;
+    a.tab_n = c->ptab_n;
+    a.tab_i0 = c->ptab_i0;
+    a.tab_inv_h = (real)c->ptab_inv_h;
     a.F = (real *)force;
     a.accumulate = accumulate;
     a.fpart = c->fpart;

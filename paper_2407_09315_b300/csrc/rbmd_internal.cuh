@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/rbmd.h"
 
 #define RBMD_STREAM_RBE 1u
@@ -188,6 +190,10 @@ struct rbmd_ctx {
     double2 *rho;         // [R][Pm]
     double *emode;        // [R][Pm]
     void *coef;           // ModeCoef<real>[R][Pm]
+    void *ptab;           // pair look-up table, real4 [2 ptab_n] (pairtab.cu)
+    int ptab_n, ptab_i0;
+    double ptab_inv_h;
+    bool use_table;       // pair kernels read the table instead of erfc/exp
     int rho_tile;         // atoms per structure-factor tile (512, 1024 or 2048)
     int rho_mode_tile;    // modes per structure-factor block (64, 128 or 256)
     int ntiles_max;       // tiles at the smallest tile size (rho_part capacity)
@@ -266,6 +272,8 @@ rbmd_status sampler_table_host(double L, double alpha, int32_t *M, uint64_t *T, 
 rbmd_status rbe_sample(rbmd_ctx *c, StepRef s);
 rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between = -1);
 rbmd_status rbe_configure(rbmd_ctx *c);  // kernel attributes (dynamic shared memory)
+rbmd_status pair_table_host(double alpha, double r_cut, int n, std::vector<double> &coef,
+                            int32_t *i0, double *inv_h);
 rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate);
 
 // RBL (rbl.cu)
