@@ -13,7 +13,8 @@
  *     p shell neighbours (r_core <= r <= r_cut, weight N_s/p), erfc-Coulomb
  *     (Eq. 10) plus Lennard-Jones (Eq. 2, Lorentz-Berthelot mixing Eq. 4), and
  *     the momentum correction F_corr = -(1/N) sum_i (F_core + F_shell*) (Eq. 16);
- *   - velocity-Verlet with an optional Berendsen thermostat (Sec. 2.1).
+ *   - velocity-Verlet with an optional Berendsen, Langevin or Nose-Hoover
+ *     thermostat (Sec. 2.1).
  *
  * Naming: r_core is the paper's inner radius r_c and r_cut its outer radius r_s.
  *
@@ -81,16 +82,18 @@ typedef struct {
     double r_core;       /* inner radius (paper r_c), 0 <= r_core <= r_cut */
     double r_cut;        /* outer radius (paper r_s), r_cut < L/2 */
     int32_t rbl_p;       /* RBL shell batch size p, 1..32 (Eq. 15) */
-    int32_t thermostat;  /* 0 none (NVE), 1 Berendsen */
+    int32_t thermostat;  /* 0 none (NVE), 1 Berendsen, 2 Langevin, 3 Nose-Hoover (rbmd_step) */
     double coulomb_k;    /* Coulomb prefactor (1/(4 pi eps0) of Eq. 3; Bjerrum length in reduced units) */
     double dt;           /* time step */
-    double temperature;  /* Berendsen target T0 (k_B = 1) */
-    double tau_T;        /* Berendsen coupling time; <= 0 selects 0.1 */
+    double temperature;  /* thermostat target T0 (k_B = 1) */
+    double tau_T;        /* thermostat time: Berendsen coupling time, Langevin 1/gamma,
+                            Nose-Hoover period scale (Q = g T0 tau^2); <= 0 selects 0.1 */
     uint64_t seed;       /* Philox key of every random draw */
     uint32_t replica;    /* replica index mixed into the random streams */
     int32_t precision;   /* rbmd_precision */
     uint32_t flags;      /* RBMD_* flags above */
-    int32_t cell_div;    /* cells per r_cut along each axis: 1 or 2; 0 = autotune */
+    int32_t cell_div;    /* cells per r_cut along each axis: 1 or 2; 0 = 2 (rbmd_set_tiles
+                            and rbmd_autotune change it later) */
 } rbmd_params;
 
 /* Energies and diagnostics (host, FP64).  Potential terms follow Eq. 8 with the
@@ -244,11 +247,34 @@ rbmd_status rbmd_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumulate
 /*
  * rbmd_step -- advance n_steps velocity-Verlet steps (Sec. 2.1): half kick,
  * drift of the fixed-point positions (wrapping is modular), forces of the new
- * configuration keyed by the new step number, half kick, Berendsen rescale.
+ * configuration keyed by the new step number, half kick, thermostat.  Unit
+ * masses, k_B = 1, g = 3N - 3 degrees of freedom per system, T = 2 KE / g.
+ *   1 Berendsen: v *= lambda = sqrt(1 + (dt/tau)(T0/T - 1)), clamped to [0.8, 1.25].
+ *   2 Langevin (Schneider-Stoll): after the forces of the new configuration every
+ *     atom gets F_L = -gamma v + sqrt(2 gamma T0 / dt) G, gamma = 1/tau, v the
+ *     half-step velocity, G standard normal (Philox4x32-10, key = seed, counter
+ *     (replica-local atom id, step of that force evaluation, 0, 3 | replica << 8),
+ *     uniforms (w + 1/2) 2^-32 (FP32 contexts: ((w >> 8) + 1/2) 2^-24), Box-Muller:
+ *     (G_x, G_y) = sqrt(-2 ln u0)(cos, sin)(2 pi u1), G_z = sqrt(-2 ln u2) cos(2 pi u3));
+ *     F + F_L drives the second half-kick and the next first half-kick.
+ *   3 Nose-Hoover, one variable xi, Q = g T0 tau^2: xi += dt/2 (2 KE - g T0)/Q,
+ *     v *= e^{-xi dt/2}, kick-drift-force-kick, v *= e^{-xi dt/2},
+ *     xi += dt/2 (2 KE - g T0)/Q.
  * The context's step counter advances by n_steps.  Queued as one CUDA graph per
  * step after the first call.
  */
 rbmd_status rbmd_step(rbmd_ctx *ctx, int64_t n_steps);
+
+/*
+ * Nose-Hoover variable xi of every replica at the step boundary (host double [R]),
+ * for checkpoints; rbmd_set_thermostat also makes the next rbmd_step recompute the
+ * forces.  A Berendsen factor is folded into the velocities that rbmd_get_state
+ * returns; the Langevin random force of the last step is not part of the state
+ * (a resumed Langevin run draws the same later noise but restarts its first
+ * half-kick from the conservative force).
+ */
+rbmd_status rbmd_get_thermostat(rbmd_ctx *ctx, double *xi);
+rbmd_status rbmd_set_thermostat(rbmd_ctx *ctx, const double *xi);
 
 /*
  * rbmd_energy -- energies and diagnostics of the current state, with the random

@@ -53,7 +53,8 @@ def lib():
         L.orc_energy_grad.argtypes = [i64, P, P, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, i32,
                                       i32, u64, i64, u32, i32, P, P, P, P, P]
         L.orc_vv.argtypes = [i64, P, P, P, P, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, i32,
-                             i32, u64, i64, u32, i32, dbl, i32, dbl, dbl, i64]
+                             i32, u64, i64, u32, i32, dbl, i32, dbl, dbl, i64, P]
+        L.orc_langevin_normals.argtypes = [u64, u32, i64, u32, P]
         _lib = L
     return _lib
 
@@ -237,8 +238,10 @@ def forces(u, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P, seed
 
 
 def vv(u, v, F, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P, seed, step0,
-       dt, n_steps, thermostat=0, T0=1.0, tau=0.1, replica=0, exact=False):
-    """Velocity-Verlet (+ Berendsen) from step0; returns new (u, v, F)."""
+       dt, n_steps, thermostat=0, T0=1.0, tau=0.1, replica=0, exact=False, xi=0.0,
+       return_xi=False):
+    """Velocity-Verlet with thermostat 0 (none), 1 (Berendsen), 2 (Langevin) or 3
+    (Nose-Hoover, variable xi) from step0; returns new (u, v, F) (and xi)."""
     u = _u(u).copy()
     v = _d(v).copy()
     F = _d(F).copy()
@@ -246,10 +249,20 @@ def vv(u, v, F, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P, se
     types = np.ascontiguousarray(types, dtype=np.int32)
     eps = _d(eps)
     sig = _d(sig)
+    x = C.c_double(xi)
     lib().orc_vv(len(u), _p(u), _p(v), _p(F), _p(q), _p(types), len(eps), _p(eps), _p(sig),
                  L, alpha, coulomb_k, r_core, r_cut, p, P, seed, step0, replica, int(exact),
-                 dt, thermostat, T0, tau, n_steps)
+                 dt, thermostat, T0, tau, n_steps, C.byref(x))
+    if return_xi:
+        return u, v, F, x.value
     return u, v, F
+
+
+def langevin_normals(seed, atom, step, replica=0):
+    """The three standard normal deviates of the Langevin force of one atom."""
+    g = np.zeros(3)
+    lib().orc_langevin_normals(seed, atom, step, replica, _p(g))
+    return g
 
 
 def decode(u, L):

@@ -32,6 +32,7 @@
 /* Counter word 3 tags which random stream a draw belongs to. */
 #define ORC_STREAM_RBE 1u
 #define ORC_STREAM_RBL 2u
+#define ORC_STREAM_LANGEVIN 3u
 #define ORC_MAX_ATTEMPTS 256
 
 /* ------------------------------------------------------------------------ */
@@ -679,23 +680,71 @@ void orc_forces(int64_t n, const uint32_t *u, const double *q, const int32_t *ty
 }
 
 /* ------------------------------------------------------------------------ */
-/* Velocity-Verlet (Sec. 2.1) with the Berendsen thermostat (Sec. 2.1, 4).   */
-/* Readings: unit masses (reduced units, Sec. 4.1); positions are the       */
-/* fixed-point u, drifted by rint(v_d * (dt * 2^32 / L)) and wrapped mod     */
-/* 2^32; Berendsen lambda = sqrt(1 + (dt/tau)(T0/T - 1)) clamped to          */
-/* [0.8, 1.25], T = 2 KE / (3N - 3), applied after the second half-kick;     */
-/* thermostat = 0 switches it off.  One call advances step0 -> step0+n_steps.*/
-/* F (in/out): forces of the configuration at step0 (keyed by step0), on    */
-/* return those at step0 + n_steps.                                          */
+/* Standard normal deviates of the Langevin random force for atom `id` at    */
+/* force evaluation `step`: one Philox4x32-10 call, key = seed, counter      */
+/* (id, step, 0, 3 | replica << 8); uniforms u_k = (w_k + 1/2) / 2^32 in     */
+/* (0, 1); Box-Muller: g_x, g_y = sqrt(-2 ln u_0) (cos, sin)(2 pi u_1),      */
+/* g_z = sqrt(-2 ln u_2) cos(2 pi u_3).                                      */
 /* ------------------------------------------------------------------------ */
+void orc_langevin_normals(uint64_t seed, uint32_t id, int64_t step, uint32_t replica,
+                          double g[3])
+{
+    uint32_t key[2], w[4];
+    orc_seed_key(seed, key);
+    const uint32_t ctr[4] = {id, (uint32_t)step, 0u, ORC_STREAM_LANGEVIN | (replica << 8)};
+    orc_philox4x32_10(ctr, key, w);
+    double u[4];
+    for (int k = 0; k < 4; ++k) u[k] = ((double)w[k] + 0.5) / ORC_TWO32;
+    const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+    g[0] = r0 * cos(2.0 * ORC_PI * u[1]);
+    g[1] = r0 * sin(2.0 * ORC_PI * u[1]);
+    g[2] = r1 * cos(2.0 * ORC_PI * u[3]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Velocity-Verlet (Sec. 2.1) with the thermostats of Sec. 2.1.             */
+/* Readings: unit masses and k_B = 1 (reduced units, Sec. 4.1); positions    */
+/* are the fixed-point u, drifted by rint(v_d * (dt * 2^32 / L)) and wrapped */
+/* mod 2^32; T = 2 KE / g with g = 3N - 3 degrees of freedom.                */
+/*  thermostat 0: none (NVE).                                                */
+/*  thermostat 1: Berendsen, lambda = sqrt(1 + (dt/tau)(T0/T - 1)) clamped   */
+/*     to [0.8, 1.25], applied to v after the second half-kick.              */
+/*  thermostat 2: Langevin (Schneider-Stoll): after the forces of the new    */
+/*     configuration, every atom gets F_L = -gamma v + sqrt(2 gamma T0 / dt) */
+/*     G with gamma = 1/tau, v the half-step velocity and G standard normal  */
+/*     (orc_langevin_normals, keyed by the step of that force evaluation);   */
+/*     F + F_L drives the second half-kick and the next first half-kick.     */
+/*  thermostat 3: Nose-Hoover, one thermostat variable xi, Q = g T0 tau^2,   */
+/*     symmetric splitting: xi += dt/2 (2 KE - g T0)/Q; v *= e^{-xi dt/2};  */
+/*     half-kick, drift, forces, half-kick; v *= e^{-xi dt/2};               */
+/*     xi += dt/2 (2 KE - g T0)/Q (KE of the scaled velocities).             */
+/*     *xi (in/out) carries the variable between calls.                      */
+/* One call advances step0 -> step0 + n_steps.  F (in/out): the forces used  */
+/* by the first half-kick (those of step0, plus its Langevin force if any);  */
+/* on return those of step0 + n_steps.                                       */
+/* ------------------------------------------------------------------------ */
+static double orc_kinetic(int64_t n, const double *v)
+{
+    double ke = 0.0;
+    for (int64_t i = 0; i < 3 * n; ++i) ke += 0.5 * v[i] * v[i];
+    return ke;
+}
+
 void orc_vv(int64_t n, uint32_t *u, double *v, double *F, const double *q, const int32_t *type,
             int32_t n_types, const double *eps, const double *sig, double L, double alpha,
             double coulomb_k, double r_core, double r_cut, int32_t p, int32_t P, uint64_t seed,
             int64_t step0, uint32_t replica, int32_t exact, double dt, int32_t thermostat,
-            double T0, double tau, int64_t n_steps)
+            double T0, double tau, int64_t n_steps, double *xi)
 {
     double c = dt * (ORC_TWO32 / L);
+    const double g = 3.0 * (double)n - 3.0;
+    const double Q = g * T0 * tau * tau;
     for (int64_t s = 0; s < n_steps; ++s) {
+        if (thermostat == 3 && n > 1) {
+            *xi += 0.5 * dt * (2.0 * orc_kinetic(n, v) - g * T0) / Q;
+            const double f = exp(-0.5 * dt * *xi);
+            for (int64_t i = 0; i < 3 * n; ++i) v[i] *= f;
+        }
         for (int64_t i = 0; i < 3 * n; ++i) {
             v[i] += 0.5 * dt * F[i];
             int64_t du = (int64_t)nearbyint(v[i] * c);
@@ -703,17 +752,26 @@ void orc_vv(int64_t n, uint32_t *u, double *v, double *F, const double *q, const
         }
         orc_forces(n, u, q, type, n_types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P,
                    seed, step0 + s + 1, replica, exact, F, NULL);
-        double ke = 0.0;
-        for (int64_t i = 0; i < 3 * n; ++i) {
-            v[i] += 0.5 * dt * F[i];
-            ke += 0.5 * v[i] * v[i];
+        if (thermostat == 2) {
+            const double gamma = 1.0 / tau, sd = sqrt(2.0 * gamma * T0 / dt);
+            for (int64_t i = 0; i < n; ++i) {
+                double gn[3];
+                orc_langevin_normals(seed, (uint32_t)i, step0 + s + 1, replica, gn);
+                for (int d = 0; d < 3; ++d) F[3 * i + d] += -gamma * v[3 * i + d] + sd * gn[d];
+            }
         }
+        for (int64_t i = 0; i < 3 * n; ++i) v[i] += 0.5 * dt * F[i];
         if (thermostat == 1 && n > 1) {
-            double T = 2.0 * ke / (3.0 * (double)n - 3.0);
+            double T = 2.0 * orc_kinetic(n, v) / g;
             double lam = sqrt(1.0 + (dt / tau) * (T0 / T - 1.0));
             if (lam < 0.8) lam = 0.8;
             if (lam > 1.25) lam = 1.25;
             for (int64_t i = 0; i < 3 * n; ++i) v[i] *= lam;
+        }
+        if (thermostat == 3 && n > 1) {
+            const double f = exp(-0.5 * dt * *xi);
+            for (int64_t i = 0; i < 3 * n; ++i) v[i] *= f;
+            *xi += 0.5 * dt * (2.0 * orc_kinetic(n, v) - g * T0) / Q;
         }
     }
 }

@@ -75,6 +75,8 @@ def lib():
         "rbmd_get_tiles": ([P, P], C.c_int),
         "rbmd_autotune": ([P, i64, P], C.c_int),
         "rbmd_set_pair_table": ([P, i32], C.c_int),
+        "rbmd_get_thermostat": ([P, P], C.c_int),
+        "rbmd_set_thermostat": ([P, P], C.c_int),
         "rbmd_pair_table": ([dbl, dbl, i32, C.POINTER(i32), C.POINTER(dbl), P], C.c_int),
         "rbmd_energy_batch": ([P, i64, C.POINTER(EnergyTerms)], C.c_int),
         "rbmd_destroy": ([P], None),
@@ -328,6 +330,16 @@ class RBMD:
             vel = self._torch.from_numpy(np.ascontiguousarray(vel)).to(self.device, self.dtype)
         _check(lib().rbmd_set_state_u(self._h, _ptr(ut), _ptr(vel), step), "set_state_u")
         self._torch.cuda.current_stream(self.device).synchronize()
+
+    def thermostat_state(self):
+        """Nose-Hoover variable xi of every replica (numpy [R])."""
+        xi = np.zeros(self.R)
+        _check(lib().rbmd_get_thermostat(self._h, _ptr(xi)), "get_thermostat")
+        return xi
+
+    def set_thermostat_state(self, xi):
+        xi = np.ascontiguousarray(np.atleast_1d(xi), dtype=np.float64)
+        _check(lib().rbmd_set_thermostat(self._h, _ptr(xi)), "set_thermostat")
 
     def sync(self):
         _check(lib().rbmd_sync(self._h), "sync")

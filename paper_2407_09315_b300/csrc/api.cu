@@ -79,12 +79,16 @@ __global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
 __global__ void k_init_scal(double *scal, int R)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < R * SCAL_COUNT) scal[t] = (t % SCAL_COUNT == SCAL_LAMBDA) ? 1.0 : 0.0;
+    if (t < R * SCAL_COUNT)
+        scal[t] = (t % SCAL_COUNT == SCAL_LAMBDA || t % SCAL_COUNT == SCAL_LAMBDA_KICK) ? 1.0 : 0.0;
 }
 __global__ void k_set_lambda(double *scal, int R, double v)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < R) scal[(int64_t)r * SCAL_COUNT + SCAL_LAMBDA] = v;
+    if (r < R) {
+        scal[(int64_t)r * SCAL_COUNT + SCAL_LAMBDA] = v;
+        scal[(int64_t)r * SCAL_COUNT + SCAL_LAMBDA_KICK] = v;
+    }
 }
 
 template <typename real>
@@ -381,7 +385,7 @@ rbmd_status record_step(rbmd_ctx *c)
     RBMD_CHECK(md_kick_drift(c));
     RBMD_CHECK(forces_into(c, next, c->force, 0, false, true));
     prof_mark(c, 10);
-    RBMD_CHECK(md_kick_thermo(c, true));
+    RBMD_CHECK(md_kick_thermo(c, true, next));
     prof_mark(c, 11);
     return RBMD_OK;
 }
@@ -455,7 +459,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     if (!(p.r_core >= 0.0) || p.r_core > p.r_cut) return RBMD_ERR_INVALID;
     if (p.rbe_P < 1 || p.rbl_p < 1 || p.rbl_p > 32) return RBMD_ERR_INVALID;
     if (p.precision != RBMD_FP32 && p.precision != RBMD_FP64) return RBMD_ERR_INVALID;
-    if (p.thermostat != 0 && p.thermostat != 1) return RBMD_ERR_INVALID;
+    if (p.thermostat < 0 || p.thermostat > 3) return RBMD_ERR_INVALID;
     if (p.cell_div < 0 || p.cell_div > 2) return RBMD_ERR_INVALID;
     if ((p.flags & RBMD_FULL_EWALD_MODES) && R != 1) return RBMD_ERR_UNSUPPORTED;
     for (int t = 0; t < p.n_types; ++t)
@@ -749,6 +753,7 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
     if (!c->have_force) {
         k_set_i64<<<1, 1, 0, c->stream>>>(c->d_step, c->step);
         s = forces_into(c, StepRef{nullptr, c->step}, c->force, 0, false);
+        if (s == RBMD_OK) s = md_thermo_prepare(c);
         if (s != RBMD_OK) return leave(c, s);
         c->have_force = true;
     }
@@ -1176,6 +1181,32 @@ rbmd_status rbmd_set_state_u(rbmd_ctx *c, const uint32_t *u, const void *vel, in
     }
     c->step = step;
     c->have_force = false;
+    return leave(c, s);
+}
+
+rbmd_status rbmd_get_thermostat(rbmd_ctx *c, double *xi)
+{
+    if (!c || !xi) return RBMD_ERR_INVALID;
+    enter(c);
+    std::vector<double> h((size_t)c->R * SCAL_COUNT);
+    rbmd_status s = cuda_status(cudaMemcpyAsync(h.data(), c->scal, sizeof(double) * h.size(),
+                                                cudaMemcpyDeviceToHost, c->stream));
+    if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    if (s == RBMD_OK)
+        for (int r = 0; r < c->R; ++r) xi[r] = h[(size_t)r * SCAL_COUNT + SCAL_XI];
+    return leave(c, s);
+}
+
+rbmd_status rbmd_set_thermostat(rbmd_ctx *c, const double *xi)
+{
+    if (!c || !xi) return RBMD_ERR_INVALID;
+    enter(c);
+    rbmd_status s = RBMD_OK;
+    for (int r = 0; r < c->R && s == RBMD_OK; ++r)
+        s = cuda_status(cudaMemcpyAsync(c->scal + (size_t)r * SCAL_COUNT + SCAL_XI, xi + r,
+                                        sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    c->have_force = false;  // the next rbmd_step redoes the first half update
     return leave(c, s);
 }
 

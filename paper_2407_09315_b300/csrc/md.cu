@@ -140,7 +140,7 @@ rbmd_status md_sum_replicas(rbmd_ctx *c, const double *parts, int ncomp, int slo
     return RBMD_OK;
 }
 
-// First half kick (with the pending Berendsen factor) and drift.
+// First half kick (with the pending thermostat factor) and drift.
 template <typename real>
 __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
                              const real *__restrict__ F, const int2 *__restrict__ map,
@@ -151,7 +151,7 @@ __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
     if (!a.ok) return;
     const int64_t i = a.i;
     const double *sc = scal + (int64_t)a.r * SCAL_COUNT;
-    const real lam = (real)sc[SCAL_LAMBDA];
+    const real lam = (real)sc[SCAL_LAMBDA_KICK];
     const double dtc = reps[a.r].dtc;
     uint4 A = u4[i];
     uint32_t *pu = &A.x;
@@ -167,19 +167,73 @@ __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
     u4[i] = A;
 }
 
+// Standard normal deviates of the Langevin force (thermostat 2) of replica-local
+// atom `id` at force evaluation `step`: Philox4x32-10, key = seed, counter
+// (id, step, 0, 3 | replica << 8), uniforms (w + 1/2) 2^-32, Box-Muller.
+__device__ __forceinline__ void langevin_normals(uint32_t id, uint32_t step, const Rep &rp,
+                                                 double g[3])
+{
+    const uint4 w = philox10(make_uint4(id, step, 0u, (rp.tag_rbe & ~0xFFu) | RBMD_STREAM_LANGEVIN),
+                             rp.key);
+    const double u0 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
+    const double u1 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+    const double u2 = ((double)w.z + 0.5) * 2.3283064365386963e-10;
+    const double u3 = ((double)w.w + 0.5) * 2.3283064365386963e-10;
+    const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+    double s1, c1, s3, c3;
+    sincospi(2.0 * u1, &s1, &c1);
+    sincospi(2.0 * u3, &s3, &c3);
+    g[0] = r0 * c1;
+    g[1] = r0 * s1;
+    g[2] = r1 * c3;
+}
+__device__ __forceinline__ void langevin_normals(uint32_t id, uint32_t step, const Rep &rp,
+                                                 float g[3])
+{
+    const uint4 w = philox10(make_uint4(id, step, 0u, (rp.tag_rbe & ~0xFFu) | RBMD_STREAM_LANGEVIN),
+                             rp.key);
+    const float u0 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-8f;  // 2^-24
+    const float u1 = ((float)(w.y >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float u3 = ((float)(w.w >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    g[0] = r0 * c1;
+    g[1] = r0 * s1;
+    g[2] = r1 * c3;
+}
+
 // Second half kick and FP64 kinetic-energy block partials; non-finite
-// velocities latch RBMD_ERR_NONFINITE.
+// velocities latch RBMD_ERR_NONFINITE.  With the Langevin thermostat the
+// friction and random force F_L = -gamma v + sqrt(2 gamma T0 / dt) G of the
+// half-step velocity v is added to the force first, and kept in F for the next
+// step's first half kick.
 template <typename real>
-__global__ void k_kick_ke(real *__restrict__ v, const real *__restrict__ F,
+__global__ void k_kick_ke(real *__restrict__ v, real *__restrict__ F,
                           const int2 *__restrict__ map, const Rep *__restrict__ reps,
                           const double *__restrict__ scal, real hdt, double *__restrict__ kepart,
-                          int *__restrict__ err)
+                          int *__restrict__ err, int langevin, double gamma, double dt,
+                          StepRef sref)
 {
     const AtomSlot a = atom_slot(map, reps);
     double ke = 0.0;
     if (a.ok) {
         const int64_t i = a.i;
         const double *sc = scal + (int64_t)a.r * SCAL_COUNT;
+        real fl[3] = {0, 0, 0};
+        if (langevin) {
+            const Rep &rp = reps[a.r];
+            real gn[3];
+            langevin_normals((uint32_t)(i - rp.atom0), (uint32_t)step_of(sref), rp, gn);
+            const real gm = (real)gamma, sd = (real)sqrt(2.0 * gamma * rp.T0 / dt);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                fl[d] = -gm * v[3 * i + d] + sd * gn[d];
+                F[3 * i + d] += fl[d];
+            }
+        }
         bool bad = false;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -201,8 +255,15 @@ __global__ void k_kick_ke(real *__restrict__ v, const real *__restrict__ F,
     }
 }
 
-// One block per replica: KE, temperature and the Berendsen factor; block 0
+// One block per replica: KE, temperature and the thermostat factors; block 0
 // optionally advances the device step counter.
+//   Berendsen:   lambda = sqrt(1 + (dt/tau)(T0/T - 1)) in [0.8, 1.25], applied on
+//                read-out and by the next kick;
+//   Langevin:    no rescale;
+//   Nose-Hoover: lambda1 = e^{-xi dt/2} (second half of the step), the end-of-
+//                step update xi += dt/2 (2K' - g T0)/Q with K' = lambda1^2 K, then
+//                the next step's first update (same K') and lambda2 = e^{-xi dt/2};
+//                read-out uses lambda1, the next kick lambda1 lambda2.
 __global__ void k_thermo(const double *__restrict__ kepart, const Rep *__restrict__ reps,
                          double *__restrict__ scal, int thermostat, double dt, double tau,
                          int64_t *__restrict__ d_step, int advance)
@@ -219,16 +280,49 @@ __global__ void k_thermo(const double *__restrict__ kepart, const Rep *__restric
     }
     if (threadIdx.x != 0) return;
     const double ke = 0.5 * s[0];
-    double lam = 1.0;
+    double *sc = scal + (int64_t)blockIdx.x * SCAL_COUNT;
+    double lam = 1.0, lam_kick = 1.0;
+    const double g = 3.0 * (double)rp.N - 3.0;
     if (thermostat == 1 && rp.N > 1) {
-        const double T = 2.0 * ke / (3.0 * (double)rp.N - 3.0);
+        const double T = 2.0 * ke / g;
         lam = sqrt(1.0 + (dt / tau) * (rp.T0 / T - 1.0));
         lam = fmin(fmax(lam, 0.8), 1.25);
+        lam_kick = lam;
+    } else if (thermostat == 3 && rp.N > 1) {
+        const double Q = g * rp.T0 * tau * tau;
+        const double lam1 = exp(-0.5 * dt * sc[SCAL_XI_RUN]);
+        const double k1 = lam1 * lam1 * ke;
+        const double xi_b = sc[SCAL_XI_RUN] + 0.5 * dt * (2.0 * k1 - g * rp.T0) / Q;
+        const double xi_r = xi_b + 0.5 * dt * (2.0 * k1 - g * rp.T0) / Q;
+        sc[SCAL_XI] = xi_b;
+        sc[SCAL_XI_RUN] = xi_r;
+        lam = lam1;
+        lam_kick = lam1 * exp(-0.5 * dt * xi_r);
     }
-    double *sc = scal + (int64_t)blockIdx.x * SCAL_COUNT;
     sc[SCAL_KE] = ke;
     sc[SCAL_LAMBDA] = lam;
+    sc[SCAL_LAMBDA_KICK] = lam_kick;
     if (advance && blockIdx.x == 0) *d_step += 1;
+}
+
+// Before the first step of a run (Nose-Hoover only): the first half update of the
+// step, xi_run = xi + dt/2 (2K - g T0)/Q with K the kinetic energy of the read-out
+// velocities (SCAL_KE_TRUE), and the kick factor lambda e^{-xi_run dt/2}.
+__global__ void k_nh_prepare(const Rep *__restrict__ reps, int R, double *__restrict__ scal,
+                             double dt, double tau)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const Rep rp = reps[r];
+    double *sc = scal + (int64_t)r * SCAL_COUNT;
+    if (rp.N < 2) {
+        sc[SCAL_LAMBDA_KICK] = sc[SCAL_LAMBDA];
+        return;
+    }
+    const double g = 3.0 * (double)rp.N - 3.0, Q = g * rp.T0 * tau * tau;
+    const double xi_r = sc[SCAL_XI] + 0.5 * dt * (2.0 * sc[SCAL_KE_TRUE] - g * rp.T0) / Q;
+    sc[SCAL_XI_RUN] = xi_r;
+    sc[SCAL_LAMBDA_KICK] = sc[SCAL_LAMBDA] * exp(-0.5 * dt * xi_r);
 }
 
 rbmd_status md_kick_drift(rbmd_ctx *c)
@@ -245,17 +339,21 @@ rbmd_status md_kick_drift(rbmd_ctx *c)
     return RBMD_OK;
 }
 
-rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step)
+rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step, StepRef sref)
 {
     const double hdt = 0.5 * c->prm.dt;
+    const int lgv = c->prm.thermostat == 2 ? 1 : 0;
+    const double gamma = 1.0 / c->tau;
     if (c->fp64)
-        k_kick_ke<double><<<c->nb256, 256, 0, c->stream>>>((double *)c->vel, (const double *)c->force,
+        k_kick_ke<double><<<c->nb256, 256, 0, c->stream>>>((double *)c->vel, (double *)c->force,
                                                            c->map256, c->reps, c->scal, hdt,
-                                                           c->kepart, c->err);
+                                                           c->kepart, c->err, lgv, gamma,
+                                                           c->prm.dt, sref);
     else
-        k_kick_ke<float><<<c->nb256, 256, 0, c->stream>>>((float *)c->vel, (const float *)c->force,
+        k_kick_ke<float><<<c->nb256, 256, 0, c->stream>>>((float *)c->vel, (float *)c->force,
                                                           c->map256, c->reps, c->scal, (float)hdt,
-                                                          c->kepart, c->err);
+                                                          c->kepart, c->err, lgv, gamma,
+                                                          c->prm.dt, sref);
     RBMD_LAUNCH_CHECK();
     k_thermo<<<c->R, 1024, 0, c->stream>>>(c->kepart, c->reps, c->scal, c->prm.thermostat,
                                           c->prm.dt, c->tau, c->d_step, advance_step ? 1 : 0);
@@ -316,6 +414,16 @@ rbmd_status md_kinetic(rbmd_ctx *c, int slot)
                                                           c->reps, c->scal, c->kepart);
     RBMD_LAUNCH_CHECK();
     k_sum_ke<<<c->R, 1024, 0, c->stream>>>(c->kepart, c->reps, c->scal, slot);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+rbmd_status md_thermo_prepare(rbmd_ctx *c)
+{
+    if (c->prm.thermostat != 3) return RBMD_OK;
+    RBMD_CHECK(md_kinetic(c, SCAL_KE_TRUE));
+    k_nh_prepare<<<(c->R + 127) / 128, 128, 0, c->stream>>>(c->reps, c->R, c->scal, c->prm.dt,
+                                                            c->tau);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }

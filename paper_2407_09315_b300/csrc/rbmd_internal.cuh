@@ -24,6 +24,7 @@
 
 #define RBMD_STREAM_RBE 1u
 #define RBMD_STREAM_RBL 2u
+#define RBMD_STREAM_LANGEVIN 3u
 #define RBMD_MAX_ATTEMPTS 256
 #define RBMD_MAX_TYPES 64
 #define RBMD_MAX_P 128
@@ -252,7 +253,10 @@ enum {
     SCAL_KE_TRUE = 11,
     SCAL_FCORR_AUX = 12,  // [3] correction of stand-alone force calls
     SCAL_ESELF = 15,      // self energy (kept on the device for batched read-out)
-    SCAL_COUNT = 16
+    SCAL_LAMBDA_KICK = 16,  // factor applied to the stored velocities by the next kick
+    SCAL_XI = 17,         // Nose-Hoover variable at the step boundary
+    SCAL_XI_RUN = 18,     // Nose-Hoover variable during the step (after its first half update)
+    SCAL_COUNT = 20
 };
 
 namespace rbmd {
@@ -290,7 +294,8 @@ rbmd_status adjoint_run(rbmd_ctx *c, double g, void *dpos, void *dq, double *tsu
 
 // MD (md.cu)
 rbmd_status md_kick_drift(rbmd_ctx *c);
-rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step);
+rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step, StepRef s);
+rbmd_status md_thermo_prepare(rbmd_ctx *c);  // Nose-Hoover first half update before a run
 rbmd_status md_sum(rbmd_ctx *c, const double *parts, int nparts, int ncomp, double *out,
                    double scale);
 // Per replica r: out[r * SCAL_COUNT + slot + comp] = scale_r * (sum of the parts of
