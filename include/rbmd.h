@@ -367,7 +367,8 @@ rbmd_status rbmd_sampler_table(double box_length, double alpha, int32_t *M, uint
  *   0 kick+drift, 1 cell sort, 2 RBL list scan, 3 RBL batch selection,
  *   4 RBL pair forces (+ overflow fallback), 5 F_corr reduction,
  *   6 RBE mode sampling, 7 structure-factor partials, 8 structure-factor
- *   final reduction, 9 RBE force kernel, 10 kick+thermostat.
+ *   final reduction, 9 RBE force kernel (which also does the second half kick),
+ *   10 thermostat (and the second half kick when RBE is off).
  * rbmd_profile_read: accumulated milliseconds per stage (host double
  *   [RBMD_PROFILE_STAGES]) and the number of profiled steps; reset != 0 zeroes them.
  * rbmd_step_kernel_count: kernel launches in one step graph (captured on the

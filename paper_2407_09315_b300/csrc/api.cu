@@ -341,9 +341,12 @@ rbmd_status charge_sums(rbmd_ctx *c, bool check_neutral = true)
     return RBMD_OK;
 }
 
+// kick != NULL (the integrator's step): the RBE force kernel also does the second
+// half kick; *kicked tells whether it ran.
 rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool apply_corr,
-                        bool marks = false)
+                        bool marks = false, const StepRef *kick = nullptr, bool *kicked = nullptr)
 {
+    if (kicked) *kicked = false;
     const bool do_rbe = !(c->prm.flags & RBMD_NO_RBE);
     const bool do_rbl = !(c->prm.flags & RBMD_NO_RBL);
     int acc = accumulate;
@@ -368,7 +371,8 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
         if (marks) prof_mark(c, 7);
         RBMD_CHECK(rbe_structure_factors(c, marks ? 8 : -1));
         if (marks) prof_mark(c, 9);
-        RBMD_CHECK(rbe_apply_forces(c, force, acc));
+        RBMD_CHECK(rbe_apply_forces(c, force, acc, kick));
+        if (kicked && kick) *kicked = true;
         acc = 1;
     } else if (marks) {
         for (int k = 7; k <= 9; ++k) prof_mark(c, k);
@@ -383,9 +387,10 @@ rbmd_status record_step(rbmd_ctx *c)
     StepRef next{c->d_step, 1};
     prof_mark(c, 0);
     RBMD_CHECK(md_kick_drift(c));
-    RBMD_CHECK(forces_into(c, next, c->force, 0, false, true));
+    bool kicked = false;
+    RBMD_CHECK(forces_into(c, next, c->force, 0, false, true, &next, &kicked));
     prof_mark(c, 10);
-    RBMD_CHECK(md_kick_thermo(c, true, next));
+    RBMD_CHECK(md_kick_thermo(c, true, next, kicked));
     prof_mark(c, 11);
     return RBMD_OK;
 }

@@ -167,92 +167,20 @@ __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
     u4[i] = A;
 }
 
-// Standard normal deviates of the Langevin force (thermostat 2) of replica-local
-// atom `id` at force evaluation `step`: Philox4x32-10, key = seed, counter
-// (id, step, 0, 3 | replica << 8), uniforms (w + 1/2) 2^-32, Box-Muller.
-__device__ __forceinline__ void langevin_normals(uint32_t id, uint32_t step, const Rep &rp,
-                                                 double g[3])
-{
-    const uint4 w = philox10(make_uint4(id, step, 0u, (rp.tag_rbe & ~0xFFu) | RBMD_STREAM_LANGEVIN),
-                             rp.key);
-    const double u0 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
-    const double u1 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
-    const double u2 = ((double)w.z + 0.5) * 2.3283064365386963e-10;
-    const double u3 = ((double)w.w + 0.5) * 2.3283064365386963e-10;
-    const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
-    double s1, c1, s3, c3;
-    sincospi(2.0 * u1, &s1, &c1);
-    sincospi(2.0 * u3, &s3, &c3);
-    g[0] = r0 * c1;
-    g[1] = r0 * s1;
-    g[2] = r1 * c3;
-}
-__device__ __forceinline__ void langevin_normals(uint32_t id, uint32_t step, const Rep &rp,
-                                                 float g[3])
-{
-    const uint4 w = philox10(make_uint4(id, step, 0u, (rp.tag_rbe & ~0xFFu) | RBMD_STREAM_LANGEVIN),
-                             rp.key);
-    const float u0 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-8f;  // 2^-24
-    const float u1 = ((float)(w.y >> 8) + 0.5f) * 5.9604644775390625e-8f;
-    const float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604644775390625e-8f;
-    const float u3 = ((float)(w.w >> 8) + 0.5f) * 5.9604644775390625e-8f;
-    const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
-    float s1, c1, s3, c3;
-    sincospif(2.0f * u1, &s1, &c1);
-    sincospif(2.0f * u3, &s3, &c3);
-    g[0] = r0 * c1;
-    g[1] = r0 * s1;
-    g[2] = r1 * c3;
-}
-
-// Second half kick and FP64 kinetic-energy block partials; non-finite
-// velocities latch RBMD_ERR_NONFINITE.  With the Langevin thermostat the
-// friction and random force F_L = -gamma v + sqrt(2 gamma T0 / dt) G of the
-// half-step velocity v is added to the force first, and kept in F for the next
-// step's first half kick.
+// Second half kick and FP64 kinetic-energy block partials (second_kick); used when
+// the step has no RBE force kernel to carry the kick in its epilogue.
 template <typename real>
 __global__ void k_kick_ke(real *__restrict__ v, real *__restrict__ F,
                           const int2 *__restrict__ map, const Rep *__restrict__ reps,
-                          const double *__restrict__ scal, real hdt, double *__restrict__ kepart,
-                          int *__restrict__ err, int langevin, double gamma, double dt,
-                          StepRef sref)
+                          KickArgs<real> k)
 {
     const AtomSlot a = atom_slot(map, reps);
     double ke = 0.0;
     if (a.ok) {
-        const int64_t i = a.i;
-        const double *sc = scal + (int64_t)a.r * SCAL_COUNT;
-        real fl[3] = {0, 0, 0};
-        if (langevin) {
-            const Rep &rp = reps[a.r];
-            real gn[3];
-            langevin_normals((uint32_t)(i - rp.atom0), (uint32_t)step_of(sref), rp, gn);
-            const real gm = (real)gamma, sd = (real)sqrt(2.0 * gamma * rp.T0 / dt);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                fl[d] = -gm * v[3 * i + d] + sd * gn[d];
-                F[3 * i + d] += fl[d];
-            }
-        }
-        bool bad = false;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            real vd = v[3 * i + d] + hdt * (F[3 * i + d] + (real)sc[SCAL_FCORR + d]);
-            v[3 * i + d] = vd;
-            bad |= !isfinite(vd);
-            ke += (double)vd * (double)vd;
-        }
-        if (bad) latch_error(err, RBMD_ERR_NONFINITE);
+        real f[3] = {F[3 * a.i], F[3 * a.i + 1], F[3 * a.i + 2]};
+        ke = second_kick(k, reps[a.r], a.r, a.i, v, F, f);
     }
-    for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
-    __shared__ double s[32];
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = ke;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
-        kepart[blockIdx.x] = t;
-    }
+    block_ke_partial(ke, k.kepart);
 }
 
 // One block per replica: KE, temperature and the thermostat factors; block 0
@@ -339,22 +267,35 @@ rbmd_status md_kick_drift(rbmd_ctx *c)
     return RBMD_OK;
 }
 
-rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step, StepRef sref)
+template <typename real>
+KickArgs<real> kick_args(rbmd_ctx *c, StepRef sref)
 {
-    const double hdt = 0.5 * c->prm.dt;
-    const int lgv = c->prm.thermostat == 2 ? 1 : 0;
-    const double gamma = 1.0 / c->tau;
-    if (c->fp64)
-        k_kick_ke<double><<<c->nb256, 256, 0, c->stream>>>((double *)c->vel, (double *)c->force,
-                                                           c->map256, c->reps, c->scal, hdt,
-                                                           c->kepart, c->err, lgv, gamma,
-                                                           c->prm.dt, sref);
-    else
-        k_kick_ke<float><<<c->nb256, 256, 0, c->stream>>>((float *)c->vel, (float *)c->force,
-                                                          c->map256, c->reps, c->scal, (float)hdt,
-                                                          c->kepart, c->err, lgv, gamma,
-                                                          c->prm.dt, sref);
-    RBMD_LAUNCH_CHECK();
+    KickArgs<real> k;
+    k.v = (real *)c->vel;
+    k.scal = c->scal;
+    k.hdt = (real)(0.5 * c->prm.dt);
+    k.kepart = c->kepart;
+    k.err = c->err;
+    k.langevin = c->prm.thermostat == 2 ? 1 : 0;
+    k.gamma = 1.0 / c->tau;
+    k.dt = c->prm.dt;
+    k.sref = sref;
+    return k;
+}
+template KickArgs<float> kick_args<float>(rbmd_ctx *, StepRef);
+template KickArgs<double> kick_args<double>(rbmd_ctx *, StepRef);
+
+rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step, StepRef sref, bool kicked)
+{
+    if (!kicked) {
+        if (c->fp64)
+            k_kick_ke<double><<<c->nb256, 256, 0, c->stream>>>(
+                (double *)c->vel, (double *)c->force, c->map256, c->reps, kick_args<double>(c, sref));
+        else
+            k_kick_ke<float><<<c->nb256, 256, 0, c->stream>>>(
+                (float *)c->vel, (float *)c->force, c->map256, c->reps, kick_args<float>(c, sref));
+        RBMD_LAUNCH_CHECK();
+    }
     k_thermo<<<c->R, 1024, 0, c->stream>>>(c->kepart, c->reps, c->scal, c->prm.thermostat,
                                           c->prm.dt, c->tau, c->d_step, advance_step ? 1 : 0);
     RBMD_LAUNCH_CHECK();

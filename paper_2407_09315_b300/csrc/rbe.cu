@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
             re += s_acc[s * mode_tile + l].x;
             im += s_acc[s * mode_tile + l].y;
         }
-        part[(int64_t)blockIdx.x * Pm + l0 + l] = make_double2(re, im);
+        part[(l0 + l) * (int64_t)gridDim.x + blockIdx.x] = make_double2(re, im);
     }
 }
 
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
 //   c_l = -(4 pi coulomb_k / V) W_l / k_l^2,  A_l = c_l Im rho_l,  B_l = c_l Re rho_l,
 //   e_l = coulomb_k (2 pi / V) W_l |rho_l|^2 / k_l^2   (energy estimate term).
 template <typename real>
-__global__ void k_rho_final(const double2 *__restrict__ part, const Rep *__restrict__ reps, int R,
+__global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, const Rep *__restrict__ reps, int R,
                             int64_t Pm, const int4 *__restrict__ modes,
                             const double *__restrict__ W, double ck, double2 *__restrict__ rho,
                             double *__restrict__ emode, ModeCoef<real> *__restrict__ coef)
@@ -220,7 +220,7 @@ __global__ void k_rho_final(const double2 *__restrict__ part, const Rep *__restr
     const Rep rp = reps[r];
     double re = 0.0, im = 0.0;
     for (int k = lane; k < rp.ntiles; k += 32) {
-        double2 p = part[(int64_t)(rp.tile0 + k) * Pm + lm];
+        double2 p = part[lm * (int64_t)ntiles + rp.tile0 + k];
         re += p.x;
         im += p.y;
     }
@@ -294,7 +294,7 @@ rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
         RBMD_LAUNCH_CHECK();
         if (mark_between >= 0) prof_mark(c, mark_between);
         k_rho_final<double><<<fin_blocks, 256, 0, c->stream>>>(
-            c->rho_part, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
+            c->rho_part, c->ntiles, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
             (ModeCoef<double> *)c->coef);
     } else {
         k_rho_partial<float><<<grid, threads, smem, c->stream>>>(
@@ -302,7 +302,7 @@ rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
         RBMD_LAUNCH_CHECK();
         if (mark_between >= 0) prof_mark(c, mark_between);
         k_rho_final<float><<<fin_blocks, 256, 0, c->stream>>>(
-            c->rho_part, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
+            c->rho_part, c->ntiles, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
             (ModeCoef<float> *)c->coef);
     }
     RBMD_LAUNCH_CHECK();
@@ -316,11 +316,14 @@ rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
 // than stored per atom-mode (N P complex numbers would cost more HBM traffic
 // than the recomputation).
 // --------------------------------------------------------------------------
-template <typename real, int CHUNK>
+// With KICK (the integrator's step) the epilogue also performs the second half
+// kick of the atom with its final force and writes the block's kinetic-energy
+// partial, saving a pass over the forces and velocities.
+template <typename real, int CHUNK, bool KICK>
 __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restrict__ q64,
                             const int2 *__restrict__ map, const Rep *__restrict__ reps,
                             const ModeCoef<real> *__restrict__ coef_all, int64_t Pm,
-                            real *__restrict__ F, int accumulate)
+                            real *__restrict__ F, int accumulate, KickArgs<real> kick)
 {
     __shared__ ModeCoef<real> s_c[CHUNK];
     const AtomSlot sl = atom_slot(map, reps);  // the whole block belongs to replica sl.r
@@ -349,33 +352,51 @@ __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restri
             }
         }
     }
-    if (!active) return;
-    real q;
-    if constexpr (sizeof(real) == 4) q = __uint_as_float(A.w);
-    else q = q64[i];
-    const real s = q * tk;
-    real *f = F + 3 * i;
-    if (accumulate) {
-        f[0] += s * fx;
-        f[1] += s * fy;
-        f[2] += s * fz;
-    } else {
-        f[0] = s * fx;
-        f[1] = s * fy;
-        f[2] = s * fz;
+    double ke = 0.0;
+    if (active) {
+        real q;
+        if constexpr (sizeof(real) == 4) q = __uint_as_float(A.w);
+        else q = q64[i];
+        const real s = q * tk;
+        real *f = F + 3 * i;
+        real fo[3] = {s * fx, s * fy, s * fz};
+        if (accumulate) {
+            fo[0] += f[0];
+            fo[1] += f[1];
+            fo[2] += f[2];
+        }
+        f[0] = fo[0];
+        f[1] = fo[1];
+        f[2] = fo[2];
+        if constexpr (KICK) ke = second_kick(kick, reps[sl.r], sl.r, i, kick.v, F, fo);
     }
+    if constexpr (KICK) block_ke_partial(ke, kick.kepart);
 }
 
-rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate)
+rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate, const StepRef *kick)
 {
     if (c->fp64) {
-        k_rbe_force<double, 128><<<c->nb256, 256, 0, c->stream>>>(
-            c->u4, c->q64, c->map256, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
-            (double *)force, accumulate);
+        KickArgs<double> k{};
+        if (kick) k = kick_args<double>(c, *kick);
+        if (kick)
+            k_rbe_force<double, 128, true><<<c->nb256, 256, 0, c->stream>>>(
+                c->u4, c->q64, c->map256, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
+                (double *)force, accumulate, k);
+        else
+            k_rbe_force<double, 128, false><<<c->nb256, 256, 0, c->stream>>>(
+                c->u4, c->q64, c->map256, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
+                (double *)force, accumulate, k);
     } else {
-        k_rbe_force<float, 256><<<c->nb256, 256, 0, c->stream>>>(
-            c->u4, nullptr, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
-            (float *)force, accumulate);
+        KickArgs<float> k{};
+        if (kick) k = kick_args<float>(c, *kick);
+        if (kick)
+            k_rbe_force<float, 256, true><<<c->nb256, 256, 0, c->stream>>>(
+                c->u4, nullptr, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
+                (float *)force, accumulate, k);
+        else
+            k_rbe_force<float, 256, false><<<c->nb256, 256, 0, c->stream>>>(
+                c->u4, nullptr, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
+                (float *)force, accumulate, k);
     }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;

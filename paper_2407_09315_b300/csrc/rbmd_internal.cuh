@@ -187,7 +187,7 @@ struct rbmd_ctx {
     uint64_t *cdf;        // sampler thresholds of every replica (2M_r + 1 each)
     int4 *modes;          // [R][Pm]
     double *W;            // [Pm] weights (full-mode list, one replica), else NULL
-    double2 *rho_part;    // [ntiles][Pm]
+    double2 *rho_part;    // [Pm][ntiles] mode-major, so a warp sums one mode over consecutive tiles
     double2 *rho;         // [R][Pm]
     double *emode;        // [R][Pm]
     void *coef;           // ModeCoef<real>[R][Pm]
@@ -273,12 +273,113 @@ inline void prof_mark(rbmd_ctx *c, int k)
 rbmd_status sampler_table_host(double L, double alpha, int32_t *M, uint64_t *T, double *H);
 
 // RBE (rbe.cu)
+// Standard normal deviates of the Langevin force (thermostat 2) of replica-local
+// atom `id` at force evaluation `step`: Philox4x32-10, key = seed, counter
+// (id, step, 0, 3 | replica << 8), uniforms (w + 1/2) 2^-32, Box-Muller.
+__device__ __forceinline__ void langevin_normals(uint32_t id, uint32_t step, const Rep &rp,
+                                                 double g[3])
+{
+    const uint4 w = philox10(make_uint4(id, step, 0u, (rp.tag_rbe & ~0xFFu) | RBMD_STREAM_LANGEVIN),
+                             rp.key);
+    const double u0 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
+    const double u1 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+    const double u2 = ((double)w.z + 0.5) * 2.3283064365386963e-10;
+    const double u3 = ((double)w.w + 0.5) * 2.3283064365386963e-10;
+    const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+    double s1, c1, s3, c3;
+    sincospi(2.0 * u1, &s1, &c1);
+    sincospi(2.0 * u3, &s3, &c3);
+    g[0] = r0 * c1;
+    g[1] = r0 * s1;
+    g[2] = r1 * c3;
+}
+__device__ __forceinline__ void langevin_normals(uint32_t id, uint32_t step, const Rep &rp,
+                                                 float g[3])
+{
+    const uint4 w = philox10(make_uint4(id, step, 0u, (rp.tag_rbe & ~0xFFu) | RBMD_STREAM_LANGEVIN),
+                             rp.key);
+    const float u0 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-8f;  // 2^-24
+    const float u1 = ((float)(w.y >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float u3 = ((float)(w.w >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    g[0] = r0 * c1;
+    g[1] = r0 * s1;
+    g[2] = r1 * c3;
+}
+
+// Arguments of the second half kick.
+template <typename real> struct KickArgs {
+    real *v;
+    const double *scal;
+    real hdt;
+    double *kepart;  // [nb256] kinetic-energy partial of each 256-atom block
+    int *err;
+    int langevin;    // thermostat 2: add the friction and random force first
+    double gamma, dt;
+    StepRef sref;    // step of the force evaluation (Langevin counter)
+};
+
+// Second half kick of atom i of replica r with force f (the atom's final force
+// of the step, stored to F when the Langevin force is added to it); returns
+// |v|^2.  Non-finite velocities latch RBMD_ERR_NONFINITE.
+template <typename real>
+__device__ __forceinline__ double second_kick(const KickArgs<real> &k, const Rep &rp, int r,
+                                              int64_t i, real *__restrict__ v, real *__restrict__ F,
+                                              real f[3])
+{
+    const double *sc = k.scal + (int64_t)r * SCAL_COUNT;
+    if (k.langevin) {
+        real gn[3];
+        langevin_normals((uint32_t)(i - rp.atom0), (uint32_t)step_of(k.sref), rp, gn);
+        const real gm = (real)k.gamma, sd = (real)sqrt(2.0 * k.gamma * rp.T0 / k.dt);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            f[d] += -gm * v[3 * i + d] + sd * gn[d];
+            F[3 * i + d] = f[d];
+        }
+    }
+    double ke = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const real vd = v[3 * i + d] + k.hdt * (f[d] + (real)sc[SCAL_FCORR + d]);
+        v[3 * i + d] = vd;
+        bad |= !isfinite(vd);
+        ke += (double)vd * (double)vd;
+    }
+    if (bad) latch_error(k.err, RBMD_ERR_NONFINITE);
+    return ke;
+}
+
+// Block sum of ke (every thread of the 256-thread block calls it) to kepart[block].
+__device__ __forceinline__ void block_ke_partial(double ke, double *__restrict__ kepart)
+{
+    for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
+    __shared__ double s_ke[32];
+    if ((threadIdx.x & 31) == 0) s_ke[threadIdx.x >> 5] = ke;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_ke[w];
+        kepart[blockIdx.x] = t;
+    }
+}
+
+template <typename real> KickArgs<real> kick_args(rbmd_ctx *c, StepRef sref);
+
 rbmd_status rbe_sample(rbmd_ctx *c, StepRef s);
 rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between = -1);
 rbmd_status rbe_configure(rbmd_ctx *c);  // kernel attributes (dynamic shared memory)
 rbmd_status pair_table_host(double alpha, double r_cut, int n, std::vector<double> &coef,
                             int32_t *i0, double *inv_h);
-rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate);
+// kick != NULL: the integrator's step; the kernel also does the second half kick
+// (KickArgs of that step) and the kinetic-energy partials.
+rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate,
+                             const StepRef *kick = nullptr);
 
 // RBL (rbl.cu)
 rbmd_status cells_build(rbmd_ctx *c);
@@ -294,7 +395,9 @@ rbmd_status adjoint_run(rbmd_ctx *c, double g, void *dpos, void *dq, double *tsu
 
 // MD (md.cu)
 rbmd_status md_kick_drift(rbmd_ctx *c);
-rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step, StepRef s);
+// Second half kick (unless `kicked`: the RBE force kernel already did it) and the
+// thermostat; advance_step increments the device step counter.
+rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step, StepRef s, bool kicked);
 rbmd_status md_thermo_prepare(rbmd_ctx *c);  // Nose-Hoover first half update before a run
 rbmd_status md_sum(rbmd_ctx *c, const double *parts, int nparts, int ncomp, double *out,
                    double scale);
