@@ -344,7 +344,8 @@ rbmd_status charge_sums(rbmd_ctx *c, bool check_neutral = true)
 // kick != NULL (the integrator's step): the RBE force kernel also does the second
 // half kick; *kicked tells whether it ran.
 rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool apply_corr,
-                        bool marks = false, const StepRef *kick = nullptr, bool *kicked = nullptr)
+                        bool marks = false, const StepRef *kick = nullptr, bool *kicked = nullptr,
+                        bool counted = false)
 {
     if (kicked) *kicked = false;
     const bool do_rbe = !(c->prm.flags & RBMD_NO_RBE);
@@ -352,7 +353,7 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
     int acc = accumulate;
     if (marks) prof_mark(c, 1);
     if (do_rbl) {
-        RBMD_CHECK(cells_build(c));
+        RBMD_CHECK(cells_build(c, counted));
         if (marks) prof_mark(c, 2);  // stages 3 and 4 are marked inside
         RBMD_CHECK(rbl_pairs(c, s, force, acc, false, nullptr, nullptr, nullptr, marks));
         if (marks) prof_mark(c, 5);
@@ -386,9 +387,10 @@ rbmd_status record_step(rbmd_ctx *c)
 {
     StepRef next{c->d_step, 1};
     prof_mark(c, 0);
-    RBMD_CHECK(md_kick_drift(c));
+    const bool bin = !(c->prm.flags & RBMD_NO_RBL);  // the drift kernel also bins the atoms
+    RBMD_CHECK(md_kick_drift(c, bin));
     bool kicked = false;
-    RBMD_CHECK(forces_into(c, next, c->force, 0, false, true, &next, &kicked));
+    RBMD_CHECK(forces_into(c, next, c->force, 0, false, true, &next, &kicked, bin));
     prof_mark(c, 10);
     RBMD_CHECK(md_kick_thermo(c, true, next, kicked));
     prof_mark(c, 11);

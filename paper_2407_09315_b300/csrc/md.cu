@@ -145,7 +145,8 @@ template <typename real>
 __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
                              const real *__restrict__ F, const int2 *__restrict__ map,
                              const Rep *__restrict__ reps, const double *__restrict__ scal,
-                             real hdt)
+                             real hdt, int32_t *__restrict__ count, int32_t *__restrict__ cell_of,
+                             int32_t *__restrict__ rank)
 {
     const AtomSlot a = atom_slot(map, reps);
     if (!a.ok) return;
@@ -165,6 +166,15 @@ __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
         pu[d] = pu[d] + (uint32_t)du;
     }
     u4[i] = A;
+    if (count) {
+        const Rep &rp = reps[a.r];
+        const int nc = rp.nc;
+        const int64_t c = rp.cell0 +
+                          ((int64_t)cell_coord(A.x, nc) * nc + cell_coord(A.y, nc)) * nc +
+                          cell_coord(A.z, nc);
+        cell_of[i] = (int32_t)c;
+        rank[i] = atomicAdd(&count[c], 1);
+    }
 }
 
 // Second half kick and FP64 kinetic-energy block partials (second_kick); used when
@@ -253,16 +263,20 @@ __global__ void k_nh_prepare(const Rep *__restrict__ reps, int R, double *__rest
     sc[SCAL_LAMBDA_KICK] = sc[SCAL_LAMBDA] * exp(-0.5 * dt * xi_r);
 }
 
-rbmd_status md_kick_drift(rbmd_ctx *c)
+rbmd_status md_kick_drift(rbmd_ctx *c, bool bin)
 {
     const double hdt = 0.5 * c->prm.dt;
+    int32_t *count = bin ? c->cell_count : nullptr;
+    if (bin)
+        RBMD_CHECK_CUDA(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, c->stream));
     if (c->fp64)
         k_kick_drift<double><<<c->nb256, 256, 0, c->stream>>>(
-            c->u4, (double *)c->vel, (const double *)c->force, c->map256, c->reps, c->scal, hdt);
+            c->u4, (double *)c->vel, (const double *)c->force, c->map256, c->reps, c->scal, hdt,
+            count, c->cell_of, c->cell_rank);
     else
         k_kick_drift<float><<<c->nb256, 256, 0, c->stream>>>(
             c->u4, (float *)c->vel, (const float *)c->force, c->map256, c->reps, c->scal,
-            (float)hdt);
+            (float)hdt, count, c->cell_of, c->cell_rank);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }

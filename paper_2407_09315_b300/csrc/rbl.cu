@@ -21,11 +21,6 @@
 
 namespace rbmd {
 
-__device__ __forceinline__ int cell_coord(uint32_t u, int nc)
-{
-    return (int)(((uint64_t)u * (uint64_t)nc) >> 32);
-}
-
 // ---------------------------------------------------------------- binning
 __global__ void k_cell_count(const uint4 *__restrict__ u4, const int2 *__restrict__ map,
                              const Rep *__restrict__ reps, int32_t *__restrict__ count,
@@ -155,14 +150,16 @@ __global__ void k_cell_order(const int32_t *__restrict__ start, int64_t ncell,
     for (int a = b; a < e; ++a) sidx[spos[a].w] = a;
 }
 
-rbmd_status cells_build(rbmd_ctx *c)
+rbmd_status cells_build(rbmd_ctx *c, bool counted)
 {
     const int th = 256;
     const unsigned nb = (unsigned)((c->N + th - 1) / th);
-    RBMD_CHECK_CUDA(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, c->stream));
-    k_cell_count<<<c->nb256, 256, 0, c->stream>>>(c->u4, c->map256, c->reps, c->cell_count,
-                                                   c->cell_of, c->cell_rank);
-    RBMD_LAUNCH_CHECK();
+    if (!counted) {
+        RBMD_CHECK_CUDA(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, c->stream));
+        k_cell_count<<<c->nb256, 256, 0, c->stream>>>(c->u4, c->map256, c->reps, c->cell_count,
+                                                       c->cell_of, c->cell_rank);
+        RBMD_LAUNCH_CHECK();
+    }
     const int ntiles = (int)((c->ncell + SCAN_TILE - 1) / SCAN_TILE);
     k_scan_tiles<<<ntiles, 256, 0, c->stream>>>(c->cell_count, c->ncell, c->scan_part);
     RBMD_LAUNCH_CHECK();

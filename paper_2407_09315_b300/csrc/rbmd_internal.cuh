@@ -117,6 +117,12 @@ __device__ __forceinline__ int64_t lidx(int64_t i, int e, int64_t /*N*/, int cap
     return i * cap + e;
 }
 
+// Cell index along one axis of a fixed-point coordinate for nc cells per axis.
+__device__ __forceinline__ int cell_coord(uint32_t u, int nc)
+{
+    return (int)(((uint64_t)u * (uint64_t)nc) >> 32);
+}
+
 __device__ __forceinline__ AtomSlot atom_slot_at(const int2 *__restrict__ map,
                                                  const Rep *__restrict__ reps, int b)
 {
@@ -382,7 +388,9 @@ rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate,
                              const StepRef *kick = nullptr);
 
 // RBL (rbl.cu)
-rbmd_status cells_build(rbmd_ctx *c);
+// counted: the cell counts, cells and ranks are already there (the integrator's
+// drift kernel bins the atoms it moves).
+rbmd_status cells_build(rbmd_ctx *c, bool counted = false);
 rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
                       int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks = false);
 rbmd_status rbl_correction(rbmd_ctx *c, void *force, bool apply, int slot);
@@ -394,7 +402,9 @@ rbmd_status rbl_max_counts(rbmd_ctx *c, int32_t *out_dev);
 rbmd_status adjoint_run(rbmd_ctx *c, double g, void *dpos, void *dq, double *tsum_dev);
 
 // MD (md.cu)
-rbmd_status md_kick_drift(rbmd_ctx *c);
+// First half kick and drift; with bin, the moved atoms are also binned into the
+// (zeroed) cell counts, as k_cell_count does, for cells_build(c, true).
+rbmd_status md_kick_drift(rbmd_ctx *c, bool bin = false);
 // Second half kick (unless `kicked`: the RBE force kernel already did it) and the
 // thermostat; advance_step increments the device step counter.
 rbmd_status md_kick_thermo(rbmd_ctx *c, bool advance_step, StepRef s, bool kicked);
