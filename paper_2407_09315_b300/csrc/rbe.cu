@@ -12,6 +12,8 @@
 // to a fraction of a turn rounds.
 #include <math.h>
 
+#include <algorithm>
+
 #include "rbmd_internal.cuh"
 
 namespace rbmd {
@@ -65,16 +67,25 @@ __device__ __forceinline__ int draw_axis(uint64_t U, const uint64_t *__restrict_
 // One thread per mode l: attempt t draws U_x, U_y from Philox(l, t, step, stream)
 // and U_z from Philox(l, t | 2^31, step, stream); m = 0 is redrawn (k != 0 in
 // Eq. 12).  After RBMD_MAX_ATTEMPTS zero draws the mode stays 0 (zero weight).
+// Grid (mode blocks, replicas): each block stages its replica's threshold table in
+// shared memory when it fits (SAMPLE_SMEM_MAX entries) and searches it there.
+constexpr int SAMPLE_SMEM_MAX = 6144;  // 48 KB of thresholds
+
 __global__ void k_rbe_sample(const uint64_t *__restrict__ Tall, const Rep *__restrict__ reps,
-                             int R, int64_t P, StepRef sref, int4 *__restrict__ modes)
+                             int64_t P, StepRef sref, int4 *__restrict__ modes)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)R * P) return;
-    const int r = (int)(t / P);
-    const int64_t l = t - (int64_t)r * P;
+    extern __shared__ uint64_t s_T[];
+    const int r = blockIdx.y;
     const Rep rp = reps[r];
+    const int M = rp.M, nT = 2 * M + 1;
     const uint64_t *T = Tall + rp.cdf0;
-    const int M = rp.M;
+    if (nT <= SAMPLE_SMEM_MAX) {
+        for (int j = threadIdx.x; j < nT; j += blockDim.x) s_T[j] = T[j];
+        __syncthreads();
+        T = s_T;
+    }
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= P) return;
     const uint2 key = rp.key;
     const uint32_t step = (uint32_t)step_of(sref);
     const uint32_t tag = rp.tag_rbe;
@@ -87,15 +98,18 @@ __global__ void k_rbe_sample(const uint64_t *__restrict__ Tall, const Rep *__res
         mz = draw_axis(((uint64_t)w2.x << 32) | w2.y, T, M);
         if (mx != 0 || my != 0 || mz != 0) break;
     }
-    modes[t] = make_int4(mx, my, mz, 0);
+    modes[(int64_t)r * P + l] = make_int4(mx, my, mz, 0);
 }
 
 rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
 {
     if (c->full_modes) return RBMD_OK;  // fixed list built at init
     const int threads = 128;
-    const int blocks = (int)((c->R * c->Pm + threads - 1) / threads);
-    k_rbe_sample<<<blocks, threads, 0, c->stream>>>(c->cdf, c->reps, c->R, c->Pm, s, c->modes);
+    const dim3 grid((unsigned)((c->Pm + threads - 1) / threads), (unsigned)c->R);
+    int nmax = 0;
+    for (int r = 0; r < c->R; ++r) nmax = std::max(nmax, 2 * c->reps_h[r].M + 1);
+    const size_t smem = sizeof(uint64_t) * (size_t)std::min(nmax, SAMPLE_SMEM_MAX);
+    k_rbe_sample<<<grid, threads, smem, c->stream>>>(c->cdf, c->reps, c->Pm, s, c->modes);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
@@ -202,8 +216,10 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
     }
 }
 
-// Second stage: one warp per mode sums the atom-tile partials in FP64 (lane-strided,
-// then a fixed xor-shuffle tree), and derives the force and energy coefficients:
+// Second stage: one block of 128 threads (32 when every replica has at most 128
+// tiles) per (replica, mode) sums the atom-tile partials in FP64 (thread-strided,
+// then a fixed shuffle and shared-memory tree),
+// and derives the force and energy coefficients:
 //   c_l = -(4 pi coulomb_k / V) W_l / k_l^2,  A_l = c_l Im rho_l,  B_l = c_l Re rho_l,
 //   e_l = coulomb_k (2 pi / V) W_l |rho_l|^2 / k_l^2   (energy estimate term).
 template <typename real>
@@ -212,14 +228,14 @@ __global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, const 
                             const double *__restrict__ W, double ck, double2 *__restrict__ rho,
                             double *__restrict__ emode, ModeCoef<real> *__restrict__ coef)
 {
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // r Pm + l
+    __shared__ double2 s_p[4];
+    const int64_t t = blockIdx.x;  // r Pm + l
     const int lane = threadIdx.x & 31;
-    if (t >= (int64_t)R * Pm) return;
     const int r = (int)(t / Pm);
     const int64_t lm = t - (int64_t)r * Pm;
     const Rep rp = reps[r];
     double re = 0.0, im = 0.0;
-    for (int k = lane; k < rp.ntiles; k += 32) {
+    for (int k = threadIdx.x; k < rp.ntiles; k += blockDim.x) {
         double2 p = part[lm * (int64_t)ntiles + rp.tile0 + k];
         re += p.x;
         im += p.y;
@@ -229,7 +245,15 @@ __global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, const 
         re += __shfl_xor_sync(0xffffffffu, re, o);
         im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane != 0) return;
+    if (blockDim.x > 32) {
+        if (lane == 0) s_p[threadIdx.x >> 5] = make_double2(re, im);
+        __syncthreads();
+        if (threadIdx.x != 0) return;
+        re = (s_p[0].x + s_p[1].x) + (s_p[2].x + s_p[3].x);
+        im = (s_p[0].y + s_p[1].y) + (s_p[2].y + s_p[3].y);
+    } else if (lane != 0) {
+        return;
+    }
     const int64_t l = t;
     const int4 m = modes[l];
     const double L = rp.L;
@@ -287,13 +311,16 @@ rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
     threads = min(threads, 1024);
     dim3 grid((unsigned)c->ntiles, (unsigned)((c->Pm + mode_tile - 1) / mode_tile));
     const size_t smem = rho_smem(c->fp64, tile, mode_tile, sub);
-    const unsigned fin_blocks = (unsigned)((c->R * c->Pm * 32 + 255) / 256);
+    const unsigned fin_blocks = (unsigned)(c->R * c->Pm);
+    int max_tiles = 0;
+    for (int r = 0; r < c->R; ++r) max_tiles = std::max(max_tiles, (int)c->reps_h[r].ntiles);
+    const int fin_threads = max_tiles > 128 ? 128 : 32;
     if (c->fp64) {
         k_rho_partial<double><<<grid, threads, smem, c->stream>>>(
             c->u4, c->q64, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
         RBMD_LAUNCH_CHECK();
         if (mark_between >= 0) prof_mark(c, mark_between);
-        k_rho_final<double><<<fin_blocks, 256, 0, c->stream>>>(
+        k_rho_final<double><<<fin_blocks, fin_threads, 0, c->stream>>>(
             c->rho_part, c->ntiles, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
             (ModeCoef<double> *)c->coef);
     } else {
@@ -301,7 +328,7 @@ rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
             c->u4, nullptr, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
         RBMD_LAUNCH_CHECK();
         if (mark_between >= 0) prof_mark(c, mark_between);
-        k_rho_final<float><<<fin_blocks, 256, 0, c->stream>>>(
+        k_rho_final<float><<<fin_blocks, fin_threads, 0, c->stream>>>(
             c->rho_part, c->ntiles, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
             (ModeCoef<float> *)c->coef);
     }
