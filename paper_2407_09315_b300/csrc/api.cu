@@ -208,7 +208,7 @@ void free_ctx(rbmd_ctx *c)
                     c->epart,     c->kepart,    c->ibuf,     c->lj_f,       c->lj_d,
                     c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp,
                     c->adj_lj,    c->adj_tpart, c->adj_tsum, c->reps,       c->map256,
-                    c->map128,    c->tiles,     c->red_rep,   c->ptab};
+                    c->map128,    c->tiles,     c->red_rep,   c->ptab,       c->heavy};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -634,6 +634,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(alloc_n(&c->lshell, (size_t)N * c->list_cs));
     TRY(alloc_n(&c->ncount, (size_t)N));
     TRY(alloc_n(&c->bk, (size_t)N * p.rbl_p));
+    if (p.rbl_p > 10) TRY(alloc_n(&c->heavy, (size_t)N));
     TRY(dev_alloc(&c->adj_lj, 2 * (size_t)c->T * rs));
     TRY(alloc_n(&c->adj_tpart, (size_t)c->nb128 * 2 * c->T));
     TRY(alloc_n(&c->adj_tsum, 2 * (size_t)c->T));

@@ -233,6 +233,8 @@ template <typename real> struct PairArgs {
     int2 *ncount;      // [N] (|C|, N_s)
     int32_t *bk;       // [N][p] sorted indices of the batch
     const int32_t *sidx;  // [N] sorted index of every atom (by global id)
+    int2 *heavy;          // [N] (sorted index, replica) of atoms with N_s > p (p > 10)
+    int32_t *heavy_n;     // [1] their count
     int32_t *ovf;      // [0] set when any list overflowed
     int CC, CS;
 };
@@ -575,12 +577,9 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
 // The shell list holds atom ids, so a priority needs one list load and no
 // lookup; only the p winners are mapped to sorted indices.
 template <typename real, int CAP, bool LISTS>
-__global__ void __launch_bounds__(256, (CAP <= 10 ? 3 : 1)) k_rbl_select(PairArgs<real> a)
+__device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is, int r)
 {
-    const AtomSlot sl = atom_slot(a.map, a.reps);
-    if (!sl.ok) return;
-    const int64_t is = sl.i;
-    const Rep rp = a.reps[sl.r];
+    const Rep rp = a.reps[r];
     const uint32_t id0 = (uint32_t)rp.atom0;
     const int2 cnt = a.ncount[is];
     if (overflowed(a, cnt)) return;
@@ -622,6 +621,70 @@ __global__ void __launch_bounds__(256, (CAP <= 10 ? 3 : 1)) k_rbl_select(PairArg
         for (int e = 0; e < a.p; ++e) out[e] = -1;
         for (int e = 0; e < nb; ++e) {
             const int32_t v = (int32_t)(ids[e] + id0);
+            int y = e - 1;
+            while (y >= 0 && out[y] > v) {
+                out[y + 1] = out[y];
+                --y;
+            }
+            out[y + 1] = v;
+        }
+    }
+}
+
+// One thread per cell-sorted atom (p <= 10).
+template <typename real, int CAP, bool LISTS>
+__global__ void __launch_bounds__(256, 3) k_rbl_select(PairArgs<real> a)
+{
+    const AtomSlot sl = atom_slot(a.map, a.reps);
+    if (sl.ok) select_atom<real, CAP, LISTS>(a, sl.i, sl.r);
+}
+
+// p > 10: the register heap is large, so the kernel runs a grid-stride loop over
+// the compact list of atoms that need a selection (N_s > p), made by
+// k_rbl_take_shell; each atom's output depends on that atom only, so the list
+// order does not matter.
+template <typename real, int CAP, bool LISTS>
+__global__ void __launch_bounds__(256) k_rbl_select_list(PairArgs<real> a)
+{
+    const int32_t n = *a.heavy_n;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int2 h = a.heavy[j];
+        select_atom<real, CAP, LISTS>(a, h.x, h.y);
+    }
+}
+
+// Step 1b for atoms with N_s <= p: the batch is the whole shell (weight 1); the
+// others go to the list of k_rbl_select_list.
+template <typename real, bool LISTS>
+__global__ void __launch_bounds__(256) k_rbl_take_shell(PairArgs<real> a)
+{
+    const AtomSlot sl = atom_slot(a.map, a.reps);
+    if (!sl.ok) return;
+    const int64_t is = sl.i;
+    const int2 cnt = a.ncount[is];
+    const bool heavy = !overflowed(a, cnt) && cnt.y > a.p;
+    // warp-aggregated append of the atoms that need a selection
+    const unsigned m = __ballot_sync(__activemask(), heavy);
+    if (heavy) {
+        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(a.heavy_n, __popc(m));
+        base = __shfl_sync(m, base, leader);
+        a.heavy[base + __popc(m & ((1u << lane) - 1))] = make_int2((int)is, sl.r);
+        return;
+    }
+    if (overflowed(a, cnt)) return;
+    const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
+    const int64_t N = a.N;
+    const int32_t *ls = a.lshell + lidx(is, 0, N, a.CS);
+    for (int e = 0; e < cnt.y; ++e) a.bk[lidx(is, e, N, a.p)] = a.sidx[id0 + (uint32_t)ls[e]];
+    if constexpr (LISTS) {
+        // batch ids ascending, -1 padded (verification path only)
+        int32_t *out = a.batch + (int64_t)a.spos[is].w * a.p;
+        for (int e = 0; e < a.p; ++e) out[e] = -1;
+        for (int e = 0; e < cnt.y; ++e) {
+            const int32_t v = (int32_t)(ls[e] + id0);
             int y = e - 1;
             while (y >= 0 && out[y] > v) {
                 out[y + 1] = out[y];
@@ -867,6 +930,21 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
     }
 }
 
+// Batch selection over the 256-atom block map: one kernel for p <= 10; above, the
+// light kernel takes whole shells and lists the rest for the heap kernel.
+template <typename real, int CAP, bool LISTS>
+static void launch_select(const PairArgs<real> &a256, unsigned nb256, cudaStream_t st)
+{
+    if constexpr (CAP <= 10) {
+        k_rbl_select<real, CAP, LISTS><<<nb256, 256, 0, st>>>(a256);
+    } else {
+        cudaMemsetAsync(a256.heavy_n, 0, sizeof(int32_t), st);
+        k_rbl_take_shell<real, LISTS><<<nb256, 256, 0, st>>>(a256);
+        // one resident block per SM at this register count, a few waves of work
+        k_rbl_select_list<real, CAP, LISTS><<<min(nb256, 2u * 148u), 256, 0, st>>>(a256);
+    }
+}
+
 template <typename real, int CAP>
 static void launch_rbl(rbmd_ctx *c, const PairArgs<real> &a, cudaStream_t st, bool energy,
                        bool lists, bool marks)
@@ -882,12 +960,12 @@ static void launch_rbl(rbmd_ctx *c, const PairArgs<real> &a, cudaStream_t st, bo
         if (energy) k_rbl_scan<real, true, true><<<nb256, 256, 0, st>>>(a256);
         else k_rbl_scan<real, false, true><<<nb256, 256, 0, st>>>(a256);
         if (marks) prof_mark(c, 3);
-        if (!a.exact) k_rbl_select<real, CAP, true><<<nb256, 256, 0, st>>>(a256);
+        if (!a.exact) launch_select<real, CAP, true>(a256, nb256, st);
     } else {
         if (energy) k_rbl_scan<real, true, false><<<nb256, 256, 0, st>>>(a256);
         else k_rbl_scan<real, false, false><<<nb256, 256, 0, st>>>(a256);
         if (marks) prof_mark(c, 3);
-        if (!a.exact) k_rbl_select<real, CAP, false><<<nb256, 256, 0, st>>>(a256);
+        if (!a.exact) launch_select<real, CAP, false>(a256, nb256, st);
     }
     if (marks) prof_mark(c, 4);
     if (a.tab) {
@@ -944,6 +1022,8 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     a.lcore = c->lcore;
     a.lshell = c->lshell;
     a.sidx = c->cell_rank;
+    a.heavy = c->heavy;
+    a.heavy_n = c->ibuf + 3;
     a.ncount = c->ncount;
     a.bk = c->bk;
     a.ovf = c->ibuf + 2;
@@ -982,6 +1062,8 @@ static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
     a.lcore = c->lcore;
     a.lshell = c->lshell;
     a.sidx = c->cell_rank;
+    a.heavy = c->heavy;
+    a.heavy_n = c->ibuf + 3;
     a.ncount = c->ncount;
     a.bk = c->bk;
     a.ovf = c->ibuf + 2;
@@ -992,9 +1074,9 @@ static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
     k_rbl_scan<real, true, false><<<nb256, 256, 0, c->stream>>>(a);
     if (!a.exact) {
         const int p = c->prm.rbl_p;
-        if (p <= 10) k_rbl_select<real, 10, false><<<nb256, 256, 0, c->stream>>>(a);
-        else if (p <= 16) k_rbl_select<real, 16, false><<<nb256, 256, 0, c->stream>>>(a);
-        else k_rbl_select<real, 32, false><<<nb256, 256, 0, c->stream>>>(a);
+        if (p <= 10) launch_select<real, 10, false>(a, nb256, c->stream);
+        else if (p <= 16) launch_select<real, 16, false>(a, nb256, c->stream);
+        else launch_select<real, 32, false>(a, nb256, c->stream);
     }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;

@@ -226,6 +226,7 @@ struct rbmd_ctx {
     int32_t *lshell;      // [N][list_cs] shell lists (replica-local atom ids)
     int2 *ncount;         // [N] (|C|, N_s)
     int32_t *bk;          // [N][p] batch (sorted indices)
+    int2 *heavy;          // [N] atoms that need a batch selection (p > 10 only)
     int list_cc, list_cs; // list capacities per atom
     void *adj_lj;         // real [2T]: eps_t, sigma_t (adjoint)
     double *adj_tpart;    // [adjoint blocks][2T]
