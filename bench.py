@@ -9,6 +9,10 @@ a full velocity-Verlet step: half kick + drift, RBE (mode sampling, structure
 factors, force), RBL (cell sort, core list + shell batch pair forces, momentum
 correction), half kick + thermostat.
 
+Before timing, the context's tile shapes (cell division, structure-factor tiles,
+pair look-up table) are autotuned on the initial state (rbmd_autotune; the chosen
+shape is reported under "tiles"; --no-autotune keeps the defaults).
+
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
 on the context's stream; the L2 cache (126 MB, larger than the 1M-atom working
 set) is flushed by writing a 256 MB buffer before every timed step, outside
@@ -61,7 +65,7 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default tile shapes on workloads that autotune")
+                    help="keep the default tile shapes (the run autotunes them otherwise)")
     ap.add_argument("--pair-table", action="store_true",
                     help="erfc-Coulomb pair terms from the look-up table (RBMD_PAIR_TABLE)")
     ap.add_argument("--cpu-sample", type=int, default=400_000)
@@ -92,7 +96,7 @@ WORKLOADS = {
     "c2": dict(n=100_000, charges="1:1", n_types=1, density=0.2, params={}),
     "c4": dict(n=10_000_000, charges="1:1", n_types=1, density=0.2, params=dict(rbe_P=500)),
     "c5": dict(n=None, replicas=64, n_lo=2000, n_hi=200_000, charges="1:1", n_types=1,
-               density=0.2, params=dict(rbe_P=100), autotune=True),
+               density=0.2, params=dict(rbe_P=100)),
     "lj001": dict(n=1_000_000, charges="none", n_types=1, density=0.01,
                   params=dict(r_core=2.5, r_cut=5.0, rbl_p=30, flags=4)),
     "el001": dict(n=100_000, charges="1:1", n_types=1, density=0.01,
@@ -402,7 +406,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     footprint = free0 - torch.cuda.mem_get_info(device)[0]
     tiles = {"shape": ctx.tiles(), "autotuned": False}
-    if WORKLOADS[args.workload].get("autotune") and not args.no_autotune:
+    if not args.no_autotune:
         t0 = time.perf_counter()
         tiles = {"shape": ctx.autotune(step=0), "autotuned": True,
                  "tuning_s": round(time.perf_counter() - t0, 3)}
@@ -432,7 +436,8 @@ def run_ours(args):
     fp64 = None
     if not args.skip_fp64:
         c64 = make_ctx(system, rb.FP64, device)
-        c64.set_tiles(*tiles["shape"])
+        c64.set_tiles(*tiles["shape"][:3])
+        c64.set_pair_table(tiles["shape"][3])
         ms64, st64 = time_steps(c64, args.fp64_steps, 2, flush, profile=True)
         c64.close()
         m64 = sum(ms64) / len(ms64)
