@@ -81,7 +81,8 @@ typedef struct {
     double alpha;        /* splitting parameter of Eq. 6 (erfc(sqrt(alpha) r)) */
     double r_core;       /* inner radius (paper r_c), 0 <= r_core <= r_cut */
     double r_cut;        /* outer radius (paper r_s), r_cut < L/2 */
-    int32_t rbl_p;       /* RBL shell batch size p, 1..32 (Eq. 15) */
+    int32_t rbl_p;       /* RBL shell batch size p, 1..1024 (Eq. 15); above 32 an atom
+                            whose lists overflow latches RBMD_ERR_CELL_OVERFLOW */
     int32_t thermostat;  /* 0 none (NVE), 1 Berendsen, 2 Langevin, 3 Nose-Hoover (rbmd_step) */
     double coulomb_k;    /* Coulomb prefactor (1/(4 pi eps0) of Eq. 3; Bjerrum length in reduced units) */
     double dt;           /* time step */

@@ -464,7 +464,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     if (p.n_types < 1 || p.n_types > RBMD_MAX_TYPES) return RBMD_ERR_INVALID;
     if (!(p.alpha > 0.0) || !(p.r_cut > 0.0)) return RBMD_ERR_INVALID;
     if (!(p.r_core >= 0.0) || p.r_core > p.r_cut) return RBMD_ERR_INVALID;
-    if (p.rbe_P < 1 || p.rbl_p < 1 || p.rbl_p > 32) return RBMD_ERR_INVALID;
+    if (p.rbe_P < 1 || p.rbl_p < 1 || p.rbl_p > 1024) return RBMD_ERR_INVALID;
     if (p.precision != RBMD_FP32 && p.precision != RBMD_FP64) return RBMD_ERR_INVALID;
     if (p.thermostat < 0 || p.thermostat > 3) return RBMD_ERR_INVALID;
     if (p.cell_div < 0 || p.cell_div > 2) return RBMD_ERR_INVALID;
@@ -668,6 +668,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     }
     TRY(upload_lj(c, lj_eps, lj_sigma));
     TRY(rbe_configure(c));
+    TRY(rbl_configure(c));
     TRY(cuda_status(cudaMemcpy(c->reps, c->reps_h, sizeof(Rep) * R, cudaMemcpyHostToDevice)));
     TRY(cuda_status(cudaMemcpy(c->map256, m256.data(), sizeof(int2) * m256.size(), cudaMemcpyHostToDevice)));
     TRY(cuda_status(cudaMemcpy(c->map128, m128.data(), sizeof(int2) * m128.size(), cudaMemcpyHostToDevice)));

@@ -654,6 +654,100 @@ __global__ void __launch_bounds__(256) k_rbl_select_list(PairArgs<real> a)
     }
 }
 
+// p > 32: one warp per listed atom sorts its whole shell by priority in shared
+// memory (bitonic sort of (w0 << 32 | w1, id) pairs, the exact order of the batch
+// rule) and keeps the first p.  The priorities are computed by the lanes in
+// parallel.  Shared memory: SEL_WARPS warps x n2 entries of 12 bytes, n2 the
+// power of two at or above the shell capacity.
+constexpr int SEL_WARPS = 4;
+
+template <typename real, bool LISTS>
+__global__ void __launch_bounds__(32 * SEL_WARPS) k_rbl_select_warp(PairArgs<real> a, int n2)
+{
+    extern __shared__ __align__(16) unsigned char smem_sel[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(smem_sel) + (size_t)w * n2;
+    uint32_t *s_id = reinterpret_cast<uint32_t *>(reinterpret_cast<uint64_t *>(smem_sel) +
+                                                  (size_t)SEL_WARPS * n2) + (size_t)w * n2;
+    const int32_t n = *a.heavy_n;
+    const int64_t N = a.N;
+    for (int64_t j = (int64_t)blockIdx.x * SEL_WARPS + w; j < n;
+         j += (int64_t)gridDim.x * SEL_WARPS) {
+        const int2 h = a.heavy[j];
+        const int64_t is = h.x;
+        const Rep rp = a.reps[h.y];
+        const uint32_t id0 = (uint32_t)rp.atom0;
+        const int ns = a.ncount[is].y;
+        const uint32_t id_i = a.spos[is].w;
+        const Philox0 r0 =
+            philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key);
+        const int32_t *ls = a.lshell + lidx(is, 0, N, a.CS);
+        int m = 1;
+        while (m < ns) m <<= 1;  // sort length: power of two, at most n2
+        for (int e = lane; e < m; e += 32) {
+            if (e < ns) {
+                const uint32_t id = (uint32_t)ls[e];
+                const uint2 pw = philox_rest(r0, id, rp.key);
+                s_key[e] = ((uint64_t)pw.x << 32) | pw.y;
+                s_id[e] = id;
+            } else {
+                s_key[e] = ~0ull;  // padding sorts last
+                s_id[e] = 0xFFFFFFFFu;
+            }
+        }
+        __syncwarp();
+        for (int k = 2; k <= m; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = lane; i < m; i += 32) {
+                    const int l = i ^ jj;
+                    if (l > i) {
+                        const uint64_t ki = s_key[i], kl = s_key[l];
+                        const uint32_t ii = s_id[i], il = s_id[l];
+                        const bool gt = ki > kl || (ki == kl && ii > il);
+                        if (((i & k) == 0) == gt) {  // ascending where i & k == 0
+                            s_key[i] = kl;
+                            s_key[l] = ki;
+                            s_id[i] = il;
+                            s_id[l] = ii;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int e = lane; e < a.p; e += 32)
+            a.bk[lidx(is, e, N, a.p)] = a.sidx[id0 + s_id[e]];
+        if constexpr (LISTS) {
+            // batch ids ascending, -1 padded (verification path only): sort the p kept
+            // ids by a second bitonic pass over ids (priorities no longer needed)
+            int mp = 1;
+            while (mp < a.p) mp <<= 1;
+            __syncwarp();
+            for (int e = lane; e < mp; e += 32) {
+                s_key[e] = e < a.p ? (uint64_t)s_id[e] : ~0ull;
+            }
+            __syncwarp();
+            for (int k = 2; k <= mp; k <<= 1)
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (int i = lane; i < mp; i += 32) {
+                        const int l = i ^ jj;
+                        if (l > i) {
+                            const uint64_t ki = s_key[i], kl = s_key[l];
+                            if (((i & k) == 0) == (ki > kl)) {
+                                s_key[i] = kl;
+                                s_key[l] = ki;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            int32_t *out = a.batch + (int64_t)id_i * a.p;
+            for (int e = lane; e < a.p; e += 32) out[e] = (int32_t)(s_key[e] + id0);
+        }
+        __syncwarp();
+    }
+}
+
 // Step 1b for atoms with N_s <= p: the batch is the whole shell (weight 1); the
 // others go to the list of k_rbl_select_list.
 template <typename real, bool LISTS>
@@ -930,6 +1024,47 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
     }
 }
 
+// The exact fallback's register heap holds at most 32 entries: with a larger batch
+// an atom whose lists overflowed is reported (RBMD_ERR_CELL_OVERFLOW), not
+// computed; the fallback's partial sums are zero.
+template <bool ENERGY>
+__global__ void k_rbl_no_fallback(const int32_t *__restrict__ ovf, int *__restrict__ err,
+                                  double *__restrict__ fpart, double *__restrict__ epart,
+                                  int64_t part0, int64_t nparts)
+{
+    const int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j0 == 0 && *ovf != 0) latch_error(err, RBMD_ERR_CELL_OVERFLOW);
+    for (int64_t j = j0; j < nparts; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t part = part0 + j;
+        fpart[3 * part + 0] = 0.0;
+        fpart[3 * part + 1] = 0.0;
+        fpart[3 * part + 2] = 0.0;
+        if constexpr (ENERGY) {
+            epart[2 * part + 0] = 0.0;
+            epart[2 * part + 1] = 0.0;
+        }
+    }
+}
+
+// Largest shell capacity the large-batch selection sorts in shared memory.
+constexpr int SEL_WARP_MAX_CS = 4096;
+
+rbmd_status rbl_configure(rbmd_ctx *c)
+{
+    if (c->prm.rbl_p <= 32) return RBMD_OK;
+    if (c->list_cs > SEL_WARP_MAX_CS) return RBMD_ERR_UNSUPPORTED;
+    const size_t smem = (size_t)SEL_WARPS * SEL_WARP_MAX_CS * (sizeof(uint64_t) + sizeof(uint32_t));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_select_warp<float, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_select_warp<float, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_select_warp<double, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_select_warp<double, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return RBMD_OK;
+}
+
 // Batch selection over the 256-atom block map: one kernel for p <= 10; above, the
 // light kernel takes whole shells and lists the rest for the heap kernel.
 template <typename real, int CAP, bool LISTS>
@@ -937,6 +1072,13 @@ static void launch_select(const PairArgs<real> &a256, unsigned nb256, cudaStream
 {
     if constexpr (CAP <= 10) {
         k_rbl_select<real, CAP, LISTS><<<nb256, 256, 0, st>>>(a256);
+    } else if constexpr (CAP > 32) {
+        cudaMemsetAsync(a256.heavy_n, 0, sizeof(int32_t), st);
+        k_rbl_take_shell<real, LISTS><<<nb256, 256, 0, st>>>(a256);
+        int n2 = 1;
+        while (n2 < a256.CS) n2 <<= 1;
+        const size_t smem = (size_t)SEL_WARPS * n2 * (sizeof(uint64_t) + sizeof(uint32_t));
+        k_rbl_select_warp<real, LISTS><<<4u * 148u, 32 * SEL_WARPS, smem, st>>>(a256, n2);
     } else {
         cudaMemsetAsync(a256.heavy_n, 0, sizeof(int32_t), st);
         k_rbl_take_shell<real, LISTS><<<nb256, 256, 0, st>>>(a256);
@@ -975,7 +1117,15 @@ static void launch_rbl(rbmd_ctx *c, const PairArgs<real> &a, cudaStream_t st, bo
         if (energy) k_rbl_force<real, true, false><<<nbp, kPairBlock, 0, st>>>(a128);
         else k_rbl_force<real, false, false><<<nbp, kPairBlock, 0, st>>>(a128);
     }
-    if (lists) {
+    if constexpr (CAP > 32) {
+        const int64_t nparts = (int64_t)c->nb128 * (kPairBlock / 32);
+        if (energy)
+            k_rbl_no_fallback<true><<<nfb, kPairBlock, 0, st>>>(a.ovf, c->err, a.fpart, a.epart,
+                                                                a.fb_part0, nparts);
+        else
+            k_rbl_no_fallback<false><<<nfb, kPairBlock, 0, st>>>(a.ovf, c->err, a.fpart, a.epart,
+                                                                 a.fb_part0, nparts);
+    } else if (lists) {
         if (energy) k_rbl_fused<real, CAP, true, true><<<nfb, kPairBlock, 0, st>>>(a128);
         else k_rbl_fused<real, CAP, false, true><<<nfb, kPairBlock, 0, st>>>(a128);
     } else {
@@ -1032,10 +1182,11 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf + 2, 0, sizeof(int32_t), c->stream));
     const bool lists = n_core != nullptr;
     const int p = c->prm.rbl_p;
+    if (p > 32 && c->list_cs > SEL_WARP_MAX_CS) return RBMD_ERR_UNSUPPORTED;
     if (p <= 10) launch_rbl<real, 10>(c, a, c->stream, energy, lists, marks);
     else if (p <= 16) launch_rbl<real, 16>(c, a, c->stream, energy, lists, marks);
     else if (p <= 32) launch_rbl<real, 32>(c, a, c->stream, energy, lists, marks);
-    else return RBMD_ERR_UNSUPPORTED;
+    else launch_rbl<real, 1024>(c, a, c->stream, energy, lists, marks);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
@@ -1074,9 +1225,11 @@ static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
     k_rbl_scan<real, true, false><<<nb256, 256, 0, c->stream>>>(a);
     if (!a.exact) {
         const int p = c->prm.rbl_p;
+        if (p > 32 && c->list_cs > SEL_WARP_MAX_CS) return RBMD_ERR_UNSUPPORTED;
         if (p <= 10) launch_select<real, 10, false>(a, nb256, c->stream);
         else if (p <= 16) launch_select<real, 16, false>(a, nb256, c->stream);
-        else launch_select<real, 32, false>(a, nb256, c->stream);
+        else if (p <= 32) launch_select<real, 32, false>(a, nb256, c->stream);
+        else launch_select<real, 1024, false>(a, nb256, c->stream);
     }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;

@@ -381,6 +381,7 @@ template <typename real> KickArgs<real> kick_args(rbmd_ctx *c, StepRef sref);
 rbmd_status rbe_sample(rbmd_ctx *c, StepRef s);
 rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between = -1);
 rbmd_status rbe_configure(rbmd_ctx *c);  // kernel attributes (dynamic shared memory)
+rbmd_status rbl_configure(rbmd_ctx *c);  // the same for the large-batch selection
 rbmd_status pair_table_host(double alpha, double r_cut, int n, std::vector<double> &coef,
                             int32_t *i0, double *inv_h);
 // kick != NULL: the integrator's step; the kernel also does the second half kick
