@@ -215,6 +215,23 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# --------------------------------------------------------------------------- ranks
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_per_step):
+    """Whole-job throughput of `world` ranks that each process units_per_rank per step,
+    timed by the slowest rank."""
+    return units_per_rank * world / (ms_per_step * 1e-3)
+
+
 # --------------------------------------------------------------------------- ours
 def make_ctx(system, precision, device):
     import torch
@@ -418,19 +435,19 @@ def run_ours(args):
     ms, stages = time_steps(ctx, args.steps, args.warmup, flush, profile=True)
     clk = clocks.stop()
     kernels_per_step = ctx.step_kernel_count()
-    total_ms = sum(ms)
+    total_ms = max_over_ranks(sum(ms), dist, device)
     if dist:
-        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = args.n * world / (ms_per_step * 1e-3)
+    value = job_rate(args.n, world, ms_per_step)
     stage_ms = {k: v / args.steps for k, v in stages.items()}
 
     e2e = None
     if not args.skip_e2e:
         e2e = e2e_force_step(ctx, system, args.e2e_steps, 2, device)
+        if dist:
+            e2e["ms_per_step"] = max_over_ranks(e2e["ms_per_step"], dist, device)
+            e2e["value"] = job_rate(system.n, world, e2e["ms_per_step"])
     ctx.close()
 
     fp64 = None
