@@ -55,6 +55,8 @@ def lib():
         L.orc_vv.argtypes = [i64, P, P, P, P, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, i32,
                              i32, u64, i64, u32, i32, dbl, i32, dbl, dbl, i64, P]
         L.orc_langevin_normals.argtypes = [u64, u32, i64, u32, P]
+        L.orc_rbe_metropolis.argtypes = [u64, i64, u32, i32, dbl, dbl, i32, P]
+        L.orc_metropolis_table.argtypes = [dbl, dbl, i32, P]
         _lib = L
     return _lib
 
@@ -289,3 +291,18 @@ def energy_grad(u, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P,
                           coulomb_k, r_core, r_cut, p, P, seed, step, replica, int(exact),
                           _p(E), _p(dr), _p(dq), _p(de), _p(ds))
     return E, dr, dq, de, ds
+
+
+def rbe_metropolis(seed, step, P, L, alpha, moves, replica=0):
+    """Modes [P, 3] of the Metropolis chains at `step` (see orc_rbe_metropolis)."""
+    m = np.zeros((P, 3), dtype=np.int32)
+    lib().orc_rbe_metropolis(seed, step, replica, P, L, alpha, moves, _p(m))
+    return m
+
+
+def metropolis_table(L, alpha):
+    """Acceptance thresholds A_k, k = 0..2M, of the Metropolis chains."""
+    M = sampler_M(L, alpha)
+    A = np.zeros(2 * M + 1, dtype=np.uint64)
+    lib().orc_metropolis_table(L, alpha, M, _p(A))
+    return A

@@ -33,6 +33,7 @@
 #define ORC_STREAM_RBE 1u
 #define ORC_STREAM_RBL 2u
 #define ORC_STREAM_LANGEVIN 3u
+#define ORC_STREAM_METROPOLIS 4u
 #define ORC_MAX_ATTEMPTS 256
 
 /* ------------------------------------------------------------------------ */
@@ -677,6 +678,67 @@ void orc_forces(int64_t n, const uint32_t *u, const double *q, const int32_t *ty
     }
     free(Fs);
     free(Fr);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Metropolis mode chains (Algorithm 1 step 1: the paper draws the modes by  */
+/* the Metropolis procedure).  Reading: P independent chains, one per mode   */
+/* slot, each a random walk on Z^3 \ {0} with the symmetric proposal         */
+/* m' = m + delta e_d (axis d uniform, delta = +-1) accepted with            */
+/* min(1, exp(-a (|m'|^2 - |m|^2))), a = pi^2/(alpha L^2); m' = 0 rejected.    */
+/* |m'|^2 - |m|^2 = 2 delta m_d + 1: moves that lower |m| are always        */
+/* accepted; the others, with k = |m_d|, when the 64-bit uniform U is below  */
+/* A_k = min(2^64 - 1, floor(exp(-a (2k + 1)) 2^64)), k = 0..2M (beyond 2M   */
+/* the move is rejected: exp(-a (4M + 1)) < 1e-32).                          */
+/* Chain l starts at step 0 from the exact draw of step 0 (orc_rbe_sample),   */
+/* so it is stationary from the start; every later step s makes `moves`       */
+/* moves; move t uses Philox(ctr = (l, t, s, 4 | replica<<8), key = seed):    */
+/* d = w0 mod 3, delta = +1 if w1 is odd else -1, U = w2<<32 | w3.           */
+/* ------------------------------------------------------------------------ */
+void orc_metropolis_table(double L, double alpha, int M, uint64_t *A)
+{
+    const double a = ORC_PI * ORC_PI / (alpha * L * L);
+    for (int k = 0; k <= 2 * M; ++k) {
+        double x = exp(-a * (2.0 * k + 1.0)) * ORC_TWO64;
+        A[k] = (x >= ORC_TWO64) ? UINT64_MAX : (uint64_t)x;
+    }
+}
+
+void orc_rbe_metropolis(uint64_t seed, int64_t step, uint32_t replica, int P, double L,
+                        double alpha, int moves, int32_t *m_out)
+{
+    orc_rbe_sample(seed, 0, replica, P, L, alpha, m_out);
+    const int M = orc_sampler_M(L, alpha);
+    uint64_t *A = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(2 * M + 1));
+    orc_metropolis_table(L, alpha, M, A);
+    uint32_t key[2];
+    orc_seed_key(seed, key);
+    for (int l = 0; l < P; ++l) {
+        int32_t *m = m_out + 3 * l;
+        for (int64_t st = 1; st <= step; ++st) {
+            for (int t = 0; t < moves; ++t) {
+                uint32_t ctr[4] = {(uint32_t)l, (uint32_t)t, (uint32_t)st,
+                                   ORC_STREAM_METROPOLIS | (replica << 8)};
+                uint32_t w[4];
+                orc_philox4x32_10(ctr, key, w);
+                const int d = (int)(w[0] % 3u);
+                const int delta = (w[1] & 1u) ? 1 : -1;
+                const uint64_t U = ((uint64_t)w[2] << 32) | w[3];
+                int32_t mn[3] = {m[0], m[1], m[2]};
+                mn[d] += delta;
+                if (mn[0] == 0 && mn[1] == 0 && mn[2] == 0) continue;
+                int accept;
+                if (delta * m[d] < 0) {
+                    accept = 1;
+                } else {
+                    const int k = m[d] < 0 ? -m[d] : m[d];
+                    accept = k <= 2 * M && U < A[k];
+                }
+                if (accept) m[d] = mn[d];
+            }
+        }
+    }
+    free(A);
 }
 
 /* ------------------------------------------------------------------------ */
