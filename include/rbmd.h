@@ -72,6 +72,8 @@ typedef enum { RBMD_FP32 = 0, RBMD_FP64 = 1 } rbmd_precision;
 #define RBMD_NO_RBL 8u           /* skip the short-range part */
 #define RBMD_PAIR_TABLE 16u      /* erfc-Coulomb pair terms from a cubic look-up table
                                     (Sec. 3.3; rbmd_pair_table) instead of erfc/exp */
+#define RBMD_METROPOLIS_MODES 32u /* RBE modes from Metropolis chains (Algorithm 1 step 1)
+                                     instead of exact i.i.d. draws; see rbmd_metropolis_table */
 
 typedef struct {
     int64_t n_atoms;     /* N >= 1 */
@@ -95,6 +97,7 @@ typedef struct {
     uint32_t flags;      /* RBMD_* flags above */
     int32_t cell_div;    /* cells per r_cut along each axis: 1 or 2; 0 = 2 (rbmd_set_tiles
                             and rbmd_autotune change it later) */
+    int32_t mh_moves;    /* RBMD_METROPOLIS_MODES: moves per chain per step (0 = 8) */
 } rbmd_params;
 
 /* Energies and diagnostics (host, FP64).  Potential terms follow Eq. 8 with the
@@ -349,6 +352,23 @@ int64_t rbmd_rbe_mode_count(rbmd_ctx *ctx);
 rbmd_status rbmd_rbe_modes(rbmd_ctx *ctx, int64_t step, int32_t *m, double *rho);
 rbmd_status rbmd_rbl_lists(rbmd_ctx *ctx, int64_t step, int32_t *n_core, int32_t *n_shell,
                            int32_t *batch);
+
+/*
+ * rbmd_metropolis_table -- acceptance thresholds of the Metropolis mode chains
+ * (RBMD_METROPOLIS_MODES; the paper draws the modes by the Metropolis procedure,
+ * Algorithm 1 step 1).  Chain l of a context is one mode slot: a random walk on
+ * Z^3 \ {0} with the symmetric proposal m' = m + delta e_d, accepted with
+ * min(1, exp(-a (|m'|^2 - |m|^2))), a = pi^2/(alpha L^2), m' = 0 rejected.  A move
+ * that raises |m| (delta m_d >= 0, k = |m_d|) is accepted when the 64-bit uniform
+ * U < A[k] = min(2^64 - 1, floor(exp(-a (2k + 1)) 2^64)), k = 0..2M (rejected for
+ * k > 2M).  The chains start at step 0 from the exact draw of step 0 (stationary);
+ * each later step s makes mh_moves moves, move t from Philox4x32-10 (key = seed,
+ * counter (l, t, s, 4 | replica << 8)): d = w0 mod 3, delta = +1 if w1 is odd
+ * else -1, U = w2 << 32 | w3.  The modes of a step are a function of (seed,
+ * replica, step): a call for an earlier step replays the chains from step 0.
+ * A must hold 2M + 1 entries (M from rbmd_sampler_table).
+ */
+rbmd_status rbmd_metropolis_table(double box_length, double alpha, uint64_t *A);
 
 /*
  * rbmd_sampler_table -- host-side inverse-CDF thresholds of the per-dimension

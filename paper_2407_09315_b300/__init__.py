@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librbmd.so")
 
 FP32, FP64 = 0, 1
-FULL_EWALD_MODES, RBL_EXACT, NO_RBE, NO_RBL, PAIR_TABLE = 1, 2, 4, 8, 16
+FULL_EWALD_MODES, RBL_EXACT, NO_RBE, NO_RBL, PAIR_TABLE, METROPOLIS_MODES = 1, 2, 4, 8, 16, 32
 
 STATUS = {
     0: "RBMD_OK", 1: "RBMD_ERR_INVALID", 2: "RBMD_ERR_NOT_NEUTRAL",
@@ -40,6 +40,7 @@ class Params(C.Structure):
         ("coulomb_k", C.c_double), ("dt", C.c_double), ("temperature", C.c_double),
         ("tau_T", C.c_double), ("seed", C.c_uint64), ("replica", C.c_uint32),
         ("precision", C.c_int32), ("flags", C.c_uint32), ("cell_div", C.c_int32),
+        ("mh_moves", C.c_int32),
     ]
 
 
@@ -78,6 +79,7 @@ def lib():
         "rbmd_get_thermostat": ([P, P], C.c_int),
         "rbmd_set_thermostat": ([P, P], C.c_int),
         "rbmd_pair_table": ([dbl, dbl, i32, C.POINTER(i32), C.POINTER(dbl), P], C.c_int),
+        "rbmd_metropolis_table": ([dbl, dbl, P], C.c_int),
         "rbmd_energy_batch": ([P, i64, C.POINTER(EnergyTerms)], C.c_int),
         "rbmd_destroy": ([P], None),
         "rbmd_rbe_forces": ([P, i64, P, C.c_int], C.c_int),
@@ -135,6 +137,14 @@ def sampler_table(box_length: float, alpha: float):
     return M.value, T, H.value
 
 
+def metropolis_table(box_length, alpha):
+    """Acceptance thresholds A_k (uint64 [2M + 1]) of the Metropolis mode chains."""
+    M, _, _ = sampler_table(box_length, alpha)
+    A = np.zeros(2 * M + 1, dtype=np.uint64)
+    _check(lib().rbmd_metropolis_table(box_length, alpha, _ptr(A)), "metropolis_table")
+    return A
+
+
 def pair_table(alpha, r_cut, n):
     """The erfc-Coulomb look-up table: (i0, inv_h, coef [n, 2, 4]) (see rbmd.h)."""
     i0 = C.c_int32(0)
@@ -179,7 +189,7 @@ class RBMD:
     def __init__(self, pos, charge, eps, sigma, *, box_length, alpha=0.62, r_core=2.0,
                  r_cut=3.5, rbl_p=10, rbe_P=100, coulomb_k=1.0, dt=0.001, temperature=1.0,
                  tau_T=0.1, thermostat=0, seed=0, replica=0, precision=FP32, flags=0,
-                 cell_div=0, vel=None, types=None, stream=None, n_atoms=None):
+                 cell_div=0, vel=None, types=None, stream=None, n_atoms=None, mh_moves=0):
         import torch
 
         self._torch = torch
@@ -214,7 +224,7 @@ class RBMD:
                             rbl_p=rbl_p, thermostat=thermostat, coulomb_k=coulomb_k, dt=dt,
                             temperature=temps[r], tau_T=tau_T, seed=seeds[r],
                             replica=reps[r], precision=precision, flags=flags,
-                            cell_div=cell_div)
+                            cell_div=cell_div, mh_moves=mh_moves)
         self.params = prm[0]
         self._params = prm
         pos = pos.to(self.dtype).contiguous()

@@ -208,7 +208,8 @@ void free_ctx(rbmd_ctx *c)
                     c->epart,     c->kepart,    c->ibuf,     c->lj_f,       c->lj_d,
                     c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp,
                     c->adj_lj,    c->adj_tpart, c->adj_tsum, c->reps,       c->map256,
-                    c->map128,    c->tiles,     c->red_rep,   c->ptab,       c->heavy};
+                    c->map128,    c->tiles,     c->red_rep,   c->ptab,       c->heavy,
+                    c->modes0,    c->acc,       c->chain_step};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -437,6 +438,14 @@ rbmd_status rbmd_sampler_table(double box_length, double alpha, int32_t *M, uint
     return sampler_table_host(box_length, alpha, M, T, H);
 }
 
+rbmd_status rbmd_metropolis_table(double box_length, double alpha, uint64_t *A)
+{
+    int32_t M = 0;
+    RBMD_CHECK(sampler_table_host(box_length, alpha, &M, nullptr, nullptr));
+    if (!A) return RBMD_ERR_INVALID;
+    return metropolis_table_host(box_length, alpha, M, A);
+}
+
 rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos, const void *vel,
                             const void *charge, const int32_t *type, const double *lj_eps,
                             const double *lj_sigma, void *stream, rbmd_ctx **out)
@@ -455,7 +464,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
             q.r_core != p.r_core || q.r_cut != p.r_cut || q.rbl_p != p.rbl_p ||
             q.thermostat != p.thermostat || q.coulomb_k != p.coulomb_k || q.dt != p.dt ||
             q.tau_T != p.tau_T || q.precision != p.precision || q.flags != p.flags ||
-            q.cell_div != p.cell_div)
+            q.cell_div != p.cell_div || q.mh_moves != p.mh_moves)
             return RBMD_ERR_INVALID;
         if (!(q.r_cut < 0.5 * q.box_length)) return RBMD_ERR_BOX_TOO_SMALL;
         Ntot += q.n_atoms;
@@ -469,6 +478,9 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     if (p.thermostat < 0 || p.thermostat > 3) return RBMD_ERR_INVALID;
     if (p.cell_div < 0 || p.cell_div > 2) return RBMD_ERR_INVALID;
     if ((p.flags & RBMD_FULL_EWALD_MODES) && R != 1) return RBMD_ERR_UNSUPPORTED;
+    if ((p.flags & RBMD_FULL_EWALD_MODES) && (p.flags & RBMD_METROPOLIS_MODES))
+        return RBMD_ERR_INVALID;
+    if (p.mh_moves < 0) return RBMD_ERR_INVALID;
     for (int t = 0; t < p.n_types; ++t)
         if (!(lj_eps[t] >= 0.0) || !(lj_sigma[t] >= 0.0)) return RBMD_ERR_INVALID;
 
@@ -616,6 +628,12 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(alloc_n(&c->d_step, 1));
     TRY(alloc_n(&c->cdf, T.size()));
     TRY(alloc_n(&c->modes, (size_t)R * c->Pm));
+    if (p.flags & RBMD_METROPOLIS_MODES) {
+        TRY(alloc_n(&c->modes0, (size_t)R * c->Pm));
+        TRY(alloc_n(&c->acc, T.size()));
+        TRY(alloc_n(&c->chain_step, 1));
+        c->mh_moves = p.mh_moves > 0 ? p.mh_moves : 8;
+    }
     if (c->full_modes) TRY(alloc_n(&c->W, c->Pm));
     TRY(alloc_n(&c->rho_part, (size_t)c->ntiles_max * c->Pm));
     TRY(alloc_n(&c->rho, (size_t)R * c->Pm));
@@ -674,6 +692,13 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(cuda_status(cudaMemcpy(c->map128, m128.data(), sizeof(int2) * m128.size(), cudaMemcpyHostToDevice)));
     TRY(cuda_status(cudaMemcpy(c->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice)));
     TRY(cuda_status(cudaMemcpy(c->cdf, T.data(), sizeof(uint64_t) * T.size(), cudaMemcpyHostToDevice)));
+    if (c->modes0) {
+        std::vector<uint64_t> A(T.size());
+        for (int r = 0; r < R; ++r)
+            TRY(metropolis_table_host(c->reps_h[r].L, p.alpha, c->reps_h[r].M, A.data() + c->reps_h[r].cdf0));
+        TRY(cuda_status(cudaMemcpy(c->acc, A.data(), sizeof(uint64_t) * A.size(), cudaMemcpyHostToDevice)));
+        TRY(rbe_metropolis_init(c));
+    }
     if (c->full_modes) {
         TRY(cuda_status(cudaMemcpy(c->modes, full.data(), sizeof(int4) * full.size(), cudaMemcpyHostToDevice)));
         TRY(cuda_status(cudaMemcpy(c->W, fullW.data(), sizeof(double) * fullW.size(), cudaMemcpyHostToDevice)));

@@ -101,10 +101,103 @@ __global__ void k_rbe_sample(const uint64_t *__restrict__ Tall, const Rep *__res
     modes[(int64_t)r * P + l] = make_int4(mx, my, mz, 0);
 }
 
+// --------------------------------------------------------------------------
+// Metropolis mode chains (Algorithm 1 step 1), one thread per (replica, chain).
+// Acceptance thresholds A_k = min(2^64 - 1, floor(exp(-a (2k + 1)) 2^64)) on the
+// host; the chains advance from the step they hold to the requested one (or are
+// replayed from step 0 when it lies before), `moves` moves per step.
+// --------------------------------------------------------------------------
+rbmd_status metropolis_table_host(double L, double alpha, int M, uint64_t *A)
+{
+    if (!(L > 0.0) || !(alpha > 0.0) || M < 1) return RBMD_ERR_INVALID;
+    const double a = kPi * kPi / (alpha * L * L);
+    for (int k = 0; k <= 2 * M; ++k) {
+        const double x = exp(-a * (2.0 * k + 1.0)) * kTwo64;
+        A[k] = (x >= kTwo64) ? UINT64_MAX : (uint64_t)x;
+    }
+    return RBMD_OK;
+}
+
+__global__ void k_rbe_metropolis(const uint64_t *__restrict__ Aall, const Rep *__restrict__ reps,
+                                 int64_t P, StepRef sref, const int64_t *__restrict__ chain_step,
+                                 const int4 *__restrict__ modes0, int4 *__restrict__ modes,
+                                 int moves)
+{
+    const int r = blockIdx.y;
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= P) return;
+    const Rep rp = reps[r];
+    const uint64_t *A = Aall + rp.cdf0;
+    const int kmax = 2 * rp.M;
+    const int64_t target = step_of(sref);
+    int64_t s0 = *chain_step;
+    const int64_t t = (int64_t)r * P + l;
+    int4 m = modes[t];
+    if (target < s0) {  // replay from step 0
+        m = modes0[t];
+        s0 = 0;
+    }
+    const uint32_t tag = (rp.tag_rbe & ~0xFFu) | RBMD_STREAM_METROPOLIS;
+    for (int64_t st = s0 + 1; st <= target; ++st) {
+        for (int mv = 0; mv < moves; ++mv) {
+            const uint4 w = philox10(make_uint4((uint32_t)l, (uint32_t)mv, (uint32_t)st, tag), rp.key);
+            const int d = (int)(w.x % 3u);
+            const int delta = (w.y & 1u) ? 1 : -1;
+            const uint64_t U = ((uint64_t)w.z << 32) | w.w;
+            const int md = d == 0 ? m.x : (d == 1 ? m.y : m.z);
+            const int mn = md + delta;
+            // m' = 0 is rejected
+            const bool zero = mn == 0 && (d == 0 ? (m.y == 0 && m.z == 0)
+                                                 : d == 1 ? (m.x == 0 && m.z == 0)
+                                                          : (m.x == 0 && m.y == 0));
+            bool accept;
+            if (delta * md < 0) {
+                accept = true;
+            } else {
+                const int k = md < 0 ? -md : md;
+                accept = k <= kmax && U < A[k];
+            }
+            if (accept && !zero) {
+                if (d == 0) m.x = mn;
+                else if (d == 1) m.y = mn;
+                else m.z = mn;
+            }
+        }
+    }
+    modes[t] = m;
+}
+
+__global__ void k_set_chain_step(int64_t *chain_step, StepRef sref) { *chain_step = step_of(sref); }
+
+rbmd_status rbe_metropolis_init(rbmd_ctx *c)
+{
+    const int threads = 128;
+    const dim3 grid((unsigned)((c->Pm + threads - 1) / threads), (unsigned)c->R);
+    int nmax = 0;
+    for (int r = 0; r < c->R; ++r) nmax = std::max(nmax, 2 * c->reps_h[r].M + 1);
+    const size_t smem = sizeof(uint64_t) * (size_t)std::min(nmax, SAMPLE_SMEM_MAX);
+    k_rbe_sample<<<grid, threads, smem, c->stream>>>(c->cdf, c->reps, c->Pm, StepRef{nullptr, 0},
+                                                      c->modes0);
+    RBMD_LAUNCH_CHECK();
+    RBMD_CHECK_CUDA(cudaMemcpyAsync(c->modes, c->modes0, sizeof(int4) * (size_t)c->R * c->Pm,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    RBMD_CHECK_CUDA(cudaMemsetAsync(c->chain_step, 0, sizeof(int64_t), c->stream));
+    return RBMD_OK;
+}
+
 rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
 {
     if (c->full_modes) return RBMD_OK;  // fixed list built at init
     const int threads = 128;
+    if (c->modes0) {
+        const dim3 g((unsigned)((c->Pm + threads - 1) / threads), (unsigned)c->R);
+        k_rbe_metropolis<<<g, threads, 0, c->stream>>>(c->acc, c->reps, c->Pm, s, c->chain_step,
+                                                       c->modes0, c->modes, c->mh_moves);
+        RBMD_LAUNCH_CHECK();
+        k_set_chain_step<<<1, 1, 0, c->stream>>>(c->chain_step, s);
+        RBMD_LAUNCH_CHECK();
+        return RBMD_OK;
+    }
     const dim3 grid((unsigned)((c->Pm + threads - 1) / threads), (unsigned)c->R);
     int nmax = 0;
     for (int r = 0; r < c->R; ++r) nmax = std::max(nmax, 2 * c->reps_h[r].M + 1);

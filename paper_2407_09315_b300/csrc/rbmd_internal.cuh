@@ -25,6 +25,7 @@
 #define RBMD_STREAM_RBE 1u
 #define RBMD_STREAM_RBL 2u
 #define RBMD_STREAM_LANGEVIN 3u
+#define RBMD_STREAM_METROPOLIS 4u
 #define RBMD_MAX_ATTEMPTS 256
 #define RBMD_MAX_TYPES 64
 #define RBMD_MAX_P 128
@@ -192,6 +193,10 @@ struct rbmd_ctx {
     // RBE
     uint64_t *cdf;        // sampler thresholds of every replica (2M_r + 1 each)
     int4 *modes;          // [R][Pm]
+    int4 *modes0;         // [R][Pm] Metropolis chains at step 0 (RBMD_METROPOLIS_MODES)
+    uint64_t *acc;        // Metropolis acceptance thresholds, same offsets as cdf
+    int64_t *chain_step;  // [1] step the chains in `modes` belong to
+    int mh_moves;
     double *W;            // [Pm] weights (full-mode list, one replica), else NULL
     double2 *rho_part;    // [Pm][ntiles] mode-major, so a warp sums one mode over consecutive tiles
     double2 *rho;         // [R][Pm]
@@ -379,6 +384,8 @@ __device__ __forceinline__ void block_ke_partial(double ke, double *__restrict__
 template <typename real> KickArgs<real> kick_args(rbmd_ctx *c, StepRef sref);
 
 rbmd_status rbe_sample(rbmd_ctx *c, StepRef s);
+rbmd_status rbe_metropolis_init(rbmd_ctx *c);  // chains at step 0 (exact draw)
+rbmd_status metropolis_table_host(double L, double alpha, int M, uint64_t *A);
 rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between = -1);
 rbmd_status rbe_configure(rbmd_ctx *c);  // kernel attributes (dynamic shared memory)
 rbmd_status rbl_configure(rbmd_ctx *c);  // the same for the large-batch selection

@@ -99,3 +99,11 @@ def test_init_batch_rejects_mismatched_shared_parameters_without_device():
     code = lib.rbmd_init_batch(prm, 0, rb._ptr(dummy), None, rb._ptr(dummy), None,
                                rb._ptr(eps), rb._ptr(eps), None, C.byref(h))
     assert code == 1
+
+
+@pytest.mark.parametrize("L,alpha", [(17.1, 0.62), (170.99759466766966, 0.62), (8.0, 0.62),
+                                     (368.40314986403854, 0.62)])
+def test_metropolis_table_matches_oracle_bitwise(L, alpha):
+    A = rb.metropolis_table(L, alpha)
+    Ao = oracle.metropolis_table(L, alpha)
+    assert A.dtype == np.uint64 and np.array_equal(A, Ao)
