@@ -211,8 +211,8 @@ rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
 // Structure factors, Eq. 9 (Algorithm 1 steps 2-3, the paper's Reduce-by-Key).
 // Block (x = atom tile, y = mode tile): the atom tile and the modes are staged
 // in shared memory; work item (mode l, sub-tile s) sums q_j e^{i theta_jl} over
-// its atoms with the thread's own compensated (Kahan) FP32 accumulators (plain
-// FP64 in FP64 contexts).  Items of one warp share s, so every lane reads the
+// its atoms with the thread's own compensated (Kahan) FP32 accumulators, one
+// compensated addition per pair of atoms (plain FP64 in FP64 contexts).  Items of one warp share s, so every lane reads the
 // same atom: a shared-memory broadcast.  The sub-tile sums are combined in FP64
 // in a fixed order and one partial per (atom tile, mode) goes to HBM.
 // --------------------------------------------------------------------------
@@ -274,7 +274,18 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
         double2 out;
         if constexpr (sizeof(real) == 4) {
             float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-            for (int a = b; a < e; ++a) {
+            int a = b;
+            // two atoms per compensated addition: their plain FP32 sum, then Kahan
+            for (; a + 1 < e; a += 2) {
+                const uint4 A0 = s_at[a], A1 = s_at[a + 1];
+                float s0, c0, s1, c1;
+                phase_sincos(mx * A0.x + my * A0.y + mz * A0.z, s0, c0);
+                phase_sincos(mx * A1.x + my * A1.y + mz * A1.z, s1, c1);
+                const float q0 = __uint_as_float(A0.w), q1 = __uint_as_float(A1.w);
+                kahan_add(sr, cr, q0 * c0 + q1 * c1);
+                kahan_add(si, ci, q0 * s0 + q1 * s1);
+            }
+            for (; a < e; ++a) {
                 const uint4 A = s_at[a];
                 const uint32_t ph = mx * A.x + my * A.y + mz * A.z;
                 float sn, cs;
@@ -493,6 +504,76 @@ __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restri
     if constexpr (KICK) block_ke_partial(ke, kick.kepart);
 }
 
+// FP32 force pass with two atoms per thread (atoms j and j + 128 of the 256-atom
+// block): each staged mode coefficient is read once for both, halving the
+// shared-memory traffic per atom-mode; otherwise as k_rbe_force.
+template <int CHUNK, bool KICK>
+__global__ void __launch_bounds__(128) k_rbe_force2(const uint4 *__restrict__ u4,
+                                                    const int2 *__restrict__ map,
+                                                    const Rep *__restrict__ reps,
+                                                    const ModeCoef<float> *__restrict__ coef_all,
+                                                    int64_t Pm, float *__restrict__ F,
+                                                    int accumulate, KickArgs<float> kick)
+{
+    __shared__ ModeCoef<float> s_c[CHUNK];
+    const int2 mb = map[blockIdx.x];
+    const int r = mb.x;
+    const Rep rp = reps[r];
+    const int64_t end = rp.atom0 + rp.N;
+    const int64_t i0 = (int64_t)mb.y + threadIdx.x, i1 = i0 + 128;
+    const bool ok0 = i0 < end, ok1 = i1 < end;
+    const ModeCoef<float> *coef = coef_all + (int64_t)r * Pm;
+    const float tk = (float)(2.0 * kPi / rp.L);
+    const uint4 A0 = ok0 ? u4[i0] : make_uint4(0, 0, 0, 0);
+    const uint4 A1 = ok1 ? u4[i1] : make_uint4(0, 0, 0, 0);
+    float fx0 = 0, fy0 = 0, fz0 = 0, fx1 = 0, fy1 = 0, fz1 = 0;
+    for (int64_t c0 = 0; c0 < Pm; c0 += CHUNK) {
+        const int nc = (int)min((int64_t)CHUNK, Pm - c0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) s_c[k] = coef[c0 + k];
+        __syncthreads();
+        if (ok0) {
+            for (int k = 0; k < nc; ++k) {
+                const ModeCoef<float> mc = s_c[k];
+                float s0, c0v, s1, c1v;
+                phase_sincos((uint32_t)mc.mx * A0.x + (uint32_t)mc.my * A0.y + (uint32_t)mc.mz * A0.z,
+                             s0, c0v);
+                phase_sincos((uint32_t)mc.mx * A1.x + (uint32_t)mc.my * A1.y + (uint32_t)mc.mz * A1.z,
+                             s1, c1v);
+                const float g0 = mc.A * c0v - mc.B * s0, g1 = mc.A * c1v - mc.B * s1;
+                fx0 += g0 * mc.kx;
+                fy0 += g0 * mc.ky;
+                fz0 += g0 * mc.kz;
+                fx1 += g1 * mc.kx;
+                fy1 += g1 * mc.ky;
+                fz1 += g1 * mc.kz;
+            }
+        }
+    }
+    double ke = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const bool ok = h == 0 ? ok0 : ok1;
+        if (!ok) continue;
+        const int64_t i = h == 0 ? i0 : i1;
+        const uint4 &A = h == 0 ? A0 : A1;
+        const float sc = __uint_as_float(A.w) * tk;
+        float *f = F + 3 * i;
+        float fo[3] = {sc * (h == 0 ? fx0 : fx1), sc * (h == 0 ? fy0 : fy1),
+                       sc * (h == 0 ? fz0 : fz1)};
+        if (accumulate) {
+            fo[0] += f[0];
+            fo[1] += f[1];
+            fo[2] += f[2];
+        }
+        f[0] = fo[0];
+        f[1] = fo[1];
+        f[2] = fo[2];
+        if constexpr (KICK) ke += second_kick(kick, rp, r, i, kick.v, F, fo);
+    }
+    if constexpr (KICK) block_ke_partial(ke, kick.kepart);
+}
+
 rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate, const StepRef *kick)
 {
     if (c->fp64) {
@@ -510,12 +591,12 @@ rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate, const Ste
         KickArgs<float> k{};
         if (kick) k = kick_args<float>(c, *kick);
         if (kick)
-            k_rbe_force<float, 256, true><<<c->nb256, 256, 0, c->stream>>>(
-                c->u4, nullptr, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
+            k_rbe_force2<256, true><<<c->nb256, 128, 0, c->stream>>>(
+                c->u4, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
                 (float *)force, accumulate, k);
         else
-            k_rbe_force<float, 256, false><<<c->nb256, 256, 0, c->stream>>>(
-                c->u4, nullptr, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
+            k_rbe_force2<256, false><<<c->nb256, 128, 0, c->stream>>>(
+                c->u4, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
                 (float *)force, accumulate, k);
     }
     RBMD_LAUNCH_CHECK();
