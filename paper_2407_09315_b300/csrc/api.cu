@@ -581,6 +581,9 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     // the exact fallback
     c->list_cc = ((int)ceil(max_mc + 8.0 * sqrt(max_mc) + 8.0) + 3) / 4 * 4;
     c->list_cs = ((int)ceil(max_ms + 8.0 * sqrt(max_ms) + 8.0) + 3) / 4 * 4;
+    // RBMD_SELECT_EXACT=1 sends every batch selection through the exact path that
+    // otherwise only atoms with equal priority words take, so that tests reach it
+    if (const char *env = getenv("RBMD_SELECT_EXACT")) c->sel_exact = atoi(env) != 0;
     // RBMD_LIST_CAPS="cc,cs" shrinks the capacities so that tests can drive
     // atoms through the overflow path
     if (const char *env = getenv("RBMD_LIST_CAPS")) {

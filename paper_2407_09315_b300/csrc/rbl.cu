@@ -233,6 +233,7 @@ template <typename real> struct PairArgs {
     int2 *ncount;      // [N] (|C|, N_s)
     int32_t *bk;       // [N][p] sorted indices of the batch
     const int32_t *sidx;  // [N] sorted index of every atom (by global id)
+    int sel_exact;        // every selection by select_exact (RBMD_SELECT_EXACT, tests)
     int2 *heavy;          // [N] (sorted index, replica) of atoms with N_s > p (p > 10)
     int32_t *heavy_n;     // [1] their count
     int32_t *ovf;      // [0] set when any list overflowed
@@ -576,6 +577,70 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
 // (all of them when N_s <= p), as sorted indices in bk[i][0..min(N_s,p)).
 // The shell list holds atom ids, so a priority needs one list load and no
 // lookup; only the p winners are mapped to sorted indices.
+// Insertion keyed by the high priority word alone.  An equal word (probability
+// about 2^-32 per kept entry, markers included) only raises `tie`: the caller then
+// redoes the atom's selection with select_exact, so this path needs no call.
+template <int CAP>
+__device__ __forceinline__ void sel_insert_fast(uint32_t (&hh)[CAP], int (&hk)[CAP], uint32_t h,
+                                                int k, bool &tie)
+{
+    bool below[CAP];
+#pragma unroll
+    for (int e = 0; e < CAP; ++e) {
+        below[e] = hh[e] < h;
+        tie |= hh[e] == h;
+    }
+    if (below[CAP - 1]) return;
+#pragma unroll
+    for (int e = CAP - 1; e > 0; --e) {
+        const bool b = below[e], bp = below[e - 1];
+        const uint32_t nh = b ? hh[e] : (bp ? h : hh[e - 1]);
+        const int nk = b ? hk[e] : (bp ? k : hk[e - 1]);
+        hh[e] = nh;
+        hk[e] = nk;
+    }
+    if (!below[0]) {
+        hh[0] = h;
+        hk[0] = k;
+    }
+}
+
+// The exact selection of one atom (full 64-bit priorities, then the id), for the
+// rare atoms where sel_insert_fast saw equal high words; fills hk like the heap:
+// CAP - p "minus infinity" markers, then the p smallest ascending (or empty slots).
+template <int CAP>
+__device__ __noinline__ void select_exact(const Philox0 &r0, uint2 key, const int32_t *ls, int ns,
+                                          int p, int (&hk)[CAP])
+{
+    uint64_t kk[CAP];
+    uint32_t kid[CAP];
+    int kept = 0;
+    for (int e = 0; e < ns; ++e) {
+        const uint32_t id = (uint32_t)ls[e];
+        const uint2 w = philox_rest(r0, id, key);
+        const uint64_t v = ((uint64_t)w.x << 32) | w.y;
+        int j;  // the slot the shifting starts from
+        if (kept == p) {
+            if (!(v < kk[p - 1] || (v == kk[p - 1] && id < kid[p - 1]))) continue;
+            j = p - 1;  // the largest kept entry drops out
+        } else {
+            j = kept;
+        }
+        while (j > 0 && (v < kk[j - 1] || (v == kk[j - 1] && id < kid[j - 1]))) {
+            kk[j] = kk[j - 1];
+            kid[j] = kid[j - 1];
+            --j;
+        }
+        kk[j] = v;
+        kid[j] = id;
+        if (kept < p) ++kept;
+    }
+    for (int e = 0; e < CAP; ++e) {
+        const int j = e - (CAP - p);
+        hk[e] = j < 0 ? SEL_NEG : (j < kept ? (int)kid[j] : SEL_POS);
+    }
+}
+
 template <typename real, int CAP, bool LISTS>
 __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is, int r)
 {
@@ -602,11 +667,13 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
         int hk[CAP];
         sel_init<CAP>(hh, hk, a.p);
         const int32_t *ls = a.lshell + lidx(is, 0, N, a.CS);
+        bool tie = false;
         for (int e = 0; e < ns; ++e) {
             const uint32_t id = (uint32_t)ls[e];
             const uint2 w = philox_rest(sel.r0, id, rp.key);
-            sel_insert<CAP>(hh, hk, w.x, (int)id, id, sel);
+            sel_insert_fast<CAP>(hh, hk, w.x, (int)id, tie);
         }
+        if (tie || a.sel_exact) select_exact<CAP>(sel.r0, rp.key, ls, ns, a.p, hk);
 #pragma unroll
         for (int e = 0; e < CAP; ++e)
             if (hk[e] >= 0) {
@@ -1174,6 +1241,7 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     a.sidx = c->cell_rank;
     a.heavy = c->heavy;
     a.heavy_n = c->ibuf + 3;
+    a.sel_exact = c->sel_exact;
     a.ncount = c->ncount;
     a.bk = c->bk;
     a.ovf = c->ibuf + 2;
@@ -1215,6 +1283,7 @@ static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
     a.sidx = c->cell_rank;
     a.heavy = c->heavy;
     a.heavy_n = c->ibuf + 3;
+    a.sel_exact = c->sel_exact;
     a.ncount = c->ncount;
     a.bk = c->bk;
     a.ovf = c->ibuf + 2;

@@ -232,6 +232,7 @@ struct rbmd_ctx {
     int2 *ncount;         // [N] (|C|, N_s)
     int32_t *bk;          // [N][p] batch (sorted indices)
     int2 *heavy;          // [N] atoms that need a batch selection (p > 10 only)
+    int sel_exact;        // RBMD_SELECT_EXACT: every batch by the exact slow path (tests)
     int list_cc, list_cs; // list capacities per atom
     void *adj_lj;         // real [2T]: eps_t, sigma_t (adjoint)
     double *adj_tpart;    // [adjoint blocks][2T]

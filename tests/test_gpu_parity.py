@@ -260,3 +260,20 @@ def test_list_overflow_fallback_is_exact(sys_ragged, prec, monkeypatch):
     E = ctx.energy(4)
     assert abs(E["e_lj"] - o["E_lj"]) <= (1e-10 if prec == rb.FP64 else 1e-5) * abs(o["E_lj"])
     ctx.close()
+
+
+@pytest.mark.parametrize("p", [10, 16, 30])
+def test_exact_selection_path(sys_ragged, p, monkeypatch):
+    # the exact slow path of the batch selection (taken by atoms whose priority
+    # words tie) gives the same batches as the oracle when every atom takes it
+    s = sys_ragged
+    monkeypatch.setenv("RBMD_SELECT_EXACT", "1")
+    ctx, _ = make_ctx(s, rb.FP32, rbl_p=p, seed=12)
+    monkeypatch.delenv("RBMD_SELECT_EXACT")
+    for step in (0, 2):
+        nc, ns, b = (to_np(t).astype(np.int64) for t in ctx.rbl_lists(step))
+        o = oracle.rbl(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, p, 12, step)
+        assert np.array_equal(b, o["batch"]), step
+    F = to_np(ctx.rbl_forces(2))
+    assert rel_err(F, o["F"] - o["Fsum"] / s.n) < TOL[rb.FP32]
+    ctx.close()
