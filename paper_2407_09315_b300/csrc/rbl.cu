@@ -698,9 +698,10 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
     }
 }
 
-// One thread per cell-sorted atom (p <= 10).
+// One thread per cell-sorted atom (p <= 10); four resident blocks per SM (56
+// registers, no spills) measured faster than three.
 template <typename real, int CAP, bool LISTS>
-__global__ void __launch_bounds__(256, 3) k_rbl_select(PairArgs<real> a)
+__global__ void __launch_bounds__(256, 4) k_rbl_select(PairArgs<real> a)
 {
     const AtomSlot sl = atom_slot(a.map, a.reps);
     if (sl.ok) select_atom<real, CAP, LISTS>(a, sl.i, sl.r);
