@@ -318,6 +318,39 @@ __device__ __forceinline__ void eval_k(const PairArgs<real> &a, const real *s_lj
                             I.se * s_lj[tj], I.hs + s_lj[a.T + tj], fx, fy, fz, ec, el);
 }
 
+// Pair forces of the sorted atoms idx[0..n) in order, the next neighbour's
+// position, type and charge loaded before the current pair is evaluated (the
+// gathers, not the arithmetic, bound the pair kernel).
+template <typename real, bool ENERGY, bool TAB>
+__device__ __forceinline__ void eval_list(const PairArgs<real> &a, const real *s_lj,
+                                          const AtomI<real> &I, const int32_t *idx, int n,
+                                          real &fx, real &fy, real &fz, double &ec, double &el)
+{
+    if (n <= 0) return;
+    int k = idx[0];
+    uint4 B = a.spos[k];
+    int tj = a.stype[k];
+    real qj = a.sq[k];
+    for (int e = 0; e < n; ++e) {
+        uint4 Bn = B;
+        int tn = tj;
+        real qn = qj;
+        if (e + 1 < n) {
+            const int kn = idx[e + 1];
+            Bn = a.spos[kn];
+            tn = a.stype[kn];
+            qn = a.sq[kn];
+        }
+        pair_eval<real, ENERGY, TAB>(a, (real)(int32_t)(B.x - I.A.x) * I.lscale,
+                                     (real)(int32_t)(B.y - I.A.y) * I.lscale,
+                                     (real)(int32_t)(B.z - I.A.z) * I.lscale, I.qi * qj,
+                                     I.se * s_lj[tj], I.hs + s_lj[a.T + tj], fx, fy, fz, ec, el);
+        B = Bn;
+        tj = tn;
+        qj = qn;
+    }
+}
+
 // Table or closed forms chosen at run time (the rarely used fallback kernel).
 template <typename real, bool ENERGY>
 __device__ __forceinline__ void eval_any(const PairArgs<real> &a, const real *s_lj,
@@ -879,8 +912,8 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
             I.se = s_lj[ti];
             I.hs = s_lj[a.T + ti];
             const int64_t N = a.N;
-            for (int e = 0; e < cnt.x; ++e)
-                eval_k<real, ENERGY, TAB>(a, s_lj, I, a.lcore[lidx(is, e, N, a.CC)], fx, fy, fz, ec, el);
+            eval_list<real, ENERGY, TAB>(a, s_lj, I, a.lcore + lidx(is, 0, N, a.CC), cnt.x, fx, fy,
+                                         fz, ec, el);
             if (a.exact) {
                 const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
                 for (int e = 0; e < cnt.y; ++e)
@@ -892,8 +925,8 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
                 const real w = cnt.y > a.p ? (real)cnt.y / (real)a.p : (real)1;
                 real bx = 0, by = 0, bz = 0;
                 double bec = 0.0, bel = 0.0;
-                for (int e = 0; e < nb; ++e)
-                    eval_k<real, ENERGY, TAB>(a, s_lj, I, a.bk[lidx(is, e, N, a.p)], bx, by, bz, bec, bel);
+                eval_list<real, ENERGY, TAB>(a, s_lj, I, a.bk + lidx(is, 0, N, a.p), nb, bx, by, bz,
+                                             bec, bel);
                 fx += w * bx;
                 fy += w * by;
                 fz += w * bz;
