@@ -701,8 +701,10 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
         sel_init<CAP>(hh, hk, a.p);
         const int32_t *ls = a.lshell + lidx(is, 0, N, a.CS);
         bool tie = false;
+        uint32_t idn = (uint32_t)ls[0];  // ns > p >= 1
         for (int e = 0; e < ns; ++e) {
-            const uint32_t id = (uint32_t)ls[e];
+            const uint32_t id = idn;
+            if (e + 1 < ns) idn = (uint32_t)ls[e + 1];
             const uint2 w = philox_rest(sel.r0, id, rp.key);
             sel_insert_fast<CAP>(hh, hk, w.x, (int)id, tie);
         }
