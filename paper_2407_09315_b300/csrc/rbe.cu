@@ -377,13 +377,13 @@ __global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, const 
     mc.mx = m.x;
     mc.my = m.y;
     mc.mz = m.z;
-    mc.pad = 0;
+    if constexpr (sizeof(real) == 8) mc.pad = 0;
     mc.A = (real)(cl * im);
     mc.B = (real)(cl * re);
     mc.kx = (real)m.x;
     mc.ky = (real)m.y;
     mc.kz = (real)m.z;
-    mc.pad2 = mc.pad3 = mc.pad4 = (real)0;
+    if constexpr (sizeof(real) == 8) mc.pad2 = mc.pad3 = mc.pad4 = (real)0;
     coef[l] = mc;
 }
 

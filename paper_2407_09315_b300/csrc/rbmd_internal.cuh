@@ -148,6 +148,11 @@ template <typename real> struct ModeCoef {
     int32_t mx, my, mz, pad;
     real A, B, kx, ky, kz, pad2, pad3, pad4;
 };
+// FP32: 32 bytes, two 16-byte shared-memory loads per mode.
+template <> struct __align__(16) ModeCoef<float> {
+    int32_t mx, my, mz;
+    float A, B, kx, ky, kz;
+};
 
 }  // namespace rbmd
 
