@@ -504,63 +504,66 @@ __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restri
     if constexpr (KICK) block_ke_partial(ke, kick.kepart);
 }
 
-// FP32 force pass with two atoms per thread (atoms j and j + 128 of the 256-atom
-// block): each staged mode coefficient is read once for both, halving the
-// shared-memory traffic per atom-mode; otherwise as k_rbe_force.
-template <int CHUNK, bool KICK>
-__global__ void __launch_bounds__(128) k_rbe_force2(const uint4 *__restrict__ u4,
-                                                    const int2 *__restrict__ map,
-                                                    const Rep *__restrict__ reps,
-                                                    const ModeCoef<float> *__restrict__ coef_all,
-                                                    int64_t Pm, float *__restrict__ F,
-                                                    int accumulate, KickArgs<float> kick)
+// FP32 force pass with AT atoms per thread (atoms j, j + 256/AT, ... of the
+// 256-atom block): each staged mode coefficient is read once for all of them,
+// dividing the shared-memory traffic per atom-mode by AT; otherwise as k_rbe_force.
+constexpr int FORCE_AT = 2;  // measured: 2 beats 1 (mode-table reads) and 4 (registers)
+
+template <int CHUNK, bool KICK, int AT>
+__global__ void __launch_bounds__(256 / AT) k_rbe_force_at(const uint4 *__restrict__ u4,
+                                                           const int2 *__restrict__ map,
+                                                           const Rep *__restrict__ reps,
+                                                           const ModeCoef<float> *__restrict__ coef_all,
+                                                           int64_t Pm, float *__restrict__ F,
+                                                           int accumulate, KickArgs<float> kick)
 {
+    constexpr int TB = 256 / AT;  // threads per block
     __shared__ ModeCoef<float> s_c[CHUNK];
     const int2 mb = map[blockIdx.x];
     const int r = mb.x;
     const Rep rp = reps[r];
     const int64_t end = rp.atom0 + rp.N;
-    const int64_t i0 = (int64_t)mb.y + threadIdx.x, i1 = i0 + 128;
-    const bool ok0 = i0 < end, ok1 = i1 < end;
     const ModeCoef<float> *coef = coef_all + (int64_t)r * Pm;
     const float tk = (float)(2.0 * kPi / rp.L);
-    const uint4 A0 = ok0 ? u4[i0] : make_uint4(0, 0, 0, 0);
-    const uint4 A1 = ok1 ? u4[i1] : make_uint4(0, 0, 0, 0);
-    float fx0 = 0, fy0 = 0, fz0 = 0, fx1 = 0, fy1 = 0, fz1 = 0;
+    uint4 A[AT];
+    float f3[AT][3];
+#pragma unroll
+    for (int h = 0; h < AT; ++h) {
+        const int64_t i = (int64_t)mb.y + threadIdx.x + h * TB;
+        A[h] = i < end ? u4[i] : make_uint4(0, 0, 0, 0);
+        f3[h][0] = f3[h][1] = f3[h][2] = 0.f;
+    }
+    const bool any = (int64_t)mb.y + threadIdx.x < end;
     for (int64_t c0 = 0; c0 < Pm; c0 += CHUNK) {
         const int nc = (int)min((int64_t)CHUNK, Pm - c0);
         __syncthreads();
         for (int k = threadIdx.x; k < nc; k += blockDim.x) s_c[k] = coef[c0 + k];
         __syncthreads();
-        if (ok0) {
+        if (any) {
             for (int k = 0; k < nc; ++k) {
                 const ModeCoef<float> mc = s_c[k];
-                float s0, c0v, s1, c1v;
-                phase_sincos((uint32_t)mc.mx * A0.x + (uint32_t)mc.my * A0.y + (uint32_t)mc.mz * A0.z,
-                             s0, c0v);
-                phase_sincos((uint32_t)mc.mx * A1.x + (uint32_t)mc.my * A1.y + (uint32_t)mc.mz * A1.z,
-                             s1, c1v);
-                const float g0 = mc.A * c0v - mc.B * s0, g1 = mc.A * c1v - mc.B * s1;
-                fx0 += g0 * mc.kx;
-                fy0 += g0 * mc.ky;
-                fz0 += g0 * mc.kz;
-                fx1 += g1 * mc.kx;
-                fy1 += g1 * mc.ky;
-                fz1 += g1 * mc.kz;
+#pragma unroll
+                for (int h = 0; h < AT; ++h) {
+                    float sn, cs;
+                    phase_sincos((uint32_t)mc.mx * A[h].x + (uint32_t)mc.my * A[h].y +
+                                     (uint32_t)mc.mz * A[h].z,
+                                 sn, cs);
+                    const float g = mc.A * cs - mc.B * sn;
+                    f3[h][0] += g * mc.kx;
+                    f3[h][1] += g * mc.ky;
+                    f3[h][2] += g * mc.kz;
+                }
             }
         }
     }
     double ke = 0.0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const bool ok = h == 0 ? ok0 : ok1;
-        if (!ok) continue;
-        const int64_t i = h == 0 ? i0 : i1;
-        const uint4 &A = h == 0 ? A0 : A1;
-        const float sc = __uint_as_float(A.w) * tk;
+    for (int h = 0; h < AT; ++h) {
+        const int64_t i = (int64_t)mb.y + threadIdx.x + h * TB;
+        if (i >= end) continue;
+        const float sc = __uint_as_float(A[h].w) * tk;
         float *f = F + 3 * i;
-        float fo[3] = {sc * (h == 0 ? fx0 : fx1), sc * (h == 0 ? fy0 : fy1),
-                       sc * (h == 0 ? fz0 : fz1)};
+        float fo[3] = {sc * f3[h][0], sc * f3[h][1], sc * f3[h][2]};
         if (accumulate) {
             fo[0] += f[0];
             fo[1] += f[1];
@@ -591,11 +594,11 @@ rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate, const Ste
         KickArgs<float> k{};
         if (kick) k = kick_args<float>(c, *kick);
         if (kick)
-            k_rbe_force2<256, true><<<c->nb256, 128, 0, c->stream>>>(
+            k_rbe_force_at<256, true, FORCE_AT><<<c->nb256, 256 / FORCE_AT, 0, c->stream>>>(
                 c->u4, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
                 (float *)force, accumulate, k);
         else
-            k_rbe_force2<256, false><<<c->nb256, 128, 0, c->stream>>>(
+            k_rbe_force_at<256, false, FORCE_AT><<<c->nb256, 256 / FORCE_AT, 0, c->stream>>>(
                 c->u4, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
                 (float *)force, accumulate, k);
     }
