@@ -229,6 +229,16 @@ __device__ __forceinline__ void phase_sincos(uint32_t ph, double &s, double &c)
     sincospi((double)(int32_t)ph * 4.656612873077392578125e-10, &s, &c);
 }
 
+// Explicitly rounded operations for the force passes: the same force must come out
+// of the kernel variants with and without the integrator's kick (a resumed run
+// computes its first force without it), so no contraction is left to the compiler.
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_r(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_r(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_r(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_r(double a, double b) { return __dadd_rn(a, b); }
+
 __device__ __forceinline__ void kahan_add(float &s, float &comp, float x)
 {
     float y = x - comp;
@@ -476,10 +486,10 @@ __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restri
                                     (uint32_t)mc.mz * A.z;
                 real sn, cs;
                 phase_sincos(ph, sn, cs);
-                const real g = mc.A * cs - mc.B * sn;
-                fx += g * mc.kx;
-                fy += g * mc.ky;
-                fz += g * mc.kz;
+                const real g = fma_r(mc.A, cs, -mul_r(mc.B, sn));
+                fx = fma_r(g, mc.kx, fx);
+                fy = fma_r(g, mc.ky, fy);
+                fz = fma_r(g, mc.kz, fz);
             }
         }
     }
@@ -488,13 +498,13 @@ __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restri
         real q;
         if constexpr (sizeof(real) == 4) q = __uint_as_float(A.w);
         else q = q64[i];
-        const real s = q * tk;
+        const real s = mul_r(q, tk);
         real *f = F + 3 * i;
-        real fo[3] = {s * fx, s * fy, s * fz};
+        real fo[3] = {mul_r(s, fx), mul_r(s, fy), mul_r(s, fz)};
         if (accumulate) {
-            fo[0] += f[0];
-            fo[1] += f[1];
-            fo[2] += f[2];
+            fo[0] = add_r(fo[0], f[0]);
+            fo[1] = add_r(fo[1], f[1]);
+            fo[2] = add_r(fo[2], f[2]);
         }
         f[0] = fo[0];
         f[1] = fo[1];
@@ -548,10 +558,10 @@ __global__ void __launch_bounds__(256 / AT) k_rbe_force_at(const uint4 *__restri
                     phase_sincos((uint32_t)mc.mx * A[h].x + (uint32_t)mc.my * A[h].y +
                                      (uint32_t)mc.mz * A[h].z,
                                  sn, cs);
-                    const float g = mc.A * cs - mc.B * sn;
-                    f3[h][0] += g * mc.kx;
-                    f3[h][1] += g * mc.ky;
-                    f3[h][2] += g * mc.kz;
+                    const float g = fma_r(mc.A, cs, -mul_r(mc.B, sn));
+                    f3[h][0] = fma_r(g, mc.kx, f3[h][0]);
+                    f3[h][1] = fma_r(g, mc.ky, f3[h][1]);
+                    f3[h][2] = fma_r(g, mc.kz, f3[h][2]);
                 }
             }
         }
@@ -561,13 +571,13 @@ __global__ void __launch_bounds__(256 / AT) k_rbe_force_at(const uint4 *__restri
     for (int h = 0; h < AT; ++h) {
         const int64_t i = (int64_t)mb.y + threadIdx.x + h * TB;
         if (i >= end) continue;
-        const float sc = __uint_as_float(A[h].w) * tk;
+        const float sc = mul_r(__uint_as_float(A[h].w), tk);
         float *f = F + 3 * i;
-        float fo[3] = {sc * f3[h][0], sc * f3[h][1], sc * f3[h][2]};
+        float fo[3] = {mul_r(sc, f3[h][0]), mul_r(sc, f3[h][1]), mul_r(sc, f3[h][2])};
         if (accumulate) {
-            fo[0] += f[0];
-            fo[1] += f[1];
-            fo[2] += f[2];
+            fo[0] = add_r(fo[0], f[0]);
+            fo[1] = add_r(fo[1], f[1]);
+            fo[2] = add_r(fo[2], f[2]);
         }
         f[0] = fo[0];
         f[1] = fo[1];
