@@ -17,6 +17,10 @@ Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
 on the context's stream; the L2 cache (126 MB, larger than the 1M-atom working
 set) is flushed by writing a 256 MB buffer before every timed step, outside
 the timed region.  The FP64 path is timed the same way on the same system.
+Per-stage times (and the roofline of the dominant kernel) come from a second
+pass of K steps whose step graph records CUDA events between the stages; that
+pass runs the stages one after another on one stream, so it is a little slower
+than the timed steps, where the RBE structure factors overlap the RBL kernels.
 `e2e` times the force step through the C ABI with host buffers: positions
 copied in from pinned host memory, forces copied back, every step.
 
@@ -432,7 +436,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    ms, stages = time_steps(ctx, args.steps, args.warmup, flush, profile=True)
+    ms, _ = time_steps(ctx, args.steps, args.warmup, flush, profile=False)
     clk = clocks.stop()
     kernels_per_step = ctx.step_kernel_count()
     total_ms = max_over_ranks(sum(ms), dist, device)
@@ -440,6 +444,10 @@ def run_ours(args):
         dist.barrier()
     ms_per_step = total_ms / args.steps
     value = job_rate(args.n, world, ms_per_step)
+    # per-stage times: a second pass of K steps whose graph records CUDA events
+    # between the stages (the stages then run one after another on one stream)
+    ms_prof, stages = time_steps(ctx, args.steps, 2, flush, profile=True)
+    ctx.profile(False)
     stage_ms = {k: v / args.steps for k, v in stages.items()}
 
     e2e = None
@@ -455,7 +463,8 @@ def run_ours(args):
         c64 = make_ctx(system, rb.FP64, device)
         c64.set_tiles(*tiles["shape"][:3])
         c64.set_pair_table(tiles["shape"][3])
-        ms64, st64 = time_steps(c64, args.fp64_steps, 2, flush, profile=True)
+        ms64, _ = time_steps(c64, args.fp64_steps, 2, flush, profile=False)
+        _, st64 = time_steps(c64, args.fp64_steps, 1, flush, profile=True)
         c64.close()
         m64 = sum(ms64) / len(ms64)
         fp64 = {"ms_per_step": round(m64, 4), "atom_steps_per_s": args.n / (m64 * 1e-3),
@@ -472,6 +481,9 @@ def run_ours(args):
         "data": "synthetic (seeded %s, see DESIGN.md)" % WORKLOADS[args.workload]["charges"].replace("none", "LJ fluid"),
         "config": workload_config(args, world, system),
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_pass": {"ms_per_step": round(sum(ms_prof) / len(ms_prof), 4),
+                       "what": "second pass of K steps with CUDA events between the stages, "
+                               "stages serialised on one stream"},
         "roofline": roofline(stage_ms, system, 2032.0),
         "gpu_launches": kernels_per_step * args.steps,
         "device_memory_bytes": int(footprint),

@@ -30,7 +30,13 @@
  *     the context's own layout and the context owns all its device state.
  *   - Work is queued on the stream given to rbmd_init.  Calls that return host
  *     values (rbmd_energy, rbmd_get_state, rbmd_sync, rbmd_rbe_modes) wait for
- *     the stream; the others return as soon as the work is queued.
+ *     the stream; the others return as soon as the work is queued.  A force
+ *     evaluation (every step, rbmd_forces) forks the RBE sampling and structure
+ *     factors onto a second stream owned by the context and joins it back before
+ *     the RBE force pass, so work queued on the caller's stream after the call
+ *     sees the whole evaluation.  The environment variable RBMD_ONE_STREAM=1 at
+ *     rbmd_init keeps everything on the caller's stream (same results, bit for
+ *     bit).
  *   - Errors are returned, never raised or aborted on.  Device-side faults
  *     (non-finite forces, timeouts) are latched in a device error word and
  *     returned by the next call that synchronises.

@@ -215,6 +215,9 @@ void free_ctx(rbmd_ctx *c)
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
         if (c->prof_ev[k]) cudaEventDestroy(c->prof_ev[k]);
     delete[] c->reps_h;
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream) {
         cudaStreamDestroy(c->stream);
         cudaEventDestroy(c->ev_in);
@@ -352,13 +355,36 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
     const bool do_rbe = !(c->prm.flags & RBMD_NO_RBE);
     const bool do_rbl = !(c->prm.flags & RBMD_NO_RBL);
     int acc = accumulate;
+    // the RBE sampling and structure factors depend on the positions only: on the
+    // side stream they overlap the cell sort and the RBL kernels (not while the
+    // stages are timed one by one)
+    const bool fork = do_rbe && do_rbl && c->side && !c->profiling;
+    if (fork) {
+        RBMD_CHECK_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+        RBMD_CHECK_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        const cudaStream_t main = c->stream;
+        c->stream = c->side;
+        rbmd_status st = rbe_sample(c, s);
+        if (st == RBMD_OK) st = rbe_structure_factors(c, -1);
+        c->stream = main;
+        RBMD_CHECK_CUDA(cudaEventRecord(c->ev_join, c->side));
+        if (st != RBMD_OK) {
+            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+            return st;
+        }
+    }
     if (marks) prof_mark(c, 1);
     if (do_rbl) {
-        RBMD_CHECK(cells_build(c, counted));
+        rbmd_status st = cells_build(c, counted);
         if (marks) prof_mark(c, 2);  // stages 3 and 4 are marked inside
-        RBMD_CHECK(rbl_pairs(c, s, force, acc, false, nullptr, nullptr, nullptr, marks));
+        if (st == RBMD_OK) st = rbl_pairs(c, s, force, acc, false, nullptr, nullptr, nullptr, marks);
         if (marks) prof_mark(c, 5);
-        RBMD_CHECK(rbl_correction(c, force, apply_corr, apply_corr ? SCAL_FCORR_AUX : SCAL_FCORR));
+        if (st == RBMD_OK)
+            st = rbl_correction(c, force, apply_corr, apply_corr ? SCAL_FCORR_AUX : SCAL_FCORR);
+        if (st != RBMD_OK) {
+            if (fork) cudaStreamWaitEvent(c->stream, c->ev_join, 0);  // no side work left unjoined
+            return st;
+        }
         acc = 1;
     } else {
         for (int k = 2; k <= 5 && marks; ++k) prof_mark(c, k);
@@ -368,11 +394,15 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
         }
     }
     if (marks) prof_mark(c, 6);
-    if (do_rbe) {
+    if (fork) {
+        RBMD_CHECK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    } else if (do_rbe) {
         RBMD_CHECK(rbe_sample(c, s));
         if (marks) prof_mark(c, 7);
         RBMD_CHECK(rbe_structure_factors(c, marks ? 8 : -1));
         if (marks) prof_mark(c, 9);
+    }
+    if (do_rbe) {
         RBMD_CHECK(rbe_apply_forces(c, force, acc, kick));
         if (kicked && kick) *kicked = true;
         acc = 1;
@@ -523,6 +553,13 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
         TRY(cuda_status(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)));
         TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)));
         TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)));
+    }
+    // RBMD_ONE_STREAM=1 keeps every force evaluation on the context's stream
+    // (the two-stream and one-stream evaluations compute the same bits)
+    if (!(getenv("RBMD_ONE_STREAM") && atoi(getenv("RBMD_ONE_STREAM")) != 0)) {
+        TRY(cuda_status(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)));
+        TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)));
+        TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)));
     }
     enter(c);
 

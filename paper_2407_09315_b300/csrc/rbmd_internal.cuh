@@ -164,6 +164,11 @@ struct rbmd_ctx {
     cudaStream_t stream;
     bool own_stream;      // created here because the caller passed the legacy stream
     cudaEvent_t ev_in, ev_out;
+    // second stream of a force evaluation: the RBE sampling and structure factors
+    // run on it beside the RBL kernels (they share no buffer), joined before the
+    // RBE force pass; null when the evaluation stays on one stream
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
 
     // replicas
     int32_t R;
