@@ -394,7 +394,9 @@ __device__ __forceinline__ uint2 philox_rest(const Philox0 &r0, uint32_t id_j, u
 }
 
 // Bottom-p selection over (priority, id), in registers, keyed by the high 32
-// bits of the priority.  The CAP slots hold a sorted list, ascending.  For a
+// bits of the priority, as the overflow fallback kernel runs it (select_atom
+// uses packed keys and a min/max insertion instead).  The CAP slots hold a
+// sorted list, ascending.  For a
 // batch size p < CAP the lowest CAP - p slots hold "minus infinity" markers, so
 // the largest kept entry is always slot CAP - 1; empty slots hold "plus
 // infinity" (key 0xFFFFFFFF).  An insertion is a branch-free shift in which every
@@ -610,36 +612,9 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
 // (all of them when N_s <= p), as sorted indices in bk[i][0..min(N_s,p)).
 // The shell list holds atom ids, so a priority needs one list load and no
 // lookup; only the p winners are mapped to sorted indices.
-// Insertion keyed by the high priority word alone.  An equal word (probability
-// about 2^-32 per kept entry, markers included) only raises `tie`: the caller then
-// redoes the atom's selection with select_exact, so this path needs no call.
-template <int CAP>
-__device__ __forceinline__ void sel_insert_fast(uint32_t (&hh)[CAP], int (&hk)[CAP], uint32_t h,
-                                                int k, bool &tie)
-{
-    bool below[CAP];
-#pragma unroll
-    for (int e = 0; e < CAP; ++e) {
-        below[e] = hh[e] < h;
-        tie |= hh[e] == h;
-    }
-    if (below[CAP - 1]) return;
-#pragma unroll
-    for (int e = CAP - 1; e > 0; --e) {
-        const bool b = below[e], bp = below[e - 1];
-        const uint32_t nh = b ? hh[e] : (bp ? h : hh[e - 1]);
-        const int nk = b ? hk[e] : (bp ? k : hk[e - 1]);
-        hh[e] = nh;
-        hk[e] = nk;
-    }
-    if (!below[0]) {
-        hh[0] = h;
-        hk[0] = k;
-    }
-}
 
 // The exact selection of one atom (full 64-bit priorities, then the id), for the
-// rare atoms where sel_insert_fast saw equal high words; fills hk like the heap:
+// rare atoms where the fast selection met equal truncated keys; fills hk with
 // CAP - p "minus infinity" markers, then the p smallest ascending (or empty slots).
 template <int CAP>
 __device__ __noinline__ void select_exact(const Philox0 &r0, uint2 key, const int32_t *ls, int ns,
@@ -696,26 +671,53 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
     } else {
         const SelCtx sel{
             philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key), rp.key};
-        uint32_t hh[CAP];
-        int hk[CAP];
-        sel_init<CAP>(hh, hk, a.p);
         const int32_t *ls = a.lshell + lidx(is, 0, N, a.CS);
-        bool tie = false;
+        // keys: the priority's high word with its low b bits replaced by the
+        // member's list position (2^b > CS, so no key is all ones and no two are
+        // equal); the CAP + 1 smallest kept sorted by a min/max insertion
+        const int b = 32 - __clz(a.CS);
+        const uint32_t lo_mask = (1u << b) - 1u;
+        uint32_t sk[CAP + 1];
+#pragma unroll
+        for (int e = 0; e <= CAP; ++e) sk[e] = 0xFFFFFFFFu;
         uint32_t idn = (uint32_t)ls[0];  // ns > p >= 1
         for (int e = 0; e < ns; ++e) {
             const uint32_t id = idn;
             if (e + 1 < ns) idn = (uint32_t)ls[e + 1];
             const uint2 w = philox_rest(sel.r0, id, rp.key);
-            sel_insert_fast<CAP>(hh, hk, w.x, (int)id, tie);
+            uint32_t x = (w.x & ~lo_mask) | (uint32_t)e;
+#pragma unroll
+            for (int j = 0; j <= CAP; ++j) {
+                const uint32_t m = min(sk[j], x);
+                x = max(sk[j], x);
+                sk[j] = m;
+            }
         }
-        if (tie || a.sel_exact) select_exact<CAP>(sel.r0, rp.key, ls, ns, a.p, hk);
+        // the key order is the priority order unless two of the p + 1 smallest
+        // share their truncated high words (then the exact selection decides)
+        bool tie = a.sel_exact != 0;
 #pragma unroll
         for (int e = 0; e < CAP; ++e)
-            if (hk[e] >= 0) {
-                if constexpr (LISTS) ids[nb] = hk[e];
-                a.bk[lidx(is, nb, N, a.p)] = a.sidx[id0 + (uint32_t)hk[e]];
-                ++nb;
-            }
+            if (e < a.p) tie |= ((sk[e] ^ sk[e + 1]) & ~lo_mask) == 0u;
+        if (!tie) {
+#pragma unroll
+            for (int e = 0; e < CAP; ++e)
+                if (e < a.p) {
+                    const int32_t id = ls[sk[e] & lo_mask];
+                    if constexpr (LISTS) ids[e] = id;
+                    a.bk[lidx(is, e, N, a.p)] = a.sidx[id0 + (uint32_t)id];
+                }
+            nb = a.p;
+        } else {
+            int hk[CAP];
+            select_exact<CAP>(sel.r0, rp.key, ls, ns, a.p, hk);
+            for (int e = 0; e < CAP; ++e)
+                if (hk[e] >= 0) {
+                    if constexpr (LISTS) ids[nb] = hk[e];
+                    a.bk[lidx(is, nb, N, a.p)] = a.sidx[id0 + (uint32_t)hk[e]];
+                    ++nb;
+                }
+        }
     }
     if constexpr (LISTS) {
         // batch ids ascending, -1 padded (verification path only)
@@ -733,8 +735,8 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
     }
 }
 
-// One thread per cell-sorted atom (p <= 10); four resident blocks per SM (56
-// registers, no spills) measured faster than three.
+// One thread per cell-sorted atom (p <= 10); four resident blocks per SM (61
+// registers, no spills): three measured the same, five (spilling) slower.
 template <typename real, int CAP, bool LISTS>
 __global__ void __launch_bounds__(256, 4) k_rbl_select(PairArgs<real> a)
 {
