@@ -61,25 +61,48 @@ __global__ void k_scan_tiles(const int32_t *__restrict__ in, int64_t n, int32_t 
     }
 }
 
+// Inclusive scan of v over the block (blockDim a multiple of 32, at most 1024):
+// warp shuffles, then one warp scans the warp totals.  Returns the inclusive
+// prefix; *total receives the block sum.
+__device__ __forceinline__ int block_scan_incl(int v, int *total)
+{
+    __shared__ int ws[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        int y = lane < nw ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        ws[lane] = y;
+    }
+    __syncthreads();
+    const int incl = x + (w > 0 ? ws[w - 1] : 0);
+    *total = ws[(blockDim.x >> 5) - 1];
+    __syncthreads();  // ws is reused by the next call
+    return incl;
+}
+
 __global__ void k_scan_top(int32_t *__restrict__ tsum, int ntiles)
 {
     // one block: exclusive scan in chunks of blockDim
-    __shared__ int32_t s[1024];
     int carry = 0;
     for (int b = 0; b < ntiles; b += blockDim.x) {
-        int k = b + threadIdx.x;
-        int v = k < ntiles ? tsum[k] : 0;
-        s[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-            int t = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
-            __syncthreads();
-            s[threadIdx.x] += t;
-            __syncthreads();
-        }
-        if (k < ntiles) tsum[k] = carry + s[threadIdx.x] - v;
-        int tot = s[blockDim.x - 1];
-        __syncthreads();
+        const int k = b + threadIdx.x;
+        const int v = k < ntiles ? tsum[k] : 0;
+        int tot;
+        const int incl = block_scan_incl(v, &tot);
+        if (k < ntiles) tsum[k] = carry + incl - v;
         carry += tot;
     }
 }
@@ -87,20 +110,13 @@ __global__ void k_scan_top(int32_t *__restrict__ tsum, int ntiles)
 __global__ void k_scan_final(const int32_t *__restrict__ in, int64_t n,
                              const int32_t *__restrict__ toff, int32_t *__restrict__ out)
 {
-    // blockDim = 1024, one element per thread
-    __shared__ int32_t s[SCAN_TILE];
-    int64_t k = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x;
-    int v = k < n ? in[k] : 0;
-    s[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < SCAN_TILE; o <<= 1) {
-        int t = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
-        __syncthreads();
-        s[threadIdx.x] += t;
-        __syncthreads();
-    }
-    if (k < n) out[k] = toff[blockIdx.x] + s[threadIdx.x] - v;
-    if (k == n - 1) out[n] = toff[blockIdx.x] + s[threadIdx.x];
+    // blockDim = SCAN_TILE, one element per thread
+    const int64_t k = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x;
+    const int v = k < n ? in[k] : 0;
+    int tot;
+    const int incl = block_scan_incl(v, &tot);
+    if (k < n) out[k] = toff[blockIdx.x] + incl - v;
+    if (k == n - 1) out[n] = toff[blockIdx.x] + incl;
 }
 
 template <typename real>
