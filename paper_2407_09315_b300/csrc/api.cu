@@ -621,6 +621,10 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     // RBMD_SELECT_EXACT=1 sends every batch selection through the exact path that
     // otherwise only atoms with equal priority words take, so that tests reach it
     if (const char *env = getenv("RBMD_SELECT_EXACT")) c->sel_exact = atoi(env) != 0;
+    // RBMD_SELECT_KEY_BITS=k keeps only the k high bits of the priority word in the
+    // fast selection's keys, so that equal truncated keys (and with them the
+    // exact path) become common; the batches must not change
+    if (const char *env = getenv("RBMD_SELECT_KEY_BITS")) c->sel_key_bits = atoi(env);
     // RBMD_LIST_CAPS="cc,cs" shrinks the capacities so that tests can drive
     // atoms through the overflow path
     if (const char *env = getenv("RBMD_LIST_CAPS")) {

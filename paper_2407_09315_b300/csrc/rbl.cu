@@ -250,6 +250,7 @@ template <typename real> struct PairArgs {
     int32_t *bk;       // [N][p] sorted indices of the batch
     const int32_t *sidx;  // [N] sorted index of every atom (by global id)
     int sel_exact;        // every selection by select_exact (RBMD_SELECT_EXACT, tests)
+    int sel_key_bits;     // 1..31: priority bits kept in the fast keys (RBMD_SELECT_KEY_BITS, tests)
     int2 *heavy;          // [N] (sorted index, replica) of atoms with N_s > p (p > 10)
     int32_t *heavy_n;     // [1] their count
     int32_t *ovf;      // [0] set when any list overflowed
@@ -693,6 +694,8 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
         // equal); the CAP + 1 smallest kept sorted by a min/max insertion
         const int b = 32 - __clz(a.CS);
         const uint32_t lo_mask = (1u << b) - 1u;
+        uint32_t keep = ~lo_mask;  // the priority bits a key holds
+        if (a.sel_key_bits > 0 && a.sel_key_bits < 32) keep &= ~(0xFFFFFFFFu >> a.sel_key_bits);
         uint32_t sk[CAP + 1];
 #pragma unroll
         for (int e = 0; e <= CAP; ++e) sk[e] = 0xFFFFFFFFu;
@@ -701,7 +704,7 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
             const uint32_t id = idn;
             if (e + 1 < ns) idn = (uint32_t)ls[e + 1];
             const uint2 w = philox_rest(sel.r0, id, rp.key);
-            uint32_t x = (w.x & ~lo_mask) | (uint32_t)e;
+            uint32_t x = (w.x & keep) | (uint32_t)e;
 #pragma unroll
             for (int j = 0; j <= CAP; ++j) {
                 const uint32_t m = min(sk[j], x);
@@ -714,7 +717,7 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
         bool tie = a.sel_exact != 0;
 #pragma unroll
         for (int e = 0; e < CAP; ++e)
-            if (e < a.p) tie |= ((sk[e] ^ sk[e + 1]) & ~lo_mask) == 0u;
+            if (e < a.p) tie |= ((sk[e] ^ sk[e + 1]) & keep) == 0u;
         if (!tie) {
 #pragma unroll
             for (int e = 0; e < CAP; ++e)
@@ -1296,6 +1299,7 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     a.heavy = c->heavy;
     a.heavy_n = c->ibuf + 3;
     a.sel_exact = c->sel_exact;
+    a.sel_key_bits = c->sel_key_bits;
     a.ncount = c->ncount;
     a.bk = c->bk;
     a.ovf = c->ibuf + 2;
@@ -1338,6 +1342,7 @@ static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
     a.heavy = c->heavy;
     a.heavy_n = c->ibuf + 3;
     a.sel_exact = c->sel_exact;
+    a.sel_key_bits = c->sel_key_bits;
     a.ncount = c->ncount;
     a.bk = c->bk;
     a.ovf = c->ibuf + 2;

@@ -243,6 +243,7 @@ struct rbmd_ctx {
     int32_t *bk;          // [N][p] batch (sorted indices)
     int2 *heavy;          // [N] atoms that need a batch selection (p > 10 only)
     int sel_exact;        // RBMD_SELECT_EXACT: every batch by the exact slow path (tests)
+    int sel_key_bits;     // RBMD_SELECT_KEY_BITS: fewer priority bits in the fast keys (tests)
     int list_cc, list_cs; // list capacities per atom
     void *adj_lj;         // real [2T]: eps_t, sigma_t (adjoint)
     double *adj_tpart;    // [adjoint blocks][2T]

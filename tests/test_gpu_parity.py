@@ -262,6 +262,31 @@ def test_list_overflow_fallback_is_exact(sys_ragged, prec, monkeypatch):
     ctx.close()
 
 
+@pytest.mark.parametrize("bits", [16, 8, 3])
+@pytest.mark.parametrize("p", [10, 16, 30])
+def test_truncated_selection_keys(sys_ragged, p, bits, monkeypatch):
+    # the fast selection ranks packed keys (the priority's high word, its low bits
+    # replaced by the member's list position) and hands an atom to the exact path
+    # when two of its p + 1 smallest keys share their priority bits.  Keeping only
+    # `bits` of them makes that common (3 bits: nearly every atom; 16: a few), and
+    # the batches, their order (the FP32 pair sums follow it) and the oracle's
+    # batches must not change.
+    import torch
+
+    s = sys_ragged
+    ref, _ = make_ctx(s, rb.FP32, rbl_p=p, seed=12)
+    monkeypatch.setenv("RBMD_SELECT_KEY_BITS", str(bits))
+    ctx, _ = make_ctx(s, rb.FP32, rbl_p=p, seed=12)
+    monkeypatch.delenv("RBMD_SELECT_KEY_BITS")
+    for step in (0, 3):
+        b = to_np(ctx.rbl_lists(step)[2]).astype(np.int64)
+        o = oracle.rbl(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, p, 12, step)
+        assert np.array_equal(b, o["batch"]), step
+        assert torch.equal(ctx.rbl_forces(step), ref.rbl_forces(step)), step
+    ctx.close()
+    ref.close()
+
+
 @pytest.mark.parametrize("p", [10, 16, 30])
 def test_exact_selection_path(sys_ragged, p, monkeypatch):
     # the exact slow path of the batch selection (taken by atoms whose priority
