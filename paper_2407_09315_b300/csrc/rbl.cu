@@ -368,6 +368,38 @@ __device__ __forceinline__ void eval_list(const PairArgs<real> &a, const real *s
     }
 }
 
+// eval_list over a 16-byte aligned index row: four indices per load, then the
+// four neighbours' gathers issued together (entries past n stay inside the row
+// and are not used).  Same pair order as eval_list.
+template <typename real, bool ENERGY, bool TAB>
+__device__ __forceinline__ void eval_list4(const PairArgs<real> &a, const real *s_lj,
+                                           const AtomI<real> &I, const int32_t *idx, int n,
+                                           real &fx, real &fy, real &fz, double &ec, double &el)
+{
+    for (int e0 = 0; e0 < n; e0 += 4) {
+        const int4 kk = reinterpret_cast<const int4 *>(idx)[e0 >> 2];
+        const int ks[4] = {kk.x, kk.y, kk.z, kk.w};
+        uint4 B[4];
+        int tj[4];
+        real qj[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = e0 + q < n ? ks[q] : ks[0];
+            B[q] = a.spos[k];
+            tj[q] = a.stype[k];
+            qj[q] = a.sq[k];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (e0 + q < n)
+                pair_eval<real, ENERGY, TAB>(a, (real)(int32_t)(B[q].x - I.A.x) * I.lscale,
+                                             (real)(int32_t)(B[q].y - I.A.y) * I.lscale,
+                                             (real)(int32_t)(B[q].z - I.A.z) * I.lscale,
+                                             I.qi * qj[q], I.se * s_lj[tj[q]],
+                                             I.hs + s_lj[a.T + tj[q]], fx, fy, fz, ec, el);
+    }
+}
+
 // Table or closed forms chosen at run time (the rarely used fallback kernel).
 template <typename real, bool ENERGY>
 __device__ __forceinline__ void eval_any(const PairArgs<real> &a, const real *s_lj,
@@ -699,10 +731,7 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
         uint32_t sk[CAP + 1];
 #pragma unroll
         for (int e = 0; e <= CAP; ++e) sk[e] = 0xFFFFFFFFu;
-        uint32_t idn = (uint32_t)ls[0];  // ns > p >= 1
-        for (int e = 0; e < ns; ++e) {
-            const uint32_t id = idn;
-            if (e + 1 < ns) idn = (uint32_t)ls[e + 1];
+        auto insert = [&](uint32_t id, int e) {
             const uint2 w = philox_rest(sel.r0, id, rp.key);
             uint32_t x = (w.x & keep) | (uint32_t)e;
 #pragma unroll
@@ -710,6 +739,29 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
                 const uint32_t m = min(sk[j], x);
                 x = max(sk[j], x);
                 sk[j] = m;
+            }
+        };
+        if ((a.CS & 3) == 0) {
+            // 16-byte rows: four list entries per load, the next four loaded
+            // before the current ones are ranked (entries past N_s stay inside
+            // the row and are skipped)
+            const int4 *l4 = reinterpret_cast<const int4 *>(ls);
+            int4 cur = l4[0];  // ns > p >= 1
+            for (int e0 = 0; e0 < ns; e0 += 4) {
+                int4 nxt = cur;
+                if (e0 + 4 < ns) nxt = l4[(e0 >> 2) + 1];
+                insert((uint32_t)cur.x, e0);
+                if (e0 + 1 < ns) insert((uint32_t)cur.y, e0 + 1);
+                if (e0 + 2 < ns) insert((uint32_t)cur.z, e0 + 2);
+                if (e0 + 3 < ns) insert((uint32_t)cur.w, e0 + 3);
+                cur = nxt;
+            }
+        } else {
+            uint32_t idn = (uint32_t)ls[0];  // ns > p >= 1
+            for (int e = 0; e < ns; ++e) {
+                const uint32_t id = idn;
+                if (e + 1 < ns) idn = (uint32_t)ls[e + 1];
+                insert(id, e);
             }
         }
         // the key order is the priority order unless two of the p + 1 smallest
@@ -935,8 +987,12 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
             I.se = s_lj[ti];
             I.hs = s_lj[a.T + ti];
             const int64_t N = a.N;
-            eval_list<real, ENERGY, TAB>(a, s_lj, I, a.lcore + lidx(is, 0, N, a.CC), cnt.x, fx, fy,
-                                         fz, ec, el);
+            if ((a.CC & 3) == 0)
+                eval_list4<real, ENERGY, TAB>(a, s_lj, I, a.lcore + lidx(is, 0, N, a.CC), cnt.x, fx,
+                                              fy, fz, ec, el);
+            else
+                eval_list<real, ENERGY, TAB>(a, s_lj, I, a.lcore + lidx(is, 0, N, a.CC), cnt.x, fx, fy,
+                                             fz, ec, el);
             if (a.exact) {
                 const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
                 for (int e = 0; e < cnt.y; ++e)
