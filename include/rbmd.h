@@ -261,6 +261,22 @@ rbmd_status rbmd_rbl_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumu
 rbmd_status rbmd_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumulate);
 
 /*
+ * rbmd_forces_host -- host buffers in and out: the positions become the state
+ * (as rbmd_set_state(ctx, pos, NULL, step)) and the forces of rbmd_forces(step)
+ * are written to the host array, bit for bit the same as that sequence followed
+ * by a copy.  The positions are copied in chunks on a copy stream; each chunk is
+ * encoded and binned, and its structure-factor tiles summed, while the next one
+ * is copied, and the RBE force pass runs in chunks whose forces are copied out
+ * while the next chunk is computed.  Returns when the forces are on the host.
+ *   pos        host (pinned for overlap), real [N][3], caller's atom order.
+ *   force      host, real [N][3]; overwritten.
+ * With RBMD_NO_RBE or RBMD_NO_RBL, or while stages are timed (rbmd_profile), the
+ * same work runs in sequence on the context's stream.  Device-side faults are
+ * latched as for rbmd_forces.
+ */
+rbmd_status rbmd_forces_host(rbmd_ctx *ctx, const void *pos, void *force, int64_t step);
+
+/*
  * rbmd_step -- advance n_steps velocity-Verlet steps (Sec. 2.1): half kick,
  * drift of the fixed-point positions (wrapping is modular), forces of the new
  * configuration keyed by the new step number, half kick, thermostat.  Unit

@@ -85,6 +85,7 @@ def lib():
         "rbmd_rbe_forces": ([P, i64, P, C.c_int], C.c_int),
         "rbmd_rbl_forces": ([P, i64, P, C.c_int], C.c_int),
         "rbmd_forces": ([P, i64, P, C.c_int], C.c_int),
+        "rbmd_forces_host": ([P, P, P, i64], C.c_int),
         "rbmd_step": ([P, i64], C.c_int),
         "rbmd_energy": ([P, i64, C.POINTER(EnergyTerms)], C.c_int),
         "rbmd_energy_backward": ([P, i64, dbl, P, P, P, P], C.c_int),
@@ -270,6 +271,18 @@ class RBMD:
     def forces(self, step, out=None, accumulate=False):
         out = self._new3() if out is None else out
         _check(lib().rbmd_forces(self._h, step, _ptr(out), int(accumulate)), "forces")
+        return out
+
+    def forces_host(self, pos, out=None, step=0):
+        """Host positions in (they become the state, as set_state), host forces out:
+        rbmd_forces_host.  pos: CPU tensor [N, 3] of the context's dtype (pinned
+        memory lets the copies overlap the kernels); out: CPU tensor or None."""
+        t = self._torch
+        if pos.device.type != "cpu" or pos.dtype != self.dtype or not pos.is_contiguous():
+            raise ValueError("pos must be a contiguous CPU tensor of the context's dtype")
+        if out is None:
+            out = t.empty((self.n, 3), dtype=self.dtype, pin_memory=pos.is_pinned())
+        _check(lib().rbmd_forces_host(self._h, _ptr(pos), _ptr(out), step), "forces_host")
         return out
 
     # -- dynamics ---------------------------------------------------------

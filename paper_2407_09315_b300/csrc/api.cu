@@ -218,6 +218,12 @@ void free_ctx(rbmd_ctx *c)
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->copy) cudaStreamDestroy(c->copy);
+    for (int k = 0; k < 8; ++k) {
+        if (c->ev_h2d[k]) cudaEventDestroy(c->ev_h2d[k]);
+        if (c->ev_enc[k]) cudaEventDestroy(c->ev_enc[k]);
+        if (c->ev_fin[k]) cudaEventDestroy(c->ev_fin[k]);
+    }
     if (c->own_stream) {
         cudaStreamDestroy(c->stream);
         cudaEventDestroy(c->ev_in);
@@ -560,6 +566,12 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
         TRY(cuda_status(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)));
         TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)));
         TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)));
+        TRY(cuda_status(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking)));
+        for (int k = 0; k < 8; ++k) {
+            TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_h2d[k], cudaEventDisableTiming)));
+            TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_enc[k], cudaEventDisableTiming)));
+            TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_fin[k], cudaEventDisableTiming)));
+        }
     }
     enter(c);
 
@@ -820,6 +832,98 @@ rbmd_status rbmd_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
     if (!c || !force) return RBMD_ERR_INVALID;
     enter(c);
     return leave(c, forces_into(c, StepRef{nullptr, step}, force, accumulate, true));
+}
+
+rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t step)
+{
+    if (!c || !pos || !force) return RBMD_ERR_INVALID;
+    const size_t row = 3 * real_size(c);
+    void *dev = c->scratch_force;  // staged positions, then the forces
+    const bool do_rbe = !(c->prm.flags & RBMD_NO_RBE);
+    const bool do_rbl = !(c->prm.flags & RBMD_NO_RBL);
+    if (!c->copy || !do_rbe || !do_rbl || c->profiling) {
+        // nothing to overlap (or stages being timed): the same work in sequence
+        rbmd_status s = rbmd_set_state(c, pos, nullptr, step);
+        if (s == RBMD_OK) s = rbmd_forces(c, step, dev, 0);
+        if (s != RBMD_OK) return s;
+        enter(c);
+        s = cuda_status(cudaMemcpyAsync(force, dev, c->N * row, cudaMemcpyDefault, c->stream));
+        if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+        return leave(c, s);
+    }
+    enter(c);
+    // chunks: ranges of structure-factor tiles; a tile starts on a 256-atom block
+    // boundary of its replica, so each chunk is also a range of map256 blocks and
+    // of atoms
+    std::vector<int64_t> ta;
+    for (int r = 0; r < c->R; ++r)
+        for (int64_t a = 0; a < c->reps_h[r].N; a += c->rho_tile) ta.push_back(c->reps_h[r].atom0 + a);
+    const int ntl = (int)ta.size();
+    int nch = std::min(4, ntl);
+    if (const char *e = getenv("RBMD_HOST_CHUNKS")) nch = std::max(1, std::min(std::min(8, atoi(e)), ntl));
+    int T[9], B[9];
+    int64_t A[9];
+    for (int k = 0; k <= nch; ++k) {
+        T[k] = (int)((int64_t)k * ntl / nch);
+        A[k] = T[k] < ntl ? ta[T[k]] : c->N;
+        B[k] = c->nb256;
+        for (int r = 0; r < c->R && T[k] < ntl; ++r) {
+            const Rep &rp = c->reps_h[r];
+            if (A[k] >= rp.atom0 && A[k] < rp.atom0 + rp.N) B[k] = rp.b256_0 + (int)((A[k] - rp.atom0) / 256);
+        }
+    }
+    const StepRef s{nullptr, step};
+    const cudaStream_t main = c->stream;
+    rbmd_status st = RBMD_OK;
+    auto on = [&](cudaStream_t q, auto &&f) {  // host helpers launch on c->stream
+        c->stream = q;
+        if (st == RBMD_OK) st = f();
+        c->stream = main;
+    };
+    // the copies reuse the staging buffer only after the caller's earlier work
+    cudaEventRecord(c->ev_fork, main);
+    cudaStreamWaitEvent(c->copy, c->ev_fork, 0);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    st = cuda_status(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, main));
+    on(c->side, [&] { return rbe_sample(c, s); });
+    for (int k = 0; k < nch; ++k) {
+        // positions of chunk k: copied in, encoded and binned, then its tiles' partial
+        // structure factors on the side stream while the next chunk is copied
+        const size_t off = (size_t)A[k] * row, bytes = (size_t)(A[k + 1] - A[k]) * row;
+        if (st == RBMD_OK)
+            st = cuda_status(cudaMemcpyAsync((char *)dev + off, (const char *)pos + off, bytes,
+                                             cudaMemcpyDefault, c->copy));
+        cudaEventRecord(c->ev_h2d[k], c->copy);
+        cudaStreamWaitEvent(main, c->ev_h2d[k], 0);
+        if (st == RBMD_OK) st = md_encode_blocks(c, dev, B[k], B[k + 1]);
+        if (st == RBMD_OK) st = cells_count_blocks(c, B[k], B[k + 1]);
+        cudaEventRecord(c->ev_enc[k], main);
+        cudaStreamWaitEvent(c->side, c->ev_enc[k], 0);
+        on(c->side, [&] { return rbe_rho_partial(c, T[k], T[k + 1]); });
+    }
+    on(c->side, [&] { return rbe_rho_final(c); });
+    cudaEventRecord(c->ev_join, c->side);
+    // the short-range part (same kernels as rbmd_forces), then the RBE force pass
+    // chunk by chunk, each chunk's forces copied out while the next is computed
+    if (st == RBMD_OK) st = cells_build(c, true);
+    if (st == RBMD_OK) st = rbl_pairs(c, s, dev, 0, false, nullptr, nullptr, nullptr);
+    if (st == RBMD_OK) st = rbl_correction(c, dev, true, SCAL_FCORR_AUX);
+    cudaStreamWaitEvent(main, c->ev_join, 0);
+    for (int k = 0; k < nch; ++k) {
+        const size_t off = (size_t)A[k] * row, bytes = (size_t)(A[k + 1] - A[k]) * row;
+        if (st == RBMD_OK) st = rbe_apply_forces(c, dev, 1, nullptr, B[k], B[k + 1]);
+        cudaEventRecord(c->ev_fin[k], main);
+        cudaStreamWaitEvent(c->copy, c->ev_fin[k], 0);
+        if (st == RBMD_OK)
+            st = cuda_status(cudaMemcpyAsync((char *)force + off, (const char *)dev + off, bytes,
+                                             cudaMemcpyDefault, c->copy));
+    }
+    const rbmd_status sync = cuda_status(cudaStreamSynchronize(c->copy));
+    if (st == RBMD_OK) st = sync;
+    cudaStreamSynchronize(c->side);
+    c->step = step;
+    c->have_force = false;
+    return leave(c, st);
 }
 
 rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)

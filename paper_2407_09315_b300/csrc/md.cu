@@ -435,6 +435,17 @@ rbmd_status md_encode_positions(rbmd_ctx *c, const void *pos)
     return RBMD_OK;
 }
 
+// The same for the atoms of the 256-atom blocks [b0, b1) of map256.
+rbmd_status md_encode_blocks(rbmd_ctx *c, const void *pos, int b0, int b1)
+{
+    if (b1 <= b0) return RBMD_OK;
+    const unsigned nb = (unsigned)(b1 - b0);
+    if (c->fp64) k_encode<double><<<nb, 256, 0, c->stream>>>((const double *)pos, c->map256 + b0, c->reps, c->u4);
+    else k_encode<float><<<nb, 256, 0, c->stream>>>((const float *)pos, c->map256 + b0, c->reps, c->u4);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
 rbmd_status md_decode_state(rbmd_ctx *c, void *pos, void *vel)
 {
     if (c->fp64)

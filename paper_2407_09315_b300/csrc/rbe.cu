@@ -251,7 +251,8 @@ template <typename real>
 __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial(const uint4 *__restrict__ u4, const double *__restrict__ q64,
                               const int2 *__restrict__ tiles, const Rep *__restrict__ reps,
                               const int4 *__restrict__ modes_all, int64_t Pm, int tile_atoms,
-                              int mode_tile, int sub, double2 *__restrict__ part)
+                              int mode_tile, int sub, double2 *__restrict__ part, int tile0,
+                              int ntiles_all)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint4 *s_at = reinterpret_cast<uint4 *>(smem);
@@ -259,7 +260,8 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
     int4 *s_m = reinterpret_cast<int4 *>(s_q + (sizeof(real) == 8 ? tile_atoms : 0));
     double2 *s_acc = reinterpret_cast<double2 *>(s_m + mode_tile);
 
-    const int2 tl = tiles[blockIdx.x];  // (replica, first atom); tiles never straddle replicas
+    const int tix = tile0 + (int)blockIdx.x;  // launches may cover a range of the tiles
+    const int2 tl = tiles[tix];  // (replica, first atom); tiles never straddle replicas
     const int64_t a0 = tl.y;
     const int na = (int)min((int64_t)tile_atoms, reps[tl.x].atom0 + reps[tl.x].N - a0);
     const int4 *modes = modes_all + (int64_t)tl.x * Pm;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
             re += s_acc[s * mode_tile + l].x;
             im += s_acc[s * mode_tile + l].y;
         }
-        part[(l0 + l) * (int64_t)gridDim.x + blockIdx.x] = make_double2(re, im);
+        part[(l0 + l) * (int64_t)ntiles_all + tix] = make_double2(re, im);
     }
 }
 
@@ -415,39 +417,54 @@ rbmd_status rbe_configure(rbmd_ctx *c)
     return RBMD_OK;
 }
 
-rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
+// Partial sums of the tiles [t0, t1) (Eq. 9 per tile and mode).
+rbmd_status rbe_rho_partial(rbmd_ctx *c, int t0, int t1)
 {
+    if (t1 <= t0) return RBMD_OK;
     const int tile = c->rho_tile;
     const int mode_tile = (int)(c->Pm < c->rho_mode_tile ? c->Pm : c->rho_mode_tile);
     int sub = max(1, 1024 / mode_tile);
     sub = min(sub, tile);
     int threads = ((mode_tile * sub + 31) / 32) * 32;
     threads = min(threads, 1024);
-    dim3 grid((unsigned)c->ntiles, (unsigned)((c->Pm + mode_tile - 1) / mode_tile));
+    dim3 grid((unsigned)(t1 - t0), (unsigned)((c->Pm + mode_tile - 1) / mode_tile));
     const size_t smem = rho_smem(c->fp64, tile, mode_tile, sub);
+    if (c->fp64)
+        k_rho_partial<double><<<grid, threads, smem, c->stream>>>(
+            c->u4, c->q64, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part, t0,
+            c->ntiles);
+    else
+        k_rho_partial<float><<<grid, threads, smem, c->stream>>>(
+            c->u4, nullptr, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part, t0,
+            c->ntiles);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+// rho of every mode from the tile partials, then the force-pass coefficients.
+rbmd_status rbe_rho_final(rbmd_ctx *c)
+{
     const unsigned fin_blocks = (unsigned)(c->R * c->Pm);
     int max_tiles = 0;
     for (int r = 0; r < c->R; ++r) max_tiles = std::max(max_tiles, (int)c->reps_h[r].ntiles);
     const int fin_threads = max_tiles > 128 ? 128 : 32;
-    if (c->fp64) {
-        k_rho_partial<double><<<grid, threads, smem, c->stream>>>(
-            c->u4, c->q64, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
-        RBMD_LAUNCH_CHECK();
-        if (mark_between >= 0) prof_mark(c, mark_between);
+    if (c->fp64)
         k_rho_final<double><<<fin_blocks, fin_threads, 0, c->stream>>>(
             c->rho_part, c->ntiles, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
             (ModeCoef<double> *)c->coef);
-    } else {
-        k_rho_partial<float><<<grid, threads, smem, c->stream>>>(
-            c->u4, nullptr, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part);
-        RBMD_LAUNCH_CHECK();
-        if (mark_between >= 0) prof_mark(c, mark_between);
+    else
         k_rho_final<float><<<fin_blocks, fin_threads, 0, c->stream>>>(
             c->rho_part, c->ntiles, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
             (ModeCoef<float> *)c->coef);
-    }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
+}
+
+rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between)
+{
+    RBMD_CHECK(rbe_rho_partial(c, 0, c->ntiles));
+    if (mark_between >= 0) prof_mark(c, mark_between);
+    return rbe_rho_final(c);
 }
 
 // --------------------------------------------------------------------------
@@ -587,29 +604,37 @@ __global__ void __launch_bounds__(256 / AT) k_rbe_force_at(const uint4 *__restri
     if constexpr (KICK) block_ke_partial(ke, kick.kepart);
 }
 
-rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate, const StepRef *kick)
+rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate, const StepRef *kick,
+                             int b0, int b1)
 {
+    // the atoms of the 256-atom blocks [b0, b1) of map256 (all of them when b1 < 0);
+    // the integrator's kick (kinetic-energy partials per block) covers all blocks
+    if (b1 < 0) b1 = c->nb256;
+    if (kick && (b0 != 0 || b1 != c->nb256)) return RBMD_ERR_INVALID;
+    if (b1 <= b0) return RBMD_OK;
+    const unsigned nb = (unsigned)(b1 - b0);
+    const int2 *map = c->map256 + b0;
     if (c->fp64) {
         KickArgs<double> k{};
         if (kick) k = kick_args<double>(c, *kick);
         if (kick)
-            k_rbe_force<double, 128, true><<<c->nb256, 256, 0, c->stream>>>(
-                c->u4, c->q64, c->map256, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
+            k_rbe_force<double, 128, true><<<nb, 256, 0, c->stream>>>(
+                c->u4, c->q64, map, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
                 (double *)force, accumulate, k);
         else
-            k_rbe_force<double, 128, false><<<c->nb256, 256, 0, c->stream>>>(
-                c->u4, c->q64, c->map256, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
+            k_rbe_force<double, 128, false><<<nb, 256, 0, c->stream>>>(
+                c->u4, c->q64, map, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
                 (double *)force, accumulate, k);
     } else {
         KickArgs<float> k{};
         if (kick) k = kick_args<float>(c, *kick);
         if (kick)
-            k_rbe_force_at<256, true, FORCE_AT><<<c->nb256, 256 / FORCE_AT, 0, c->stream>>>(
-                c->u4, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
+            k_rbe_force_at<256, true, FORCE_AT><<<nb, 256 / FORCE_AT, 0, c->stream>>>(
+                c->u4, map, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
                 (float *)force, accumulate, k);
         else
-            k_rbe_force_at<256, false, FORCE_AT><<<c->nb256, 256 / FORCE_AT, 0, c->stream>>>(
-                c->u4, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
+            k_rbe_force_at<256, false, FORCE_AT><<<nb, 256 / FORCE_AT, 0, c->stream>>>(
+                c->u4, map, c->reps, (const ModeCoef<float> *)c->coef, c->Pm,
                 (float *)force, accumulate, k);
     }
     RBMD_LAUNCH_CHECK();

@@ -166,6 +166,17 @@ __global__ void k_cell_order(const int32_t *__restrict__ start, int64_t ncell,
     for (int a = b; a < e; ++a) sidx[spos[a].w] = a;
 }
 
+// Cell counts, cells and ranks of the atoms of the 256-atom blocks [b0, b1) of
+// map256 (the counts zeroed beforehand); cells_build(c, true) then completes the sort.
+rbmd_status cells_count_blocks(rbmd_ctx *c, int b0, int b1)
+{
+    if (b1 <= b0) return RBMD_OK;
+    k_cell_count<<<(unsigned)(b1 - b0), 256, 0, c->stream>>>(c->u4, c->map256 + b0, c->reps,
+                                                             c->cell_count, c->cell_of, c->cell_rank);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
 rbmd_status cells_build(rbmd_ctx *c, bool counted)
 {
     const int th = 256;

@@ -169,6 +169,10 @@ struct rbmd_ctx {
     // RBE force pass; null when the evaluation stays on one stream
     cudaStream_t side;
     cudaEvent_t ev_fork, ev_join;
+    // rbmd_forces_host: a copy stream and per-chunk events (positions copied in,
+    // positions encoded, forces final), 8 chunks at most
+    cudaStream_t copy;
+    cudaEvent_t ev_h2d[8], ev_enc[8], ev_fin[8];
 
     // replicas
     int32_t R;
@@ -399,19 +403,23 @@ rbmd_status rbe_sample(rbmd_ctx *c, StepRef s);
 rbmd_status rbe_metropolis_init(rbmd_ctx *c);  // chains at step 0 (exact draw)
 rbmd_status metropolis_table_host(double L, double alpha, int M, uint64_t *A);
 rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between = -1);
+rbmd_status rbe_rho_partial(rbmd_ctx *c, int t0, int t1);  // tile partials of tiles [t0, t1)
+rbmd_status rbe_rho_final(rbmd_ctx *c);                    // rho and coefficients from them
 rbmd_status rbe_configure(rbmd_ctx *c);  // kernel attributes (dynamic shared memory)
 rbmd_status rbl_configure(rbmd_ctx *c);  // the same for the large-batch selection
 rbmd_status pair_table_host(double alpha, double r_cut, int n, std::vector<double> &coef,
                             int32_t *i0, double *inv_h);
 // kick != NULL: the integrator's step; the kernel also does the second half kick
-// (KickArgs of that step) and the kinetic-energy partials.
+// (KickArgs of that step) and the kinetic-energy partials.  [b0, b1): the 256-atom
+// blocks of map256 to cover (b1 < 0: all; a kick needs all).
 rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate,
-                             const StepRef *kick = nullptr);
+                             const StepRef *kick = nullptr, int b0 = 0, int b1 = -1);
 
 // RBL (rbl.cu)
 // counted: the cell counts, cells and ranks are already there (the integrator's
 // drift kernel bins the atoms it moves).
 rbmd_status cells_build(rbmd_ctx *c, bool counted = false);
+rbmd_status cells_count_blocks(rbmd_ctx *c, int b0, int b1);
 rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
                       int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks = false);
 rbmd_status rbl_correction(rbmd_ctx *c, void *force, bool apply, int slot);
@@ -439,6 +447,7 @@ rbmd_status md_sum_replicas(rbmd_ctx *c, const double *parts, int ncomp, int slo
                             bool per_atom, bool two_segments);
 rbmd_status md_decode_state(rbmd_ctx *c, void *pos, void *vel);
 rbmd_status md_encode_positions(rbmd_ctx *c, const void *pos);
+rbmd_status md_encode_blocks(rbmd_ctx *c, const void *pos, int b0, int b1);
 rbmd_status md_kinetic(rbmd_ctx *c, int slot);
 
 inline rbmd_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RBMD_OK : RBMD_ERR_CUDA; }
