@@ -452,13 +452,18 @@ def run_ours(args):
     fp64 = None
     if not args.skip_fp64:
         c64 = make_ctx(system, rb.FP64, device)
-        c64.set_tiles(*tiles["shape"][:3])
-        c64.set_pair_table(tiles["shape"][3])
+        if args.no_autotune:
+            c64.set_tiles(*tiles["shape"][:3])
+            c64.set_pair_table(tiles["shape"][3])
+            shape64 = tiles["shape"]
+        else:
+            shape64 = c64.autotune(step=0)  # the FP64 kernels have their own best shape
         ms64, _ = time_steps(c64, args.fp64_steps, 2, flush, profile=False)
         _, st64 = time_steps(c64, args.fp64_steps, 1, flush, profile=True)
         c64.close()
         m64 = sum(ms64) / len(ms64)
         fp64 = {"ms_per_step": round(m64, 4), "atom_steps_per_s": args.n / (m64 * 1e-3),
+                "tiles": list(shape64),
                 "stage_ms": {k: round(v / args.fp64_steps, 4) for k, v in st64.items()}}
 
     if rank != 0:

@@ -209,7 +209,7 @@ void free_ctx(rbmd_ctx *c)
                     c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp,
                     c->adj_lj,    c->adj_tpart, c->adj_tsum, c->reps,       c->map256,
                     c->map128,    c->tiles,     c->red_rep,   c->ptab,       c->heavy,
-                    c->modes0,    c->acc,       c->chain_step};
+                    c->modes0,    c->acc,       c->chain_step, c->phtab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)

@@ -219,14 +219,40 @@ rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
 // sin and cos of the wrapped phase 2 pi ph / 2^32.  ph is read as a signed
 // fraction of a turn, so the angle lies in [-pi, pi): there the hardware SFU
 // sin/cos (__sincosf) needs no range reduction and its documented absolute error
-// is at most 2^-21.41.  The FP64 path uses sincospi.
+// is at most 2^-21.41.  The FP64 kernels use phase_sincos_tab below.
 __device__ __forceinline__ void phase_sincos(uint32_t ph, float &s, float &c)
 {
     __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &s, &c);  // 2 pi / 2^32
 }
-__device__ __forceinline__ void phase_sincos(uint32_t ph, double &s, double &c)
+
+// FP64 phase factors by angle addition.  The phase is an exact 32-bit fraction of
+// a turn, so with ph = h 2^16 + l, e^{i theta} = T[h] T'[l] where
+// T[h] = e^{2 pi i h/2^16} and T'[l] = e^{2 pi i l/2^32}: two reads of a 2 MB
+// table (L2-resident) and one complex product replace a sincospi, whose cost
+// bounds the FP64 kernels (B300 runs few FP64 operations per clock).  The entries
+// are sincospi of exact arguments; the product adds a few units in the last
+// place.  Layout: {cos, sin}, T at [0, 65536), T' at [65536, 131072).  (A
+// 10 + 11 + 11-bit split with an 80 KB table and two products measured slower:
+// the FP64 operations, not the table reads, bound these kernels.)
+constexpr int PHASE_TAB = 131072;
+
+__global__ void k_phase_table(double2 *__restrict__ tab)
 {
-    sincospi((double)(int32_t)ph * 4.656612873077392578125e-10, &s, &c);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= PHASE_TAB) return;
+    const double x = j < 65536 ? (double)j * 0x1p-15 : (double)(j - 65536) * 0x1p-31;  // angle / pi
+    double s, c;
+    sincospi(x, &s, &c);
+    tab[j] = make_double2(c, s);
+}
+
+__device__ __forceinline__ void phase_sincos_tab(const double2 *__restrict__ tab, uint32_t ph,
+                                                 double &s, double &c)
+{
+    const double2 a = __ldg(tab + (ph >> 16));
+    const double2 d = __ldg(tab + 65536 + (ph & 65535u));
+    c = __fma_rn(a.x, d.x, -__dmul_rn(a.y, d.y));
+    s = __fma_rn(a.x, d.y, __dmul_rn(a.y, d.x));
 }
 
 // Explicitly rounded operations for the force passes: the same force must come out
@@ -252,7 +278,7 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
                               const int2 *__restrict__ tiles, const Rep *__restrict__ reps,
                               const int4 *__restrict__ modes_all, int64_t Pm, int tile_atoms,
                               int mode_tile, int sub, double2 *__restrict__ part, int tile0,
-                              int ntiles_all)
+                              int ntiles_all, const double2 *__restrict__ ptab)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint4 *s_at = reinterpret_cast<uint4 *>(smem);
@@ -313,7 +339,7 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
                 const uint4 A = s_at[a];
                 const uint32_t ph = mx * A.x + my * A.y + mz * A.z;
                 double sn, cs;
-                phase_sincos(ph, sn, cs);
+                phase_sincos_tab(ptab, ph, sn, cs);
                 sr += s_q[a] * cs;
                 si += s_q[a] * sn;
             }
@@ -408,6 +434,11 @@ static size_t rho_smem(bool fp64, int tile, int mode_tile, int sub)
 
 rbmd_status rbe_configure(rbmd_ctx *c)
 {
+    if (c->fp64 && !c->phtab) {
+        RBMD_CHECK_CUDA(cudaMalloc(&c->phtab, sizeof(double2) * PHASE_TAB));
+        k_phase_table<<<(PHASE_TAB + 255) / 256, 256, 0, c->stream>>>(c->phtab);
+        RBMD_LAUNCH_CHECK();
+    }
     // the largest tile shape (2048 atoms, 256 modes x 4 sub-tiles) needs 68 KB in FP64
     const int bytes = (int)rho_smem(true, 2048, 256, 4);
     RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rho_partial<float>,
@@ -432,11 +463,11 @@ rbmd_status rbe_rho_partial(rbmd_ctx *c, int t0, int t1)
     if (c->fp64)
         k_rho_partial<double><<<grid, threads, smem, c->stream>>>(
             c->u4, c->q64, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part, t0,
-            c->ntiles);
+            c->ntiles, c->phtab);
     else
         k_rho_partial<float><<<grid, threads, smem, c->stream>>>(
             c->u4, nullptr, c->tiles, c->reps, c->modes, c->Pm, tile, mode_tile, sub, c->rho_part, t0,
-            c->ntiles);
+            c->ntiles, nullptr);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
@@ -481,7 +512,8 @@ template <typename real, int CHUNK, bool KICK>
 __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restrict__ q64,
                             const int2 *__restrict__ map, const Rep *__restrict__ reps,
                             const ModeCoef<real> *__restrict__ coef_all, int64_t Pm,
-                            real *__restrict__ F, int accumulate, KickArgs<real> kick)
+                            real *__restrict__ F, int accumulate, KickArgs<real> kick,
+                            const double2 *__restrict__ ptab)
 {
     __shared__ ModeCoef<real> s_c[CHUNK];
     const AtomSlot sl = atom_slot(map, reps);  // the whole block belongs to replica sl.r
@@ -502,7 +534,8 @@ __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restri
                 const uint32_t ph = (uint32_t)mc.mx * A.x + (uint32_t)mc.my * A.y +
                                     (uint32_t)mc.mz * A.z;
                 real sn, cs;
-                phase_sincos(ph, sn, cs);
+                if constexpr (sizeof(real) == 8) phase_sincos_tab(ptab, ph, sn, cs);
+                else phase_sincos(ph, sn, cs);  // (the FP32 path runs k_rbe_force_at)
                 const real g = fma_r(mc.A, cs, -mul_r(mc.B, sn));
                 fx = fma_r(g, mc.kx, fx);
                 fy = fma_r(g, mc.ky, fy);
@@ -620,11 +653,11 @@ rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate, const Ste
         if (kick)
             k_rbe_force<double, 128, true><<<nb, 256, 0, c->stream>>>(
                 c->u4, c->q64, map, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
-                (double *)force, accumulate, k);
+                (double *)force, accumulate, k, c->phtab);
         else
             k_rbe_force<double, 128, false><<<nb, 256, 0, c->stream>>>(
                 c->u4, c->q64, map, c->reps, (const ModeCoef<double> *)c->coef, c->Pm,
-                (double *)force, accumulate, k);
+                (double *)force, accumulate, k, c->phtab);
     } else {
         KickArgs<float> k{};
         if (kick) k = kick_args<float>(c, *kick);

@@ -217,6 +217,7 @@ struct rbmd_ctx {
     double *emode;        // [R][Pm]
     void *coef;           // ModeCoef<real>[R][Pm]
     void *ptab;           // pair look-up table, real4 [2 ptab_n] (pairtab.cu)
+    double2 *phtab;       // FP64 contexts: phase factors {cos, sin} for the RBE kernels (rbe.cu)
     int ptab_n, ptab_i0;
     double ptab_inv_h;
     bool use_table;       // pair kernels read the table instead of erfc/exp
