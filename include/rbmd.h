@@ -37,9 +37,9 @@
  *     sees the whole evaluation.  The environment variable RBMD_ONE_STREAM=1 at
  *     rbmd_init keeps everything on the caller's stream (same results, bit for
  *     bit).
- *   - Test hooks, read by rbmd_init unless noted (none changes a result): RBMD_LIST_CAPS
- *     ="cc,cs" shrinks the core and shell list capacities so that atoms take
- *     the exact overflow path; RBMD_SELECT_EXACT=1 sends every batch selection
+ *   - Test hooks, read by rbmd_init unless noted (none changes a result):
+ *     RBMD_LIST_CAPS="cc,cs" shrinks the core and shell list capacities so that
+ *     atoms take the exact overflow path; RBMD_SELECT_EXACT=1 sends every batch selection
  *     through the exact 64-bit path; RBMD_SELECT_KEY_BITS=k keeps only k
  *     priority bits in the fast selection's keys (equal keys then send atoms
  *     to the exact path); RBMD_HOST_CHUNKS=k (1..8, read per call) sets the
