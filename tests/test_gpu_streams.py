@@ -112,3 +112,44 @@ def test_rbe_only_and_rbl_only_stay_on_one_stream(sys5k):
             Fo = o["F"] - o["Fsum"] / s.n
         assert rel_err(F, Fo) < 1e-10, key
         ctx.close()
+
+
+def test_user_stream(sys5k):
+    # a context on a caller's stream: the fork and join of the force evaluation and
+    # the host-buffer call order themselves against that stream, and the results
+    # are those of a context on the default stream
+    import torch
+
+    s = sys5k
+    ref, _ = make_ctx(s, rb.FP32, rbe_P=70, seed=9, thermostat=1)
+    ref.set_state_u(s.u, vel=s.v, step=0)
+    user = torch.cuda.Stream()
+    with torch.cuda.stream(user):
+        ctx, _ = make_ctx(s, rb.FP32, rbe_P=70, seed=9, thermostat=1)
+        ctx.set_state_u(s.u, vel=s.v, step=0)
+        assert ctx.stream.cuda_stream == user.cuda_stream
+        ctx.step(3)
+        F = ctx.forces(3)
+        pos = torch.from_numpy(s.x).float().pin_memory()
+        Fh = ctx.forces_host(pos, step=5)
+    user.synchronize()
+    ref.step(3)
+    assert torch.equal(F, ref.forces(3))
+    assert torch.equal(Fh, ref.forces_host(pos, step=5))
+    ctx.close()
+    ref.close()
+
+
+def test_host_call_while_profiling(sys5k):
+    # with stage events on (rbmd_profile) the host-buffer call runs its work in
+    # sequence on one stream; the forces do not change
+    import torch
+
+    s = sys5k
+    a, _ = make_ctx(s, rb.FP32, rbe_P=70, seed=10)
+    b, _ = make_ctx(s, rb.FP32, rbe_P=70, seed=10)
+    b.profile(True)
+    pos = torch.from_numpy(s.x).float().pin_memory()
+    assert torch.equal(a.forces_host(pos, step=2), b.forces_host(pos, step=2))
+    a.close()
+    b.close()
