@@ -586,6 +586,8 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
         rp.L = q.box_length;
         rp.lscale = rp.L / kTwo32;
         rp.dtc = q.dt * (kTwo32 / rp.L);
+        rp.dtc_hi = (float)rp.dtc;
+        rp.dtc_lo = (float)(rp.dtc - (double)rp.dtc_hi);
         rp.T0 = q.temperature;
         rp.key = make_uint2((uint32_t)(q.seed & 0xFFFFFFFFu), (uint32_t)(q.seed >> 32));
         rp.tag_rbe = RBMD_STREAM_RBE | (q.replica << 8);

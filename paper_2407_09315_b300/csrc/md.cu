@@ -162,7 +162,22 @@ __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
         // read-out does, so a resumed run is bit-identical to an unbroken one
         real vd = mul_rn(lam, v[3 * i + d]) + hdt * (F[3 * i + d] + (real)sc[SCAL_FCORR + d]);
         v[3 * i + d] = vd;
-        const long long du = llrint((double)vd * dtc);
+        long long du;
+        if constexpr (sizeof(real) == 4) {
+            // vd * dtc with dtc = dhi + dlo (two floats): p1 + e1 = vd dhi exactly,
+            // t = vd dlo + e1; the rounding of p1 + t to an integer, in FP32 (FP64
+            // operations are scarce on this GPU).  The product is good to about
+            // 1e-10 units, so the integer is that of the FP64 product except within
+            // that distance of a half-integer.
+            const float dhi = reps[a.r].dtc_hi, dlo = reps[a.r].dtc_lo;
+            const float p1 = __fmul_rn(vd, dhi);
+            const float e1 = __fmaf_rn(vd, dhi, -p1);
+            const float t = __fmaf_rn(vd, dlo, e1);
+            const float r = rintf(p1);
+            du = (long long)r + (long long)rintf(__fadd_rn(__fsub_rn(p1, r), t));
+        } else {
+            du = llrint((double)vd * dtc);
+        }
         pu[d] = pu[d] + (uint32_t)du;
     }
     u4[i] = A;

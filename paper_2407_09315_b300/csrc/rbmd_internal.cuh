@@ -94,6 +94,7 @@ struct Rep {
     uint32_t tag_rbe, tag_rbl;
     int32_t nc, M;          // cells per axis, sampler half-width
     float cull_r;           // r_cut in cell widths (+ margin)
+    float dtc_hi, dtc_lo;   // dtc as a sum of two floats (FP32 drift)
     int64_t atom0, N;
     int64_t cell0, ncell;
     int64_t cdf0;           // offset of the replica's sampler thresholds
