@@ -48,7 +48,8 @@ L2_FLUSH_BYTES = 256 << 20
 WORKLOAD = ["c3"]
 
 # Algorithmic FP32-pipe lane operations per unit of work (each elementary
-# function counted as one operation; FMA as one): see the design doc, roofline.
+# function counted as one operation; FMA as one); the roofline's peak is one such
+# operation per lane per clock: 148 SMs x 128 lanes x 2032 MHz.
 OPS_RHO_PER_ATOM_MODE = 8      # 3 phase IMAD, 1 convert, sin, cos, 2 FMA
 OPS_FORCE_PER_ATOM_MODE = 11   # 3 phase IMAD, 1 convert, sin, cos, 2 (g), 3 FMA
 OPS_CLASSIFY_PER_NEIGHBOUR = 7  # 3 sub, 3 IMAD, 1 compare
@@ -328,7 +329,7 @@ def roofline(stages_ms_per_step, system, peaks_clock_mhz):
     traffic = captured_traffic().get(top) if (N == 1_000_000 and WORKLOAD[0] == "c3") else None
     return {"bound": "alu", "kernel": top, "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "Top/s (FP32-pipe lane ops)", "frac": round(achieved / peak, 4),
-            "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2032 MHz (see DESIGN.md)",
+            "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2032 MHz",
             "traffic": traffic, "ms_per_launch": round(stages_ms_per_step[top], 4),
             "algorithmic_ops_per_launch": ops[top]}
 
@@ -474,7 +475,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "ms_per_step_median": round(statistics.median(ms), 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded %s, see DESIGN.md)" % WORKLOADS[args.workload]["charges"].replace("none", "LJ fluid"),
+        "data": "synthetic (seeded %s, paper-shaped recipe in synth.py)" % WORKLOADS[args.workload]["charges"].replace("none", "LJ fluid"),
         "config": workload_config(args, world, system),
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_pass": {"ms_per_step": round(sum(ms_prof) / len(ms_prof), 4),
@@ -525,7 +526,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded %s, see DESIGN.md)" % WORKLOADS[args.workload]["charges"].replace("none", "LJ fluid"),
+           "data": "synthetic (seeded %s, paper-shaped recipe in synth.py)" % WORKLOADS[args.workload]["charges"].replace("none", "LJ fluid"),
            "config": workload_config(args, world),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
