@@ -203,7 +203,9 @@ __global__ void k_kick_ke(real *__restrict__ v, real *__restrict__ F,
     double ke = 0.0;
     if (a.ok) {
         real f[3] = {F[3 * a.i], F[3 * a.i + 1], F[3 * a.i + 2]};
-        ke = second_kick(k, reps[a.r], a.r, a.i, v, F, f);
+        real fc[3];
+        kick_fcorr(k, a.r, fc);
+        ke = second_kick(k, reps[a.r], a.r, a.i, v, F, f, fc);
     }
     block_ke_partial(ke, k.kepart);
 }

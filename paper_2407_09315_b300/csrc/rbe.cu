@@ -559,7 +559,11 @@ __global__ void k_rbe_force(const uint4 *__restrict__ u4, const double *__restri
         f[0] = fo[0];
         f[1] = fo[1];
         f[2] = fo[2];
-        if constexpr (KICK) ke = second_kick(kick, reps[sl.r], sl.r, i, kick.v, F, fo);
+        if constexpr (KICK) {
+            real fc[3];
+            kick_fcorr(kick, sl.r, fc);
+            ke = second_kick(kick, reps[sl.r], sl.r, i, kick.v, F, fo, fc);
+        }
     }
     if constexpr (KICK) block_ke_partial(ke, kick.kepart);
 }
@@ -617,6 +621,8 @@ __global__ void __launch_bounds__(256 / AT) k_rbe_force_at(const uint4 *__restri
         }
     }
     double ke = 0.0;
+    float fc[3] = {0.f, 0.f, 0.f};
+    if constexpr (KICK) kick_fcorr(kick, r, fc);  // once for the thread's atoms
 #pragma unroll
     for (int h = 0; h < AT; ++h) {
         const int64_t i = (int64_t)mb.y + threadIdx.x + h * TB;
@@ -632,7 +638,7 @@ __global__ void __launch_bounds__(256 / AT) k_rbe_force_at(const uint4 *__restri
         f[0] = fo[0];
         f[1] = fo[1];
         f[2] = fo[2];
-        if constexpr (KICK) ke += second_kick(kick, rp, r, i, kick.v, F, fo);
+        if constexpr (KICK) ke += second_kick(kick, rp, r, i, kick.v, F, fo, fc);
     }
     if constexpr (KICK) block_ke_partial(ke, kick.kepart);
 }

@@ -353,15 +353,28 @@ template <typename real> struct KickArgs {
     StepRef sref;    // step of the force evaluation (Langevin counter)
 };
 
+__device__ __forceinline__ float kick_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double kick_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// F_corr of replica r in the working precision (the kick's constant force term).
+template <typename real>
+__device__ __forceinline__ void kick_fcorr(const KickArgs<real> &k, int r, real fc[3])
+{
+    const double *sc = k.scal + (int64_t)r * SCAL_COUNT;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) fc[d] = (real)sc[SCAL_FCORR + d];
+}
+
 // Second half kick of atom i of replica r with force f (the atom's final force
-// of the step, stored to F when the Langevin force is added to it); returns
-// |v|^2.  Non-finite velocities latch RBMD_ERR_NONFINITE.
+// of the step, stored to F when the Langevin force is added to it) and F_corr fc
+// (kick_fcorr); returns |v|^2, summed in the working precision (the block and
+// replica sums are FP64).  Non-finite velocities latch RBMD_ERR_NONFINITE.
 template <typename real>
 __device__ __forceinline__ double second_kick(const KickArgs<real> &k, const Rep &rp, int r,
                                               int64_t i, real *__restrict__ v, real *__restrict__ F,
-                                              real f[3])
+                                              real f[3], const real fc[3])
 {
-    const double *sc = k.scal + (int64_t)r * SCAL_COUNT;
+    (void)r;
     if (k.langevin) {
         real gn[3];
         langevin_normals((uint32_t)(i - rp.atom0), (uint32_t)step_of(k.sref), rp, gn);
@@ -372,17 +385,17 @@ __device__ __forceinline__ double second_kick(const KickArgs<real> &k, const Rep
             F[3 * i + d] = f[d];
         }
     }
-    double ke = 0.0;
+    real ke = 0;
     bool bad = false;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const real vd = v[3 * i + d] + k.hdt * (f[d] + (real)sc[SCAL_FCORR + d]);
+        const real vd = v[3 * i + d] + k.hdt * (f[d] + fc[d]);
         v[3 * i + d] = vd;
         bad |= !isfinite(vd);
-        ke += (double)vd * (double)vd;
+        ke = kick_fma(vd, vd, ke);
     }
     if (bad) latch_error(k.err, RBMD_ERR_NONFINITE);
-    return ke;
+    return (double)ke;
 }
 
 // Block sum of ke (every thread of the 256-thread block calls it) to kepart[block].
