@@ -327,11 +327,19 @@ def roofline(stages_ms_per_step, system, peaks_clock_mhz):
     peak = 148 * 128 * clock * 1e6 / 1e12  # Top/s, one FP32 lane-op per lane per clock
     achieved = ops[top] / t / 1e12
     traffic = captured_traffic().get(top) if (N == 1_000_000 and WORKLOAD[0] == "c3") else None
+    cap = captured_traffic() if (N == 1_000_000 and WORKLOAD[0] == "c3") else {}
+    every = {}
+    for k, n_ops in ops.items():
+        ms = stages_ms_per_step.get(k, 0.0)
+        if ms > 0:
+            a = n_ops / (ms * 1e-3) / 1e12
+            every[k] = {"achieved": round(a, 3), "frac": round(a / peak, 4),
+                        "ms_per_launch": round(ms, 4), "traffic": cap.get(k)}
     return {"bound": "alu", "kernel": top, "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "Top/s (FP32-pipe lane ops)", "frac": round(achieved / peak, 4),
             "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2032 MHz",
             "traffic": traffic, "ms_per_launch": round(stages_ms_per_step[top], 4),
-            "algorithmic_ops_per_launch": ops[top]}
+            "algorithmic_ops_per_launch": ops[top], "every_kernel": every}
 
 
 def e2e_force_step(ctx, system, K, W, device):
