@@ -449,7 +449,8 @@ int32_t rbmd_step_kernel_count(rbmd_ctx *ctx);
  * the previous call, but calls that overlap on the GPU (two streams of the
  * same device) race on it; calls are also not thread-safe on the host.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.
+ * any stream capture.  The address is kept for the life of the process, so a
+ * device reset (cudaDeviceReset) between calls is not supported.
  * Errors: RBMD_ERR_INVALID for null pointers, N < 1 or N > 2^31 - 1,
  * P > RBMD_NOALLOC_MAX_P, or a sampler table longer than RBMD_NOALLOC_MAX_TABLE
  * entries (box too large for alpha); RBMD_ERR_CUDA if a launch fails.

@@ -161,16 +161,33 @@ def rbe_forces_noalloc(u, charge, box_length, *, alpha, coulomb_k, P, seed, step
     """RBE force without a context or any device allocation (FP32).
 
     u: CUDA int32/uint32 tensor [N, 3] of fixed-point positions; charge: CUDA
-    float32 [N]; out: CUDA float32 [N, 3], overwritten.  For callers that cannot
-    allocate device memory; all scratch is a fixed static device array.
+    float32 [N]; out: CUDA float32 [N, 3], overwritten.  All three must be
+    contiguous and on one device.  For callers that cannot allocate device
+    memory; all scratch is a fixed static device array.
     """
     import torch
 
-    if stream is None:
-        stream = torch.cuda.current_stream(out.device)
-    _check(lib().rbmd_rbe_forces_noalloc(_ptr(u), _ptr(charge), int(u.shape[0]), box_length,
-                                         alpha, coulomb_k, P, seed, step, replica, _ptr(out),
-                                         C.c_void_p(stream.cuda_stream)), "rbe_forces_noalloc")
+    ok_u = getattr(torch, "uint32", None)
+    if not all(isinstance(t, torch.Tensor) and t.is_cuda for t in (u, charge, out)):
+        raise ValueError("u, charge and out must be CUDA tensors")
+    if not (u.device == charge.device == out.device):
+        raise ValueError("u, charge and out must be on one device")
+    if not all(t.is_contiguous() for t in (u, charge, out)):
+        raise ValueError("u, charge and out must be contiguous")
+    if u.dim() != 2 or u.shape[1] != 3 or u.dtype not in (torch.int32, ok_u):
+        raise ValueError("u must be an int32 or uint32 tensor of shape [N, 3]")
+    n = int(u.shape[0])
+    if charge.dtype != torch.float32 or tuple(charge.shape) != (n,):
+        raise ValueError("charge must be a float32 tensor of shape [N]")
+    if out.dtype != torch.float32 or tuple(out.shape) != (n, 3):
+        raise ValueError("out must be a float32 tensor of shape [N, 3]")
+    with torch.cuda.device(out.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(out.device)
+        _check(lib().rbmd_rbe_forces_noalloc(_ptr(u), _ptr(charge), n, box_length, alpha,
+                                             coulomb_k, P, seed, step, replica, _ptr(out),
+                                             C.c_void_p(stream.cuda_stream)),
+               "rbe_forces_noalloc")
     return out
 
 

@@ -39,17 +39,33 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+    """Compile every csrc/*.cu to an object file (in parallel), then link them
+    into librbmd.so with the CUDA runtime linked statically."""
     if not force and up_to_date():
         return OUT
-    tmp = OUT + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), "-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-ffp-contract=off", "-shared", "-cudart", "static",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp, *sources()]
+    from concurrent.futures import ThreadPoolExecutor
+
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    flags = ["-O3", "-lineinfo", "-std=c++17", *ARCH, "-Xcompiler", "-fPIC",
+             "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
+        flags.insert(0, "-Xptxas=-v")
     if extra:
-        cmd[1:1] = list(extra)
-    subprocess.check_call(cmd)
+        flags[0:0] = list(extra)
+    objs = []
+    cmds = []
+    for src in sources():
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".%d.o" % os.getpid())
+        objs.append(obj)
+        cmds.append([nvcc(), *flags, "-c", "-o", obj, src])
+    with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+        for f in [ex.submit(subprocess.check_call, c) for c in cmds]:
+            f.result()
+    tmp = OUT + ".tmp%d" % os.getpid()
+    subprocess.check_call([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, OUT)
     return OUT
 

@@ -2,7 +2,9 @@
 in the launch configuration bench.py times (its context, autotuned tiles, the
 integrator's step graph): modes and lists bit-exact, and forces and energies of a
 seeded sample of atoms against the oracle, which computes them one by one (the
-momentum correction and the energies over all atoms)."""
+momentum correction and the energies over all atoms).  Both the FP32 path and the
+plain FP64 path its speed-up is quoted against (with the FP64 leg's own autotuned
+shape, which picks the pair look-up table) are checked."""
 import numpy as np
 import pytest
 
@@ -27,7 +29,20 @@ def setup():
     ctx.close()
 
 
-def _check_state(prm, s, u, ctx, step, sample):
+@pytest.fixture(scope="module")
+def setup64():
+    import torch
+
+    import bench
+
+    system = bench.make_system(1_000_000, 2, "c3")
+    ctx = bench.make_ctx(system, rb.FP64, torch.device("cuda:0"))
+    ctx.autotune(step=0)
+    yield bench.PARAMS, system.systems[0], ctx
+    ctx.close()
+
+
+def _check_state(prm, s, u, ctx, step, sample, prec=rb.FP32):
     # modes of the step, bit for bit
     m, _ = ctx.rbe_modes(step)
     mo = oracle.rbe_sample(2, step, prm["rbe_P"], s.L, prm["alpha"])
@@ -44,10 +59,10 @@ def _check_state(prm, s, u, ctx, step, sample):
     Fr, Er, _, _ = oracle.rbe_forces(u, s.q, s.L, prm["alpha"], prm["coulomb_k"], prm["rbe_P"], 2,
                                      step, sel=sample)
     Fo = Fr + o["F"] - o["Fsum"] / s.n
-    assert rel_err(F, Fo) < TOL[rb.FP32], rel_err(F, Fo)
+    assert rel_err(F, Fo) < TOL[prec], rel_err(F, Fo)
     E = ctx.energy(step)
     for k, ref in (("e_coul_real", o["E_coul"]), ("e_lj", o["E_lj"]), ("e_rbe", Er)):
-        assert abs(E[k] - ref) <= 1e-5 * abs(ref), (k, E[k], ref)
+        assert abs(E[k] - ref) <= TOL[prec] * abs(ref), (k, E[k], ref)
 
 
 def test_full_size_initial_state(setup):
@@ -67,3 +82,15 @@ def test_full_size_after_steps(setup):
     assert np.abs(d).max() < 2 ** 32 // 1000
     sample = np.sort(np.random.default_rng(6).choice(s.n, 400, replace=False))
     _check_state(prm, s, u, ctx, 3, sample)
+
+
+def test_full_size_fp64_path(setup64):
+    prm, s, ctx = setup64
+    assert ctx.tiles()[3] in (0, 1)
+    sample = np.sort(np.random.default_rng(7).choice(s.n, 200, replace=False))
+    _check_state(prm, s, s.u, ctx, 0, sample, rb.FP64)
+    ctx.step(2)
+    u, _, st = ctx.get_state_u()
+    assert st == 2
+    u = (to_np(u).astype(np.int64) % 2 ** 32).astype(np.uint32)
+    _check_state(prm, s, u, ctx, 2, sample, rb.FP64)

@@ -180,16 +180,93 @@ def test_fp64_trajectory_matches_oracle(thermostat):
     ctx.close()
 
 
-def test_fp32_step_stays_close_to_oracle():
-    s = synth.electrolyte(1000, seed=14, charges="1:1", n_types=1)
-    ctx, _ = make_ctx(s, rb.FP32, rbe_P=50, seed=3, dt=0.001, thermostat=1)
+def _wrap_diff(a, b):
+    a = np.asarray(a).astype(np.int64)
+    b = np.asarray(b).astype(np.int64)
+    return (a - b + 2 ** 31) % 2 ** 32 - 2 ** 31
+
+
+def _half_gap(y):
+    """Distance of y from the nearest half-integer (where rint changes)."""
+    return np.abs(np.abs(y - np.floor(y)) - 0.5)
+
+
+@pytest.mark.parametrize("L,dt,vscale", [(17.1, 0.001, 1.0), (17.1, 0.001, 1000.0),
+                                          (170.99759466766966, 0.002, 30.0)])
+def test_fp32_drift_fixed_point_exact(L, dt, vscale):
+    # Sec. 2.1 drift of the fixed-point state in isolation: with every force
+    # exactly zero on both sides the velocities stay
+    # the stored FP32 values and each step adds rint(v dt 2^32/L) to u.  The FP32
+    # path forms that product from two floats (v * (dhi + dlo)); it must give the
+    # oracle's FP64 integer exactly, except within 1e-5 units of a half-integer,
+    # where a rounding of the product may decide (counted, and rare).  vscale up
+    # to 1000 makes |v dt 2^32/L| reach 2.5e8, far beyond the 24-bit mantissa of
+    # one float, so a dropped low part of the factor fails.
+    n = 2000
+    rng = np.random.default_rng(41)
+    u0 = rng.integers(0, 2 ** 32, size=(n, 3), dtype=np.uint64).astype(np.uint32)
+    v = (rng.standard_normal((n, 3)) * vscale).astype(np.float32).astype(np.float64)
+    s = synth.System(L=L, u=u0, q=np.zeros(n), types=np.zeros(n, np.int32),
+                     eps=np.array([0.0]), sig=np.array([1.0]), v=v)
+    # the library skips both force parts (its forces are then exactly zero); the
+    # oracle computes them with q = 0 and eps = 0, which is exactly zero too
+    ctx, _ = make_ctx(s, rb.FP32, rbe_P=20, seed=1, dt=dt, thermostat=0, r_core=1.0, r_cut=2.0,
+                      flags=rb.NO_RBE | rb.NO_RBL)
     ctx.set_state_u(s.u, vel=s.v, step=0)
-    ctx.step(3)
-    u, v, _ = ctx.get_state_u()
-    F0, _ = oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 50, 3, 0)
-    uo, vo, _ = oracle.vv(s.u, s.v, F0, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10,
-                          50, seed=3, step0=0, dt=0.001, n_steps=3, thermostat=1)
-    assert rel_err(to_np(v), vo) < 1e-5
+    u_ref = u0.copy()
+    F0 = np.zeros((n, 3))
+    near_total = 0
+    for k in range(3):
+        ctx.step(1)
+        u, vg, st = ctx.get_state_u()
+        assert st == k + 1
+        assert np.array_equal(to_np(vg), v)  # zero force: velocities unchanged, bit for bit
+        u_ref, vo, _ = oracle.vv(u_ref, v, F0, s.q, s.types, s.eps, s.sig, L, 0.62, 1.0, 1.0, 2.0,
+                                 10, 20, seed=1, step0=k, dt=dt, n_steps=1)
+        assert np.array_equal(vo, v)
+        du = _wrap_diff(to_np(u).astype(np.int64) % 2 ** 32, u_ref)
+        near = _half_gap(v * (dt * (4294967296.0 / L))) < 1e-5
+        assert np.all(du[~near] == 0), (k, np.argwhere(du[~near] != 0)[:5])
+        assert np.all(np.abs(du[near]) <= 1)
+        near_total += int(near.sum())
+        u_ref = (to_np(u).astype(np.int64) % 2 ** 32).astype(np.uint32)  # continue from the GPU state
+    assert near_total <= 3  # probability ~2e-5 per coordinate
+    ctx.close()
+
+
+@pytest.mark.parametrize("thermostat", [0, 1])
+def test_fp32_step_positions_track_oracle_each_step(thermostat):
+    # One FP32 step at a time from the GPU's own state (u_k, v_k): the oracle
+    # takes the same state and its FP64 force of step k and makes one
+    # velocity-Verlet step (Sec. 2.1).  The half-kick velocity differs only by
+    # FP32 rounding of v + F dt/2 (relative 1e-7) and the FP32 force error, so the
+    # drift integer rint(v_half dt 2^32/L) may differ by one unit only where the
+    # oracle's v_half dt 2^32/L lies near a half-integer; everywhere else u must
+    # be identical.  Velocities after the step within the FP32 tolerance.
+    s = synth.electrolyte(1000, seed=14, charges="1:1", n_types=1)
+    dt = 0.001
+    c = dt * (4294967296.0 / s.L)
+    ctx, _ = make_ctx(s, rb.FP32, rbe_P=50, seed=3, dt=dt, thermostat=thermostat)
+    ctx.set_state_u(s.u, vel=s.v, step=0)
+    flips = 0
+    for k in range(4):
+        uk, vk, st = ctx.get_state_u()
+        assert st == k
+        uk = (to_np(uk).astype(np.int64) % 2 ** 32).astype(np.uint32)
+        vk = to_np(vk)
+        Fk, _ = oracle.forces(uk, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 50, 3, k)
+        uo, vo, _ = oracle.vv(uk, vk, Fk, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10,
+                              50, seed=3, step0=k, dt=dt, n_steps=1, thermostat=thermostat)
+        ctx.step(1)
+        u, v, _ = ctx.get_state_u()
+        du = _wrap_diff(to_np(u).astype(np.int64) % 2 ** 32, uo)
+        assert np.max(np.abs(du)) <= 1, k
+        gap = _half_gap((vk + 0.5 * dt * Fk) * c)
+        # a flipped coordinate sits within the velocity error's reach of a tie
+        assert np.all(gap[du != 0] < 0.05), (k, gap[du != 0].max())
+        flips += int(np.count_nonzero(du))
+        assert rel_err(to_np(v), vo) < 1e-5, k
+    assert flips <= 0.02 * 4 * 3 * s.n, flips
     ctx.close()
 
 
