@@ -47,7 +47,10 @@ def lib():
         L.orc_rbl_R2.argtypes = [dbl, dbl]
         L.orc_rbl_R2.restype = u64
         L.orc_rbl.argtypes = [i64, P, P, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, i32, u64,
-                              i64, u32, i32, i32, i64, P, P, P, P, P, P, i32, P, P, P]
+                              i64, u32, i32, i32, i64, P, P, P, P, P, P, i32, P, P, P, P, P]
+        L.orc_mode_virial.argtypes = [i64, P, P, dbl, dbl, dbl, i64, P, P, P]
+        L.orc_rbe_virial.argtypes = [i64, P, P, dbl, dbl, dbl, C.c_int, u64, i64, u32, P]
+        L.orc_ewald_virial.argtypes = [i64, P, P, dbl, dbl, dbl, dbl, C.c_int, P, P]
         L.orc_forces.argtypes = [i64, P, P, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, i32, i32,
                                  u64, i64, u32, i32, P, P]
         L.orc_energy_grad.argtypes = [i64, P, P, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, i32,
@@ -187,6 +190,46 @@ def ewald(u, q, L, alpha, coulomb_k, r_cut, M):
 
 
 # --------------------------------------------------------------------------
+# Virial tensors (W = -dE/d strain at fixed fractional coordinates)
+# --------------------------------------------------------------------------
+def tensor(w6):
+    """3x3 symmetric matrix of the six components xx, yy, zz, xy, xz, yz."""
+    w = np.asarray(w6, dtype=np.float64)
+    return np.array([[w[0], w[3], w[4]], [w[3], w[1], w[5]], [w[4], w[5], w[2]]])
+
+
+def mode_virial(u, q, L, alpha, coulomb_k, m, W):
+    """Virial of the weighted Fourier-mode energy (3x3)."""
+    u = _u(u)
+    q = _d(q)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    W = _d(W)
+    out = np.zeros(6)
+    lib().orc_mode_virial(len(u), _p(u), _p(q), L, alpha, coulomb_k, len(m), _p(m), _p(W),
+                          _p(out))
+    return tensor(out)
+
+
+def rbe_virial(u, q, L, alpha, coulomb_k, P, seed, step, replica=0):
+    """RBE estimate of the Fourier-space virial of one step (3x3)."""
+    u = _u(u)
+    q = _d(q)
+    out = np.zeros(6)
+    lib().orc_rbe_virial(len(u), _p(u), _p(q), L, alpha, coulomb_k, P, seed, step, replica,
+                         _p(out))
+    return tensor(out)
+
+
+def ewald_virial(u, q, L, alpha, coulomb_k, r_cut, M):
+    """Full Ewald virial: (real-space 3x3, Fourier 3x3)."""
+    u = _u(u)
+    q = _d(q)
+    wr, wk = np.zeros(6), np.zeros(6)
+    lib().orc_ewald_virial(len(u), _p(u), _p(q), L, alpha, coulomb_k, r_cut, M, _p(wr), _p(wk))
+    return tensor(wr), tensor(wk)
+
+
+# --------------------------------------------------------------------------
 # Random batch list (Sec. 2.3, Eqs. 13-16, Algorithm 2)
 # --------------------------------------------------------------------------
 def rbl_R2(r, L):
@@ -197,7 +240,8 @@ def rbl(u, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, seed, step
         replica=0, exact=False, use_cells=True, sel=None, want_all=True):
     """Returns dict with F (uncorrected F_core + F_shell*), n_core, n_shell,
     n_batch, batch (ids ascending, -1 padded), Fsum (over all atoms, if
-    want_all), E_coul, E_lj."""
+    want_all), E_coul, E_lj, and the virial tensors W_coul, W_lj (3x3, over all
+    atoms, if want_all)."""
     u = _u(u)
     q = _d(q)
     types = np.ascontiguousarray(types, dtype=np.int32)
@@ -214,12 +258,13 @@ def rbl(u, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, seed, step
     b = np.zeros((ns, p), dtype=np.int64)
     Fs = np.zeros(3)
     Ec, El = C.c_double(), C.c_double()
+    Wc, Wl = np.zeros(6), np.zeros(6)
     lib().orc_rbl(n, _p(u), _p(q), _p(types), len(eps), _p(eps), _p(sig), L, alpha, coulomb_k,
                   r_core, r_cut, p, seed, step, replica, int(exact), int(use_cells),
                   0 if sel is None else len(sel), _p(sel), _p(F), _p(nc), _p(nsh), _p(nb),
-                  _p(b), int(want_all), _p(Fs), C.byref(Ec), C.byref(El))
+                  _p(b), int(want_all), _p(Fs), C.byref(Ec), C.byref(El), _p(Wc), _p(Wl))
     return dict(F=F, n_core=nc, n_shell=nsh, n_batch=nb, batch=b, Fsum=Fs,
-                E_coul=Ec.value, E_lj=El.value)
+                E_coul=Ec.value, E_lj=El.value, W_coul=tensor(Wc), W_lj=tensor(Wl))
 
 
 def forces(u, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P, seed, step,

@@ -287,6 +287,62 @@ void orc_rbe_forces(int64_t n, const uint32_t *u, const double *q, double L, dou
 }
 
 /* ------------------------------------------------------------------------ */
+/* Virial tensor of the weighted Fourier-mode energy (pressure, Sec. 2.2).   */
+/* The virial is W_ab = -dE/d e_ab, the derivative of the energy under the   */
+/* affine strain x -> (1 + e) x of the box and of every position at fixed    */
+/* fractional coordinates (reading: the paper names the virial among its     */
+/* outputs but prints no formula).  Under that strain V -> V (1 + tr e),     */
+/* k -> (1 - e^T) k and every phase k.r_j is unchanged, so rho(k) is too.    */
+/* For the mode energy e_l = coulomb_k W_l (2 pi/V) |rho_l|^2 / k_l^2 with   */
+/* W_l = exp(-k_l^2/4 alpha) (the Ewald term of Eq. 8) the derivative is     */
+/*   W_ab = sum_l e_l [delta_ab - 2 k_a k_b (1/k_l^2 + 1/(4 alpha))],        */
+/* the 1/(4 alpha) part coming from the Gaussian.  The RBE estimate (Eq. 12 */
+/* sampling) reuses it with W_l = S/P: it is then an unbiased estimate of    */
+/* the Ewald virial, not the derivative of the RBE energy estimate (whose   */
+/* modes and S depend on L).  W_out[6] = xx, yy, zz, xy, xz, yz.            */
+/* ------------------------------------------------------------------------ */
+void orc_mode_virial(int64_t n, const uint32_t *u, const double *q, double L, double alpha,
+                     double coulomb_k, int64_t nm, const int32_t *m, const double *W,
+                     double *W_out)
+{
+    double V = L * L * L;
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(2 * (nm > 0 ? nm : 1)));
+    orc_structure_factor(n, u, q, L, nm, m, rho);
+    for (int c = 0; c < 6; ++c) W_out[c] = 0.0;
+    for (int64_t l = 0; l < nm; ++l) {
+        double k[3];
+        for (int d = 0; d < 3; ++d) k[d] = 2.0 * ORC_PI * m[3 * l + d] / L;
+        double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        if (k2 == 0.0) continue;
+        double re = rho[2 * l], im = rho[2 * l + 1];
+        double e = coulomb_k * W[l] * (2.0 * ORC_PI / V) * (re * re + im * im) / k2;
+        double b = 2.0 * (1.0 / k2 + 1.0 / (4.0 * alpha));
+        W_out[0] += e * (1.0 - b * k[0] * k[0]);
+        W_out[1] += e * (1.0 - b * k[1] * k[1]);
+        W_out[2] += e * (1.0 - b * k[2] * k[2]);
+        W_out[3] += e * (-b * k[0] * k[1]);
+        W_out[4] += e * (-b * k[0] * k[2]);
+        W_out[5] += e * (-b * k[1] * k[2]);
+    }
+    free(rho);
+}
+
+/* RBE virial estimate of one step: the modes of orc_rbe_sample, W_l = S/P. */
+void orc_rbe_virial(int64_t n, const uint32_t *u, const double *q, double L, double alpha,
+                    double coulomb_k, int P, uint64_t seed, int64_t step, uint32_t replica,
+                    double *W_out)
+{
+    int32_t *m = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * P));
+    double *W = (double *)malloc(sizeof(double) * (size_t)P);
+    orc_rbe_sample(seed, step, replica, P, L, alpha, m);
+    double S = orc_rbe_S(L, alpha);
+    for (int l = 0; l < P; ++l) W[l] = S / (double)P;
+    orc_mode_virial(n, u, q, L, alpha, coulomb_k, P, m, W, W_out);
+    free(W);
+    free(m);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Full Ewald sum (Eqs. 8, 10, 11) as the physics reference.                 */
 /*  real space: explicit images n with |r_ij + nL| < r_cut (i != j or n != 0)*/
 /*  reciprocal: all m != 0 with |m_d| <= M                                   */
@@ -332,6 +388,51 @@ void orc_ewald(int64_t n, const uint32_t *u, const double *q, double L, double a
     double q2 = 0.0;
     for (int64_t i = 0; i < n; ++i) q2 += q[i] * q[i];
     *E_self = -coulomb_k * sqrt(alpha / ORC_PI) * q2;
+    free(W);
+    free(m);
+    free(x);
+}
+
+/* Virial tensor of the full Ewald sum (same readings as orc_ewald): the     */
+/* real-space part over explicit images, 1/2 sum over ordered pairs of       */
+/* r_ij (x) F_ij with F_ij the erfc-Coulomb force on i from j (Eq. 10) and   */
+/* r_ij = r_i - r_j + nL; the Fourier part from orc_mode_virial over every   */
+/* m != 0 with |m_d| <= M.  The self term does not depend on the strain.     */
+void orc_ewald_virial(int64_t n, const uint32_t *u, const double *q, double L, double alpha,
+                      double coulomb_k, double r_cut, int M, double *W_real, double *W_recip)
+{
+    double *x = (double *)malloc(sizeof(double) * (size_t)(3 * n));
+    orc_decode(n, u, L, x);
+    double sa = sqrt(alpha);
+    int nimg = (int)ceil(r_cut / L) + 1;
+    for (int c = 0; c < 6; ++c) W_real[c] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            for (int a = -nimg; a <= nimg; ++a)
+                for (int b = -nimg; b <= nimg; ++b)
+                    for (int c = -nimg; c <= nimg; ++c) {
+                        if (i == j && a == 0 && b == 0 && c == 0) continue;
+                        double r3[3] = {x[3 * i] - x[3 * j] + a * L,
+                                        x[3 * i + 1] - x[3 * j + 1] + b * L,
+                                        x[3 * i + 2] - x[3 * j + 2] + c * L};
+                        double r = sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
+                        if (r >= r_cut) continue;
+                        double qq = coulomb_k * q[i] * q[j];
+                        double g = qq * (erfc(sa * r) / (r * r) +
+                                         2.0 * sa / sqrt(ORC_PI) * exp(-alpha * r * r) / r);
+                        double f[3] = {g * r3[0] / r, g * r3[1] / r, g * r3[2] / r};
+                        W_real[0] += 0.5 * r3[0] * f[0];
+                        W_real[1] += 0.5 * r3[1] * f[1];
+                        W_real[2] += 0.5 * r3[2] * f[2];
+                        W_real[3] += 0.5 * r3[0] * f[1];
+                        W_real[4] += 0.5 * r3[0] * f[2];
+                        W_real[5] += 0.5 * r3[1] * f[2];
+                    }
+    int64_t nm = orc_full_modes(L, alpha, M, NULL, NULL);
+    int32_t *m = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * nm));
+    double *W = (double *)malloc(sizeof(double) * (size_t)nm);
+    orc_full_modes(L, alpha, M, m, W);
+    orc_mode_virial(n, u, q, L, alpha, coulomb_k, nm, m, W, W_recip);
     free(W);
     free(m);
     free(x);
@@ -410,9 +511,11 @@ static uint64_t orc_priority(const orc_rbl_sys *S, int64_t i, int64_t j)
     return ((uint64_t)w[0] << 32) | w[1];
 }
 
-/* Pair energy and the force on i from j (vector along r_i - r_j, min image). */
+/* Pair energy and the force on i from j (vector along r_i - r_j, min image).
+ * rij (may be NULL) receives r_i - r_j, gparts (may be NULL) the Coulomb and LJ
+ * parts of -dU/dr. */
 static void orc_pair(const orc_rbl_sys *S, const double *x, int64_t i, int64_t j,
-                     double *e_coul, double *e_lj, double f[3])
+                     double *e_coul, double *e_lj, double f[3], double rij[3], double gparts[2])
 {
     double r3[3];
     for (int d = 0; d < 3; ++d) {
@@ -431,9 +534,25 @@ static void orc_pair(const orc_rbl_sys *S, const double *x, int64_t i, int64_t j
     *e_coul = qq * erfc(sa * r) / r;
     *e_lj = 4.0 * eps * (sr12 - sr6);
     /* -dU/dr */
-    double g = qq * (erfc(sa * r) / (r * r) + 2.0 * sa / sqrt(ORC_PI) * exp(-S->alpha * r * r) / r) +
-               24.0 * eps * (2.0 * sr12 - sr6) / r;
+    double gc = qq * (erfc(sa * r) / (r * r) + 2.0 * sa / sqrt(ORC_PI) * exp(-S->alpha * r * r) / r);
+    double gl = 24.0 * eps * (2.0 * sr12 - sr6) / r;
+    double g = gc + gl;
     for (int d = 0; d < 3; ++d) f[d] = g * r3[d] / r;
+    if (rij) for (int d = 0; d < 3; ++d) rij[d] = r3[d];
+    if (gparts) { gparts[0] = gc; gparts[1] = gl; }
+}
+
+/* Adds s * r (x) (g r / |r|) to the 6-component tensor acc (xx yy zz xy xz yz). */
+static void orc_add_virial(double *acc, double s, const double r3[3], double g)
+{
+    double r = sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
+    double h = s * g / r;
+    acc[0] += h * r3[0] * r3[0];
+    acc[1] += h * r3[1] * r3[1];
+    acc[2] += h * r3[2] * r3[2];
+    acc[3] += h * r3[0] * r3[1];
+    acc[4] += h * r3[0] * r3[2];
+    acc[5] += h * r3[1] * r3[2];
 }
 
 /* Candidate enumeration: brute force over all j, or the 27 (deduplicated)
@@ -566,6 +685,13 @@ static void orc_build_cells(orc_rbl_sys *S)
  *               ascending, -1 padded (batch only if p-width fits; any may be NULL)
  *   Fsum_out  : sum over ALL atoms of F_core + F_shell* (so F_corr = -Fsum/N)
  *   E_coul_out, E_lj_out : energy of Sec. 2.3 reading, over ALL atoms
+ *   W_coul_out, W_lj_out : (may be NULL) virial tensors [6] (xx yy zz xy xz yz)
+ *               of the erfc-Coulomb and LJ parts of that energy, over ALL
+ *               atoms: W = -dE/d(strain) with the list weights held fixed,
+ *               1/2 sum_i [sum_{C(i)} r_ij (x) F_ij + w_i sum_{B(i)} r_ij (x) F_ij],
+ *               r_ij = r_i - r_j (minimum image), F_ij the pair force on i.
+ *               The momentum correction (Eq. 16) is not a pair force and
+ *               adds nothing (reading).
  *   want_all  : 1 to evaluate every atom (needed for Fsum and energies)
  */
 void orc_rbl(int64_t n, const uint32_t *u, const double *q, const int32_t *type,
@@ -574,7 +700,7 @@ void orc_rbl(int64_t n, const uint32_t *u, const double *q, const int32_t *type,
              int64_t step, uint32_t replica, int32_t exact, int32_t use_cells, int64_t n_sel,
              const int64_t *sel, double *F_out, int32_t *n_core, int32_t *n_shell,
              int32_t *n_batch, int64_t *batch, int32_t want_all, double *Fsum_out,
-             double *E_coul_out, double *E_lj_out)
+             double *E_coul_out, double *E_lj_out, double *W_coul_out, double *W_lj_out)
 {
     orc_rbl_sys S;
     memset(&S, 0, sizeof(S));
@@ -592,6 +718,7 @@ void orc_rbl(int64_t n, const uint32_t *u, const double *q, const int32_t *type,
 
     /* per-atom evaluation */
     double Fs[3] = {0, 0, 0}, Ec = 0.0, El = 0.0;
+    double Wc[6] = {0, 0, 0, 0, 0, 0}, Wl[6] = {0, 0, 0, 0, 0, 0};
     int64_t ns = sel ? n_sel : n;
     int64_t nloop = want_all ? n : ns;
     /* map atom -> selected slot when both are needed */
@@ -612,16 +739,20 @@ void orc_rbl(int64_t n, const uint32_t *u, const double *q, const int32_t *type,
         }
         int32_t nb = 0;
         double w = orc_rbl_lists(&S, i, &cand, &core, &shell, bt, &nb);
-        double Fi[3] = {0, 0, 0}, ec, el, f[3];
+        double Fi[3] = {0, 0, 0}, ec, el, f[3], r3[3], gp[2];
         for (int64_t k = 0; k < core.count; ++k) {
-            orc_pair(&S, x, i, core.ids[k], &ec, &el, f);
+            orc_pair(&S, x, i, core.ids[k], &ec, &el, f, r3, gp);
             Ec += 0.5 * ec; El += 0.5 * el;
+            orc_add_virial(Wc, 0.5, r3, gp[0]);
+            orc_add_virial(Wl, 0.5, r3, gp[1]);
             for (int d = 0; d < 3; ++d) Fi[d] += f[d];
         }
         double Fb[3] = {0, 0, 0};
         for (int k = 0; k < nb; ++k) {
-            orc_pair(&S, x, i, bt[k], &ec, &el, f);
+            orc_pair(&S, x, i, bt[k], &ec, &el, f, r3, gp);
             Ec += 0.5 * w * ec; El += 0.5 * w * el;
+            orc_add_virial(Wc, 0.5 * w, r3, gp[0]);
+            orc_add_virial(Wl, 0.5 * w, r3, gp[1]);
             for (int d = 0; d < 3; ++d) Fb[d] += f[d];
         }
         for (int d = 0; d < 3; ++d) Fi[d] += w * Fb[d];
@@ -639,6 +770,8 @@ void orc_rbl(int64_t n, const uint32_t *u, const double *q, const int32_t *type,
     if (Fsum_out) for (int d = 0; d < 3; ++d) Fsum_out[d] = Fs[d];
     if (E_coul_out) *E_coul_out = Ec;
     if (E_lj_out) *E_lj_out = El;
+    if (W_coul_out) for (int c = 0; c < 6; ++c) W_coul_out[c] = Wc[c];
+    if (W_lj_out) for (int c = 0; c < 6; ++c) W_lj_out[c] = Wl[c];
     free(slot);
     free(bt);
     free(cand.ids); free(core.ids); free(shell.ids);
@@ -664,7 +797,8 @@ void orc_forces(int64_t n, const uint32_t *u, const double *q, const int32_t *ty
     orc_rbe_forces(n, u, q, L, alpha, coulomb_k, P, seed, step, replica, 0, NULL, Fr, &Erbe,
                    NULL, NULL);
     orc_rbl(n, u, q, type, n_types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, seed, step,
-            replica, exact, 1, 0, NULL, Fs, NULL, NULL, NULL, NULL, 1, Fsum, &Ec, &El);
+            replica, exact, 1, 0, NULL, Fs, NULL, NULL, NULL, NULL, 1, Fsum, &Ec, &El, NULL,
+            NULL);
     for (int64_t i = 0; i < n; ++i)
         for (int d = 0; d < 3; ++d)
             F_out[3 * i + d] = Fr[3 * i + d] + Fs[3 * i + d] - Fsum[d] / (double)n;
