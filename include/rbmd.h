@@ -130,6 +130,20 @@ typedef struct {
     int64_t step;         /* step the energies were evaluated at */
     int32_t max_shell;    /* largest N_s over atoms */
     int32_t max_cell;     /* largest cell occupancy */
+    /* Virial W_ab = -dE/d(strain_ab) at fixed fractional coordinates (the box and
+     * every position deformed together).  Pair part (list weights held fixed):
+     * 1/2 sum_i [sum_{C(i)} r_ij (x) F_ij + (N_s/p) sum_{B(i)} r_ij (x) F_ij],
+     * r_ij = r_i - r_j (minimum image), F_ij the erfc-Coulomb + LJ pair force on i
+     * (Eqs. 2, 10, 15).  Fourier part: sum_l e_l [delta_ab - 2 k_a k_b (1/k_l^2 +
+     * 1/(4 alpha))] over the drawn modes with e_l the terms of e_rbe, an unbiased
+     * estimate of the virial of Eq. 8's Fourier term (the strain derivative of
+     * its Gaussian weights and 1/V).  The self term and the momentum correction
+     * (Eq. 16) add nothing.  FP64 reductions. */
+    double virial[6];        /* xx, yy, zz, xy, xz, yz of the total */
+    double virial_coul_real; /* trace of the erfc-Coulomb pair part */
+    double virial_lj;        /* trace of the LJ pair part */
+    double virial_rbe;       /* trace of the Fourier (RBE) part */
+    double pressure;         /* (2 e_kinetic + trace of virial) / (3 V) */
 } rbmd_energy_terms;
 
 /* Name of a status code (static string). */

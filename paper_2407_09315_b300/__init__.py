@@ -50,6 +50,8 @@ class EnergyTerms(C.Structure):
         ("e_self", C.c_double), ("e_potential", C.c_double), ("e_kinetic", C.c_double),
         ("temperature", C.c_double), ("S", C.c_double), ("fsum_short", C.c_double * 3),
         ("step", C.c_int64), ("max_shell", C.c_int32), ("max_cell", C.c_int32),
+        ("virial", C.c_double * 6), ("virial_coul_real", C.c_double), ("virial_lj", C.c_double),
+        ("virial_rbe", C.c_double), ("pressure", C.c_double),
     ]
 
 
@@ -310,6 +312,8 @@ class RBMD:
     def _terms(e) -> dict:
         d = {k: getattr(e, k) for k, _ in EnergyTerms._fields_}
         d["fsum_short"] = list(e.fsum_short)
+        w = list(e.virial)
+        d["virial"] = np.array([[w[0], w[3], w[4]], [w[3], w[1], w[5]], [w[4], w[5], w[2]]])
         return d
 
     def energy(self, step) -> dict:

@@ -171,20 +171,51 @@ __global__ void k_zero_slots(double *scal, int R, int slot0, int count)
     if (t < R * count) scal[(int64_t)(t / count) * SCAL_COUNT + slot0 + t % count] = 0.0;
 }
 
-// One block per replica: sum of its P mode energies, fixed order.
-__global__ void k_sum_modes(const double *__restrict__ emode, int64_t P, double *__restrict__ scal,
-                            int slot)
+// One block (256 threads) per replica: the sum of its P mode energies e_l into
+// scal[SCAL_ERBE] and the RBE virial estimate into scal[SCAL_VRBE + 0..5]:
+//   W_ab = sum_l e_l [delta_ab - 2 k_a k_b (1/k^2 + 1/(4 alpha))],
+// the strain derivative of the Fourier energy of Eq. 8 (V -> V (1 + tr e),
+// k -> (1 - e^T) k, rho unchanged) applied to the sampled modes with weight S/P:
+// an unbiased estimate of the Ewald virial.  FP64, fixed order.
+__global__ void k_sum_modes(const double *__restrict__ emode, const int4 *__restrict__ modes,
+                            const Rep *__restrict__ reps, int64_t P, double alpha,
+                            double *__restrict__ scal)
 {
-    __shared__ double s[256];
-    double v = 0.0;
-    for (int64_t l = threadIdx.x; l < P; l += blockDim.x) v += emode[(int64_t)blockIdx.x * P + l];
-    s[threadIdx.x] = v;
+    __shared__ double s[7][256];
+    const double tk = 2.0 * kPi / reps[blockIdx.x].L;
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t l = threadIdx.x; l < P; l += blockDim.x) {
+        const int64_t g = (int64_t)blockIdx.x * P + l;
+        const double e = emode[g];
+        const int4 m = modes[g];
+        const double kx = tk * m.x, ky = tk * m.y, kz = tk * m.z;
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        v[0] += e;
+        if (k2 > 0.0) {
+            const double b = 2.0 * (1.0 / k2 + 1.0 / (4.0 * alpha));
+            v[1] += e * (1.0 - b * kx * kx);
+            v[2] += e * (1.0 - b * ky * ky);
+            v[3] += e * (1.0 - b * kz * kz);
+            v[4] -= e * b * kx * ky;
+            v[5] -= e * b * kx * kz;
+            v[6] -= e * b * ky * kz;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 7; ++c) s[c][threadIdx.x] = v[c];
     __syncthreads();
     for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
-        if (threadIdx.x < (unsigned)o) s[threadIdx.x] += s[threadIdx.x + o];
+        if (threadIdx.x < (unsigned)o) {
+#pragma unroll
+            for (int c = 0; c < 7; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + o];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) scal[(int64_t)blockIdx.x * SCAL_COUNT + slot] = s[0];
+    if (threadIdx.x < 7) {
+        double *sc = scal + (int64_t)blockIdx.x * SCAL_COUNT;
+        if (threadIdx.x == 0) sc[SCAL_ERBE] = s[0][0];
+        else sc[SCAL_VRBE + threadIdx.x - 1] = s[threadIdx.x][0];
+    }
 }
 
 __global__ void k_max_count(const int32_t *__restrict__ count, int64_t n, int32_t *__restrict__ out)
@@ -681,7 +712,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(dev_alloc(&c->scratch_force, 3 * N * (rs > 4 ? rs : 8) + 64));
     TRY(alloc_n(&c->scal, (size_t)R * SCAL_COUNT));
     TRY(alloc_n(&c->red_tmp, (size_t)RED_BLOCKS * 8));
-    TRY(alloc_n(&c->red_rep, (size_t)R * RED_SPLIT * 8));
+    TRY(alloc_n(&c->red_rep, (size_t)R * RED_SPLIT * RED_STRIDE));
     TRY(alloc_n(&c->err, 1));
     TRY(alloc_n(&c->d_step, 1));
     TRY(alloc_n(&c->cdf, T.size()));
@@ -714,7 +745,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(dev_alloc(&c->adj_lj, 2 * (size_t)c->T * rs));
     TRY(alloc_n(&c->adj_tpart, (size_t)c->nb128 * 2 * c->T));
     TRY(alloc_n(&c->adj_tsum, 2 * (size_t)c->T));
-    TRY(alloc_n(&c->epart, 2 * (size_t)c->pair_parts));
+    TRY(alloc_n(&c->epart, EPART * (size_t)c->pair_parts));
     TRY(alloc_n(&c->kepart, (size_t)c->nb256 * 3));
     TRY(alloc_n(&c->ibuf, 4));
     g_alloc_countdown = -1;
@@ -1023,11 +1054,14 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
     rbmd_status s = RBMD_OK;
     cudaMemsetAsync(c->ibuf, 0, 4 * sizeof(int32_t), c->stream);
     k_zero_slots<<<(R * 6 + 255) / 256, 256, 0, c->stream>>>(c->scal, R, SCAL_FSUM, 6);
+    k_zero_slots<<<(R * (SCAL_COUNT - SCAL_EPAIR) + 255) / 256, 256, 0, c->stream>>>(
+        c->scal, R, SCAL_EPAIR, SCAL_COUNT - SCAL_EPAIR);
     if (!(c->prm.flags & RBMD_NO_RBE)) {
         s = rbe_sample(c, r);
         if (s == RBMD_OK) s = rbe_structure_factors(c);
         if (s == RBMD_OK) {
-            k_sum_modes<<<R, 256, 0, c->stream>>>(c->emode, c->Pm, c->scal, SCAL_ERBE);
+            k_sum_modes<<<R, 256, 0, c->stream>>>(c->emode, c->modes, c->reps, c->Pm,
+                                                   c->prm.alpha, c->scal);
             s = cuda_status(cudaPeekAtLastError());
         }
     }
@@ -1036,7 +1070,7 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
         if (s == RBMD_OK)
             s = rbl_pairs(c, r, c->scratch_force, 0, true, nullptr, nullptr, nullptr);
         if (s == RBMD_OK) s = md_sum_replicas(c, c->fpart, 3, SCAL_FSUM, 1.0, false, true);
-        if (s == RBMD_OK) s = md_sum_replicas(c, c->epart, 2, SCAL_ECOUL, 1.0, false, true);
+        if (s == RBMD_OK) s = md_sum_replicas(c, c->epart, EPART, SCAL_EPAIR, 1.0, false, true);
         if (s == RBMD_OK) {
             k_max_count<<<(unsigned)((c->ncell + 255) / 256), 256, 0, c->stream>>>(
                 c->cell_count, c->ncell, c->ibuf + 1);
@@ -1056,8 +1090,8 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
         const double *hr = h.data() + (size_t)q * SCAL_COUNT;
         const Rep &rp = c->reps_h[q];
         rbmd_energy_terms &o = out[q];
-        o.e_coul_real = hr[SCAL_ECOUL];
-        o.e_lj = hr[SCAL_ELJ];
+        o.e_coul_real = hr[SCAL_EPAIR + 0];
+        o.e_lj = hr[SCAL_EPAIR + 1];
         o.e_rbe = hr[SCAL_ERBE];
         o.e_self = rp.e_self;
         o.e_potential = o.e_coul_real + o.e_lj + o.e_rbe + o.e_self;
@@ -1068,6 +1102,12 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
         o.step = step;
         o.max_shell = hi[0];
         o.max_cell = hi[1];
+        o.virial_coul_real = hr[SCAL_EPAIR + 2];
+        o.virial_lj = hr[SCAL_EPAIR + 3];
+        o.virial_rbe = hr[SCAL_VRBE + 0] + hr[SCAL_VRBE + 1] + hr[SCAL_VRBE + 2];
+        for (int k = 0; k < 6; ++k) o.virial[k] = hr[SCAL_EPAIR + 4 + k] + hr[SCAL_VRBE + k];
+        const double V = rp.L * rp.L * rp.L;
+        o.pressure = (2.0 * o.e_kinetic + o.virial[0] + o.virial[1] + o.virial[2]) / (3.0 * V);
     }
     return RBMD_OK;
 }

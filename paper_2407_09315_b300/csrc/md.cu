@@ -110,7 +110,7 @@ __global__ void k_sum_replicas1(const double *__restrict__ parts, int64_t seg2,
         __syncthreads();
     }
     if (threadIdx.x < NC)
-        tmp[((int64_t)blockIdx.y * RED_SPLIT + blockIdx.x) * 8 + threadIdx.x] = s[threadIdx.x][0];
+        tmp[((int64_t)blockIdx.y * RED_SPLIT + blockIdx.x) * RED_STRIDE + threadIdx.x] = s[threadIdx.x][0];
 }
 
 __global__ void k_sum_replicas2(const double *__restrict__ tmp, int ncomp,
@@ -121,7 +121,7 @@ __global__ void k_sum_replicas2(const double *__restrict__ tmp, int ncomp,
     if (c >= ncomp) return;
     const double sc = per_atom ? scale / (double)reps[blockIdx.x].N : scale;
     double v = 0.0;
-    for (int k = 0; k < RED_SPLIT; ++k) v += tmp[((int64_t)blockIdx.x * RED_SPLIT + k) * 8 + c];
+    for (int k = 0; k < RED_SPLIT; ++k) v += tmp[((int64_t)blockIdx.x * RED_SPLIT + k) * RED_STRIDE + c];
     scal[(int64_t)blockIdx.x * SCAL_COUNT + slot + c] = sc * v;
 }
 
@@ -132,6 +132,8 @@ rbmd_status md_sum_replicas(rbmd_ctx *c, const double *parts, int ncomp, int slo
     const dim3 grid(RED_SPLIT, c->R);
     if (ncomp == 3) k_sum_replicas1<3><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
     else if (ncomp == 2) k_sum_replicas1<2><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
+    else if (ncomp == EPART)
+        k_sum_replicas1<EPART><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
     else return RBMD_ERR_INVALID;
     RBMD_LAUNCH_CHECK();
     k_sum_replicas2<<<c->R, 32, 0, c->stream>>>(c->red_rep, ncomp, c->reps, c->scal, slot, scale,

@@ -250,7 +250,7 @@ template <typename real> struct PairArgs {
     real *F;
     int accumulate;
     double *fpart;     // [parts][3]: pair kernel per warp, then the fallback per warp
-    double *epart;     // [parts][2]
+    double *epart;     // [parts][EPART]
     int64_t fb_part0;  // first partial slot of the fallback kernel
     int32_t *imax;     // [0] max N_s
     int32_t *n_core, *n_shell, *batch;  // verification outputs (caller order) or NULL
@@ -275,9 +275,43 @@ __device__ __forceinline__ double erfc_r(double x) { return erfc(x); }
 __device__ __forceinline__ float exp_r(float x) { return expf(x); }
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 
+// Energy and virial accumulators of one atom's pairs (ENERGY kernels only): the
+// pair energies in FP64, and in the working precision the traces r.(-dU/dr) of
+// the erfc-Coulomb and LJ virials and the tensor g d (x) d of both (d = r_j - r_i,
+// the pair force on i is -g d, so r_ij (x) F_ij = g d (x) d; xx yy zz xy xz yz).
+// The virial is W = -dE/d(strain) of the list energy with its weights held fixed.
+template <typename real> struct EAcc {
+    double ec, el;
+    real wc, wl;
+    real w[6];
+};
+
+template <typename real>
+__device__ __forceinline__ void eacc_zero(EAcc<real> &e)
+{
+    e.ec = 0.0;
+    e.el = 0.0;
+    e.wc = 0;
+    e.wl = 0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e.w[c] = 0;
+}
+
+// e += s b (the batch part with its weight N_s/p)
+template <typename real>
+__device__ __forceinline__ void eacc_add(EAcc<real> &e, const EAcc<real> &b, real s)
+{
+    e.ec += (double)s * b.ec;
+    e.el += (double)s * b.el;
+    e.wc += s * b.wc;
+    e.wl += s * b.wl;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e.w[c] += s * b.w[c];
+}
+
 // Force on i from j (d = r_j - r_i, minimum image) for erfc-Coulomb (Eq. 10) +
 // Lennard-Jones (Eq. 2) with Lorentz-Berthelot parameters (Eq. 4); adds F_ij to
-// f and, with ENERGY, u_ij to (ec, el).
+// f and, with ENERGY, u_ij and the pair virial to e.
 template <typename real> struct Real4;
 template <> struct Real4<float> { using type = float4; };
 template <> struct Real4<double> { using type = double4_32a; };
@@ -285,7 +319,7 @@ template <> struct Real4<double> { using type = double4_32a; };
 template <typename real, bool ENERGY, bool TAB>
 __device__ __forceinline__ void pair_eval(const PairArgs<real> &a, real dx, real dy, real dz,
                                           real qq, real eps, real sig, real &fx, real &fy,
-                                          real &fz, double &ec, double &el)
+                                          real &fz, EAcc<real> &e)
 {
     const real r2 = dx * dx + dy * dy + dz * dz;
     const real rinv = rsqrt_r(r2);
@@ -293,7 +327,7 @@ __device__ __forceinline__ void pair_eval(const PairArgs<real> &a, real dx, real
     const real s6 = s2 * s2 * s2;
     const real s12 = s6 * s6;
     const real glj = (real)24 * eps * ((real)2 * s12 - s6);  // r * (-dU_lj/dr)
-    real g, eu = 0;
+    real g, eu = 0, gcr = 0;  // gcr: r * (-dU_coul/dr)
     if constexpr (TAB) {
         // cubic piece of the tabulated factors at s = r^2; below the knot i0 the
         // pieces hold the remainders and the bare Coulomb terms are added exactly
@@ -309,6 +343,7 @@ __device__ __forceinline__ void pair_eval(const PairArgs<real> &a, real dx, real
             const typename Real4<real>::type ce = T[2 * k + 1];
             eu = ((ce.w * t + ce.z) * t + ce.y) * t + ce.x;
             if (k < a.tab_i0) eu += rinv;
+            gcr = qq * fc * r2;
         }
     } else {
         const real r = r2 * rinv;
@@ -317,13 +352,22 @@ __device__ __forceinline__ void pair_eval(const PairArgs<real> &a, real dx, real
         const real gc = qq * (er * rinv + a.c2 * ex);  // r * (-dU_coul/dr)
         g = (gc + glj) * rinv * rinv;
         eu = er * rinv;
+        gcr = gc;
     }
     fx -= g * dx;
     fy -= g * dy;
     fz -= g * dz;
     if constexpr (ENERGY) {
-        ec += (double)(qq * eu);
-        el += (double)((real)4 * eps * (s12 - s6));
+        e.ec += (double)(qq * eu);
+        e.el += (double)((real)4 * eps * (s12 - s6));
+        e.wc += gcr;
+        e.wl += glj;
+        e.w[0] += g * dx * dx;
+        e.w[1] += g * dy * dy;
+        e.w[2] += g * dz * dz;
+        e.w[3] += g * dx * dy;
+        e.w[4] += g * dx * dz;
+        e.w[5] += g * dy * dz;
     }
 }
 
@@ -336,14 +380,14 @@ template <typename real> struct AtomI {
 template <typename real, bool ENERGY, bool TAB = false>
 __device__ __forceinline__ void eval_k(const PairArgs<real> &a, const real *s_lj,
                                        const AtomI<real> &I, int k, real &fx, real &fy, real &fz,
-                                       double &ec, double &el)
+                                       EAcc<real> &e)
 {
     const uint4 B = a.spos[k];
     const int tj = a.stype[k];
     pair_eval<real, ENERGY, TAB>(a, (real)(int32_t)(B.x - I.A.x) * I.lscale,
                             (real)(int32_t)(B.y - I.A.y) * I.lscale,
                             (real)(int32_t)(B.z - I.A.z) * I.lscale, I.qi * a.sq[k],
-                            I.se * s_lj[tj], I.hs + s_lj[a.T + tj], fx, fy, fz, ec, el);
+                            I.se * s_lj[tj], I.hs + s_lj[a.T + tj], fx, fy, fz, e);
 }
 
 // Pair forces of the sorted atoms idx[0..n) in order, the next neighbour's
@@ -352,19 +396,19 @@ __device__ __forceinline__ void eval_k(const PairArgs<real> &a, const real *s_lj
 template <typename real, bool ENERGY, bool TAB>
 __device__ __forceinline__ void eval_list(const PairArgs<real> &a, const real *s_lj,
                                           const AtomI<real> &I, const int32_t *idx, int n,
-                                          real &fx, real &fy, real &fz, double &ec, double &el)
+                                          real &fx, real &fy, real &fz, EAcc<real> &e)
 {
     if (n <= 0) return;
     int k = idx[0];
     uint4 B = a.spos[k];
     int tj = a.stype[k];
     real qj = a.sq[k];
-    for (int e = 0; e < n; ++e) {
+    for (int t = 0; t < n; ++t) {
         uint4 Bn = B;
         int tn = tj;
         real qn = qj;
-        if (e + 1 < n) {
-            const int kn = idx[e + 1];
+        if (t + 1 < n) {
+            const int kn = idx[t + 1];
             Bn = a.spos[kn];
             tn = a.stype[kn];
             qn = a.sq[kn];
@@ -372,7 +416,7 @@ __device__ __forceinline__ void eval_list(const PairArgs<real> &a, const real *s
         pair_eval<real, ENERGY, TAB>(a, (real)(int32_t)(B.x - I.A.x) * I.lscale,
                                      (real)(int32_t)(B.y - I.A.y) * I.lscale,
                                      (real)(int32_t)(B.z - I.A.z) * I.lscale, I.qi * qj,
-                                     I.se * s_lj[tj], I.hs + s_lj[a.T + tj], fx, fy, fz, ec, el);
+                                     I.se * s_lj[tj], I.hs + s_lj[a.T + tj], fx, fy, fz, e);
         B = Bn;
         tj = tn;
         qj = qn;
@@ -385,7 +429,7 @@ __device__ __forceinline__ void eval_list(const PairArgs<real> &a, const real *s
 template <typename real, bool ENERGY, bool TAB>
 __device__ __forceinline__ void eval_list4(const PairArgs<real> &a, const real *s_lj,
                                            const AtomI<real> &I, const int32_t *idx, int n,
-                                           real &fx, real &fy, real &fz, double &ec, double &el)
+                                           real &fx, real &fy, real &fz, EAcc<real> &e)
 {
     for (int e0 = 0; e0 < n; e0 += 4) {
         const int4 kk = reinterpret_cast<const int4 *>(idx)[e0 >> 2];
@@ -407,7 +451,7 @@ __device__ __forceinline__ void eval_list4(const PairArgs<real> &a, const real *
                                              (real)(int32_t)(B[q].y - I.A.y) * I.lscale,
                                              (real)(int32_t)(B[q].z - I.A.z) * I.lscale,
                                              I.qi * qj[q], I.se * s_lj[tj[q]],
-                                             I.hs + s_lj[a.T + tj[q]], fx, fy, fz, ec, el);
+                                             I.hs + s_lj[a.T + tj[q]], fx, fy, fz, e);
     }
 }
 
@@ -415,10 +459,10 @@ __device__ __forceinline__ void eval_list4(const PairArgs<real> &a, const real *
 template <typename real, bool ENERGY>
 __device__ __forceinline__ void eval_any(const PairArgs<real> &a, const real *s_lj,
                                          const AtomI<real> &I, int k, real &fx, real &fy, real &fz,
-                                         double &ec, double &el)
+                                         EAcc<real> &e)
 {
-    if (a.tab) eval_k<real, ENERGY, true>(a, s_lj, I, k, fx, fy, fz, ec, el);
-    else eval_k<real, ENERGY, false>(a, s_lj, I, k, fx, fy, fz, ec, el);
+    if (a.tab) eval_k<real, ENERGY, true>(a, s_lj, I, k, fx, fy, fz, e);
+    else eval_k<real, ENERGY, false>(a, s_lj, I, k, fx, fy, fz, e);
 }
 
 // Philox4x32-10 of the batch priority for the counter (id_i, id_j, step, tag).
@@ -976,6 +1020,31 @@ __global__ void __launch_bounds__(256) k_rbl_take_shell(PairArgs<real> a)
     }
 }
 
+// Warp sums of the force (and, with ENERGY, of the halved energies and virials)
+// into the FP64 partial slot `part` (every lane of the warp calls it).
+template <typename real, bool ENERGY>
+__device__ __forceinline__ void warp_partials(const PairArgs<real> &a, int64_t part, real fx,
+                                              real fy, real fz, const EAcc<real> &e)
+{
+    constexpr int NV = ENERGY ? 3 + EPART : 3;  // FP64 shuffles are costly: only what is used
+    double v[3 + EPART] = {(double)fx, (double)fy, (double)fz, 0.5 * e.ec, 0.5 * e.el,
+                           0.5 * (double)e.wc, 0.5 * (double)e.wl};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v[7 + c] = 0.5 * (double)e.w[c];
+#pragma unroll
+    for (int c = 0; c < NV; ++c)
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    if ((threadIdx.x & 31) == 0) {
+        a.fpart[3 * part + 0] = v[0];
+        a.fpart[3 * part + 1] = v[1];
+        a.fpart[3 * part + 2] = v[2];
+        if constexpr (ENERGY) {
+#pragma unroll
+            for (int c = 0; c < EPART; ++c) a.epart[EPART * part + c] = v[3 + c];
+        }
+    }
+}
+
 // Step 2 (+ the partial sums of step 3).
 template <typename real, bool ENERGY, bool TAB>
 __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
@@ -986,7 +1055,8 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
     const AtomSlot sl = atom_slot(a.map, a.reps);
     const int64_t is = sl.i;
     real fx = 0, fy = 0, fz = 0;
-    double ec = 0.0, el = 0.0;
+    EAcc<real> e;
+    eacc_zero(e);
     if (sl.ok) {
         const int2 cnt = a.ncount[is];
         if (!overflowed(a, cnt)) {
@@ -1000,30 +1070,28 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
             const int64_t N = a.N;
             if ((a.CC & 3) == 0)
                 eval_list4<real, ENERGY, TAB>(a, s_lj, I, a.lcore + lidx(is, 0, N, a.CC), cnt.x, fx,
-                                              fy, fz, ec, el);
+                                              fy, fz, e);
             else
                 eval_list<real, ENERGY, TAB>(a, s_lj, I, a.lcore + lidx(is, 0, N, a.CC), cnt.x, fx, fy,
-                                             fz, ec, el);
+                                             fz, e);
             if (a.exact) {
                 const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
-                for (int e = 0; e < cnt.y; ++e)
+                for (int k = 0; k < cnt.y; ++k)
                     eval_k<real, ENERGY, TAB>(a, s_lj, I,
-                                              a.sidx[id0 + (uint32_t)a.lshell[lidx(is, e, N, a.CS)]],
-                                         fx, fy, fz, ec, el);
+                                              a.sidx[id0 + (uint32_t)a.lshell[lidx(is, k, N, a.CS)]],
+                                              fx, fy, fz, e);
             } else {
                 const int nb = min(cnt.y, a.p);
                 const real w = cnt.y > a.p ? (real)cnt.y / (real)a.p : (real)1;
                 real bx = 0, by = 0, bz = 0;
-                double bec = 0.0, bel = 0.0;
+                EAcc<real> be;
+                eacc_zero(be);
                 eval_list<real, ENERGY, TAB>(a, s_lj, I, a.bk + lidx(is, 0, N, a.p), nb, bx, by, bz,
-                                             bec, bel);
+                                             be);
                 fx += w * bx;
                 fy += w * by;
                 fz += w * bz;
-                if constexpr (ENERGY) {
-                    ec += (double)w * bec;
-                    el += (double)w * bel;
-                }
+                if constexpr (ENERGY) eacc_add(e, be, w);
             }
             real *f = a.F + 3 * (int64_t)I.A.w;
             if (a.accumulate) {
@@ -1037,21 +1105,8 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
             }
         }
     }
-    constexpr int NV = ENERGY ? 5 : 3;  // FP64 shuffles are costly: only what is used
-    double v[5] = {(double)fx, (double)fy, (double)fz, 0.5 * ec, 0.5 * el};
-#pragma unroll
-    for (int c = 0; c < NV; ++c)
-        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-    if ((threadIdx.x & 31) == 0) {
-        const int64_t part = (int64_t)blockIdx.x * (kPairBlock / 32) + (threadIdx.x >> 5);
-        a.fpart[3 * part + 0] = v[0];
-        a.fpart[3 * part + 1] = v[1];
-        a.fpart[3 * part + 2] = v[2];
-        if constexpr (ENERGY) {
-            a.epart[2 * part + 0] = v[3];
-            a.epart[2 * part + 1] = v[4];
-        }
-    }
+    const int64_t part = (int64_t)blockIdx.x * (kPairBlock / 32) + (threadIdx.x >> 5);
+    warp_partials<real, ENERGY>(a, part, fx, fy, fz, e);
 }
 
 // Exact fallback for atoms whose lists overflowed (Algorithm 2 for one atom,
@@ -1078,8 +1133,7 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
             a.fpart[3 * part + 1] = 0.0;
             a.fpart[3 * part + 2] = 0.0;
             if constexpr (ENERGY) {
-                a.epart[2 * part + 0] = 0.0;
-                a.epart[2 * part + 1] = 0.0;
+                for (int c = 0; c < EPART; ++c) a.epart[EPART * part + c] = 0.0;
             }
         }
         return;
@@ -1088,7 +1142,8 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
     __syncthreads();
     for (int mb = blockIdx.x; mb < a.nmap; mb += gridDim.x) {
         real fx = 0, fy = 0, fz = 0;
-        double ec = 0.0, el = 0.0;
+        EAcc<real> e;
+        eacc_zero(e);
         const AtomSlot sl = atom_slot_at(a.map, a.reps, mb);
         {
             const int64_t is = sl.i;
@@ -1110,20 +1165,21 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                 int hk[CAP];
                 sel_init<CAP>(hh, hk, a.p);
                 real ax = 0, ay = 0, az = 0;
-                double aec = 0.0, ael = 0.0;
+                EAcc<real> ae;
+                eacc_zero(ae);
                 int lc = 0, lsn = 0, ncore = 0, ns = 0;
                 auto flush = [&]() {
-                    for (int e = 0; e < lsn; ++e) {
-                        const int k = s_k[FB_LIST - 1 - e][tid];
+                    for (int t = 0; t < lsn; ++t) {
+                        const int k = s_k[FB_LIST - 1 - t][tid];
                         if (a.exact) {
-                            eval_any<real, ENERGY>(a, s_lj, I, k, ax, ay, az, aec, ael);
+                            eval_any<real, ENERGY>(a, s_lj, I, k, ax, ay, az, ae);
                         } else {
-                            const uint32_t id = s_id[FB_LIST - 1 - e][tid] - id0;
+                            const uint32_t id = s_id[FB_LIST - 1 - t][tid] - id0;
                             const uint2 w = philox_rest(sel.r0, id, rp.key);
                             sel_insert<CAP>(hh, hk, w.x, (int)id, id, sel);
                         }
                     }
-                    for (int e = 0; e < lc; ++e) eval_any<real, ENERGY>(a, s_lj, I, s_k[e][tid], ax, ay, az, aec, ael);
+                    for (int t = 0; t < lc; ++t) eval_any<real, ENERGY>(a, s_lj, I, s_k[t][tid], ax, ay, az, ae);
                     lc = 0;
                     lsn = 0;
                 };
@@ -1149,19 +1205,17 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                 if (!a.exact) {
                     const real w = ns > a.p ? (real)ns / (real)a.p : (real)1;
                     real bx = 0, by = 0, bz = 0;
-                    double bec = 0.0, bel = 0.0;
+                    EAcc<real> be;
+                    eacc_zero(be);
 #pragma unroll
-                    for (int e = 0; e < CAP; ++e)
-                        if (hk[e] >= 0)
-                            eval_any<real, ENERGY>(a, s_lj, I, a.sidx[id0 + (uint32_t)hk[e]], bx, by,
-                                                 bz, bec, bel);
+                    for (int t = 0; t < CAP; ++t)
+                        if (hk[t] >= 0)
+                            eval_any<real, ENERGY>(a, s_lj, I, a.sidx[id0 + (uint32_t)hk[t]], bx, by,
+                                                   bz, be);
                     ax += w * bx;
                     ay += w * by;
                     az += w * bz;
-                    if constexpr (ENERGY) {
-                        aec += (double)w * bec;
-                        ael += (double)w * bel;
-                    }
+                    if constexpr (ENERGY) eacc_add(ae, be, w);
                     if constexpr (LISTS) {
                         int32_t *out = a.batch + (int64_t)id_i * a.p;
                         for (int e = 0; e < a.p; ++e) out[e] = -1;
@@ -1193,25 +1247,10 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                 fx += ax;
                 fy += ay;
                 fz += az;
-                ec += aec;
-                el += ael;
+                if constexpr (ENERGY) eacc_add(e, ae, (real)1);
             }
         }
-        constexpr int NV = ENERGY ? 5 : 3;
-        double v[5] = {(double)fx, (double)fy, (double)fz, 0.5 * ec, 0.5 * el};
-#pragma unroll
-        for (int c = 0; c < NV; ++c)
-            for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-        if ((tid & 31) == 0) {
-            const int64_t part = a.fb_part0 + (int64_t)mb * WPB + (tid >> 5);
-            a.fpart[3 * part + 0] = v[0];
-            a.fpart[3 * part + 1] = v[1];
-            a.fpart[3 * part + 2] = v[2];
-            if constexpr (ENERGY) {
-                a.epart[2 * part + 0] = v[3];
-                a.epart[2 * part + 1] = v[4];
-            }
-        }
+        warp_partials<real, ENERGY>(a, a.fb_part0 + (int64_t)mb * WPB + (tid >> 5), fx, fy, fz, e);
     }
 }
 
@@ -1231,8 +1270,7 @@ __global__ void k_rbl_no_fallback(const int32_t *__restrict__ ovf, int *__restri
         fpart[3 * part + 1] = 0.0;
         fpart[3 * part + 2] = 0.0;
         if constexpr (ENERGY) {
-            epart[2 * part + 0] = 0.0;
-            epart[2 * part + 1] = 0.0;
+            for (int c = 0; c < EPART; ++c) epart[EPART * part + c] = 0.0;
         }
     }
 }

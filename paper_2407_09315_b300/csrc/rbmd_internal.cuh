@@ -38,6 +38,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kPairBlock = 128;  // threads per block of the RBL pair kernel
 constexpr int RED_BLOCKS = 256;  // first-stage blocks of the long FP64 reductions
 constexpr int RED_SPLIT = 32;    // first-stage chunks per replica of the per-replica sums
+constexpr int RED_STRIDE = 16;   // components per first-stage chunk slot (at most 16)
 
 // Step number used by a kernel: (*ptr) + add when ptr is set (graph replays read
 // the device counter), else add.
@@ -201,7 +202,7 @@ struct rbmd_ctx {
     void *scratch_force;  // force buffer for energy evaluations
     double *scal;         // [R][SCAL_COUNT] FP64 scalars, see SCAL_* below
     double *red_tmp;      // [RED_BLOCKS][8] first stage of long reductions
-    double *red_rep;      // [R][RED_SPLIT][8] first stage of the per-replica sums
+    double *red_rep;      // [R][RED_SPLIT][RED_STRIDE] first stage of the per-replica sums
     int *err;
     int64_t *d_step;
 
@@ -237,7 +238,7 @@ struct rbmd_ctx {
     void *sq;             // real [N]
     int32_t *stype;       // [N]
     double *fpart;        // [pair_parts][3] force partial sums (per warp)
-    double *epart;        // [pair_parts][2] energy partial sums
+    double *epart;        // [pair_parts][EPART] energy and virial partial sums
     double *kepart;       // [nb256]
     int32_t *ibuf;        // [4] integer diagnostics
     float *lj_f;          // [2*T] sqrt(eps), sigma/2 (FP32 path)
@@ -278,16 +279,22 @@ enum {
     SCAL_KE = 4,      // kinetic energy after the last kick (before lambda)
     SCAL_FSUM = 5,    // [3] sum of short-range forces before the correction
     SCAL_ERBE = 8,    // RBE energy estimate
-    SCAL_ECOUL = 9,
-    SCAL_ELJ = 10,
     SCAL_KE_TRUE = 11,
     SCAL_FCORR_AUX = 12,  // [3] correction of stand-alone force calls
     SCAL_ESELF = 15,      // self energy (kept on the device for batched read-out)
     SCAL_LAMBDA_KICK = 16,  // factor applied to the stored velocities by the next kick
     SCAL_XI = 17,         // Nose-Hoover variable at the step boundary
     SCAL_XI_RUN = 18,     // Nose-Hoover variable during the step (after its first half update)
-    SCAL_COUNT = 20
+    SCAL_EPAIR = 20,      // [EPART] pair-list sums: E_coul, E_lj, tr W_coul, tr W_lj, W[6]
+    SCAL_VRBE = 30,       // [6] RBE virial estimate xx yy zz xy xz yz
+    SCAL_COUNT = 36
 };
+
+// Components of the pair kernels' energy partial sums (per warp, FP64): the
+// erfc-Coulomb and LJ energies of the lists, the traces of their virials and the
+// virial tensor of both (xx yy zz xy xz yz), each already halved (every ordered
+// pair of the lists is visited once from each side).
+constexpr int EPART = 10;
 
 namespace rbmd {
 
