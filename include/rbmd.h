@@ -111,6 +111,10 @@ typedef struct {
     int32_t cell_div;    /* cells per r_cut along each axis: 1 or 2; 0 = 2 (rbmd_set_tiles
                             and rbmd_autotune change it later) */
     int32_t mh_moves;    /* RBMD_METROPOLIS_MODES: moves per chain per step (0 = 8) */
+    double skin;         /* rbmd_step's neighbour candidates: every atom within r_cut + skin
+                            at the last rebuild (sigma units); 0 selects 0.4, < 0 turns the
+                            candidate lists off (every step walks the cells).  The lists,
+                            batches and forces do not depend on it (see rbmd_step). */
 } rbmd_params;
 
 /* Energies and diagnostics (host, FP64).  Potential terms follow Eq. 8 with the
@@ -309,8 +313,25 @@ rbmd_status rbmd_forces_host(rbmd_ctx *ctx, const void *pos, void *force, int64_
  *     xi += dt/2 (2 KE - g T0)/Q.
  * The context's step counter advances by n_steps.  Queued as one CUDA graph per
  * step after the first call.
+ * Short-range lists of the step (Algorithm 2 step 1): unless params.skin < 0 (or
+ * with RBMD_RBL_EXACT, p > 16 or r_cut + skin >= L/2), the step keeps for every
+ * atom its candidates, the atoms within r_cut + skin at the last rebuild, and
+ * classifies them exactly each step on the integer positions.  A rebuild (cell
+ * sort and candidates) runs inside the step, on the device, when some atom has
+ * moved more than skin/2 since the last one (an exact integer test) or when
+ * another call changed the sorted layout.  The core list, N_s and the batch are
+ * the sets of the cell walk that rbmd_rbl_forces does; the core list and a whole
+ * shell are summed in atom-id order and a drawn batch in priority order, so the
+ * forces do not depend on when rebuilds happen (a resumed run stays
+ * bit-identical), but they may differ from rbmd_rbl_forces in the last bits.  An
+ * atom beyond the lists' capacities (a density fluctuation of over 4 standard
+ * deviations) is computed by the exact cell walk instead.
  */
 rbmd_status rbmd_step(rbmd_ctx *ctx, int64_t n_steps);
+
+/* Rebuilds of the step's candidate lists so far (0 when they are off, see
+ * rbmd_step); -1 for NULL.  Synchronises. */
+int64_t rbmd_candidate_rebuilds(rbmd_ctx *ctx);
 
 /*
  * Nose-Hoover variable xi of every replica at the step boundary (host double [R]),

@@ -40,7 +40,7 @@ class Params(C.Structure):
         ("coulomb_k", C.c_double), ("dt", C.c_double), ("temperature", C.c_double),
         ("tau_T", C.c_double), ("seed", C.c_uint64), ("replica", C.c_uint32),
         ("precision", C.c_int32), ("flags", C.c_uint32), ("cell_div", C.c_int32),
-        ("mh_moves", C.c_int32),
+        ("mh_moves", C.c_int32), ("skin", C.c_double),
     ]
 
 
@@ -74,6 +74,7 @@ def lib():
         "rbmd_init": ([C.POINTER(Params), P, P, P, P, P, P, P, C.POINTER(P)], C.c_int),
         "rbmd_init_batch": ([C.POINTER(Params), i32, P, P, P, P, P, P, P, C.POINTER(P)], C.c_int),
         "rbmd_replica_count": ([P], i32),
+        "rbmd_candidate_rebuilds": ([P], i64),
         "rbmd_set_tiles": ([P, i32, i32, i32], C.c_int),
         "rbmd_get_tiles": ([P, P], C.c_int),
         "rbmd_autotune": ([P, i64, P], C.c_int),
@@ -209,7 +210,8 @@ class RBMD:
     def __init__(self, pos, charge, eps, sigma, *, box_length, alpha=0.62, r_core=2.0,
                  r_cut=3.5, rbl_p=10, rbe_P=100, coulomb_k=1.0, dt=0.001, temperature=1.0,
                  tau_T=0.1, thermostat=0, seed=0, replica=0, precision=FP32, flags=0,
-                 cell_div=0, vel=None, types=None, stream=None, n_atoms=None, mh_moves=0):
+                 cell_div=0, vel=None, types=None, stream=None, n_atoms=None, mh_moves=0,
+                 skin=0.0):
         import torch
 
         self._torch = torch
@@ -244,7 +246,7 @@ class RBMD:
                             rbl_p=rbl_p, thermostat=thermostat, coulomb_k=coulomb_k, dt=dt,
                             temperature=temps[r], tau_T=tau_T, seed=seeds[r],
                             replica=reps[r], precision=precision, flags=flags,
-                            cell_div=cell_div, mh_moves=mh_moves)
+                            cell_div=cell_div, mh_moves=mh_moves, skin=skin)
         self.params = prm[0]
         self._params = prm
         pos = pos.to(self.dtype).contiguous()
@@ -387,6 +389,10 @@ class RBMD:
 
     def sync(self):
         _check(lib().rbmd_sync(self._h), "sync")
+
+    def candidate_rebuilds(self) -> int:
+        """Rebuilds of the step's neighbour candidate lists so far (0: lists off)."""
+        return int(lib().rbmd_candidate_rebuilds(self._h))
 
     # -- inspection -------------------------------------------------------
     def mode_count(self) -> int:

@@ -76,6 +76,13 @@ rbmd_status leave(rbmd_ctx *c, rbmd_status s)
 }
 
 __global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
+
+// Sorted slots hold valid atom ids from the start (every later sort rewrites them).
+__global__ void k_iota_spos(uint4 *spos, int64_t N)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) spos[i] = make_uint4(0u, 0u, 0u, (uint32_t)i);
+}
 __global__ void k_init_scal(double *scal, int R)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -240,7 +247,8 @@ void free_ctx(rbmd_ctx *c)
                     c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp,
                     c->adj_lj,    c->adj_tpart, c->adj_tsum, c->reps,       c->map256,
                     c->map128,    c->tiles,     c->red_rep,   c->ptab,       c->heavy,
-                    c->modes0,    c->acc,       c->chain_step, c->phtab};
+                    c->modes0,    c->acc,       c->chain_step, c->phtab,      c->vl_cand,
+                    c->vl_ncand,  c->vl_sref};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -317,24 +325,28 @@ __global__ void k_sum_charges(const double *__restrict__ parts, const Rep *__res
         for (int k = 0; k < 3; ++k) out[3 * (int64_t)blockIdx.x + k] = s[k][0];
 }
 
-// Cells of every replica for `div` cells per r_cut (Sec. 2.3 binning): the side
-// is at least r_cut / div, and the count is capped so that sparse boxes do not
-// get more cells than atoms (bigger cells stay correct: the stencil still covers
-// r_cut).  Returns the total; with apply, stores nc, the culling radius and the
-// cell ranges in the host replica table.
-int64_t cell_layout(rbmd_ctx *c, double r_cut, int div, bool apply)
+// Cells of every replica for `div` cells per r_list = r_cut (+ skin when the step
+// keeps candidate lists) (Sec. 2.3 binning): the side is at least r_list / div,
+// and the count is capped so that sparse boxes do not get more cells than atoms
+// (bigger cells stay correct: the stencil still covers r_list).  Returns the
+// total; with apply, stores nc, the culling radii and the cell ranges in the host
+// replica table.
+int64_t cell_layout(rbmd_ctx *c, int div, bool apply)
 {
+    const double r_cut = c->prm.r_cut;
+    const double r_list = r_cut + (c->verlet ? c->skin : 0.0);
     int64_t cell0 = 0;
     for (int r = 0; r < c->R; ++r) {
         Rep &rp = c->reps_h[r];
-        int nc = (int)floor(rp.L * div / r_cut);
+        int nc = (int)floor(rp.L * div / r_list);
         if (nc < 1) nc = 1;
-        while (nc > 1 && (double)rp.Rlin * (double)nc > (double)div * kTwo32) --nc;
+        while (nc > 1 && (double)rp.Rv * (double)nc > (double)div * kTwo32) --nc;
         const double max_cells = fmax(8.0 * (double)rp.N, 1048576.0);
         while (nc > 1 && (double)nc * nc * nc > max_cells) --nc;
         if (apply) {
             rp.nc = nc;
             rp.cull_r = (float)(r_cut * nc / rp.L * (1.0 + 1e-5) + 1e-6);
+            rp.cull_v = (float)(r_list * nc / rp.L * (1.0 + 1e-5) + 1e-6);
             rp.cell0 = cell0;
             rp.ncell = (int64_t)nc * nc * nc;
         }
@@ -384,9 +396,11 @@ rbmd_status charge_sums(rbmd_ctx *c, bool check_neutral = true)
 
 // kick != NULL (the integrator's step): the RBE force kernel also does the second
 // half kick; *kicked tells whether it ran.
+// verlet: the short-range part of the integrator's step on its candidate lists
+// (rbl_pairs_verlet); the same lists, batches and forces as the cell walk.
 rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool apply_corr,
                         bool marks = false, const StepRef *kick = nullptr, bool *kicked = nullptr,
-                        bool counted = false)
+                        bool counted = false, bool verlet = false)
 {
     if (kicked) *kicked = false;
     const bool do_rbe = !(c->prm.flags & RBMD_NO_RBE);
@@ -412,9 +426,16 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
     }
     if (marks) prof_mark(c, 1);
     if (do_rbl) {
-        rbmd_status st = cells_build(c, counted);
-        if (marks) prof_mark(c, 2);  // stages 3 and 4 are marked inside
-        if (st == RBMD_OK) st = rbl_pairs(c, s, force, acc, false, nullptr, nullptr, nullptr, marks);
+        rbmd_status st = RBMD_OK;
+        if (verlet && !accumulate) {
+            st = verlet_prepare(c);
+            if (marks) prof_mark(c, 2);  // stages 3 and 4 are marked inside
+            if (st == RBMD_OK) st = rbl_pairs_verlet(c, s, force, marks);
+        } else {
+            st = cells_build(c, counted);
+            if (marks) prof_mark(c, 2);  // stages 3 and 4 are marked inside
+            if (st == RBMD_OK) st = rbl_pairs(c, s, force, acc, false, nullptr, nullptr, nullptr, marks);
+        }
         if (marks) prof_mark(c, 5);
         if (st == RBMD_OK)
             st = rbl_correction(c, force, apply_corr, apply_corr ? SCAL_FCORR_AUX : SCAL_FCORR);
@@ -455,10 +476,12 @@ rbmd_status record_step(rbmd_ctx *c)
 {
     StepRef next{c->d_step, 1};
     prof_mark(c, 0);
-    const bool bin = !(c->prm.flags & RBMD_NO_RBL);  // the drift kernel also bins the atoms
+    // the drift kernel also bins the atoms (not when the candidate lists are used:
+    // they re-sort only at a rebuild)
+    const bool bin = !(c->prm.flags & RBMD_NO_RBL) && !c->verlet;
     RBMD_CHECK(md_kick_drift(c, bin));
     bool kicked = false;
-    RBMD_CHECK(forces_into(c, next, c->force, 0, false, true, &next, &kicked, bin));
+    RBMD_CHECK(forces_into(c, next, c->force, 0, false, true, &next, &kicked, bin, c->verlet));
     prof_mark(c, 10);
     RBMD_CHECK(md_kick_thermo(c, true, next, kicked));
     prof_mark(c, 11);
@@ -531,7 +554,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
             q.r_core != p.r_core || q.r_cut != p.r_cut || q.rbl_p != p.rbl_p ||
             q.thermostat != p.thermostat || q.coulomb_k != p.coulomb_k || q.dt != p.dt ||
             q.tau_T != p.tau_T || q.precision != p.precision || q.flags != p.flags ||
-            q.cell_div != p.cell_div || q.mh_moves != p.mh_moves)
+            q.cell_div != p.cell_div || q.mh_moves != p.mh_moves || q.skin != p.skin)
             return RBMD_ERR_INVALID;
         if (!(q.r_cut < 0.5 * q.box_length)) return RBMD_ERR_BOX_TOO_SMALL;
         Ntot += q.n_atoms;
@@ -635,6 +658,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
         rp.Rc2 = radius2_units(p.r_core, rp.L);
         rp.Rs2 = radius2_units(p.r_cut, rp.L);
         rp.Rlin = isqrt64(rp.Rs2);
+        rp.Rv = rp.Rlin;
         rp.atom0 = atom0;
         rp.N = q.n_atoms;
         rp.b256_0 = (int32_t)m256.size();
@@ -649,10 +673,43 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
         max_mc = fmax(max_mc, mc);
         max_ms = fmax(max_ms, n * 4.0 / 3.0 * kPi * (p.r_cut * p.r_cut * p.r_cut) - mc);
     }
+    // candidate lists of the integrator's step (the lists, batches and forces are
+    // the same without them; they only save the per-step cell walk): a skin of
+    // p.skin (0: 0.4 sigma), off for exact lists, large batches, RBL off, or a box
+    // where r_cut + skin reaches half the box
+    c->skin = p.skin == 0.0 ? 0.4 : p.skin;
+    c->verlet = c->skin > 0.0 && !(p.flags & (RBMD_RBL_EXACT | RBMD_NO_RBL)) && p.rbl_p <= 16;
+    if (const char *env = getenv("RBMD_NO_CANDIDATES")) c->verlet = c->verlet && atoi(env) == 0;
+    double max_mv = 0.0;
+    for (int r = 0; r < R && c->verlet; ++r) {
+        Rep &rp = c->reps_h[r];
+        const double h = floor(0.5 * c->skin * (kTwo32 / rp.L));
+        const double Rv = (double)rp.Rlin + 1.0 + 2.0 * h;
+        if (!(p.r_cut + c->skin < 0.5 * rp.L) || Rv >= 2147483000.0) {
+            c->verlet = false;
+            break;
+        }
+        rp.H2 = (uint64_t)h * (uint64_t)h;
+        rp.Rv = (uint32_t)Rv;
+        rp.Rv2 = (uint64_t)rp.Rv * (uint64_t)rp.Rv;
+        const double n = (double)rp.N / (rp.L * rp.L * rp.L);
+        const double rl = p.r_cut + c->skin;
+        max_mv = fmax(max_mv, n * 4.0 / 3.0 * kPi * rl * rl * rl);
+    }
+    if (!c->verlet)
+        for (int r = 0; r < R; ++r) c->reps_h[r].Rv = c->reps_h[r].Rlin;
+    // capacities: candidates mean + 5 sd + 8; the core and shell entries a thread
+    // keeps in shared memory mean + 5 sd + 4 (beyond them: the exact fallback)
+    c->vl_cv = ((int)ceil(max_mv + 5.0 * sqrt(max_mv) + 8.0) + 3) / 4 * 4;
+    c->vl_ccs = (int)ceil(max_mc + 5.0 * sqrt(max_mc) + 4.0);
+    c->vl_css = (int)ceil(max_ms + 5.0 * sqrt(max_ms) + 4.0);
+    if ((c->vl_ccs + c->vl_css) * 128 * 4 > 160 * 1024) c->verlet = false;
+    c->vl_dirty = true;
+
     // cell arrays and tile partials sized for every layout rbmd_set_tiles allows
-    c->ncell_max = std::max(cell_layout(c, p.r_cut, 1, false), cell_layout(c, p.r_cut, 2, false));
+    c->ncell_max = std::max(cell_layout(c, 1, false), cell_layout(c, 2, false));
     c->ntiles_max = tile_layout(c, 512, false, tl);
-    c->ncell = cell_layout(c, p.r_cut, c->div, true);
+    c->ncell = cell_layout(c, c->div, true);
     c->ntiles = tile_layout(c, c->rho_tile, true, tl);
     c->cdf_total = (int64_t)T.size();
     c->nb256 = (int)m256.size();
@@ -677,6 +734,8 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
         if (sscanf(env, "%d,%d", &cc, &cs) == 2 && cc >= 1 && cs >= 1) {
             c->list_cc = cc;
             c->list_cs = cs;
+            c->vl_ccs = std::min(c->vl_ccs, cc);
+            c->vl_css = std::min(c->vl_css, cs);
         }
     }
 
@@ -747,7 +806,12 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(alloc_n(&c->adj_tsum, 2 * (size_t)c->T));
     TRY(alloc_n(&c->epart, EPART * (size_t)c->pair_parts));
     TRY(alloc_n(&c->kepart, (size_t)c->nb256 * 3));
-    TRY(alloc_n(&c->ibuf, 4));
+    TRY(alloc_n(&c->ibuf, 8));
+    if (c->verlet) {
+        TRY(alloc_n(&c->vl_cand, (size_t)((N + 31) / 32) * 32 * c->vl_cv));
+        TRY(alloc_n(&c->vl_ncand, (size_t)N));
+        TRY(alloc_n(&c->vl_sref, (size_t)N));
+    }
     g_alloc_countdown = -1;
 
     // LJ tables: sqrt(eps_t), sigma_t/2 (Lorentz-Berthelot, Eq. 4)
@@ -776,6 +840,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(upload_lj(c, lj_eps, lj_sigma));
     TRY(rbe_configure(c));
     TRY(rbl_configure(c));
+    TRY(verlet_configure(c));
     TRY(cuda_status(cudaMemcpy(c->reps, c->reps_h, sizeof(Rep) * R, cudaMemcpyHostToDevice)));
     TRY(cuda_status(cudaMemcpy(c->map256, m256.data(), sizeof(int2) * m256.size(), cudaMemcpyHostToDevice)));
     TRY(cuda_status(cudaMemcpy(c->map128, m128.data(), sizeof(int2) * m128.size(), cudaMemcpyHostToDevice)));
@@ -794,6 +859,8 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     }
     TRY(cuda_status(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)));
     TRY(cuda_status(cudaMemsetAsync(c->u4, 0, sizeof(uint4) * N, c->stream)));
+    TRY(cuda_status(cudaMemsetAsync(c->ibuf, 0, 8 * sizeof(int32_t), c->stream)));
+    k_iota_spos<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->spos, N);
     k_init_scal<<<(R * SCAL_COUNT + 255) / 256, 256, 0, c->stream>>>(c->scal, R);
     k_set_i64<<<1, 1, 0, c->stream>>>(c->d_step, 0);
 
@@ -814,6 +881,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
 #undef TRY
     c->step = 0;
     c->have_force = false;
+    c->vl_dirty = true;
     leave(c, RBMD_OK);
     *out = c;
     return RBMD_OK;
@@ -956,6 +1024,7 @@ rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t 
     cudaStreamSynchronize(c->side);
     c->step = step;
     c->have_force = false;
+    c->vl_dirty = true;
     return leave(c, st);
 }
 
@@ -965,9 +1034,16 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
     if (n_steps == 0) return RBMD_OK;
     enter(c);
     rbmd_status s = RBMD_OK;
+    if (c->verlet && c->vl_dirty) {
+        // the sorted layout was changed outside the step: rebuild the candidates
+        if (cudaMemsetAsync(c->ibuf + 4, 1, sizeof(int32_t), c->stream) != cudaSuccess)
+            return leave(c, RBMD_ERR_CUDA);
+        c->vl_dirty = false;
+    }
     if (!c->have_force) {
         k_set_i64<<<1, 1, 0, c->stream>>>(c->d_step, c->step);
-        s = forces_into(c, StepRef{nullptr, c->step}, c->force, 0, false);
+        s = forces_into(c, StepRef{nullptr, c->step}, c->force, 0, false, false, nullptr, nullptr,
+                        false, c->verlet);
         if (s == RBMD_OK) s = md_thermo_prepare(c);
         if (s != RBMD_OK) return leave(c, s);
         c->have_force = true;
@@ -1120,6 +1196,18 @@ rbmd_status rbmd_energy(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
 
 int32_t rbmd_replica_count(rbmd_ctx *c) { return c ? c->R : 0; }
 
+int64_t rbmd_candidate_rebuilds(rbmd_ctx *c)
+{
+    if (!c) return -1;
+    if (!c->verlet) return 0;
+    int32_t n = 0;
+    if (cudaMemcpyAsync(&n, c->ibuf + 5, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return -1;
+    return n;
+}
+
 rbmd_status rbmd_set_tiles(rbmd_ctx *c, int32_t cell_div, int32_t rho_tile, int32_t rho_mode_tile)
 {
     if (!c) return RBMD_ERR_INVALID;
@@ -1128,7 +1216,8 @@ rbmd_status rbmd_set_tiles(rbmd_ctx *c, int32_t cell_div, int32_t rho_tile, int3
     if (rho_mode_tile != 64 && rho_mode_tile != 128 && rho_mode_tile != 256) return RBMD_ERR_INVALID;
     RBMD_CHECK_CUDA(cudaStreamSynchronize(c->stream));
     std::vector<int2> tl;
-    c->ncell = cell_layout(c, c->prm.r_cut, cell_div, true);
+    c->ncell = cell_layout(c, cell_div, true);
+    c->vl_dirty = true;
     c->ntiles = tile_layout(c, rho_tile, true, tl);
     c->div = cell_div;
     c->rho_tile = rho_tile;
@@ -1313,6 +1402,7 @@ rbmd_status rbmd_set_charges(rbmd_ctx *c, const void *charge)
                                                  c->type, c->T, c->err);
     rbmd_status s = charge_sums(c, false);
     c->have_force = false;
+    c->vl_dirty = true;
     return leave(c, s);
 }
 
@@ -1322,6 +1412,7 @@ rbmd_status rbmd_set_lj(rbmd_ctx *c, const double *lj_eps, const double *lj_sigm
     enter(c);
     rbmd_status s = upload_lj(c, lj_eps, lj_sigma);
     c->have_force = false;
+    c->vl_dirty = true;
     return leave(c, s);
 }
 
@@ -1364,6 +1455,7 @@ rbmd_status rbmd_set_state(rbmd_ctx *c, const void *pos, const void *vel, int64_
     }
     c->step = step;
     c->have_force = false;
+    c->vl_dirty = true;
     return leave(c, s);
 }
 
@@ -1405,6 +1497,7 @@ rbmd_status rbmd_set_state_u(rbmd_ctx *c, const uint32_t *u, const void *vel, in
     }
     c->step = step;
     c->have_force = false;
+    c->vl_dirty = true;
     return leave(c, s);
 }
 
@@ -1430,7 +1523,8 @@ rbmd_status rbmd_set_thermostat(rbmd_ctx *c, const double *xi)
         s = cuda_status(cudaMemcpyAsync(c->scal + (size_t)r * SCAL_COUNT + SCAL_XI, xi + r,
                                         sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
-    c->have_force = false;  // the next rbmd_step redoes the first half update
+    c->have_force = false;
+    c->vl_dirty = true;  // the next rbmd_step redoes the first half update
     return leave(c, s);
 }
 

@@ -22,10 +22,14 @@
 namespace rbmd {
 
 // ---------------------------------------------------------------- binning
+// cond (every kernel of the cell sort): when not NULL the kernel does nothing
+// unless *cond is set (the integrator's conditional rebuild inside its graph).
 __global__ void k_cell_count(const uint4 *__restrict__ u4, const int2 *__restrict__ map,
                              const Rep *__restrict__ reps, int32_t *__restrict__ count,
-                             int32_t *__restrict__ cell_of, int32_t *__restrict__ rank)
+                             int32_t *__restrict__ cell_of, int32_t *__restrict__ rank,
+                             const int32_t *__restrict__ cond = nullptr)
 {
+    if (cond && !*cond) return;
     const AtomSlot sl = atom_slot(map, reps);
     if (!sl.ok) return;
     const int64_t i = sl.i;
@@ -44,8 +48,10 @@ __global__ void k_cell_count(const uint4 *__restrict__ u4, const int2 *__restric
 // tile scans).  SCAN_TILE elements per block.
 constexpr int SCAN_TILE = 1024;
 
-__global__ void k_scan_tiles(const int32_t *__restrict__ in, int64_t n, int32_t *__restrict__ tsum)
+__global__ void k_scan_tiles(const int32_t *__restrict__ in, int64_t n, int32_t *__restrict__ tsum,
+                             const int32_t *__restrict__ cond = nullptr)
 {
+    if (cond && !*cond) return;
     __shared__ int32_t s[32];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     int v = 0;
@@ -93,8 +99,10 @@ __device__ __forceinline__ int block_scan_incl(int v, int *total)
     return incl;
 }
 
-__global__ void k_scan_top(int32_t *__restrict__ tsum, int ntiles)
+__global__ void k_scan_top(int32_t *__restrict__ tsum, int ntiles,
+                           const int32_t *__restrict__ cond = nullptr)
 {
+    if (cond && !*cond) return;
     // one block: exclusive scan in chunks of blockDim
     int carry = 0;
     for (int b = 0; b < ntiles; b += blockDim.x) {
@@ -108,8 +116,10 @@ __global__ void k_scan_top(int32_t *__restrict__ tsum, int ntiles)
 }
 
 __global__ void k_scan_final(const int32_t *__restrict__ in, int64_t n,
-                             const int32_t *__restrict__ toff, int32_t *__restrict__ out)
+                             const int32_t *__restrict__ toff, int32_t *__restrict__ out,
+                             const int32_t *__restrict__ cond = nullptr)
 {
+    if (cond && !*cond) return;
     // blockDim = SCAN_TILE, one element per thread
     const int64_t k = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x;
     const int v = k < n ? in[k] : 0;
@@ -125,8 +135,10 @@ __global__ void k_cell_scatter(const uint4 *__restrict__ u4, const double *__res
                                const int32_t *__restrict__ cell_of,
                                const int32_t *__restrict__ rank,
                                const int32_t *__restrict__ start, uint4 *__restrict__ spos,
-                               real *__restrict__ sq, int32_t *__restrict__ stype)
+                               real *__restrict__ sq, int32_t *__restrict__ stype,
+                               const int32_t *__restrict__ cond = nullptr)
 {
+    if (cond && !*cond) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     uint4 A = u4[i];
@@ -143,8 +155,10 @@ __global__ void k_cell_scatter(const uint4 *__restrict__ u4, const double *__res
 template <typename real>
 __global__ void k_cell_order(const int32_t *__restrict__ start, int64_t ncell,
                              uint4 *__restrict__ spos, real *__restrict__ sq,
-                             int32_t *__restrict__ stype, int32_t *__restrict__ sidx)
+                             int32_t *__restrict__ stype, int32_t *__restrict__ sidx,
+                             const int32_t *__restrict__ cond = nullptr)
 {
+    if (cond && !*cond) return;
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     int b = start[c], e = start[c + 1];
@@ -166,6 +180,14 @@ __global__ void k_cell_order(const int32_t *__restrict__ start, int64_t ncell,
     for (int a = b; a < e; ++a) sidx[spos[a].w] = a;
 }
 
+// Zeroes n counts when *cond is set (the conditional rebuild's memset).
+__global__ void k_vl_zero(int32_t *__restrict__ v, int64_t n, const int32_t *__restrict__ cond)
+{
+    if (!*cond) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = 0;
+}
+
 // Cell counts, cells and ranks of the atoms of the 256-atom blocks [b0, b1) of
 // map256 (the counts zeroed beforehand); cells_build(c, true) then completes the sort.
 rbmd_status cells_count_blocks(rbmd_ctx *c, int b0, int b1)
@@ -177,42 +199,57 @@ rbmd_status cells_count_blocks(rbmd_ctx *c, int b0, int b1)
     return RBMD_OK;
 }
 
-rbmd_status cells_build(rbmd_ctx *c, bool counted)
+// The counting sort of the atoms by cell.  cond == NULL: now (the caller's
+// sorted layout replaces the step's candidate lists, which are then rebuilt before
+// the next step); else every kernel checks *cond on the device.
+static rbmd_status cells_sort(rbmd_ctx *c, bool counted, const int32_t *cond)
 {
     const int th = 256;
     const unsigned nb = (unsigned)((c->N + th - 1) / th);
     if (!counted) {
-        RBMD_CHECK_CUDA(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, c->stream));
+        if (cond) {
+            k_vl_zero<<<(unsigned)((c->ncell + 255) / 256), 256, 0, c->stream>>>(c->cell_count,
+                                                                                c->ncell, cond);
+        } else {
+            RBMD_CHECK_CUDA(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, c->stream));
+        }
         k_cell_count<<<c->nb256, 256, 0, c->stream>>>(c->u4, c->map256, c->reps, c->cell_count,
-                                                       c->cell_of, c->cell_rank);
+                                                       c->cell_of, c->cell_rank, cond);
         RBMD_LAUNCH_CHECK();
     }
     const int ntiles = (int)((c->ncell + SCAN_TILE - 1) / SCAN_TILE);
-    k_scan_tiles<<<ntiles, 256, 0, c->stream>>>(c->cell_count, c->ncell, c->scan_part);
+    k_scan_tiles<<<ntiles, 256, 0, c->stream>>>(c->cell_count, c->ncell, c->scan_part, cond);
     RBMD_LAUNCH_CHECK();
-    k_scan_top<<<1, 1024, 0, c->stream>>>(c->scan_part, ntiles);
+    k_scan_top<<<1, 1024, 0, c->stream>>>(c->scan_part, ntiles, cond);
     RBMD_LAUNCH_CHECK();
     k_scan_final<<<ntiles, SCAN_TILE, 0, c->stream>>>(c->cell_count, c->ncell, c->scan_part,
-                                                      c->cell_start);
+                                                      c->cell_start, cond);
     RBMD_LAUNCH_CHECK();
     const unsigned ncb = (unsigned)((c->ncell + th - 1) / th);
     if (c->fp64) {
         k_cell_scatter<double><<<nb, th, 0, c->stream>>>(c->u4, c->q64, c->type, c->N, c->cell_of,
                                                          c->cell_rank, c->cell_start, c->spos,
-                                                         (double *)c->sq, c->stype);
+                                                         (double *)c->sq, c->stype, cond);
         RBMD_LAUNCH_CHECK();
         k_cell_order<double><<<ncb, th, 0, c->stream>>>(c->cell_start, c->ncell, c->spos,
-                                                        (double *)c->sq, c->stype, c->cell_rank);
+                                                        (double *)c->sq, c->stype, c->cell_rank,
+                                                        cond);
     } else {
         k_cell_scatter<float><<<nb, th, 0, c->stream>>>(c->u4, nullptr, c->type, c->N, c->cell_of,
                                                         c->cell_rank, c->cell_start, c->spos,
-                                                        (float *)c->sq, c->stype);
+                                                        (float *)c->sq, c->stype, cond);
         RBMD_LAUNCH_CHECK();
         k_cell_order<float><<<ncb, th, 0, c->stream>>>(c->cell_start, c->ncell, c->spos,
-                                                       (float *)c->sq, c->stype, c->cell_rank);
+                                                       (float *)c->sq, c->stype, c->cell_rank, cond);
     }
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
+}
+
+rbmd_status cells_build(rbmd_ctx *c, bool counted)
+{
+    c->vl_dirty = true;
+    return cells_sort(c, counted, nullptr);
 }
 
 // ---------------------------------------------------------------- pair kernels
@@ -266,6 +303,8 @@ template <typename real> struct PairArgs {
     int32_t *heavy_n;     // [1] their count
     int32_t *ovf;      // [0] set when any list overflowed
     int CC, CS;
+    int stale;         // the cells are those of the last rebuild of the step's candidate
+                       // lists (atoms have moved since): cull at r_cut + skin
 };
 
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
@@ -591,7 +630,7 @@ __device__ __forceinline__ void stencil_ranges(const PairArgs<real> &a, const Re
     const bool full = nc >= 2 * dv + 1;  // else every cell along an axis, once
     const int span = full ? 2 * dv + 1 : nc;
     const float fxc = cell_frac(A.x, nc), fyc = cell_frac(A.y, nc), fzc = cell_frac(A.z, nc);
-    const float Rw = rp.cull_r, Rw2 = rp.cull_r * rp.cull_r;
+    const float Rw = a.stale ? rp.cull_v : rp.cull_r, Rw2 = Rw * Rw;
     for (int ox = 0; ox < span; ++ox) {
         float wx = 0.f;
         int gx = ox;
@@ -722,13 +761,13 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
 // CAP - p "minus infinity" markers, then the p smallest ascending (or empty slots).
 template <int CAP>
 __device__ __noinline__ void select_exact(const Philox0 &r0, uint2 key, const int32_t *ls, int ns,
-                                          int p, int (&hk)[CAP])
+                                          int p, int (&hk)[CAP], int stride = 1)
 {
     uint64_t kk[CAP];
     uint32_t kid[CAP];
     int kept = 0;
     for (int e = 0; e < ns; ++e) {
-        const uint32_t id = (uint32_t)ls[e];
+        const uint32_t id = (uint32_t)ls[e * stride];
         const uint2 w = philox_rest(r0, id, key);
         const uint64_t v = ((uint64_t)w.x << 32) | w.y;
         int j;  // the slot the shifting starts from
@@ -1363,11 +1402,13 @@ static void launch_rbl(rbmd_ctx *c, const PairArgs<real> &a, cudaStream_t st, bo
     }
 }
 
+// Launch arguments of the RBL kernels from the context (force output, flags and
+// verification outputs left for the caller).
 template <typename real>
-static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
-                               int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks)
+static PairArgs<real> pair_args(rbmd_ctx *c, StepRef s)
 {
     PairArgs<real> a;
+    memset(&a, 0, sizeof(a));
     a.spos = c->spos;
     a.sq = (const real *)c->sq;
     a.stype = c->stype;
@@ -1389,15 +1430,10 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     a.tab_n = c->ptab_n;
     a.tab_i0 = c->ptab_i0;
     a.tab_inv_h = (real)c->ptab_inv_h;
-    a.F = (real *)force;
-    a.accumulate = accumulate;
     a.fpart = c->fpart;
     a.epart = c->epart;
     a.fb_part0 = 4 * (int64_t)c->nb128;
     a.imax = c->ibuf;
-    a.n_core = n_core;
-    a.n_shell = n_shell;
-    a.batch = batch;
     a.lcore = c->lcore;
     a.lshell = c->lshell;
     a.sidx = c->cell_rank;
@@ -1410,6 +1446,19 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
     a.ovf = c->ibuf + 2;
     a.CC = c->list_cc;
     a.CS = c->list_cs;
+    return a;
+}
+
+template <typename real>
+static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
+                               int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks)
+{
+    PairArgs<real> a = pair_args<real>(c, s);
+    a.F = (real *)force;
+    a.accumulate = accumulate;
+    a.n_core = n_core;
+    a.n_shell = n_shell;
+    a.batch = batch;
     RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf + 2, 0, sizeof(int32_t), c->stream));
     const bool lists = n_core != nullptr;
     const int p = c->prm.rbl_p;
@@ -1426,33 +1475,7 @@ static rbmd_status rbl_pairs_t(rbmd_ctx *c, StepRef s, void *force, int accumula
 template <typename real>
 static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
 {
-    PairArgs<real> a;
-    memset(&a, 0, sizeof(a));
-    a.spos = c->spos;
-    a.sq = (const real *)c->sq;
-    a.stype = c->stype;
-    a.cell_start = c->cell_start;
-    a.N = c->N;
-    a.reps = c->reps;
-    a.map = c->map256;
-    a.div = c->div;
-    a.T = c->T;
-    a.p = c->prm.rbl_p;
-    a.exact = (c->prm.flags & RBMD_RBL_EXACT) ? 1 : 0;
-    a.step = s;
-    a.imax = c->ibuf;
-    a.lcore = c->lcore;
-    a.lshell = c->lshell;
-    a.sidx = c->cell_rank;
-    a.heavy = c->heavy;
-    a.heavy_n = c->ibuf + 3;
-    a.sel_exact = c->sel_exact;
-    a.sel_key_bits = c->sel_key_bits;
-    a.ncount = c->ncount;
-    a.bk = c->bk;
-    a.ovf = c->ibuf + 2;
-    a.CC = c->list_cc;
-    a.CS = c->list_cs;
+    PairArgs<real> a = pair_args<real>(c, s);
     RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf, 0, 3 * sizeof(int32_t), c->stream));
     const unsigned nb256 = (unsigned)c->nb256;
     k_rbl_scan<real, true, false><<<nb256, 256, 0, c->stream>>>(a);
@@ -1497,6 +1520,295 @@ rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool 
     if (c->fp64)
         return rbl_pairs_t<double>(c, s, force, accumulate, energy, n_core, n_shell, batch, marks);
     return rbl_pairs_t<float>(c, s, force, accumulate, energy, n_core, n_shell, batch, marks);
+}
+
+// ---------------------------------------------------------------- the step's candidate lists
+//
+// The integrator's short-range part keeps, per cell-sorted atom, the list of its
+// candidates: every atom within Rv of it at the last rebuild (Rv = Rlin + 1 + 2h
+// fixed-point units, h = floor(skin/2 in units)), and keeps the sorted order of
+// that rebuild between rebuilds (positions gathered into it every step).  A
+// rebuild happens when some atom's displacement d since the rebuild has
+// |d|^2 > h^2 (exact integers).  Until then every pair with D <= Rs2 is on the
+// candidate list: with |d_i|, |d_j| <= h, the rebuild's separation satisfies
+// |r_ref| <= |r_now| + 2h < Rlin + 1 + 2h = Rv.  Every step classifies the
+// candidates exactly (core D < Rc2, shell Rc2 <= D <= Rs2, as classify), so the
+// core list, N_s and the batch are the sets the cell walk gives; the core list
+// and a whole-shell batch are put in atom-id order and a drawn batch is in
+// priority order, so the pair sums do not depend on when the lists were built.
+struct VlArgs {
+    const int32_t *cand;  // [ceil(N/32)][cv][32]
+    int32_t *cand_w;      // the same array, written by the rebuild
+    int32_t *ncand;
+    uint4 *sref;
+    int32_t *flag;        // rebuild pending
+    int32_t *nrebuild;
+    int cv, ccs, css;
+};
+
+__device__ __forceinline__ int64_t vl_slot(int64_t is, int t, int cv)
+{
+    return (is >> 5) * (int64_t)cv * 32 + (int64_t)t * 32 + (is & 31);
+}
+
+// Positions of the current state in the sorted order of the last rebuild, and
+// the displacement test that asks for a rebuild.  Nothing to do when a rebuild is
+// already pending (it sorts the state afresh).
+__global__ void k_vl_gather(const Rep *__restrict__ reps, const int2 *__restrict__ map,
+                            uint4 *__restrict__ spos, const uint4 *__restrict__ u4,
+                            const uint4 *__restrict__ sref, int32_t *__restrict__ flag)
+{
+    if (*flag) return;
+    const AtomSlot sl = atom_slot(map, reps);
+    if (!sl.ok) return;
+    const uint32_t id = spos[sl.i].w;
+    const uint4 U = u4[id];
+    spos[sl.i] = make_uint4(U.x, U.y, U.z, id);
+    const uint4 R = sref[sl.i];
+    const int32_t dx = (int32_t)(U.x - R.x), dy = (int32_t)(U.y - R.y), dz = (int32_t)(U.z - R.z);
+    const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
+                       (uint64_t)((int64_t)dz * dz);
+    if (D > reps[sl.r].H2) *flag = 1;
+}
+
+// Rebuild (only when *flag): every atom within Rv of each sorted atom, from the
+// freshly sorted cells (stencil culled at r_cut + skin), and the reference
+// positions.
+template <typename real>
+__global__ void __launch_bounds__(256) k_vl_build(PairArgs<real> a, VlArgs v)
+{
+    if (!*v.flag) return;
+    const AtomSlot sl = atom_slot(a.map, a.reps);
+    if (!sl.ok) return;
+    const int64_t is = sl.i;
+    const Rep rp = a.reps[sl.r];
+    const uint4 A = a.spos[is];
+    v.sref[is] = A;
+    const uint32_t R2x = 2u * rp.Rv;
+    int n = 0;
+    stencil_ranges(a, rp, A, [&](int kb, int ke) {
+        for (int k = kb; k < ke; ++k) {
+            const uint4 B = a.spos[k];
+            const int32_t dx = (int32_t)(B.x - A.x), dy = (int32_t)(B.y - A.y),
+                          dz = (int32_t)(B.z - A.z);
+            if (((uint32_t)dx + rp.Rv > R2x) | ((uint32_t)dy + rp.Rv > R2x) |
+                ((uint32_t)dz + rp.Rv > R2x) | (k == (int)is))
+                continue;
+            const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
+                               (uint64_t)((int64_t)dz * dz);
+            if (D > rp.Rv2) continue;
+            if (n < v.cv) v.cand_w[vl_slot(is, n, v.cv)] = k;
+            ++n;
+        }
+    });
+    v.ncand[is] = n;
+}
+
+__global__ void k_vl_done(int32_t *__restrict__ flag, int32_t *__restrict__ nrebuild)
+{
+    if (*flag) {
+        *flag = 0;
+        ++*nrebuild;
+    }
+}
+
+// Ascending insertion sort of n values at v[0], v[s], v[2s], ...
+__device__ __forceinline__ void sort_strided(int32_t *v, int n, int s)
+{
+    for (int e = 1; e < n; ++e) {
+        const int32_t x = v[e * s];
+        int y = e - 1;
+        while (y >= 0 && v[y * s] > x) {
+            v[(y + 1) * s] = v[y * s];
+            --y;
+        }
+        v[(y + 1) * s] = x;
+    }
+}
+
+// Algorithm 2 step 1 for the step: classification of the candidates, N_s, the
+// batch and the core list, one thread per sorted atom (128 per block).  The core
+// and shell members (replica-local atom ids) are kept in shared memory,
+// [ccs + css][128] int32 (the shell list never goes to device memory); the batch
+// is the bottom-p selection of select_atom over them.  Outputs: lcore and bk rows
+// (sorted indices) and ncount, read by k_rbl_force.  An atom beyond a capacity
+// is marked overflowed for the exact fallback.
+template <typename real, int CAP>
+__global__ void __launch_bounds__(128) k_rbl_vclass(PairArgs<real> a, VlArgs v)
+{
+    extern __shared__ int32_t s_vl[];
+    const AtomSlot sl = atom_slot(a.map, a.reps);
+    if (!sl.ok) return;
+    const int64_t is = sl.i;
+    const Rep rp = a.reps[sl.r];
+    const uint4 A = a.spos[is];
+    const uint32_t id0 = (uint32_t)rp.atom0;
+    int32_t *s_core = s_vl + threadIdx.x;
+    int32_t *s_sh = s_vl + v.ccs * 128 + threadIdx.x;
+    const int n = v.ncand[is];
+    int nc = 0, ns = 0;
+    if (n <= v.cv) {
+        const int32_t *cl = v.cand + vl_slot(is, 0, v.cv);
+        int kn = n > 0 ? cl[0] : 0;
+        for (int t = 0; t < n; ++t) {
+            const int k = kn;
+            if (t + 1 < n) kn = cl[(t + 1) * 32];
+            const uint4 B = a.spos[k];
+            const int cls = classify(rp, A, B);
+            if (cls == 1) {
+                if (nc < v.ccs) s_core[nc * 128] = (int32_t)(B.w - id0);
+                ++nc;
+            } else if (cls == 2) {
+                if (ns < v.css) s_sh[ns * 128] = (int32_t)(B.w - id0);
+                ++ns;
+            }
+        }
+    }
+    if (n > v.cv || nc > v.ccs || ns > v.css || nc > a.CC) {
+        a.ncount[is] = make_int2(a.CC + 1, 0);
+        *a.ovf = 1;
+        return;
+    }
+    const int32_t *sidx = a.sidx + id0;
+    sort_strided(s_core, nc, 128);
+    int32_t *lc = a.lcore + is * a.CC;
+    for (int e = 0; e < nc; ++e) lc[e] = sidx[s_core[e * 128]];
+    int32_t *bk = a.bk + is * a.p;
+    if (ns <= a.p) {
+        sort_strided(s_sh, ns, 128);
+        for (int e = 0; e < ns; ++e) bk[e] = sidx[s_sh[e * 128]];
+    } else {
+        const Philox0 r0 = philox_round0(A.w - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key);
+        // packed keys as select_atom: the priority's high word with its low b bits
+        // replaced by the member's position (2^b > css), CAP + 1 smallest kept
+        const int b = 32 - __clz(v.css);
+        const uint32_t lo_mask = (1u << b) - 1u;
+        uint32_t keep = ~lo_mask;
+        if (a.sel_key_bits > 0 && a.sel_key_bits < 32) keep &= ~(0xFFFFFFFFu >> a.sel_key_bits);
+        uint32_t sk[CAP + 1];
+#pragma unroll
+        for (int e = 0; e <= CAP; ++e) sk[e] = 0xFFFFFFFFu;
+        for (int e = 0; e < ns; ++e) {
+            const uint2 w = philox_rest(r0, (uint32_t)s_sh[e * 128], rp.key);
+            uint32_t x = (w.x & keep) | (uint32_t)e;
+#pragma unroll
+            for (int j = 0; j <= CAP; ++j) {
+                const uint32_t m = min(sk[j], x);
+                x = max(sk[j], x);
+                sk[j] = m;
+            }
+        }
+        bool tie = a.sel_exact != 0;
+#pragma unroll
+        for (int e = 0; e < CAP; ++e)
+            if (e < a.p) tie |= ((sk[e] ^ sk[e + 1]) & keep) == 0u;
+        if (!tie) {
+#pragma unroll
+            for (int e = 0; e < CAP; ++e)
+                if (e < a.p) bk[e] = sidx[s_sh[(sk[e] & lo_mask) * 128]];
+        } else {
+            int hk[CAP];
+            select_exact<CAP>(r0, rp.key, s_sh, ns, a.p, hk, 128);
+            int nb = 0;
+            for (int e = 0; e < CAP; ++e)
+                if (hk[e] >= 0) bk[nb++] = sidx[hk[e]];
+        }
+    }
+    a.ncount[is] = make_int2(nc, ns);
+}
+
+template <typename real>
+static VlArgs vl_args(rbmd_ctx *c)
+{
+    VlArgs v;
+    v.cand = c->vl_cand;
+    v.cand_w = c->vl_cand;
+    v.ncand = c->vl_ncand;
+    v.sref = c->vl_sref;
+    v.flag = c->ibuf + 4;
+    v.nrebuild = c->ibuf + 5;
+    v.cv = c->vl_cv;
+    v.ccs = c->vl_ccs;
+    v.css = c->vl_css;
+    return v;
+}
+
+template <typename real>
+static rbmd_status verlet_prepare_t(rbmd_ctx *c)
+{
+    int32_t *flag = c->ibuf + 4;
+    k_vl_gather<<<c->nb256, 256, 0, c->stream>>>(c->reps, c->map256, c->spos, c->u4, c->vl_sref,
+                                                  flag);
+    RBMD_LAUNCH_CHECK();
+    RBMD_CHECK(cells_sort(c, false, flag));
+    PairArgs<real> a = pair_args<real>(c, StepRef{nullptr, 0});
+    a.stale = 1;  // cull at r_cut + skin: the candidates reach Rv
+    k_vl_build<real><<<c->nb256, 256, 0, c->stream>>>(a, vl_args<real>(c));
+    RBMD_LAUNCH_CHECK();
+    k_vl_done<<<1, 1, 0, c->stream>>>(flag, c->ibuf + 5);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+rbmd_status verlet_prepare(rbmd_ctx *c)
+{
+    if (c->fp64) return verlet_prepare_t<double>(c);
+    return verlet_prepare_t<float>(c);
+}
+
+static size_t vl_smem(const rbmd_ctx *c) { return (size_t)(c->vl_ccs + c->vl_css) * 128 * sizeof(int32_t); }
+
+template <typename real, int CAP>
+static void launch_vl(rbmd_ctx *c, const PairArgs<real> &a, bool marks)
+{
+    PairArgs<real> a128 = a;
+    a128.map = c->map128;
+    a128.nmap = c->nb128;
+    const unsigned nbp = (unsigned)c->nb128;
+    const unsigned nfb = (unsigned)min(c->nb128, 4 * 148);
+    k_rbl_vclass<real, CAP><<<nbp, 128, vl_smem(c), c->stream>>>(a128, vl_args<real>(c));
+    if (marks) {
+        prof_mark(c, 3);
+        prof_mark(c, 4);
+    }
+    if (a.tab) k_rbl_force<real, false, true><<<nbp, kPairBlock, 0, c->stream>>>(a128);
+    else k_rbl_force<real, false, false><<<nbp, kPairBlock, 0, c->stream>>>(a128);
+    k_rbl_fused<real, CAP, false, false><<<nfb, kPairBlock, 0, c->stream>>>(a128);
+}
+
+template <typename real>
+static rbmd_status rbl_pairs_verlet_t(rbmd_ctx *c, StepRef s, void *force, bool marks)
+{
+    PairArgs<real> a = pair_args<real>(c, s);
+    a.F = (real *)force;
+    a.accumulate = 0;
+    a.stale = 1;  // the fallback walks the cells of the last rebuild
+    RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf + 2, 0, sizeof(int32_t), c->stream));
+    if (c->prm.rbl_p <= 10) launch_vl<real, 10>(c, a, marks);
+    else launch_vl<real, 16>(c, a, marks);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+rbmd_status rbl_pairs_verlet(rbmd_ctx *c, StepRef s, void *force, bool marks)
+{
+    if (c->fp64) return rbl_pairs_verlet_t<double>(c, s, force, marks);
+    return rbl_pairs_verlet_t<float>(c, s, force, marks);
+}
+
+rbmd_status verlet_configure(rbmd_ctx *c)
+{
+    if (!c->verlet) return RBMD_OK;
+    const int bytes = (int)vl_smem(c);
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vclass<float, 10>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vclass<float, 16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vclass<double, 10>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vclass<double, 16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return RBMD_OK;
 }
 
 // ---------------------------------------------------------------- correction

@@ -92,9 +92,12 @@ struct Rep {
     uint64_t Rc2, Rs2;
     uint2 key;              // Philox key (seed)
     uint32_t Rlin;          // floor(sqrt(Rs2)): per-axis early reject
+    uint32_t Rv;            // candidate radius of the step's lists: Rlin + 1 + 2 h (= Rlin without them)
+    uint64_t Rv2, H2;       // Rv^2; h^2 with h = floor(skin/2 in fixed-point units)
     uint32_t tag_rbe, tag_rbl;
     int32_t nc, M;          // cells per axis, sampler half-width
-    float cull_r;           // r_cut in cell widths (+ margin)
+    float cull_r;           // r_cut in cell widths (+ margin): cells sorted for these positions
+    float cull_v;           // r_cut + skin in cell widths (+ margin): cells of the last rebuild
     float dtc_hi, dtc_lo;   // dtc as a sum of two floats (FP32 drift)
     int64_t atom0, N;
     int64_t cell0, ncell;
@@ -240,7 +243,9 @@ struct rbmd_ctx {
     double *fpart;        // [pair_parts][3] force partial sums (per warp)
     double *epart;        // [pair_parts][EPART] energy and virial partial sums
     double *kepart;       // [nb256]
-    int32_t *ibuf;        // [4] integer diagnostics
+    int32_t *ibuf;        // [8] integer diagnostics and flags: 0 max N_s, 1 max cell,
+                          // 2 list overflow, 3 heavy atoms, 4 rebuild the step's candidates,
+                          // 5 rebuilds so far
     float *lj_f;          // [2*T] sqrt(eps), sigma/2 (FP32 path)
     double *lj_d;         // [2*T] (FP64 path)
     int pair_parts;       // per-warp partial sums: pair kernel (4 nb128), then the fallback (4 nb128)
@@ -255,6 +260,18 @@ struct rbmd_ctx {
     void *adj_lj;         // real [2T]: eps_t, sigma_t (adjoint)
     double *adj_tpart;    // [adjoint blocks][2T]
     double *adj_tsum;     // [2T]
+
+    // neighbour candidates of the integrator's step (Verlet lists with a skin):
+    // built from the cells at a rebuild, classified exactly every step
+    bool verlet;          // the step uses them (skin > 0, p <= 16, batches not exact)
+    bool vl_dirty;        // the sorted layout changed outside the step: rebuild before the next
+    double skin;
+    int vl_cv;            // candidate capacity per atom
+    int vl_ccs, vl_css;   // core and shell entries per thread kept in shared memory
+    int32_t *vl_cand;     // [ceil(N/32)][vl_cv][32] sorted indices (entry t of atom i at
+                          //  (i/32) cv 32 + 32 t + i%32: a warp's loads of entry t coalesce)
+    int32_t *vl_ncand;    // [N] candidate count (> vl_cv: the atom takes the exact fallback)
+    uint4 *vl_sref;       // [N] sorted positions at the last rebuild
 
     // integrator state
     int64_t step;
@@ -447,6 +464,14 @@ rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool 
 rbmd_status rbl_correction(rbmd_ctx *c, void *force, bool apply, int slot);
 
 rbmd_status rbl_lists(rbmd_ctx *c, StepRef s);
+// The integrator's short-range part on the candidate lists: the sorted positions
+// gathered from the current state, the cell sort and the candidate lists rebuilt
+// on the device when an atom has moved more than half the skin since the last
+// rebuild (or the layout was changed outside the step), then the exact
+// classification, batch selection and pair forces (same sets as rbl_pairs).
+rbmd_status verlet_prepare(rbmd_ctx *c);
+rbmd_status rbl_pairs_verlet(rbmd_ctx *c, StepRef s, void *force, bool marks);
+rbmd_status verlet_configure(rbmd_ctx *c);
 rbmd_status rbl_max_counts(rbmd_ctx *c, int32_t *out_dev);
 
 // adjoint (adjoint.cu)

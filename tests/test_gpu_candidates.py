@@ -1,0 +1,136 @@
+"""The integrator's neighbour candidate lists (rbmd_step with a skin).
+
+The step keeps, per atom, the atoms within r_cut + skin at the last rebuild and
+classifies them exactly on the integer positions every step; a rebuild runs on
+the device when an atom has moved more than skin/2 (or the sorted layout was
+changed by another call).  The core list, N_s and the batch (Algorithm 2 step 1)
+are then the sets of the per-step cell walk, and the forces are summed in an
+order that does not depend on when rebuilds happen:
+
+  * FP64 trajectories with and without the lists agree to rounding, for a skin
+    that rebuilds almost every step and for the default one;
+  * an FP32 run whose rebuilds are forced at other steps (other calls between
+    the steps) is bit-identical to an unbroken run;
+  * atoms beyond the lists' capacities take the exact fallback;
+  * batched replicas with their shared rebuild decision match stand-alone runs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2407_09315_b300 as rb
+from paper_2407_09315_b300 import synth
+
+from gpu_util import make_ctx, rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _wrap_diff(a, b):
+    a = np.asarray(a).astype(np.int64)
+    b = np.asarray(b).astype(np.int64)
+    return (a - b + 2 ** 31) % 2 ** 32 - 2 ** 31
+
+
+def _run(s, prec, n_steps, **kw):
+    ctx, _ = make_ctx(s, prec, rbe_P=40, seed=5, dt=0.002, thermostat=1, **kw)
+    ctx.set_state_u(s.u, vel=s.v, step=0)
+    ctx.step(n_steps)
+    u, v, st = ctx.get_state_u()
+    reb = ctx.candidate_rebuilds()
+    ctx.close()
+    return to_np(u).astype(np.int64) % 2 ** 32, to_np(v), st, reb
+
+
+@pytest.mark.parametrize("skin", [0.003, 0.4])
+def test_candidate_lists_match_cell_walk_fp64(skin):
+    s = synth.electrolyte(2000, seed=61, charges="2:1", n_types=2, T0=1.5)
+    u0, v0, _, r0 = _run(s, rb.FP64, 8, skin=-1.0)
+    u1, v1, st, r1 = _run(s, rb.FP64, 8, skin=skin)
+    assert st == 8 and r0 == 0
+    if skin < 0.01:
+        assert r1 >= 5, r1  # a tiny skin rebuilds nearly every step
+    else:
+        assert 1 <= r1 <= 2, r1  # the first step builds; 8 steps stay within 0.2
+    assert np.max(np.abs(_wrap_diff(u1, u0))) <= 1
+    assert rel_err(v1, v0) < 1e-12
+
+
+def test_fp64_candidate_trajectory_matches_oracle():
+    s = synth.electrolyte(700, seed=62, charges="1:1", n_types=2, T0=1.2)
+    ctx, _ = make_ctx(s, rb.FP64, rbe_P=30, seed=6, dt=0.002, thermostat=1, skin=0.01)
+    ctx.set_state_u(s.u, vel=s.v, step=0)
+    ctx.step(6)
+    u, v, _ = ctx.get_state_u()
+    assert ctx.candidate_rebuilds() >= 2
+    F0, _ = oracle.forces(s.u, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10, 30, 6, 0)
+    uo, vo, _ = oracle.vv(s.u, s.v, F0, s.q, s.types, s.eps, s.sig, s.L, 0.62, 1.0, 2.0, 3.5, 10,
+                          30, seed=6, step0=0, dt=0.002, n_steps=6, thermostat=1)
+    assert np.max(np.abs(_wrap_diff(to_np(u).astype(np.int64) % 2 ** 32, uo))) <= 2
+    assert rel_err(to_np(v), vo) < 1e-9
+    ctx.close()
+
+
+def test_rebuild_schedule_does_not_change_fp32_results():
+    s = synth.electrolyte(3000, seed=63, charges="2:1", n_types=3)
+    a, _ = make_ctx(s, rb.FP32, seed=2, thermostat=1)
+    a.set_state_u(s.u, vel=s.v, step=0)
+    a.step(7)
+    ua, va, _ = a.get_state_u()
+    b, _ = make_ctx(s, rb.FP32, seed=2, thermostat=1)
+    b.set_state_u(s.u, vel=s.v, step=0)
+    for k in (2, 2, 3):
+        b.step(k)
+        b.forces(0)  # re-sorts the cells: the next step rebuilds its candidates
+    ub, vb, st = b.get_state_u()
+    assert st == 7
+    assert b.candidate_rebuilds() > a.candidate_rebuilds()
+    assert torch.equal(ua, ub) and torch.equal(va, vb)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [rb.FP64, rb.FP32])
+def test_candidate_overflow_takes_exact_fallback(prec, monkeypatch):
+    s = synth.electrolyte(1500, seed=64, charges="2:1", n_types=2)
+    ref, _ = make_ctx(s, prec, seed=3, skin=-1.0)
+    monkeypatch.setenv("RBMD_LIST_CAPS", "4,12")
+    ctx, _ = make_ctx(s, prec, seed=3)
+    monkeypatch.delenv("RBMD_LIST_CAPS")
+    for c in (ref, ctx):
+        c.set_state_u(s.u, vel=s.v, step=0)
+        c.step(3)
+    u0, v0, _ = ref.get_state_u()
+    u1, v1, _ = ctx.get_state_u()
+    d = _wrap_diff(to_np(u1).astype(np.int64) % 2 ** 32, to_np(u0).astype(np.int64) % 2 ** 32)
+    assert np.max(np.abs(d)) <= 1
+    assert rel_err(to_np(v1), to_np(v0)) < (1e-12 if prec == rb.FP64 else 1e-5)
+    ref.close()
+    ctx.close()
+
+
+def test_batch_candidates_match_standalone():
+    sizes = [900, 2100, 1300]
+    reps = [synth.electrolyte(n, seed=70 + r, charges="1:1", n_types=1) for r, n in enumerate(sizes)]
+    dev = torch.device("cuda:0")
+    cat = lambda k: np.concatenate([getattr(x, k) for x in reps])
+    pos = torch.from_numpy(np.concatenate([x.x for x in reps])).to(dev, torch.float32)
+    q = torch.from_numpy(cat("q")).to(dev, torch.float32)
+    vel = torch.from_numpy(cat("v")).to(dev, torch.float32)
+    ctx = rb.RBMD(pos, q, reps[0].eps, reps[0].sig, box_length=[x.L for x in reps],
+                  n_atoms=sizes, seed=[3, 4, 5], replica=[0, 1, 2], precision=rb.FP32,
+                  rbe_P=50, vel=vel, thermostat=1, skin=0.02, dt=0.002)
+    ctx.set_state_u(cat("u"), vel=cat("v"), step=0)
+    ctx.step(5)
+    ub, vb, _ = ctx.get_state_u()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for r, x in enumerate(reps):
+        c, _ = make_ctx(x, rb.FP32, rbe_P=50, seed=3 + r, replica=r, thermostat=1, skin=0.02,
+                        dt=0.002)
+        c.set_state_u(x.u, vel=x.v, step=0)
+        c.step(5)
+        u, v, _ = c.get_state_u()
+        assert torch.equal(u, ub[off[r]:off[r + 1]]) and torch.equal(v, vb[off[r]:off[r + 1]])
+        c.close()
+    ctx.close()
