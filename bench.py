@@ -60,7 +60,7 @@ OPS_PAIR = 22                  # r^2, rsqrt, erfc, exp, Coulomb, LJ, accumulate
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
@@ -436,8 +436,12 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    reb0 = ctx.candidate_rebuilds()
     ms, _ = time_steps(ctx, args.steps, args.warmup, flush, profile=False)
     clk = clocks.stop()
+    # rebuilds of the step's neighbour candidate lists inside the warm-up and timed
+    # steps (the timed mean includes them as they come)
+    rebuilds = ctx.candidate_rebuilds() - reb0
     kernels_per_step = ctx.step_kernel_count()
     total_ms = max_over_ranks(sum(ms), dist, device)
     if dist:
@@ -493,6 +497,8 @@ def run_ours(args):
         "gpu_launches": kernels_per_step * args.steps,
         "device_memory_bytes": int(footprint),
         "kernels_per_step": kernels_per_step,
+        "candidate_rebuilds": {"in_warmup_and_timed_steps": rebuilds,
+                               "steps": args.steps + args.warmup},
         "tiles": dict(tiles, names=["cell_div", "rho_tile", "rho_mode_tile", "pair_table"]),
     }
     if fp64:

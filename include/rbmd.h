@@ -324,7 +324,7 @@ rbmd_status rbmd_forces_host(rbmd_ctx *ctx, const void *pos, void *force, int64_
  * shell are summed in atom-id order and a drawn batch in priority order, so the
  * forces do not depend on when rebuilds happen (a resumed run stays
  * bit-identical), but they may differ from rbmd_rbl_forces in the last bits.  An
- * atom beyond the lists' capacities (a density fluctuation of over 4 standard
+ * atom beyond the lists' capacities (a density fluctuation of over 5 standard
  * deviations) is computed by the exact cell walk instead.
  */
 rbmd_status rbmd_step(rbmd_ctx *ctx, int64_t n_steps);

@@ -698,12 +698,11 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     }
     if (!c->verlet)
         for (int r = 0; r < R; ++r) c->reps_h[r].Rv = c->reps_h[r].Rlin;
-    // capacities: candidates mean + 5 sd + 8; the core and shell entries a thread
-    // keeps in shared memory mean + 5 sd + 4 (beyond them: the exact fallback)
+    // capacities: candidates mean + 5 sd + 8; the core members a thread keeps in
+    // shared memory mean + 5 sd + 4 (beyond them: the exact fallback)
     c->vl_cv = ((int)ceil(max_mv + 5.0 * sqrt(max_mv) + 8.0) + 3) / 4 * 4;
     c->vl_ccs = (int)ceil(max_mc + 5.0 * sqrt(max_mc) + 4.0);
-    c->vl_css = (int)ceil(max_ms + 5.0 * sqrt(max_ms) + 4.0);
-    if ((c->vl_ccs + c->vl_css) * 128 * 4 > 160 * 1024) c->verlet = false;
+    if (std::max(c->vl_ccs, p.rbl_p) * 128 * 4 > 160 * 1024) c->verlet = false;
     c->vl_dirty = true;
 
     // cell arrays and tile partials sized for every layout rbmd_set_tiles allows
@@ -735,7 +734,6 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
             c->list_cc = cc;
             c->list_cs = cs;
             c->vl_ccs = std::min(c->vl_ccs, cc);
-            c->vl_css = std::min(c->vl_css, cs);
         }
     }
 

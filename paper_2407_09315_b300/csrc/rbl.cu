@@ -17,6 +17,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "rbmd_internal.cuh"
 
 namespace rbmd {
@@ -536,6 +538,47 @@ __device__ __forceinline__ uint2 philox_rest(const Philox0 &r0, uint32_t id_j, u
     return make_uint2(c.x, c.y);  // priority = x << 32 | y
 }
 
+// Round keys of rounds 1-9 (the seed plus r Weyl increments), computed once per
+// atom for philox_rest4.
+struct PhiloxKeys {
+    uint2 k[9];
+};
+
+__device__ __forceinline__ PhiloxKeys philox_keys(uint2 key)
+{
+    PhiloxKeys K;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        key.x += 0x9E3779B9u;
+        key.y += 0xBB67AE85u;
+        K.k[r] = key;
+    }
+    return K;
+}
+
+// Four priorities at once (the same rounds as philox_rest, the four chains
+// interleaved so that their dependent multiplies overlap): pri[q] = (w0, w1) of
+// counter (id_i, id_j[q], step, tag).
+__device__ __forceinline__ void philox_rest4(const Philox0 &r0, const uint32_t (&id)[4],
+                                             const PhiloxKeys &K, uint2 (&pri)[4])
+{
+    uint4 c[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[q] = make_uint4(r0.x ^ id[q], r0.y, r0.z, r0.w);
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t h0, l0, h1, l1;
+            philox_mulhilo(0xD2511F53u, c[q].x, h0, l0);
+            philox_mulhilo(0xCD9E8D57u, c[q].z, h1, l1);
+            c[q] = make_uint4(h1 ^ c[q].y ^ K.k[r].x, l1, h0 ^ c[q].w ^ K.k[r].y, l0);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pri[q] = make_uint2(c[q].x, c[q].y);
+}
+
 // Bottom-p selection over (priority, id), in registers, keyed by the high 32
 // bits of the priority, as the overflow fallback kernel runs it (select_atom
 // uses packed keys and a min/max insertion instead).  The CAP slots hold a
@@ -697,6 +740,19 @@ __device__ __forceinline__ int classify(const Rep &a, const uint4 &A, const uint
     if (((uint32_t)dx + a.Rlin > R2x) | ((uint32_t)dy + a.Rlin > R2x) |
         ((uint32_t)dz + a.Rlin > R2x))
         return 0;
+    const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
+                       (uint64_t)((int64_t)dz * dz);
+    if (D > a.Rs2) return 0;
+    return D < a.Rc2 ? 1 : 2;
+}
+
+// classify for a pair known to lie within Rv < 2^31 units on every axis (a
+// candidate of the step's lists): no per-axis reject, the same result.
+__device__ __forceinline__ int classify_near(const Rep &a, const uint4 &A, const uint4 &B)
+{
+    const int32_t dx = (int32_t)(B.x - A.x);
+    const int32_t dy = (int32_t)(B.y - A.y);
+    const int32_t dz = (int32_t)(B.z - A.z);
     const uint64_t D = (uint64_t)((int64_t)dx * dx) + (uint64_t)((int64_t)dy * dy) +
                        (uint64_t)((int64_t)dz * dz);
     if (D > a.Rs2) return 0;
@@ -1543,8 +1599,10 @@ struct VlArgs {
     uint4 *sref;
     int32_t *flag;        // rebuild pending
     int32_t *nrebuild;
-    int cv, ccs, css;
+    int cv, ccs;
 };
+
+
 
 __device__ __forceinline__ int64_t vl_slot(int64_t is, int t, int cv)
 {
@@ -1626,15 +1684,57 @@ __device__ __forceinline__ void sort_strided(int32_t *v, int n, int s)
     }
 }
 
+// The exact batch of one atom from its candidates (full 64-bit priorities, ties
+// to the smaller id), for the rare atoms whose truncated keys tie: fills hk as
+// select_exact does (replica-local ids).
+template <int CAP>
+__device__ __noinline__ void vl_select_exact(const Philox0 &r0, uint2 key, const Rep &rp,
+                                             const uint4 A, const uint4 *spos, const int32_t *cl,
+                                             int n, uint32_t id0, int p, int (&hk)[CAP])
+{
+    uint64_t kk[CAP];
+    uint32_t kid[CAP];
+    int kept = 0;
+    for (int t = 0; t < n; ++t) {
+        const uint4 B = spos[cl[t * 32]];
+        if (classify_near(rp, A, B) != 2) continue;
+        const uint32_t id = B.w - id0;
+        const uint2 w = philox_rest(r0, id, key);
+        const uint64_t v = ((uint64_t)w.x << 32) | w.y;
+        int j;
+        if (kept == p) {
+            if (!(v < kk[p - 1] || (v == kk[p - 1] && id < kid[p - 1]))) continue;
+            j = p - 1;
+        } else {
+            j = kept;
+        }
+        while (j > 0 && (v < kk[j - 1] || (v == kk[j - 1] && id < kid[j - 1]))) {
+            kk[j] = kk[j - 1];
+            kid[j] = kid[j - 1];
+            --j;
+        }
+        kk[j] = v;
+        kid[j] = id;
+        if (kept < p) ++kept;
+    }
+    for (int e = 0; e < CAP; ++e) {
+        const int j = e - (CAP - p);
+        hk[e] = j < 0 ? SEL_NEG : (j < kept ? (int)kid[j] : SEL_POS);
+    }
+}
+
 // Algorithm 2 step 1 for the step: classification of the candidates, N_s, the
-// batch and the core list, one thread per sorted atom (128 per block).  The core
-// and shell members (replica-local atom ids) are kept in shared memory,
-// [ccs + css][128] int32 (the shell list never goes to device memory); the batch
-// is the bottom-p selection of select_atom over them.  Outputs: lcore and bk rows
-// (sorted indices) and ncount, read by k_rbl_force.  An atom beyond a capacity
-// is marked overflowed for the exact fallback.
+// batch and the core list, one thread per sorted atom (128 per block).  The shell
+// is never stored: the Philox priority of every candidate of a round is computed
+// with the round (four interleaved chains, used for the shell members only) and
+// the bottom-p keys of select_atom are kept in registers, keyed by the
+// candidate's position in the list, so a winner's sorted index is its candidate
+// entry.  Shared memory holds the core members' replica-local ids,
+// [max(ccs, p)][128] int32, put in id order.  Outputs: lcore and bk rows (sorted
+// indices) and ncount, read by k_rbl_force.  An atom beyond a capacity is marked
+// overflowed for the exact fallback.
 template <typename real, int CAP>
-__global__ void __launch_bounds__(128) k_rbl_vclass(PairArgs<real> a, VlArgs v)
+__global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
 {
     extern __shared__ int32_t s_vl[];
     const AtomSlot sl = atom_slot(a.map, a.reps);
@@ -1644,27 +1744,71 @@ __global__ void __launch_bounds__(128) k_rbl_vclass(PairArgs<real> a, VlArgs v)
     const uint4 A = a.spos[is];
     const uint32_t id0 = (uint32_t)rp.atom0;
     int32_t *s_core = s_vl + threadIdx.x;
-    int32_t *s_sh = s_vl + v.ccs * 128 + threadIdx.x;
     const int n = v.ncand[is];
+    const int32_t *cl = v.cand + vl_slot(is, 0, v.cv);
+    const Philox0 r0 = philox_round0(A.w - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key);
+    const PhiloxKeys K = philox_keys(rp.key);
+    const int b = 32 - __clz(v.cv);  // 2^b > cv > every candidate position
+    const uint32_t lo_mask = (1u << b) - 1u;
+    uint32_t keep = ~lo_mask;
+    if (a.sel_key_bits > 0 && a.sel_key_bits < 32) keep &= ~(0xFFFFFFFFu >> a.sel_key_bits);
+    uint32_t sk[CAP + 1];
+#pragma unroll
+    for (int e = 0; e <= CAP; ++e) sk[e] = 0xFFFFFFFFu;
     int nc = 0, ns = 0;
     if (n <= v.cv) {
-        const int32_t *cl = v.cand + vl_slot(is, 0, v.cv);
-        int kn = n > 0 ? cl[0] : 0;
-        for (int t = 0; t < n; ++t) {
-            const int k = kn;
-            if (t + 1 < n) kn = cl[(t + 1) * 32];
-            const uint4 B = a.spos[k];
-            const int cls = classify(rp, A, B);
-            if (cls == 1) {
-                if (nc < v.ccs) s_core[nc * 128] = (int32_t)(B.w - id0);
-                ++nc;
-            } else if (cls == 2) {
-                if (ns < v.css) s_sh[ns * 128] = (int32_t)(B.w - id0);
-                ++ns;
+        // four candidates per round: their positions are gathered one round
+        // ahead and their indices (one coalesced row of the warp each) two rounds
+        // ahead, so the gathers overlap the previous round's Philox work
+        constexpr int VB = 4;
+        int kk[VB];
+        uint4 Bn[VB];
+#pragma unroll
+        for (int q = 0; q < VB; ++q) {
+            const int k0 = q < n ? cl[q * 32] : -1;
+            Bn[q] = k0 >= 0 ? a.spos[k0] : A;
+            kk[q] = VB + q < n ? cl[(VB + q) * 32] : -1;
+        }
+        for (int t0 = 0; t0 < n; t0 += VB) {
+            uint4 B[VB];
+#pragma unroll
+            for (int q = 0; q < VB; ++q) {
+                B[q] = Bn[q];
+                Bn[q] = kk[q] >= 0 ? a.spos[kk[q]] : A;
+                kk[q] = t0 + 2 * VB + q < n ? cl[(t0 + 2 * VB + q) * 32] : -1;
+            }
+            bool sh[VB];
+            uint32_t ids[VB];
+#pragma unroll
+            for (int q = 0; q < VB; ++q) {
+                const int cls = t0 + q < n ? classify_near(rp, A, B[q]) : 0;
+                ids[q] = B[q].w - id0;
+                if (cls == 1) {
+                    if (nc < v.ccs) s_core[nc * 128] = (int32_t)ids[q];
+                    ++nc;
+                }
+                sh[q] = cls == 2;
+                ns += sh[q] ? 1 : 0;
+            }
+#pragma unroll
+            for (int h = 0; h < VB; h += 4) {
+                const uint32_t id4[4] = {ids[h], ids[h + 1], ids[h + 2], ids[h + 3]};
+                uint2 w[4];
+                philox_rest4(r0, id4, K, w);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t x = sh[h + q] ? (w[q].x & keep) | (uint32_t)(t0 + h + q) : 0xFFFFFFFFu;
+#pragma unroll
+                    for (int j = 0; j <= CAP; ++j) {
+                        const uint32_t m = min(sk[j], x);
+                        x = max(sk[j], x);
+                        sk[j] = m;
+                    }
+                }
             }
         }
     }
-    if (n > v.cv || nc > v.ccs || ns > v.css || nc > a.CC) {
+    if (n > v.cv || nc > v.ccs || nc > a.CC) {
         a.ncount[is] = make_int2(a.CC + 1, 0);
         *a.ovf = 1;
         return;
@@ -1675,29 +1819,13 @@ __global__ void __launch_bounds__(128) k_rbl_vclass(PairArgs<real> a, VlArgs v)
     for (int e = 0; e < nc; ++e) lc[e] = sidx[s_core[e * 128]];
     int32_t *bk = a.bk + is * a.p;
     if (ns <= a.p) {
-        sort_strided(s_sh, ns, 128);
-        for (int e = 0; e < ns; ++e) bk[e] = sidx[s_sh[e * 128]];
+        // the whole shell (its keys are all kept), in atom-id order
+#pragma unroll
+        for (int e = 0; e < CAP; ++e)
+            if (e < ns) s_core[e * 128] = (int32_t)(a.spos[cl[(sk[e] & lo_mask) * 32]].w - id0);
+        sort_strided(s_core, ns, 128);
+        for (int e = 0; e < ns; ++e) bk[e] = sidx[s_core[e * 128]];
     } else {
-        const Philox0 r0 = philox_round0(A.w - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key);
-        // packed keys as select_atom: the priority's high word with its low b bits
-        // replaced by the member's position (2^b > css), CAP + 1 smallest kept
-        const int b = 32 - __clz(v.css);
-        const uint32_t lo_mask = (1u << b) - 1u;
-        uint32_t keep = ~lo_mask;
-        if (a.sel_key_bits > 0 && a.sel_key_bits < 32) keep &= ~(0xFFFFFFFFu >> a.sel_key_bits);
-        uint32_t sk[CAP + 1];
-#pragma unroll
-        for (int e = 0; e <= CAP; ++e) sk[e] = 0xFFFFFFFFu;
-        for (int e = 0; e < ns; ++e) {
-            const uint2 w = philox_rest(r0, (uint32_t)s_sh[e * 128], rp.key);
-            uint32_t x = (w.x & keep) | (uint32_t)e;
-#pragma unroll
-            for (int j = 0; j <= CAP; ++j) {
-                const uint32_t m = min(sk[j], x);
-                x = max(sk[j], x);
-                sk[j] = m;
-            }
-        }
         bool tie = a.sel_exact != 0;
 #pragma unroll
         for (int e = 0; e < CAP; ++e)
@@ -1705,10 +1833,10 @@ __global__ void __launch_bounds__(128) k_rbl_vclass(PairArgs<real> a, VlArgs v)
         if (!tie) {
 #pragma unroll
             for (int e = 0; e < CAP; ++e)
-                if (e < a.p) bk[e] = sidx[s_sh[(sk[e] & lo_mask) * 128]];
+                if (e < a.p) bk[e] = cl[(sk[e] & lo_mask) * 32];
         } else {
             int hk[CAP];
-            select_exact<CAP>(r0, rp.key, s_sh, ns, a.p, hk, 128);
+            vl_select_exact<CAP>(r0, rp.key, rp, A, a.spos, cl, n, id0, a.p, hk);
             int nb = 0;
             for (int e = 0; e < CAP; ++e)
                 if (hk[e] >= 0) bk[nb++] = sidx[hk[e]];
@@ -1729,7 +1857,6 @@ static VlArgs vl_args(rbmd_ctx *c)
     v.nrebuild = c->ibuf + 5;
     v.cv = c->vl_cv;
     v.ccs = c->vl_ccs;
-    v.css = c->vl_css;
     return v;
 }
 
@@ -1756,7 +1883,10 @@ rbmd_status verlet_prepare(rbmd_ctx *c)
     return verlet_prepare_t<float>(c);
 }
 
-static size_t vl_smem(const rbmd_ctx *c) { return (size_t)(c->vl_ccs + c->vl_css) * 128 * sizeof(int32_t); }
+static size_t vl_smem(const rbmd_ctx *c)
+{
+    return (size_t)std::max(c->vl_ccs, c->prm.rbl_p) * 128 * sizeof(int32_t);
+}
 
 template <typename real, int CAP>
 static void launch_vl(rbmd_ctx *c, const PairArgs<real> &a, bool marks)
@@ -1766,7 +1896,7 @@ static void launch_vl(rbmd_ctx *c, const PairArgs<real> &a, bool marks)
     a128.nmap = c->nb128;
     const unsigned nbp = (unsigned)c->nb128;
     const unsigned nfb = (unsigned)min(c->nb128, 4 * 148);
-    k_rbl_vclass<real, CAP><<<nbp, 128, vl_smem(c), c->stream>>>(a128, vl_args<real>(c));
+    k_rbl_vsel<real, CAP><<<nbp, 128, vl_smem(c), c->stream>>>(a128, vl_args<real>(c));
     if (marks) {
         prof_mark(c, 3);
         prof_mark(c, 4);
@@ -1800,13 +1930,13 @@ rbmd_status verlet_configure(rbmd_ctx *c)
 {
     if (!c->verlet) return RBMD_OK;
     const int bytes = (int)vl_smem(c);
-    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vclass<float, 10>,
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vsel<float, 10>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vclass<float, 16>,
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vsel<float, 16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vclass<double, 10>,
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vsel<double, 10>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vclass<double, 16>,
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vsel<double, 16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     return RBMD_OK;
 }

@@ -267,7 +267,7 @@ struct rbmd_ctx {
     bool vl_dirty;        // the sorted layout changed outside the step: rebuild before the next
     double skin;
     int vl_cv;            // candidate capacity per atom
-    int vl_ccs, vl_css;   // core and shell entries per thread kept in shared memory
+    int vl_ccs;           // core members per thread kept in shared memory
     int32_t *vl_cand;     // [ceil(N/32)][vl_cv][32] sorted indices (entry t of atom i at
                           //  (i/32) cv 32 + 32 t + i%32: a warp's loads of entry t coalesce)
     int32_t *vl_ncand;    // [N] candidate count (> vl_cv: the atom takes the exact fallback)
