@@ -50,7 +50,7 @@ def test_two_streams_same_trajectory(sys5k, prec, thermostat, monkeypatch):
     assert torch.equal(u1, u2) and torch.equal(v1, v2)
     e1, e2 = one.energy(6), two.energy(6)
     for k in e1:
-        assert e1[k] == e2[k], k
+        assert np.array_equal(e1[k], e2[k]), k
     one.close()
     two.close()
 
