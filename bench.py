@@ -23,10 +23,15 @@ pass runs the stages one after another on one stream, so it is a little slower
 than the timed steps, where the RBE structure factors overlap the RBL kernels.
 `e2e` times the force step through the C ABI with host buffers
 (rbmd_forces_host): positions copied in from pinned host memory, forces copied
-back, every step, host wall clock per call.
+back, every step, host wall clock per call.  `fwd_bwd` times the forward energy
+and the backward gradients (positions, charges, eps, sigma) of one state, with
+the adjoint kernels' stage times and the dominant one's roofline.  The timed
+steps include the rebuilds of the step's neighbour candidate lists as they come
+(`candidate_rebuilds`).
 
---impl reference times the FP64 CPU oracle (the checker, run as it stands on
-the host cores) on a bounded sample of the same workload.
+`cpu_baseline` is the FP64 CPU oracle (the checker, as it stands) on a bounded
+sample of the workload, on every host core and on one; --impl reference times it
+on every host core, per step, on a bounded sample of the same workload.
 """
 import argparse
 import json
@@ -49,12 +54,15 @@ WORKLOAD = ["c3"]
 
 # Algorithmic FP32-pipe lane operations per unit of work (each elementary
 # function counted as one operation; FMA as one); the roofline's peak is one such
-# operation per lane per clock: 148 SMs x 128 lanes x 2032 MHz.
+# operation per lane per clock: SMs (read from the device) x 128 lanes x 2032 MHz.
 OPS_RHO_PER_ATOM_MODE = 8      # 3 phase IMAD, 1 convert, sin, cos, 2 FMA
 OPS_FORCE_PER_ATOM_MODE = 11   # 3 phase IMAD, 1 convert, sin, cos, 2 (g), 3 FMA
 OPS_CLASSIFY_PER_NEIGHBOUR = 7  # 3 sub, 3 IMAD, 1 compare
 OPS_PHILOX = 80                # 10 rounds x (2 mul.hi + 2 mul.lo + 4 xor/add)
 OPS_PAIR = 22                  # r^2, rsqrt, erfc, exp, Coulomb, LJ, accumulate
+OPS_RBE_ADJ_PER_ATOM_MODE = 13  # 3 phase IMAD, convert, sin, cos, 2 (g), 3 FMA (force), 2 (potential)
+OPS_RBL_ADJ_PER_PAIR = 40       # pair energy and force, eps and sigma derivatives, both atoms
+SM_COUNT = [148]                # replaced by the device's count when a GPU is present
 
 
 def parse():
@@ -70,6 +78,8 @@ def parse():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-fwd-bwd", action="store_true")
+    ap.add_argument("--fwd-bwd-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shapes (the run autotunes them otherwise)")
     ap.add_argument("--pair-table", action="store_true",
@@ -324,7 +334,7 @@ def roofline(stages_ms_per_step, system, peaks_clock_mhz):
     top = max(ops, key=lambda k: stages_ms_per_step.get(k, 0.0))
     t = stages_ms_per_step[top] * 1e-3
     clock = 2032.0 if not peaks_clock_mhz else peaks_clock_mhz
-    peak = 148 * 128 * clock * 1e6 / 1e12  # Top/s, one FP32 lane-op per lane per clock
+    peak = SM_COUNT[0] * 128 * clock * 1e6 / 1e12  # Top/s, one FP32 lane-op per lane per clock
     achieved = ops[top] / t / 1e12
     traffic = captured_traffic().get(top) if (N == 1_000_000 and WORKLOAD[0] == "c3") else None
     cap = captured_traffic() if (N == 1_000_000 and WORKLOAD[0] == "c3") else {}
@@ -337,9 +347,65 @@ def roofline(stages_ms_per_step, system, peaks_clock_mhz):
                         "ms_per_launch": round(ms, 4), "traffic": cap.get(k)}
     return {"bound": "alu", "kernel": top, "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "Top/s (FP32-pipe lane ops)", "frac": round(achieved / peak, 4),
-            "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2032 MHz",
+            "peak_source": "derived: %d SMs (device) x 128 FP32 lanes x %.0f MHz" % (SM_COUNT[0], clock),
             "traffic": traffic, "ms_per_launch": round(stages_ms_per_step[top], 4),
             "algorithmic_ops_per_launch": ops[top], "every_kernel": every}
+
+
+def fwd_bwd(ctx, system, K, W, flush, step, clock_mhz):
+    """Forward energy (rbmd_energy: RBE + RBL energies and virials, FP64 sums) plus
+    backward gradients (rbmd_energy_backward: dE/dr, dE/dq, dE/d eps, dE/d sigma)
+    of one state, timed with CUDA events around the two calls (each synchronises),
+    then a second pass with stage events for the per-kernel times."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        ctx.energy(step)
+        ctx.energy_backward(step)
+    torch.cuda.synchronize()
+    f_ms, b_ms = [], []
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ctx.energy(step)
+        e1.record(stream)
+        ctx.energy_backward(step)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        f_ms.append(e0.elapsed_time(e1))
+        b_ms.append(e1.elapsed_time(e2))
+    ctx.profile(True)
+    ctx.profile_read_grad(reset=True)
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        ctx.energy(step)
+        ctx.energy_backward(step)
+    fwd, bwd, calls = ctx.profile_read_grad(reset=True)
+    ctx.profile(False)
+    fwd = {k: round(v / max(calls[0], 1), 4) for k, v in fwd.items()}
+    bwd = {k: round(v / max(calls[1], 1), 4) for k, v in bwd.items()}
+    N, P, p = system.n, PARAMS["rbe_P"], PARAMS["rbl_p"]
+    core, shell = mean_lists(system)
+    ops = {"rbe_adjoint": N * P * OPS_RBE_ADJ_PER_ATOM_MODE,
+           "rbl_adjoint": N * OPS_RBL_ADJ_PER_PAIR * (core + min(shell, p))}
+    top = max(ops, key=lambda k: bwd.get(k, 0.0))
+    peak = SM_COUNT[0] * 128 * clock_mhz * 1e6 / 1e12
+    ach = ops[top] / (bwd[top] * 1e-3) / 1e12 if bwd.get(top) else None
+    fm, bm = sum(f_ms) / K, sum(b_ms) / K
+    return {"ms": round(fm + bm, 4), "forward_ms": round(fm, 4), "backward_ms": round(bm, 4),
+            "atom_steps_per_s": N / ((fm + bm) * 1e-3),
+            "what": "rbmd_energy + rbmd_energy_backward of one state (gradients w.r.t. "
+                    "positions, charges, eps and sigma), CUDA events around each call, L2 "
+                    "flushed before each pair",
+            "forward_stage_ms": fwd, "backward_stage_ms": bwd,
+            "roofline": {"bound": "alu", "kernel": top,
+                         "achieved": None if ach is None else round(ach, 3),
+                         "peak": round(peak, 3), "unit": "Top/s (FP32-pipe lane ops)",
+                         "frac": None if ach is None else round(ach / peak, 4),
+                         "algorithmic_ops_per_launch": ops[top],
+                         "ms_per_launch": bwd.get(top)}}
 
 
 def e2e_force_step(ctx, system, K, W, device):
@@ -390,16 +456,33 @@ def oracle_forces(systems, step):
                       step, replica=r if len(systems) > 1 else 0)
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(n_sample, seed, workload="c3"):
+    """The oracle's force evaluation on a sample of the workload, on every host core
+    (its per-atom and per-mode loops in OpenMP threads), and on one core."""
+    import oracle
     systems, n = oracle_sample(n_sample, seed, workload)
-    t0 = time.perf_counter()
-    oracle_forces(systems, 0)
-    t = time.perf_counter() - t0
+    cores = host_cores()
+    rates = {}
+    for th in sorted({cores, 1}, reverse=True):
+        oracle.set_threads(th)
+        t0 = time.perf_counter()
+        oracle_forces(systems, 0)
+        rates[th] = (n / (time.perf_counter() - t0), time.perf_counter() - t0)
+    oracle.set_threads(1)
     what = ("a %d-atom system" % n if not WORKLOADS[workload].get("replicas") else
             "the first %d replica(s) (%d atoms)" % (len(systems), n))
-    return {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one FP64 force evaluation (RBE + RBL + F_corr) of %s of the "
-                      "same recipe, single thread, %.1f s" % (what, t)}
+    return {"value": rates[cores][0], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one FP64 force evaluation (RBE + RBL + F_corr) of %s of the same "
+                      "recipe on %d host threads, %.1f s" % (what, cores, rates[cores][1]),
+            "single_core": {"value": rates[1][0], "unit": UNIT, "cores": 1,
+                            "seconds": round(rates[1][1], 2)}}
 
 
 def run_ours(args):
@@ -417,6 +500,7 @@ def run_ours(args):
     device = torch.device("cuda", local)
 
     WORKLOAD[0] = args.workload
+    SM_COUNT[0] = torch.cuda.get_device_properties(device).multi_processor_count
     system = make_system(args.n, 2 + rank, args.workload)
     args.n = system.n
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
@@ -453,6 +537,11 @@ def run_ours(args):
     ms_prof, stages = time_steps(ctx, args.steps, 2, flush, profile=True)
     ctx.profile(False)
     stage_ms = {k: v / args.steps for k, v in stages.items()}
+
+    fb = None
+    if not args.skip_fwd_bwd and system.R == 1:
+        fb = fwd_bwd(ctx, system, args.fwd_bwd_steps, 2, flush, 0,
+                     2032.0 if not clk else clk["sm_max_mhz"])
 
     e2e = None
     if not args.skip_e2e:
@@ -494,6 +583,7 @@ def run_ours(args):
                        "what": "second pass of K steps with CUDA events between the stages, "
                                "stages serialised on one stream"},
         "roofline": roofline(stage_ms, system, 2032.0),
+        "sm_count": SM_COUNT[0],
         "gpu_launches": kernels_per_step * args.steps,
         "device_memory_bytes": int(footprint),
         "kernels_per_step": kernels_per_step,
@@ -506,6 +596,8 @@ def run_ours(args):
         out["speedup_fp32_over_fp64"] = round(fp64["ms_per_step"] / ms_per_step, 2)
     if e2e:
         out["e2e"] = e2e
+    if fb:
+        out["fwd_bwd"] = fb
     if clk:
         out["clocks"] = clk
     out["paper_context"] = ("8.20 ms/step nonbonded at N=1e6 (SPC/E water, A100 + 1 CPU core); "
@@ -525,6 +617,8 @@ def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     n_sample = min(args.ref_sample, args.n) if args.n else args.ref_sample
     systems, n = oracle_sample(n_sample, 2, args.workload)
+    cores = host_cores()
+    oracle.set_threads(cores)
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -536,13 +630,13 @@ def run_reference(args):
     what = ("a %d-atom system" % n if not WORKLOADS[args.workload].get("replicas") else
             "the first %d replica(s) (%d atoms)" % (len(systems), n))
     sample = ("one FP64 force evaluation (RBE + RBL + F_corr) per step of %s of the "
-              "same recipe, single thread" % what)
+              "same recipe on %d host threads" % (what, cores))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded %s, paper-shaped recipe in synth.py)" % WORKLOADS[args.workload]["charges"].replace("none", "LJ fluid"),
            "config": workload_config(args, world),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

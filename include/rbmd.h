@@ -465,6 +465,23 @@ rbmd_status rbmd_profile_read(rbmd_ctx *ctx, double *ms, int64_t *steps, int res
 int32_t rbmd_step_kernel_count(rbmd_ctx *ctx);
 
 /*
+ * rbmd_profile_read_grad: while profiling is enabled, rbmd_energy and
+ * rbmd_energy_backward also record events between their stages; accumulated
+ * milliseconds (host double) and call counts (host int64 [2]: forward,
+ * backward; any pointer may be NULL); reset != 0 zeroes them.
+ *   forward [RBMD_PROFILE_FWD_STAGES]: 0 RBE sampling, structure factors and mode
+ *     energy/virial sums, 1 cell sort, 2 RBL lists, batches and pair
+ *     energies/virials, 3 FP64 sums and kinetic energy;
+ *   backward [RBMD_PROFILE_GRAD_STAGES]: 0 cell sort and complete lists, 1 RBE
+ *     sampling and structure factors, 2 output initialisation and the self
+ *     term, 3 RBL adjoint (pair gradients and per-type sums), 4 RBE adjoint.
+ */
+#define RBMD_PROFILE_FWD_STAGES 4
+#define RBMD_PROFILE_GRAD_STAGES 5
+rbmd_status rbmd_profile_read_grad(rbmd_ctx *ctx, double *fwd_ms, double *bwd_ms, int64_t *calls,
+                                   int reset);
+
+/*
  * rbmd_rbe_forces_noalloc -- the RBE force of rbmd_rbe_forces (same mode draws,
  * same structure factors and force pass, FP32 arithmetic) for callers that
  * cannot allocate device memory: code that runs while another framework owns

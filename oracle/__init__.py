@@ -60,8 +60,19 @@ def lib():
         L.orc_langevin_normals.argtypes = [u64, u32, i64, u32, P]
         L.orc_rbe_metropolis.argtypes = [u64, i64, u32, i32, dbl, dbl, i32, P]
         L.orc_metropolis_table.argtypes = [dbl, dbl, i32, P]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
         _lib = L
     return _lib
+
+
+def set_threads(n):
+    """Host threads of the oracle's per-atom and per-mode loops (1 by default)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads():
+    return int(lib().orc_get_threads())
 
 
 def _p(a):

@@ -19,7 +19,7 @@ def build(force: bool = False) -> str:
         return OUT
     tmp = OUT + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
+           "-fopenmp", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, OUT)
     return OUT

@@ -24,6 +24,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_TWO32 4294967296.0
 #define ORC_TWO64 18446744073709551616.0
@@ -35,6 +38,24 @@
 #define ORC_STREAM_LANGEVIN 3u
 #define ORC_STREAM_METROPOLIS 4u
 #define ORC_MAX_ATTEMPTS 256
+
+/* Host threads of the per-mode and per-atom loops (1 unless orc_set_threads
+ * raises it; every element is computed by the same operations in the same
+ * order whatever the count, only the order of the RBL sums over atoms changes). */
+static int orc_threads = 1;
+
+void orc_set_threads(int n) { orc_threads = n > 0 ? n : 1; }
+
+int orc_get_threads(void) { return orc_threads; }
+
+static int orc_thread_id(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (SC'11, Sec. 3): 10 rounds of two 32x32->64 multiplies with  */
@@ -202,6 +223,7 @@ void orc_structure_factor(int64_t n, const uint32_t *u, const double *q, double 
 {
     double *x = (double *)malloc(sizeof(double) * (size_t)(3 * n));
     orc_decode(n, u, L, x);
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
     for (int64_t l = 0; l < nm; ++l) {
         double kx = 2.0 * ORC_PI * m[3 * l + 0] / L;
         double ky = 2.0 * ORC_PI * m[3 * l + 1] / L;
@@ -241,7 +263,6 @@ void orc_mode_forces(int64_t n, const uint32_t *u, const double *q, double L,
     orc_decode(n, u, L, x);
     orc_structure_factor(n, u, q, L, nm, m, rho);
     int64_t ns = sel ? n_sel : n;
-    for (int64_t s = 0; s < 3 * ns; ++s) F_out[s] = 0.0;
     double E = 0.0;
     for (int64_t l = 0; l < nm; ++l) {
         double kx = 2.0 * ORC_PI * m[3 * l + 0] / L;
@@ -251,16 +272,30 @@ void orc_mode_forces(int64_t n, const uint32_t *u, const double *q, double L,
         if (k2 == 0.0) continue; /* exhausted sample: zero weight */
         double re = rho[2 * l], im = rho[2 * l + 1];
         E += coulomb_k * W[l] * (2.0 * ORC_PI / V) * (re * re + im * im) / k2;
-        for (int64_t s = 0; s < ns; ++s) {
-            int64_t i = sel ? sel[s] : s;
+    }
+    /* every atom sums its modes in mode order */
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+    for (int64_t s = 0; s < ns; ++s) {
+        int64_t i = sel ? sel[s] : s;
+        double f[3] = {0.0, 0.0, 0.0};
+        for (int64_t l = 0; l < nm; ++l) {
+            double kx = 2.0 * ORC_PI * m[3 * l + 0] / L;
+            double ky = 2.0 * ORC_PI * m[3 * l + 1] / L;
+            double kz = 2.0 * ORC_PI * m[3 * l + 2] / L;
+            double k2 = kx * kx + ky * ky + kz * kz;
+            if (k2 == 0.0) continue;
+            double re = rho[2 * l], im = rho[2 * l + 1];
             double th = kx * x[3 * i] + ky * x[3 * i + 1] + kz * x[3 * i + 2];
             /* Im(e^{-i th} (re + i im)) = im cos th - re sin th */
             double imag = im * cos(th) - re * sin(th);
             double c = -coulomb_k * W[l] * 4.0 * ORC_PI * q[i] / (V * k2) * imag;
-            F_out[3 * s + 0] += c * kx;
-            F_out[3 * s + 1] += c * ky;
-            F_out[3 * s + 2] += c * kz;
+            f[0] += c * kx;
+            f[1] += c * ky;
+            f[2] += c * kz;
         }
+        F_out[3 * s + 0] = f[0];
+        F_out[3 * s + 1] = f[1];
+        F_out[3 * s + 2] = f[2];
     }
     if (E_out) *E_out = E;
     if (rho_out) memcpy(rho_out, rho, sizeof(double) * (size_t)(2 * nm));
@@ -712,13 +747,12 @@ void orc_rbl(int64_t n, const uint32_t *u, const double *q, const int32_t *type,
     if (use_cells) orc_build_cells(&S);
     double *x = (double *)malloc(sizeof(double) * (size_t)(3 * (n > 0 ? n : 1)));
     orc_decode(n, u, L, x);
-    orc_list cand = {0}, core = {0}, shell = {0};
-    int64_t cap_b = 16;
-    int64_t *bt = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap_b);
 
-    /* per-atom evaluation */
-    double Fs[3] = {0, 0, 0}, Ec = 0.0, El = 0.0;
-    double Wc[6] = {0, 0, 0, 0, 0, 0}, Wl[6] = {0, 0, 0, 0, 0, 0};
+    /* per-atom evaluation; the sums over atoms are kept per thread (atoms in
+     * contiguous static chunks) and added in thread order */
+    enum { ACC_F = 0, ACC_EC = 3, ACC_EL = 4, ACC_WC = 5, ACC_WL = 11, ACC_N = 17 };
+    const int nth = orc_threads;
+    double *acc_all = (double *)calloc((size_t)nth * ACC_N, sizeof(double));
     int64_t ns = sel ? n_sel : n;
     int64_t nloop = want_all ? n : ns;
     /* map atom -> selected slot when both are needed */
@@ -728,53 +762,66 @@ void orc_rbl(int64_t n, const uint32_t *u, const double *q, const int32_t *type,
         for (int64_t i = 0; i < n; ++i) slot[i] = -1;
         for (int64_t s = 0; s < n_sel; ++s) slot[sel[s]] = s;
     }
-    for (int64_t it = 0; it < nloop; ++it) {
-        int64_t i, s;
-        if (want_all) { i = it; s = sel ? slot[i] : i; }
-        else { s = it; i = sel ? sel[it] : it; }
-        orc_candidates(&S, i, &cand);
-        if (cand.count > cap_b) {
-            cap_b = cand.count;
-            bt = (int64_t *)realloc(bt, sizeof(int64_t) * (size_t)cap_b);
-        }
-        int32_t nb = 0;
-        double w = orc_rbl_lists(&S, i, &cand, &core, &shell, bt, &nb);
-        double Fi[3] = {0, 0, 0}, ec, el, f[3], r3[3], gp[2];
-        for (int64_t k = 0; k < core.count; ++k) {
-            orc_pair(&S, x, i, core.ids[k], &ec, &el, f, r3, gp);
-            Ec += 0.5 * ec; El += 0.5 * el;
-            orc_add_virial(Wc, 0.5, r3, gp[0]);
-            orc_add_virial(Wl, 0.5, r3, gp[1]);
-            for (int d = 0; d < 3; ++d) Fi[d] += f[d];
-        }
-        double Fb[3] = {0, 0, 0};
-        for (int k = 0; k < nb; ++k) {
-            orc_pair(&S, x, i, bt[k], &ec, &el, f, r3, gp);
-            Ec += 0.5 * w * ec; El += 0.5 * w * el;
-            orc_add_virial(Wc, 0.5 * w, r3, gp[0]);
-            orc_add_virial(Wl, 0.5 * w, r3, gp[1]);
-            for (int d = 0; d < 3; ++d) Fb[d] += f[d];
-        }
-        for (int d = 0; d < 3; ++d) Fi[d] += w * Fb[d];
-        for (int d = 0; d < 3; ++d) Fs[d] += Fi[d];
-        if (s >= 0) {
-            if (F_out) for (int d = 0; d < 3; ++d) F_out[3 * s + d] = Fi[d];
-            if (n_core) n_core[s] = (int32_t)core.count;
-            if (n_shell) n_shell[s] = (int32_t)shell.count;
-            if (n_batch) n_batch[s] = nb;
-            if (batch) {
-                for (int k = 0; k < p; ++k) batch[(int64_t)p * s + k] = (k < nb) ? bt[k] : -1;
+#pragma omp parallel num_threads(nth)
+    {
+        double *acc = acc_all + (size_t)orc_thread_id() * ACC_N;
+        orc_list cand = {0}, core = {0}, shell = {0};
+        int64_t cap_b = 16;
+        int64_t *bt = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap_b);
+#pragma omp for schedule(static)
+        for (int64_t it = 0; it < nloop; ++it) {
+            int64_t i, s;
+            if (want_all) { i = it; s = sel ? slot[i] : i; }
+            else { s = it; i = sel ? sel[it] : it; }
+            orc_candidates(&S, i, &cand);
+            if (cand.count > cap_b) {
+                cap_b = cand.count;
+                bt = (int64_t *)realloc(bt, sizeof(int64_t) * (size_t)cap_b);
+            }
+            int32_t nb = 0;
+            double w = orc_rbl_lists(&S, i, &cand, &core, &shell, bt, &nb);
+            double Fi[3] = {0, 0, 0}, ec, el, f[3], r3[3], gp[2];
+            for (int64_t k = 0; k < core.count; ++k) {
+                orc_pair(&S, x, i, core.ids[k], &ec, &el, f, r3, gp);
+                acc[ACC_EC] += 0.5 * ec; acc[ACC_EL] += 0.5 * el;
+                orc_add_virial(acc + ACC_WC, 0.5, r3, gp[0]);
+                orc_add_virial(acc + ACC_WL, 0.5, r3, gp[1]);
+                for (int d = 0; d < 3; ++d) Fi[d] += f[d];
+            }
+            double Fb[3] = {0, 0, 0};
+            for (int k = 0; k < nb; ++k) {
+                orc_pair(&S, x, i, bt[k], &ec, &el, f, r3, gp);
+                acc[ACC_EC] += 0.5 * w * ec; acc[ACC_EL] += 0.5 * w * el;
+                orc_add_virial(acc + ACC_WC, 0.5 * w, r3, gp[0]);
+                orc_add_virial(acc + ACC_WL, 0.5 * w, r3, gp[1]);
+                for (int d = 0; d < 3; ++d) Fb[d] += f[d];
+            }
+            for (int d = 0; d < 3; ++d) Fi[d] += w * Fb[d];
+            for (int d = 0; d < 3; ++d) acc[ACC_F + d] += Fi[d];
+            if (s >= 0) {
+                if (F_out) for (int d = 0; d < 3; ++d) F_out[3 * s + d] = Fi[d];
+                if (n_core) n_core[s] = (int32_t)core.count;
+                if (n_shell) n_shell[s] = (int32_t)shell.count;
+                if (n_batch) n_batch[s] = nb;
+                if (batch) {
+                    for (int k = 0; k < p; ++k) batch[(int64_t)p * s + k] = (k < nb) ? bt[k] : -1;
+                }
             }
         }
+        free(bt);
+        free(cand.ids); free(core.ids); free(shell.ids);
     }
-    if (Fsum_out) for (int d = 0; d < 3; ++d) Fsum_out[d] = Fs[d];
-    if (E_coul_out) *E_coul_out = Ec;
-    if (E_lj_out) *E_lj_out = El;
-    if (W_coul_out) for (int c = 0; c < 6; ++c) W_coul_out[c] = Wc[c];
-    if (W_lj_out) for (int c = 0; c < 6; ++c) W_lj_out[c] = Wl[c];
+    double tot[ACC_N];
+    for (int c = 0; c < ACC_N; ++c) tot[c] = 0.0;
+    for (int t = 0; t < nth; ++t)
+        for (int c = 0; c < ACC_N; ++c) tot[c] += acc_all[(size_t)t * ACC_N + c];
+    free(acc_all);
+    if (Fsum_out) for (int d = 0; d < 3; ++d) Fsum_out[d] = tot[ACC_F + d];
+    if (E_coul_out) *E_coul_out = tot[ACC_EC];
+    if (E_lj_out) *E_lj_out = tot[ACC_EL];
+    if (W_coul_out) for (int c = 0; c < 6; ++c) W_coul_out[c] = tot[ACC_WC + c];
+    if (W_lj_out) for (int c = 0; c < 6; ++c) W_lj_out[c] = tot[ACC_WL + c];
     free(slot);
-    free(bt);
-    free(cand.ids); free(core.ids); free(shell.ids);
     free(x);
     free(S.cell_start);
     free(S.cell_atoms);

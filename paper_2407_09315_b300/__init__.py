@@ -105,6 +105,7 @@ def lib():
         "rbmd_profile": ([P, C.c_int], C.c_int),
         "rbmd_profile_read": ([P, P, C.POINTER(i64), C.c_int], C.c_int),
         "rbmd_step_kernel_count": ([P], i32),
+        "rbmd_profile_read_grad": ([P, P, P, P, C.c_int], C.c_int),
         "rbmd_set_charges": ([P, P], C.c_int),
         "rbmd_set_lj": ([P, P, P], C.c_int),
         "rbmd_rbe_forces_noalloc": ([P, P, i64, dbl, dbl, dbl, i32, C.c_uint64, i64, C.c_uint32,
@@ -427,6 +428,20 @@ class RBMD:
         n = C.c_int64(0)
         _check(lib().rbmd_profile_read(self._h, _ptr(ms), C.byref(n), int(reset)), "profile_read")
         return dict(zip(self.PROFILE_STAGES, ms.tolist())), n.value
+
+    FWD_STAGES = ("rbe", "cell_sort", "rbl_pairs", "sums")
+    BWD_STAGES = ("lists", "rbe_rho", "init", "rbl_adjoint", "rbe_adjoint")
+
+    def profile_read_grad(self, reset=False):
+        """Accumulated stage times (ms) of rbmd_energy and rbmd_energy_backward while
+        profiling: (forward dict, backward dict, (forward calls, backward calls))."""
+        f = np.zeros(len(self.FWD_STAGES))
+        b = np.zeros(len(self.BWD_STAGES))
+        n = np.zeros(2, dtype=np.int64)
+        _check(lib().rbmd_profile_read_grad(self._h, _ptr(f), _ptr(b), _ptr(n), int(reset)),
+               "profile_read_grad")
+        return (dict(zip(self.FWD_STAGES, f.tolist())), dict(zip(self.BWD_STAGES, b.tolist())),
+                (int(n[0]), int(n[1])))
 
     def set_tiles(self, cell_div, rho_tile, rho_mode_tile):
         _check(lib().rbmd_set_tiles(self._h, cell_div, rho_tile, rho_mode_tile), "set_tiles")

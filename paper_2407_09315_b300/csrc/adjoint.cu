@@ -214,8 +214,10 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
 {
     const unsigned nb = (unsigned)((c->N + 255) / 256);
     const double gself = -2.0 * g * c->prm.coulomb_k * sqrt(c->prm.alpha / kPi);
+    gprof_mark(c, 2);
     k_adj_init<real><<<nb, 256, 0, c->stream>>>((real *)dpos, (real *)dq, c->u4, c->q64, c->N, gself);
     RBMD_LAUNCH_CHECK();
+    gprof_mark(c, 3);
     if (!(c->prm.flags & RBMD_NO_RBL)) {
         AdjArgs<real> a;
         a.reps = c->reps;
@@ -251,6 +253,7 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
     } else {
         RBMD_CHECK_CUDA(cudaMemsetAsync(tsum_dev, 0, sizeof(double) * 2 * c->T, c->stream));
     }
+    gprof_mark(c, 4);
     if (!(c->prm.flags & RBMD_NO_RBE)) {
         if constexpr (sizeof(real) == 4)
             k_rbe_adjoint<float, 256><<<c->nb256, 256, 0, c->stream>>>(

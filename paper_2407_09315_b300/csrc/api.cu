@@ -253,6 +253,8 @@ void free_ctx(rbmd_ctx *c)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
         if (c->prof_ev[k]) cudaEventDestroy(c->prof_ev[k]);
+    for (int k = 0; k <= RBMD_PROFILE_GRAD_STAGES; ++k)
+        if (c->gprof_ev[k]) cudaEventDestroy(c->gprof_ev[k]);
     delete[] c->reps_h;
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -1118,6 +1120,26 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
     return leave(c, RBMD_OK);
 }
 
+// Adds the stage times of the last profiled forward (which = 0, nst stages) or
+// backward (which = 1) call, once its work has finished.
+static void gprof_collect(rbmd_ctx *c, int which, int nst)
+{
+    if (!c->profiling || !c->gprof_ev[0]) return;
+    if (cudaEventSynchronize(c->gprof_ev[nst]) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    double *acc = which == 0 ? c->gprof_fwd : c->gprof_bwd;
+    for (int k = 0; k < nst; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->gprof_ev[k], c->gprof_ev[k + 1]) == cudaSuccess)
+            acc[k] += ms;
+        else
+            cudaGetLastError();
+    }
+    ++c->gprof_calls[which];
+}
+
 rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
 {
     if (!c || !out) return RBMD_ERR_INVALID;
@@ -1130,6 +1152,7 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
     k_zero_slots<<<(R * 6 + 255) / 256, 256, 0, c->stream>>>(c->scal, R, SCAL_FSUM, 6);
     k_zero_slots<<<(R * (SCAL_COUNT - SCAL_EPAIR) + 255) / 256, 256, 0, c->stream>>>(
         c->scal, R, SCAL_EPAIR, SCAL_COUNT - SCAL_EPAIR);
+    gprof_mark(c, 0);
     if (!(c->prm.flags & RBMD_NO_RBE)) {
         s = rbe_sample(c, r);
         if (s == RBMD_OK) s = rbe_structure_factors(c);
@@ -1139,10 +1162,13 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
             s = cuda_status(cudaPeekAtLastError());
         }
     }
+    gprof_mark(c, 1);
     if (s == RBMD_OK && !(c->prm.flags & RBMD_NO_RBL)) {
         s = cells_build(c);
+        gprof_mark(c, 2);
         if (s == RBMD_OK)
             s = rbl_pairs(c, r, c->scratch_force, 0, true, nullptr, nullptr, nullptr);
+        gprof_mark(c, 3);
         if (s == RBMD_OK) s = md_sum_replicas(c, c->fpart, 3, SCAL_FSUM, 1.0, false, true);
         if (s == RBMD_OK) s = md_sum_replicas(c, c->epart, EPART, SCAL_EPAIR, 1.0, false, true);
         if (s == RBMD_OK) {
@@ -1150,7 +1176,12 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
                 c->cell_count, c->ncell, c->ibuf + 1);
         }
     }
+    else {
+        gprof_mark(c, 2);
+        gprof_mark(c, 3);
+    }
     if (s == RBMD_OK) s = md_kinetic(c, SCAL_KE_TRUE);
+    gprof_mark(c, 4);
     std::vector<double> h((size_t)R * SCAL_COUNT);
     int32_t hi[4];
     if (s == RBMD_OK)
@@ -1159,6 +1190,7 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
     if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
     s = leave(c, s);
     if (s != RBMD_OK) return s;
+    gprof_collect(c, 0, RBMD_PROFILE_FWD_STAGES);
     RBMD_CHECK(check_latched(c));
     for (int q = 0; q < R; ++q) {
         const double *hr = h.data() + (size_t)q * SCAL_COUNT;
@@ -1334,6 +1366,7 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
     enter(c);
     StepRef r{nullptr, step};
     rbmd_status s = RBMD_OK;
+    gprof_mark(c, 0);
     if (!(c->prm.flags & RBMD_NO_RBL)) {
         // complete lists of the step: grow the capacities until nothing overflows
         for (int attempt = 0; attempt < 8; ++attempt) {
@@ -1367,12 +1400,14 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
             }
         }
     }
+    gprof_mark(c, 1);
     if (!(c->prm.flags & RBMD_NO_RBE)) {
         s = rbe_sample(c, r);
         if (s == RBMD_OK) s = rbe_structure_factors(c);
         if (s != RBMD_OK) return leave(c, s);
     }
-    s = adjoint_run(c, grad_out, d_pos, d_q, c->adj_tsum);
+    s = adjoint_run(c, grad_out, d_pos, d_q, c->adj_tsum);  // marks stages 2-4
+    gprof_mark(c, 5);
     if (s == RBMD_OK && (d_eps || d_sigma)) {
         std::vector<double> h(2 * c->T);
         s = cuda_status(cudaMemcpyAsync(h.data(), c->adj_tsum, sizeof(double) * 2 * c->T,
@@ -1384,7 +1419,9 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
                 if (d_sigma) d_sigma[t] = h[c->T + t];
             }
     }
-    return leave(c, s);
+    s = leave(c, s);
+    if (s == RBMD_OK) gprof_collect(c, 1, RBMD_PROFILE_GRAD_STAGES);
+    return s;
 }
 
 rbmd_status rbmd_set_charges(rbmd_ctx *c, const void *charge)
@@ -1570,11 +1607,32 @@ rbmd_status rbmd_profile(rbmd_ctx *c, int enable)
     if (on && !c->prof_ev[0])
         for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
             RBMD_CHECK_CUDA(cudaEventCreate(&c->prof_ev[k]));
+    if (on && !c->gprof_ev[0])
+        for (int k = 0; k <= RBMD_PROFILE_GRAD_STAGES; ++k)
+            RBMD_CHECK_CUDA(cudaEventCreate(&c->gprof_ev[k]));
     if (on != c->profiling) {
         RBMD_CHECK_CUDA(cudaStreamSynchronize(c->stream));
         if (c->graph_ready) cudaGraphExecDestroy(c->graph);
         c->graph_ready = false;  // re-captured with (or without) the stage events
         c->profiling = on;
+    }
+    return RBMD_OK;
+}
+
+rbmd_status rbmd_profile_read_grad(rbmd_ctx *c, double *fwd_ms, double *bwd_ms, int64_t *calls,
+                                   int reset)
+{
+    if (!c) return RBMD_ERR_INVALID;
+    for (int k = 0; k < RBMD_PROFILE_FWD_STAGES && fwd_ms; ++k) fwd_ms[k] = c->gprof_fwd[k];
+    for (int k = 0; k < RBMD_PROFILE_GRAD_STAGES && bwd_ms; ++k) bwd_ms[k] = c->gprof_bwd[k];
+    if (calls) {
+        calls[0] = c->gprof_calls[0];
+        calls[1] = c->gprof_calls[1];
+    }
+    if (reset) {
+        for (int k = 0; k < RBMD_PROFILE_FWD_STAGES; ++k) c->gprof_fwd[k] = 0.0;
+        for (int k = 0; k < RBMD_PROFILE_GRAD_STAGES; ++k) c->gprof_bwd[k] = 0.0;
+        c->gprof_calls[0] = c->gprof_calls[1] = 0;
     }
     return RBMD_OK;
 }

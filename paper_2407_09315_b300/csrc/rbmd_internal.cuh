@@ -287,6 +287,11 @@ struct rbmd_ctx {
     cudaEvent_t prof_ev[RBMD_PROFILE_STAGES + 1];
     double prof_ms[RBMD_PROFILE_STAGES];
     int64_t prof_steps;
+    // stages of rbmd_energy (forward) and rbmd_energy_backward while profiling
+    cudaEvent_t gprof_ev[RBMD_PROFILE_GRAD_STAGES + 1];
+    double gprof_fwd[RBMD_PROFILE_FWD_STAGES];
+    double gprof_bwd[RBMD_PROFILE_GRAD_STAGES];
+    int64_t gprof_calls[2];
 };
 
 // FP64 scalar slots in ctx->scal
@@ -314,6 +319,13 @@ enum {
 constexpr int EPART = 10;
 
 namespace rbmd {
+
+// Records the event that opens stage `k` of rbmd_energy or rbmd_energy_backward
+// (profiling only; eager launches).
+inline void gprof_mark(rbmd_ctx *c, int k)
+{
+    if (c->profiling && c->gprof_ev[0]) cudaEventRecord(c->gprof_ev[k], c->stream);
+}
 
 // Records the event that opens stage `k` of the step (profiling only).
 inline void prof_mark(rbmd_ctx *c, int k)
