@@ -62,14 +62,60 @@ __device__ __forceinline__ double sqrt_a(double x) { return sqrt(x); }
 
 constexpr int ADJ_BLOCK = 128;
 
+// true if sorted index x is one of the n entries of a batch row (p entries,
+// rows of an even length are read 8 bytes at a time)
+__device__ __forceinline__ bool in_batch_row(const int32_t *row, int n, int p, int32_t x)
+{
+    bool hit = false;
+    if ((p & 1) == 0) {
+        const int2 *r2 = reinterpret_cast<const int2 *>(row);
+        for (int b = 0; b < n; b += 2) {
+            const int2 v = r2[b >> 1];
+            hit |= v.x == x;
+            hit |= (b + 1 < n) & (v.y == x);
+        }
+    } else {
+        for (int b = 0; b < n; ++b) hit |= row[b] == x;
+    }
+    return hit;
+}
+
+// acc[t] += v for a run-time type t < TT: TT <= 8 keeps the accumulators in
+// registers (an unrolled select), larger TT index an array.
+template <int TT>
+__device__ __forceinline__ void acc_add(double (&acc)[2 * TT], int t, double v)
+{
+    if constexpr (TT <= 8) {
+#pragma unroll
+        for (int u = 0; u < 2 * TT; ++u)
+            if (u == t) acc[u] += v;
+    } else {
+        acc[t] += v;
+    }
+}
+
 // One thread per cell-sorted atom k.  Symmetric weights for dE/dr and dE/dq;
 // one-sided weights W_kj for the type sums (each ordered pair counted once).
-template <typename real>
+// TT >= the number of LJ types.
+template <typename real, int TT>
 __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
 {
-    __shared__ double s_t[2 * RBMD_MAX_TYPES][ADJ_BLOCK / 32];
-    double acc[2 * RBMD_MAX_TYPES];
-    for (int t = 0; t < 2 * a.T; ++t) acc[t] = 0.0;
+    __shared__ double s_t[2 * TT][ADJ_BLOCK / 32];
+    // type-pair factors of the eps and sigma derivatives (Eq. 4), TT <= 16:
+    // [tk TT + tj] = 1/2 sqrt(eps_j / eps_k) and 1 / sigma_kj
+    constexpr int TP = TT <= 16 ? TT * TT : 1;
+    __shared__ double s_er[TP], s_is[TP];
+    if constexpr (TT <= 16) {
+        for (int u = threadIdx.x; u < a.T * a.T; u += blockDim.x) {
+            const int t1 = u / a.T, t2 = u % a.T;
+            s_er[t1 * TT + t2] = 0.5 * sqrt((double)a.eps[t2] / (double)a.eps[t1]);
+            s_is[t1 * TT + t2] = 1.0 / (0.5 * ((double)a.sig[t1] + (double)a.sig[t2]));
+        }
+        __syncthreads();
+    }
+    double acc[2 * TT];
+#pragma unroll
+    for (int t = 0; t < 2 * TT; ++t) acc[t] = 0.0;
     const AtomSlot sl = atom_slot(a.map, a.reps);
     const int64_t ks = sl.i;
     if (sl.ok) {
@@ -90,14 +136,12 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
                                 : a.sidx[id0 + (uint32_t)a.lshell[lidx(ks, e - cnt.x, N, a.CS)]];
             real Wkj = 1, Wjk = 1;
             if (!core && !a.exact) {
-                Wkj = 0;
-                for (int b = 0; b < nbk; ++b)
-                    if (a.bk[lidx(ks, b, N, a.p)] == js) Wkj = wk;
+                Wkj = in_batch_row(a.bk + lidx(ks, 0, N, a.p), nbk, a.p, js) ? wk : (real)0;
                 const int2 cj = a.ncount[js];
                 const int nbj = min(cj.y, a.p);
-                Wjk = 0;
-                for (int b = 0; b < nbj; ++b)
-                    if (a.bk[lidx(js, b, N, a.p)] == (int32_t)ks) Wjk = cj.y > a.p ? (real)cj.y / (real)a.p : (real)1;
+                Wjk = in_batch_row(a.bk + lidx(js, 0, N, a.p), nbj, a.p, (int32_t)ks)
+                          ? (cj.y > a.p ? (real)cj.y / (real)a.p : (real)1)
+                          : (real)0;
             }
             const real W = (real)0.5 * (Wkj + Wjk);
             if (W == (real)0 && Wkj == (real)0) continue;
@@ -128,11 +172,21 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
                 // one-sided: 1/2 W_kj du/d eps_kj d eps_kj/d eps_t (Eq. 4), same for sigma
                 const double hw = 0.5 * (double)Wkj;
                 const double due = 4.0 * ((double)s12 - (double)s6);
-                const double dus = 4.0 * (double)eij * (12.0 * (double)s12 - 6.0 * (double)s6) / (double)sij;
-                acc[tk] += hw * due * 0.5 * sqrt((double)a.eps[tj] / (double)a.eps[tk]);
-                acc[tj] += hw * due * 0.5 * sqrt((double)a.eps[tk] / (double)a.eps[tj]);
-                acc[a.T + tk] += hw * dus * 0.5;
-                acc[a.T + tj] += hw * dus * 0.5;
+                double dus = 4.0 * (double)eij * (12.0 * (double)s12 - 6.0 * (double)s6);
+                double rkj, rjk;
+                if constexpr (TT <= 16) {
+                    dus *= s_is[tk * TT + tj];
+                    rkj = s_er[tk * TT + tj];
+                    rjk = s_er[tj * TT + tk];
+                } else {
+                    dus /= (double)sij;
+                    rkj = 0.5 * sqrt((double)a.eps[tj] / (double)a.eps[tk]);
+                    rjk = 0.5 * sqrt((double)a.eps[tk] / (double)a.eps[tj]);
+                }
+                acc_add<TT>(acc, tk, hw * due * rkj);
+                acc_add<TT>(acc, tj, hw * due * rjk);
+                acc_add<TT>(acc, TT + tk, hw * dus * 0.5);
+                acc_add<TT>(acc, TT + tj, hw * dus * 0.5);
             }
         }
         const int64_t id = A.w;
@@ -143,17 +197,20 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
         }
         if (a.dq) a.dq[id] += (real)a.g * gq;
     }
-    // per-type block partials, fixed order
+    // per-type block partials, fixed order (eps of type t at acc[t], sigma at acc[TT + t])
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int t = 0; t < 2 * a.T; ++t) {
+#pragma unroll
+    for (int t = 0; t < 2 * TT; ++t) {
+        if ((t % TT) >= a.T) continue;
         double v = acc[t] * a.g;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) s_t[t][warp] = v;
     }
     __syncthreads();
     if (threadIdx.x < 2 * a.T) {
+        const int t = threadIdx.x < a.T ? threadIdx.x : TT + threadIdx.x - a.T;
         double v = 0.0;
-        for (int w = 0; w < ADJ_BLOCK / 32; ++w) v += s_t[threadIdx.x][w];
+        for (int w = 0; w < ADJ_BLOCK / 32; ++w) v += s_t[t][w];
         a.tpart[(int64_t)blockIdx.x * 2 * a.T + threadIdx.x] = v;
     }
 }
@@ -247,7 +304,9 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
         a.dq = (real *)dq;
         a.tpart = c->adj_tpart;
         const unsigned nba = (unsigned)c->nb128;
-        k_rbl_adjoint<real><<<nba, ADJ_BLOCK, 0, c->stream>>>(a);
+        if (c->T <= 4) k_rbl_adjoint<real, 4><<<nba, ADJ_BLOCK, 0, c->stream>>>(a);
+        else if (c->T <= 16) k_rbl_adjoint<real, 16><<<nba, ADJ_BLOCK, 0, c->stream>>>(a);
+        else k_rbl_adjoint<real, RBMD_MAX_TYPES><<<nba, ADJ_BLOCK, 0, c->stream>>>(a);
         RBMD_LAUNCH_CHECK();
         RBMD_CHECK(md_sum(c, c->adj_tpart, (int)nba, 2 * c->T, tsum_dev, 1.0));
     } else {
