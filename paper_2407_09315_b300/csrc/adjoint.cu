@@ -82,8 +82,8 @@ __device__ __forceinline__ bool in_batch_row(const int32_t *row, int n, int p, i
 
 // acc[t] += v for a run-time type t < TT: TT <= 8 keeps the accumulators in
 // registers (an unrolled select), larger TT index an array.
-template <int TT>
-__device__ __forceinline__ void acc_add(double (&acc)[2 * TT], int t, double v)
+template <typename real, int TT>
+__device__ __forceinline__ void acc_add(real (&acc)[2 * TT], int t, real v)
 {
     if constexpr (TT <= 8) {
 #pragma unroll
@@ -104,18 +104,20 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
     // type-pair factors of the eps and sigma derivatives (Eq. 4), TT <= 16:
     // [tk TT + tj] = 1/2 sqrt(eps_j / eps_k) and 1 / sigma_kj
     constexpr int TP = TT <= 16 ? TT * TT : 1;
-    __shared__ double s_er[TP], s_is[TP];
+    __shared__ real s_er[TP], s_is[TP];
     if constexpr (TT <= 16) {
         for (int u = threadIdx.x; u < a.T * a.T; u += blockDim.x) {
             const int t1 = u / a.T, t2 = u % a.T;
-            s_er[t1 * TT + t2] = 0.5 * sqrt((double)a.eps[t2] / (double)a.eps[t1]);
-            s_is[t1 * TT + t2] = 1.0 / (0.5 * ((double)a.sig[t1] + (double)a.sig[t2]));
+            s_er[t1 * TT + t2] = (real)(0.5 * sqrt((double)a.eps[t2] / (double)a.eps[t1]));
+            s_is[t1 * TT + t2] = (real)(1.0 / (0.5 * ((double)a.sig[t1] + (double)a.sig[t2])));
         }
         __syncthreads();
     }
-    double acc[2 * TT];
+    // per-thread type sums in the working precision (a few tens of pairs; the
+    // block and type sums are FP64)
+    real acc[2 * TT];
 #pragma unroll
-    for (int t = 0; t < 2 * TT; ++t) acc[t] = 0.0;
+    for (int t = 0; t < 2 * TT; ++t) acc[t] = 0;
     const AtomSlot sl = atom_slot(a.map, a.reps);
     const int64_t ks = sl.i;
     if (sl.ok) {
@@ -170,23 +172,23 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
             gq += W * a.ck * qj * er * rinv;
             if (Wkj != (real)0) {
                 // one-sided: 1/2 W_kj du/d eps_kj d eps_kj/d eps_t (Eq. 4), same for sigma
-                const double hw = 0.5 * (double)Wkj;
-                const double due = 4.0 * ((double)s12 - (double)s6);
-                double dus = 4.0 * (double)eij * (12.0 * (double)s12 - 6.0 * (double)s6);
-                double rkj, rjk;
+                const real hw = (real)0.5 * Wkj;
+                const real due = (real)4 * (s12 - s6);
+                real dus = (real)4 * eij * ((real)12 * s12 - (real)6 * s6);
+                real rkj, rjk;
                 if constexpr (TT <= 16) {
                     dus *= s_is[tk * TT + tj];
                     rkj = s_er[tk * TT + tj];
                     rjk = s_er[tj * TT + tk];
                 } else {
-                    dus /= (double)sij;
-                    rkj = 0.5 * sqrt((double)a.eps[tj] / (double)a.eps[tk]);
-                    rjk = 0.5 * sqrt((double)a.eps[tk] / (double)a.eps[tj]);
+                    dus /= sij;
+                    rkj = (real)0.5 * sqrt_a(a.eps[tj] / a.eps[tk]);
+                    rjk = (real)0.5 * sqrt_a(a.eps[tk] / a.eps[tj]);
                 }
-                acc_add<TT>(acc, tk, hw * due * rkj);
-                acc_add<TT>(acc, tj, hw * due * rjk);
-                acc_add<TT>(acc, TT + tk, hw * dus * 0.5);
-                acc_add<TT>(acc, TT + tj, hw * dus * 0.5);
+                acc_add<real, TT>(acc, tk, hw * due * rkj);
+                acc_add<real, TT>(acc, tj, hw * due * rjk);
+                acc_add<real, TT>(acc, TT + tk, hw * dus * (real)0.5);
+                acc_add<real, TT>(acc, TT + tj, hw * dus * (real)0.5);
             }
         }
         const int64_t id = A.w;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
 #pragma unroll
     for (int t = 0; t < 2 * TT; ++t) {
         if ((t % TT) >= a.T) continue;
-        double v = acc[t] * a.g;
+        double v = (double)acc[t] * a.g;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) s_t[t][warp] = v;
     }

@@ -248,7 +248,7 @@ void free_ctx(rbmd_ctx *c)
                     c->adj_lj,    c->adj_tpart, c->adj_tsum, c->reps,       c->map256,
                     c->map128,    c->tiles,     c->red_rep,   c->ptab,       c->heavy,
                     c->modes0,    c->acc,       c->chain_step, c->phtab,      c->vl_cand,
-                    c->vl_ncand,  c->vl_sref};
+                    c->vl_ncand,  c->vl_sref,   c->rho_acc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -785,6 +785,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     if (c->full_modes) TRY(alloc_n(&c->W, c->Pm));
     TRY(alloc_n(&c->rho_part, (size_t)c->ntiles_max * c->Pm));
     TRY(alloc_n(&c->rho, (size_t)R * c->Pm));
+    TRY(alloc_n(&c->rho_acc, (size_t)R * c->Pm * 2));
     TRY(alloc_n(&c->emode, (size_t)R * c->Pm));
     TRY(dev_alloc(&c->coef, (size_t)R * c->Pm * (c->fp64 ? sizeof(ModeCoef<double>) : sizeof(ModeCoef<float>))));
     TRY(alloc_n(&c->cell_count, c->ncell_max));

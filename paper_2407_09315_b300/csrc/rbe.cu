@@ -358,46 +358,48 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
     }
 }
 
-// Second stage: one block of 128 threads (32 when every replica has at most 128
-// tiles) per (replica, mode) sums the atom-tile partials in FP64 (thread-strided,
-// then a fixed shuffle and shared-memory tree),
-// and derives the force and energy coefficients:
+// Exact, order-independent sums of the tile partials: every FP64 partial is
+// turned into a 128-bit fixed-point integer in units of 2^-64 (bits below are
+// dropped, deterministically), and integers add associatively, so a mode's sum
+// is the same for any grouping of its tiles: one context summing all of them, or
+// the slab contexts of a spatial decomposition adding their partial sums.
+__device__ __forceinline__ __int128 fx_from_double(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0) return 0;  // zero (or below 2^-1022)
+    const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+    const int sh = ex - 1075 + 64;  // |x| 2^64 = mant 2^sh (|x| < 2^62 keeps it below 2^127)
+    if (sh <= -53) return 0;
+    __int128 v = (__int128)mant;
+    v = sh >= 0 ? (v << sh) : (v >> (-sh));
+    return (b >> 63) ? -v : v;
+}
+
+__device__ __forceinline__ double fx_to_double(__int128 v)
+{
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    return (double)hi + (double)lo * 5.421010862427522170e-20;  // 2^-64
+}
+
+__device__ __forceinline__ __int128 shfl_xor_128(__int128 v, int o)
+{
+    const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(v >> 64), o);
+    const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+    return ((__int128)hi << 64) | (__int128)lo;
+}
+
+// Force and energy coefficients of mode l (replica rp, local index lm) from its
+// structure factor:
 //   c_l = -(4 pi coulomb_k / V) W_l / k_l^2,  A_l = c_l Im rho_l,  B_l = c_l Re rho_l,
 //   e_l = coulomb_k (2 pi / V) W_l |rho_l|^2 / k_l^2   (energy estimate term).
 template <typename real>
-__global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, const Rep *__restrict__ reps, int R,
-                            int64_t Pm, const int4 *__restrict__ modes,
-                            const double *__restrict__ W, double ck, double2 *__restrict__ rho,
-                            double *__restrict__ emode, ModeCoef<real> *__restrict__ coef)
+__device__ __forceinline__ void mode_coef(const Rep &rp, int64_t l, int64_t lm, int4 m,
+                                          const double *__restrict__ W, double ck, double re,
+                                          double im, double2 *__restrict__ rho,
+                                          double *__restrict__ emode, ModeCoef<real> *__restrict__ coef)
 {
-    __shared__ double2 s_p[4];
-    const int64_t t = blockIdx.x;  // r Pm + l
-    const int lane = threadIdx.x & 31;
-    const int r = (int)(t / Pm);
-    const int64_t lm = t - (int64_t)r * Pm;
-    const Rep rp = reps[r];
-    double re = 0.0, im = 0.0;
-    for (int k = threadIdx.x; k < rp.ntiles; k += blockDim.x) {
-        double2 p = part[lm * (int64_t)ntiles + rp.tile0 + k];
-        re += p.x;
-        im += p.y;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
-    }
-    if (blockDim.x > 32) {
-        if (lane == 0) s_p[threadIdx.x >> 5] = make_double2(re, im);
-        __syncthreads();
-        if (threadIdx.x != 0) return;
-        re = (s_p[0].x + s_p[1].x) + (s_p[2].x + s_p[3].x);
-        im = (s_p[0].y + s_p[1].y) + (s_p[2].y + s_p[3].y);
-    } else if (lane != 0) {
-        return;
-    }
-    const int64_t l = t;
-    const int4 m = modes[l];
     const double L = rp.L;
     const double V = L * L * L;
     const double tk = 2.0 * kPi / L;
@@ -423,6 +425,66 @@ __global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, const 
     mc.kz = (real)m.z;
     if constexpr (sizeof(real) == 8) mc.pad2 = mc.pad3 = mc.pad4 = (real)0;
     coef[l] = mc;
+}
+
+// Second stage: one block of 128 threads (32 when every replica has at most 128
+// tiles) per (replica, mode) sums the atom-tile partials exactly (fixed point,
+// above), stores the sums (acc, [R][Pm][2] re, im) and derives rho and the
+// coefficients (mode_coef).
+template <typename real>
+__global__ void k_rho_final(const double2 *__restrict__ part, int ntiles, const Rep *__restrict__ reps, int R,
+                            int64_t Pm, const int4 *__restrict__ modes,
+                            const double *__restrict__ W, double ck, double2 *__restrict__ rho,
+                            double *__restrict__ emode, ModeCoef<real> *__restrict__ coef,
+                            __int128 *__restrict__ acc)
+{
+    __shared__ __int128 s_p[4][2];
+    const int64_t t = blockIdx.x;  // r Pm + l
+    const int lane = threadIdx.x & 31;
+    const int r = (int)(t / Pm);
+    const int64_t lm = t - (int64_t)r * Pm;
+    const Rep rp = reps[r];
+    __int128 re = 0, im = 0;
+    for (int k = threadIdx.x; k < rp.ntiles; k += blockDim.x) {
+        const double2 p = part[lm * (int64_t)ntiles + rp.tile0 + k];
+        re += fx_from_double(p.x);
+        im += fx_from_double(p.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += shfl_xor_128(re, o);
+        im += shfl_xor_128(im, o);
+    }
+    if (blockDim.x > 32) {
+        if (lane == 0) {
+            s_p[threadIdx.x >> 5][0] = re;
+            s_p[threadIdx.x >> 5][1] = im;
+        }
+        __syncthreads();
+        if (threadIdx.x != 0) return;
+        re = s_p[0][0] + s_p[1][0] + s_p[2][0] + s_p[3][0];
+        im = s_p[0][1] + s_p[1][1] + s_p[2][1] + s_p[3][1];
+    } else if (lane != 0) {
+        return;
+    }
+    acc[2 * t] = re;
+    acc[2 * t + 1] = im;
+    mode_coef<real>(rp, t, lm, modes[t], W, ck, fx_to_double(re), fx_to_double(im), rho, emode, coef);
+}
+
+// rho and the coefficients of every mode from given exact sums (acc, [R][Pm][2]),
+// for a structure factor summed over several contexts.
+template <typename real>
+__global__ void k_rho_from_acc(const __int128 *__restrict__ acc, const Rep *__restrict__ reps,
+                               int64_t RPm, int64_t Pm, const int4 *__restrict__ modes,
+                               const double *__restrict__ W, double ck, double2 *__restrict__ rho,
+                               double *__restrict__ emode, ModeCoef<real> *__restrict__ coef)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= RPm) return;
+    const int r = (int)(t / Pm);
+    mode_coef<real>(reps[r], t, t - (int64_t)r * Pm, modes[t], W, ck, fx_to_double(acc[2 * t]),
+                    fx_to_double(acc[2 * t + 1]), rho, emode, coef);
 }
 
 // Dynamic shared memory of k_rho_partial for a tile shape.
@@ -482,11 +544,28 @@ rbmd_status rbe_rho_final(rbmd_ctx *c)
     if (c->fp64)
         k_rho_final<double><<<fin_blocks, fin_threads, 0, c->stream>>>(
             c->rho_part, c->ntiles, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
-            (ModeCoef<double> *)c->coef);
+            (ModeCoef<double> *)c->coef, c->rho_acc);
     else
         k_rho_final<float><<<fin_blocks, fin_threads, 0, c->stream>>>(
             c->rho_part, c->ntiles, c->reps, c->R, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho, c->emode,
-            (ModeCoef<float> *)c->coef);
+            (ModeCoef<float> *)c->coef, c->rho_acc);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+// rho and the coefficients from given exact sums (device [R][Pm][2] __int128).
+rbmd_status rbe_rho_from_acc(rbmd_ctx *c, const void *acc)
+{
+    const int64_t RPm = (int64_t)c->R * c->Pm;
+    const unsigned nb = (unsigned)((RPm + 127) / 128);
+    if (c->fp64)
+        k_rho_from_acc<double><<<nb, 128, 0, c->stream>>>(
+            (const __int128 *)acc, c->reps, RPm, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho,
+            c->emode, (ModeCoef<double> *)c->coef);
+    else
+        k_rho_from_acc<float><<<nb, 128, 0, c->stream>>>(
+            (const __int128 *)acc, c->reps, RPm, c->Pm, c->modes, c->W, c->prm.coulomb_k, c->rho,
+            c->emode, (ModeCoef<float> *)c->coef);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }

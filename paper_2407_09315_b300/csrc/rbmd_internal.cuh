@@ -219,6 +219,7 @@ struct rbmd_ctx {
     double *W;            // [Pm] weights (full-mode list, one replica), else NULL
     double2 *rho_part;    // [Pm][ntiles] mode-major, so a warp sums one mode over consecutive tiles
     double2 *rho;         // [R][Pm]
+    __int128 *rho_acc;    // [R][Pm][2] exact sums of the tile partials (units of 2^-64)
     double *emode;        // [R][Pm]
     void *coef;           // ModeCoef<real>[R][Pm]
     void *ptab;           // pair look-up table, real4 [2 ptab_n] (pairtab.cu)
@@ -456,6 +457,7 @@ rbmd_status metropolis_table_host(double L, double alpha, int M, uint64_t *A);
 rbmd_status rbe_structure_factors(rbmd_ctx *c, int mark_between = -1);
 rbmd_status rbe_rho_partial(rbmd_ctx *c, int t0, int t1);  // tile partials of tiles [t0, t1)
 rbmd_status rbe_rho_final(rbmd_ctx *c);                    // rho and coefficients from them
+rbmd_status rbe_rho_from_acc(rbmd_ctx *c, const void *acc);  // the same from given exact sums
 rbmd_status rbe_configure(rbmd_ctx *c);  // kernel attributes (dynamic shared memory)
 rbmd_status rbl_configure(rbmd_ctx *c);  // the same for the large-batch selection
 rbmd_status pair_table_host(double alpha, double r_cut, int n, std::vector<double> &coef,
