@@ -515,6 +515,60 @@ rbmd_status rbmd_rbe_forces_noalloc(const uint32_t *u, const float *charge, int6
                                     int32_t P, uint64_t seed, int64_t step, uint32_t replica,
                                     float *force, void *stream);
 
+/*
+ * Spatial decomposition of one system over several contexts (one per GPU): the
+ * paper names running on several GPUs as future work (Sec. 5); the split follows
+ * the RBE's structure (Sec. 2.2 below Eq. 12: the structure factors are sums over
+ * atoms, so each rank sums its own atoms and the ranks exchange 2P numbers) and
+ * the short range of the RBL (Sec. 2.3: an atom needs the atoms within r_cut).
+ *
+ * rbmd_init_slab -- a context over the atoms one rank owns, rows 0 .. n_owned-1,
+ *   followed by its halo, rows n_owned .. N-1: atoms of other ranks within r_cut
+ *   (with a margin) of the owned ones, all in the global box.  params->n_atoms =
+ *   N (owned + halo); gid (device, uint32 [N]) the global ids of the rows: every
+ *   random draw (RBE modes, RBL batch priorities and their ties) is keyed by the
+ *   global ids, so the modes, |C(i)|, N_s and B(i) of an owned atom are those of
+ *   one context holding all n_global atoms.  The slab need not be neutral.
+ *   Supported calls on a slab context: rbmd_rbe_rho_partial, rbmd_rbe_forces_rho,
+ *   rbmd_rbl_forces_slab, rbmd_add_correction, rbmd_rbl_lists, rbmd_set_state(_u),
+ *   rbmd_get_state(_u), rbmd_sync, rbmd_destroy (others: RBMD_ERR_UNSUPPORTED).
+ *   Errors: as rbmd_init; INVALID for n_owned outside [1, N], n_global < n_owned,
+ *   p > 32 or RBMD_FULL_EWALD_MODES.
+ *
+ * rbmd_rbe_rho_partial -- the structure factors of the owned atoms for the modes
+ *   of `step` as exact sums (Eq. 9): acc (host, int64 [P][4]) holds, per mode,
+ *   Re and Im as 128-bit fixed-point integers in units of 2^-64, each two int64
+ *   words (low word first, as unsigned, then the signed high word).  The atoms'
+ *   tile partials are added as integers, so the sum over ranks (rbmd_rho_acc_add,
+ *   in any order) equals bit for bit the sums of one context whose atom tiles hold
+ *   the same atoms (an ordinary context returns its full sums here too).
+ *   Synchronises.
+ * rbmd_rho_acc_add -- sum[k] += part[k] for n_modes modes of acc words (host
+ *   arithmetic on 128-bit integers, wrapping like the device sums).
+ * rbmd_rbe_forces_rho -- the RBE force (Eq. 12) of the owned atoms of `step` from
+ *   given summed structure factors acc (host, int64 [P][4]): every rank passing the
+ *   same sums computes the same rho and coefficients.  force (device, real [N][3]):
+ *   owned rows overwritten (or added to when accumulate != 0); halo rows are
+ *   unspecified.
+ * rbmd_rbl_forces_slab -- the RBL force of the owned atoms without the momentum
+ *   correction (Eqs. 13-15; halo rows set to zero unless accumulate), and in
+ *   fsum (host double [3]) the sum of those forces over the owned atoms.
+ *   Synchronises.
+ * rbmd_add_correction -- adds -fsum_total / n_global (Eq. 16: fsum_total the sum
+ *   of every rank's fsum) to the owned rows of force (device, real [N][3]).
+ */
+rbmd_status rbmd_init_slab(const rbmd_params *params, int64_t n_owned, int64_t n_global,
+                           const uint32_t *gid, const void *pos, const void *vel,
+                           const void *charge, const int32_t *type, const double *lj_eps,
+                           const double *lj_sigma, void *stream, rbmd_ctx **out);
+rbmd_status rbmd_rbe_rho_partial(rbmd_ctx *ctx, int64_t step, int64_t *acc);
+void rbmd_rho_acc_add(int64_t *sum, const int64_t *part, int64_t n_modes);
+rbmd_status rbmd_rbe_forces_rho(rbmd_ctx *ctx, int64_t step, const int64_t *acc, void *force,
+                                int accumulate);
+rbmd_status rbmd_rbl_forces_slab(rbmd_ctx *ctx, int64_t step, void *force, int accumulate,
+                                 double *fsum);
+rbmd_status rbmd_add_correction(rbmd_ctx *ctx, void *force, const double *fsum_total);
+
 /* Device error word injection for failure-path tests: sets the latched error to
  * `code` exactly as a kernel would. */
 rbmd_status rbmd_debug_latch_error(rbmd_ctx *ctx, int32_t code);

@@ -75,6 +75,13 @@ def lib():
         "rbmd_init_batch": ([C.POINTER(Params), i32, P, P, P, P, P, P, P, C.POINTER(P)], C.c_int),
         "rbmd_replica_count": ([P], i32),
         "rbmd_candidate_rebuilds": ([P], i64),
+        "rbmd_init_slab": ([C.POINTER(Params), i64, i64, P, P, P, P, P, P, P, P, C.POINTER(P)],
+                           C.c_int),
+        "rbmd_rbe_rho_partial": ([P, i64, P], C.c_int),
+        "rbmd_rho_acc_add": ([P, P, i64], None),
+        "rbmd_rbe_forces_rho": ([P, i64, P, P, C.c_int], C.c_int),
+        "rbmd_rbl_forces_slab": ([P, i64, P, C.c_int, P], C.c_int),
+        "rbmd_add_correction": ([P, P, P], C.c_int),
         "rbmd_set_tiles": ([P, i32, i32, i32], C.c_int),
         "rbmd_get_tiles": ([P, P], C.c_int),
         "rbmd_autotune": ([P, i64, P], C.c_int),
@@ -160,6 +167,19 @@ def pair_table(alpha, r_cut, n):
     return i0.value, inv_h.value, coef
 
 
+def rho_acc_add(total, part):
+    """total += part for exact structure-factor sums (int64 numpy [P, 4], the
+    128-bit words of rbmd_rbe_rho_partial); in place, returns total."""
+    t = np.ascontiguousarray(total, dtype=np.int64)
+    q = np.ascontiguousarray(part, dtype=np.int64)
+    if t.shape != q.shape or t.ndim != 2 or t.shape[1] != 4:
+        raise ValueError("acc arrays must be int64 [P, 4] of one shape")
+    lib().rbmd_rho_acc_add(_ptr(t), _ptr(q), t.shape[0])
+    if t is not total:
+        total[...] = t
+    return total
+
+
 def rbe_forces_noalloc(u, charge, box_length, *, alpha, coulomb_k, P, seed, step, out,
                        replica=0, stream=None):
     """RBE force without a context or any device allocation (FP32).
@@ -212,7 +232,7 @@ class RBMD:
                  r_cut=3.5, rbl_p=10, rbe_P=100, coulomb_k=1.0, dt=0.001, temperature=1.0,
                  tau_T=0.1, thermostat=0, seed=0, replica=0, precision=FP32, flags=0,
                  cell_div=0, vel=None, types=None, stream=None, n_atoms=None, mh_moves=0,
-                 skin=0.0):
+                 skin=0.0, slab=None):
         import torch
 
         self._torch = torch
@@ -258,9 +278,22 @@ class RBMD:
             stream = torch.cuda.current_stream(self.device)
         self.stream = stream
         h = C.c_void_p()
-        _check(lib().rbmd_init_batch(prm, R, _ptr(pos), _ptr(vel), _ptr(charge), _ptr(types),
-                                     _ptr(eps), _ptr(sigma), C.c_void_p(stream.cuda_stream),
-                                     C.byref(h)), "rbmd_init_batch")
+        self.slab = slab
+        if slab is not None:
+            # (n_owned, n_global, gid): a slab context of a spatial decomposition
+            n_owned, n_global, gid = slab
+            gid = gid.to(self.device, torch.int32).contiguous()
+            self.n_owned = int(n_owned)
+            _check(lib().rbmd_init_slab(prm, int(n_owned), int(n_global), _ptr(gid), _ptr(pos),
+                                        _ptr(vel), _ptr(charge), _ptr(types), _ptr(eps),
+                                        _ptr(sigma), C.c_void_p(stream.cuda_stream), C.byref(h)),
+                   "rbmd_init_slab")
+            self._gid = gid
+        else:
+            self.n_owned = n
+            _check(lib().rbmd_init_batch(prm, R, _ptr(pos), _ptr(vel), _ptr(charge), _ptr(types),
+                                         _ptr(eps), _ptr(sigma), C.c_void_p(stream.cuda_stream),
+                                         C.byref(h)), "rbmd_init_batch")
         self._h = h
         self._keep = (pos, charge, vel, types)
 
@@ -294,6 +327,37 @@ class RBMD:
         out = self._new3() if out is None else out
         _check(lib().rbmd_forces(self._h, step, _ptr(out), int(accumulate)), "forces")
         return out
+
+    # -- spatial decomposition (slab contexts) -----------------------------
+    def rho_partial(self, step):
+        """Exact structure-factor sums of the owned atoms (int64 numpy [R*P, 4])."""
+        acc = np.zeros((self.R * self.mode_count(), 4), dtype=np.int64)
+        _check(lib().rbmd_rbe_rho_partial(self._h, step, _ptr(acc)), "rbe_rho_partial")
+        return acc
+
+    def forces_rho(self, step, acc, out=None, accumulate=False):
+        """RBE force of the owned atoms from summed structure factors (rho_partial
+        summed over ranks with rho_acc_add)."""
+        out = self._new3() if out is None else out
+        acc = np.ascontiguousarray(acc, dtype=np.int64)
+        _check(lib().rbmd_rbe_forces_rho(self._h, step, _ptr(acc), _ptr(out), int(accumulate)),
+               "rbe_forces_rho")
+        return out
+
+    def rbl_forces_slab(self, step, out=None, accumulate=False):
+        """RBL force of the owned atoms without the momentum correction, and the sum
+        of those forces (numpy [3])."""
+        out = self._new3() if out is None else out
+        fsum = np.zeros(3)
+        _check(lib().rbmd_rbl_forces_slab(self._h, step, _ptr(out), int(accumulate), _ptr(fsum)),
+               "rbl_forces_slab")
+        return out, fsum
+
+    def add_correction(self, force, fsum_total):
+        """force (owned rows) += -fsum_total / n_global (Eq. 16 over all ranks)."""
+        f = np.ascontiguousarray(fsum_total, dtype=np.float64)
+        _check(lib().rbmd_add_correction(self._h, _ptr(force), _ptr(f)), "add_correction")
+        return force
 
     def forces_host(self, pos, out=None, step=0):
         """Host positions in (they become the state, as set_state), host forces out:

@@ -172,6 +172,19 @@ __global__ void k_u3_to_u4(const uint32_t *__restrict__ u3, int64_t N, uint4 *__
     u4[i] = A;
 }
 
+// F += fc on the owned rows of every replica (the momentum correction of a slab
+// context, Eq. 16, with a correction summed over all ranks).
+template <typename real>
+__global__ void k_add_owned(real *__restrict__ F, const int2 *__restrict__ map,
+                            const Rep *__restrict__ reps, double fx, double fy, double fz)
+{
+    const AtomSlot sl = atom_slot(map, reps);
+    if (!sl.ok || sl.i - reps[sl.r].atom0 >= reps[sl.r].n_own) return;
+    F[3 * sl.i + 0] += (real)fx;
+    F[3 * sl.i + 1] += (real)fy;
+    F[3 * sl.i + 2] += (real)fz;
+}
+
 __global__ void k_zero_slots(double *scal, int R, int slot0, int count)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -248,7 +261,7 @@ void free_ctx(rbmd_ctx *c)
                     c->adj_lj,    c->adj_tpart, c->adj_tsum, c->reps,       c->map256,
                     c->map128,    c->tiles,     c->red_rep,   c->ptab,       c->heavy,
                     c->modes0,    c->acc,       c->chain_step, c->phtab,      c->vl_cand,
-                    c->vl_ncand,  c->vl_sref,   c->rho_acc};
+                    c->vl_ncand,  c->vl_sref,   c->rho_acc,   c->gid};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -365,7 +378,7 @@ int tile_layout(rbmd_ctx *c, int tile, bool apply, std::vector<int2> &tl)
     for (int r = 0; r < c->R; ++r) {
         Rep &rp = c->reps_h[r];
         const int t0 = (int)tl.size();
-        for (int64_t a = 0; a < rp.N; a += tile) tl.push_back(make_int2(r, (int)(rp.atom0 + a)));
+        for (int64_t a = 0; a < rp.n_own; a += tile) tl.push_back(make_int2(r, (int)(rp.atom0 + a)));
         if (apply) {
             rp.tile0 = t0;
             rp.ntiles = (int32_t)tl.size() - t0;
@@ -538,9 +551,19 @@ rbmd_status rbmd_metropolis_table(double box_length, double alpha, uint64_t *A)
     return metropolis_table_host(box_length, alpha, M, A);
 }
 
-rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos, const void *vel,
-                            const void *charge, const int32_t *type, const double *lj_eps,
-                            const double *lj_sigma, void *stream, rbmd_ctx **out)
+}  // extern "C"
+
+namespace {
+
+// A slab context of a spatial decomposition (rbmd_init_slab).
+struct SlabInit {
+    int64_t n_owned, n_global;
+    const uint32_t *gid;  // device [N]
+};
+
+rbmd_status init_ctx(const rbmd_params *prms, int32_t R, const void *pos, const void *vel,
+                     const void *charge, const int32_t *type, const double *lj_eps,
+                     const double *lj_sigma, void *stream, const SlabInit *slab, rbmd_ctx **out)
 {
     if (!out) return RBMD_ERR_INVALID;
     *out = nullptr;
@@ -663,6 +686,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
         rp.Rv = rp.Rlin;
         rp.atom0 = atom0;
         rp.N = q.n_atoms;
+        rp.n_own = slab ? slab->n_owned : q.n_atoms;
         rp.b256_0 = (int32_t)m256.size();
         for (int64_t a = 0; a < rp.N; a += 256) m256.push_back(make_int2(r, (int)(atom0 + a)));
         rp.nb256 = (int32_t)m256.size() - rp.b256_0;
@@ -680,7 +704,8 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     // p.skin (0: 0.4 sigma), off for exact lists, large batches, RBL off, or a box
     // where r_cut + skin reaches half the box
     c->skin = p.skin == 0.0 ? 0.4 : p.skin;
-    c->verlet = c->skin > 0.0 && !(p.flags & (RBMD_RBL_EXACT | RBMD_NO_RBL)) && p.rbl_p <= 16;
+    c->verlet = c->skin > 0.0 && !(p.flags & (RBMD_RBL_EXACT | RBMD_NO_RBL)) && p.rbl_p <= 16 &&
+                !slab;
     if (const char *env = getenv("RBMD_NO_CANDIDATES")) c->verlet = c->verlet && atoi(env) == 0;
     double max_mv = 0.0;
     for (int r = 0; r < R && c->verlet; ++r) {
@@ -808,6 +833,12 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     TRY(alloc_n(&c->epart, EPART * (size_t)c->pair_parts));
     TRY(alloc_n(&c->kepart, (size_t)c->nb256 * 3));
     TRY(alloc_n(&c->ibuf, 8));
+    c->n_glob = slab ? slab->n_global : Ntot;
+    if (slab) {
+        TRY(alloc_n(&c->gid, (size_t)N));
+        TRY(cuda_status(cudaMemcpyAsync(c->gid, slab->gid, sizeof(uint32_t) * N, cudaMemcpyDefault,
+                                        c->stream)));
+    }
     if (c->verlet) {
         TRY(alloc_n(&c->vl_cand, (size_t)((N + 31) / 32) * 32 * c->vl_cv));
         TRY(alloc_n(&c->vl_ncand, (size_t)N));
@@ -878,7 +909,7 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     else TRY(cuda_status(cudaMemsetAsync(c->vel, 0, 3 * N * rs, c->stream)));
 
     // neutrality of every replica (Sec. 2.2) and the self energies (third term of Eq. 8)
-    TRY(charge_sums(c));
+    TRY(charge_sums(c, !slab));  // a slab need not be neutral (the whole system is)
 #undef TRY
     c->step = 0;
     c->have_force = false;
@@ -886,6 +917,32 @@ rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos,
     leave(c, RBMD_OK);
     *out = c;
     return RBMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rbmd_status rbmd_init_batch(const rbmd_params *prms, int32_t R, const void *pos, const void *vel,
+                            const void *charge, const int32_t *type, const double *lj_eps,
+                            const double *lj_sigma, void *stream, rbmd_ctx **out)
+{
+    return init_ctx(prms, R, pos, vel, charge, type, lj_eps, lj_sigma, stream, nullptr, out);
+}
+
+rbmd_status rbmd_init_slab(const rbmd_params *params, int64_t n_owned, int64_t n_global,
+                           const uint32_t *gid, const void *pos, const void *vel,
+                           const void *charge, const int32_t *type, const double *lj_eps,
+                           const double *lj_sigma, void *stream, rbmd_ctx **out)
+{
+    if (!out) return RBMD_ERR_INVALID;
+    *out = nullptr;
+    if (!params || !gid || n_owned < 1 || n_owned > params->n_atoms || n_global < n_owned ||
+        n_global > (int64_t)UINT32_MAX || params->rbl_p > 32 ||
+        (params->flags & RBMD_FULL_EWALD_MODES))
+        return RBMD_ERR_INVALID;
+    const SlabInit sl{n_owned, n_global, gid};
+    return init_ctx(params, 1, pos, vel, charge, type, lj_eps, lj_sigma, stream, &sl, out);
 }
 
 rbmd_status rbmd_init(const rbmd_params *prm, const void *pos, const void *vel, const void *charge,
@@ -900,6 +957,7 @@ void rbmd_destroy(rbmd_ctx *c) { free_ctx(c); }
 rbmd_status rbmd_rbe_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
 {
     if (!c || !force) return RBMD_ERR_INVALID;
+    if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
     rbmd_status s = RBMD_OK;
     if (c->prm.flags & RBMD_NO_RBE) {
@@ -916,6 +974,7 @@ rbmd_status rbmd_rbe_forces(rbmd_ctx *c, int64_t step, void *force, int accumula
 rbmd_status rbmd_rbl_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
 {
     if (!c || !force) return RBMD_ERR_INVALID;
+    if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
     rbmd_status s = RBMD_OK;
     if (c->prm.flags & RBMD_NO_RBL) {
@@ -932,6 +991,7 @@ rbmd_status rbmd_rbl_forces(rbmd_ctx *c, int64_t step, void *force, int accumula
 rbmd_status rbmd_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
 {
     if (!c || !force) return RBMD_ERR_INVALID;
+    if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
     return leave(c, forces_into(c, StepRef{nullptr, step}, force, accumulate, true));
 }
@@ -939,6 +999,7 @@ rbmd_status rbmd_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
 rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t step)
 {
     if (!c || !pos || !force) return RBMD_ERR_INVALID;
+    if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     const size_t row = 3 * real_size(c);
     void *dev = c->scratch_force;  // staged positions, then the forces
     const bool do_rbe = !(c->prm.flags & RBMD_NO_RBE);
@@ -1032,6 +1093,7 @@ rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t 
 rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
 {
     if (!c || n_steps < 0) return RBMD_ERR_INVALID;
+    if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     if (n_steps == 0) return RBMD_OK;
     enter(c);
     rbmd_status s = RBMD_OK;
@@ -1144,6 +1206,7 @@ static void gprof_collect(rbmd_ctx *c, int which, int nst)
 rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
 {
     if (!c || !out) return RBMD_ERR_INVALID;
+    if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
     const int R = c->R;
     memset(out, 0, sizeof(*out) * (size_t)R);
@@ -1313,6 +1376,7 @@ static rbmd_status tune_time(rbmd_ctx *c, bool rbl, StepRef s, int reps, float *
 rbmd_status rbmd_autotune(rbmd_ctx *c, int64_t step, int32_t *chosen)
 {
     if (!c) return RBMD_ERR_INVALID;
+    if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
     const StepRef s{nullptr, step};
     const int reps = 3;
@@ -1364,6 +1428,7 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
                                  double *d_eps, double *d_sigma)
 {
     if (!c) return RBMD_ERR_INVALID;
+    if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
     StepRef r{nullptr, step};
     rbmd_status s = RBMD_OK;
@@ -1652,6 +1717,89 @@ rbmd_status rbmd_profile_read(rbmd_ctx *c, double *ms, int64_t *steps, int reset
 }
 
 int32_t rbmd_step_kernel_count(rbmd_ctx *c) { return c ? c->graph_kernels : 0; }
+
+rbmd_status rbmd_rbe_rho_partial(rbmd_ctx *c, int64_t step, int64_t *acc)
+{
+    if (!c || !acc) return RBMD_ERR_INVALID;
+    if (c->prm.flags & RBMD_NO_RBE) return RBMD_ERR_UNSUPPORTED;
+    enter(c);
+    rbmd_status s = rbe_sample(c, StepRef{nullptr, step});
+    if (s == RBMD_OK) s = rbe_structure_factors(c);
+    if (s == RBMD_OK)
+        s = cuda_status(cudaMemcpyAsync(acc, c->rho_acc, sizeof(__int128) * 2 * c->R * c->Pm,
+                                        cudaMemcpyDeviceToHost, c->stream));
+    if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    s = leave(c, s);
+    if (s != RBMD_OK) return s;
+    return check_latched(c);
+}
+
+void rbmd_rho_acc_add(int64_t *sum, const int64_t *part, int64_t n_modes)
+{
+    if (!sum || !part) return;
+    for (int64_t k = 0; k < 2 * n_modes; ++k) {
+        // words (low as unsigned, high as signed) of 128-bit two's-complement integers
+        const unsigned __int128 a = ((unsigned __int128)(uint64_t)sum[2 * k + 1] << 64) |
+                                    (uint64_t)sum[2 * k];
+        const unsigned __int128 b = ((unsigned __int128)(uint64_t)part[2 * k + 1] << 64) |
+                                    (uint64_t)part[2 * k];
+        const unsigned __int128 t = a + b;
+        sum[2 * k] = (int64_t)(uint64_t)t;
+        sum[2 * k + 1] = (int64_t)(uint64_t)(t >> 64);
+    }
+}
+
+rbmd_status rbmd_rbe_forces_rho(rbmd_ctx *c, int64_t step, const int64_t *acc, void *force,
+                                int accumulate)
+{
+    if (!c || !acc || !force) return RBMD_ERR_INVALID;
+    if (c->prm.flags & RBMD_NO_RBE) return RBMD_ERR_UNSUPPORTED;
+    enter(c);
+    rbmd_status s = rbe_sample(c, StepRef{nullptr, step});
+    if (s == RBMD_OK)
+        s = cuda_status(cudaMemcpyAsync(c->rho_acc, acc, sizeof(__int128) * 2 * c->R * c->Pm,
+                                        cudaMemcpyHostToDevice, c->stream));
+    if (s == RBMD_OK) s = rbe_rho_from_acc(c, c->rho_acc);
+    if (s == RBMD_OK) s = rbe_apply_forces(c, force, accumulate);
+    return leave(c, s);
+}
+
+rbmd_status rbmd_rbl_forces_slab(rbmd_ctx *c, int64_t step, void *force, int accumulate,
+                                 double *fsum)
+{
+    if (!c || !force || !fsum) return RBMD_ERR_INVALID;
+    if (c->prm.flags & RBMD_NO_RBL) return RBMD_ERR_UNSUPPORTED;
+    enter(c);
+    const StepRef r{nullptr, step};
+    rbmd_status s = cells_build(c);
+    if (s == RBMD_OK) s = rbl_pairs(c, r, force, accumulate, false, nullptr, nullptr, nullptr);
+    if (s == RBMD_OK) s = md_sum_replicas(c, c->fpart, 3, SCAL_FSUM, 1.0, false, true);
+    if (s == RBMD_OK)
+        s = cuda_status(cudaMemcpyAsync(fsum, c->scal + SCAL_FSUM, 3 * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream));
+    if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+    c->have_force = false;
+    c->vl_dirty = true;
+    s = leave(c, s);
+    if (s != RBMD_OK) return s;
+    return check_latched(c);
+}
+
+rbmd_status rbmd_add_correction(rbmd_ctx *c, void *force, const double *fsum_total)
+{
+    if (!c || !force || !fsum_total) return RBMD_ERR_INVALID;
+    enter(c);
+    const double sc = -1.0 / (double)c->n_glob;
+    if (c->fp64)
+        k_add_owned<double><<<c->nb256, 256, 0, c->stream>>>((double *)force, c->map256, c->reps,
+                                                             sc * fsum_total[0], sc * fsum_total[1],
+                                                             sc * fsum_total[2]);
+    else
+        k_add_owned<float><<<c->nb256, 256, 0, c->stream>>>((float *)force, c->map256, c->reps,
+                                                            sc * fsum_total[0], sc * fsum_total[1],
+                                                            sc * fsum_total[2]);
+    return leave(c, cuda_status(cudaPeekAtLastError()));
+}
 
 rbmd_status rbmd_debug_latch_error(rbmd_ctx *c, int32_t code)
 {

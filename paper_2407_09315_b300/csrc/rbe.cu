@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
     const int tix = tile0 + (int)blockIdx.x;  // launches may cover a range of the tiles
     const int2 tl = tiles[tix];  // (replica, first atom); tiles never straddle replicas
     const int64_t a0 = tl.y;
-    const int na = (int)min((int64_t)tile_atoms, reps[tl.x].atom0 + reps[tl.x].N - a0);
+    const int na = (int)min((int64_t)tile_atoms, reps[tl.x].atom0 + reps[tl.x].n_own - a0);
     const int4 *modes = modes_all + (int64_t)tl.x * Pm;
     const int64_t l0 = (int64_t)blockIdx.y * mode_tile;
     const int nl = (int)min((int64_t)mode_tile, Pm - l0);

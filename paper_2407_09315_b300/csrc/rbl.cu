@@ -307,7 +307,16 @@ template <typename real> struct PairArgs {
     int CC, CS;
     int stale;         // the cells are those of the last rebuild of the step's candidate
                        // lists (atoms have moved since): cull at r_cut + skin
+    const uint32_t *gid;  // [N] global ids of a slab context's rows (Philox counters and
+                          // ties), NULL: the replica-local id
 };
+
+// Id of replica-local atom `id` (replica starting at row id0) in the random draws.
+template <typename real>
+__device__ __forceinline__ uint32_t pid(const PairArgs<real> &a, uint32_t id0, uint32_t id)
+{
+    return a.gid ? a.gid[id0 + id] : id;
+}
 
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return 1.0 / sqrt(x); }
@@ -595,18 +604,21 @@ constexpr int SEL_POS = -1;  // slot marker: plus infinity (empty)
 struct SelCtx {
     Philox0 r0;
     uint2 key;
+    const uint32_t *g;  // global ids of the replica's rows (slab contexts), or NULL
 };
 
-// true if slot (replica-local atom id hk) orders before the candidate `id`.
+// true if slot (replica-local atom id hk) orders before the candidate `id`
+// (priorities and ties on the ids of the draws).
 __device__ __noinline__ bool sel_slot_before(const SelCtx &s, int hk, uint32_t id)
 {
     if (hk == SEL_NEG) return true;
     if (hk == SEL_POS) return false;
-    const uint32_t hid = (uint32_t)hk;
-    const uint2 pa = philox_rest(s.r0, hid, s.key), pb = philox_rest(s.r0, id, s.key);
+    const uint32_t hid = s.g ? s.g[hk] : (uint32_t)hk;
+    const uint32_t cid = s.g ? s.g[id] : id;
+    const uint2 pa = philox_rest(s.r0, hid, s.key), pb = philox_rest(s.r0, cid, s.key);
     if (pa.x != pb.x) return pa.x < pb.x;
     if (pa.y != pb.y) return pa.y < pb.y;
-    return hid < id;
+    return hid < cid;
 }
 
 template <int CAP>
@@ -817,13 +829,15 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
 // CAP - p "minus infinity" markers, then the p smallest ascending (or empty slots).
 template <int CAP>
 __device__ __noinline__ void select_exact(const Philox0 &r0, uint2 key, const int32_t *ls, int ns,
-                                          int p, int (&hk)[CAP], int stride = 1)
+                                          int p, int (&hk)[CAP], int stride = 1,
+                                          const uint32_t *g = nullptr)
 {
     uint64_t kk[CAP];
-    uint32_t kid[CAP];
+    uint32_t kid[CAP], kloc[CAP];  // ids of the draws (ties), and replica-local ids
     int kept = 0;
     for (int e = 0; e < ns; ++e) {
-        const uint32_t id = (uint32_t)ls[e * stride];
+        const uint32_t loc = (uint32_t)ls[e * stride];
+        const uint32_t id = g ? g[loc] : loc;
         const uint2 w = philox_rest(r0, id, key);
         const uint64_t v = ((uint64_t)w.x << 32) | w.y;
         int j;  // the slot the shifting starts from
@@ -836,15 +850,17 @@ __device__ __noinline__ void select_exact(const Philox0 &r0, uint2 key, const in
         while (j > 0 && (v < kk[j - 1] || (v == kk[j - 1] && id < kid[j - 1]))) {
             kk[j] = kk[j - 1];
             kid[j] = kid[j - 1];
+            kloc[j] = kloc[j - 1];
             --j;
         }
         kk[j] = v;
         kid[j] = id;
+        kloc[j] = loc;
         if (kept < p) ++kept;
     }
     for (int e = 0; e < CAP; ++e) {
         const int j = e - (CAP - p);
-        hk[e] = j < 0 ? SEL_NEG : (j < kept ? (int)kid[j] : SEL_POS);
+        hk[e] = j < 0 ? SEL_NEG : (j < kept ? (int)kloc[j] : SEL_POS);
     }
 }
 
@@ -868,8 +884,9 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
         }
         nb = ns;
     } else {
-        const SelCtx sel{
-            philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key), rp.key};
+        const SelCtx sel{philox_round0(pid(a, id0, id_i - id0), (uint32_t)step_of(a.step),
+                                       rp.tag_rbl, rp.key),
+                         rp.key, a.gid ? a.gid + id0 : nullptr};
         const int32_t *ls = a.lshell + lidx(is, 0, N, a.CS);
         // keys: the priority's high word with its low b bits replaced by the
         // member's list position (2^b > CS, so no key is all ones and no two are
@@ -882,7 +899,7 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
 #pragma unroll
         for (int e = 0; e <= CAP; ++e) sk[e] = 0xFFFFFFFFu;
         auto insert = [&](uint32_t id, int e) {
-            const uint2 w = philox_rest(sel.r0, id, rp.key);
+            const uint2 w = philox_rest(sel.r0, pid(a, id0, id), rp.key);
             uint32_t x = (w.x & keep) | (uint32_t)e;
 #pragma unroll
             for (int j = 0; j <= CAP; ++j) {
@@ -931,7 +948,7 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
             nb = a.p;
         } else {
             int hk[CAP];
-            select_exact<CAP>(sel.r0, rp.key, ls, ns, a.p, hk);
+            select_exact<CAP>(sel.r0, rp.key, ls, ns, a.p, hk, 1, sel.g);
             for (int e = 0; e < CAP; ++e)
                 if (hk[e] >= 0) {
                     if constexpr (LISTS) ids[nb] = hk[e];
@@ -1006,14 +1023,14 @@ __global__ void __launch_bounds__(32 * SEL_WARPS) k_rbl_select_warp(PairArgs<rea
         const int ns = a.ncount[is].y;
         const uint32_t id_i = a.spos[is].w;
         const Philox0 r0 =
-            philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key);
+            philox_round0(pid(a, id0, id_i - id0), (uint32_t)step_of(a.step), rp.tag_rbl, rp.key);
         const int32_t *ls = a.lshell + lidx(is, 0, N, a.CS);
         int m = 1;
         while (m < ns) m <<= 1;  // sort length: power of two, at most n2
         for (int e = lane; e < m; e += 32) {
             if (e < ns) {
                 const uint32_t id = (uint32_t)ls[e];
-                const uint2 pw = philox_rest(r0, id, rp.key);
+                const uint2 pw = philox_rest(r0, pid(a, id0, id), rp.key);
                 s_key[e] = ((uint64_t)pw.x << 32) | pw.y;
                 s_id[e] = id;
             } else {
@@ -1152,7 +1169,17 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_force(PairArgs<real> a)
     real fx = 0, fy = 0, fz = 0;
     EAcc<real> e;
     eacc_zero(e);
-    if (sl.ok) {
+    bool own = sl.ok;
+    if (own && a.gid) {
+        // a slab context's halo rows are neighbours only: zero force, no sums
+        const Rep &rq = a.reps[sl.r];
+        own = (int64_t)a.spos[is].w - rq.atom0 < rq.n_own;
+        if (!own && !a.accumulate) {
+            real *f = a.F + 3 * (int64_t)a.spos[is].w;
+            f[0] = f[1] = f[2] = (real)0;
+        }
+    }
+    if (own) {
         const int2 cnt = a.ncount[is];
         if (!overflowed(a, cnt)) {
             AtomI<real> I;
@@ -1242,7 +1269,10 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
         const AtomSlot sl = atom_slot_at(a.map, a.reps, mb);
         {
             const int64_t is = sl.i;
-            if (sl.ok && overflowed(a, a.ncount[is])) {
+            bool own = sl.ok;
+            if (own && a.gid)
+                own = (int64_t)a.spos[is].w - a.reps[sl.r].atom0 < a.reps[sl.r].n_own;
+            if (own && overflowed(a, a.ncount[is])) {
                 const Rep rp = a.reps[sl.r];
                 const uint32_t id0 = (uint32_t)rp.atom0;
                 AtomI<real> I;
@@ -1253,9 +1283,9 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                 I.se = s_lj[ti];
                 I.hs = s_lj[a.T + ti];
                 const uint32_t id_i = I.A.w;
-                const SelCtx sel{
-                    philox_round0(id_i - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key),
-                    rp.key};
+                const SelCtx sel{philox_round0(pid(a, id0, id_i - id0), (uint32_t)step_of(a.step),
+                                               rp.tag_rbl, rp.key),
+                                 rp.key, a.gid ? a.gid + id0 : nullptr};
                 uint32_t hh[CAP];
                 int hk[CAP];
                 sel_init<CAP>(hh, hk, a.p);
@@ -1270,7 +1300,7 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                             eval_any<real, ENERGY>(a, s_lj, I, k, ax, ay, az, ae);
                         } else {
                             const uint32_t id = s_id[FB_LIST - 1 - t][tid] - id0;
-                            const uint2 w = philox_rest(sel.r0, id, rp.key);
+                            const uint2 w = philox_rest(sel.r0, pid(a, id0, id), rp.key);
                             sel_insert<CAP>(hh, hk, w.x, (int)id, id, sel);
                         }
                     }
@@ -1502,6 +1532,7 @@ static PairArgs<real> pair_args(rbmd_ctx *c, StepRef s)
     a.ovf = c->ibuf + 2;
     a.CC = c->list_cc;
     a.CS = c->list_cs;
+    a.gid = c->gid;
     return a;
 }
 

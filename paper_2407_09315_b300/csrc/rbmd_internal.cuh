@@ -100,6 +100,8 @@ struct Rep {
     float cull_v;           // r_cut + skin in cell widths (+ margin): cells of the last rebuild
     float dtc_hi, dtc_lo;   // dtc as a sum of two floats (FP32 drift)
     int64_t atom0, N;
+    int64_t n_own;          // atoms [atom0, atom0 + n_own) own forces and structure-factor
+                            // terms; the rest (a slab context's halo) are neighbours only
     int64_t cell0, ncell;
     int64_t cdf0;           // offset of the replica's sampler thresholds
     int32_t b256_0, nb256;  // blocks of the 256-thread atom kernels
@@ -178,6 +180,11 @@ struct rbmd_ctx {
     // positions encoded, forces final), 8 chunks at most
     cudaStream_t copy;
     cudaEvent_t ev_h2d[8], ev_enc[8], ev_fin[8];
+
+    // spatial decomposition (rbmd_init_slab): global atom ids of the rows (every
+    // random draw is keyed by them) and the global atom count; NULL / N otherwise
+    uint32_t *gid;
+    int64_t n_glob;
 
     // replicas
     int32_t R;
