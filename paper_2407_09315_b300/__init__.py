@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librbmd.so")
+# RBMD_LIBRARY selects another build of the library (the bounds-checked
+# librbmd_checked.so, for debugging); by default the in-tree librbmd.so
+LIB_PATH = os.environ.get("RBMD_LIBRARY") or os.path.join(_HERE, "librbmd.so")
 
 FP32, FP64 = 0, 1
 FULL_EWALD_MODES, RBL_EXACT, NO_RBE, NO_RBL, PAIR_TABLE, METROPOLIS_MODES = 1, 2, 4, 8, 16, 32
@@ -22,7 +24,7 @@ STATUS = {
     0: "RBMD_OK", 1: "RBMD_ERR_INVALID", 2: "RBMD_ERR_NOT_NEUTRAL",
     3: "RBMD_ERR_BOX_TOO_SMALL", 4: "RBMD_ERR_OOM", 5: "RBMD_ERR_CUDA",
     6: "RBMD_ERR_CELL_OVERFLOW", 7: "RBMD_ERR_NONFINITE", 8: "RBMD_ERR_TIMEOUT",
-    9: "RBMD_ERR_UNSUPPORTED",
+    9: "RBMD_ERR_UNSUPPORTED", 10: "RBMD_ERR_BOUNDS",
 }
 
 

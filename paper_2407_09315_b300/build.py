@@ -13,6 +13,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librbmd.so")
+# the same sources with every list and cell index bounds-checked on the device
+# (-DRBMD_CHECKED: a bad index latches RBMD_ERR_BOUNDS instead of being used)
+OUT_CHECKED = os.path.join(HERE, "librbmd_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,18 +34,22 @@ def headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "rbmd.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(OUT):
+def up_to_date(out=OUT) -> bool:
+    if not os.path.exists(out):
         return False
-    t = os.path.getmtime(OUT)
+    t = os.path.getmtime(out)
     return all(os.path.getmtime(f) <= t for f in sources() + headers())
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+def build(force: bool = False, verbose: bool = False, extra=None, checked: bool = False) -> str:
     """Compile every csrc/*.cu to an object file (in parallel), then link them
-    into librbmd.so with the CUDA runtime linked statically."""
-    if not force and up_to_date():
-        return OUT
+    into librbmd.so (librbmd_checked.so with checked=True) with the CUDA runtime
+    linked statically."""
+    out = OUT_CHECKED if checked else OUT
+    if not force and up_to_date(out):
+        return out
+    if checked:
+        extra = list(extra or []) + ["-DRBMD_CHECKED"]
     from concurrent.futures import ThreadPoolExecutor
 
     objdir = os.path.join(HERE, "_build")
@@ -56,19 +63,21 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     objs = []
     cmds = []
     for src in sources():
-        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".%d.o" % os.getpid())
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".%s%d.o" % ("c" if checked else "",
+                                                                           os.getpid()))
         objs.append(obj)
         cmds.append([nvcc(), *flags, "-c", "-o", obj, src])
     with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
         for f in [ex.submit(subprocess.check_call, c) for c in cmds]:
             f.result()
-    tmp = OUT + ".tmp%d" % os.getpid()
+    tmp = out + ".tmp%d" % os.getpid()
     subprocess.check_call([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
     for o in objs:
         os.remove(o)
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -441,6 +441,7 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
     }
     if (marks) prof_mark(c, 1);
     if (do_rbl) {
+        NvtxRange nvtx_range("rbl");
         rbmd_status st = RBMD_OK;
         if (verlet && !accumulate) {
             st = verlet_prepare(c);
@@ -532,6 +533,7 @@ const char *rbmd_status_string(rbmd_status s)
     case RBMD_ERR_NONFINITE: return "non-finite force or velocity";
     case RBMD_ERR_TIMEOUT: return "bounded device wait timed out";
     case RBMD_ERR_UNSUPPORTED: return "unsupported option";
+    case RBMD_ERR_BOUNDS: return "index out of range (bounds-checked build)";
     }
     return "unknown status";
 }
@@ -956,6 +958,7 @@ void rbmd_destroy(rbmd_ctx *c) { free_ctx(c); }
 
 rbmd_status rbmd_rbe_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
 {
+    NvtxRange nvtx_range("rbmd_rbe_forces");
     if (!c || !force) return RBMD_ERR_INVALID;
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
@@ -973,6 +976,7 @@ rbmd_status rbmd_rbe_forces(rbmd_ctx *c, int64_t step, void *force, int accumula
 
 rbmd_status rbmd_rbl_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
 {
+    NvtxRange nvtx_range("rbmd_rbl_forces");
     if (!c || !force) return RBMD_ERR_INVALID;
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
@@ -990,6 +994,7 @@ rbmd_status rbmd_rbl_forces(rbmd_ctx *c, int64_t step, void *force, int accumula
 
 rbmd_status rbmd_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
 {
+    NvtxRange nvtx_range("rbmd_forces");
     if (!c || !force) return RBMD_ERR_INVALID;
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
@@ -998,6 +1003,7 @@ rbmd_status rbmd_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
 
 rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t step)
 {
+    NvtxRange nvtx_range("rbmd_forces_host");
     if (!c || !pos || !force) return RBMD_ERR_INVALID;
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     const size_t row = 3 * real_size(c);
@@ -1092,6 +1098,7 @@ rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t 
 
 rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
 {
+    NvtxRange nvtx_range("rbmd_step");
     if (!c || n_steps < 0) return RBMD_ERR_INVALID;
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     if (n_steps == 0) return RBMD_OK;
@@ -1205,6 +1212,7 @@ static void gprof_collect(rbmd_ctx *c, int which, int nst)
 
 rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
 {
+    NvtxRange nvtx_range("rbmd_energy");
     if (!c || !out) return RBMD_ERR_INVALID;
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
@@ -1375,6 +1383,7 @@ static rbmd_status tune_time(rbmd_ctx *c, bool rbl, StepRef s, int reps, float *
 
 rbmd_status rbmd_autotune(rbmd_ctx *c, int64_t step, int32_t *chosen)
 {
+    NvtxRange nvtx_range("rbmd_autotune");
     if (!c) return RBMD_ERR_INVALID;
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
@@ -1427,6 +1436,7 @@ rbmd_status rbmd_autotune(rbmd_ctx *c, int64_t step, int32_t *chosen)
 rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, void *d_pos, void *d_q,
                                  double *d_eps, double *d_sigma)
 {
+    NvtxRange nvtx_range("rbmd_energy_backward");
     if (!c) return RBMD_ERR_INVALID;
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
@@ -1720,6 +1730,7 @@ int32_t rbmd_step_kernel_count(rbmd_ctx *c) { return c ? c->graph_kernels : 0; }
 
 rbmd_status rbmd_rbe_rho_partial(rbmd_ctx *c, int64_t step, int64_t *acc)
 {
+    NvtxRange nvtx_range("rbmd_rbe_rho_partial");
     if (!c || !acc) return RBMD_ERR_INVALID;
     if (c->prm.flags & RBMD_NO_RBE) return RBMD_ERR_UNSUPPORTED;
     enter(c);
@@ -1752,6 +1763,7 @@ void rbmd_rho_acc_add(int64_t *sum, const int64_t *part, int64_t n_modes)
 rbmd_status rbmd_rbe_forces_rho(rbmd_ctx *c, int64_t step, const int64_t *acc, void *force,
                                 int accumulate)
 {
+    NvtxRange nvtx_range("rbmd_rbe_forces_rho");
     if (!c || !acc || !force) return RBMD_ERR_INVALID;
     if (c->prm.flags & RBMD_NO_RBE) return RBMD_ERR_UNSUPPORTED;
     enter(c);
@@ -1767,6 +1779,7 @@ rbmd_status rbmd_rbe_forces_rho(rbmd_ctx *c, int64_t step, const int64_t *acc, v
 rbmd_status rbmd_rbl_forces_slab(rbmd_ctx *c, int64_t step, void *force, int accumulate,
                                  double *fsum)
 {
+    NvtxRange nvtx_range("rbmd_rbl_forces_slab");
     if (!c || !force || !fsum) return RBMD_ERR_INVALID;
     if (c->prm.flags & RBMD_NO_RBL) return RBMD_ERR_UNSUPPORTED;
     enter(c);

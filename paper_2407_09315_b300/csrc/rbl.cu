@@ -309,6 +309,7 @@ template <typename real> struct PairArgs {
                        // lists (atoms have moved since): cull at r_cut + skin
     const uint32_t *gid;  // [N] global ids of a slab context's rows (Philox counters and
                           // ties), NULL: the replica-local id
+    int *err;             // device error word (bounds-checked builds report through it)
 };
 
 // Id of replica-local atom `id` (replica starting at row id0) in the random draws.
@@ -432,6 +433,7 @@ __device__ __forceinline__ void eval_k(const PairArgs<real> &a, const real *s_lj
                                        const AtomI<real> &I, int k, real &fx, real &fy, real &fz,
                                        EAcc<real> &e)
 {
+    k = (int)RBMD_IDX(k, a.N, a.err);
     const uint4 B = a.spos[k];
     const int tj = a.stype[k];
     pair_eval<real, ENERGY, TAB>(a, (real)(int32_t)(B.x - I.A.x) * I.lscale,
@@ -449,7 +451,7 @@ __device__ __forceinline__ void eval_list(const PairArgs<real> &a, const real *s
                                           real &fx, real &fy, real &fz, EAcc<real> &e)
 {
     if (n <= 0) return;
-    int k = idx[0];
+    int k = (int)RBMD_IDX(idx[0], a.N, a.err);
     uint4 B = a.spos[k];
     int tj = a.stype[k];
     real qj = a.sq[k];
@@ -458,7 +460,7 @@ __device__ __forceinline__ void eval_list(const PairArgs<real> &a, const real *s
         int tn = tj;
         real qn = qj;
         if (t + 1 < n) {
-            const int kn = idx[t + 1];
+            const int kn = (int)RBMD_IDX(idx[t + 1], a.N, a.err);
             Bn = a.spos[kn];
             tn = a.stype[kn];
             qn = a.sq[kn];
@@ -489,7 +491,7 @@ __device__ __forceinline__ void eval_list4(const PairArgs<real> &a, const real *
         real qj[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int k = e0 + q < n ? ks[q] : ks[0];
+            const int k = (int)RBMD_IDX(e0 + q < n ? ks[q] : ks[0], a.N, a.err);
             B[q] = a.spos[k];
             tj[q] = a.stype[k];
             qj[q] = a.sq[k];
@@ -793,7 +795,7 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
         for (int k = kb; k < ke; k += 4) {
             uint4 B[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) B[q] = (k + q < ke) ? a.spos[k + q] : A;
+            for (int q = 0; q < 4; ++q) B[q] = (k + q < ke) ? a.spos[RBMD_IDX(k + q, N, a.err)] : A;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = (k + q < ke && k + q != (int)is) ? classify(rp, A, B[q]) : 0;
@@ -880,7 +882,7 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
         for (int e = 0; e < ns; ++e) {
             const int32_t id = a.lshell[lidx(is, e, N, a.CS)];
             if constexpr (LISTS) ids[e < CAP ? e : 0] = id;
-            a.bk[lidx(is, e, N, a.p)] = a.sidx[id0 + (uint32_t)id];
+            a.bk[lidx(is, e, N, a.p)] = a.sidx[RBMD_IDX(id0 + (uint32_t)id, N, a.err)];
         }
         nb = ns;
     } else {
@@ -943,7 +945,7 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
                 if (e < a.p) {
                     const int32_t id = ls[sk[e] & lo_mask];
                     if constexpr (LISTS) ids[e] = id;
-                    a.bk[lidx(is, e, N, a.p)] = a.sidx[id0 + (uint32_t)id];
+                    a.bk[lidx(is, e, N, a.p)] = a.sidx[RBMD_IDX(id0 + (uint32_t)id, N, a.err)];
                 }
             nb = a.p;
         } else {
@@ -952,7 +954,7 @@ __device__ __forceinline__ void select_atom(const PairArgs<real> &a, int64_t is,
             for (int e = 0; e < CAP; ++e)
                 if (hk[e] >= 0) {
                     if constexpr (LISTS) ids[nb] = hk[e];
-                    a.bk[lidx(is, nb, N, a.p)] = a.sidx[id0 + (uint32_t)hk[e]];
+                    a.bk[lidx(is, nb, N, a.p)] = a.sidx[RBMD_IDX(id0 + (uint32_t)hk[e], N, a.err)];
                     ++nb;
                 }
         }
@@ -1115,7 +1117,8 @@ __global__ void __launch_bounds__(256) k_rbl_take_shell(PairArgs<real> a)
     const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
     const int64_t N = a.N;
     const int32_t *ls = a.lshell + lidx(is, 0, N, a.CS);
-    for (int e = 0; e < cnt.y; ++e) a.bk[lidx(is, e, N, a.p)] = a.sidx[id0 + (uint32_t)ls[e]];
+    for (int e = 0; e < cnt.y; ++e)
+        a.bk[lidx(is, e, N, a.p)] = a.sidx[RBMD_IDX(id0 + (uint32_t)ls[e], N, a.err)];
     if constexpr (LISTS) {
         // batch ids ascending, -1 padded (verification path only)
         int32_t *out = a.batch + (int64_t)a.spos[is].w * a.p;
@@ -1311,7 +1314,7 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
                 stencil_ranges(a, rp, I.A, [&](int kb, int ke) {
                     for (int k = kb; k < ke; ++k) {
                         if (k == (int)is) continue;
-                        const uint4 B = a.spos[k];
+                        const uint4 B = a.spos[RBMD_IDX(k, a.N, a.err)];
                         const int c = classify(rp, I.A, B);
                         if (c == 1) {
                             s_k[lc][tid] = k;
@@ -1533,6 +1536,7 @@ static PairArgs<real> pair_args(rbmd_ctx *c, StepRef s)
     a.CC = c->list_cc;
     a.CS = c->list_cs;
     a.gid = c->gid;
+    a.err = c->err;
     return a;
 }
 
@@ -1645,13 +1649,14 @@ __device__ __forceinline__ int64_t vl_slot(int64_t is, int t, int cv)
 // already pending (it sorts the state afresh).
 __global__ void k_vl_gather(const Rep *__restrict__ reps, const int2 *__restrict__ map,
                             uint4 *__restrict__ spos, const uint4 *__restrict__ u4,
-                            const uint4 *__restrict__ sref, int32_t *__restrict__ flag)
+                            const uint4 *__restrict__ sref, int32_t *__restrict__ flag,
+                            int64_t N, int *__restrict__ err)
 {
     if (*flag) return;
     const AtomSlot sl = atom_slot(map, reps);
     if (!sl.ok) return;
     const uint32_t id = spos[sl.i].w;
-    const uint4 U = u4[id];
+    const uint4 U = u4[RBMD_IDX(id, N, err)];
     spos[sl.i] = make_uint4(U.x, U.y, U.z, id);
     const uint4 R = sref[sl.i];
     const int32_t dx = (int32_t)(U.x - R.x), dy = (int32_t)(U.y - R.y), dz = (int32_t)(U.z - R.z);
@@ -1677,7 +1682,7 @@ __global__ void __launch_bounds__(256) k_vl_build(PairArgs<real> a, VlArgs v)
     int n = 0;
     stencil_ranges(a, rp, A, [&](int kb, int ke) {
         for (int k = kb; k < ke; ++k) {
-            const uint4 B = a.spos[k];
+            const uint4 B = a.spos[RBMD_IDX(k, a.N, a.err)];
             const int32_t dx = (int32_t)(B.x - A.x), dy = (int32_t)(B.y - A.y),
                           dz = (int32_t)(B.z - A.z);
             if (((uint32_t)dx + rp.Rv > R2x) | ((uint32_t)dy + rp.Rv > R2x) |
@@ -1797,7 +1802,7 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
 #pragma unroll
         for (int q = 0; q < VB; ++q) {
             const int k0 = q < n ? cl[q * 32] : -1;
-            Bn[q] = k0 >= 0 ? a.spos[k0] : A;
+            Bn[q] = k0 >= 0 ? a.spos[RBMD_IDX(k0, a.N, a.err)] : A;
             kk[q] = VB + q < n ? cl[(VB + q) * 32] : -1;
         }
         for (int t0 = 0; t0 < n; t0 += VB) {
@@ -1805,7 +1810,7 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
 #pragma unroll
             for (int q = 0; q < VB; ++q) {
                 B[q] = Bn[q];
-                Bn[q] = kk[q] >= 0 ? a.spos[kk[q]] : A;
+                Bn[q] = kk[q] >= 0 ? a.spos[RBMD_IDX(kk[q], a.N, a.err)] : A;
                 kk[q] = t0 + 2 * VB + q < n ? cl[(t0 + 2 * VB + q) * 32] : -1;
             }
             bool sh[VB];
@@ -1853,7 +1858,9 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
         // the whole shell (its keys are all kept), in atom-id order
 #pragma unroll
         for (int e = 0; e < CAP; ++e)
-            if (e < ns) s_core[e * 128] = (int32_t)(a.spos[cl[(sk[e] & lo_mask) * 32]].w - id0);
+            if (e < ns)
+                s_core[e * 128] =
+                    (int32_t)(a.spos[RBMD_IDX(cl[(sk[e] & lo_mask) * 32], a.N, a.err)].w - id0);
         sort_strided(s_core, ns, 128);
         for (int e = 0; e < ns; ++e) bk[e] = sidx[s_core[e * 128]];
     } else {
@@ -1896,7 +1903,7 @@ static rbmd_status verlet_prepare_t(rbmd_ctx *c)
 {
     int32_t *flag = c->ibuf + 4;
     k_vl_gather<<<c->nb256, 256, 0, c->stream>>>(c->reps, c->map256, c->spos, c->u4, c->vl_sref,
-                                                  flag);
+                                                  flag, c->N, c->err);
     RBMD_LAUNCH_CHECK();
     RBMD_CHECK(cells_sort(c, false, flag));
     PairArgs<real> a = pair_args<real>(c, StepRef{nullptr, 0});

@@ -16,6 +16,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
@@ -82,6 +83,32 @@ __host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k)
 
 // Device error word: first error wins.
 __device__ __forceinline__ void latch_error(int *err, int code) { atomicCAS(err, 0, code); }
+
+// Index i of an array of n elements.  Built with -DRBMD_CHECKED, an index outside
+// [0, n) latches RBMD_ERR_BOUNDS and reads element 0 instead (a debugging build in
+// place of a memory checker: nothing faults, the error is reported by the next
+// synchronising call); otherwise the index itself.
+__device__ __forceinline__ int64_t checked_index(int64_t i, int64_t n, int *err)
+{
+    if (i < 0 || i >= n) {
+        if (err) latch_error(err, RBMD_ERR_BOUNDS);
+        return 0;
+    }
+    return i;
+}
+#ifdef RBMD_CHECKED
+#define RBMD_IDX(i, n, err) rbmd::checked_index((int64_t)(i), (int64_t)(n), (err))
+#else
+#define RBMD_IDX(i, n, err) (i)
+#endif
+
+// A named host range for profilers (nothing happens without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Per-replica constants, on the device (array of R) and on the host.  A context
 // holds R >= 1 independent replicas concatenated: atoms [atom0, atom0 + N),
