@@ -302,12 +302,14 @@ def mean_lists(system):
     return core, shell
 
 
-def captured_traffic():
-    """DRAM bytes per launch from the committed ncu summary, per stage, or {} when
-    a kernel source changed since the capture (the counters no longer apply)."""
+def captured_traffic(n_atoms):
+    """DRAM bytes per launch of the hot kernels, from the committed ncu summary of
+    a 200k-atom capture of this workload's recipe, scaled to n_atoms (every
+    kernel's traffic grows with the atoms it processes), per stage; {} when a
+    kernel source changed since the capture (the counters no longer apply)."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", "hot_kernels_step_1M.md")
+    path = os.path.join(ROOT, "profiles", "hot_kernels_200k.md")
     try:
         m = re.search(r"```json\n(.*?)\n```", open(path).read(), re.S)
         d = json.loads(m.group(1))
@@ -315,9 +317,27 @@ def captured_traffic():
             src = os.path.join(ROOT, "paper_2407_09315_b300", "csrc", name)
             if hashlib.sha256(open(src, "rb").read()).hexdigest() != sha:
                 return {}
-        return d["traffic_bytes"]
+        f = n_atoms / d["atoms"]
+        return {k: int(round(v * f)) for k, v in d["traffic_bytes_per_launch"].items()}
     except Exception:
         return {}
+
+
+def step_stage_names(stages, candidates):
+    """Stage times under the names of the kernels that run.  With the step's
+    neighbour candidate lists (rbmd_step's default), the cell-sort stage holds the
+    gather of the positions into the lists' order and the conditional rebuild, and
+    one kernel (k_rbl_vsel) classifies the candidates and draws the batch, so the
+    selection stage is empty; without them the cell walk scans (k_rbl_scan) and a
+    second kernel selects (k_rbl_select)."""
+    if not candidates:
+        return dict(stages)
+    out = {}
+    for k, v in stages.items():
+        if k == "rbl_select":
+            continue
+        out[{"cell_sort": "cand_gather_rebuild", "rbl_scan": "rbl_classify_select"}.get(k, k)] = v
+    return out
 
 
 def roofline(stages_ms_per_step, system, peaks_clock_mhz):
@@ -329,15 +349,18 @@ def roofline(stages_ms_per_step, system, peaks_clock_mhz):
         "rbe_force": N * P * OPS_FORCE_PER_ATOM_MODE,
         "rbl_scan": N * OPS_CLASSIFY_PER_NEIGHBOUR * (core + shell),
         "rbl_select": N * OPS_PHILOX * shell,
+        # classification of the in-range neighbours and a priority per shell member
+        "rbl_classify_select": N * (OPS_CLASSIFY_PER_NEIGHBOUR * (core + shell) + OPS_PHILOX * shell),
         "rbl_force": N * OPS_PAIR * (core + min(shell, p)),
     }
+    ops = {k: v for k, v in ops.items() if stages_ms_per_step.get(k, 0.0) > 0}
     top = max(ops, key=lambda k: stages_ms_per_step.get(k, 0.0))
     t = stages_ms_per_step[top] * 1e-3
     clock = 2032.0 if not peaks_clock_mhz else peaks_clock_mhz
     peak = SM_COUNT[0] * 128 * clock * 1e6 / 1e12  # Top/s, one FP32 lane-op per lane per clock
     achieved = ops[top] / t / 1e12
-    traffic = captured_traffic().get(top) if (N == 1_000_000 and WORKLOAD[0] == "c3") else None
-    cap = captured_traffic() if (N == 1_000_000 and WORKLOAD[0] == "c3") else {}
+    cap = captured_traffic(N) if (WORKLOAD[0] == "c3" and system.R == 1) else {}
+    traffic = cap.get(top)
     every = {}
     for k, n_ops in ops.items():
         ms = stages_ms_per_step.get(k, 0.0)
@@ -536,7 +559,7 @@ def run_ours(args):
     # between the stages (the stages then run one after another on one stream)
     ms_prof, stages = time_steps(ctx, args.steps, 2, flush, profile=True)
     ctx.profile(False)
-    stage_ms = {k: v / args.steps for k, v in stages.items()}
+    stage_ms = step_stage_names({k: v / args.steps for k, v in stages.items()}, rebuilds > 0)
 
     fb = None
     if not args.skip_fwd_bwd and system.R == 1:
@@ -562,6 +585,7 @@ def run_ours(args):
             shape64 = c64.autotune(step=0)  # the FP64 kernels have their own best shape
         ms64, _ = time_steps(c64, args.fp64_steps, 2, flush, profile=False)
         _, st64 = time_steps(c64, args.fp64_steps, 1, flush, profile=True)
+        st64 = step_stage_names(st64, c64.candidate_rebuilds() > 0)
         c64.close()
         m64 = sum(ms64) / len(ms64)
         fp64 = {"ms_per_step": round(m64, 4), "atom_steps_per_s": args.n / (m64 * 1e-3),

@@ -1635,6 +1635,7 @@ struct VlArgs {
     int32_t *flag;        // rebuild pending
     int32_t *nrebuild;
     int cv, ccs;
+    int core_rows;        // max(ccs, p): rows of k_rbl_vsel's core-id array
 };
 
 
@@ -1761,26 +1762,34 @@ __device__ __noinline__ void vl_select_exact(const Philox0 &r0, uint2 key, const
 
 // Algorithm 2 step 1 for the step: classification of the candidates, N_s, the
 // batch and the core list, one thread per sorted atom (128 per block).  The shell
-// is never stored: the Philox priority of every candidate of a round is computed
-// with the round (four interleaved chains, used for the shell members only) and
-// the bottom-p keys of select_atom are kept in registers, keyed by the
-// candidate's position in the list, so a winner's sorted index is its candidate
-// entry.  Shared memory holds the core members' replica-local ids,
-// [max(ccs, p)][128] int32, put in id order.  Outputs: lcore and bk rows (sorted
-// indices) and ncount, read by k_rbl_force.  An atom beyond a capacity is marked
-// overflowed for the exact fallback.
+// is never stored.  A lane classifies four candidates per round and queues its
+// shell members (replica-local id, candidate position) in a 16-entry ring in
+// shared memory; the warp computes Philox priorities four per lane at once (four
+// interleaved chains) when every lane has four queued or has finished its list,
+// or when some lane's ring is three-quarters full, so that the priorities are
+// computed for shell members only and mostly with all lanes busy.  The bottom-p
+// keys of select_atom are kept in registers, keyed by the candidate's position
+// in the list, so a winner's sorted index is its candidate entry; the kept set
+// does not depend on the order the keys arrive in.  Shared memory: the core
+// members' replica-local ids, [max(ccs, p)][128] int32, put in id order, then the
+// rings, [16][128] uint2.  Outputs: lcore and bk rows (sorted indices) and
+// ncount, read by k_rbl_force.  An atom beyond a capacity is marked overflowed
+// for the exact fallback.
 template <typename real, int CAP>
 __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
 {
     extern __shared__ int32_t s_vl[];
+    constexpr unsigned FULL = 0xFFFFFFFFu;
+    // every lane runs to the end: the warp votes on when to compute priorities
     const AtomSlot sl = atom_slot(a.map, a.reps);
-    if (!sl.ok) return;
     const int64_t is = sl.i;
     const Rep rp = a.reps[sl.r];
-    const uint4 A = a.spos[is];
+    const uint4 A = sl.ok ? a.spos[is] : make_uint4(0u, 0u, 0u, 0u);
     const uint32_t id0 = (uint32_t)rp.atom0;
     int32_t *s_core = s_vl + threadIdx.x;
-    const int n = v.ncand[is];
+    uint2 *s_ring = reinterpret_cast<uint2 *>(s_vl + v.core_rows * 128) + threadIdx.x;
+    const int n_all = sl.ok ? v.ncand[is] : 0;
+    const int n = n_all <= v.cv ? n_all : 0;  // beyond the capacity: the fallback
     const int32_t *cl = v.cand + vl_slot(is, 0, v.cv);
     const Philox0 r0 = philox_round0(A.w - id0, (uint32_t)step_of(a.step), rp.tag_rbl, rp.key);
     const PhiloxKeys K = philox_keys(rp.key);
@@ -1792,10 +1801,36 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
 #pragma unroll
     for (int e = 0; e <= CAP; ++e) sk[e] = 0xFFFFFFFFu;
     int nc = 0, ns = 0;
-    if (n <= v.cv) {
+    int head = 0, cnt = 0;  // the ring holds entries head .. head + cnt - 1 (mod 16)
+    // up to four queued members: their priorities, their keys into the kept set
+    auto drain4 = [&]() {
+        uint32_t id4[4], t4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint2 e = q < cnt ? s_ring[((head + q) & 15) * 128] : make_uint2(0u, FULL);
+            id4[q] = e.x;
+            t4[q] = e.y;
+        }
+        const int took = min(cnt, 4);
+        head += took;
+        cnt -= took;
+        uint2 w[4];
+        philox_rest4(r0, id4, K, w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t x = t4[q] != FULL ? (w[q].x & keep) | t4[q] : FULL;
+#pragma unroll
+            for (int j = 0; j <= CAP; ++j) {
+                const uint32_t m = min(sk[j], x);
+                x = max(sk[j], x);
+                sk[j] = m;
+            }
+        }
+    };
+    {
         // four candidates per round: their positions are gathered one round
         // ahead and their indices (one coalesced row of the warp each) two rounds
-        // ahead, so the gathers overlap the previous round's Philox work
+        // ahead, so the gathers overlap the previous round's work
         constexpr int VB = 4;
         int kk[VB];
         uint4 Bn[VB];
@@ -1805,7 +1840,7 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
             Bn[q] = k0 >= 0 ? a.spos[RBMD_IDX(k0, a.N, a.err)] : A;
             kk[q] = VB + q < n ? cl[(VB + q) * 32] : -1;
         }
-        for (int t0 = 0; t0 < n; t0 += VB) {
+        for (int t0 = 0; __any_sync(FULL, t0 < n); t0 += VB) {
             uint4 B[VB];
 #pragma unroll
             for (int q = 0; q < VB; ++q) {
@@ -1813,38 +1848,28 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
                 Bn[q] = kk[q] >= 0 ? a.spos[RBMD_IDX(kk[q], a.N, a.err)] : A;
                 kk[q] = t0 + 2 * VB + q < n ? cl[(t0 + 2 * VB + q) * 32] : -1;
             }
-            bool sh[VB];
-            uint32_t ids[VB];
 #pragma unroll
             for (int q = 0; q < VB; ++q) {
                 const int cls = t0 + q < n ? classify_near(rp, A, B[q]) : 0;
-                ids[q] = B[q].w - id0;
+                const uint32_t id = B[q].w - id0;
                 if (cls == 1) {
-                    if (nc < v.ccs) s_core[nc * 128] = (int32_t)ids[q];
+                    if (nc < v.ccs) s_core[nc * 128] = (int32_t)id;
                     ++nc;
-                }
-                sh[q] = cls == 2;
-                ns += sh[q] ? 1 : 0;
-            }
-#pragma unroll
-            for (int h = 0; h < VB; h += 4) {
-                const uint32_t id4[4] = {ids[h], ids[h + 1], ids[h + 2], ids[h + 3]};
-                uint2 w[4];
-                philox_rest4(r0, id4, K, w);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t x = sh[h + q] ? (w[q].x & keep) | (uint32_t)(t0 + h + q) : 0xFFFFFFFFu;
-#pragma unroll
-                    for (int j = 0; j <= CAP; ++j) {
-                        const uint32_t m = min(sk[j], x);
-                        x = max(sk[j], x);
-                        sk[j] = m;
-                    }
+                } else if (cls == 2) {
+                    s_ring[((head + cnt) & 15) * 128] = make_uint2(id, (uint32_t)(t0 + q));
+                    ++cnt;
+                    ++ns;
                 }
             }
+            // before the pushes every ring holds at most 11 (else the warp drained
+            // four from each), so it never exceeds 15
+            const bool go = __all_sync(FULL, cnt >= 4 || t0 + VB >= n) | __any_sync(FULL, cnt >= 12);
+            if (go) drain4();
         }
+        while (__any_sync(FULL, cnt > 0)) drain4();
     }
-    if (n > v.cv || nc > v.ccs || nc > a.CC) {
+    if (!sl.ok) return;
+    if (n_all > v.cv || nc > v.ccs || nc > a.CC) {
         a.ncount[is] = make_int2(a.CC + 1, 0);
         *a.ovf = 1;
         return;
@@ -1895,6 +1920,7 @@ static VlArgs vl_args(rbmd_ctx *c)
     v.nrebuild = c->ibuf + 5;
     v.cv = c->vl_cv;
     v.ccs = c->vl_ccs;
+    v.core_rows = std::max(c->vl_ccs, c->prm.rbl_p);
     return v;
 }
 
@@ -1923,7 +1949,8 @@ rbmd_status verlet_prepare(rbmd_ctx *c)
 
 static size_t vl_smem(const rbmd_ctx *c)
 {
-    return (size_t)std::max(c->vl_ccs, c->prm.rbl_p) * 128 * sizeof(int32_t);
+    return (size_t)std::max(c->vl_ccs, c->prm.rbl_p) * 128 * sizeof(int32_t) +
+           (size_t)16 * 128 * sizeof(uint2);
 }
 
 template <typename real, int CAP>
