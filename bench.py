@@ -532,6 +532,7 @@ def run_ours(args):
     free0 = torch.cuda.mem_get_info(device)[0]
     ctx = make_ctx(system, rb.FP32, device)
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()  # the input tensors' blocks: the context keeps its own copies
     footprint = free0 - torch.cuda.mem_get_info(device)[0]
     tiles = {"shape": ctx.tiles(), "autotuned": False}
     if not args.no_autotune:

@@ -297,7 +297,9 @@ class RBMD:
                                          _ptr(eps), _ptr(sigma), C.c_void_p(stream.cuda_stream),
                                          C.byref(h)), "rbmd_init_batch")
         self._h = h
-        self._keep = (pos, charge, vel, types)
+        # the context copied the inputs on `stream`; once that work is done the
+        # caller's tensors (and any converted copies made here) can go
+        stream.synchronize()
 
     # -- lifetime ---------------------------------------------------------
     def close(self):

@@ -35,6 +35,12 @@ rbmd_status dev_alloc(void **p, size_t bytes)
     return RBMD_OK;
 }
 
+// Entries of the step's candidate lists ([ceil(N/32)][cv][32] int32), 0 without them.
+static size_t cand_entries(const rbmd_ctx *c)
+{
+    return c->verlet ? (size_t)((c->N + 31) / 32) * 32 * c->vl_cv : 0;
+}
+
 template <typename T> rbmd_status alloc_n(T **p, size_t n)
 {
     return dev_alloc(reinterpret_cast<void **>(p), n * sizeof(T));
@@ -260,7 +266,8 @@ void free_ctx(rbmd_ctx *c)
                     c->lcore,     c->lshell,    c->ncount,   c->bk,         c->red_tmp,
                     c->adj_lj,    c->adj_tpart, c->adj_tsum, c->reps,       c->map256,
                     c->map128,    c->tiles,     c->red_rep,   c->ptab,       c->heavy,
-                    c->modes0,    c->acc,       c->chain_step, c->phtab,      c->vl_cand,
+                    c->modes0,    c->acc,       c->chain_step, c->phtab,
+                    c->vl_cand != c->lshell ? c->vl_cand : nullptr,
                     c->vl_ncand,  c->vl_sref,   c->rho_acc,   c->gid};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -727,9 +734,10 @@ rbmd_status init_ctx(const rbmd_params *prms, int32_t R, const void *pos, const 
     }
     if (!c->verlet)
         for (int r = 0; r < R; ++r) c->reps_h[r].Rv = c->reps_h[r].Rlin;
-    // capacities: candidates mean + 5 sd + 8; the core members a thread keeps in
-    // shared memory mean + 5 sd + 4 (beyond them: the exact fallback)
-    c->vl_cv = ((int)ceil(max_mv + 5.0 * sqrt(max_mv) + 8.0) + 3) / 4 * 4;
+    // capacities: candidates mean + 4 sd + 8 (a liquid's counts vary less than
+    // Poisson's); the core members a thread keeps in shared memory mean + 5 sd + 4
+    // (beyond them: the exact fallback)
+    c->vl_cv = ((int)ceil(max_mv + 4.0 * sqrt(max_mv) + 8.0) + 3) / 4 * 4;
     c->vl_ccs = (int)ceil(max_mc + 5.0 * sqrt(max_mc) + 4.0);
     if (std::max(c->vl_ccs, p.rbl_p) * 128 * 4 > 160 * 1024) c->verlet = false;
     c->vl_dirty = true;
@@ -743,10 +751,10 @@ rbmd_status init_ctx(const rbmd_params *prms, int32_t R, const void *pos, const 
     c->nb256 = (int)m256.size();
     c->nb128 = (int)m128.size();
     c->pair_parts = 2 * 4 * c->nb128;  // per warp: pair kernel, then the fallback
-    // list capacities: mean + 8 sd + 8 of a uniform fluid at the densest
-    // replica's density, rounded up to a multiple of 4; atoms beyond them take
-    // the exact fallback
-    c->list_cc = ((int)ceil(max_mc + 8.0 * sqrt(max_mc) + 8.0) + 3) / 4 * 4;
+    // list capacities: mean + 5 sd + 8 (core) and mean + 8 sd + 8 (shell) of a
+    // uniform fluid at the densest replica's density, rounded up to a multiple of
+    // 4; atoms beyond them take the exact fallback
+    c->list_cc = ((int)ceil(max_mc + 5.0 * sqrt(max_mc) + 8.0) + 3) / 4 * 4;
     c->list_cs = ((int)ceil(max_ms + 8.0 * sqrt(max_ms) + 8.0) + 3) / 4 * 4;
     // RBMD_SELECT_EXACT=1 sends every batch selection through the exact path that
     // otherwise only atoms with equal priority words take, so that tests reach it
@@ -825,7 +833,10 @@ rbmd_status init_ctx(const rbmd_params *prms, int32_t R, const void *pos, const 
     TRY(alloc_n(&c->stype, N));
     TRY(alloc_n(&c->fpart, 3 * (size_t)c->pair_parts));
     TRY(alloc_n(&c->lcore, (size_t)N * c->list_cc));
-    TRY(alloc_n(&c->lshell, (size_t)N * c->list_cs));
+    // the cell walk's shell lists and the step's candidate lists share one array: a
+    // cell walk re-sorts the atoms, which makes the candidates stale anyway (every
+    // cell walk marks them for a rebuild before the next step)
+    TRY(alloc_n(&c->lshell, std::max((size_t)N * c->list_cs, cand_entries(c))));
     TRY(alloc_n(&c->ncount, (size_t)N));
     TRY(alloc_n(&c->bk, (size_t)N * p.rbl_p));
     if (p.rbl_p > 10) TRY(alloc_n(&c->heavy, (size_t)N));
@@ -842,7 +853,7 @@ rbmd_status init_ctx(const rbmd_params *prms, int32_t R, const void *pos, const 
                                         c->stream)));
     }
     if (c->verlet) {
-        TRY(alloc_n(&c->vl_cand, (size_t)((N + 31) / 32) * 32 * c->vl_cv));
+        c->vl_cand = c->lshell;
         TRY(alloc_n(&c->vl_ncand, (size_t)N));
         TRY(alloc_n(&c->vl_sref, (size_t)N));
     }
@@ -1460,7 +1471,7 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
             const int cc = (max(h[0], c->list_cc) + 8 + 3) / 4 * 4, cs = (max(h[1], c->list_cs) + 8 + 3) / 4 * 4;
             uint32_t *lc = nullptr, *ls = nullptr;
             if (dev_alloc((void **)&lc, sizeof(int32_t) * (size_t)c->N * cc) != RBMD_OK ||
-                dev_alloc((void **)&ls, sizeof(int32_t) * (size_t)c->N * cs) != RBMD_OK) {
+                dev_alloc((void **)&ls, sizeof(int32_t) * std::max((size_t)c->N * cs, cand_entries(c))) != RBMD_OK) {
                 if (lc) cudaFree(lc);
                 return leave(c, RBMD_ERR_OOM);
             }
@@ -1468,6 +1479,8 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
             cudaFree(c->lshell);
             c->lcore = (int32_t *)lc;
             c->lshell = (int32_t *)ls;
+            if (c->verlet) c->vl_cand = c->lshell;  // shared (the lists were rebuilt anyway)
+            c->vl_dirty = true;
             c->list_cc = cc;
             c->list_cs = cs;
             if (c->graph_ready) {  // the step graph holds the old list pointers
