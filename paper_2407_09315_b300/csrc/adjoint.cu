@@ -5,9 +5,11 @@
 // the gradient of its energy expressions (Eqs. 2, 4, 8, 10 with the random-batch
 // estimators of Eqs. 12 and 15):
 //   E_RBL = 1/2 sum_i sum_j W_ij u_ij,  W_ij = 1 (j in C(i)), N_s(i)/p (j in B(i));
-// since the lists are one-sided, dE/dr_k = sum_j 1/2 (W_kj + W_jk) u'(r_kj) r_hat,
-// which needs, for every shell neighbour j of k, whether k is in j's batch: the
-// kernel reads j's batch from the lists the forward pass built.
+// since the lists are one-sided, dE/dr_k = sum_j 1/2 (W_kj + W_jk) u'(r_kj) r_hat.
+// W_jk is nonzero for a shell neighbour j of k only when k is in j's batch, so the
+// kernel walks three lists per atom: its core (weight 1 both ways), its batch
+// (1/2 W_kj) and its reverse batch, the atoms whose batch holds k (1/2 W_jk),
+// built by scattering every batch entry before the kernel runs.
 #include <math.h>
 
 #include "rbmd_internal.cuh"
@@ -42,6 +44,9 @@ template <typename real> struct AdjArgs {
     const real *sq;
     const int32_t *stype;
     const int32_t *lcore, *lshell, *bk;  // per-atom lists, entry e of atom i at lidx(i, e, N, cap)
+    int32_t *rb;                         // reverse batches, [N][CS] sorted indices (each row
+                                         // sorted in place by its own atom's thread)
+    const int32_t *rbn;                  // reverse-batch counts
     const int32_t *sidx;                 // sorted index of every atom (by global id)
     const int2 *ncount;
     int64_t N;
@@ -61,24 +66,6 @@ __device__ __forceinline__ float sqrt_a(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_a(double x) { return sqrt(x); }
 
 constexpr int ADJ_BLOCK = 128;
-
-// true if sorted index x is one of the n entries of a batch row (p entries,
-// rows of an even length are read 8 bytes at a time)
-__device__ __forceinline__ bool in_batch_row(const int32_t *row, int n, int p, int32_t x)
-{
-    bool hit = false;
-    if ((p & 1) == 0) {
-        const int2 *r2 = reinterpret_cast<const int2 *>(row);
-        for (int b = 0; b < n; b += 2) {
-            const int2 v = r2[b >> 1];
-            hit |= v.x == x;
-            hit |= (b + 1 < n) & (v.y == x);
-        }
-    } else {
-        for (int b = 0; b < n; ++b) hit |= row[b] == x;
-    }
-    return hit;
-}
 
 // acc[t] += v for a run-time type t < TT: TT <= 8 keeps the accumulators in
 // registers (an unrolled select), larger TT index an array.
@@ -131,22 +118,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
         const int64_t N = a.N;
         const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
         real gx = 0, gy = 0, gz = 0, gq = 0;
-        const int ntot = cnt.x + cnt.y;
-        for (int e = 0; e < ntot; ++e) {
-            const bool core = e < cnt.x;
-            const int js = core ? a.lcore[lidx(ks, e, N, a.CC)]
-                                : a.sidx[id0 + (uint32_t)a.lshell[lidx(ks, e - cnt.x, N, a.CS)]];
-            real Wkj = 1, Wjk = 1;
-            if (!core && !a.exact) {
-                Wkj = in_batch_row(a.bk + lidx(ks, 0, N, a.p), nbk, a.p, js) ? wk : (real)0;
-                const int2 cj = a.ncount[js];
-                const int nbj = min(cj.y, a.p);
-                Wjk = in_batch_row(a.bk + lidx(js, 0, N, a.p), nbj, a.p, (int32_t)ks)
-                          ? (cj.y > a.p ? (real)cj.y / (real)a.p : (real)1)
-                          : (real)0;
-            }
-            const real W = (real)0.5 * (Wkj + Wjk);
-            if (W == (real)0 && Wkj == (real)0) continue;
+        // one pair (k, js): W the symmetric weight of dE/dr and dE/dq, Wkj the
+        // one-sided weight of the type sums (0: counted from js's side)
+        auto pair = [&](int32_t js, real W, real Wkj) {
             const uint4 B = a.spos[js];
             const real dx = (real)(int32_t)(B.x - A.x) * lscale;  // r_j - r_k
             const real dy = (real)(int32_t)(B.y - A.y) * lscale;
@@ -190,6 +164,32 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
                 acc_add<real, TT>(acc, TT + tk, hw * dus * (real)0.5);
                 acc_add<real, TT>(acc, TT + tj, hw * dus * (real)0.5);
             }
+        };
+        for (int e = 0; e < cnt.x; ++e) pair(a.lcore[lidx(ks, e, N, a.CC)], (real)1, (real)1);
+        if (a.exact) {
+            for (int e = 0; e < cnt.y; ++e)
+                pair(a.sidx[id0 + (uint32_t)a.lshell[lidx(ks, e, N, a.CS)]], (real)1, (real)1);
+        } else {
+            for (int e = 0; e < nbk; ++e) pair(a.bk[lidx(ks, e, N, a.p)], (real)0.5 * wk, wk);
+            // the reverse batch in ascending sorted index (the scatter's order is not
+            // fixed): sorted in place, one row per thread
+            int32_t *rrow = a.rb + lidx(ks, 0, N, a.CS);
+            const int nrb = min(a.rbn[ks], a.CS);
+            for (int e = 1; e < nrb; ++e) {
+                const int32_t x = rrow[e];
+                int y = e - 1;
+                while (y >= 0 && rrow[y] > x) {
+                    rrow[y + 1] = rrow[y];
+                    --y;
+                }
+                rrow[y + 1] = x;
+            }
+            for (int e = 0; e < nrb; ++e) {
+                const int32_t js = rrow[e];
+                const int2 cj = a.ncount[js];
+                const real wj = cj.y > a.p ? (real)cj.y / (real)a.p : (real)1;
+                pair(js, (real)0.5 * wj, (real)0);
+            }
         }
         const int64_t id = A.w;
         if (a.dpos) {
@@ -217,13 +217,34 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
     }
 }
 
+// Reverse batches: for every batch entry j of atom k (sorted indices), k is
+// appended to j's row.  A batch member is a shell member and the shell relation is
+// symmetric, so a row never holds more than N_s(j) <= CS entries on complete lists;
+// a count beyond CS latches an error instead of writing.
+template <typename real>
+__global__ void k_adj_reverse_batches(AdjArgs<real> a, int32_t *__restrict__ rb,
+                                      int32_t *__restrict__ rbn, int *__restrict__ err)
+{
+    const AtomSlot sl = atom_slot(a.map, a.reps);
+    if (!sl.ok) return;
+    const int64_t ks = sl.i;
+    const int nb = min(a.ncount[ks].y, a.p);
+    for (int e = 0; e < nb; ++e) {
+        const int32_t j = a.bk[lidx(ks, e, a.N, a.p)];
+        const int pos = atomicAdd(rbn + j, 1);
+        if (pos < a.CS) rb[lidx(j, pos, a.N, a.CS)] = (int32_t)ks;
+        else latch_error(err, RBMD_ERR_CELL_OVERFLOW);
+    }
+}
+
 // RBE part: dE/dr_i = -F_i (Eq. 12) and dE/dq_i = -sum_l (B_l cos th + A_l sin th),
 // with the coefficients of the forward pass (A = c Im rho, B = c Re rho).
 template <typename real, int CHUNK>
 __global__ void k_rbe_adjoint(const uint4 *__restrict__ u4, const double *__restrict__ q64,
                               const int2 *__restrict__ map, const Rep *__restrict__ reps,
                               const ModeCoef<real> *__restrict__ coef_all, int64_t Pm, double g,
-                              real *__restrict__ dpos, real *__restrict__ dq)
+                              const double2 *__restrict__ ptab, real *__restrict__ dpos,
+                              real *__restrict__ dq)
 {
     __shared__ ModeCoef<real> s_c[CHUNK];
     const AtomSlot sl = atom_slot(map, reps);
@@ -243,10 +264,8 @@ __global__ void k_rbe_adjoint(const uint4 *__restrict__ u4, const double *__rest
             const ModeCoef<real> mc = s_c[k];
             const uint32_t ph = (uint32_t)mc.mx * A.x + (uint32_t)mc.my * A.y + (uint32_t)mc.mz * A.z;
             real sn, cs;
-            if constexpr (sizeof(real) == 4)
-                sincospif((float)(int32_t)ph * 4.656612873077392578125e-10f, (float *)&sn, (float *)&cs);
-            else
-                sincospi((double)(int32_t)ph * 4.656612873077392578125e-10, (double *)&sn, (double *)&cs);
+            if constexpr (sizeof(real) == 4) phase_sincos(ph, sn, cs);  // as the force pass
+            else phase_sincos_tab(ptab, ph, sn, cs);
             const real gg = mc.A * cs - mc.B * sn;
             fx += gg * mc.kx;
             fy += gg * mc.ky;
@@ -306,6 +325,16 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
         a.dq = (real *)dq;
         a.tpart = c->adj_tpart;
         const unsigned nba = (unsigned)c->nb128;
+        // reverse batches in the shell-list array (the adjoint does not read the
+        // shell list outside exact mode) and their counts in the scratch array
+        int32_t *rb = c->lshell, *rbn = (int32_t *)c->scratch_force;
+        a.rb = rb;
+        a.rbn = rbn;
+        if (!a.exact) {
+            RBMD_CHECK_CUDA(cudaMemsetAsync(rbn, 0, sizeof(int32_t) * (size_t)c->N, c->stream));
+            k_adj_reverse_batches<real><<<nba, ADJ_BLOCK, 0, c->stream>>>(a, rb, rbn, c->err);
+            RBMD_LAUNCH_CHECK();
+        }
         if (c->T <= 4) k_rbl_adjoint<real, 4><<<nba, ADJ_BLOCK, 0, c->stream>>>(a);
         else if (c->T <= 16) k_rbl_adjoint<real, 16><<<nba, ADJ_BLOCK, 0, c->stream>>>(a);
         else k_rbl_adjoint<real, RBMD_MAX_TYPES><<<nba, ADJ_BLOCK, 0, c->stream>>>(a);
@@ -319,11 +348,11 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
         if constexpr (sizeof(real) == 4)
             k_rbe_adjoint<float, 256><<<c->nb256, 256, 0, c->stream>>>(
                 c->u4, nullptr, c->map256, c->reps, (const ModeCoef<float> *)c->coef, c->Pm, g,
-                (float *)dpos, (float *)dq);
+                nullptr, (float *)dpos, (float *)dq);
         else
             k_rbe_adjoint<double, 128><<<c->nb256, 256, 0, c->stream>>>(
                 c->u4, c->q64, c->map256, c->reps, (const ModeCoef<double> *)c->coef, c->Pm, g,
-                (double *)dpos, (double *)dq);
+                c->phtab, (double *)dpos, (double *)dq);
         RBMD_LAUNCH_CHECK();
     }
     (void)eps_h;

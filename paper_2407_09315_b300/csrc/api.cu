@@ -1114,6 +1114,7 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     if (n_steps == 0) return RBMD_OK;
     enter(c);
+    c->lists_cached = c->rho_cached = false;
     rbmd_status s = RBMD_OK;
     if (c->verlet && c->vl_dirty) {
         // the sorted layout was changed outside the step: rebuild the candidates
@@ -1275,6 +1276,16 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
     if (s != RBMD_OK) return s;
     gprof_collect(c, 0, RBMD_PROFILE_FWD_STAGES);
     RBMD_CHECK(check_latched(c));
+    // the lists (complete when no atom overflowed: hi[2]) and the modes and
+    // structure factors of this state and step stay for rbmd_energy_backward
+    if (!(c->prm.flags & RBMD_NO_RBL) && hi[2] == 0) {
+        c->lists_cached = true;
+        c->lists_step = step;
+    }
+    if (!(c->prm.flags & RBMD_NO_RBE)) {
+        c->rho_cached = true;
+        c->rho_step = step;
+    }
     for (int q = 0; q < R; ++q) {
         const double *hr = h.data() + (size_t)q * SCAL_COUNT;
         const Rep &rp = c->reps_h[q];
@@ -1454,7 +1465,7 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
     StepRef r{nullptr, step};
     rbmd_status s = RBMD_OK;
     gprof_mark(c, 0);
-    if (!(c->prm.flags & RBMD_NO_RBL)) {
+    if (!(c->prm.flags & RBMD_NO_RBL) && !(c->lists_cached && c->lists_step == step)) {
         // complete lists of the step: grow the capacities until nothing overflows
         for (int attempt = 0; attempt < 8; ++attempt) {
             s = cells_build(c);
@@ -1490,12 +1501,13 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
         }
     }
     gprof_mark(c, 1);
-    if (!(c->prm.flags & RBMD_NO_RBE)) {
+    if (!(c->prm.flags & RBMD_NO_RBE) && !(c->rho_cached && c->rho_step == step)) {
         s = rbe_sample(c, r);
         if (s == RBMD_OK) s = rbe_structure_factors(c);
         if (s != RBMD_OK) return leave(c, s);
     }
     s = adjoint_run(c, grad_out, d_pos, d_q, c->adj_tsum);  // marks stages 2-4
+    c->lists_cached = false;  // the reverse batches took the shell lists' array
     gprof_mark(c, 5);
     if (s == RBMD_OK && (d_eps || d_sigma)) {
         std::vector<double> h(2 * c->T);
@@ -1527,6 +1539,7 @@ rbmd_status rbmd_set_charges(rbmd_ctx *c, const void *charge)
     rbmd_status s = charge_sums(c, false);
     c->have_force = false;
     c->vl_dirty = true;
+    c->lists_cached = c->rho_cached = false;
     return leave(c, s);
 }
 
@@ -1622,6 +1635,7 @@ rbmd_status rbmd_set_state_u(rbmd_ctx *c, const uint32_t *u, const void *vel, in
     c->step = step;
     c->have_force = false;
     c->vl_dirty = true;
+    c->lists_cached = c->rho_cached = false;
     return leave(c, s);
 }
 

@@ -448,6 +448,7 @@ __global__ void k_decode(const uint4 *__restrict__ u4, const real *__restrict__ 
 
 rbmd_status md_encode_positions(rbmd_ctx *c, const void *pos)
 {
+    c->lists_cached = c->rho_cached = false;
     if (c->fp64) k_encode<double><<<c->nb256, 256, 0, c->stream>>>((const double *)pos, c->map256, c->reps, c->u4);
     else k_encode<float><<<c->nb256, 256, 0, c->stream>>>((const float *)pos, c->map256, c->reps, c->u4);
     RBMD_LAUNCH_CHECK();
@@ -457,6 +458,7 @@ rbmd_status md_encode_positions(rbmd_ctx *c, const void *pos)
 // The same for the atoms of the 256-atom blocks [b0, b1) of map256.
 rbmd_status md_encode_blocks(rbmd_ctx *c, const void *pos, int b0, int b1)
 {
+    c->lists_cached = c->rho_cached = false;
     if (b1 <= b0) return RBMD_OK;
     const unsigned nb = (unsigned)(b1 - b0);
     if (c->fp64) k_encode<double><<<nb, 256, 0, c->stream>>>((const double *)pos, c->map256 + b0, c->reps, c->u4);

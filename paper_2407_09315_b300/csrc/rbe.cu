@@ -187,6 +187,7 @@ rbmd_status rbe_metropolis_init(rbmd_ctx *c)
 
 rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
 {
+    c->rho_cached = false;
     if (c->full_modes) return RBMD_OK;  // fixed list built at init
     const int threads = 128;
     if (c->modes0) {
@@ -216,15 +217,6 @@ rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
 // same atom: a shared-memory broadcast.  The sub-tile sums are combined in FP64
 // in a fixed order and one partial per (atom tile, mode) goes to HBM.
 // --------------------------------------------------------------------------
-// sin and cos of the wrapped phase 2 pi ph / 2^32.  ph is read as a signed
-// fraction of a turn, so the angle lies in [-pi, pi): there the hardware SFU
-// sin/cos (__sincosf) needs no range reduction and its documented absolute error
-// is at most 2^-21.41.  The FP64 kernels use phase_sincos_tab below.
-__device__ __forceinline__ void phase_sincos(uint32_t ph, float &s, float &c)
-{
-    __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &s, &c);  // 2 pi / 2^32
-}
-
 // FP64 phase factors by angle addition.  The phase is an exact 32-bit fraction of
 // a turn, so with ph = h 2^16 + l, e^{i theta} = T[h] T'[l] where
 // T[h] = e^{2 pi i h/2^16} and T'[l] = e^{2 pi i l/2^32}: two reads of a 2 MB
@@ -234,6 +226,7 @@ __device__ __forceinline__ void phase_sincos(uint32_t ph, float &s, float &c)
 // place.  Layout: {cos, sin}, T at [0, 65536), T' at [65536, 131072).  (A
 // 10 + 11 + 11-bit split with an 80 KB table and two products measured slower:
 // the FP64 operations, not the table reads, bound these kernels.)
+// (phase_sincos_tab in rbmd_internal.cuh reads it.)
 constexpr int PHASE_TAB = 131072;
 
 __global__ void k_phase_table(double2 *__restrict__ tab)
@@ -244,15 +237,6 @@ __global__ void k_phase_table(double2 *__restrict__ tab)
     double s, c;
     sincospi(x, &s, &c);
     tab[j] = make_double2(c, s);
-}
-
-__device__ __forceinline__ void phase_sincos_tab(const double2 *__restrict__ tab, uint32_t ph,
-                                                 double &s, double &c)
-{
-    const double2 a = __ldg(tab + (ph >> 16));
-    const double2 d = __ldg(tab + 65536 + (ph & 65535u));
-    c = __fma_rn(a.x, d.x, -__dmul_rn(a.y, d.y));
-    s = __fma_rn(a.x, d.y, __dmul_rn(a.y, d.x));
 }
 
 // Explicitly rounded operations for the force passes: the same force must come out
@@ -513,6 +497,7 @@ rbmd_status rbe_configure(rbmd_ctx *c)
 // Partial sums of the tiles [t0, t1) (Eq. 9 per tile and mode).
 rbmd_status rbe_rho_partial(rbmd_ctx *c, int t0, int t1)
 {
+    c->rho_cached = false;
     if (t1 <= t0) return RBMD_OK;
     const int tile = c->rho_tile;
     const int mode_tile = (int)(c->Pm < c->rho_mode_tile ? c->Pm : c->rho_mode_tile);
@@ -537,6 +522,7 @@ rbmd_status rbe_rho_partial(rbmd_ctx *c, int t0, int t1)
 // rho of every mode from the tile partials, then the force-pass coefficients.
 rbmd_status rbe_rho_final(rbmd_ctx *c)
 {
+    c->rho_cached = false;
     const unsigned fin_blocks = (unsigned)(c->R * c->Pm);
     int max_tiles = 0;
     for (int r = 0; r < c->R; ++r) max_tiles = std::max(max_tiles, (int)c->reps_h[r].ntiles);
@@ -556,6 +542,7 @@ rbmd_status rbe_rho_final(rbmd_ctx *c)
 // rho and the coefficients from given exact sums (device [R][Pm][2] __int128).
 rbmd_status rbe_rho_from_acc(rbmd_ctx *c, const void *acc)
 {
+    c->rho_cached = false;
     const int64_t RPm = (int64_t)c->R * c->Pm;
     const unsigned nb = (unsigned)((RPm + 127) / 128);
     if (c->fp64)

@@ -206,6 +206,7 @@ rbmd_status cells_count_blocks(rbmd_ctx *c, int b0, int b1)
 // the next step); else every kernel checks *cond on the device.
 static rbmd_status cells_sort(rbmd_ctx *c, bool counted, const int32_t *cond)
 {
+    c->lists_cached = false;
     const int th = 256;
     const unsigned nb = (unsigned)((c->N + th - 1) / th);
     if (!counted) {
@@ -1642,6 +1643,7 @@ __global__ void k_max_counts(const int2 *__restrict__ cnt, int64_t N, int32_t *_
 
 rbmd_status rbl_lists(rbmd_ctx *c, StepRef s)
 {
+    c->lists_cached = false;
     if (c->fp64) return rbl_lists_t<double>(c, s);
     return rbl_lists_t<float>(c, s);
 }
@@ -1657,6 +1659,7 @@ rbmd_status rbl_max_counts(rbmd_ctx *c, int32_t *out_dev)
 rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
                       int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks)
 {
+    c->lists_cached = false;
     if (c->fp64)
         return rbl_pairs_t<double>(c, s, force, accumulate, energy, n_core, n_shell, batch, marks);
     return rbl_pairs_t<float>(c, s, force, accumulate, energy, n_core, n_shell, batch, marks);
@@ -1693,6 +1696,7 @@ __device__ __forceinline__ int64_t vl_slot(int64_t is, int t, int cv)
 {
     return (is >> 5) * (int64_t)cv * 32 + (int64_t)t * 32 + (is & 31);
 }
+
 
 // Positions of the current state in the sorted order of the last rebuild, and
 // the displacement test that asks for a rebuild.  Nothing to do when a rebuild is
@@ -2036,6 +2040,7 @@ static rbmd_status rbl_pairs_verlet_t(rbmd_ctx *c, StepRef s, void *force, bool 
 
 rbmd_status rbl_pairs_verlet(rbmd_ctx *c, StepRef s, void *force, bool marks)
 {
+    c->lists_cached = false;
     if (c->fp64) return rbl_pairs_verlet_t<double>(c, s, force, marks);
     return rbl_pairs_verlet_t<float>(c, s, force, marks);
 }

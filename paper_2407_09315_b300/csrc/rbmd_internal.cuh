@@ -102,6 +102,27 @@ __device__ __forceinline__ int64_t checked_index(int64_t i, int64_t n, int *err)
 #define RBMD_IDX(i, n, err) (i)
 #endif
 
+// sin and cos of the wrapped phase 2 pi ph / 2^32.  ph is read as a signed
+// fraction of a turn, so the angle lies in [-pi, pi): there the hardware SFU
+// sin/cos (__sincosf) needs no range reduction and its documented absolute error
+// is at most 2^-21.41.  The FP64 kernels use phase_sincos_tab below.
+__device__ __forceinline__ void phase_sincos(uint32_t ph, float &s, float &c)
+{
+    __sincosf((float)(int32_t)ph * 1.4629180792671596e-09f, &s, &c);  // 2 pi / 2^32
+}
+
+// FP64 phase factors by angle addition from the table of k_phase_table (rbe.cu):
+// with ph = h 2^16 + l, e^{i theta} = T[h] T'[l], T at [0, 65536), T' at
+// [65536, 131072), entries {cos, sin}.
+__device__ __forceinline__ void phase_sincos_tab(const double2 *__restrict__ tab, uint32_t ph,
+                                                 double &s, double &c)
+{
+    const double2 a = __ldg(tab + (ph >> 16));
+    const double2 d = __ldg(tab + 65536 + (ph & 65535u));
+    c = __fma_rn(a.x, d.x, -__dmul_rn(a.y, d.y));
+    s = __fma_rn(a.x, d.y, __dmul_rn(a.y, d.x));
+}
+
 // A named host range for profilers (nothing happens without one attached).
 struct NvtxRange {
     explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
@@ -299,6 +320,12 @@ struct rbmd_ctx {
     // neighbour candidates of the integrator's step (Verlet lists with a skin):
     // built from the cells at a rebuild, classified exactly every step
     bool verlet;          // the step uses them (skin > 0, p <= 16, batches not exact)
+    // what the list and mode arrays hold, so that rbmd_energy_backward right after
+    // rbmd_energy of the same state and step reuses them: set by rbmd_energy,
+    // cleared by every call that writes the lists, the modes or structure factors,
+    // the positions or the charges
+    bool lists_cached = false, rho_cached = false;
+    int64_t lists_step = 0, rho_step = 0;
     bool vl_dirty;        // the sorted layout changed outside the step: rebuild before the next
     double skin;
     int vl_cv;            // candidate capacity per atom

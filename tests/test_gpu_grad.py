@@ -150,3 +150,26 @@ def test_backward_grows_overflowing_lists(monkeypatch):
     ctx.step(2)
     ctx.sync()
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [rb.FP64, rb.FP32])
+def test_backward_after_energy_reuses_lists_and_modes(sys_g, prec):
+    """rbmd_energy_backward right after rbmd_energy of the same state and step reuses
+    the forward's lists, modes and structure factors; the gradients are the same bits
+    as a backward that builds its own (another call in between clears the reuse), and
+    two backward passes agree bit for bit (the reverse batches are summed in a fixed
+    order)."""
+    s = sys_g
+    ctx, _ = make_ctx(s, prec, **KW)
+    step = 4
+    ctx.rbe_modes(step + 1)  # other modes in the arrays: nothing to reuse
+    ctx.rbl_lists(step + 1)
+    cold = [g if isinstance(g, np.ndarray) else to_np(g) for g in ctx.energy_backward(step, 1.0)]
+    again = [g if isinstance(g, np.ndarray) else to_np(g) for g in ctx.energy_backward(step, 1.0)]
+    ctx.energy(step)
+    warm = [g if isinstance(g, np.ndarray) else to_np(g) for g in ctx.energy_backward(step, 1.0)]
+    ctx.energy(step + 1)  # a forward of another step is not reused for this one
+    other = [g if isinstance(g, np.ndarray) else to_np(g) for g in ctx.energy_backward(step, 1.0)]
+    for a, b, c, d in zip(cold, again, warm, other):
+        assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, d)
+    ctx.close()
