@@ -91,12 +91,14 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
     // type-pair factors of the eps and sigma derivatives (Eq. 4), TT <= 16:
     // [tk TT + tj] = 1/2 sqrt(eps_j / eps_k) and 1 / sigma_kj
     constexpr int TP = TT <= 16 ? TT * TT : 1;
-    __shared__ real s_er[TP], s_is[TP];
+    __shared__ real s_er[TP], s_is[TP], s_e[TP], s_s[TP];  // + eps_kj and sigma_kj (Eq. 4)
     if constexpr (TT <= 16) {
         for (int u = threadIdx.x; u < a.T * a.T; u += blockDim.x) {
             const int t1 = u / a.T, t2 = u % a.T;
             s_er[t1 * TT + t2] = (real)(0.5 * sqrt((double)a.eps[t2] / (double)a.eps[t1]));
             s_is[t1 * TT + t2] = (real)(1.0 / (0.5 * ((double)a.sig[t1] + (double)a.sig[t2])));
+            s_e[t1 * TT + t2] = sqrt_a(a.eps[t1] * a.eps[t2]);
+            s_s[t1 * TT + t2] = (real)0.5 * (a.sig[t1] + a.sig[t2]);
         }
         __syncthreads();
     }
@@ -118,6 +120,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
         const int64_t N = a.N;
         const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
         real gx = 0, gy = 0, gz = 0, gq = 0;
+        real ak_e = 0, ak_s = 0;  // the type sums of k's own type, added to acc at the end
         // one pair (k, js): W the symmetric weight of dE/dr and dE/dq, Wkj the
         // one-sided weight of the type sums (0: counted from js's side)
         auto pair = [&](int32_t js, real W, real Wkj) {
@@ -130,8 +133,14 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
             const real rinv = (real)1 / r;
             const int tj = a.stype[js];
             const real qj = a.sq[js];
-            const real eij = sqrt_a(a.eps[tk] * a.eps[tj]);
-            const real sij = (real)0.5 * (a.sig[tk] + a.sig[tj]);
+            real eij, sij;
+            if constexpr (TT <= 16) {
+                eij = s_e[tk * TT + tj];
+                sij = s_s[tk * TT + tj];
+            } else {
+                eij = sqrt_a(a.eps[tk] * a.eps[tj]);
+                sij = (real)0.5 * (a.sig[tk] + a.sig[tj]);
+            }
             const real s2 = sij * sij * rinv * rinv;
             const real s6 = s2 * s2 * s2, s12 = s6 * s6;
             const real er = erfc_a(a.sqrt_alpha * r);
@@ -159,9 +168,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
                     rkj = (real)0.5 * sqrt_a(a.eps[tj] / a.eps[tk]);
                     rjk = (real)0.5 * sqrt_a(a.eps[tk] / a.eps[tj]);
                 }
-                acc_add<real, TT>(acc, tk, hw * due * rkj);
+                ak_e += hw * due * rkj;
                 acc_add<real, TT>(acc, tj, hw * due * rjk);
-                acc_add<real, TT>(acc, TT + tk, hw * dus * (real)0.5);
+                ak_s += hw * dus * (real)0.5;
                 acc_add<real, TT>(acc, TT + tj, hw * dus * (real)0.5);
             }
         };
@@ -191,6 +200,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
                 pair(js, (real)0.5 * wj, (real)0);
             }
         }
+        acc_add<real, TT>(acc, tk, ak_e);
+        acc_add<real, TT>(acc, TT + tk, ak_s);
         const int64_t id = A.w;
         if (a.dpos) {
             a.dpos[3 * id] += (real)a.g * gx;

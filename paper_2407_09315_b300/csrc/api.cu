@@ -420,6 +420,19 @@ rbmd_status charge_sums(rbmd_ctx *c, bool check_neutral = true)
 // half kick; *kicked tells whether it ran.
 // verlet: the short-range part of the integrator's step on its candidate lists
 // (rbl_pairs_verlet); the same lists, batches and forces as the cell walk.
+// A force evaluation outside the step graph uses the candidate lists when the
+// context keeps them; after a cell walk or a new layout they are rebuilt first (on
+// the device, as in rbmd_step).  Returns whether to use them.
+static bool candidates_for_call(rbmd_ctx *c, int accumulate)
+{
+    if (!c->verlet || accumulate) return false;
+    if (c->vl_dirty) {
+        if (cudaMemsetAsync(c->ibuf + 4, 1, sizeof(int32_t), c->stream) != cudaSuccess) return false;
+        c->vl_dirty = false;
+    }
+    return true;
+}
+
 rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool apply_corr,
                         bool marks = false, const StepRef *kick = nullptr, bool *kicked = nullptr,
                         bool counted = false, bool verlet = false)
@@ -1009,7 +1022,9 @@ rbmd_status rbmd_forces(rbmd_ctx *c, int64_t step, void *force, int accumulate)
     if (!c || !force) return RBMD_ERR_INVALID;
     if (c->gid) return RBMD_ERR_UNSUPPORTED;  // slab contexts: the calls of rbmd_init_slab
     enter(c);
-    return leave(c, forces_into(c, StepRef{nullptr, step}, force, accumulate, true));
+    const bool vl = candidates_for_call(c, accumulate);
+    return leave(c, forces_into(c, StepRef{nullptr, step}, force, accumulate, true, false, nullptr,
+                                nullptr, false, vl));
 }
 
 rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t step)
@@ -1064,7 +1079,10 @@ rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t 
     cudaEventRecord(c->ev_fork, main);
     cudaStreamWaitEvent(c->copy, c->ev_fork, 0);
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-    st = cuda_status(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, main));
+    // the candidate lists (rebuilt on the device when an atom moved too far), else
+    // the cell walk with the atoms binned chunk by chunk as they arrive
+    const bool vl = candidates_for_call(c, 0);
+    if (!vl) st = cuda_status(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, main));
     on(c->side, [&] { return rbe_sample(c, s); });
     for (int k = 0; k < nch; ++k) {
         // positions of chunk k: copied in, encoded and binned, then its tiles' partial
@@ -1076,7 +1094,7 @@ rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t 
         cudaEventRecord(c->ev_h2d[k], c->copy);
         cudaStreamWaitEvent(main, c->ev_h2d[k], 0);
         if (st == RBMD_OK) st = md_encode_blocks(c, dev, B[k], B[k + 1]);
-        if (st == RBMD_OK) st = cells_count_blocks(c, B[k], B[k + 1]);
+        if (st == RBMD_OK && !vl) st = cells_count_blocks(c, B[k], B[k + 1]);
         cudaEventRecord(c->ev_enc[k], main);
         cudaStreamWaitEvent(c->side, c->ev_enc[k], 0);
         on(c->side, [&] { return rbe_rho_partial(c, T[k], T[k + 1]); });
@@ -1085,8 +1103,13 @@ rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t 
     cudaEventRecord(c->ev_join, c->side);
     // the short-range part (same kernels as rbmd_forces), then the RBE force pass
     // chunk by chunk, each chunk's forces copied out while the next is computed
-    if (st == RBMD_OK) st = cells_build(c, true);
-    if (st == RBMD_OK) st = rbl_pairs(c, s, dev, 0, false, nullptr, nullptr, nullptr);
+    if (vl) {
+        if (st == RBMD_OK) st = verlet_prepare(c);
+        if (st == RBMD_OK) st = rbl_pairs_verlet(c, s, dev, false);
+    } else {
+        if (st == RBMD_OK) st = cells_build(c, true);
+        if (st == RBMD_OK) st = rbl_pairs(c, s, dev, 0, false, nullptr, nullptr, nullptr);
+    }
     if (st == RBMD_OK) st = rbl_correction(c, dev, true, SCAL_FCORR_AUX);
     cudaStreamWaitEvent(main, c->ev_join, 0);
     for (int k = 0; k < nch; ++k) {
@@ -1103,7 +1126,7 @@ rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t 
     cudaStreamSynchronize(c->side);
     c->step = step;
     c->have_force = false;
-    c->vl_dirty = true;
+    if (!vl) c->vl_dirty = true;  // the cell walk re-sorted the atoms
     return leave(c, st);
 }
 

@@ -82,7 +82,7 @@ def test_rebuild_schedule_does_not_change_fp32_results():
     b.set_state_u(s.u, vel=s.v, step=0)
     for k in (2, 2, 3):
         b.step(k)
-        b.forces(0)  # re-sorts the cells: the next step rebuilds its candidates
+        b.rbl_lists(0)  # the cell walk re-sorts the atoms: the next step rebuilds
     ub, vb, st = b.get_state_u()
     assert st == 7
     assert b.candidate_rebuilds() > a.candidate_rebuilds()
@@ -134,3 +134,36 @@ def test_batch_candidates_match_standalone():
         assert torch.equal(u, ub[off[r]:off[r + 1]]) and torch.equal(v, vb[off[r]:off[r + 1]])
         c.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [rb.FP64, rb.FP32])
+def test_force_calls_use_the_candidates(prec):
+    """rbmd_forces and rbmd_forces_host evaluate through the candidate lists (rebuilt
+    on the device only when an atom has moved more than skin/2): the forces equal
+    the cell walk's (a context with skin < 0) to rounding, for a sequence of slightly
+    moved states, and the rebuilds stay rare."""
+    s = synth.electrolyte(3000, seed=65, charges="2:1", n_types=3)
+    ctx, _ = make_ctx(s, prec, seed=5)
+    ref, _ = make_ctx(s, prec, seed=5, skin=-1.0)
+    tol = 1e-12 if prec == rb.FP64 else 2e-6
+    rng = np.random.default_rng(5)
+    u = s.u.astype(np.int64)
+    scale = 2.0 ** 32 / s.L
+    r0 = ctx.candidate_rebuilds()
+    for k in range(6):
+        # every atom moves up to 0.03 sigma per call: a rebuild about every fourth call
+        u = (u + np.rint(rng.uniform(-0.03, 0.03, size=u.shape) * scale).astype(np.int64)) % 2 ** 32
+        uu = u.astype(np.uint32)
+        if k % 2 == 0:
+            ctx.set_state_u(uu, step=k)
+            F1 = to_np(ctx.forces(k))
+        else:
+            x = torch.from_numpy(uu.astype(np.float64) * (s.L / 2.0 ** 32))
+            F1 = to_np(ctx.forces_host(x.to(ctx.dtype).pin_memory(), step=k))
+        ref.set_state_u(ctx.get_state_u()[0], step=k)  # the state ctx encoded
+        F0 = to_np(ref.forces(k))
+        assert rel_err(F1, F0) < tol, (k, rel_err(F1, F0))
+    assert ctx.candidate_rebuilds() - r0 <= 6
+    ctx.close()
+    ref.close()
+
