@@ -44,8 +44,9 @@ template <typename real> struct AdjArgs {
     const real *sq;
     const int32_t *stype;
     const int32_t *lcore, *lshell, *bk;  // per-atom lists, entry e of atom i at lidx(i, e, N, cap)
-    int32_t *rb;                         // reverse batches, [N][CS] sorted indices (each row
+    int32_t *rb;                         // reverse batches, [N][RC] sorted indices (each row
                                          // sorted in place by its own atom's thread)
+    int RC;                              // their capacity (>= CS: never exceeded)
     const int32_t *rbn;                  // reverse-batch counts
     const int32_t *sidx;                 // sorted index of every atom (by global id)
     const int2 *ncount;
@@ -182,8 +183,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
             for (int e = 0; e < nbk; ++e) pair(a.bk[lidx(ks, e, N, a.p)], (real)0.5 * wk, wk);
             // the reverse batch in ascending sorted index (the scatter's order is not
             // fixed): sorted in place, one row per thread
-            int32_t *rrow = a.rb + lidx(ks, 0, N, a.CS);
-            const int nrb = min(a.rbn[ks], a.CS);
+            int32_t *rrow = a.rb + lidx(ks, 0, N, a.RC);
+            const int nrb = min(a.rbn[ks], a.RC);
             for (int e = 1; e < nrb; ++e) {
                 const int32_t x = rrow[e];
                 int y = e - 1;
@@ -230,8 +231,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
 
 // Reverse batches: for every batch entry j of atom k (sorted indices), k is
 // appended to j's row.  A batch member is a shell member and the shell relation is
-// symmetric, so a row never holds more than N_s(j) <= CS entries on complete lists;
-// a count beyond CS latches an error instead of writing.
+// symmetric, so a row never holds more than N_s(j) entries, at most the shell
+// capacity on complete lists; a count beyond the row capacity latches an error
+// instead of writing.
 template <typename real>
 __global__ void k_adj_reverse_batches(AdjArgs<real> a, int32_t *__restrict__ rb,
                                       int32_t *__restrict__ rbn, int *__restrict__ err)
@@ -243,7 +245,7 @@ __global__ void k_adj_reverse_batches(AdjArgs<real> a, int32_t *__restrict__ rb,
     for (int e = 0; e < nb; ++e) {
         const int32_t j = a.bk[lidx(ks, e, a.N, a.p)];
         const int pos = atomicAdd(rbn + j, 1);
-        if (pos < a.CS) rb[lidx(j, pos, a.N, a.CS)] = (int32_t)ks;
+        if (pos < a.RC) rb[lidx(j, pos, a.N, a.RC)] = (int32_t)ks;
         else latch_error(err, RBMD_ERR_CELL_OVERFLOW);
     }
 }
@@ -336,10 +338,20 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
         a.dq = (real *)dq;
         a.tpart = c->adj_tpart;
         const unsigned nba = (unsigned)c->nb128;
-        // reverse batches in the shell-list array (the adjoint does not read the
-        // shell list outside exact mode) and their counts in the scratch array
-        int32_t *rb = c->lshell, *rbn = (int32_t *)c->scratch_force;
+        // reverse batches in their own array (allocated on the first use, for the
+        // shell capacity: the lists the step keeps are left as they are) and their
+        // counts in the scratch array
+        if (!a.exact && c->adj_rb_cap < c->list_cs) {
+            if (c->adj_rb) cudaFree(c->adj_rb);
+            c->adj_rb = nullptr;
+            c->adj_rb_cap = 0;
+            RBMD_CHECK(dev_alloc(reinterpret_cast<void **>(&c->adj_rb),
+                                 sizeof(int32_t) * (size_t)c->N * c->list_cs));
+            c->adj_rb_cap = c->list_cs;
+        }
+        int32_t *rb = c->adj_rb, *rbn = (int32_t *)c->scratch_force;
         a.rb = rb;
+        a.RC = c->adj_rb_cap;
         a.rbn = rbn;
         if (!a.exact) {
             RBMD_CHECK_CUDA(cudaMemsetAsync(rbn, 0, sizeof(int32_t) * (size_t)c->N, c->stream));

@@ -18,7 +18,9 @@ namespace {
 // makes the k-th device allocation of the next rbmd_init report failure.
 int g_alloc_countdown = -1;
 
-rbmd_status dev_alloc(void **p, size_t bytes)
+}  // namespace
+
+rbmd_status rbmd::dev_alloc(void **p, size_t bytes)
 {
     if (g_alloc_countdown == 0) {
         *p = nullptr;
@@ -34,6 +36,8 @@ rbmd_status dev_alloc(void **p, size_t bytes)
     }
     return RBMD_OK;
 }
+
+namespace {
 
 // Entries of the step's candidate lists ([ceil(N/32)][cv][32] int32), 0 without them.
 static size_t cand_entries(const rbmd_ctx *c)
@@ -268,7 +272,7 @@ void free_ctx(rbmd_ctx *c)
                     c->map128,    c->tiles,     c->red_rep,   c->ptab,       c->heavy,
                     c->modes0,    c->acc,       c->chain_step, c->phtab,
                     c->vl_cand != c->lshell ? c->vl_cand : nullptr,
-                    c->vl_ncand,  c->vl_sref,   c->rho_acc,   c->gid};
+                    c->vl_ncand,  c->vl_sref,   c->rho_acc,   c->gid,      c->adj_rb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= RBMD_PROFILE_STAGES; ++k)
@@ -1271,10 +1275,13 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
     }
     gprof_mark(c, 1);
     if (s == RBMD_OK && !(c->prm.flags & RBMD_NO_RBL)) {
-        s = cells_build(c);
+        // through the candidate lists when the context keeps them, else the cell walk
+        const bool vl = candidates_for_call(c, 0);
+        s = vl ? verlet_prepare(c) : cells_build(c);
         gprof_mark(c, 2);
         if (s == RBMD_OK)
-            s = rbl_pairs(c, r, c->scratch_force, 0, true, nullptr, nullptr, nullptr);
+            s = vl ? rbl_pairs_verlet(c, r, c->scratch_force, false, true)
+                   : rbl_pairs(c, r, c->scratch_force, 0, true, nullptr, nullptr, nullptr);
         gprof_mark(c, 3);
         if (s == RBMD_OK) s = md_sum_replicas(c, c->fpart, 3, SCAL_FSUM, 1.0, false, true);
         if (s == RBMD_OK) s = md_sum_replicas(c, c->epart, EPART, SCAL_EPAIR, 1.0, false, true);
@@ -1488,7 +1495,18 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
     StepRef r{nullptr, step};
     rbmd_status s = RBMD_OK;
     gprof_mark(c, 0);
-    if (!(c->prm.flags & RBMD_NO_RBL) && !(c->lists_cached && c->lists_step == step)) {
+    bool have_lists = !(c->prm.flags & RBMD_NO_RBL) && c->lists_cached && c->lists_step == step;
+    if (!(c->prm.flags & RBMD_NO_RBL) && !have_lists && candidates_for_call(c, 0)) {
+        // the lists from the candidates, when no atom overflows a capacity
+        int32_t ovf = 1;
+        s = verlet_prepare(c);
+        if (s == RBMD_OK) s = rbl_lists_verlet(c, r);
+        if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(&ovf, c->ibuf + 2, sizeof(ovf), cudaMemcpyDeviceToHost, c->stream));
+        if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+        if (s != RBMD_OK) return leave(c, s);
+        have_lists = ovf == 0;
+    }
+    if (!(c->prm.flags & RBMD_NO_RBL) && !have_lists) {
         // complete lists of the step: grow the capacities until nothing overflows
         for (int attempt = 0; attempt < 8; ++attempt) {
             s = cells_build(c);
@@ -1530,7 +1548,6 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
         if (s != RBMD_OK) return leave(c, s);
     }
     s = adjoint_run(c, grad_out, d_pos, d_q, c->adj_tsum);  // marks stages 2-4
-    c->lists_cached = false;  // the reverse batches took the shell lists' array
     gprof_mark(c, 5);
     if (s == RBMD_OK && (d_eps || d_sigma)) {
         std::vector<double> h(2 * c->T);

@@ -1688,6 +1688,7 @@ struct VlArgs {
     int32_t *nrebuild;
     int cv, ccs;
     int core_rows;        // max(ccs, p): rows of k_rbl_vsel's core-id array
+    int32_t *imax;        // when set: the largest N_s (atomicMax, one per warp)
 };
 
 
@@ -1921,6 +1922,10 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
         }
         while (__any_sync(FULL, cnt > 0)) drain4();
     }
+    if (v.imax) {
+        const int m = __reduce_max_sync(FULL, sl.ok ? ns : 0);
+        if ((threadIdx.x & 31) == 0) atomicMax(v.imax, m);
+    }
     if (!sl.ok) return;
     if (n_all > v.cv || nc > v.ccs || nc > a.CC) {
         a.ncount[is] = make_int2(a.CC + 1, 0);
@@ -1974,6 +1979,7 @@ static VlArgs vl_args(rbmd_ctx *c)
     v.cv = c->vl_cv;
     v.ccs = c->vl_ccs;
     v.core_rows = std::max(c->vl_ccs, c->prm.rbl_p);
+    v.imax = nullptr;
     return v;
 }
 
@@ -2006,43 +2012,65 @@ static size_t vl_smem(const rbmd_ctx *c)
            (size_t)16 * 128 * sizeof(uint2);
 }
 
+// energy: the pair kernels also sum the energies and virials, and the selection
+// records the largest N_s; pairs = false: the lists only (for the adjoint)
 template <typename real, int CAP>
-static void launch_vl(rbmd_ctx *c, const PairArgs<real> &a, bool marks)
+static void launch_vl(rbmd_ctx *c, const PairArgs<real> &a, bool marks, bool energy, bool pairs)
 {
     PairArgs<real> a128 = a;
     a128.map = c->map128;
     a128.nmap = c->nb128;
     const unsigned nbp = (unsigned)c->nb128;
     const unsigned nfb = (unsigned)min(c->nb128, 4 * 148);
-    k_rbl_vsel<real, CAP><<<nbp, 128, vl_smem(c), c->stream>>>(a128, vl_args<real>(c));
+    VlArgs v = vl_args<real>(c);
+    if (energy) v.imax = c->ibuf;
+    k_rbl_vsel<real, CAP><<<nbp, 128, vl_smem(c), c->stream>>>(a128, v);
     if (marks) {
         prof_mark(c, 3);
         prof_mark(c, 4);
     }
-    if (a.tab) k_rbl_force<real, false, true><<<nbp, kPairBlock, 0, c->stream>>>(a128);
-    else k_rbl_force<real, false, false><<<nbp, kPairBlock, 0, c->stream>>>(a128);
-    k_rbl_fused<real, CAP, false, false><<<nfb, kPairBlock, 0, c->stream>>>(a128);
+    if (!pairs) return;
+    if (energy) {
+        if (a.tab) k_rbl_force<real, true, true><<<nbp, kPairBlock, 0, c->stream>>>(a128);
+        else k_rbl_force<real, true, false><<<nbp, kPairBlock, 0, c->stream>>>(a128);
+        k_rbl_fused<real, CAP, true, false><<<nfb, kPairBlock, 0, c->stream>>>(a128);
+    } else {
+        if (a.tab) k_rbl_force<real, false, true><<<nbp, kPairBlock, 0, c->stream>>>(a128);
+        else k_rbl_force<real, false, false><<<nbp, kPairBlock, 0, c->stream>>>(a128);
+        k_rbl_fused<real, CAP, false, false><<<nfb, kPairBlock, 0, c->stream>>>(a128);
+    }
 }
 
 template <typename real>
-static rbmd_status rbl_pairs_verlet_t(rbmd_ctx *c, StepRef s, void *force, bool marks)
+static rbmd_status rbl_pairs_verlet_t(rbmd_ctx *c, StepRef s, void *force, bool marks, bool energy,
+                                      bool pairs)
 {
     PairArgs<real> a = pair_args<real>(c, s);
     a.F = (real *)force;
     a.accumulate = 0;
     a.stale = 1;  // the fallback walks the cells of the last rebuild
     RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf + 2, 0, sizeof(int32_t), c->stream));
-    if (c->prm.rbl_p <= 10) launch_vl<real, 10>(c, a, marks);
-    else launch_vl<real, 16>(c, a, marks);
+    if (c->prm.rbl_p <= 10) launch_vl<real, 10>(c, a, marks, energy, pairs);
+    else launch_vl<real, 16>(c, a, marks, energy, pairs);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
 
-rbmd_status rbl_pairs_verlet(rbmd_ctx *c, StepRef s, void *force, bool marks)
+rbmd_status rbl_pairs_verlet(rbmd_ctx *c, StepRef s, void *force, bool marks, bool energy)
 {
     c->lists_cached = false;
-    if (c->fp64) return rbl_pairs_verlet_t<double>(c, s, force, marks);
-    return rbl_pairs_verlet_t<float>(c, s, force, marks);
+    if (c->fp64) return rbl_pairs_verlet_t<double>(c, s, force, marks, energy, true);
+    return rbl_pairs_verlet_t<float>(c, s, force, marks, energy, true);
+}
+
+// The core lists, batches and counts of step s from the candidates (after
+// verlet_prepare), without the pair forces; an atom beyond a capacity sets the
+// overflow word (ibuf[2]) as in the cell walk.
+rbmd_status rbl_lists_verlet(rbmd_ctx *c, StepRef s)
+{
+    c->lists_cached = false;
+    if (c->fp64) return rbl_pairs_verlet_t<double>(c, s, nullptr, false, false, false);
+    return rbl_pairs_verlet_t<float>(c, s, nullptr, false, false, false);
 }
 
 rbmd_status verlet_configure(rbmd_ctx *c)

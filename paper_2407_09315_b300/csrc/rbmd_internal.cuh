@@ -325,6 +325,8 @@ struct rbmd_ctx {
     // cleared by every call that writes the lists, the modes or structure factors,
     // the positions or the charges
     bool lists_cached = false, rho_cached = false;
+    int32_t *adj_rb = nullptr;  // reverse batches of the adjoint, [N][adj_rb_cap] (on first use)
+    int adj_rb_cap = 0;
     int64_t lists_step = 0, rho_step = 0;
     bool vl_dirty;        // the sorted layout changed outside the step: rebuild before the next
     double skin;
@@ -533,6 +535,8 @@ rbmd_status rbe_apply_forces(rbmd_ctx *c, void *force, int accumulate,
 // counted: the cell counts, cells and ranks are already there (the integrator's
 // drift kernel bins the atoms it moves).
 rbmd_status cells_build(rbmd_ctx *c, bool counted = false);
+// cudaMalloc with the test hook of RBMD_FAIL_ALLOC_AFTER (api.cu)
+rbmd_status dev_alloc(void **p, size_t bytes);
 rbmd_status cells_count_blocks(rbmd_ctx *c, int b0, int b1);
 rbmd_status rbl_pairs(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool energy,
                       int32_t *n_core, int32_t *n_shell, int32_t *batch, bool marks = false);
@@ -545,7 +549,8 @@ rbmd_status rbl_lists(rbmd_ctx *c, StepRef s);
 // rebuild (or the layout was changed outside the step), then the exact
 // classification, batch selection and pair forces (same sets as rbl_pairs).
 rbmd_status verlet_prepare(rbmd_ctx *c);
-rbmd_status rbl_pairs_verlet(rbmd_ctx *c, StepRef s, void *force, bool marks);
+rbmd_status rbl_pairs_verlet(rbmd_ctx *c, StepRef s, void *force, bool marks, bool energy = false);
+rbmd_status rbl_lists_verlet(rbmd_ctx *c, StepRef s);
 rbmd_status verlet_configure(rbmd_ctx *c);
 rbmd_status rbl_max_counts(rbmd_ctx *c, int32_t *out_dev);
 
