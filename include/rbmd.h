@@ -278,7 +278,14 @@ rbmd_status rbmd_rbe_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumu
  */
 rbmd_status rbmd_rbl_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumulate);
 
-/* rbmd_forces -- RBE + RBL (with correction) in one call; same arguments. */
+/*
+ * rbmd_forces -- RBE + RBL (with correction) in one call; same arguments.  Without
+ * accumulate, a context that keeps the step's candidate lists (see rbmd_step)
+ * evaluates the short-range part through them at the current positions,
+ * rebuilding them on the device when an atom has moved more than skin/2 (the same
+ * sets as the cell walk of rbmd_rbl_forces, summed in the step's order: equal to
+ * it up to the last bits).  rbmd_energy and rbmd_energy_backward do the same.
+ */
 rbmd_status rbmd_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumulate);
 
 /*
@@ -287,7 +294,8 @@ rbmd_status rbmd_forces(rbmd_ctx *ctx, int64_t step, void *force, int accumulate
  * are written to the host array, bit for bit the same as that sequence followed
  * by a copy.  The positions are copied in chunks on a copy stream; each chunk is
  * encoded and binned, and its structure-factor tiles summed, while the next one
- * is copied, and the RBE force pass runs in chunks whose forces are copied out
+ * is copied, the short-range part goes through the candidate lists as in
+ * rbmd_forces, and the RBE force pass runs in chunks whose forces are copied out
  * while the next chunk is computed.  Returns when the forces are on the host.
  *   pos        host (pinned for overlap), real [N][3], caller's atom order.
  *   force      host, real [N][3]; overwritten.
@@ -316,7 +324,7 @@ rbmd_status rbmd_forces_host(rbmd_ctx *ctx, const void *pos, void *force, int64_
  * The context's step counter advances by n_steps.  Queued as one CUDA graph per
  * step after the first call.
  * Short-range lists of the step (Algorithm 2 step 1): unless params.skin < 0 (or
- * with RBMD_RBL_EXACT, p > 16 or r_cut + skin >= L/2), the step keeps for every
+ * with RBMD_RBL_EXACT, p > 32 or r_cut + skin >= L/2), the step keeps for every
  * atom its candidates, the atoms within r_cut + skin at the last rebuild, and
  * classifies them exactly each step on the integer positions.  A rebuild (cell
  * sort and candidates) runs inside the step, on the device, when some atom has

@@ -730,7 +730,7 @@ rbmd_status init_ctx(const rbmd_params *prms, int32_t R, const void *pos, const 
     // p.skin (0: 0.4 sigma), off for exact lists, large batches, RBL off, or a box
     // where r_cut + skin reaches half the box
     c->skin = p.skin == 0.0 ? 0.4 : p.skin;
-    c->verlet = c->skin > 0.0 && !(p.flags & (RBMD_RBL_EXACT | RBMD_NO_RBL)) && p.rbl_p <= 16 &&
+    c->verlet = c->skin > 0.0 && !(p.flags & (RBMD_RBL_EXACT | RBMD_NO_RBL)) && p.rbl_p <= 32 &&
                 !slab;
     if (const char *env = getenv("RBMD_NO_CANDIDATES")) c->verlet = c->verlet && atoi(env) == 0;
     double max_mv = 0.0;

@@ -2051,7 +2051,8 @@ static rbmd_status rbl_pairs_verlet_t(rbmd_ctx *c, StepRef s, void *force, bool 
     a.stale = 1;  // the fallback walks the cells of the last rebuild
     RBMD_CHECK_CUDA(cudaMemsetAsync(c->ibuf + 2, 0, sizeof(int32_t), c->stream));
     if (c->prm.rbl_p <= 10) launch_vl<real, 10>(c, a, marks, energy, pairs);
-    else launch_vl<real, 16>(c, a, marks, energy, pairs);
+    else if (c->prm.rbl_p <= 16) launch_vl<real, 16>(c, a, marks, energy, pairs);
+    else launch_vl<real, 32>(c, a, marks, energy, pairs);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }
@@ -2084,6 +2085,10 @@ rbmd_status verlet_configure(rbmd_ctx *c)
     RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vsel<double, 10>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vsel<double, 16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vsel<float, 32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    RBMD_CHECK_CUDA(cudaFuncSetAttribute(k_rbl_vsel<double, 32>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     return RBMD_OK;
 }

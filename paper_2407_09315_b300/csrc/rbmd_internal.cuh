@@ -319,7 +319,7 @@ struct rbmd_ctx {
 
     // neighbour candidates of the integrator's step (Verlet lists with a skin):
     // built from the cells at a rebuild, classified exactly every step
-    bool verlet;          // the step uses them (skin > 0, p <= 16, batches not exact)
+    bool verlet;          // the step uses them (skin > 0, p <= 32, batches not exact)
     // what the list and mode arrays hold, so that rbmd_energy_backward right after
     // rbmd_energy of the same state and step reuses them: set by rbmd_energy,
     // cleared by every call that writes the lists, the modes or structure factors,

@@ -57,6 +57,40 @@ def test_candidate_lists_match_cell_walk_fp64(skin):
     assert rel_err(v1, v0) < 1e-12
 
 
+@pytest.mark.parametrize("shape", ["el001", "lj001"])
+def test_candidate_lists_p30_paper_shapes_fp64(shape):
+    """Batches of p = 30 (the selection with 33 kept keys) in the paper's density-0.01
+    regimes: the primitive electrolyte (r 6/12, about 63 shell members) and the LJ
+    fluid (r 2.5/5, mostly whole shells): the trajectory through the candidate lists
+    equals the cell walk's to rounding, and the oracle's."""
+    if shape == "el001":
+        s = synth.electrolyte(1500, seed=66, charges="1:1", n_types=1, density=0.01)
+        kw = dict(alpha=0.362, r_core=6.0, r_cut=12.0, rbl_p=30, rbe_P=40, coulomb_k=3.5)
+    else:
+        s = synth.electrolyte(1500, seed=67, charges="1:1", n_types=1, density=0.01)
+        s.q = s.q * 0.0
+        kw = dict(alpha=0.62, r_core=2.5, r_cut=5.0, rbl_p=30, rbe_P=10, coulomb_k=1.0,
+                  flags=rb.NO_RBE)
+    out = []
+    for skin in (-1.0, 0.4):
+        ctx, _ = make_ctx(s, rb.FP64, seed=7, dt=0.002, thermostat=1, skin=skin, **kw)
+        ctx.set_state_u(s.u, vel=s.v, step=0)
+        F = to_np(ctx.forces(0))
+        ctx.step(6)
+        u, v, _ = ctx.get_state_u()
+        out.append((F, to_np(u).astype(np.int64) % 2 ** 32, to_np(v), ctx.candidate_rebuilds()))
+        ctx.close()
+    (F0, u0, v0, r0), (F1, u1, v1, r1) = out
+    assert r0 == 0 and r1 >= 1
+    assert rel_err(F1, F0) < 1e-12
+    assert np.max(np.abs(_wrap_diff(u1, u0))) <= 1
+    assert rel_err(v1, v0) < 1e-12
+    o = oracle.rbl(s.u, s.q, s.types, s.eps, s.sig, s.L, kw["alpha"], kw["coulomb_k"], kw["r_core"],
+                   kw["r_cut"], 30, 7, 0)
+    if shape == "lj001":
+        assert rel_err(F1, o["F"] - o["Fsum"] / s.n) < 1e-10
+
+
 def test_fp64_candidate_trajectory_matches_oracle():
     s = synth.electrolyte(700, seed=62, charges="1:1", n_types=2, T0=1.2)
     ctx, _ = make_ctx(s, rb.FP64, rbe_P=30, seed=6, dt=0.002, thermostat=1, skin=0.01)
