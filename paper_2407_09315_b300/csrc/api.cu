@@ -1283,7 +1283,7 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
             s = vl ? rbl_pairs_verlet(c, r, c->scratch_force, false, true)
                    : rbl_pairs(c, r, c->scratch_force, 0, true, nullptr, nullptr, nullptr);
         gprof_mark(c, 3);
-        if (s == RBMD_OK) s = md_sum_replicas(c, c->fpart, 3, SCAL_FSUM, 1.0, false, true);
+        if (s == RBMD_OK) s = md_sum_replicas_fix(c, c->fpart, SCAL_FSUM, 1.0, false, true);
         if (s == RBMD_OK) s = md_sum_replicas(c, c->epart, EPART, SCAL_EPAIR, 1.0, false, true);
         if (s == RBMD_OK) {
             k_max_count<<<(unsigned)((c->ncell + 255) / 256), 256, 0, c->stream>>>(
@@ -1853,7 +1853,7 @@ rbmd_status rbmd_rbl_forces_slab(rbmd_ctx *c, int64_t step, void *force, int acc
     const StepRef r{nullptr, step};
     rbmd_status s = cells_build(c);
     if (s == RBMD_OK) s = rbl_pairs(c, r, force, accumulate, false, nullptr, nullptr, nullptr);
-    if (s == RBMD_OK) s = md_sum_replicas(c, c->fpart, 3, SCAL_FSUM, 1.0, false, true);
+    if (s == RBMD_OK) s = md_sum_replicas_fix(c, c->fpart, SCAL_FSUM, 1.0, false, true);
     if (s == RBMD_OK)
         s = cuda_status(cudaMemcpyAsync(fsum, c->scal + SCAL_FSUM, 3 * sizeof(double),
                                         cudaMemcpyDeviceToHost, c->stream));

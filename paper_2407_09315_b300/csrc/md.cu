@@ -80,18 +80,19 @@ rbmd_status md_sum(rbmd_ctx *c, const double *parts, int nparts, int ncomp, doub
 // (k, r) sums chunk k of RED_SPLIT equal chunks of replica r's range, then one
 // block per replica adds its RED_SPLIT chunk sums.  The chunking depends only on
 // the replica's own size, so a replica sums identically alone or in a batch.
-template <int NC>
-__global__ void k_sum_replicas1(const double *__restrict__ parts, int64_t seg2,
-                                const Rep *__restrict__ reps, double *__restrict__ tmp)
+// T: double, or long long for fixed-point partials (exact sums).
+template <int NC, typename T>
+__global__ void k_sum_replicas1(const T *__restrict__ parts, int64_t seg2,
+                                const Rep *__restrict__ reps, T *__restrict__ tmp)
 {
-    __shared__ double s[NC][256];
+    __shared__ T s[NC][256];
     const Rep rp = reps[blockIdx.y];
     const int64_t j0 = 4 * (int64_t)rp.b128_0, nj = 4 * (int64_t)rp.nb128;
     const int64_t chunk = (nj + RED_SPLIT - 1) / RED_SPLIT;
     const int64_t b = blockIdx.x * chunk, e = min(nj, b + chunk);
-    double v[NC];
+    T v[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) v[c] = 0.0;
+    for (int c = 0; c < NC; ++c) v[c] = 0;
     for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -113,16 +114,18 @@ __global__ void k_sum_replicas1(const double *__restrict__ parts, int64_t seg2,
         tmp[((int64_t)blockIdx.y * RED_SPLIT + blockIdx.x) * RED_STRIDE + threadIdx.x] = s[threadIdx.x][0];
 }
 
-__global__ void k_sum_replicas2(const double *__restrict__ tmp, int ncomp,
+// unit: the value of one unit of T (2^-32 for the fixed-point force sums)
+template <typename T>
+__global__ void k_sum_replicas2(const T *__restrict__ tmp, int ncomp,
                                 const Rep *__restrict__ reps, double *__restrict__ scal, int slot,
-                                double scale, int per_atom)
+                                double scale, int per_atom, double unit)
 {
     const int c = threadIdx.x;
     if (c >= ncomp) return;
     const double sc = per_atom ? scale / (double)reps[blockIdx.x].N : scale;
-    double v = 0.0;
+    T v = 0;
     for (int k = 0; k < RED_SPLIT; ++k) v += tmp[((int64_t)blockIdx.x * RED_SPLIT + k) * RED_STRIDE + c];
-    scal[(int64_t)blockIdx.x * SCAL_COUNT + slot + c] = sc * v;
+    scal[(int64_t)blockIdx.x * SCAL_COUNT + slot + c] = sc * ((double)v * unit);
 }
 
 rbmd_status md_sum_replicas(rbmd_ctx *c, const double *parts, int ncomp, int slot, double scale,
@@ -130,14 +133,30 @@ rbmd_status md_sum_replicas(rbmd_ctx *c, const double *parts, int ncomp, int slo
 {
     const int64_t seg2 = two_segments ? 4 * (int64_t)c->nb128 : -1;
     const dim3 grid(RED_SPLIT, c->R);
-    if (ncomp == 3) k_sum_replicas1<3><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
-    else if (ncomp == 2) k_sum_replicas1<2><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
+    if (ncomp == 3)
+        k_sum_replicas1<3, double><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
+    else if (ncomp == 2)
+        k_sum_replicas1<2, double><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
     else if (ncomp == EPART)
-        k_sum_replicas1<EPART><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
+        k_sum_replicas1<EPART, double><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
     else return RBMD_ERR_INVALID;
     RBMD_LAUNCH_CHECK();
-    k_sum_replicas2<<<c->R, 32, 0, c->stream>>>(c->red_rep, ncomp, c->reps, c->scal, slot, scale,
-                                                per_atom ? 1 : 0);
+    k_sum_replicas2<double><<<c->R, 32, 0, c->stream>>>(c->red_rep, ncomp, c->reps, c->scal, slot,
+                                                        scale, per_atom ? 1 : 0, 1.0);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
+rbmd_status md_sum_replicas_fix(rbmd_ctx *c, const long long *parts, int slot, double scale,
+                                bool per_atom, bool two_segments)
+{
+    const int64_t seg2 = two_segments ? 4 * (int64_t)c->nb128 : -1;
+    const dim3 grid(RED_SPLIT, c->R);
+    long long *tmp = reinterpret_cast<long long *>(c->red_rep);  // same 8-byte slots
+    k_sum_replicas1<3, long long><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, tmp);
+    RBMD_LAUNCH_CHECK();
+    k_sum_replicas2<long long><<<c->R, 32, 0, c->stream>>>(tmp, 3, c->reps, c->scal, slot, scale,
+                                                           per_atom ? 1 : 0, 0x1p-32);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
 }

@@ -289,7 +289,7 @@ template <typename real> struct PairArgs {
     real tab_inv_h;
     real *F;
     int accumulate;
-    double *fpart;     // [parts][3]: pair kernel per warp, then the fallback per warp
+    long long *fpart;  // [parts][3]: pair kernel per warp, then the fallback per warp (2^-32)
     double *epart;     // [parts][EPART]
     int64_t fb_part0;  // first partial slot of the fallback kernel
     int32_t *imax;     // [0] max N_s
@@ -332,8 +332,11 @@ __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 // the erfc-Coulomb and LJ virials and the tensor g d (x) d of both (d = r_j - r_i,
 // the pair force on i is -g d, so r_ij (x) F_ij = g d (x) d; xx yy zz xy xz yz).
 // The virial is W = -dE/d(strain) of the list energy with its weights held fixed.
+// A thread's sums over its pairs (a few tens) in the working precision; the warp
+// and global sums of the energies and virials are taken on from there (FP64
+// across warps).
 template <typename real> struct EAcc {
-    double ec, el;
+    real ec, el;
     real wc, wl;
     real w[6];
 };
@@ -341,8 +344,8 @@ template <typename real> struct EAcc {
 template <typename real>
 __device__ __forceinline__ void eacc_zero(EAcc<real> &e)
 {
-    e.ec = 0.0;
-    e.el = 0.0;
+    e.ec = 0;
+    e.el = 0;
     e.wc = 0;
     e.wl = 0;
 #pragma unroll
@@ -353,8 +356,8 @@ __device__ __forceinline__ void eacc_zero(EAcc<real> &e)
 template <typename real>
 __device__ __forceinline__ void eacc_add(EAcc<real> &e, const EAcc<real> &b, real s)
 {
-    e.ec += (double)s * b.ec;
-    e.el += (double)s * b.el;
+    e.ec += s * b.ec;
+    e.el += s * b.el;
     e.wc += s * b.wc;
     e.wl += s * b.wl;
 #pragma unroll
@@ -410,8 +413,8 @@ __device__ __forceinline__ void pair_eval(const PairArgs<real> &a, real dx, real
     fy -= g * dy;
     fz -= g * dz;
     if constexpr (ENERGY) {
-        e.ec += (double)(qq * eu);
-        e.el += (double)((real)4 * eps * (s12 - s6));
+        e.ec += qq * eu;
+        e.el += (real)4 * eps * (s12 - s6);
         e.wc += gcr;
         e.wl += glj;
         e.w[0] += g * dx * dx;
@@ -1191,21 +1194,30 @@ template <typename real, bool ENERGY>
 __device__ __forceinline__ void warp_partials(const PairArgs<real> &a, int64_t part, real fx,
                                               real fy, real fz, const EAcc<real> &e)
 {
-    constexpr int NV = ENERGY ? 3 + EPART : 3;  // FP64 shuffles are costly: only what is used
-    double v[3 + EPART] = {(double)fx, (double)fy, (double)fz, 0.5 * e.ec, 0.5 * e.el,
-                           0.5 * (double)e.wc, 0.5 * (double)e.wl};
+    // the force sums as exact fixed-point integers (fix32): the momentum correction,
+    // and with it the trajectory, does not depend on which atoms share a warp (the
+    // sorted order of the last candidate rebuild).  The energies and virials
+    // (reported, not integrated) are summed over the warp in the working precision
+    // (FP64 operations are scarce on this GPU) and across warps in FP64.
+    long long f[3] = {fix32(fx), fix32(fy), fix32(fz)};
 #pragma unroll
-    for (int c = 0; c < 6; ++c) v[7 + c] = 0.5 * (double)e.w[c];
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o > 0; o >>= 1) f[c] += __shfl_down_sync(0xffffffffu, f[c], o);
+    real v[EPART] = {e.ec, e.el, e.wc, e.wl};
+    if constexpr (ENERGY) {
 #pragma unroll
-    for (int c = 0; c < NV; ++c)
-        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+        for (int c = 0; c < 6; ++c) v[4 + c] = e.w[c];
+#pragma unroll
+        for (int c = 0; c < EPART; ++c)
+            for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    }
     if ((threadIdx.x & 31) == 0) {
-        a.fpart[3 * part + 0] = v[0];
-        a.fpart[3 * part + 1] = v[1];
-        a.fpart[3 * part + 2] = v[2];
+        a.fpart[3 * part + 0] = f[0];
+        a.fpart[3 * part + 1] = f[1];
+        a.fpart[3 * part + 2] = f[2];
         if constexpr (ENERGY) {
 #pragma unroll
-            for (int c = 0; c < EPART; ++c) a.epart[EPART * part + c] = v[3 + c];
+            for (int c = 0; c < EPART; ++c) a.epart[EPART * part + c] = 0.5 * (double)v[c];
         }
     }
 }
@@ -1304,9 +1316,9 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + tid; j < (int64_t)a.nmap * WPB;
              j += (int64_t)gridDim.x * blockDim.x) {
             const int64_t part = a.fb_part0 + j;
-            a.fpart[3 * part + 0] = 0.0;
-            a.fpart[3 * part + 1] = 0.0;
-            a.fpart[3 * part + 2] = 0.0;
+            a.fpart[3 * part + 0] = 0;
+            a.fpart[3 * part + 1] = 0;
+            a.fpart[3 * part + 2] = 0;
             if constexpr (ENERGY) {
                 for (int c = 0; c < EPART; ++c) a.epart[EPART * part + c] = 0.0;
             }
@@ -1437,16 +1449,16 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
 // computed; the fallback's partial sums are zero.
 template <bool ENERGY>
 __global__ void k_rbl_no_fallback(const int32_t *__restrict__ ovf, int *__restrict__ err,
-                                  double *__restrict__ fpart, double *__restrict__ epart,
+                                  long long *__restrict__ fpart, double *__restrict__ epart,
                                   int64_t part0, int64_t nparts)
 {
     const int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j0 == 0 && *ovf != 0) latch_error(err, RBMD_ERR_CELL_OVERFLOW);
     for (int64_t j = j0; j < nparts; j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t part = part0 + j;
-        fpart[3 * part + 0] = 0.0;
-        fpart[3 * part + 1] = 0.0;
-        fpart[3 * part + 2] = 0.0;
+        fpart[3 * part + 0] = 0;
+        fpart[3 * part + 1] = 0;
+        fpart[3 * part + 2] = 0;
         if constexpr (ENERGY) {
             for (int c = 0; c < EPART; ++c) epart[EPART * part + c] = 0.0;
         }
@@ -2112,7 +2124,7 @@ __global__ void k_add_corr(real *__restrict__ F, const int2 *__restrict__ map,
 // correction in SCAL_FCORR and adds it in the kicks instead of in a separate pass.
 rbmd_status rbl_correction(rbmd_ctx *c, void *force, bool apply, int slot)
 {
-    RBMD_CHECK(md_sum_replicas(c, c->fpart, 3, slot, -1.0, true, true));
+    RBMD_CHECK(md_sum_replicas_fix(c, c->fpart, slot, -1.0, true, true));
     if (apply) {
         if (c->fp64)
             k_add_corr<double><<<c->nb256, 256, 0, c->stream>>>((double *)force, c->map256, c->reps,

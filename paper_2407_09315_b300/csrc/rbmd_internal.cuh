@@ -123,6 +123,32 @@ __device__ __forceinline__ void phase_sincos_tab(const double2 *__restrict__ tab
     s = __fma_rn(a.x, d.y, __dmul_rn(a.y, d.x));
 }
 
+// x 2^32 truncated toward zero, from the bits of x (|x| < 2^31): the force sums of
+// the momentum correction are added as these integers, exactly, so they do not
+// depend on how the atoms are grouped (warps, blocks, the sorted order of a
+// candidate rebuild).
+__device__ __forceinline__ long long fix32(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const int ex = (int)((b >> 23) & 0xFFu);
+    if (ex == 0) return 0;
+    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = min(ex - 118, 39);  // x = m 2^(ex - 150)
+    const long long v = sh >= 0 ? (m << sh) : (sh > -24 ? (m >> -sh) : 0);
+    return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ long long fix32(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FFu);
+    if (ex == 0) return 0;
+    const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+    const int sh = min(ex - 1043, 10);  // x = m 2^(ex - 1075)
+    const long long v = sh >= 0 ? (m << sh) : (sh > -53 ? (m >> -sh) : 0);
+    return (b >> 63) ? -v : v;
+}
+
 // A named host range for profilers (nothing happens without one attached).
 struct NvtxRange {
     explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
@@ -296,7 +322,7 @@ struct rbmd_ctx {
     uint4 *spos;          // [N]
     void *sq;             // real [N]
     int32_t *stype;       // [N]
-    double *fpart;        // [pair_parts][3] force partial sums (per warp)
+    long long *fpart;     // [pair_parts][3] force partial sums (per warp), fixed point 2^-32
     double *epart;        // [pair_parts][EPART] energy and virial partial sums
     double *kepart;       // [nb256]
     int32_t *ibuf;        // [8] integer diagnostics and flags: 0 max N_s, 1 max cell,
@@ -570,6 +596,10 @@ rbmd_status md_sum(rbmd_ctx *c, const double *parts, int nparts, int ncomp, doub
 // Per replica r: out[r * SCAL_COUNT + slot + comp] = scale_r * (sum of the parts of
 // its 128-atom blocks, 4 per block, in pass 0 and, with two_segments, pass 1 at
 // offset 4 nb128).  scale_r = scale, or scale / N_r when per_atom.
+// The same for the fixed-point (2^-32) force partials: exact integer sums, scaled
+// to FP64 at the end.
+rbmd_status md_sum_replicas_fix(rbmd_ctx *c, const long long *parts, int slot, double scale,
+                                bool per_atom, bool two_segments);
 rbmd_status md_sum_replicas(rbmd_ctx *c, const double *parts, int ncomp, int slot, double scale,
                             bool per_atom, bool two_segments);
 rbmd_status md_decode_state(rbmd_ctx *c, void *pos, void *vel);
