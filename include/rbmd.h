@@ -380,7 +380,11 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *ctx, int64_t step, rbmd_energy_terms *ou
  * without the momentum correction.  The list weights are those of `step` and
  * are held fixed (E jumps where a membership changes).  Always synchronises
  * (the lists of the step must be complete: list capacities grow if needed).
- * dE/d eps_t needs eps_t > 0.
+ * dE/d eps_t needs eps_t > 0.  Right after rbmd_energy of the same state and
+ * step (no call in between that writes the lists, modes, positions or charges)
+ * its lists, modes and structure factors are reused: the same bits as computing
+ * them again.  The first call allocates the reverse-batch array ([N] x the
+ * shell capacity, int32) that the gradient pass keeps.
  */
 rbmd_status rbmd_energy_backward(rbmd_ctx *ctx, int64_t step, double grad_out, void *d_pos,
                                  void *d_q, double *d_eps, double *d_sigma);
