@@ -124,16 +124,30 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
         real ak_e = 0, ak_s = 0;  // the type sums of k's own type, added to acc at the end
         // one pair (k, js): W the symmetric weight of dE/dr and dE/dq, Wkj the
         // one-sided weight of the type sums (0: counted from js's side)
-        auto pair = [&](int32_t js, real W, real Wkj) {
-            const uint4 B = a.spos[js];
+        struct Nb {  // a neighbour's record; its counts only on the reverse batch
+            uint4 B;
+            int tj;
+            real qj;
+            int2 cj;
+        };
+        auto load = [&](int32_t js, bool counts) {
+            Nb n;
+            n.B = a.spos[js];
+            n.tj = a.stype[js];
+            n.qj = a.sq[js];
+            n.cj = counts ? a.ncount[js] : make_int2(0, 0);
+            return n;
+        };
+        auto pair = [&](const Nb &nb, real W, real Wkj) {
+            const uint4 B = nb.B;
             const real dx = (real)(int32_t)(B.x - A.x) * lscale;  // r_j - r_k
             const real dy = (real)(int32_t)(B.y - A.y) * lscale;
             const real dz = (real)(int32_t)(B.z - A.z) * lscale;
             const real r2 = dx * dx + dy * dy + dz * dz;
             const real r = sqrt_a(r2);
             const real rinv = (real)1 / r;
-            const int tj = a.stype[js];
-            const real qj = a.sq[js];
+            const int tj = nb.tj;
+            const real qj = nb.qj;
             real eij, sij;
             if constexpr (TT <= 16) {
                 eij = s_e[tk * TT + tj];
@@ -175,31 +189,79 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
                 acc_add<real, TT>(acc, TT + tj, hw * dus * (real)0.5);
             }
         };
-        for (int e = 0; e < cnt.x; ++e) pair(a.lcore[lidx(ks, e, N, a.CC)], (real)1, (real)1);
+        // a list of n neighbours, each one's loads issued before the previous pair is
+        // computed; weight(nb, W, Wkj) gives the pair's weights
+        auto walk = [&](auto index, int n, bool counts, auto weight) {
+            if (n <= 0) return;
+            int32_t js = index(0);
+            Nb cur = load(js, counts);
+            for (int e = 0; e < n; ++e) {
+                const int32_t jn = e + 1 < n ? index(e + 1) : js;
+                const Nb nxt = load(jn, counts);
+                real W, Wkj;
+                weight(cur, W, Wkj);
+                pair(cur, W, Wkj);
+                cur = nxt;
+                js = jn;
+            }
+        };
+        auto ones = [](const Nb &, real &W, real &Wkj) {
+            W = (real)1;
+            Wkj = (real)1;
+        };
+        walk([&](int e) { return a.lcore[lidx(ks, e, N, a.CC)]; }, cnt.x, false, ones);
         if (a.exact) {
-            for (int e = 0; e < cnt.y; ++e)
-                pair(a.sidx[id0 + (uint32_t)a.lshell[lidx(ks, e, N, a.CS)]], (real)1, (real)1);
+            walk([&](int e) { return a.sidx[id0 + (uint32_t)a.lshell[lidx(ks, e, N, a.CS)]]; },
+                 cnt.y, false, ones);
         } else {
-            for (int e = 0; e < nbk; ++e) pair(a.bk[lidx(ks, e, N, a.p)], (real)0.5 * wk, wk);
+            walk([&](int e) { return a.bk[lidx(ks, e, N, a.p)]; }, nbk, false,
+                 [&](const Nb &, real &W, real &Wkj) {
+                     W = (real)0.5 * wk;
+                     Wkj = wk;
+                 });
             // the reverse batch in ascending sorted index (the scatter's order is not
             // fixed): sorted in place, one row per thread
             int32_t *rrow = a.rb + lidx(ks, 0, N, a.RC);
             const int nrb = min(a.rbn[ks], a.RC);
-            for (int e = 1; e < nrb; ++e) {
-                const int32_t x = rrow[e];
-                int y = e - 1;
-                while (y >= 0 && rrow[y] > x) {
-                    rrow[y + 1] = rrow[y];
-                    --y;
+            if (nrb <= 16) {
+                // up to 16 entries (most rows: about p on average) by a bitonic network in
+                // registers, padded with INT_MAX; the loads and stores are independent
+                int32_t r[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) r[i] = i < nrb ? rrow[i] : 0x7FFFFFFF;
+#pragma unroll
+                for (int k = 2; k <= 16; k <<= 1)
+#pragma unroll
+                    for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int l = i ^ j;
+                            if (l > i) {
+                                const int32_t lo = min(r[i], r[l]), hi = max(r[i], r[l]);
+                                const bool up = (i & k) == 0;
+                                r[i] = up ? lo : hi;
+                                r[l] = up ? hi : lo;
+                            }
+                        }
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (i < nrb) rrow[i] = r[i];
+            } else {
+                for (int e = 1; e < nrb; ++e) {
+                    const int32_t x = rrow[e];
+                    int y = e - 1;
+                    while (y >= 0 && rrow[y] > x) {
+                        rrow[y + 1] = rrow[y];
+                        --y;
+                    }
+                    rrow[y + 1] = x;
                 }
-                rrow[y + 1] = x;
             }
-            for (int e = 0; e < nrb; ++e) {
-                const int32_t js = rrow[e];
-                const int2 cj = a.ncount[js];
-                const real wj = cj.y > a.p ? (real)cj.y / (real)a.p : (real)1;
-                pair(js, (real)0.5 * wj, (real)0);
-            }
+            walk([&](int e) { return rrow[e]; }, nrb, true, [&](const Nb &nb, real &W, real &Wkj) {
+                const real wj = nb.cj.y > a.p ? (real)nb.cj.y / (real)a.p : (real)1;
+                W = (real)0.5 * wj;
+                Wkj = (real)0;
+            });
         }
         acc_add<real, TT>(acc, tk, ak_e);
         acc_add<real, TT>(acc, TT + tk, ak_s);
