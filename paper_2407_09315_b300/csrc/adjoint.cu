@@ -224,25 +224,12 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
             int32_t *rrow = a.rb + lidx(ks, 0, N, a.RC);
             const int nrb = min(a.rbn[ks], a.RC);
             if (nrb <= 16) {
-                // up to 16 entries (most rows: about p on average) by a bitonic network in
-                // registers, padded with INT_MAX; the loads and stores are independent
+                // up to 16 entries (most rows: about p on average) in registers; the
+                // loads and stores are independent
                 int32_t r[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) r[i] = i < nrb ? rrow[i] : 0x7FFFFFFF;
-#pragma unroll
-                for (int k = 2; k <= 16; k <<= 1)
-#pragma unroll
-                    for (int j = k >> 1; j > 0; j >>= 1)
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int l = i ^ j;
-                            if (l > i) {
-                                const int32_t lo = min(r[i], r[l]), hi = max(r[i], r[l]);
-                                const bool up = (i & k) == 0;
-                                r[i] = up ? lo : hi;
-                                r[l] = up ? hi : lo;
-                            }
-                        }
+                sort16(r);
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
                     if (i < nrb) rrow[i] = r[i];

@@ -1945,9 +1945,19 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
         return;
     }
     const int32_t *sidx = a.sidx + id0;
-    sort_strided(s_core, nc, 128);
     int32_t *lc = a.lcore + is * a.CC;
-    for (int e = 0; e < nc; ++e) lc[e] = sidx[s_core[e * 128]];
+    if (nc <= 16) {
+        int32_t r[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) r[e] = e < nc ? s_core[e * 128] : 0x7FFFFFFF;
+        sort16(r);
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            if (e < nc) lc[e] = sidx[r[e]];
+    } else {
+        sort_strided(s_core, nc, 128);
+        for (int e = 0; e < nc; ++e) lc[e] = sidx[s_core[e * 128]];
+    }
     int32_t *bk = a.bk + is * a.p;
     if (ns <= a.p) {
         // the whole shell (its keys are all kept), in atom-id order

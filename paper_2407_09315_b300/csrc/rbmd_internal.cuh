@@ -149,6 +149,26 @@ __device__ __forceinline__ long long fix32(double x)
     return (b >> 63) ? -v : v;
 }
 
+// Ascending sort of n <= 16 values (the rest of r padded with INT_MAX) by a
+// bitonic network in registers: no dependent memory accesses.
+__device__ __forceinline__ void sort16(int32_t (&r)[16])
+{
+#pragma unroll
+    for (int k = 2; k <= 16; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const int32_t lo = min(r[i], r[l]), hi = max(r[i], r[l]);
+                    const bool up = (i & k) == 0;
+                    r[i] = up ? lo : hi;
+                    r[l] = up ? hi : lo;
+                }
+            }
+}
+
 // A named host range for profilers (nothing happens without one attached).
 struct NvtxRange {
     explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
