@@ -1959,8 +1959,20 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
         for (int e = 0; e < nc; ++e) lc[e] = sidx[s_core[e * 128]];
     }
     int32_t *bk = a.bk + is * a.p;
-    if (ns <= a.p) {
+    if (ns <= a.p && ns <= 16) {
         // the whole shell (its keys are all kept), in atom-id order
+        int32_t r[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            r[e] = e < ns && e <= CAP
+                       ? (int32_t)(a.spos[RBMD_IDX(cl[(sk[e < CAP ? e : CAP] & lo_mask) * 32], a.N,
+                                                   a.err)].w - id0)
+                       : 0x7FFFFFFF;
+        sort16(r);
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            if (e < ns) bk[e] = sidx[r[e]];
+    } else if (ns <= a.p) {
 #pragma unroll
         for (int e = 0; e < CAP; ++e)
             if (e < ns)
