@@ -1826,6 +1826,56 @@ __device__ __noinline__ void vl_select_exact(const Philox0 &r0, uint2 key, const
     }
 }
 
+// The CAP + 1 smallest of the kept keys sk (ascending) and four new keys x, into
+// sk.  For CAP + 5 <= 32 a bitonic merge: x sorted descending after sk and
+// all-ones padding makes one bitonic sequence, which log2 of its length
+// compare-exchange stages sort (a dependency chain of 5 or so instead of the
+// 4 (CAP + 1) of inserting the keys one by one); larger CAP insert one by one.
+// The kept set is the same either way.
+template <int CAP>
+__device__ __forceinline__ void merge4(uint32_t (&sk)[CAP + 1], uint32_t (&x)[4])
+{
+    constexpr int M = CAP + 1;
+    if constexpr (M + 4 <= 32) {
+        constexpr int NP = M + 4 <= 16 ? 16 : 32;
+        auto ce = [](uint32_t &lo, uint32_t &hi) {  // lo <- min, hi <- max
+            const uint32_t a = min(lo, hi), b = max(lo, hi);
+            lo = a;
+            hi = b;
+        };
+        ce(x[1], x[0]);  // descending
+        ce(x[3], x[2]);
+        ce(x[2], x[0]);
+        ce(x[3], x[1]);
+        ce(x[2], x[1]);
+        uint32_t v[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) v[i] = 0xFFFFFFFFu;
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = sk[i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[NP - 4 + q] = x[q];
+#pragma unroll
+        for (int j = NP >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < NP; ++i)
+                if ((i & j) == 0) ce(v[i], v[i + j]);
+#pragma unroll
+        for (int i = 0; i < M; ++i) sk[i] = v[i];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t y = x[q];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const uint32_t m = min(sk[j], y);
+                y = max(sk[j], y);
+                sk[j] = m;
+            }
+        }
+    }
+}
+
 // Algorithm 2 step 1 for the step: classification of the candidates, N_s, the
 // batch and the core list, one thread per sorted atom (128 per block).  The shell
 // is never stored.  A lane classifies four candidates per round and queues its
@@ -1882,16 +1932,10 @@ __global__ void __launch_bounds__(128) k_rbl_vsel(PairArgs<real> a, VlArgs v)
         cnt -= took;
         uint2 w[4];
         philox_rest4(r0, id4, K, w);
+        uint32_t x4[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t x = t4[q] != FULL ? (w[q].x & keep) | t4[q] : FULL;
-#pragma unroll
-            for (int j = 0; j <= CAP; ++j) {
-                const uint32_t m = min(sk[j], x);
-                x = max(sk[j], x);
-                sk[j] = m;
-            }
-        }
+        for (int q = 0; q < 4; ++q) x4[q] = t4[q] != FULL ? (w[q].x & keep) | t4[q] : FULL;
+        merge4<CAP>(sk, x4);
     };
     {
         // four candidates per round: their positions are gathered one round
