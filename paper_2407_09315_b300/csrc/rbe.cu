@@ -213,8 +213,8 @@ rbmd_status rbe_sample(rbmd_ctx *c, StepRef s)
 // Block (x = atom tile, y = mode tile): the atom tile and the modes are staged
 // in shared memory; work item (mode l, sub-tile s) sums q_j e^{i theta_jl} over
 // its atoms with the thread's own compensated (Kahan) FP32 accumulators, one
-// compensated addition per pair of atoms (plain FP64 in FP64 contexts).  Items of one warp share s, so every lane reads the
-// same atom: a shared-memory broadcast.  The sub-tile sums are combined in FP64
+// compensated addition per four atoms (plain FP64 in FP64 contexts).  Items of
+// one warp share s, so every lane reads the same atom: a shared-memory broadcast.  The sub-tile sums are combined in FP64
 // in a fixed order and one partial per (atom tile, mode) goes to HBM.
 // --------------------------------------------------------------------------
 // FP64 phase factors by angle addition.  The phase is an exact 32-bit fraction of
@@ -297,7 +297,23 @@ __global__ void __launch_bounds__(1024, sizeof(real) == 4 ? 2 : 1) k_rho_partial
         if constexpr (sizeof(real) == 4) {
             float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
             int a = b;
-            // two atoms per compensated addition: their plain FP32 sum, then Kahan
+            // four atoms per compensated addition: their plain FP32 sum, then Kahan
+            for (; a + 3 < e; a += 4) {
+                float pc, ps;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint4 A0 = s_at[a + 2 * h], A1 = s_at[a + 2 * h + 1];
+                    float s0, c0, s1, c1;
+                    phase_sincos(mx * A0.x + my * A0.y + mz * A0.z, s0, c0);
+                    phase_sincos(mx * A1.x + my * A1.y + mz * A1.z, s1, c1);
+                    const float q0 = __uint_as_float(A0.w), q1 = __uint_as_float(A1.w);
+                    const float tc = q0 * c0 + q1 * c1, ts = q0 * s0 + q1 * s1;
+                    pc = h ? pc + tc : tc;
+                    ps = h ? ps + ts : ts;
+                }
+                kahan_add(sr, cr, pc);
+                kahan_add(si, ci, ps);
+            }
             for (; a + 1 < e; a += 2) {
                 const uint4 A0 = s_at[a], A1 = s_at[a + 1];
                 float s0, c0, s1, c1;
