@@ -71,7 +71,9 @@ typedef enum {
     RBMD_ERR_CUDA = 5,           /* a CUDA runtime call failed */
     RBMD_ERR_CELL_OVERFLOW = 6,  /* a cell or list exceeded its capacity */
     RBMD_ERR_NONFINITE = 7,      /* a force or velocity became NaN/Inf */
-    RBMD_ERR_TIMEOUT = 8,        /* a bounded device wait gave up */
+    RBMD_ERR_TIMEOUT = 8,        /* a bounded device wait gave up (reserved: no kernel of
+                                    this library waits on another, so no call returns it;
+                                    rbmd_debug_latch_error can latch it for tests) */
     RBMD_ERR_UNSUPPORTED = 9,    /* combination of options not built */
     RBMD_ERR_BOUNDS = 10         /* an index out of range (bounds-checked builds only:
                                     compiled with -DRBMD_CHECKED, the access is skipped) */
