@@ -298,8 +298,9 @@ def forces(u, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P, seed
 def vv(u, v, F, q, types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P, seed, step0,
        dt, n_steps, thermostat=0, T0=1.0, tau=0.1, replica=0, exact=False, xi=0.0,
        return_xi=False):
-    """Velocity-Verlet with thermostat 0 (none), 1 (Berendsen), 2 (Langevin) or 3
-    (Nose-Hoover, variable xi) from step0; returns new (u, v, F) (and xi)."""
+    """Velocity-Verlet with thermostat 0 (none), 1 (Berendsen), 2 (Langevin), 3
+    (Nose-Hoover, variable xi) or 4 (energy bath, xi = the bath energy E0) from
+    step0; returns new (u, v, F) (and xi)."""
     u = _u(u).copy()
     v = _d(v).copy()
     F = _d(F).copy()

@@ -962,6 +962,15 @@ void orc_langevin_normals(uint64_t seed, uint32_t id, int64_t step, uint32_t rep
 /*     half-kick, drift, forces, half-kick; v *= e^{-xi dt/2};               */
 /*     xi += dt/2 (2 KE - g T0)/Q (KE of the scaled velocities).             */
 /*     *xi (in/out) carries the variable between calls.                      */
+/*  thermostat 4: energy bath (NVE; Sec. 2.1 names the scheme without its    */
+/*     steps).  Reading: a Berendsen-type relaxation of the total energy     */
+/*     H = K + U toward the bath energy E0 (*xi, unchanged), with U the      */
+/*     potential (all four terms of orc_forces, the random batches of that   */
+/*     step) of the new configuration and K the kinetic energy after the     */
+/*     second half-kick: K -> K + (dt/tau)(E0 - U - K), i.e.                 */
+/*     lambda^2 = a = 1 + (dt/tau)((E0 - U)/K - 1), lambda = sqrt(a) with a  */
+/*     clamped to [0.64, 1.5625] (lambda in [0.8, 1.25], as Berendsen); no  */
+/*     rescale when K = 0.  tau = dt puts H at E0 after every step.          */
 /* One call advances step0 -> step0 + n_steps.  F (in/out): the forces used  */
 /* by the first half-kick (those of step0, plus its Langevin force if any);  */
 /* on return those of step0 + n_steps.                                       */
@@ -993,8 +1002,9 @@ void orc_vv(int64_t n, uint32_t *u, double *v, double *F, const double *q, const
             int64_t du = (int64_t)nearbyint(v[i] * c);
             u[i] = (uint32_t)((uint64_t)u[i] + (uint64_t)du);
         }
+        double E[4] = {0.0, 0.0, 0.0, 0.0};
         orc_forces(n, u, q, type, n_types, eps, sig, L, alpha, coulomb_k, r_core, r_cut, p, P,
-                   seed, step0 + s + 1, replica, exact, F, NULL);
+                   seed, step0 + s + 1, replica, exact, F, E);
         if (thermostat == 2) {
             const double gamma = 1.0 / tau, sd = sqrt(2.0 * gamma * T0 / dt);
             for (int64_t i = 0; i < n; ++i) {
@@ -1015,6 +1025,15 @@ void orc_vv(int64_t n, uint32_t *u, double *v, double *F, const double *q, const
             const double f = exp(-0.5 * dt * *xi);
             for (int64_t i = 0; i < 3 * n; ++i) v[i] *= f;
             *xi += 0.5 * dt * (2.0 * orc_kinetic(n, v) - g * T0) / Q;
+        }
+        if (thermostat == 4) {
+            const double K = orc_kinetic(n, v);
+            const double U = E[0] + E[1] + E[2] + E[3];
+            if (K > 0.0) {
+                const double a = 1.0 + (dt / tau) * ((*xi - U) / K - 1.0);
+                const double lam = a <= 0.64 ? 0.8 : (a >= 1.5625 ? 1.25 : sqrt(a));
+                for (int64_t i = 0; i < 3 * n; ++i) v[i] *= lam;
+            }
         }
     }
 }
