@@ -102,12 +102,14 @@ typedef struct {
     double r_cut;        /* outer radius (paper r_s), r_cut < L/2 */
     int32_t rbl_p;       /* RBL shell batch size p, 1..1024 (Eq. 15); above 32 an atom
                             whose lists overflow latches RBMD_ERR_CELL_OVERFLOW */
-    int32_t thermostat;  /* 0 none (NVE), 1 Berendsen, 2 Langevin, 3 Nose-Hoover (rbmd_step) */
+    int32_t thermostat;  /* 0 none (NVE), 1 Berendsen, 2 Langevin, 3 Nose-Hoover, 4 energy
+                            bath (NVE held at the bath energy E0, Sec. 2.1; rbmd_step) */
     double coulomb_k;    /* Coulomb prefactor (1/(4 pi eps0) of Eq. 3; Bjerrum length in reduced units) */
     double dt;           /* time step */
     double temperature;  /* thermostat target T0 (k_B = 1) */
-    double tau_T;        /* thermostat time: Berendsen coupling time, Langevin 1/gamma,
-                            Nose-Hoover period scale (Q = g T0 tau^2); <= 0 selects 0.1 */
+    double tau_T;        /* thermostat time: Berendsen and energy-bath coupling time,
+                            Langevin 1/gamma, Nose-Hoover period scale (Q = g T0 tau^2);
+                            <= 0 selects 0.1 */
     uint64_t seed;       /* Philox key of every random draw */
     uint32_t replica;    /* replica index mixed into the random streams */
     int32_t precision;   /* rbmd_precision */
@@ -348,7 +350,16 @@ int64_t rbmd_candidate_rebuilds(rbmd_ctx *ctx);
 /*
  * Nose-Hoover variable xi of every replica at the step boundary (host double [R]),
  * for checkpoints; rbmd_set_thermostat also makes the next rbmd_step recompute the
- * forces.  A Berendsen factor is folded into the velocities that rbmd_get_state
+ * forces.  Energy bath (thermostat 4): the bath energy E0 of every replica.  The
+ * bath relaxes the total energy H = K + U toward E0 after every second half kick,
+ * lambda^2 = 1 + (dt/tau_T)((E0 - U)/K - 1) clamped to [0.64, 1.5625], U the
+ * potential of the step's force evaluation (its random batches) -- a reading of
+ * the energy-stable scheme that Sec. 2.1 names without its steps.  Unless set,
+ * the first rbmd_step of a run takes E0 = K + U of the state it starts from (NaN
+ * is returned until then); rbmd_set_state, rbmd_set_state_u, rbmd_set_charges,
+ * rbmd_set_lj and rbmd_forces_host clear it, so set it after them.  Each step of
+ * this thermostat also evaluates the potential (the energy sums of the pair
+ * kernels and of the modes).  A Berendsen factor is folded into the velocities that rbmd_get_state
  * returns; the Langevin random force of the last step is not part of the state
  * (a resumed Langevin run draws the same later noise but restarts its first
  * half-kick from the conservative force).

@@ -447,7 +447,8 @@ class RBMD:
         self._torch.cuda.current_stream(self.device).synchronize()
 
     def thermostat_state(self):
-        """Nose-Hoover variable xi of every replica (numpy [R])."""
+        """Nose-Hoover variable xi, or the energy bath's E0 (NaN until the first
+        step takes it), of every replica (numpy [R])."""
         xi = np.zeros(self.R)
         _check(lib().rbmd_get_thermostat(self._h, _ptr(xi)), "get_thermostat")
         return xi

@@ -248,6 +248,13 @@ __global__ void k_sum_modes(const double *__restrict__ emode, const int4 *__rest
     }
 }
 
+rbmd_status sum_modes(rbmd_ctx *c)
+{
+    k_sum_modes<<<c->R, 256, 0, c->stream>>>(c->emode, c->modes, c->reps, c->Pm, c->prm.alpha, c->scal);
+    RBMD_LAUNCH_CHECK();
+    return RBMD_OK;
+}
+
 __global__ void k_max_count(const int32_t *__restrict__ count, int64_t n, int32_t *__restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -437,9 +444,10 @@ static bool candidates_for_call(rbmd_ctx *c, int accumulate)
     return true;
 }
 
+// energy: also the potential's terms into scal (SCAL_EPAIR, SCAL_ERBE; the energy bath)
 rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, bool apply_corr,
                         bool marks = false, const StepRef *kick = nullptr, bool *kicked = nullptr,
-                        bool counted = false, bool verlet = false)
+                        bool counted = false, bool verlet = false, bool energy = false)
 {
     if (kicked) *kicked = false;
     const bool do_rbe = !(c->prm.flags & RBMD_NO_RBE);
@@ -456,6 +464,7 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
         c->stream = c->side;
         rbmd_status st = rbe_sample(c, s);
         if (st == RBMD_OK) st = rbe_structure_factors(c, -1);
+        if (st == RBMD_OK && energy) st = sum_modes(c);
         c->stream = main;
         RBMD_CHECK_CUDA(cudaEventRecord(c->ev_join, c->side));
         if (st != RBMD_OK) {
@@ -470,12 +479,13 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
         if (verlet && !accumulate) {
             st = verlet_prepare(c);
             if (marks) prof_mark(c, 2);  // stages 3 and 4 are marked inside
-            if (st == RBMD_OK) st = rbl_pairs_verlet(c, s, force, marks);
+            if (st == RBMD_OK) st = rbl_pairs_verlet(c, s, force, marks, energy);
         } else {
             st = cells_build(c, counted);
             if (marks) prof_mark(c, 2);  // stages 3 and 4 are marked inside
-            if (st == RBMD_OK) st = rbl_pairs(c, s, force, acc, false, nullptr, nullptr, nullptr, marks);
+            if (st == RBMD_OK) st = rbl_pairs(c, s, force, acc, energy, nullptr, nullptr, nullptr, marks);
         }
+        if (st == RBMD_OK && energy) st = md_sum_replicas(c, c->epart, EPART, SCAL_EPAIR, 1.0, false, true);
         if (marks) prof_mark(c, 5);
         if (st == RBMD_OK)
             st = rbl_correction(c, force, apply_corr, apply_corr ? SCAL_FCORR_AUX : SCAL_FCORR);
@@ -486,6 +496,10 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
         acc = 1;
     } else {
         for (int k = 2; k <= 5 && marks; ++k) prof_mark(c, k);
+        if (energy) {
+            k_zero_slots<<<(c->R * EPART + 255) / 256, 256, 0, c->stream>>>(c->scal, c->R, SCAL_EPAIR, EPART);
+            RBMD_LAUNCH_CHECK();
+        }
         if (!apply_corr) {
             k_zero_slots<<<(c->R * 3 + 255) / 256, 256, 0, c->stream>>>(c->scal, c->R, SCAL_FCORR, 3);
             RBMD_LAUNCH_CHECK();
@@ -498,7 +512,11 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
         RBMD_CHECK(rbe_sample(c, s));
         if (marks) prof_mark(c, 7);
         RBMD_CHECK(rbe_structure_factors(c, marks ? 8 : -1));
+        if (energy) RBMD_CHECK(sum_modes(c));
         if (marks) prof_mark(c, 9);
+    } else if (energy) {
+        k_zero_slots<<<(c->R + 255) / 256, 256, 0, c->stream>>>(c->scal, c->R, SCAL_ERBE, 1);
+        RBMD_LAUNCH_CHECK();
     }
     if (do_rbe) {
         RBMD_CHECK(rbe_apply_forces(c, force, acc, kick));
@@ -521,7 +539,8 @@ rbmd_status record_step(rbmd_ctx *c)
     const bool bin = !(c->prm.flags & RBMD_NO_RBL) && !c->verlet;
     RBMD_CHECK(md_kick_drift(c, bin));
     bool kicked = false;
-    RBMD_CHECK(forces_into(c, next, c->force, 0, false, true, &next, &kicked, bin, c->verlet));
+    RBMD_CHECK(forces_into(c, next, c->force, 0, false, true, &next, &kicked, bin, c->verlet,
+                           c->prm.thermostat == 4));
     prof_mark(c, 10);
     RBMD_CHECK(md_kick_thermo(c, true, next, kicked));
     prof_mark(c, 11);
@@ -616,7 +635,7 @@ rbmd_status init_ctx(const rbmd_params *prms, int32_t R, const void *pos, const 
     if (!(p.r_core >= 0.0) || p.r_core > p.r_cut) return RBMD_ERR_INVALID;
     if (p.rbe_P < 1 || p.rbl_p < 1 || p.rbl_p > 1024) return RBMD_ERR_INVALID;
     if (p.precision != RBMD_FP32 && p.precision != RBMD_FP64) return RBMD_ERR_INVALID;
-    if (p.thermostat < 0 || p.thermostat > 3) return RBMD_ERR_INVALID;
+    if (p.thermostat < 0 || p.thermostat > 4) return RBMD_ERR_INVALID;
     if (p.cell_div < 0 || p.cell_div > 2) return RBMD_ERR_INVALID;
     if ((p.flags & RBMD_FULL_EWALD_MODES) && R != 1) return RBMD_ERR_UNSUPPORTED;
     if ((p.flags & RBMD_FULL_EWALD_MODES) && (p.flags & RBMD_METROPOLIS_MODES))
@@ -1130,6 +1149,7 @@ rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t 
     cudaStreamSynchronize(c->side);
     c->step = step;
     c->have_force = false;
+    c->bath_set = false;  // a new state or potential: a new bath energy
     if (!vl) c->vl_dirty = true;  // the cell walk re-sorted the atoms
     return leave(c, st);
 }
@@ -1152,7 +1172,7 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
     if (!c->have_force) {
         k_set_i64<<<1, 1, 0, c->stream>>>(c->d_step, c->step);
         s = forces_into(c, StepRef{nullptr, c->step}, c->force, 0, false, false, nullptr, nullptr,
-                        false, c->verlet);
+                        false, c->verlet, c->prm.thermostat == 4);  // the step's kernels
         if (s == RBMD_OK) s = md_thermo_prepare(c);
         if (s != RBMD_OK) return leave(c, s);
         c->have_force = true;
@@ -1267,11 +1287,7 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
     if (!(c->prm.flags & RBMD_NO_RBE)) {
         s = rbe_sample(c, r);
         if (s == RBMD_OK) s = rbe_structure_factors(c);
-        if (s == RBMD_OK) {
-            k_sum_modes<<<R, 256, 0, c->stream>>>(c->emode, c->modes, c->reps, c->Pm,
-                                                   c->prm.alpha, c->scal);
-            s = cuda_status(cudaPeekAtLastError());
-        }
+        if (s == RBMD_OK) s = sum_modes(c);
     }
     gprof_mark(c, 1);
     if (s == RBMD_OK && !(c->prm.flags & RBMD_NO_RBL)) {
@@ -1578,6 +1594,7 @@ rbmd_status rbmd_set_charges(rbmd_ctx *c, const void *charge)
                                                  c->type, c->T, c->err);
     rbmd_status s = charge_sums(c, false);
     c->have_force = false;
+    c->bath_set = false;  // a new state or potential: a new bath energy
     c->vl_dirty = true;
     c->lists_cached = c->rho_cached = false;
     return leave(c, s);
@@ -1589,6 +1606,7 @@ rbmd_status rbmd_set_lj(rbmd_ctx *c, const double *lj_eps, const double *lj_sigm
     enter(c);
     rbmd_status s = upload_lj(c, lj_eps, lj_sigma);
     c->have_force = false;
+    c->bath_set = false;  // a new state or potential: a new bath energy
     c->vl_dirty = true;
     return leave(c, s);
 }
@@ -1632,6 +1650,7 @@ rbmd_status rbmd_set_state(rbmd_ctx *c, const void *pos, const void *vel, int64_
     }
     c->step = step;
     c->have_force = false;
+    c->bath_set = false;  // a new state or potential: a new bath energy
     c->vl_dirty = true;
     return leave(c, s);
 }
@@ -1674,6 +1693,7 @@ rbmd_status rbmd_set_state_u(rbmd_ctx *c, const uint32_t *u, const void *vel, in
     }
     c->step = step;
     c->have_force = false;
+    c->bath_set = false;  // a new state or potential: a new bath energy
     c->vl_dirty = true;
     c->lists_cached = c->rho_cached = false;
     return leave(c, s);
@@ -1689,6 +1709,8 @@ rbmd_status rbmd_get_thermostat(rbmd_ctx *c, double *xi)
     if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
     if (s == RBMD_OK)
         for (int r = 0; r < c->R; ++r) xi[r] = h[(size_t)r * SCAL_COUNT + SCAL_XI];
+    if (s == RBMD_OK && c->prm.thermostat == 4 && !c->bath_set)
+        for (int r = 0; r < c->R; ++r) xi[r] = NAN;  // taken by the next rbmd_step
     return leave(c, s);
 }
 
@@ -1702,6 +1724,7 @@ rbmd_status rbmd_set_thermostat(rbmd_ctx *c, const double *xi)
                                         sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
     c->have_force = false;
+    c->bath_set = s == RBMD_OK;
     c->vl_dirty = true;  // the next rbmd_step redoes the first half update
     return leave(c, s);
 }

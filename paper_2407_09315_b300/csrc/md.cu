@@ -239,7 +239,11 @@ __global__ void k_kick_ke(real *__restrict__ v, real *__restrict__ F,
 //   Nose-Hoover: lambda1 = e^{-xi dt/2} (second half of the step), the end-of-
 //                step update xi += dt/2 (2K' - g T0)/Q with K' = lambda1^2 K, then
 //                the next step's first update (same K') and lambda2 = e^{-xi dt/2};
-//                read-out uses lambda1, the next kick lambda1 lambda2.
+//                read-out uses lambda1, the next kick lambda1 lambda2;
+//   energy bath: lambda^2 = a = 1 + (dt/tau)((E0 - U)/K - 1), a clamped to
+//                [0.64, 1.5625], no rescale at K = 0; U the potential of the step's
+//                force evaluation (its energy sums in scal), E0 in SCAL_XI; applied
+//                like the Berendsen factor.
 __global__ void k_thermo(const double *__restrict__ kepart, const Rep *__restrict__ reps,
                          double *__restrict__ scal, int thermostat, double dt, double tau,
                          int64_t *__restrict__ d_step, int advance)
@@ -274,6 +278,11 @@ __global__ void k_thermo(const double *__restrict__ kepart, const Rep *__restric
         sc[SCAL_XI_RUN] = xi_r;
         lam = lam1;
         lam_kick = lam1 * exp(-0.5 * dt * xi_r);
+    } else if (thermostat == 4 && ke > 0.0) {
+        const double U = sc[SCAL_EPAIR] + sc[SCAL_EPAIR + 1] + sc[SCAL_ERBE] + rp.e_self;
+        const double a = 1.0 + (dt / tau) * ((sc[SCAL_XI] - U) / ke - 1.0);
+        lam = a <= 0.64 ? 0.8 : (a >= 1.5625 ? 1.25 : sqrt(a));
+        lam_kick = lam;
     }
     sc[SCAL_KE] = ke;
     sc[SCAL_LAMBDA] = lam;
@@ -411,8 +420,27 @@ rbmd_status md_kinetic(rbmd_ctx *c, int slot)
     return RBMD_OK;
 }
 
+// Energy bath at the start of a run without a set E0: E0 = K + U of the state the
+// run starts from (K of the read-out velocities, U from the energy sums of the
+// force evaluation of that state).
+__global__ void k_bath_prepare(const Rep *__restrict__ reps, int R, double *__restrict__ scal)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double *sc = scal + (int64_t)r * SCAL_COUNT;
+    const double U = sc[SCAL_EPAIR] + sc[SCAL_EPAIR + 1] + sc[SCAL_ERBE] + reps[r].e_self;
+    sc[SCAL_XI] = sc[SCAL_KE_TRUE] + U;
+}
+
 rbmd_status md_thermo_prepare(rbmd_ctx *c)
 {
+    if (c->prm.thermostat == 4 && !c->bath_set) {
+        RBMD_CHECK(md_kinetic(c, SCAL_KE_TRUE));
+        k_bath_prepare<<<(c->R + 127) / 128, 128, 0, c->stream>>>(c->reps, c->R, c->scal);
+        RBMD_LAUNCH_CHECK();
+        c->bath_set = true;
+        return RBMD_OK;
+    }
     if (c->prm.thermostat != 3) return RBMD_OK;
     RBMD_CHECK(md_kinetic(c, SCAL_KE_TRUE));
     k_nh_prepare<<<(c->R + 127) / 128, 128, 0, c->stream>>>(c->reps, c->R, c->scal, c->prm.dt,

@@ -386,6 +386,7 @@ struct rbmd_ctx {
     // integrator state
     int64_t step;
     bool have_force;
+    bool bath_set = false;  // energy bath: SCAL_XI holds E0 (set, or taken at a run's start)
     cudaGraphExec_t graph;
     bool graph_ready;
     int32_t graph_kernels;
@@ -415,7 +416,7 @@ enum {
     SCAL_FCORR_AUX = 12,  // [3] correction of stand-alone force calls
     SCAL_ESELF = 15,      // self energy (kept on the device for batched read-out)
     SCAL_LAMBDA_KICK = 16,  // factor applied to the stored velocities by the next kick
-    SCAL_XI = 17,         // Nose-Hoover variable at the step boundary
+    SCAL_XI = 17,         // Nose-Hoover variable at the step boundary; the energy bath's E0
     SCAL_XI_RUN = 18,     // Nose-Hoover variable during the step (after its first half update)
     SCAL_EPAIR = 20,      // [EPART] pair-list sums: E_coul, E_lj, tr W_coul, tr W_lj, W[6]
     SCAL_VRBE = 30,       // [6] RBE virial estimate xx yy zz xy xz yz

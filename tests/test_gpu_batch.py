@@ -130,7 +130,7 @@ def test_batch_energies_equal_standalone(systems, prec):
     b.close()
 
 
-@pytest.mark.parametrize("thermostat", [0, 1, 2, 3])
+@pytest.mark.parametrize("thermostat", [0, 1, 2, 3, 4])
 def test_batch_trajectory_equals_standalone(systems, thermostat):
     import torch
 
