@@ -268,7 +268,10 @@ def make_ctx(system, precision, device):
     return ctx
 
 
-def time_steps(ctx, K, W, flush, profile):
+def time_steps(ctx, K, W, flush, profile, timed_rebuilds=None):
+    """W warm-up and K timed steps; per-step CUDA-event times and (profile) the
+    stage times.  timed_rebuilds (a list): the candidate-list rebuilds of the K
+    timed steps are appended to it (counted outside the timed region)."""
     import torch
 
     stream = torch.cuda.current_stream()
@@ -280,6 +283,7 @@ def time_steps(ctx, K, W, flush, profile):
     torch.cuda.synchronize()
     if profile:
         ctx.profile_read(reset=True)
+    reb0 = ctx.candidate_rebuilds() if timed_rebuilds is not None else 0
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
     for k in range(K):
@@ -290,6 +294,8 @@ def time_steps(ctx, K, W, flush, profile):
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in ev]
     stages = ctx.profile_read(reset=True)[0] if profile else None
+    if timed_rebuilds is not None:
+        timed_rebuilds.append(ctx.candidate_rebuilds() - reb0)
     return ms, stages
 
 
@@ -545,12 +551,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     reb0 = ctx.candidate_rebuilds()
-    ms, _ = time_steps(ctx, args.steps, args.warmup, flush, profile=False)
+    timed_reb = []
+    ms, _ = time_steps(ctx, args.steps, args.warmup, flush, profile=False, timed_rebuilds=timed_reb)
     clk = clocks.stop()
     # rebuilds of the step's neighbour candidate lists inside the warm-up and timed
     # steps (the timed mean includes them as they come)
     rebuilds = ctx.candidate_rebuilds() - reb0
     kernels_per_step = ctx.step_kernel_count()
+    # the rebuild kernels of the step graph's conditional node run on rebuild steps only
+    rebuild_kernels = ctx.rebuild_kernel_count()
     total_ms = max_over_ranks(sum(ms), dist, device)
     if dist:
         dist.barrier()
@@ -609,9 +618,10 @@ def run_ours(args):
                                "stages serialised on one stream"},
         "roofline": roofline(stage_ms, system, 2032.0),
         "sm_count": SM_COUNT[0],
-        "gpu_launches": kernels_per_step * args.steps,
+        "gpu_launches": kernels_per_step * args.steps + rebuild_kernels * timed_reb[0],
         "device_memory_bytes": int(footprint),
         "kernels_per_step": kernels_per_step,
+        "rebuild_kernels": {"per_rebuild": rebuild_kernels, "rebuilds_in_timed_steps": timed_reb[0]},
         "candidate_rebuilds": {"in_warmup_and_timed_steps": rebuilds,
                                "steps": args.steps + args.warmup},
         "tiles": dict(tiles, names=["cell_div", "rho_tile", "rho_mode_tile", "pair_table"]),

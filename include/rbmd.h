@@ -484,12 +484,18 @@ rbmd_status rbmd_sampler_table(double box_length, double alpha, int32_t *M, uint
  * rbmd_profile_read: accumulated milliseconds per stage (host double
  *   [RBMD_PROFILE_STAGES]) and the number of profiled steps; reset != 0 zeroes them.
  * rbmd_step_kernel_count: kernel launches in one step graph (captured on the
- *   first rbmd_step; 0 before that).
+ *   first rbmd_step; 0 before that) on a step without a candidate-list rebuild.
+ * rbmd_rebuild_kernel_count: the kernels a step adds when it rebuilds the
+ *   candidate lists (the body of the graph's conditional node; 0 when the rebuild
+ *   kernels are ordinary graph nodes that return at once on other steps, which
+ *   rbmd_step_kernel_count then includes, as with RBMD_GRAPH_COND=0 in the
+ *   environment, or when the step has no candidate lists).
  */
 #define RBMD_PROFILE_STAGES 11
 rbmd_status rbmd_profile(rbmd_ctx *ctx, int enable);
 rbmd_status rbmd_profile_read(rbmd_ctx *ctx, double *ms, int64_t *steps, int reset);
 int32_t rbmd_step_kernel_count(rbmd_ctx *ctx);
+int32_t rbmd_rebuild_kernel_count(rbmd_ctx *ctx);
 
 /*
  * rbmd_profile_read_grad: while profiling is enabled, rbmd_energy and

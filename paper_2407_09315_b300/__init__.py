@@ -114,6 +114,7 @@ def lib():
         "rbmd_profile": ([P, C.c_int], C.c_int),
         "rbmd_profile_read": ([P, P, C.POINTER(i64), C.c_int], C.c_int),
         "rbmd_step_kernel_count": ([P], i32),
+        "rbmd_rebuild_kernel_count": ([P], i32),
         "rbmd_profile_read_grad": ([P, P, P, P, C.c_int], C.c_int),
         "rbmd_set_charges": ([P, P], C.c_int),
         "rbmd_set_lj": ([P, P, P], C.c_int),
@@ -533,6 +534,10 @@ class RBMD:
 
     def step_kernel_count(self) -> int:
         return lib().rbmd_step_kernel_count(self._h)
+
+    def rebuild_kernel_count(self) -> int:
+        """Kernels a step adds when it rebuilds the candidate lists."""
+        return lib().rbmd_rebuild_kernel_count(self._h)
 
     def debug_latch_error(self, code):
         _check(lib().rbmd_debug_latch_error(self._h, code))

@@ -288,6 +288,7 @@ void free_ctx(rbmd_ctx *c)
         if (c->gprof_ev[k]) cudaEventDestroy(c->gprof_ev[k]);
     delete[] c->reps_h;
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->cond_stream) cudaStreamDestroy(c->cond_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->copy) cudaStreamDestroy(c->copy);
@@ -684,6 +685,7 @@ rbmd_status init_ctx(const rbmd_params *prms, int32_t R, const void *pos, const 
         TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)));
         TRY(cuda_status(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)));
     }
+    c->cond_nodes = !(getenv("RBMD_GRAPH_COND") && atoi(getenv("RBMD_GRAPH_COND")) == 0);
     // RBMD_ONE_STREAM=1 keeps every force evaluation on the context's stream
     // (the two-stream and one-stream evaluations compute the same bits)
     if (!(getenv("RBMD_ONE_STREAM") && atoi(getenv("RBMD_ONE_STREAM")) != 0)) {
@@ -1201,6 +1203,7 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
         if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return leave(c, RBMD_ERR_CUDA);
         c->capturing = true;
+        c->graph_cond_kernels = 0;
         rbmd_status rs = record_step(c);
         c->capturing = false;
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
@@ -1817,6 +1820,7 @@ rbmd_status rbmd_profile_read(rbmd_ctx *c, double *ms, int64_t *steps, int reset
 }
 
 int32_t rbmd_step_kernel_count(rbmd_ctx *c) { return c ? c->graph_kernels : 0; }
+int32_t rbmd_rebuild_kernel_count(rbmd_ctx *c) { return c ? c->graph_cond_kernels : 0; }
 
 rbmd_status rbmd_rbe_rho_partial(rbmd_ctx *c, int64_t step, int64_t *acc)
 {

@@ -2061,13 +2061,10 @@ static VlArgs vl_args(rbmd_ctx *c)
     return v;
 }
 
+// The rebuild of the candidate lists when *flag is set (every kernel checks it).
 template <typename real>
-static rbmd_status verlet_prepare_t(rbmd_ctx *c)
+static rbmd_status vl_rebuild(rbmd_ctx *c, int32_t *flag)
 {
-    int32_t *flag = c->ibuf + 4;
-    k_vl_gather<<<c->nb256, 256, 0, c->stream>>>(c->reps, c->map256, c->spos, c->u4, c->vl_sref,
-                                                  flag, c->N, c->err);
-    RBMD_LAUNCH_CHECK();
     RBMD_CHECK(cells_sort(c, false, flag));
     PairArgs<real> a = pair_args<real>(c, StepRef{nullptr, 0});
     a.stale = 1;  // cull at r_cut + skin: the candidates reach Rv
@@ -2076,6 +2073,84 @@ static rbmd_status verlet_prepare_t(rbmd_ctx *c)
     k_vl_done<<<1, 1, 0, c->stream>>>(flag, c->ibuf + 5);
     RBMD_LAUNCH_CHECK();
     return RBMD_OK;
+}
+
+// Opens the conditional node of the step graph when the displacement test found a
+// rebuild due.
+__global__ void k_vl_cond(const int32_t *__restrict__ flag, cudaGraphConditionalHandle h)
+{
+    cudaGraphSetConditional(h, *flag != 0 ? 1u : 0u);
+}
+
+// Inside the capture of the step graph: the rebuild kernels become the body of a
+// conditional (if) node that k_vl_cond opens on the steps whose displacement test
+// asks for a rebuild, so the other steps launch none of them.  Returns false,
+// with nothing captured, when the node cannot be made (the caller then captures
+// the device-conditional kernels themselves).
+template <typename real>
+static bool vl_rebuild_node(rbmd_ctx *c, int32_t *flag, rbmd_status *st)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    cudaGraphConditionalHandle h;
+    if (!c->cond_stream &&
+        cudaStreamCreateWithFlags(&c->cond_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->cond_stream = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, &ed, &nd) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive ||
+        cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    *st = RBMD_OK;
+    k_vl_cond<<<1, 1, 0, c->stream>>>(flag, h);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, &ed, &nd) != cudaSuccess) {
+        *st = RBMD_ERR_CUDA;
+        return true;
+    }
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};  // the rest zero
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, deps, ed, nd, &np) != cudaSuccess ||
+        cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies) != cudaSuccess ||
+        cudaStreamBeginCaptureToGraph(c->cond_stream, np.conditional.phGraph_out[0], nullptr,
+                                      nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        *st = RBMD_ERR_CUDA;
+        return true;
+    }
+    const cudaStream_t main = c->stream;
+    c->stream = c->cond_stream;
+    *st = vl_rebuild<real>(c, flag);
+    c->stream = main;
+    cudaGraph_t body;
+    if (cudaStreamEndCapture(c->cond_stream, &body) != cudaSuccess && *st == RBMD_OK)
+        *st = RBMD_ERR_CUDA;
+    size_t nn = 0;
+    if (*st == RBMD_OK) cudaGraphGetNodes(np.conditional.phGraph_out[0], nullptr, &nn);
+    c->graph_cond_kernels = (int32_t)nn;  // kernel nodes only: the body holds nothing else
+    return true;
+}
+
+template <typename real>
+static rbmd_status verlet_prepare_t(rbmd_ctx *c)
+{
+    int32_t *flag = c->ibuf + 4;
+    k_vl_gather<<<c->nb256, 256, 0, c->stream>>>(c->reps, c->map256, c->spos, c->u4, c->vl_sref,
+                                                  flag, c->N, c->err);
+    RBMD_LAUNCH_CHECK();
+    rbmd_status st = RBMD_OK;
+    if (c->capturing && c->cond_nodes && vl_rebuild_node<real>(c, flag, &st)) return st;
+    return vl_rebuild<real>(c, flag);
 }
 
 rbmd_status verlet_prepare(rbmd_ctx *c)

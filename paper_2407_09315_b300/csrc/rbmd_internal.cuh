@@ -274,6 +274,11 @@ struct rbmd_ctx {
     // positions encoded, forces final), 8 chunks at most
     cudaStream_t copy;
     cudaEvent_t ev_h2d[8], ev_enc[8], ev_fin[8];
+    // the step graph: the candidate-list rebuild kernels form the body of a
+    // conditional node (captured on cond_stream); off with RBMD_GRAPH_COND=0
+    cudaStream_t cond_stream = nullptr;
+    bool cond_nodes = false;
+    int32_t graph_cond_kernels = 0;  // kernels in that body (launched on rebuild steps only)
 
     // spatial decomposition (rbmd_init_slab): global atom ids of the rows (every
     // random draw is keyed by them) and the global atom count; NULL / N otherwise
