@@ -161,28 +161,20 @@ rbmd_status md_sum_replicas_fix(rbmd_ctx *c, const long long *parts, int slot, d
     return RBMD_OK;
 }
 
-// First half kick (with the pending thermostat factor) and drift.
+// The first half kick and drift of one atom (the state update of the integrator's
+// step): v = lambda v + hdt (F + F_corr), u += rint(v dt 2^32 / L) mod 2^32.
 template <typename real>
-__global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
-                             const real *__restrict__ F, const int2 *__restrict__ map,
-                             const Rep *__restrict__ reps, const double *__restrict__ scal,
-                             real hdt, int32_t *__restrict__ count, int32_t *__restrict__ cell_of,
-                             int32_t *__restrict__ rank)
+__device__ __forceinline__ void kick_drift_atom(uint4 &A, real (&v)[3], const real (&f)[3],
+                                                real lam, const real (&fc)[3], real hdt,
+                                                const Rep &rp)
 {
-    const AtomSlot a = atom_slot(map, reps);
-    if (!a.ok) return;
-    const int64_t i = a.i;
-    const double *sc = scal + (int64_t)a.r * SCAL_COUNT;
-    const real lam = (real)sc[SCAL_LAMBDA_KICK];
-    const double dtc = reps[a.r].dtc;
-    uint4 A = u4[i];
     uint32_t *pu = &A.x;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         // lambda * v rounds on its own (no contraction), exactly as a checkpoint
         // read-out does, so a resumed run is bit-identical to an unbroken one
-        real vd = mul_rn(lam, v[3 * i + d]) + hdt * (F[3 * i + d] + (real)sc[SCAL_FCORR + d]);
-        v[3 * i + d] = vd;
+        real vd = mul_rn(lam, v[d]) + hdt * (f[d] + fc[d]);
+        v[d] = vd;
         long long du;
         if constexpr (sizeof(real) == 4) {
             // vd * dtc with dtc = dhi + dlo (two floats): p1 + e1 = vd dhi exactly,
@@ -190,26 +182,67 @@ __global__ void k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
             // operations are scarce on this GPU).  The product is good to about
             // 1e-10 units, so the integer is that of the FP64 product except within
             // that distance of a half-integer.
-            const float dhi = reps[a.r].dtc_hi, dlo = reps[a.r].dtc_lo;
+            const float dhi = rp.dtc_hi, dlo = rp.dtc_lo;
             const float p1 = __fmul_rn(vd, dhi);
             const float e1 = __fmaf_rn(vd, dhi, -p1);
             const float t = __fmaf_rn(vd, dlo, e1);
             const float r = rintf(p1);
             du = (long long)r + (long long)rintf(__fadd_rn(__fsub_rn(p1, r), t));
         } else {
-            du = llrint((double)vd * dtc);
+            du = llrint((double)vd * rp.dtc);
         }
         pu[d] = pu[d] + (uint32_t)du;
     }
-    u4[i] = A;
-    if (count) {
-        const Rep &rp = reps[a.r];
-        const int nc = rp.nc;
-        const int64_t c = rp.cell0 +
-                          ((int64_t)cell_coord(A.x, nc) * nc + cell_coord(A.y, nc)) * nc +
-                          cell_coord(A.z, nc);
-        cell_of[i] = (int32_t)c;
-        rank[i] = atomicAdd(&count[c], 1);
+}
+
+// First half kick (with the pending thermostat factor) and drift: AT atoms per
+// thread (atoms j, j + 256/AT, ... of the 256-atom block), their loads issued
+// together.
+template <typename real, int AT>
+__global__ void __launch_bounds__(256 / AT) k_kick_drift(uint4 *__restrict__ u4, real *__restrict__ v,
+                             const real *__restrict__ F, const int2 *__restrict__ map,
+                             const Rep *__restrict__ reps, const double *__restrict__ scal,
+                             real hdt, int32_t *__restrict__ count, int32_t *__restrict__ cell_of,
+                             int32_t *__restrict__ rank)
+{
+    constexpr int TB = 256 / AT;
+    const int2 mb = map[blockIdx.x];
+    const int r = mb.x;
+    const Rep &rp = reps[r];
+    const int64_t end = rp.atom0 + rp.N;
+    const double *sc = scal + (int64_t)r * SCAL_COUNT;
+    const real lam = (real)sc[SCAL_LAMBDA_KICK];
+    const real fc[3] = {(real)sc[SCAL_FCORR], (real)sc[SCAL_FCORR + 1], (real)sc[SCAL_FCORR + 2]};
+    uint4 A[AT];
+    real vv[AT][3], ff[AT][3];
+#pragma unroll
+    for (int h = 0; h < AT; ++h) {
+        const int64_t i = (int64_t)mb.y + threadIdx.x + h * TB;
+        if (i < end) {
+            A[h] = u4[i];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                vv[h][d] = v[3 * i + d];
+                ff[h][d] = F[3 * i + d];
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < AT; ++h) {
+        const int64_t i = (int64_t)mb.y + threadIdx.x + h * TB;
+        if (i >= end) continue;
+        kick_drift_atom(A[h], vv[h], ff[h], lam, fc, hdt, rp);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[3 * i + d] = vv[h][d];
+        u4[i] = A[h];
+        if (count) {
+            const int nc = rp.nc;
+            const int64_t c = rp.cell0 +
+                              ((int64_t)cell_coord(A[h].x, nc) * nc + cell_coord(A[h].y, nc)) * nc +
+                              cell_coord(A[h].z, nc);
+            cell_of[i] = (int32_t)c;
+            rank[i] = atomicAdd(&count[c], 1);
+        }
     }
 }
 
@@ -317,11 +350,11 @@ rbmd_status md_kick_drift(rbmd_ctx *c, bool bin)
     if (bin)
         RBMD_CHECK_CUDA(cudaMemsetAsync(c->cell_count, 0, sizeof(int32_t) * c->ncell, c->stream));
     if (c->fp64)
-        k_kick_drift<double><<<c->nb256, 256, 0, c->stream>>>(
+        k_kick_drift<double, 1><<<c->nb256, 256, 0, c->stream>>>(
             c->u4, (double *)c->vel, (const double *)c->force, c->map256, c->reps, c->scal, hdt,
             count, c->cell_of, c->cell_rank);
     else
-        k_kick_drift<float><<<c->nb256, 256, 0, c->stream>>>(
+        k_kick_drift<float, 2><<<c->nb256, 128, 0, c->stream>>>(
             c->u4, (float *)c->vel, (const float *)c->force, c->map256, c->reps, c->scal,
             (float)hdt, count, c->cell_of, c->cell_rank);
     RBMD_LAUNCH_CHECK();
