@@ -76,16 +76,20 @@ rbmd_status md_sum(rbmd_ctx *c, const double *parts, int nparts, int ncomp, doub
 }
 
 // Per-replica sums of the 4 nb128 per-warp partials of its 128-atom blocks (and
-// the same range of the second segment) in two fixed-order stages: block
+// the same range of the second segment, the overflow fallback's, when *use2 is
+// set: a pass without overflowed atoms leaves that segment unwritten, and adding
+// its zeros would change no bit) in two fixed-order stages: block
 // (k, r) sums chunk k of RED_SPLIT equal chunks of replica r's range, then one
 // block per replica adds its RED_SPLIT chunk sums.  The chunking depends only on
 // the replica's own size, so a replica sums identically alone or in a batch.
 // T: double, or long long for fixed-point partials (exact sums).
 template <int NC, typename T>
 __global__ void k_sum_replicas1(const T *__restrict__ parts, int64_t seg2,
-                                const Rep *__restrict__ reps, T *__restrict__ tmp)
+                                const int32_t *__restrict__ use2, const Rep *__restrict__ reps,
+                                T *__restrict__ tmp)
 {
     __shared__ T s[NC][256];
+    if (seg2 >= 0 && *use2 == 0) seg2 = -1;
     const Rep rp = reps[blockIdx.y];
     const int64_t j0 = 4 * (int64_t)rp.b128_0, nj = 4 * (int64_t)rp.nb128;
     const int64_t chunk = (nj + RED_SPLIT - 1) / RED_SPLIT;
@@ -134,11 +138,14 @@ rbmd_status md_sum_replicas(rbmd_ctx *c, const double *parts, int ncomp, int slo
     const int64_t seg2 = two_segments ? 4 * (int64_t)c->nb128 : -1;
     const dim3 grid(RED_SPLIT, c->R);
     if (ncomp == 3)
-        k_sum_replicas1<3, double><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
+        k_sum_replicas1<3, double><<<grid, 256, 0, c->stream>>>(parts, seg2, c->ibuf + 2, c->reps,
+                                                                c->red_rep);
     else if (ncomp == 2)
-        k_sum_replicas1<2, double><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
+        k_sum_replicas1<2, double><<<grid, 256, 0, c->stream>>>(parts, seg2, c->ibuf + 2, c->reps,
+                                                                c->red_rep);
     else if (ncomp == EPART)
-        k_sum_replicas1<EPART, double><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, c->red_rep);
+        k_sum_replicas1<EPART, double><<<grid, 256, 0, c->stream>>>(parts, seg2, c->ibuf + 2,
+                                                                    c->reps, c->red_rep);
     else return RBMD_ERR_INVALID;
     RBMD_LAUNCH_CHECK();
     k_sum_replicas2<double><<<c->R, 32, 0, c->stream>>>(c->red_rep, ncomp, c->reps, c->scal, slot,
@@ -153,7 +160,8 @@ rbmd_status md_sum_replicas_fix(rbmd_ctx *c, const long long *parts, int slot, d
     const int64_t seg2 = two_segments ? 4 * (int64_t)c->nb128 : -1;
     const dim3 grid(RED_SPLIT, c->R);
     long long *tmp = reinterpret_cast<long long *>(c->red_rep);  // same 8-byte slots
-    k_sum_replicas1<3, long long><<<grid, 256, 0, c->stream>>>(parts, seg2, c->reps, tmp);
+    k_sum_replicas1<3, long long><<<grid, 256, 0, c->stream>>>(parts, seg2, c->ibuf + 2, c->reps,
+                                                               tmp);
     RBMD_LAUNCH_CHECK();
     k_sum_replicas2<long long><<<c->R, 32, 0, c->stream>>>(tmp, 3, c->reps, c->scal, slot, scale,
                                                            per_atom ? 1 : 0, 0x1p-32);

@@ -1311,20 +1311,8 @@ __global__ void __launch_bounds__(kPairBlock) k_rbl_fused(PairArgs<real> a)
     __shared__ uint32_t s_id[FB_LIST][kPairBlock];
     const int tid = threadIdx.x;
     constexpr int WPB = kPairBlock / 32;  // partial slots (warps) per map block
-    if (*a.ovf == 0) {
-        // nothing overflowed: the fallback's partial slots are zero
-        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + tid; j < (int64_t)a.nmap * WPB;
-             j += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t part = a.fb_part0 + j;
-            a.fpart[3 * part + 0] = 0;
-            a.fpart[3 * part + 1] = 0;
-            a.fpart[3 * part + 2] = 0;
-            if constexpr (ENERGY) {
-                for (int c = 0; c < EPART; ++c) a.epart[EPART * part + c] = 0.0;
-            }
-        }
-        return;
-    }
+    // nothing overflowed: the partial sums skip the fallback's slots
+    if (*a.ovf == 0) return;
     for (int t = tid; t < 2 * a.T; t += blockDim.x) s_lj[t] = a.lj[t];
     __syncthreads();
     for (int mb = blockIdx.x; mb < a.nmap; mb += gridDim.x) {
@@ -1452,8 +1440,9 @@ __global__ void k_rbl_no_fallback(const int32_t *__restrict__ ovf, int *__restri
                                   long long *__restrict__ fpart, double *__restrict__ epart,
                                   int64_t part0, int64_t nparts)
 {
+    if (*ovf == 0) return;  // the partial sums skip the fallback's slots
     const int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j0 == 0 && *ovf != 0) latch_error(err, RBMD_ERR_CELL_OVERFLOW);
+    if (j0 == 0) latch_error(err, RBMD_ERR_CELL_OVERFLOW);
     for (int64_t j = j0; j < nparts; j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t part = part0 + j;
         fpart[3 * part + 0] = 0;
