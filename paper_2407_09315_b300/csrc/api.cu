@@ -255,12 +255,23 @@ rbmd_status sum_modes(rbmd_ctx *c)
     return RBMD_OK;
 }
 
+// Largest of n counts into *out: a grid-stride loop, a block maximum and one
+// atomic per block (every block's atomics go to one address).
 __global__ void k_max_count(const int32_t *__restrict__ count, int64_t n, int32_t *__restrict__ out)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int v = i < n ? count[i] : 0;
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+    int v = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v = max(v, count[i]);
+    v = __reduce_max_sync(0xffffffffu, v);
+    __shared__ int s_m[32];
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? s_m[threadIdx.x] : 0;
+        v = __reduce_max_sync(0xffffffffu, v);
+        if (threadIdx.x == 0) atomicMax(out, v);
+    }
 }
 
 void free_ctx(rbmd_ctx *c)
@@ -1305,8 +1316,8 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
         if (s == RBMD_OK) s = md_sum_replicas_fix(c, c->fpart, SCAL_FSUM, 1.0, false, true);
         if (s == RBMD_OK) s = md_sum_replicas(c, c->epart, EPART, SCAL_EPAIR, 1.0, false, true);
         if (s == RBMD_OK) {
-            k_max_count<<<(unsigned)((c->ncell + 255) / 256), 256, 0, c->stream>>>(
-                c->cell_count, c->ncell, c->ibuf + 1);
+            k_max_count<<<(unsigned)std::min<int64_t>((c->ncell + 255) / 256, 1024), 256, 0,
+                          c->stream>>>(c->cell_count, c->ncell, c->ibuf + 1);
         }
     }
     else {

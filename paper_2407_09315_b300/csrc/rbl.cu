@@ -862,7 +862,12 @@ __global__ void __launch_bounds__(256) k_rbl_scan(PairArgs<real> a)
     const int2 cnt = make_int2(ncore, ns);
     a.ncount[is] = cnt;
     if (overflowed(a, cnt)) *a.ovf = 1;
-    if constexpr (ENERGY) atomicMax(a.imax, ns);
+    if constexpr (ENERGY) {
+        // one atomic per group of converged lanes (all to one address)
+        const unsigned m = __activemask();
+        const int mx = __reduce_max_sync(m, ns);
+        if ((threadIdx.x & 31) == __ffs(m) - 1) atomicMax(a.imax, mx);
+    }
     if constexpr (LISTS) {
         a.n_core[A.w] = ncore;
         a.n_shell[A.w] = ns;
@@ -1636,10 +1641,12 @@ static rbmd_status rbl_lists_t(rbmd_ctx *c, StepRef s)
 __global__ void k_max_counts(const int2 *__restrict__ cnt, int64_t N, int32_t *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int2 c = cnt[i];
-    atomicMax(out, c.x);
-    atomicMax(out + 1, c.y);
+    const int2 c = i < N ? cnt[i] : make_int2(0, 0);
+    const int mx = __reduce_max_sync(0xffffffffu, c.x), my = __reduce_max_sync(0xffffffffu, c.y);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, mx);
+        atomicMax(out + 1, my);
+    }
 }
 
 rbmd_status rbl_lists(rbmd_ctx *c, StepRef s)

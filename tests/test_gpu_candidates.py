@@ -201,3 +201,28 @@ def test_force_calls_use_the_candidates(prec):
     ctx.close()
     ref.close()
 
+
+
+@pytest.mark.parametrize("prec", [rb.FP64, rb.FP32])
+def test_conditional_rebuild_node_matches_plain_graph_nodes(prec, monkeypatch):
+    # the step graph puts the rebuild kernels in the body of a conditional node;
+    # with RBMD_GRAPH_COND=0 they are plain graph nodes that return at once on
+    # steps without a rebuild.  Same kernels, same bits; the node adds one kernel
+    # (the one that opens it) and the body holds the nine rebuild kernels.
+    s = synth.electrolyte(2500, seed=66, charges="2:1", n_types=2)
+    runs = []
+    for cond in ("1", "0"):
+        monkeypatch.setenv("RBMD_GRAPH_COND", cond)
+        ctx, _ = make_ctx(s, prec, seed=4, thermostat=1, dt=0.005, skin=0.02)  # rebuilds often
+        ctx.set_state_u(s.u, vel=s.v, step=0)
+        ctx.step(3)
+        ctx.step(5)  # the captured graph replayed
+        u, v, st = ctx.get_state_u()
+        runs.append((u, v, ctx.step_kernel_count(), ctx.rebuild_kernel_count(),
+                     ctx.candidate_rebuilds()))
+        ctx.close()
+    (ua, va, ka, ra, na), (ub, vb, kb, rb0, nb) = runs
+    assert na == nb and na >= 3
+    assert torch.equal(ua, ub) and torch.equal(va, vb)
+    assert rb0 == 0 and ra == 9
+    assert ka + ra == kb + 1
