@@ -65,6 +65,8 @@ __device__ __forceinline__ float exp_a(float x) { return expf(x); }
 __device__ __forceinline__ double exp_a(double x) { return exp(x); }
 __device__ __forceinline__ float sqrt_a(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_a(double x) { return sqrt(x); }
+__device__ __forceinline__ float rsqrt_a(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_a(double x) { return 1.0 / sqrt(x); }
 
 constexpr int ADJ_BLOCK = 128;
 
@@ -82,9 +84,14 @@ __device__ __forceinline__ void acc_add(real (&acc)[2 * TT], int t, real v)
     }
 }
 
-// One thread per cell-sorted atom k.  Symmetric weights for dE/dr and dE/dq;
-// one-sided weights W_kj for the type sums (each ordered pair counted once).
-// TT >= the number of LJ types.
+// One thread per cell-sorted atom k, over its core (weight W = 1), its batch
+// (W = w_k / 2) and its reverse batch (the atoms j whose batch holds k, W = w_j / 2):
+// the symmetric weights of dE/dr and dE/dq.  The eps and sigma sums follow the same
+// visits.  An ordered pair (k, j) of one-sided weight W_kj adds 1/2 W_kj du/d eps_kj
+// times d eps_kj/d eps_t = [t = t_k] a_kj + [t = t_j] a_jk (a_kj = 1/2 sqrt(eps_j /
+// eps_k), Eq. 4); the [t = t_j] part of (k, j) is the [t = t_k] part of the reversed
+// pair seen from k, so each visit adds W du/d eps_kj a_kj (and W du/d sigma_kj / 2)
+// to k's own type only.  TT >= the number of LJ types.
 template <typename real, int TT>
 __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
 {
@@ -122,8 +129,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
         const uint32_t id0 = (uint32_t)a.reps[sl.r].atom0;
         real gx = 0, gy = 0, gz = 0, gq = 0;
         real ak_e = 0, ak_s = 0;  // the type sums of k's own type, added to acc at the end
-        // one pair (k, js): W the symmetric weight of dE/dr and dE/dq, Wkj the
-        // one-sided weight of the type sums (0: counted from js's side)
+        // one pair (k, js) of symmetric weight W
         struct Nb {  // a neighbour's record; its counts only on the reverse batch
             uint4 B;
             int tj;
@@ -138,14 +144,14 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
             n.cj = counts ? a.ncount[js] : make_int2(0, 0);
             return n;
         };
-        auto pair = [&](const Nb &nb, real W, real Wkj) {
+        auto pair = [&](const Nb &nb, real W) {
             const uint4 B = nb.B;
             const real dx = (real)(int32_t)(B.x - A.x) * lscale;  // r_j - r_k
             const real dy = (real)(int32_t)(B.y - A.y) * lscale;
             const real dz = (real)(int32_t)(B.z - A.z) * lscale;
             const real r2 = dx * dx + dy * dy + dz * dz;
-            const real r = sqrt_a(r2);
-            const real rinv = (real)1 / r;
+            const real rinv = rsqrt_a(r2);
+            const real r = r2 * rinv;
             const int tj = nb.tj;
             const real qj = nb.qj;
             real eij, sij;
@@ -168,29 +174,22 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
             gy -= f * dy;
             gz -= f * dz;
             gq += W * a.ck * qj * er * rinv;
-            if (Wkj != (real)0) {
-                // one-sided: 1/2 W_kj du/d eps_kj d eps_kj/d eps_t (Eq. 4), same for sigma
-                const real hw = (real)0.5 * Wkj;
-                const real due = (real)4 * (s12 - s6);
-                real dus = (real)4 * eij * ((real)12 * s12 - (real)6 * s6);
-                real rkj, rjk;
-                if constexpr (TT <= 16) {
-                    dus *= s_is[tk * TT + tj];
-                    rkj = s_er[tk * TT + tj];
-                    rjk = s_er[tj * TT + tk];
-                } else {
-                    dus /= sij;
-                    rkj = (real)0.5 * sqrt_a(a.eps[tj] / a.eps[tk]);
-                    rjk = (real)0.5 * sqrt_a(a.eps[tk] / a.eps[tj]);
-                }
-                ak_e += hw * due * rkj;
-                acc_add<real, TT>(acc, tj, hw * due * rjk);
-                ak_s += hw * dus * (real)0.5;
-                acc_add<real, TT>(acc, TT + tj, hw * dus * (real)0.5);
+            // k's own type: W du/d eps_kj a_kj and W du/d sigma_kj / 2 (Eq. 4)
+            const real due = (real)4 * (s12 - s6);
+            real dus = (real)4 * eij * ((real)12 * s12 - (real)6 * s6);
+            real rkj;
+            if constexpr (TT <= 16) {
+                dus *= s_is[tk * TT + tj];
+                rkj = s_er[tk * TT + tj];
+            } else {
+                dus /= sij;
+                rkj = (real)0.5 * sqrt_a(a.eps[tj] / a.eps[tk]);
             }
+            ak_e += W * due * rkj;
+            ak_s += W * dus * (real)0.5;
         };
         // a list of n neighbours, each one's loads issued before the previous pair is
-        // computed; weight(nb, W, Wkj) gives the pair's weights
+        // computed; weight(nb) gives the pair's weight
         auto walk = [&](auto index, int n, bool counts, auto weight) {
             if (n <= 0) return;
             int32_t js = index(0);
@@ -198,27 +197,19 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
             for (int e = 0; e < n; ++e) {
                 const int32_t jn = e + 1 < n ? index(e + 1) : js;
                 const Nb nxt = load(jn, counts);
-                real W, Wkj;
-                weight(cur, W, Wkj);
-                pair(cur, W, Wkj);
+                pair(cur, weight(cur));
                 cur = nxt;
                 js = jn;
             }
         };
-        auto ones = [](const Nb &, real &W, real &Wkj) {
-            W = (real)1;
-            Wkj = (real)1;
-        };
+        auto ones = [](const Nb &) { return (real)1; };
         walk([&](int e) { return a.lcore[lidx(ks, e, N, a.CC)]; }, cnt.x, false, ones);
         if (a.exact) {
             walk([&](int e) { return a.sidx[id0 + (uint32_t)a.lshell[lidx(ks, e, N, a.CS)]]; },
                  cnt.y, false, ones);
         } else {
             walk([&](int e) { return a.bk[lidx(ks, e, N, a.p)]; }, nbk, false,
-                 [&](const Nb &, real &W, real &Wkj) {
-                     W = (real)0.5 * wk;
-                     Wkj = wk;
-                 });
+                 [&](const Nb &) { return (real)0.5 * wk; });
             // the reverse batch in ascending sorted index (the scatter's order is not
             // fixed): sorted in place, one row per thread
             int32_t *rrow = a.rb + lidx(ks, 0, N, a.RC);
@@ -244,10 +235,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
                     rrow[y + 1] = x;
                 }
             }
-            walk([&](int e) { return rrow[e]; }, nrb, true, [&](const Nb &nb, real &W, real &Wkj) {
+            walk([&](int e) { return rrow[e]; }, nrb, true, [&](const Nb &nb) {
                 const real wj = nb.cj.y > a.p ? (real)nb.cj.y / (real)a.p : (real)1;
-                W = (real)0.5 * wj;
-                Wkj = (real)0;
+                return (real)0.5 * wj;
             });
         }
         acc_add<real, TT>(acc, tk, ak_e);
