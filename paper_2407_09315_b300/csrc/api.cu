@@ -1298,10 +1298,25 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
     k_zero_slots<<<(R * (SCAL_COUNT - SCAL_EPAIR) + 255) / 256, 256, 0, c->stream>>>(
         c->scal, R, SCAL_EPAIR, SCAL_COUNT - SCAL_EPAIR);
     gprof_mark(c, 0);
+    // as in a force evaluation, the RBE part (which writes only its own scal slots)
+    // runs on the side stream beside the RBL part, when the stages are not timed
+    const bool fork = !(c->prm.flags & RBMD_NO_RBE) && !(c->prm.flags & RBMD_NO_RBL) && c->side &&
+                      !c->profiling;
     if (!(c->prm.flags & RBMD_NO_RBE)) {
-        s = rbe_sample(c, r);
+        const cudaStream_t main = c->stream;
+        if (fork) {
+            s = cuda_status(cudaEventRecord(c->ev_fork, main));
+            if (s == RBMD_OK) s = cuda_status(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+            c->stream = c->side;
+        }
+        if (s == RBMD_OK) s = rbe_sample(c, r);
         if (s == RBMD_OK) s = rbe_structure_factors(c);
         if (s == RBMD_OK) s = sum_modes(c);
+        if (fork) {
+            c->stream = main;
+            const rbmd_status sj = cuda_status(cudaEventRecord(c->ev_join, c->side));
+            if (s == RBMD_OK) s = sj;
+        }
     }
     gprof_mark(c, 1);
     if (s == RBMD_OK && !(c->prm.flags & RBMD_NO_RBL)) {
@@ -1325,6 +1340,10 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
         gprof_mark(c, 3);
     }
     if (s == RBMD_OK) s = md_kinetic(c, SCAL_KE_TRUE);
+    if (fork) {
+        const rbmd_status sj = cuda_status(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        if (s == RBMD_OK) s = sj;
+    }
     gprof_mark(c, 4);
     std::vector<double> h((size_t)R * SCAL_COUNT);
     int32_t hi[4];

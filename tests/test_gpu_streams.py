@@ -2,7 +2,8 @@
 
 A force evaluation runs the RBE sampling and structure factors (Algorithm 1
 steps 1-2) on a second stream beside the cell sort and the RBL kernels
-(Algorithm 2), and joins them before the RBE force pass.  The two parts share
+(Algorithm 2), and joins them before the RBE force pass; an energy evaluation
+runs its RBE part (with the mode sums) there too.  The two parts share
 no buffer, so the result must be the one-stream result bit for bit:
 trajectories, forces and energies, for one system and for a batch.
 RBMD_ONE_STREAM=1 at context creation selects the one-stream evaluation.
@@ -51,6 +52,24 @@ def test_two_streams_same_trajectory(sys5k, prec, thermostat, monkeypatch):
     e1, e2 = one.energy(6), two.energy(6)
     for k in e1:
         assert np.array_equal(e1[k], e2[k]), k
+    one.close()
+    two.close()
+
+
+@pytest.mark.parametrize("prec", [rb.FP64, rb.FP32])
+def test_two_streams_energy_and_gradients(sys5k, prec, monkeypatch):
+    import torch
+
+    one, two = _pair(sys5k, prec, monkeypatch, rbe_P=120, seed=9)
+    e1, e2 = one.energy(5), two.energy(5)
+    for k in e1:
+        assert np.array_equal(e1[k], e2[k]), k
+    g1, g2 = one.energy_backward(5), two.energy_backward(5)
+    for a, b in zip(g1, g2):
+        if isinstance(a, torch.Tensor):
+            assert torch.equal(a, b)
+        else:
+            assert np.array_equal(a, b)
     one.close()
     two.close()
 
