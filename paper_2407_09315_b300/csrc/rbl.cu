@@ -2145,7 +2145,11 @@ static rbmd_status verlet_prepare_t(rbmd_ctx *c)
                                                   flag, c->N, c->err);
     RBMD_LAUNCH_CHECK();
     rbmd_status st = RBMD_OK;
-    if (c->capturing && c->cond_nodes && vl_rebuild_node<real>(c, flag, &st)) return st;
+    if (c->capturing && c->cond_nodes && vl_rebuild_node<real>(c, flag, &st)) {
+        // a failed node fails this capture; the next one uses plain graph nodes
+        if (st != RBMD_OK) c->cond_nodes = false;
+        return st;
+    }
     return vl_rebuild<real>(c, flag);
 }
 
