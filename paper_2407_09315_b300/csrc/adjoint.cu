@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
         }
         __syncthreads();
     }
-    // per-thread type sums in the working precision (a few tens of pairs; the
-    // block and type sums are FP64)
+    // per-thread type sums in the working precision (a few tens of pairs), warp sums
+    // too; the block and type sums are FP64
     real acc[2 * TT];
 #pragma unroll
     for (int t = 0; t < 2 * TT; ++t) acc[t] = 0;
@@ -250,14 +250,15 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
         }
         if (a.dq) a.dq[id] += (real)a.g * gq;
     }
-    // per-type block partials, fixed order (eps of type t at acc[t], sigma at acc[TT + t])
+    // per-type block partials, fixed order (eps of type t at acc[t], sigma at acc[TT + t]):
+    // warp sums in the working precision, then FP64
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int t = 0; t < 2 * TT; ++t) {
         if ((t % TT) >= a.T) continue;
-        double v = (double)acc[t] * a.g;
+        real v = acc[t];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) s_t[t][warp] = v;
+        if (lane == 0) s_t[t][warp] = (double)v * a.g;
     }
     __syncthreads();
     if (threadIdx.x < 2 * a.T) {
