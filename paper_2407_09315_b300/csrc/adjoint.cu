@@ -54,6 +54,7 @@ template <typename real> struct AdjArgs {
     int CC, CS, p, T, exact;
     real ck, alpha, sqrt_alpha, c2;
     const real *eps, *sig;  // per type (host values copied in)
+    const real *pairtab;    // [4][T][T]: 1/2 sqrt(eps_t2/eps_t1), 1/sigma_t1t2, eps_t1t2, sigma_t1t2
     double g;               // grad_out
     real *dpos, *dq;
     double *tpart;          // [blocks][2T] per-block (d eps, d sigma) partial sums
@@ -101,12 +102,14 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_rbl_adjoint(AdjArgs<real> a)
     constexpr int TP = TT <= 16 ? TT * TT : 1;
     __shared__ real s_er[TP], s_is[TP], s_e[TP], s_s[TP];  // + eps_kj and sigma_kj (Eq. 4)
     if constexpr (TT <= 16) {
-        for (int u = threadIdx.x; u < a.T * a.T; u += blockDim.x) {
+        // from the table the host computed once per set of parameters
+        const int T2 = a.T * a.T;
+        for (int u = threadIdx.x; u < T2; u += blockDim.x) {
             const int t1 = u / a.T, t2 = u % a.T;
-            s_er[t1 * TT + t2] = (real)(0.5 * sqrt((double)a.eps[t2] / (double)a.eps[t1]));
-            s_is[t1 * TT + t2] = (real)(1.0 / (0.5 * ((double)a.sig[t1] + (double)a.sig[t2])));
-            s_e[t1 * TT + t2] = sqrt_a(a.eps[t1] * a.eps[t2]);
-            s_s[t1 * TT + t2] = (real)0.5 * (a.sig[t1] + a.sig[t2]);
+            s_er[t1 * TT + t2] = a.pairtab[u];
+            s_is[t1 * TT + t2] = a.pairtab[T2 + u];
+            s_e[t1 * TT + t2] = a.pairtab[2 * T2 + u];
+            s_s[t1 * TT + t2] = a.pairtab[3 * T2 + u];
         }
         __syncthreads();
     }
@@ -373,6 +376,7 @@ static rbmd_status adjoint_t(rbmd_ctx *c, double g, void *dpos, void *dq, double
         a.c2 = (real)(2.0 * sqrt(c->prm.alpha / kPi));
         a.eps = (const real *)c->adj_lj;
         a.sig = (const real *)c->adj_lj + c->T;
+        a.pairtab = (const real *)c->adj_lj + 2 * c->T;
         a.g = g;
         a.dpos = (real *)dpos;
         a.dq = (real *)dq;

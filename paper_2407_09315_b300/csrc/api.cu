@@ -322,26 +322,44 @@ size_t real_size(const rbmd_ctx *c) { return c->fp64 ? sizeof(double) : sizeof(f
 // (eps, sigma), from host arrays.
 rbmd_status upload_lj(rbmd_ctx *c, const double *eps, const double *sig)
 {
-    std::vector<double> ljd(2 * c->T), raw(2 * c->T);
-    std::vector<float> ljf(2 * c->T), rawf(2 * c->T);
-    for (int t = 0; t < c->T; ++t) {
+    const int T = c->T, T2 = T * T;
+    std::vector<double> ljd(2 * T), raw(2 * T + 4 * T2);
+    std::vector<float> ljf(2 * T), rawf(2 * T + 4 * T2);
+    for (int t = 0; t < T; ++t) {
         if (!(eps[t] >= 0.0) || !(sig[t] >= 0.0)) return RBMD_ERR_INVALID;
         ljd[t] = sqrt(eps[t]);
-        ljd[c->T + t] = 0.5 * sig[t];
+        ljd[T + t] = 0.5 * sig[t];
         raw[t] = eps[t];
-        raw[c->T + t] = sig[t];
+        raw[T + t] = sig[t];
     }
-    for (int t = 0; t < 2 * c->T; ++t) {
+    for (int t = 0; t < 2 * T; ++t) {
         ljf[t] = (float)ljd[t];
         rawf[t] = (float)raw[t];
     }
+    // the adjoint's type-pair factors (Eq. 4), from the eps and sigma it holds in
+    // its working precision: [t1 T + t2] = 1/2 sqrt(eps_t2 / eps_t1), 1 / sigma_t1t2,
+    // eps_t1t2, sigma_t1t2 (IEEE operations, the same bits as on the device)
+    for (int t1 = 0; t1 < T; ++t1)
+        for (int t2 = 0; t2 < T; ++t2) {
+            const int u = t1 * T + t2;
+            const double e1 = raw[t1], e2 = raw[t2], s1 = raw[T + t1], s2 = raw[T + t2];
+            raw[2 * T + u] = 0.5 * sqrt(e2 / e1);
+            raw[2 * T + T2 + u] = 1.0 / (0.5 * (s1 + s2));
+            raw[2 * T + 2 * T2 + u] = sqrt(e1 * e2);
+            raw[2 * T + 3 * T2 + u] = 0.5 * (s1 + s2);
+            const float f1 = rawf[t1], f2 = rawf[t2], g1 = rawf[T + t1], g2 = rawf[T + t2];
+            rawf[2 * T + u] = (float)(0.5 * sqrt((double)f2 / (double)f1));
+            rawf[2 * T + T2 + u] = (float)(1.0 / (0.5 * ((double)g1 + (double)g2)));
+            rawf[2 * T + 2 * T2 + u] = sqrtf(f1 * f2);
+            rawf[2 * T + 3 * T2 + u] = 0.5f * (g1 + g2);
+        }
     RBMD_CHECK_CUDA(cudaStreamSynchronize(c->stream));
     if (c->fp64) {
-        RBMD_CHECK_CUDA(cudaMemcpy(c->lj_d, ljd.data(), sizeof(double) * 2 * c->T, cudaMemcpyHostToDevice));
-        RBMD_CHECK_CUDA(cudaMemcpy(c->adj_lj, raw.data(), sizeof(double) * 2 * c->T, cudaMemcpyHostToDevice));
+        RBMD_CHECK_CUDA(cudaMemcpy(c->lj_d, ljd.data(), sizeof(double) * 2 * T, cudaMemcpyHostToDevice));
+        RBMD_CHECK_CUDA(cudaMemcpy(c->adj_lj, raw.data(), sizeof(double) * raw.size(), cudaMemcpyHostToDevice));
     } else {
-        RBMD_CHECK_CUDA(cudaMemcpy(c->lj_f, ljf.data(), sizeof(float) * 2 * c->T, cudaMemcpyHostToDevice));
-        RBMD_CHECK_CUDA(cudaMemcpy(c->adj_lj, rawf.data(), sizeof(float) * 2 * c->T, cudaMemcpyHostToDevice));
+        RBMD_CHECK_CUDA(cudaMemcpy(c->lj_f, ljf.data(), sizeof(float) * 2 * T, cudaMemcpyHostToDevice));
+        RBMD_CHECK_CUDA(cudaMemcpy(c->adj_lj, rawf.data(), sizeof(float) * rawf.size(), cudaMemcpyHostToDevice));
     }
     return RBMD_OK;
 }
@@ -889,7 +907,7 @@ rbmd_status init_ctx(const rbmd_params *prms, int32_t R, const void *pos, const 
     TRY(alloc_n(&c->ncount, (size_t)N));
     TRY(alloc_n(&c->bk, (size_t)N * p.rbl_p));
     if (p.rbl_p > 10) TRY(alloc_n(&c->heavy, (size_t)N));
-    TRY(dev_alloc(&c->adj_lj, 2 * (size_t)c->T * rs));
+    TRY(dev_alloc(&c->adj_lj, (2 * (size_t)c->T + 4 * (size_t)c->T * c->T) * rs));
     TRY(alloc_n(&c->adj_tpart, (size_t)c->nb128 * 2 * c->T));
     TRY(alloc_n(&c->adj_tsum, 2 * (size_t)c->T));
     TRY(alloc_n(&c->epart, EPART * (size_t)c->pair_parts));

@@ -364,7 +364,7 @@ struct rbmd_ctx {
     int sel_exact;        // RBMD_SELECT_EXACT: every batch by the exact slow path (tests)
     int sel_key_bits;     // RBMD_SELECT_KEY_BITS: fewer priority bits in the fast keys (tests)
     int list_cc, list_cs; // list capacities per atom
-    void *adj_lj;         // real [2T]: eps_t, sigma_t (adjoint)
+    void *adj_lj;         // real [2T + 4T^2]: eps_t, sigma_t, then the adjoint's type-pair factors
     double *adj_tpart;    // [adjoint blocks][2T]
     double *adj_tsum;     // [2T]
 
