@@ -1365,14 +1365,20 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
     gprof_mark(c, 4);
     std::vector<double> h((size_t)R * SCAL_COUNT);
     int32_t hi[4];
+    int herr = 0;  // the latched error word, read back with the results
     if (s == RBMD_OK)
         s = cuda_status(cudaMemcpyAsync(h.data(), c->scal, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
     if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(hi, c->ibuf, sizeof(hi), cudaMemcpyDeviceToHost, c->stream));
+    if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
     s = leave(c, s);
     if (s != RBMD_OK) return s;
     gprof_collect(c, 0, RBMD_PROFILE_FWD_STAGES);
-    RBMD_CHECK(check_latched(c));
+    if (herr != 0) {
+        const int z = 0;
+        cudaMemcpy(c->err, &z, sizeof(int), cudaMemcpyHostToDevice);
+        return (rbmd_status)herr;
+    }
     // the lists (complete when no atom overflowed: hi[2]) and the modes and
     // structure factors of this state and step stay for rbmd_energy_backward
     if (!(c->prm.flags & RBMD_NO_RBL) && hi[2] == 0) {

@@ -59,3 +59,15 @@ def test_latched_error_is_reported_by_the_next_sync():
     assert _code(ctx.sync) == 8  # RBMD_ERR_TIMEOUT
     ctx.sync()
     ctx.close()
+
+
+def test_latched_error_is_reported_by_the_next_energy_call():
+    # rbmd_energy reads the error word back with its results and clears it
+    s = synth.electrolyte(300, seed=55)
+    ctx, _ = make_ctx(s, rb.FP32)
+    ctx.debug_latch_error(8)
+    assert _code(lambda: ctx.energy(0)) == 8
+    e = ctx.energy(0)
+    assert np.isfinite(e["e_potential"])
+    ctx.sync()
+    ctx.close()
