@@ -470,8 +470,22 @@ static bool candidates_for_call(rbmd_ctx *c, int accumulate)
     if (c->vl_dirty) {
         if (cudaMemsetAsync(c->ibuf + 4, 1, sizeof(int32_t), c->stream) != cudaSuccess) return false;
         c->vl_dirty = false;
+        c->vl_current = false;  // the rebuild has to run
     }
     return true;
+}
+
+// verlet_prepare outside the step graph, skipped when the sorted positions and the
+// candidate lists are already those of the current state: the last one ran on
+// these positions (they move only in the step's drift, which clears the mark, and
+// in the calls that set a new state, which make the layout dirty) and nothing
+// re-sorted the atoms since.
+static rbmd_status verlet_prepare_call(rbmd_ctx *c)
+{
+    if (!c->capturing && c->vl_current) return RBMD_OK;
+    const rbmd_status s = verlet_prepare(c);
+    c->vl_current = s == RBMD_OK && !c->capturing;
+    return s;
 }
 
 // energy: also the potential's terms into scal (SCAL_EPAIR, SCAL_ERBE; the energy bath)
@@ -507,7 +521,7 @@ rbmd_status forces_into(rbmd_ctx *c, StepRef s, void *force, int accumulate, boo
         NvtxRange nvtx_range("rbl");
         rbmd_status st = RBMD_OK;
         if (verlet && !accumulate) {
-            st = verlet_prepare(c);
+            st = verlet_prepare_call(c);
             if (marks) prof_mark(c, 2);  // stages 3 and 4 are marked inside
             if (st == RBMD_OK) st = rbl_pairs_verlet(c, s, force, marks, energy);
         } else {
@@ -568,6 +582,7 @@ rbmd_status record_step(rbmd_ctx *c)
     // they re-sort only at a rebuild)
     const bool bin = !(c->prm.flags & RBMD_NO_RBL) && !c->verlet;
     RBMD_CHECK(md_kick_drift(c, bin));
+    c->vl_current = false;  // the drift moved the atoms
     bool kicked = false;
     RBMD_CHECK(forces_into(c, next, c->force, 0, false, true, &next, &kicked, bin, c->verlet,
                            c->prm.thermostat == 4));
@@ -1157,8 +1172,9 @@ rbmd_status rbmd_forces_host(rbmd_ctx *c, const void *pos, void *force, int64_t 
     cudaEventRecord(c->ev_join, c->side);
     // the short-range part (same kernels as rbmd_forces), then the RBE force pass
     // chunk by chunk, each chunk's forces copied out while the next is computed
+    c->vl_current = false;  // new positions
     if (vl) {
-        if (st == RBMD_OK) st = verlet_prepare(c);
+        if (st == RBMD_OK) st = verlet_prepare_call(c);
         if (st == RBMD_OK) st = rbl_pairs_verlet(c, s, dev, false);
     } else {
         if (st == RBMD_OK) st = cells_build(c, true);
@@ -1199,6 +1215,7 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
         if (cudaMemsetAsync(c->ibuf + 4, 1, sizeof(int32_t), c->stream) != cudaSuccess)
             return leave(c, RBMD_ERR_CUDA);
         c->vl_dirty = false;
+        c->vl_current = false;  // the rebuild has to run
     }
     if (!c->have_force) {
         k_set_i64<<<1, 1, 0, c->stream>>>(c->d_step, c->step);
@@ -1278,6 +1295,8 @@ rbmd_status rbmd_step(rbmd_ctx *c, int64_t n_steps)
         }
     }
     c->step += n_steps;
+    // the step's candidate-list check ran after its drift: the lists are current
+    c->vl_current = c->verlet && !(c->prm.flags & RBMD_NO_RBL);
     return leave(c, RBMD_OK);
 }
 
@@ -1340,7 +1359,7 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
     if (s == RBMD_OK && !(c->prm.flags & RBMD_NO_RBL)) {
         // through the candidate lists when the context keeps them, else the cell walk
         const bool vl = candidates_for_call(c, 0);
-        s = vl ? verlet_prepare(c) : cells_build(c);
+        s = vl ? verlet_prepare_call(c) : cells_build(c);
         gprof_mark(c, 2);
         if (s == RBMD_OK)
             s = vl ? rbl_pairs_verlet(c, r, c->scratch_force, false, true)
@@ -1572,7 +1591,7 @@ rbmd_status rbmd_energy_backward(rbmd_ctx *c, int64_t step, double grad_out, voi
     if (!(c->prm.flags & RBMD_NO_RBL) && !have_lists && candidates_for_call(c, 0)) {
         // the lists from the candidates, when no atom overflows a capacity
         int32_t ovf = 1;
-        s = verlet_prepare(c);
+        s = verlet_prepare_call(c);
         if (s == RBMD_OK) s = rbl_lists_verlet(c, r);
         if (s == RBMD_OK) s = cuda_status(cudaMemcpyAsync(&ovf, c->ibuf + 2, sizeof(ovf), cudaMemcpyDeviceToHost, c->stream));
         if (s == RBMD_OK) s = cuda_status(cudaStreamSynchronize(c->stream));

@@ -379,6 +379,7 @@ struct rbmd_ctx {
     int32_t *adj_rb = nullptr;  // reverse batches of the adjoint, [N][adj_rb_cap] (on first use)
     int adj_rb_cap = 0;
     int64_t lists_step = 0, rho_step = 0;
+    bool vl_current = false;  // the sorted positions and candidate lists are those of the state
     bool vl_dirty;        // the sorted layout changed outside the step: rebuild before the next
     double skin;
     int vl_cv;            // candidate capacity per atom

@@ -226,3 +226,51 @@ def test_conditional_rebuild_node_matches_plain_graph_nodes(prec, monkeypatch):
     assert torch.equal(ua, ub) and torch.equal(va, vb)
     assert rb0 == 0 and ra == 9
     assert ka + ra == kb + 1
+
+
+@pytest.mark.parametrize("prec", [rb.FP64, rb.FP32])
+def test_calls_after_a_step_reuse_its_lists(prec):
+    # force, energy and gradient calls right after a step skip the candidate check
+    # (the step's check ran on these positions); a fresh context set to the same
+    # state checks and rebuilds: the same lists, so the same forces bit for bit (each
+    # atom's sum runs in a canonical order) and the same energies and gradients up to
+    # the order of the sums over atoms, which follows the sorted layout
+    s = synth.electrolyte(3000, seed=67, charges="2:1", n_types=2)
+    a, _ = make_ctx(s, prec, seed=5, thermostat=1, dt=0.004)
+    a.set_state_u(s.u, vel=s.v, step=0)
+    a.step(4)
+    ua, va, st = a.get_state_u()
+    b, _ = make_ctx(s, prec, seed=5, thermostat=1, dt=0.004)
+    b.set_state_u(ua, vel=va, step=st)
+    (Ea, Fa, Ga), (Eb, Fb, Gb) = ((c.energy(st), c.forces(st), c.energy_backward(st))
+                                  for c in (a, b))
+    tol = 1e-12 if prec == rb.FP64 else 2e-6
+    assert Ea["max_shell"] == Eb["max_shell"]
+    for k in ("e_coul_real", "e_lj", "e_rbe"):
+        assert abs(Ea[k] - Eb[k]) <= tol * abs(Eb[k]), k
+    assert np.allclose(Ea["virial"], Eb["virial"], rtol=tol, atol=tol * np.abs(Eb["virial"]).max())
+    assert torch.equal(Fa, Fb)
+    for x, y in zip(Ga, Gb):
+        x, y = (to_np(x), to_np(y)) if isinstance(x, torch.Tensor) else (np.asarray(x), np.asarray(y))
+        assert rel_err(x, y) <= tol
+    a.close()
+    b.close()
+
+
+def test_a_step_after_a_cell_walk_and_a_new_state_checks_the_lists():
+    # a force call marks the lists current; a cell walk re-sorts the atoms and a new
+    # state replaces the positions: the next step must rebuild, as a fresh context does
+    s = synth.electrolyte(2500, seed=68, charges="2:1", n_types=2)
+    a, _ = make_ctx(s, rb.FP32, seed=6, thermostat=1)
+    a.forces(1)
+    a.rbl_lists(1)
+    a.set_state_u(s.u, vel=s.v, step=0)
+    a.step(3)
+    b, _ = make_ctx(s, rb.FP32, seed=6, thermostat=1)
+    b.set_state_u(s.u, vel=s.v, step=0)
+    b.step(3)
+    ua, va, _ = a.get_state_u()
+    ub, vb, _ = b.get_state_u()
+    assert torch.equal(ua, ub) and torch.equal(va, vb)
+    a.close()
+    b.close()
