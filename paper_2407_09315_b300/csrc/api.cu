@@ -1349,6 +1349,8 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
         if (s == RBMD_OK) s = rbe_sample(c, r);
         if (s == RBMD_OK) s = rbe_structure_factors(c);
         if (s == RBMD_OK) s = sum_modes(c);
+        // the kinetic energy (velocities only, its own scal slot) there too
+        if (s == RBMD_OK && fork) s = md_kinetic(c, SCAL_KE_TRUE);
         if (fork) {
             c->stream = main;
             const rbmd_status sj = cuda_status(cudaEventRecord(c->ev_join, c->side));
@@ -1376,7 +1378,7 @@ rbmd_status rbmd_energy_batch(rbmd_ctx *c, int64_t step, rbmd_energy_terms *out)
         gprof_mark(c, 2);
         gprof_mark(c, 3);
     }
-    if (s == RBMD_OK) s = md_kinetic(c, SCAL_KE_TRUE);
+    if (s == RBMD_OK && !fork) s = md_kinetic(c, SCAL_KE_TRUE);
     if (fork) {
         const rbmd_status sj = cuda_status(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
         if (s == RBMD_OK) s = sj;
